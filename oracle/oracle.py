@@ -1,0 +1,175 @@
+"""ctypes wrapper of the plain FP64 CPU oracle (oracle/liboracle.so).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the CPU-baseline leg of
+the benchmark.  It takes grid/parameter objects by duck typing (attributes nx, ny, x0, ...,
+nu, tau_model, tau0, bc, wall_T, wall_U, wall_keep_es_term) and numpy arrays in the layouts
+Q[6][ny][nx], G[ny][nx][nv2][nv1], H[4][ny][nx].
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+
+
+class OrcGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("nv1", ctypes.c_int), ("nv2", ctypes.c_int),
+                ("v1min", ctypes.c_double), ("v1max", ctypes.c_double),
+                ("v2min", ctypes.c_double), ("v2max", ctypes.c_double)]
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("tau_model", ctypes.c_int), ("tau0", ctypes.c_double),
+                ("bc", ctypes.c_int * 4), ("wall_T", ctypes.c_double * 4),
+                ("wall_U", ctypes.c_double * 4), ("wall_keep_es_term", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        G, P = ctypes.POINTER(OrcGrid), ctypes.POINTER(OrcParams)
+        L.orc_step.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.orc_step.restype = ctypes.c_int
+        L.orc_dt_for_cfl.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int)]
+        L.orc_dt_for_cfl.restype = ctypes.c_double
+        L.orc_prims.argtypes = [P, _c_double_p, _c_double_p]
+        L.orc_prims.restype = ctypes.c_int
+        L.orc_maxwellian_gauss.argtypes = [P, _c_double_p, ctypes.c_double, ctypes.c_double,
+                                           _c_double_p, _c_double_p]
+        L.orc_maxwellian_gauss.restype = None
+        L.orc_project.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, _c_double_p, _c_double_p]
+        L.orc_project.restype = None
+        L.orc_kfvs_half.argtypes = [_c_double_p, ctypes.c_int, _c_double_p, _c_double_p]
+        L.orc_kfvs_half.restype = None
+        L.orc_wall_R.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.orc_wall_R.restype = ctypes.c_double
+        L.orc_trbdf2_W.argtypes = [ctypes.c_double] * 4
+        L.orc_trbdf2_W.restype = ctypes.c_double
+        L.orc_ghat.argtypes = [G, P, _c_double_p, ctypes.c_double, _c_double_p]
+        L.orc_ghat.restype = ctypes.c_int
+        L.orc_num_threads.argtypes = []
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _grid(g) -> OrcGrid:
+    return OrcGrid(int(g.nx), int(g.ny), float(g.x0), float(g.x1), float(g.y0), float(g.y1),
+                   int(g.nv1), int(g.nv2), float(g.v1min), float(g.v1max),
+                   float(g.v2min), float(g.v2max))
+
+
+def _params(p) -> OrcParams:
+    o = OrcParams()
+    o.nu = float(p.nu)
+    o.tau_model = int(p.tau_model)
+    o.tau0 = float(p.tau0)
+    for s in range(4):
+        o.bc[s] = int(p.bc[s])
+        o.wall_T[s] = float(p.wall_T[s])
+        o.wall_U[s] = float(p.wall_U[s])
+    o.wall_keep_es_term = int(p.wall_keep_es_term)
+    return o
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_c_double_p)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def step(grid, params, Q, G, dt, eps, nsteps=1):
+    """Return (Q, G, H) after nsteps steps; inputs are not modified."""
+    Q = np.array(Q, dtype=np.float64, order="C", copy=True)
+    G = np.array(G, dtype=np.float64, order="C", copy=True)
+    H = np.zeros((4, grid.ny, grid.nx), dtype=np.float64)
+    assert Q.size == 6 * grid.nx * grid.ny
+    assert G.size == grid.nx * grid.ny * grid.nv1 * grid.nv2
+    gg, pp = _grid(grid), _params(params)
+    rc = lib().orc_step(ctypes.byref(gg), ctypes.byref(pp), _ptr(Q), _ptr(G), _ptr(H),
+                        float(dt), float(eps), int(nsteps))
+    if rc != 0:
+        raise OracleError("orc_step returned %d" % rc)
+    return Q, G, H
+
+
+def dt_for_cfl(grid, cfl, t_final, form):
+    n = ctypes.c_int(0)
+    gg = _grid(grid)
+    dt = lib().orc_dt_for_cfl(ctypes.byref(gg), float(cfl), float(t_final), int(form),
+                              ctypes.byref(n))
+    return dt, n.value
+
+
+def prims(params, q):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros(8)
+    pp = _params(params)
+    rc = lib().orc_prims(ctypes.byref(pp), _ptr(q), _ptr(out))
+    if rc:
+        raise OracleError("non-physical state")
+    return out
+
+
+def maxwellian_gauss(params, q, v1, v2):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    m, g = ctypes.c_double(), ctypes.c_double()
+    pp = _params(params)
+    lib().orc_maxwellian_gauss(ctypes.byref(pp), _ptr(q), float(v1), float(v2),
+                               ctypes.byref(m), ctypes.byref(g))
+    return m.value, g.value
+
+
+def project(grid, rho, u1, u2, T, F):
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros_like(F)
+    gg = _grid(grid)
+    lib().orc_project(ctypes.byref(gg), float(rho), float(u1), float(u2), float(T),
+                      _ptr(F), _ptr(out))
+    return out
+
+
+def kfvs_half(q, direction):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    Fp, Fm = np.zeros(6), np.zeros(6)
+    lib().orc_kfvs_half(_ptr(q), int(direction), _ptr(Fp), _ptr(Fm))
+    return Fp, Fm
+
+
+def wall_R(ua, Taa, Tw, sign):
+    return lib().orc_wall_R(float(ua), float(Taa), float(Tw), int(sign))
+
+
+def trbdf2_W(tau, nu, eps, dt):
+    return lib().orc_trbdf2_W(float(tau), float(nu), float(eps), float(dt))
+
+
+def ghat(grid, params, Q, eps):
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    out = np.zeros((grid.ny, grid.nx, grid.nv2, grid.nv1))
+    gg, pp = _grid(grid), _params(params)
+    rc = lib().orc_ghat(ctypes.byref(gg), ctypes.byref(pp), _ptr(Q), float(eps), _ptr(out))
+    if rc:
+        raise OracleError("orc_ghat returned %d" % rc)
+    return out
+
+
+def num_threads():
+    return lib().orc_num_threads()

@@ -1,0 +1,377 @@
+"""Pins of the plain FP64 CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: numbers printed in the paper,
+closed forms, brute-force quadrature, an independently coded TR-BDF2 step, the exact Euler
+Riemann solution, or invariants (conservation, preserved equilibria).  A plausible slip in the
+oracle (a dropped term, a flipped sign, a swapped index, the downwind KFVS reading) fails at
+least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_21832_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ---------------------------------------------------------------------------------------------
+# time-step rule: step counts printed in Sections 4.2 and 6.2
+# ---------------------------------------------------------------------------------------------
+def test_dt_rule_matches_printed_step_counts():
+    with open(os.path.join(GOLDEN, "dt_rule.json")) as f:
+        fx = json.load(f)
+    for c in fx["cases"]:
+        g = I.Grid(nx=c["nx"], ny=c["ny"], x0=c["x0"], x1=c["x1"], y0=c["y0"], y1=c["y1"],
+                   nv1=14, nv2=14, v1min=-c["vmax"], v1max=c["vmax"], v2min=-c["vmax"],
+                   v2max=c["vmax"])
+        dt, n = O.dt_for_cfl(g, c["cfl"], c["t_final"], c["form"])
+        assert n == c["nsteps"], c["name"]
+        assert abs(dt - c["dt"]) <= c["dt_rtol"] * c["dt"], c["name"]
+        dx = (c["x1"] - c["x0"]) / c["nx"]
+        dy = (c["y1"] - c["y0"]) / c["ny"]
+        cfl = dt * c["vmax"] / dx if c["ny"] == 1 else dt * (c["vmax"] / dx + c["vmax"] / dy)
+        assert abs(cfl - c["cfl_after"]) <= c["cfl_rtol"] * c["cfl_after"], c["name"]
+    # the min form of Eq. (CFL-2D-part1) gives 107 steps for the cylindrical problem
+    c = fx["cases"][1]
+    g = I.Grid(nx=320, ny=320, x0=-1, x1=1, y0=-1, y1=1, v1min=-9, v1max=9, v2min=-9, v2max=9)
+    assert O.dt_for_cfl(g, 0.95, 0.07, I.CFL_MIN)[1] == 107
+    # the 1D-2V Sod workload: dt = 0.5 * (1/200) / 8 and exactly 640 steps to t = 0.2
+    p = I.sod_1d2v()
+    dt, n = O.dt_for_cfl(p.grid, 0.5, 0.2, I.CFL_SUM)
+    assert n == 640 and abs(dt - 3.125e-4) < 1e-18
+
+
+# ---------------------------------------------------------------------------------------------
+# KFVS half-range fluxes against brute-force quadrature of int v_d m(v) G dv over a half space
+# ---------------------------------------------------------------------------------------------
+def _gauss_legendre_box(lo, hi, n):
+    x, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (hi - lo) * x + 0.5 * (hi + lo), 0.5 * (hi - lo) * w
+
+
+def _half_flux_quadrature(q, direction, positive):
+    rho = q[0]
+    u = np.array([q[1], q[2]]) / rho
+    P = np.array([[q[3] - rho * u[0] ** 2, q[4] - rho * u[0] * u[1]],
+                  [q[4] - rho * u[0] * u[1], q[5] - rho * u[1] ** 2]])
+    Th = P / rho
+    Ti = np.linalg.inv(Th)
+    L = 14.0 * math.sqrt(max(Th[0, 0], Th[1, 1]))
+    d = direction - 1
+    o = 1 - d
+    # normal velocity on (0, u_d + L) or (u_d - L, 0); tangential on u_o -+ L, split at u_o
+    if positive:
+        vn, wn = _gauss_legendre_box(0.0, max(u[d] + L, 1e-3), 160)
+    else:
+        vn, wn = _gauss_legendre_box(min(u[d] - L, -1e-3), 0.0, 160)
+    vt1, wt1 = _gauss_legendre_box(u[o] - L, u[o], 120)
+    vt2, wt2 = _gauss_legendre_box(u[o], u[o] + L, 120)
+    vt, wt = np.concatenate([vt1, vt2]), np.concatenate([wt1, wt2])
+    VN, VT = np.meshgrid(vn, vt, indexing="ij")
+    W = wn[:, None] * wt[None, :]
+    v = [None, None]
+    v[d], v[o] = VN, VT
+    c1, c2 = v[0] - u[0], v[1] - u[1]
+    quad = Ti[0, 0] * c1 * c1 + 2 * Ti[0, 1] * c1 * c2 + Ti[1, 1] * c2 * c2
+    G = rho / (2 * math.pi * math.sqrt(np.linalg.det(Th))) * np.exp(-0.5 * quad)
+    m = [np.ones_like(c1), v[0], v[1], v[0] ** 2, v[0] * v[1], v[1] ** 2]
+    return np.array([np.sum(W * v[d] * mm * G) for mm in m])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_kfvs_half_fluxes_match_quadrature(seed):
+    rng = I.SplitMix64(seed)
+    rho = rng.uniform(0.3, 2.0)
+    u1, u2 = rng.uniform(-1.5, 1.5), rng.uniform(-1.5, 1.5)
+    T = rng.uniform(0.4, 1.6)
+    a, s = rng.uniform(-0.3, 0.3) * T, rng.uniform(-0.3, 0.3) * T
+    q = I.q_from_prims(np.array(rho), u1, u2, T, a, s)
+    for direction in (1, 2):
+        Fp, Fm = O.kfvs_half(q, direction)
+        Rp = _half_flux_quadrature(q, direction, True)
+        Rm = _half_flux_quadrature(q, direction, False)
+        scale = np.abs(Rp) + np.abs(Rm) + 1e-300
+        assert np.all(np.abs(Fp - Rp) <= 1e-11 * scale.max()), (direction, Fp, Rp)
+        assert np.all(np.abs(Fm - Rm) <= 1e-11 * scale.max()), (direction, Fm, Rm)
+
+
+# ---------------------------------------------------------------------------------------------
+# projector Pi_M: reproduces the null-space basis and annihilates a function orthogonal to it
+# ---------------------------------------------------------------------------------------------
+def test_projector_identities():
+    g = I.Grid(nx=1, ny=1, nv1=32, nv2=32)
+    rho, u1, u2, T = 1.3, 0.4, -0.25, 0.9
+    v1, v2 = g.v1()[None, :], g.v2()[:, None]
+    c1, c2 = v1 - u1, v2 - u2
+    M = rho / (2 * math.pi * T) * np.exp(-(c1 ** 2 + c2 ** 2) / (2 * T))
+    basis = [np.ones_like(c1 * c2), c1 / math.sqrt(T) + 0 * c2, c2 / math.sqrt(T) + 0 * c1,
+             (c1 ** 2 + c2 ** 2) / (2 * T) - 1]
+    for b in basis:
+        F = b * M
+        PF = O.project(g, rho, u1, u2, T, F)
+        assert np.max(np.abs(PF - F)) <= 1e-11 * np.max(np.abs(F))
+    # a Hermite function of degree 3 in c1 has zero projection
+    h3 = (c1 / math.sqrt(T)) ** 3 - 3 * c1 / math.sqrt(T) + 0 * c2
+    PF = O.project(g, rho, u1, u2, T, h3 * M)
+    assert np.max(np.abs(PF)) <= 1e-11 * np.max(np.abs(h3 * M))
+    # idempotence on an arbitrary function
+    F = np.cos(v1 * 0.7) * np.exp(-0.3 * v2 ** 2) + 0.1 * v1 * v2 * np.exp(-0.5 * (v1 ** 2 + v2 ** 2))
+    P1 = O.project(g, rho, u1, u2, T, F)
+    P2 = O.project(g, rho, u1, u2, T, P1)
+    assert np.max(np.abs(P2 - P1)) <= 1e-11 * np.max(np.abs(P1))
+
+
+# ---------------------------------------------------------------------------------------------
+# TR-BDF2 factor W against an independently coded two-stage TR-BDF2 step (gamma = 1/2)
+# ---------------------------------------------------------------------------------------------
+def _trbdf2_scalar(lam, h):
+    """y' = -lam y over one step h: trapezoid to h/2, then BDF2 on (0, h/2, h); returns y(h)/y0."""
+    y0 = 1.0
+    y1 = y0 * (1 - lam * h / 4) / (1 + lam * h / 4)
+    return (4 * y1 - y0) / 3 / (1 + lam * h / 3)
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-3, 1e-1, 10.0, 1e30])
+def test_trbdf2_factor(eps):
+    for tau, nu, dt in [(1.0, -0.5, 1e-3), (0.7, 0.0, 4e-2), (2.0, -1.0, 1e-4)]:
+        W = O.trbdf2_W(tau, nu, eps, dt)
+        lam = tau * (1 - nu) / eps     # decay rate of P11-P22 and P12 (Eq. 5-40)
+        ref = _trbdf2_scalar(lam, dt / 2)
+        assert abs(W - ref) <= 1e-14 * max(1.0, abs(ref))
+    # L-stability: W -> 0 as eps -> 0; W -> 1 as eps -> infinity
+    assert abs(O.trbdf2_W(1.0, -0.5, 1e-12, 1e-2)) < 1e-8
+    assert abs(O.trbdf2_W(1.0, -0.5, 1e30, 1e-2) - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------------------------------------
+# diffuse-wall densities: zero net mass flux through the wall
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_wall_density_zero_mass_flux(seed):
+    rng = I.SplitMix64(seed)
+    rho = rng.uniform(0.5, 2.0)
+    u1, u2 = rng.uniform(-0.8, 0.8), rng.uniform(-0.8, 0.8)
+    T = rng.uniform(0.5, 1.5)
+    a, s = rng.uniform(-0.2, 0.2) * T, rng.uniform(-0.2, 0.2) * T
+    q = I.q_from_prims(np.array(rho), u1, u2, T, a, s)
+    Th = np.array([q[3] / rho - u1 * u1, q[5] / rho - u2 * u2])
+    Tw = rng.uniform(0.6, 1.4)
+    for d, (ua, Taa) in enumerate([(u1, Th[0]), (u2, Th[1])]):
+        # wall on the low side: the wall emits v_d > 0, the cell loses its v_d < 0 half
+        out_low = _half_flux_quadrature(q, d + 1, False)[0]
+        rw = rho * O.wall_R(ua, Taa, Tw, -1)
+        assert abs(rw * math.sqrt(Tw / (2 * math.pi)) + out_low) < 1e-12
+        # wall on the high side
+        out_high = _half_flux_quadrature(q, d + 1, True)[0]
+        rw = rho * O.wall_R(ua, Taa, Tw, +1)
+        assert abs(-rw * math.sqrt(Tw / (2 * math.pi)) + out_high) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# ES Gaussian in Ghat: in the space-homogeneous state, eps * (second moments of Ghat) equals
+# rho (Tcal - T I) = nu (P - p I)  (Eq. 2-19, Eq. 5-75); its mass and momentum vanish
+# ---------------------------------------------------------------------------------------------
+def test_ghat_es_term_moments():
+    g = I.Grid(nx=3, ny=3, nv1=40, nv2=40, v1min=-10, v1max=10, v2min=-10, v2max=10)
+    for nu in (-0.5, -1.0, 0.3):
+        p = I.Params(nu=nu, bc=(I.PERIODIC,) * 4)
+        rho, u1, u2, T, a, s = 1.2, 0.3, -0.2, 0.9, 0.15, -0.1
+        Q = I.q_from_prims(np.full((3, 3), rho), u1, u2, T, a, s)
+        eps = 0.37
+        Gh = O.ghat(g, p, Q, eps)[1, 1]
+        v1, v2 = g.v1()[None, :], g.v2()[:, None]
+        c1, c2 = v1 - u1, v2 - u2
+        dv = (20.0 / 40) ** 2
+        assert abs(np.sum(Gh) * dv) < 1e-12
+        assert abs(np.sum(c1 * Gh) * dv) < 1e-12 and abs(np.sum(c2 * Gh) * dv) < 1e-12
+        P11, P12, P22 = rho * (T + a), rho * s, rho * (T - a)
+        pr = 0.5 * (P11 + P22)
+        assert abs(eps * np.sum(c1 * c2 * Gh) * dv - nu * P12) < 1e-12
+        assert abs(eps * np.sum((c1 ** 2 - c2 ** 2) * Gh) * dv - nu * (P11 - P22)) < 1e-12
+        assert abs(eps * np.sum((c1 ** 2 + c2 ** 2) * Gh) * dv) < 1e-12
+        assert abs(pr - rho * T) < 1e-14
+
+
+# ---------------------------------------------------------------------------------------------
+# Ghat transport term converges to -(1/tau)(I - Pi)[v . grad M] computed with exact derivatives
+# (Eq. 5-69): pins B, C and the discrete sigma and grad T of Eq. (5-97more)
+# ---------------------------------------------------------------------------------------------
+def _fields(x, y):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    u1 = 0.3 * np.cos(2 * np.pi * x + 0.4) * np.sin(2 * np.pi * y)
+    u2 = 0.25 * np.sin(2 * np.pi * (x + y))
+    T = 1.0 + 0.15 * np.cos(2 * np.pi * x) + 0.1 * np.sin(2 * np.pi * y + 1.0)
+    return rho, u1, u2, T
+
+
+def test_ghat_transport_term_converges_to_analytic_projection():
+    p = I.Params(nu=-0.5, bc=(I.PERIODIC,) * 4, tau_model=I.TAU_CONST, tau0=1.0)
+    errs = []
+    for n in (16, 32, 64):
+        g = I.Grid(nx=n, ny=n, nv1=32, nv2=32)
+        x, y = np.meshgrid(g.xc(), g.yc())
+        rho, u1, u2, T = _fields(x, y)
+        Q = I.q_from_prims(rho, u1, u2, T)
+        Gh = O.ghat(g, p, Q, 1e30)   # eps huge: only -(1/tau){B:sigma + C.grad T} M remains
+        i = j = n // 4               # cell centre at (0.25 - h/2, 0.25 - h/2) + h/2 ...
+        xc, yc = g.xc()[i], g.yc()[j]
+        h = 1e-5
+        v1, v2 = g.v1()[None, :], g.v2()[:, None]
+
+        def M_at(xx, yy):
+            r, a, b, t = _fields(xx, yy)
+            return r / (2 * np.pi * t) * np.exp(-((v1 - a) ** 2 + (v2 - b) ** 2) / (2 * t))
+
+        dMx = (M_at(xc + h, yc) - M_at(xc - h, yc)) / (2 * h)
+        dMy = (M_at(xc, yc + h) - M_at(xc, yc - h)) / (2 * h)
+        S = v1 * dMx + v2 * dMy
+        r, a, b, t = _fields(xc, yc)
+        ref = -(S - O.project(g, r, a, b, t, S))   # tau = 1
+        errs.append(np.max(np.abs(Gh[j, i] - ref)) / np.max(np.abs(ref)))
+    assert errs[-1] < 5e-3
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0   # second order in dx
+
+
+# ---------------------------------------------------------------------------------------------
+# invariants of the whole step
+# ---------------------------------------------------------------------------------------------
+def _totals(Q):
+    return np.array([Q[0].sum(), Q[1].sum(), Q[2].sum(), (Q[3] + Q[5]).sum()])
+
+
+def test_conservation_periodic():
+    g = I.Grid(nx=12, ny=10, nv1=16, nv2=16)
+    p = I.Params(nu=-0.5, bc=(I.PERIODIC,) * 4)
+    Q0 = I.smooth_state(g, seed=11)
+    G0 = I.seeded_g(g, seed=12, amp=0.02)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    for eps in (1e-3, 1e-1, 10.0):
+        Q, G, H = O.step(g, p, Q0, G0, dt, eps, 40)
+        t0, t1 = _totals(Q0), _totals(Q)
+        scale = np.array([t0[0], t0[0], t0[0], t0[3]])
+        assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (eps, t1 - t0)
+
+
+def test_specular_conserves_mass_and_energy():
+    g = I.Grid(nx=10, ny=12, nv1=16, nv2=16)
+    p = I.Params(nu=-0.5, bc=(I.SPECULAR,) * 4)
+    Q0 = I.smooth_state(g, seed=21, umax=0.2)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, 1e-2, 40)
+    t0, t1 = _totals(Q0), _totals(Q)
+    assert abs(t1[0] - t0[0]) <= 1e-13 * t0[0]
+    assert abs(t1[3] - t0[3]) <= 1e-13 * t0[3]
+
+
+def test_specular_mirror_symmetry():
+    """A state symmetric about x = 1/2 (u1 odd, others even) stays symmetric."""
+    g = I.Grid(nx=10, ny=6, nv1=12, nv2=12)
+    p = I.Params(nu=-0.5, bc=(I.SPECULAR,) * 4)
+    x, y = np.meshgrid(g.xc(), g.yc())
+    rho = 1 + 0.3 * np.cos(2 * np.pi * x) + 0.1 * np.cos(np.pi * y)
+    u1 = 0.2 * np.sin(2 * np.pi * x)
+    Q0 = I.q_from_prims(rho, u1, 0.05 * np.cos(np.pi * y), 1.0)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, 1e-2, 20)
+    sgn = np.array([1, -1, 1, 1, -1, 1])[:, None, None]
+    assert np.max(np.abs(Q - sgn * Q[:, :, ::-1])) < 1e-12
+    assert np.max(np.abs(G - G[:, ::-1, :, ::-1])) < 1e-12 * max(1e-300, np.max(np.abs(G)))
+
+
+@pytest.mark.parametrize("bc,u", [((I.PERIODIC,) * 4, (0.4, -0.3)), ((I.SPECULAR,) * 4, (0.0, 0.0)),
+                                  ((I.EXTRAP,) * 4, (0.3, 0.2)), ((I.DIFFUSE,) * 4, (0.0, 0.0))])
+def test_global_maxwellian_is_preserved(bc, u):
+    g = I.Grid(nx=6, ny=5, nv1=16, nv2=16)
+    p = I.Params(nu=-0.5, bc=bc, wall_T=(0.8,) * 4)
+    Q0 = I.q_from_prims(np.full((5, 6), 1.3), u[0], u[1], 0.8)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, 1e-2, 25)
+    assert np.max(np.abs(Q - Q0)) < 1e-13
+    assert np.max(np.abs(G)) < 1e-11
+
+
+def test_null_space_moments_of_g_vanish():
+    # v in [-10, 10]^2 so that the Gaussian tails beyond the mesh (the only source of
+    # non-orthogonality of the analytic projector on the midpoint grid) are below round-off
+    g = I.Grid(nx=8, ny=8, nv1=40, nv2=40, v1min=-10, v1max=10, v2min=-10, v2max=10)
+    p = I.Params(nu=-0.5, bc=(I.PERIODIC,) * 4)
+    Q0 = I.smooth_state(g, seed=31, umax=0.3)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, 5e-2, 10)
+    v1, v2 = g.v1()[None, :], g.v2()[:, None]
+    for w in (np.ones_like(v1 * v2), v1 + 0 * v2, v2 + 0 * v1, v1 ** 2 + v2 ** 2):
+        mom = np.einsum("jikl,kl->ji", G, w) * 0.25
+        assert np.max(np.abs(mom)) <= 1e-12 * np.max(np.abs(G))
+
+
+def test_space_homogeneous_es_relaxation_closed_form():
+    """Uniform rho, u, T with anisotropic P: P11 - P22 and P12 decay as W^(2N) exactly
+    (discrete closed form), tr P is preserved, and W^(2N) approaches exp(-tau(1-nu) t / eps)
+    with second order in dt (TR-BDF2)."""
+    g = I.Grid(nx=4, ny=4, nv1=24, nv2=24)
+    nu, eps, rho, T = -0.5, 0.05, 1.1, 1.0
+    p = I.Params(nu=nu, bc=(I.PERIODIC,) * 4, tau_model=I.TAU_RHO, tau0=1.0)
+    Q0 = I.q_from_prims(np.full((4, 4), rho), 0.0, 0.0, T, 0.2, -0.15)
+    D0 = Q0[3] - Q0[5]
+    errs = []
+    for nsteps in (10, 20, 40):
+        dt = 0.02 / nsteps
+        Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, eps, nsteps)
+        W = O.trbdf2_W(rho, nu, eps, dt)
+        D = Q[3] - Q[5]
+        assert np.max(np.abs(D - W ** (2 * nsteps) * D0)) < 1e-13
+        assert np.max(np.abs(Q[4] - W ** (2 * nsteps) * Q0[4])) < 1e-13
+        assert np.max(np.abs((Q[3] + Q[5]) - (Q0[3] + Q0[5]))) < 1e-13
+        errs.append(abs(W ** (2 * nsteps) - math.exp(-rho * (1 - nu) * 0.02 / eps)))
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+def test_ap_limit_g_equals_ghat():
+    """eps -> 0: one step gives G^{n+1} = Ghat^n (Eq. 5-98 limit)."""
+    g = I.Grid(nx=8, ny=6, nv1=16, nv2=16)
+    p = I.Params(nu=-0.5, bc=(I.PERIODIC,) * 4)
+    Q0 = I.smooth_state(g, seed=41, aniso=0.0)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    eps = 1e-13
+    Gh = O.ghat(g, p, Q0, eps)
+    Q, G, H = O.step(g, p, Q0, I.seeded_g(g, 42), dt, eps, 1)
+    assert np.max(np.abs(G - Gh)) <= 1e-7 * np.max(np.abs(Gh))
+
+
+def test_free_streaming_limit_converges():
+    """eps = 1e30: collisions vanish; the density of f = M + eps g follows the collisionless
+    solution of a Maxwellian with sinusoidal density, rho(x,t) = 1 + A sin(2 pi x) exp(-2 pi^2 T t^2),
+    with first-order convergence in dx."""
+    A, T, tf = 0.2, 1.0, 0.1
+    errs = []
+    for nx in (25, 50, 100):
+        g = I.Grid(nx=nx, ny=1, nv1=32, nv2=8)
+        p = I.Params(nu=-0.5, bc=(I.PERIODIC,) * 4)
+        x = g.xc()
+        Q0 = I.q_from_prims((1 + A * np.sin(2 * np.pi * x))[None, :], 0.0, 0.0, T)
+        dt, n = O.dt_for_cfl(g, 0.5, tf, I.CFL_SUM)
+        Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, 1e30, n)
+        exact = 1 + A * np.sin(2 * np.pi * x) * math.exp(-2 * math.pi ** 2 * T * tf ** 2)
+        errs.append(np.mean(np.abs(Q[0, 0] - exact)))
+    assert errs[0] / errs[1] > 1.6 and errs[1] / errs[2] > 1.6
+    assert errs[-1] < 2e-3
+
+
+@pytest.mark.slow
+def test_euler_limit_sod():
+    """Small eps: the 1D-2V Sod density approaches the exact Euler Riemann solution (gamma = 2)."""
+    from euler_exact import sample
+    errs = []
+    for eps in (1e-2, 1e-3, 1e-4):
+        pr = I.sod_1d2v(eps=eps)
+        Q, G, H = O.step(pr.grid, pr.params, pr.Q, pr.G, pr.dt, pr.eps, pr.nsteps)
+        x = pr.grid.xc()
+        ex = sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 2.0, (x - 0.5) / 0.2)
+        errs.append(np.mean(np.abs(Q[0, 0] - ex[0])))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.02
