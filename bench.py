@@ -1,0 +1,313 @@
+"""Benchmark of the micro-macro KFVS step on GB300.
+
+Workload: 2D-2V unit box, 256 x 256 cells x 32 x 32 velocities on [-8, 8]^2, specular walls on
+all sides, Gaussian density bump (seeded centre), u = 0, T = 1, g = 0, nu = -1/2, tau = rho,
+CFL 0.5 (sum form), FP64.  A step is one full time step (prims, micro x sweep, micro y sweep +
+relaxation + heat flux, macro x, macro y).  Inputs (two 537 MB FP64 phase-space buffers) are
+larger than L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--eps E] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the plain FP64 CPU oracle on this host's
+cores on a bounded sample of the same workload (a strip of rows per step).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "phase-space updates/s & %HBM roofline; mixed/learned vs FP64 at set L1 err"
+UNIT = "phase-cell updates/s"
+# Algorithmic FP64 flops per phase cell of the dominant kernel (y sweep 13, Ghat and blend 15,
+# heat-flux moments 8, Maxwellian/Gaussian from separable tables 3) and of the whole step
+# (plus the x sweep, 13); algorithmic bytes per phase cell and step: one read and one write of
+# g in FP64 plus the per-cell macro fields (6 + 6 + 4 + 4 doubles over nv = 1024 velocities).
+FLOPS_MICRO_Y = 39.0
+FLOPS_STEP = 52.0
+BYTES_PER_PHASE_FP64 = 16.0 + 160.0 / 1024.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP64 peak from unit counts and clocks: 152 SMs x 4 FP64 flops/clk/SM (2 FMA) x max SM clock.
+def fp64_peak_tflops(sm_max_mhz):
+    return 152 * 4 * sm_max_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(pr, rows, steps):
+    """Oracle (as it stands) on this host's cores over a strip of `rows` rows of the workload."""
+    from oracle import oracle as O
+    from paper_2509_21832_gb300 import inputs as I
+    g = pr.grid
+    rows = min(rows, g.ny)
+    dy = (g.y1 - g.y0) / g.ny
+    sub = I.Grid(nx=g.nx, ny=rows, x0=g.x0, x1=g.x1, y0=g.y0, y1=g.y0 + rows * dy, nv1=g.nv1,
+                 nv2=g.nv2, v1min=g.v1min, v1max=g.v1max, v2min=g.v2min, v2max=g.v2max)
+    Q = np.ascontiguousarray(pr.Q[:, :rows])
+    G = np.ascontiguousarray(pr.G[:rows])
+    t0 = time.perf_counter()
+    O.step(sub, pr.params, Q, G, pr.dt, pr.eps, steps)
+    t = time.perf_counter() - t0
+    return sub.nphase * steps / t, t, O.num_threads(), sub
+
+
+def run_reference(args, pr, world, rank):
+    if rank != 0:
+        return
+    from oracle import build as obuild
+    obuild.build()
+    rows = args.ref_rows
+    # warm-up steps (untimed), then K timed steps, each one oracle step over the strip
+    if args.warmup > 0:
+        cpu_baseline(pr, rows, args.warmup)
+    value, t, cores, sub = cpu_baseline(pr, rows, args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(pr, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d steps of a %dx%d-row strip (%d phase cells) of the "
+                                   "workload" % (args.steps, sub.nx, sub.ny, sub.nphase)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(pr, args):
+    g = pr.grid
+    return {"workload": "bump_specular_%dx%dx%dx%d_fp64" % (g.nx, g.ny, g.nv1, g.nv2),
+            "nx": g.nx, "ny": g.ny, "nv1": g.nv1, "nv2": g.nv2, "eps": pr.eps,
+            "dt": pr.dt, "bc": "specular x4", "nu": pr.params.nu, "tau": "rho",
+            "seed": pr.meta.get("seed"),
+            "l2": "inputs larger than L2: two %d MB FP64 phase-space buffers" % (g.nphase * 8 // 2**20),
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--eps", type=float, default=1e-1)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--nv", type=int, default=32)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=32)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_2509_21832_gb300 import inputs as I
+    pr = I.bump_specular(n=args.n, nv=args.nv, eps=args.eps, seed=0)
+    world, rank, local = dist_setup(args)
+
+    if args.impl == "reference":
+        run_reference(args, pr, world, rank)
+        return
+
+    import torch
+    from paper_2509_21832_gb300 import api
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    stream = torch.cuda.Stream()
+    solver = api.Solver(pr.grid, pr.params, stream=stream.cuda_stream)
+    Qd = torch.from_numpy(pr.Q).cuda()
+    Gd = torch.zeros(pr.grid.nphase, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    solver.set_state(Qd, Gd)
+    for _ in range(args.warmup):
+        solver.step(pr.dt, pr.eps, 1)
+    solver.sync()
+
+    def timed_run(K):
+        solver.set_timing(True)
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            solver.step(pr.dt, pr.eps, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        sampler.stop()
+        solver.sync()
+        ms = e0.elapsed_time(e1)
+        kt = solver.get_timing()
+        solver.set_timing(False)
+        return ms, kt, sampler.summary()
+
+    ms, kt, clocks = timed_run(args.steps)
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if set(clocks["reasons"]) & bad:
+        ms, kt, clocks = timed_run(args.steps)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+
+    nph = pr.grid.nphase
+    value = world * nph * args.steps / (ms * 1e-3)
+    launches = sum(n for (_, n) in kt.values())
+
+    peaks, peak_src = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = fp64_peak_tflops(sm_max)
+    ky_ms, ky_n = kt["micro_y"]
+    achieved = FLOPS_MICRO_Y * nph / (ky_ms / ky_n * 1e-3) / 1e12
+    hbm_gbs = BYTES_PER_PHASE_FP64 * nph * args.steps / (ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "kernel": "micro_y", "peak_source": "FP64 peak from unit counts: 152 SMs x 4 "
+                "flop/clk x %.0f MHz" % sm_max,
+                "step_fp64_frac": FLOPS_STEP * nph * args.steps / (ms * 1e-3) / 1e12 / fp64_peak,
+                "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_source": peak_src,
+                "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()}}
+
+    # end to end through the C ABI with pinned host buffers: H2D of (Q, G), one step, D2H of
+    # (Q, H) every step
+    e2e = None
+    if args.e2e_steps > 0:
+        Qh = torch.from_numpy(pr.Q.copy()).pin_memory().numpy()
+        Gh = torch.zeros(nph, dtype=torch.float64).pin_memory().numpy()
+        Qo = torch.empty(6 * pr.grid.ncell, dtype=torch.float64).pin_memory().numpy()
+        Ho = torch.empty(4 * pr.grid.ncell, dtype=torch.float64).pin_memory().numpy()
+        Qo = Qo.reshape(6, pr.grid.ny, pr.grid.nx)
+        Ho = Ho.reshape(4, pr.grid.ny, pr.grid.nx)
+        for _ in range(2):
+            solver.set_state(Qh, Gh)
+            solver.step(pr.dt, pr.eps, 1)
+            solver.get_moments(Qo, Ho)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            solver.set_state(Qh, Gh)
+            solver.step(pr.dt, pr.eps, 1)
+            solver.get_moments(Qo, Ho)
+        t = time.perf_counter() - t0
+        e2e = {"value": world * nph * args.e2e_steps / t, "unit": UNIT,
+               "h2d_bytes_per_step": int(Qh.nbytes + Gh.nbytes),
+               "d2h_bytes_per_step": int(Qo.nbytes + Ho.nbytes),
+               "steps": args.e2e_steps, "api": "mm_set_state + mm_step + mm_get_moments"}
+    solver.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # calibrate on one step of the full grid, then time enough steps for ~12 s of wall time
+        _, t1, _, _ = cpu_baseline(pr, pr.grid.ny, 1)
+        n = max(1, min(100, int(round(12.0 / max(t1, 1e-3)))))
+        v, t, cores, sub = cpu_baseline(pr, pr.grid.ny, n)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d steps of the full %dx%d grid (%d phase cells), %.1f s"
+                         % (n, sub.nx, sub.ny, sub.nphase, t)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": config_of(pr, args),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+/*
+ * mmkfvs -- C ABI of the GB300 (sm_103a) implementation of one time step of the 2D-2V
+ * micro-macro kinetic flux-vector-splitting scheme for the Boltzmann-ES-BGK equation
+ * (Rossmanith & Sar, arXiv 2509.21832, Section 5, with the diffuse walls of Section 6.3).
+ *
+ * State held on the device by a context:
+ *   Q[6][ny][nx]         conserved moments (rho, rho u1, rho u2, E11, E12, E22), Eq. (5-40),
+ *                        cell averages on the cell-centred grid of Section 5.2.
+ *   G[ny][nx][nv2][nv1]  micro part g on the phase-space grid of Section 5.2 (v1 fastest),
+ *                        FP64, or FP32 when params.precision == MM_PREC_G_FP32.
+ *   H[4][ny][nx]         heat-flux tensor (H111, H112, H122, H222) of the last step, Eq. (5-99).
+ * Host-side arrays passed to this API are always FP64, row-major, in exactly these layouts; the
+ * library copies them and keeps no host pointer.  Device pointers passed to the *_device entry
+ * points must be FP64 device memory of the same layouts, owned by the caller.
+ *
+ * Errors: every function returns an mm_status and never aborts.  Non-physical states met on the
+ * device (rho <= 0, P11 <= 0, P22 <= 0, det(P/rho) <= 0, det(Tcal) <= 0, non-finite values) are
+ * latched in a device word and reported as MM_ERR_NONPHYSICAL by the next mm_sync / mm_get_*.
+ * mm_last_error() gives a text for the last failure of a context.
+ *
+ * Threading: one context per CUDA stream; calls on one context are not thread-safe.  All work
+ * of a context is enqueued on the stream given at creation (NULL = legacy default stream).
+ */
+#ifndef MMKFVS_H
+#define MMKFVS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MM_OK = 0,
+  MM_ERR_INVALID_ARG = 1,  /* argument rejected before any device work */
+  MM_ERR_OOM = 2,          /* device allocation failed */
+  MM_ERR_CUDA = 3,         /* a CUDA call failed; see mm_last_error */
+  MM_ERR_NONPHYSICAL = 4,  /* a non-physical state was met on the device */
+  MM_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
+  MM_ERR_STATE = 6         /* call out of order (e.g. mm_step before mm_set_state) */
+} mm_status;
+
+/* Boundary kinds; side order in mm_params.bc: 0 left (x=x0), 1 right (x=x1), 2 bottom (y=y0),
+ * 3 top (y=y1).  Periodic sides must come in pairs.
+ *   PERIODIC  Eqs. (2d_periodic_micro_1..5), (2d_periodic_macro_1/2)
+ *   EXTRAP    Eqs. (2d_extrap_micro_1..5), (2d_extrap_macro_1..4)
+ *   SPECULAR  mirror ghost cells (the paper names reflecting walls without printing the specular
+ *             form); needs a velocity mesh symmetric about 0 in the wall-normal component
+ *   DIFFUSE   Section 6.3 (Eqs. lid_driven_bc_1..4, twodim_wall_densities_1/2) */
+enum { MM_BC_PERIODIC = 0, MM_BC_EXTRAP = 1, MM_BC_SPECULAR = 2, MM_BC_DIFFUSE = 3 };
+
+/* Collision frequency tau (Section 2.4 remark, Eq. tau-for-2d-es-bgk; Sections 4 and 6.2):
+ *   RHO          tau = tau0 * rho
+ *   HARDSPHERE2D tau = 3 pi C25 rho / (sqrt(2) (1 - nu)), C25 = 0.436 (equals the printed
+ *                (3 C25 pi / (2 sqrt 2)) rho at nu = -1)
+ *   PRESSURE     tau = tau0 * rho * T
+ *   CONST        tau = tau0 */
+enum { MM_TAU_RHO = 0, MM_TAU_HARDSPHERE2D = 1, MM_TAU_PRESSURE = 2, MM_TAU_CONST = 3 };
+
+/* Time-step rule for mm_dt_for_cfl: the min form of Eq. (CFL-2D-part1) or the sum form
+ * dt = CFL / (V1/dx + V2/dy) that reproduces the step counts printed in Section 6.2. */
+enum { MM_CFL_MIN = 0, MM_CFL_SUM = 1 };
+
+/* Storage of g: FP64, or FP32 with moments, projector coefficients, macro update and the
+ * Gaussian tensor inverse in FP64 (the paper uses FP64 throughout; FP32 g is this library's
+ * mixed-precision extension). */
+enum { MM_PREC_FP64 = 0, MM_PREC_G_FP32 = 1 };
+
+typedef struct {
+  int nx, ny;                        /* spatial cells, >= 1 each (ny = 1: 1D-2V, y periodic) */
+  double x0, x1, y0, y1;             /* spatial box */
+  int nv1, nv2;                      /* velocity cells, 1..1024 each */
+  double v1min, v1max, v2min, v2max; /* velocity box */
+} mm_grid;
+
+typedef struct {
+  double nu;            /* ES-BGK parameter, -1 <= nu < 1 (Eq. mod-press-esbgk), Pr = 1/(1-nu) */
+  int tau_model;        /* MM_TAU_* */
+  double tau0;          /* scale of the tau model */
+  int bc[4];            /* MM_BC_* per side */
+  double wall_T[4];     /* diffuse wall temperature per side (> 0 where DIFFUSE) */
+  double wall_U[4];     /* diffuse wall tangential velocity per side (lid speed) */
+  int wall_keep_es_term;/* 1: wall-adjacent Ghat keeps (G - M)/eps; 0: literal Section 6.3 form */
+  int precision;        /* MM_PREC_* */
+} mm_params;
+
+typedef struct mm_ctx mm_ctx;
+
+/* Create a context and allocate its device state (owned by the context).  cuda_stream is a
+ * cudaStream_t (NULL for the legacy default stream).  Validates the grid and parameters
+ * (MM_ERR_INVALID_ARG), e.g. unpaired periodic sides, nu outside [-1, 1), a velocity mesh that is
+ * not symmetric where a specular wall needs it. */
+mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
+                    mm_ctx** out);
+
+/* Device bytes mm_create allocates for this problem (state, scratch and flags). */
+size_t mm_device_bytes(const mm_grid* grid, const mm_params* params);
+
+/* Copy the state in from host memory: Q_host [6][ny][nx], G_host [ny][nx][nv2][nv1] (NULL
+ * means g = 0).  Synchronous with respect to the host buffers (they may be reused on return). */
+mm_status mm_set_state(mm_ctx* ctx, const double* Q_host, const double* G_host);
+
+/* Same from caller-owned FP64 device memory; asynchronous on the context stream. */
+mm_status mm_set_state_device(mm_ctx* ctx, const double* Q_dev, const double* G_dev);
+
+/* Advance nsteps time steps of size dt at Knudsen number eps (Section 5: micro x sweep, micro y
+ * sweep, backward-Euler relaxation, heat-flux moments, then the Strang-split macro update).
+ * Asynchronous on the context stream.  dt > 0, eps > 0, nsteps >= 0. */
+mm_status mm_step(mm_ctx* ctx, double dt, double eps, int nsteps);
+
+/* Wait for the context stream and report device-side errors (MM_ERR_NONPHYSICAL). */
+mm_status mm_sync(mm_ctx* ctx);
+
+/* Copy Q (and H unless H_host is NULL) to host memory; synchronises the stream. */
+mm_status mm_get_moments(mm_ctx* ctx, double* Q_host, double* H_host);
+
+/* Copy Q (and H unless NULL) to caller-owned FP64 device memory; asynchronous. */
+mm_status mm_get_moments_device(mm_ctx* ctx, double* Q_dev, double* H_dev);
+
+/* Copy G to host memory as FP64 [ny][nx][nv2][nv1]; synchronises the stream. */
+mm_status mm_get_g(mm_ctx* ctx, double* G_host);
+
+/* Global time step of Eq. (CFL-2D-part1/2) (form MM_CFL_MIN) or of the sum form
+ * (MM_CFL_SUM); with ny == 1 the 1D rule of Section 3.2 (dt = CFL dx / V1).  If t_final > 0,
+ * N = ceil(t_final/dt) and dt <- t_final/N (N written to *nsteps_out if not NULL).  Returns a
+ * negative value for invalid arguments. */
+double mm_dt_for_cfl(const mm_grid* grid, double cfl, double t_final, int form, int* nsteps_out);
+
+/* Text of the last error of ctx ("" if none); valid until the next call on ctx. */
+const char* mm_last_error(const mm_ctx* ctx);
+
+/* Per-kernel timing with CUDA events recorded around each launch on the context stream.
+ * mm_get_timing writes the accumulated milliseconds and launch counts of each kernel kind
+ * (arrays of mm_num_kernels() entries) since timing was enabled; synchronises the stream. */
+mm_status mm_set_timing(mm_ctx* ctx, int enable);
+mm_status mm_get_timing(mm_ctx* ctx, double* ms_out, long long* launches_out);
+int mm_num_kernels(void);
+const char* mm_kernel_name(int idx);
+
+/* Release the context and its device memory (NULL is accepted). */
+void mm_destroy(mm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMKFVS_H */

@@ -1,0 +1,243 @@
+"""Thin Python binding of libmmkfvs (include/mmkfvs.h): argument marshalling only.
+
+Every step of the scheme runs in the CUDA library; this module only converts numpy arrays /
+torch tensors to pointers.  The functions keep the C names (mm_create, mm_set_state, mm_step,
+...); ``Solver`` wraps a context.  Importing this module on a machine without the built library
+raises immediately: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MM_OK, MM_ERR_INVALID_ARG, MM_ERR_OOM, MM_ERR_CUDA, MM_ERR_NONPHYSICAL, MM_ERR_TIMEOUT, \
+    MM_ERR_STATE = range(7)
+STATUS_NAMES = {0: "MM_OK", 1: "MM_ERR_INVALID_ARG", 2: "MM_ERR_OOM", 3: "MM_ERR_CUDA",
+                4: "MM_ERR_NONPHYSICAL", 5: "MM_ERR_TIMEOUT", 6: "MM_ERR_STATE"}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class mm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("nv1", ctypes.c_int), ("nv2", ctypes.c_int),
+                ("v1min", ctypes.c_double), ("v1max", ctypes.c_double),
+                ("v2min", ctypes.c_double), ("v2max", ctypes.c_double)]
+
+
+class mm_params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("tau_model", ctypes.c_int), ("tau0", ctypes.c_double),
+                ("bc", ctypes.c_int * 4), ("wall_T", ctypes.c_double * 4),
+                ("wall_U", ctypes.c_double * 4), ("wall_keep_es_term", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device", "mm_step",
+           "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
+           "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
+           "mm_kernel_name", "mm_destroy"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libmmkfvs.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_needed else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libmmkfvs.so is not built; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    G, P = ctypes.POINTER(mm_grid), ctypes.POINTER(mm_params)
+    vp = ctypes.c_void_p
+    L.mm_create.argtypes = [G, P, vp, ctypes.POINTER(vp)]
+    L.mm_device_bytes.argtypes = [G, P]
+    L.mm_device_bytes.restype = ctypes.c_size_t
+    L.mm_set_state.argtypes = [vp, vp, vp]
+    L.mm_set_state_device.argtypes = [vp, vp, vp]
+    L.mm_step.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.mm_sync.argtypes = [vp]
+    L.mm_get_moments.argtypes = [vp, vp, vp]
+    L.mm_get_moments_device.argtypes = [vp, vp, vp]
+    L.mm_get_g.argtypes = [vp, vp]
+    L.mm_dt_for_cfl.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_int)]
+    L.mm_dt_for_cfl.restype = ctypes.c_double
+    L.mm_last_error.argtypes = [vp]
+    L.mm_last_error.restype = ctypes.c_char_p
+    L.mm_set_timing.argtypes = [vp, ctypes.c_int]
+    L.mm_get_timing.argtypes = [vp, _dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.mm_num_kernels.argtypes = []
+    L.mm_num_kernels.restype = ctypes.c_int
+    L.mm_kernel_name.argtypes = [ctypes.c_int]
+    L.mm_kernel_name.restype = ctypes.c_char_p
+    L.mm_destroy.argtypes = [vp]
+    L.mm_destroy.restype = None
+    for name in ["mm_create", "mm_set_state", "mm_set_state_device", "mm_step", "mm_sync",
+                 "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_set_timing",
+                 "mm_get_timing"]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class MMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def to_c_grid(g) -> mm_grid:
+    return mm_grid(int(g.nx), int(g.ny), float(g.x0), float(g.x1), float(g.y0), float(g.y1),
+                   int(g.nv1), int(g.nv2), float(g.v1min), float(g.v1max), float(g.v2min),
+                   float(g.v2max))
+
+
+def to_c_params(p) -> mm_params:
+    o = mm_params()
+    o.nu = float(p.nu)
+    o.tau_model = int(p.tau_model)
+    o.tau0 = float(p.tau0)
+    for s in range(4):
+        o.bc[s] = int(p.bc[s])
+        o.wall_T[s] = float(p.wall_T[s])
+        o.wall_U[s] = float(p.wall_U[s])
+    o.wall_keep_es_term = int(p.wall_keep_es_term)
+    o.precision = int(getattr(p, "precision", 0))
+    return o
+
+
+def _host_ptr(a, n):
+    if a is None:
+        return None
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    assert a.size == n, (a.size, n)
+    return a.ctypes.data
+
+
+def _dev_ptr(t, n):
+    if t is None:
+        return None
+    assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8
+    assert t.is_contiguous() and t.numel() == n, (t.numel(), n)
+    return t.data_ptr()
+
+
+# ---- the C entry points under their own names --------------------------------------------
+
+def mm_dt_for_cfl(grid, cfl, t_final, form):
+    n = ctypes.c_int(0)
+    g = to_c_grid(grid)
+    dt = load().mm_dt_for_cfl(ctypes.byref(g), float(cfl), float(t_final), int(form),
+                              ctypes.byref(n))
+    if dt < 0:
+        raise MMError(MM_ERR_INVALID_ARG, "mm_dt_for_cfl")
+    return dt, n.value
+
+
+def mm_device_bytes(grid, params):
+    g, p = to_c_grid(grid), to_c_params(params)
+    return load().mm_device_bytes(ctypes.byref(g), ctypes.byref(p))
+
+
+def mm_create(grid, params, stream=0):
+    L = load()
+    g, p = to_c_grid(grid), to_c_params(params)
+    ctx = ctypes.c_void_p()
+    st = L.mm_create(ctypes.byref(g), ctypes.byref(p), ctypes.c_void_p(int(stream)),
+                     ctypes.byref(ctx))
+    if st != MM_OK:
+        raise MMError(st, "mm_create rejected the grid/parameters or could not allocate")
+    return ctx
+
+
+def _check(ctx, st, what):
+    if st != MM_OK:
+        raise MMError(st, "%s: %s" % (what, load().mm_last_error(ctx).decode()))
+
+
+class Solver:
+    """One device context: state (Q, G, H) of a problem on the GPU."""
+
+    def __init__(self, grid, params, stream=0):
+        self.grid, self.params = grid, params
+        self.ncell = grid.nx * grid.ny
+        self.nphase = self.ncell * grid.nv1 * grid.nv2
+        self.ctx = mm_create(grid, params, stream)
+        self.L = load()
+
+    def close(self):
+        if self.ctx:
+            self.L.mm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, Q, G=None):
+        """Q [6][ny][nx] and G [ny][nx][nv2][nv1] (None: g = 0), numpy (host) or torch (cuda)."""
+        if hasattr(Q, "is_cuda") and Q.is_cuda:
+            st = self.L.mm_set_state_device(self.ctx, _dev_ptr(Q, 6 * self.ncell),
+                                            _dev_ptr(G, self.nphase))
+        else:
+            Q = np.ascontiguousarray(Q, dtype=np.float64)
+            G = None if G is None else np.ascontiguousarray(G, dtype=np.float64)
+            st = self.L.mm_set_state(self.ctx, _host_ptr(Q, 6 * self.ncell),
+                                     _host_ptr(G, self.nphase))
+        _check(self.ctx, st, "mm_set_state")
+
+    def step(self, dt, eps, nsteps=1):
+        _check(self.ctx, self.L.mm_step(self.ctx, float(dt), float(eps), int(nsteps)), "mm_step")
+
+    def sync(self):
+        _check(self.ctx, self.L.mm_sync(self.ctx), "mm_sync")
+
+    def get_moments(self, Q_out=None, H_out=None, with_H=True):
+        Q = Q_out if Q_out is not None else np.empty((6, self.grid.ny, self.grid.nx))
+        H = H_out if H_out is not None else (
+            np.empty((4, self.grid.ny, self.grid.nx)) if with_H else None)
+        st = self.L.mm_get_moments(self.ctx, _host_ptr(Q, 6 * self.ncell),
+                                   _host_ptr(H, 4 * self.ncell))
+        _check(self.ctx, st, "mm_get_moments")
+        return Q, H
+
+    def get_moments_device(self, Q_dev, H_dev=None):
+        st = self.L.mm_get_moments_device(self.ctx, _dev_ptr(Q_dev, 6 * self.ncell),
+                                          _dev_ptr(H_dev, 4 * self.ncell))
+        _check(self.ctx, st, "mm_get_moments_device")
+
+    def get_g(self):
+        G = np.empty((self.grid.ny, self.grid.nx, self.grid.nv2, self.grid.nv1))
+        _check(self.ctx, self.L.mm_get_g(self.ctx, _host_ptr(G, self.nphase)), "mm_get_g")
+        return G
+
+    def set_timing(self, enable=True):
+        _check(self.ctx, self.L.mm_set_timing(self.ctx, int(enable)), "mm_set_timing")
+
+    def get_timing(self):
+        n = self.L.mm_num_kernels()
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        _check(self.ctx, self.L.mm_get_timing(self.ctx, ms, cnt), "mm_get_timing")
+        return {self.L.mm_kernel_name(k).decode(): (ms[k], cnt[k]) for k in range(n)}
+
+    def last_error(self):
+        return self.L.mm_last_error(self.ctx).decode()

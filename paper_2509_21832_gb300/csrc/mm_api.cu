@@ -1,0 +1,479 @@
+// Host side of the C ABI declared in include/mmkfvs.h: validation, device state, launch order of
+// one time step (Section 5 of Rossmanith & Sar, arXiv 2509.21832: prims of Q^n, micro x sweep,
+// micro y sweep + relaxation + heat flux, macro collision/x transport, macro y transport/
+// collision), per-kernel event timing and error latching.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mm_internal.cuh"
+
+using namespace mmk;
+
+namespace {
+
+const char* const kKernelNames[] = {"prims", "micro_x", "micro_y", "micro_y_wall", "macro_x",
+                                    "macro_y"};
+constexpr int kNumKernels = 6;
+enum { T_PRIMS = 0, T_MICRO_X, T_MICRO_Y, T_MICRO_YW, T_MACRO_X, T_MACRO_Y };
+
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct mm_ctx {
+  mm_grid grid;
+  mm_params params;
+  KGrid kg;
+  KParams kp;
+  MicroShape ms;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool fp32 = false;
+  size_t nphase = 0, ncell = 0;
+  void* G = nullptr;   // G^n / G^{n+1}
+  void* Gs = nullptr;  // G* (scratch)
+  double* Q = nullptr;
+  double* Q2 = nullptr;  // Q** (scratch)
+  double* H = nullptr;
+  double* prim = nullptr;
+  int* err = nullptr;
+  int* wall_cells = nullptr;
+  int n_wall = 0;
+  bool have_state = false;
+  std::string last_error;
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> free_events;
+  double acc_ms[kNumKernels] = {0};
+  long long acc_n[kNumKernels] = {0};
+};
+
+namespace {
+
+mm_status fail(mm_ctx* c, mm_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+mm_status cuda_fail(mm_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, MM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+std::string validate(const mm_grid* g, const mm_params* p) {
+  if (!g || !p) return "null grid or params";
+  if (g->nx < 1 || g->ny < 1) return "nx and ny must be >= 1";
+  if (g->nv1 < 1 || g->nv2 < 1 || g->nv1 > 512 || g->nv2 > 1024)
+    return "nv1 must be in 1..512 and nv2 in 1..1024";
+  if (!(g->x1 > g->x0) || !(g->y1 > g->y0)) return "empty spatial box";
+  if (!(g->v1max > g->v1min) || !(g->v2max > g->v2min)) return "empty velocity box";
+  if (!(p->nu >= -1.0 && p->nu < 1.0)) return "nu must satisfy -1 <= nu < 1";
+  if (p->tau_model < 0 || p->tau_model > 3) return "unknown tau model";
+  if ((p->tau_model == MM_TAU_RHO || p->tau_model == MM_TAU_PRESSURE ||
+       p->tau_model == MM_TAU_CONST) && !(p->tau0 > 0.0))
+    return "tau0 must be > 0";
+  if (p->precision != MM_PREC_FP64 && p->precision != MM_PREC_G_FP32) return "unknown precision";
+  for (int s = 0; s < 4; ++s) {
+    if (p->bc[s] < 0 || p->bc[s] > 3) return "unknown boundary kind";
+    if (p->bc[s] == MM_BC_DIFFUSE && !(p->wall_T[s] > 0.0)) return "diffuse wall needs wall_T > 0";
+  }
+  if ((p->bc[0] == MM_BC_PERIODIC) != (p->bc[1] == MM_BC_PERIODIC)) return "periodic x sides must be paired";
+  if ((p->bc[2] == MM_BC_PERIODIC) != (p->bc[3] == MM_BC_PERIODIC)) return "periodic y sides must be paired";
+  const bool specx = p->bc[0] == MM_BC_SPECULAR || p->bc[1] == MM_BC_SPECULAR;
+  const bool specy = p->bc[2] == MM_BC_SPECULAR || p->bc[3] == MM_BC_SPECULAR;
+  if (specx && std::fabs(g->v1min + g->v1max) > 1e-12 * (g->v1max - g->v1min))
+    return "specular x walls need a velocity mesh symmetric in v1";
+  if (specy && std::fabs(g->v2min + g->v2max) > 1e-12 * (g->v2max - g->v2min))
+    return "specular y walls need a velocity mesh symmetric in v2";
+  return "";
+}
+
+void destroy_events(mm_ctx* c) {
+  for (auto& t : c->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  c->pending.clear();
+  for (auto e : c->free_events) cudaEventDestroy(e);
+  c->free_events.clear();
+}
+
+cudaEvent_t take_event(mm_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold finished timed launches into the per-kernel totals (requires the stream to be idle).
+void drain_timing(mm_ctx* c) {
+  for (auto& t : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      c->acc_ms[t.kind] += ms;
+      c->acc_n[t.kind] += 1;
+    }
+    c->free_events.push_back(t.a);
+    c->free_events.push_back(t.b);
+  }
+  c->pending.clear();
+}
+
+template <typename F>
+void timed(mm_ctx* c, int kind, F&& launch) {
+  if (!c->timing) {
+    launch();
+    return;
+  }
+  if (c->pending.size() > 50000) {
+    cudaStreamSynchronize(c->stream);
+    drain_timing(c);
+  }
+  TimedLaunch t{kind, take_event(c), take_event(c)};
+  cudaEventRecord(t.a, c->stream);
+  launch();
+  cudaEventRecord(t.b, c->stream);
+  c->pending.push_back(t);
+}
+
+mm_status check_device_errors(mm_ctx* c) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device error check");
+  if (h) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf,
+                  "non-physical state met on the device (flags 0x%x: 1 prims of Q^n, 2 macro "
+                  "update, 4 non-finite heat flux)", h);
+    return fail(c, MM_ERR_NONPHYSICAL, buf);
+  }
+  return MM_OK;
+}
+
+template <typename Tg>
+void enqueue_step(mm_ctx* c, double dt, double eps) {
+  Tg* G = static_cast<Tg*>(c->G);
+  Tg* Gs = static_cast<Tg*>(c->Gs);
+  const KGrid& g = c->kg;
+  const KParams& p = c->kp;
+  cudaStream_t s = c->stream;
+  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, g, p, c->err, s); });
+  timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
+  timed(c, T_MICRO_Y, [&] { launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s); });
+  if (c->n_wall > 0)
+    timed(c, T_MICRO_YW, [&] {
+      launch_micro_y_wall<Tg>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
+                              c->ms, c->err, s);
+    });
+  timed(c, T_MACRO_X, [&] { launch_macro_x(c->Q, c->H, c->Q2, g, p, dt, eps, c->err, s); });
+  timed(c, T_MACRO_Y, [&] { launch_macro_y(c->Q2, c->H, c->Q, g, p, dt, eps, c->err, s); });
+}
+
+// Copy an FP64 array of n elements into the context's G (FP64 or FP32), staging through Gs.
+mm_status copy_g_in(mm_ctx* c, const double* src, cudaMemcpyKind kind) {
+  const size_t n = c->nphase;
+  if (!c->fp32) {
+    cudaError_t e = cudaMemcpyAsync(c->G, src, n * sizeof(double), kind, c->stream);
+    return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "copy G in");
+  }
+  // FP32 storage: stage chunks of doubles through the scratch buffer Gs (n floats = n/2 doubles)
+  const size_t chunk = n / 2 > 0 ? n / 2 : 1;
+  double* stage = static_cast<double*>(c->Gs);
+  for (size_t off = 0; off < n; off += chunk) {
+    const size_t m = off + chunk <= n ? chunk : n - off;
+    cudaError_t e = cudaMemcpyAsync(stage, src + off, m * sizeof(double), kind, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy G in");
+    launch_convert_f64_to_f32(stage, static_cast<float*>(c->G) + off, m, c->stream);
+    if (kind == cudaMemcpyHostToDevice) {
+      e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "copy G in");
+    }
+  }
+  return MM_OK;
+}
+
+mm_status copy_g_out(mm_ctx* c, double* dst) {
+  const size_t n = c->nphase;
+  if (!c->fp32) {
+    cudaError_t e = cudaMemcpyAsync(dst, c->G, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "copy G out");
+  }
+  const size_t chunk = n / 2 > 0 ? n / 2 : 1;
+  double* stage = static_cast<double*>(c->Gs);
+  for (size_t off = 0; off < n; off += chunk) {
+    const size_t m = off + chunk <= n ? chunk : n - off;
+    launch_convert_f32_to_f64(static_cast<const float*>(c->G) + off, stage, m, c->stream);
+    cudaError_t e = cudaMemcpyAsync(dst + off, stage, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy G out");
+  }
+  return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mm_device_bytes(const mm_grid* g, const mm_params* p) {
+  if (!validate(g, p).empty()) return 0;
+  const size_t nc = (size_t)g->nx * g->ny;
+  const size_t np = nc * g->nv1 * g->nv2;
+  const size_t gs = p->precision == MM_PREC_G_FP32 ? sizeof(float) : sizeof(double);
+  size_t nwall = 0;
+  for (int j = 0; j < g->ny; ++j)
+    for (int i = 0; i < g->nx; ++i)
+      if ((i == 0 && p->bc[0] == MM_BC_DIFFUSE) || (i == g->nx - 1 && p->bc[1] == MM_BC_DIFFUSE) ||
+          (j == 0 && p->bc[2] == MM_BC_DIFFUSE) || (j == g->ny - 1 && p->bc[3] == MM_BC_DIFFUSE))
+        ++nwall;
+  return 2 * np * gs + (6 + 6 + 4 + NPRIM) * nc * sizeof(double) + sizeof(int) +
+         nwall * sizeof(int);
+}
+
+mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
+                    mm_ctx** out) {
+  if (!out) return MM_ERR_INVALID_ARG;
+  *out = nullptr;
+  const std::string v = validate(grid, params);
+  if (!v.empty()) return MM_ERR_INVALID_ARG;
+  mm_ctx* c = new mm_ctx();
+  c->grid = *grid;
+  c->params = *params;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&c->device);
+  c->fp32 = params->precision == MM_PREC_G_FP32;
+  c->ncell = (size_t)grid->nx * grid->ny;
+  c->nphase = c->ncell * grid->nv1 * grid->nv2;
+  KGrid& kg = c->kg;
+  kg.nx = grid->nx;
+  kg.ny = grid->ny;
+  kg.nv1 = grid->nv1;
+  kg.nv2 = grid->nv2;
+  kg.dx = (grid->x1 - grid->x0) / grid->nx;
+  kg.dy = (grid->y1 - grid->y0) / grid->ny;
+  kg.v1min = grid->v1min;
+  kg.v2min = grid->v2min;
+  kg.dv1 = (grid->v1max - grid->v1min) / grid->nv1;
+  kg.dv2 = (grid->v2max - grid->v2min) / grid->nv2;
+  KParams& kp = c->kp;
+  kp.nu = params->nu;
+  kp.tau0 = params->tau0;
+  kp.tau_model = params->tau_model;
+  for (int s = 0; s < 4; ++s) {
+    kp.bc[s] = params->bc[s];
+    kp.wall_T[s] = params->wall_T[s];
+    kp.wall_U[s] = params->wall_U[s];
+  }
+  kp.keep_es = params->wall_keep_es_term ? 1 : 0;
+  c->ms = micro_shape(grid->nv1, grid->nv2);
+
+  const size_t gsz = c->fp32 ? sizeof(float) : sizeof(double);
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes > 0 ? bytes : 1);
+  };
+  alloc(&c->G, c->nphase * gsz);
+  alloc(&c->Gs, c->nphase * gsz > 16 ? c->nphase * gsz : 16);  // also stages FP64 chunks
+  alloc((void**)&c->Q, 6 * c->ncell * sizeof(double));
+  alloc((void**)&c->Q2, 6 * c->ncell * sizeof(double));
+  alloc((void**)&c->H, 4 * c->ncell * sizeof(double));
+  alloc((void**)&c->prim, NPRIM * c->ncell * sizeof(double));
+  alloc((void**)&c->err, sizeof(int));
+  std::vector<int> walls;
+  for (int j = 0; j < grid->ny; ++j)
+    for (int i = 0; i < grid->nx; ++i)
+      if ((i == 0 && kp.bc[0] == MM_BC_DIFFUSE) || (i == grid->nx - 1 && kp.bc[1] == MM_BC_DIFFUSE) ||
+          (j == 0 && kp.bc[2] == MM_BC_DIFFUSE) || (j == grid->ny - 1 && kp.bc[3] == MM_BC_DIFFUSE))
+        walls.push_back(j * grid->nx + i);
+  c->n_wall = (int)walls.size();
+  if (c->n_wall > 0) alloc((void**)&c->wall_cells, walls.size() * sizeof(int));
+  if (e != cudaSuccess) {
+    mm_destroy(c);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA;
+  }
+  if (c->n_wall > 0)
+    e = cudaMemcpy(c->wall_cells, walls.data(), walls.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->H, 0, 4 * c->ncell * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    mm_destroy(c);
+    return MM_ERR_CUDA;
+  }
+  *out = c;
+  return MM_OK;
+}
+
+mm_status mm_set_state(mm_ctx* c, const double* Q_host, const double* G_host) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!Q_host) return fail(c, MM_ERR_INVALID_ARG, "Q_host is NULL");
+  cudaError_t e = cudaMemcpyAsync(c->Q, Q_host, 6 * c->ncell * sizeof(double),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy Q in");
+  if (G_host) {
+    mm_status s = copy_g_in(c, G_host, cudaMemcpyHostToDevice);
+    if (s != MM_OK) return s;
+  } else {
+    e = cudaMemsetAsync(c->G, 0, c->nphase * (c->fp32 ? sizeof(float) : sizeof(double)), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "zero G");
+  }
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set state");
+  c->have_state = true;
+  return MM_OK;
+}
+
+mm_status mm_set_state_device(mm_ctx* c, const double* Q_dev, const double* G_dev) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!Q_dev) return fail(c, MM_ERR_INVALID_ARG, "Q_dev is NULL");
+  cudaError_t e = cudaMemcpyAsync(c->Q, Q_dev, 6 * c->ncell * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy Q in");
+  if (G_dev) {
+    mm_status s = copy_g_in(c, G_dev, cudaMemcpyDeviceToDevice);
+    if (s != MM_OK) return s;
+  } else {
+    e = cudaMemsetAsync(c->G, 0, c->nphase * (c->fp32 ? sizeof(float) : sizeof(double)), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "zero G");
+  }
+  c->have_state = true;
+  return MM_OK;
+}
+
+mm_status mm_step(mm_ctx* c, double dt, double eps, int nsteps) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, MM_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, MM_ERR_INVALID_ARG, "eps must be > 0");
+  if (nsteps < 0) return fail(c, MM_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (!c->have_state) return fail(c, MM_ERR_STATE, "mm_step before mm_set_state");
+  for (int n = 0; n < nsteps; ++n) {
+    if (c->fp32) enqueue_step<float>(c, dt, eps);
+    else enqueue_step<double>(c, dt, eps);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  return MM_OK;
+}
+
+mm_status mm_sync(mm_ctx* c) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  return check_device_errors(c);
+}
+
+mm_status mm_get_moments(mm_ctx* c, double* Q_host, double* H_host) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!Q_host) return fail(c, MM_ERR_INVALID_ARG, "Q_host is NULL");
+  cudaError_t e = cudaMemcpyAsync(Q_host, c->Q, 6 * c->ncell * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && H_host)
+    e = cudaMemcpyAsync(H_host, c->H, 4 * c->ncell * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy moments out");
+  return check_device_errors(c);
+}
+
+mm_status mm_get_moments_device(mm_ctx* c, double* Q_dev, double* H_dev) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!Q_dev) return fail(c, MM_ERR_INVALID_ARG, "Q_dev is NULL");
+  cudaError_t e = cudaMemcpyAsync(Q_dev, c->Q, 6 * c->ncell * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && H_dev)
+    e = cudaMemcpyAsync(H_dev, c->H, 4 * c->ncell * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy moments out");
+  return MM_OK;
+}
+
+mm_status mm_get_g(mm_ctx* c, double* G_host) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!G_host) return fail(c, MM_ERR_INVALID_ARG, "G_host is NULL");
+  mm_status s = copy_g_out(c, G_host);
+  if (s != MM_OK) return s;
+  return check_device_errors(c);
+}
+
+double mm_dt_for_cfl(const mm_grid* g, double cfl, double t_final, int form, int* nsteps_out) {
+  if (!g || g->nx < 1 || g->ny < 1 || !(cfl > 0.0) || !(g->x1 > g->x0) || !(g->y1 > g->y0))
+    return -1.0;
+  const double dx = (g->x1 - g->x0) / g->nx;
+  const double dy = (g->y1 - g->y0) / g->ny;
+  const double V1 = std::fmax(std::fabs(g->v1min), std::fabs(g->v1max));
+  const double V2 = std::fmax(std::fabs(g->v2min), std::fabs(g->v2max));
+  if (!(V1 > 0.0) || (g->ny > 1 && !(V2 > 0.0))) return -1.0;
+  double dt;
+  if (g->ny == 1) dt = cfl * dx / V1;
+  else if (form == MM_CFL_MIN) dt = cfl * std::fmin(dx / V1, dy / V2);
+  else dt = cfl / (V1 / dx + V2 / dy);
+  int n = 0;
+  if (t_final > 0.0) {
+    n = (int)std::ceil(t_final / dt * (1.0 - 1e-12));
+    if (n < 1) n = 1;
+    dt = t_final / n;
+  }
+  if (nsteps_out) *nsteps_out = n;
+  return dt;
+}
+
+const char* mm_last_error(const mm_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+mm_status mm_set_timing(mm_ctx* c, int enable) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  drain_timing(c);
+  for (int k = 0; k < kNumKernels; ++k) {
+    c->acc_ms[k] = 0.0;
+    c->acc_n[k] = 0;
+  }
+  c->timing = enable != 0;
+  return MM_OK;
+}
+
+mm_status mm_get_timing(mm_ctx* c, double* ms_out, long long* launches_out) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  drain_timing(c);
+  for (int k = 0; k < kNumKernels; ++k) {
+    if (ms_out) ms_out[k] = c->acc_ms[k];
+    if (launches_out) launches_out[k] = c->acc_n[k];
+  }
+  return MM_OK;
+}
+
+int mm_num_kernels(void) { return kNumKernels; }
+
+const char* mm_kernel_name(int idx) {
+  return idx >= 0 && idx < kNumKernels ? kKernelNames[idx] : "";
+}
+
+void mm_destroy(mm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  destroy_events(c);
+  cudaFree(c->G);
+  cudaFree(c->Gs);
+  cudaFree(c->Q);
+  cudaFree(c->Q2);
+  cudaFree(c->H);
+  cudaFree(c->prim);
+  cudaFree(c->err);
+  cudaFree(c->wall_cells);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal declarations shared by the CUDA translation units of libmmkfvs (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mmkfvs.h"
+
+namespace mmk {
+
+// Grid quantities used on the device (derived once on the host).
+struct KGrid {
+  int nx, ny, nv1, nv2;
+  double dx, dy, v1min, v2min, dv1, dv2;
+};
+
+// Physical parameters used on the device.
+struct KParams {
+  double nu, tau0;
+  int tau_model;
+  int bc[4];
+  double wall_T[4], wall_U[4];
+  int keep_es;
+};
+
+// Per-cell primitive fields produced by the prims kernel, SoA [NPRIM][ny][nx].
+enum PrimField {
+  P_RHO = 0, P_U1, P_U2, P_T, P_TAU,
+  P_TI11, P_TI12, P_TI22,  // inverse of the ES tensor Tcal (Eq. 2-19)
+  P_KG,                    // rho / (2 pi sqrt(det Tcal)): normalisation of the ES Gaussian
+  P_TH11, P_TH22,          // diagonal of the temperature tensor P / rho
+  NPRIM
+};
+
+// Bits of the device error word.
+enum { ERR_NONPHYS_PRIM = 1, ERR_NONPHYS_MACRO = 2, ERR_NONFINITE_G = 4 };
+
+// Launch shape of the micro kernels: R rows of v2 per pass, threads = R * nv1 rounded up to 32.
+struct MicroShape {
+  int R;
+  int threads;
+  size_t smem_x, smem_y;
+};
+MicroShape micro_shape(int nv1, int nv2);
+
+// Kernel kinds, for per-kernel timing.
+enum KernelKind { KK_PRIMS = 0, KK_MICRO_X, KK_MICRO_Y, KK_MACRO_X, KK_MACRO_Y, KK_COUNT };
+
+void launch_prims(const double* Q, double* prim, const KGrid& g, const KParams& p, int* err,
+                  cudaStream_t s);
+template <typename Tg>
+void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
+                    const KParams& p, double dt, const MicroShape& ms, cudaStream_t s);
+template <typename Tg>
+void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
+                    const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
+                    cudaStream_t s);
+template <typename Tg>
+void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
+                         const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
+                         double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s);
+void launch_macro_x(const double* Qn, const double* H, double* Q2, const KGrid& g,
+                    const KParams& p, double dt, double eps, int* err, cudaStream_t s);
+void launch_macro_y(const double* Q2, const double* H, double* Qn, const KGrid& g,
+                    const KParams& p, double dt, double eps, int* err, cudaStream_t s);
+void launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s);
+void launch_convert_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
+
+}  // namespace mmk

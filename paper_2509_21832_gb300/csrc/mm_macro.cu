@@ -1,0 +1,355 @@
+// Per-cell kernels of the micro-macro KFVS step (Rossmanith & Sar, arXiv 2509.21832):
+//  - primitive variables of Q^n for the micro kernels (Section 2: u, P, T; Eq. 2-19: ES tensor;
+//    Eq. tau-for-2d-es-bgk: tau),
+//  - the Strang-split macro update of Section 5.4: TR-BDF2 collision half steps and the KFVS
+//    finite-volume transport in x then y with the central heat-flux differences of Eq. (5-103),
+//    with the boundary rules of Sections 5.4.1, 5.4.2 and 6.3.
+// One thread per spatial cell.  A face flux is evaluated by both cells that share the face, from
+// the same operands in the same order, so both see bitwise the same value.
+#include <cmath>
+
+#include "mm_internal.cuh"
+
+namespace mmk {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kC25 = 0.436;
+
+__device__ __forceinline__ double tau_of(const KParams& p, double rho, double T) {
+  switch (p.tau_model) {
+    case MM_TAU_RHO: return p.tau0 * rho;
+    case MM_TAU_HARDSPHERE2D: return 3.0 * kPi * kC25 * rho / (sqrt(2.0) * (1.0 - p.nu));
+    case MM_TAU_PRESSURE: return p.tau0 * rho * T;
+    default: return p.tau0;
+  }
+}
+
+__device__ __forceinline__ void load_q(const double* Q, int nc, int c, double q[6]) {
+#pragma unroll
+  for (int m = 0; m < 6; ++m) q[m] = Q[m * nc + c];
+}
+
+// Primitive quantities of a moment vector; returns false for a non-physical state.
+__device__ __forceinline__ bool prim6(const double q[6], double& rho, double& u1, double& u2,
+                                      double& P11, double& P12, double& P22) {
+  rho = q[0];
+  u1 = q[1] / rho;
+  u2 = q[2] / rho;
+  P11 = q[3] - rho * u1 * u1;
+  P12 = q[4] - rho * u1 * u2;
+  P22 = q[5] - rho * u2 * u2;
+  return rho > 0.0 && P11 > 0.0 && P22 > 0.0 && P11 * P22 - P12 * P12 > 0.0 && isfinite(u1) &&
+         isfinite(u2) && isfinite(P12) && isfinite(P11 + P22);
+}
+
+// Collision half step (Section 5.4): P <- (1/2)[[1+W,0,1-W],[0,2W,0],[1-W,0,1+W]] P with the
+// TR-BDF2 factor W of tau(q); rho and rho u unchanged; E = rho u (x) u + P.
+__device__ __forceinline__ bool coll_half(const KParams& p, const double q[6], double eps,
+                                          double dt, double o[6]) {
+  double rho, u1, u2, P11, P12, P22;
+  const bool ok = prim6(q, rho, u1, u2, P11, P12, P22);
+  const double T = (P11 + P22) / (2.0 * rho);
+  const double a = tau_of(p, rho, T) * (1.0 - p.nu);
+  const double W = (48.0 * eps * eps - 10.0 * a * eps * dt) /
+                   (48.0 * eps * eps + 14.0 * a * eps * dt + (a * dt) * (a * dt));
+  const double n11 = 0.5 * ((1.0 + W) * P11 + (1.0 - W) * P22);
+  const double n12 = 0.5 * (2.0 * W * P12);
+  const double n22 = 0.5 * ((1.0 - W) * P11 + (1.0 + W) * P22);
+  o[0] = q[0];
+  o[1] = q[1];
+  o[2] = q[2];
+  o[3] = rho * u1 * u1 + n11;
+  o[4] = rho * u1 * u2 + n12;
+  o[5] = rho * u2 * u2 + n22;
+  return ok;
+}
+
+// a, b, J, K of Eq. (flux-2D-1) (dir 1) / (flux-2D-2) (dir 2) for the Gaussian with moments q.
+__device__ __forceinline__ void abJK(const double q[6], int dir, double& a, double& b,
+                                     double J[6], double K[6]) {
+  const double rho = q[0];
+  const double u1 = q[1] / rho, u2 = q[2] / rho;
+  const double P11 = q[3] - rho * u1 * u1;
+  const double P12 = q[4] - rho * u1 * u2;
+  const double P22 = q[5] - rho * u2 * u2;
+  if (dir == 1) {
+    a = sqrt(2.0 * P11 / (kPi * rho)) * exp(-rho * u1 * u1 / (2.0 * P11));
+    b = erf(u1 * sqrt(rho / (2.0 * P11)));
+    J[0] = rho;
+    J[1] = rho * u1;
+    J[2] = rho * u2;
+    J[3] = rho * u1 * u1 + 2.0 * P11;
+    J[4] = rho * u1 * u2 + 2.0 * P12;
+    J[5] = rho * u2 * u2 + P22 + P12 * P12 / P11;
+    K[0] = rho * u1;
+    K[1] = rho * u1 * u1 + P11;
+    K[2] = rho * u1 * u2 + P12;
+    K[3] = rho * u1 * u1 * u1 + 3.0 * u1 * P11;
+    K[4] = rho * u1 * u1 * u2 + u2 * P11 + 2.0 * u1 * P12;
+    K[5] = rho * u1 * u2 * u2 + u1 * P22 + 2.0 * u2 * P12;
+  } else {
+    a = sqrt(2.0 * P22 / (kPi * rho)) * exp(-rho * u2 * u2 / (2.0 * P22));
+    b = erf(u2 * sqrt(rho / (2.0 * P22)));
+    J[0] = rho;
+    J[1] = rho * u1;
+    J[2] = rho * u2;
+    J[3] = rho * u1 * u1 + P11 + P12 * P12 / P22;
+    J[4] = rho * u1 * u2 + 2.0 * P12;
+    J[5] = rho * u2 * u2 + 2.0 * P22;
+    K[0] = rho * u2;
+    K[1] = rho * u1 * u2 + P12;
+    K[2] = rho * u2 * u2 + P22;
+    K[3] = rho * u1 * u1 * u2 + u2 * P11 + 2.0 * u1 * P12;
+    K[4] = rho * u1 * u2 * u2 + u1 * P22 + 2.0 * u2 * P12;
+    K[5] = rho * u2 * u2 * u2 + 3.0 * u2 * P22;
+  }
+}
+
+// Right-going half flux of the left state plus left-going half flux of the right state
+// (the integral form of Eq. flux-2D-1/2).
+__device__ __forceinline__ void kfvs_face(const double qa[6], const double qb[6], int dir,
+                                          double F[6]) {
+  double a, b, J[6], K[6];
+  abJK(qa, dir, a, b, J, K);
+  double Fp[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) Fp[m] = 0.5 * (a * J[m] + (1.0 + b) * K[m]);
+  abJK(qb, dir, a, b, J, K);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) F[m] = Fp[m] + 0.5 * (-a * J[m] + (1.0 - b) * K[m]);
+}
+
+__device__ __forceinline__ void kfvs_full(const double q[6], int dir, double F[6]) {
+  double a, b, J[6], K[6];
+  abJK(q, dir, a, b, J, K);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) F[m] = K[m];
+}
+
+__device__ __forceinline__ void mirror_q(const double q[6], int dir, double o[6]) {
+  o[0] = q[0];
+  o[1] = dir == 1 ? -q[1] : q[1];
+  o[2] = dir == 1 ? q[2] : -q[2];
+  o[3] = q[3];
+  o[4] = -q[4];
+  o[5] = q[5];
+}
+
+// Eq. (twodim_wall_densities_1)
+__device__ __forceinline__ double wall_R(double ua, double Taa, double Tw, double sgn) {
+  return sqrt(Taa / Tw) * exp(-ua * ua / (2.0 * Taa)) +
+         ua * sqrt(kPi / (2.0 * Tw)) * (erf(ua / sqrt(2.0 * Taa)) + sgn);
+}
+
+// Ghost state of a diffuse wall (Section 6.3): (rho_wall, wall velocity, T_wall I).
+__device__ __forceinline__ void wall_ghost(const KParams& p, const double q[6], int side,
+                                           double o[6]) {
+  const double rho = q[0];
+  const double u1 = q[1] / rho, u2 = q[2] / rho;
+  const double P11 = q[3] - rho * u1 * u1;
+  const double P22 = q[5] - rho * u2 * u2;
+  const double Tw = p.wall_T[side], U = p.wall_U[side];
+  double rw, g1, g2;
+  if (side < 2) {
+    rw = rho * wall_R(u1, P11 / rho, Tw, side == 0 ? -1.0 : 1.0);
+    g1 = 0.0;
+    g2 = U;
+  } else {
+    rw = rho * wall_R(u2, P22 / rho, Tw, side == 2 ? -1.0 : 1.0);
+    g1 = U;
+    g2 = 0.0;
+  }
+  o[0] = rw;
+  o[1] = rw * g1;
+  o[2] = rw * g2;
+  o[3] = rw * (g1 * g1 + Tw);
+  o[4] = rw * g1 * g2;
+  o[5] = rw * (g2 * g2 + Tw);
+}
+
+// Boundary flux through the face on side s of boundary cell state qc (dir = 1 for s = 0, 1).
+__device__ __forceinline__ void boundary_flux(const KParams& p, const double qc[6],
+                                              const double qper[6], int s, int dir, double F[6]) {
+  double g[6];
+  switch (p.bc[s]) {
+    case MM_BC_PERIODIC:
+      if (s == 0 || s == 2) kfvs_face(qper, qc, dir, F);
+      else kfvs_face(qc, qper, dir, F);
+      return;
+    case MM_BC_EXTRAP:
+      kfvs_full(qc, dir, F);
+      return;
+    case MM_BC_SPECULAR:
+      mirror_q(qc, dir, g);
+      break;
+    default:
+      wall_ghost(p, qc, s, g);
+      break;
+  }
+  if (s == 0 || s == 2) kfvs_face(g, qc, dir, F);
+  else kfvs_face(qc, g, dir, F);
+}
+
+// Heat-flux face value for component h at the face on side s of boundary cell value hc.
+__device__ __forceinline__ double boundary_H(const KParams& p, double hc, double hper, int s,
+                                             int h) {
+  switch (p.bc[s]) {
+    case MM_BC_PERIODIC: return 0.5 * (hc + hper);
+    case MM_BC_EXTRAP: return hc;
+    case MM_BC_SPECULAR: {
+      const bool odd = s < 2 ? (h == 0 || h == 2) : (h == 1 || h == 3);
+      return 0.5 * (hc + (odd ? -hc : hc));
+    }
+    default: return 0.5 * hc;
+  }
+}
+
+__global__ void k_prims(const double* __restrict__ Q, double* __restrict__ prim, KGrid g,
+                        KParams p, int* __restrict__ err) {
+  const int nc = g.nx * g.ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  double q[6];
+  load_q(Q, nc, c, q);
+  double rho, u1, u2, P11, P12, P22;
+  bool ok = prim6(q, rho, u1, u2, P11, P12, P22);
+  const double T = (P11 + P22) / (2.0 * rho);
+  const double nu = p.nu;
+  const double s11 = (1.0 - nu) * T + nu * (P11 / rho);
+  const double s12 = nu * (P12 / rho);
+  const double s22 = (1.0 - nu) * T + nu * (P22 / rho);
+  const double det = s11 * s22 - s12 * s12;
+  ok = ok && det > 0.0 && T > 0.0;
+  if (!ok) atomicOr(err, ERR_NONPHYS_PRIM);
+  prim[P_RHO * nc + c] = rho;
+  prim[P_U1 * nc + c] = u1;
+  prim[P_U2 * nc + c] = u2;
+  prim[P_T * nc + c] = T;
+  prim[P_TAU * nc + c] = tau_of(p, rho, T);
+  prim[P_TI11 * nc + c] = s22 / det;
+  prim[P_TI12 * nc + c] = -s12 / det;
+  prim[P_TI22 * nc + c] = s11 / det;
+  prim[P_KG * nc + c] = rho / sqrt(4.0 * kPi * kPi * det);
+  prim[P_TH11 * nc + c] = P11 / rho;
+  prim[P_TH22 * nc + c] = P22 / rho;
+}
+
+// Collision half step with tau^n, then x transport (Eq. 5-103, first line): Q^n -> Q**.
+__global__ void k_macro_x(const double* __restrict__ Qn, const double* __restrict__ H,
+                          double* __restrict__ Q2, KGrid g, KParams p, double dt, double eps,
+                          int* __restrict__ err) {
+  const int nc = g.nx * g.ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int i = c % g.nx, j = c / g.nx;
+  double q[6], qs[6], ql[6], qr[6], t[6];
+  bool ok = true;
+  load_q(Qn, nc, c, q);
+  ok &= coll_half(p, q, eps, dt, qs);
+  double FL[6], FR[6];
+  // left face
+  if (i > 0 || p.bc[0] == MM_BC_PERIODIC) {
+    const int cl = j * g.nx + (i > 0 ? i - 1 : g.nx - 1);
+    load_q(Qn, nc, cl, t);
+    ok &= coll_half(p, t, eps, dt, ql);
+  }
+  if (i > 0) kfvs_face(ql, qs, 1, FL);
+  else boundary_flux(p, qs, ql, 0, 1, FL);
+  // right face
+  if (i < g.nx - 1 || p.bc[1] == MM_BC_PERIODIC) {
+    const int cr = j * g.nx + (i < g.nx - 1 ? i + 1 : 0);
+    load_q(Qn, nc, cr, t);
+    ok &= coll_half(p, t, eps, dt, qr);
+  }
+  if (i < g.nx - 1) kfvs_face(qs, qr, 1, FR);
+  else boundary_flux(p, qs, qr, 1, 1, FR);
+  // heat-flux faces: components (H111, H112, H122) enter (E11, E12, E22)
+  double dH[3];
+  for (int h = 0; h < 3; ++h) {
+    const double hc = H[h * nc + c];
+    const double hl = H[h * nc + j * g.nx + (i > 0 ? i - 1 : g.nx - 1)];
+    const double hr = H[h * nc + j * g.nx + (i < g.nx - 1 ? i + 1 : 0)];
+    const double HL = i > 0 ? 0.5 * (hc + hl) : boundary_H(p, hc, hl, 0, h);
+    const double HR = i < g.nx - 1 ? 0.5 * (hr + hc) : boundary_H(p, hc, hr, 1, h);
+    dH[h] = HR - HL;
+  }
+  const double lam = dt / g.dx;
+  for (int m = 0; m < 6; ++m) {
+    double v = qs[m] - lam * (FR[m] - FL[m]);
+    if (m >= 3) v -= dt * (dH[m - 3] / g.dx);
+    Q2[m * nc + c] = v;
+  }
+  if (!ok) atomicOr(err, ERR_NONPHYS_MACRO);
+}
+
+// y transport (Eq. 5-103, second line), then the collision half step with tau***: Q** -> Q^{n+1}.
+__global__ void k_macro_y(const double* __restrict__ Q2, const double* __restrict__ H,
+                          double* __restrict__ Qn, KGrid g, KParams p, double dt, double eps,
+                          int* __restrict__ err) {
+  const int nc = g.nx * g.ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int i = c % g.nx, j = c / g.nx;
+  double q[6], qb[6], qt[6];
+  double r0, r1, r2, r3, r4, r5;
+  load_q(Q2, nc, c, q);
+  bool ok = prim6(q, r0, r1, r2, r3, r4, r5);
+  double FB[6], FT[6];
+  if (j > 0 || p.bc[2] == MM_BC_PERIODIC) {
+    load_q(Q2, nc, (j > 0 ? j - 1 : g.ny - 1) * g.nx + i, qb);
+    ok &= prim6(qb, r0, r1, r2, r3, r4, r5);
+  }
+  if (j > 0) kfvs_face(qb, q, 2, FB);
+  else boundary_flux(p, q, qb, 2, 2, FB);
+  if (j < g.ny - 1 || p.bc[3] == MM_BC_PERIODIC) {
+    load_q(Q2, nc, (j < g.ny - 1 ? j + 1 : 0) * g.nx + i, qt);
+    ok &= prim6(qt, r0, r1, r2, r3, r4, r5);
+  }
+  if (j < g.ny - 1) kfvs_face(q, qt, 2, FT);
+  else boundary_flux(p, q, qt, 3, 2, FT);
+  // heat-flux faces: components (H112, H122, H222) enter (E11, E12, E22)
+  double dH[3];
+  for (int h = 1; h < 4; ++h) {
+    const double hc = H[h * nc + c];
+    const double hb = H[h * nc + (j > 0 ? j - 1 : g.ny - 1) * g.nx + i];
+    const double ht = H[h * nc + (j < g.ny - 1 ? j + 1 : 0) * g.nx + i];
+    const double HB = j > 0 ? 0.5 * (hc + hb) : boundary_H(p, hc, hb, 2, h);
+    const double HT = j < g.ny - 1 ? 0.5 * (ht + hc) : boundary_H(p, hc, ht, 3, h);
+    dH[h - 1] = HT - HB;
+  }
+  const double lam = dt / g.dy;
+  double q3[6];
+  for (int m = 0; m < 6; ++m) {
+    double v = q[m] - lam * (FT[m] - FB[m]);
+    if (m >= 3) v -= dt * (dH[m - 3] / g.dy);
+    q3[m] = v;
+  }
+  double o[6];
+  ok &= coll_half(p, q3, eps, dt, o);
+  for (int m = 0; m < 6; ++m) Qn[m * nc + c] = o[m];
+  if (!ok) atomicOr(err, ERR_NONPHYS_MACRO);
+}
+
+}  // namespace
+
+void launch_prims(const double* Q, double* prim, const KGrid& g, const KParams& p, int* err,
+                  cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  k_prims<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, g, p, err);
+}
+
+void launch_macro_x(const double* Qn, const double* H, double* Q2, const KGrid& g,
+                    const KParams& p, double dt, double eps, int* err, cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  k_macro_x<<<(nc + 127) / 128, 128, 0, s>>>(Qn, H, Q2, g, p, dt, eps, err);
+}
+
+void launch_macro_y(const double* Q2, const double* H, double* Qn, const KGrid& g,
+                    const KParams& p, double dt, double eps, int* err, cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  k_macro_y<<<(nc + 127) / 128, 128, 0, s>>>(Q2, H, Qn, g, p, dt, eps, err);
+}
+
+}  // namespace mmk

@@ -1,0 +1,81 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every entry point that
+include/mmkfvs.h declares, and its host logic (time-step rule, argument validation) matches the
+oracle and the declared contract.  No GPU work is issued here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2509_21832_gb300 import api
+from paper_2509_21832_gb300 import inputs as I
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mm_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = api.load()
+    names = declared_symbols()
+    assert len(names) >= 16
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(api.EXPORTS) <= names
+
+
+def test_dt_rule_matches_oracle():
+    cases = [I.sod_1d2v().grid, I.Grid(nx=320, ny=320, x0=-1, x1=1, y0=-1, y1=1, v1min=-9, v1max=9,
+                                       v2min=-9, v2max=9),
+             I.Grid(nx=256, ny=256, nv1=32, nv2=32), I.Grid(nx=17, ny=5, v1min=-3, v1max=5)]
+    for g in cases:
+        for form in (I.CFL_MIN, I.CFL_SUM):
+            for tf in (0.0, 0.07, 0.2):
+                a = api.mm_dt_for_cfl(g, 0.8, tf, form)
+                b = O.dt_for_cfl(g, 0.8, tf, form)
+                assert a[1] == b[1] and abs(a[0] - b[0]) <= 1e-15 * b[0]
+
+
+def _create_status(grid, params):
+    L = api.load()
+    g, p = api.to_c_grid(grid), api.to_c_params(params)
+    ctx = ctypes.c_void_p()
+    return L.mm_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(ctx))
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda g, p: setattr(p, "nu", 1.0),
+    lambda g, p: setattr(p, "nu", -1.5),
+    lambda g, p: setattr(p, "bc", (I.PERIODIC, I.EXTRAP, I.EXTRAP, I.EXTRAP)),
+    lambda g, p: setattr(p, "bc", (I.SPECULAR,) * 4) or setattr(g, "v1min", -7.0),
+    lambda g, p: setattr(g, "nx", 0),
+    lambda g, p: setattr(g, "nv1", 0),
+    lambda g, p: setattr(g, "nv2", 2000),
+    lambda g, p: setattr(p, "precision", 7),
+    lambda g, p: setattr(p, "tau0", 0.0),
+    lambda g, p: setattr(p, "bc", (I.DIFFUSE,) * 4) or setattr(p, "wall_T", (1.0, 0.0, 1.0, 1.0)),
+    lambda g, p: setattr(g, "x1", g.x0),
+])
+def test_create_rejects_invalid_arguments_before_device_work(mutate):
+    g = I.Grid(nx=4, ny=4, nv1=8, nv2=8)
+    p = I.Params()
+    mutate(g, p)
+    assert _create_status(g, p) == api.MM_ERR_INVALID_ARG
+
+
+def test_device_bytes():
+    g = I.Grid(nx=256, ny=256, nv1=32, nv2=32)
+    p = I.Params(bc=(I.SPECULAR,) * 4)
+    b = api.mm_device_bytes(g, p)
+    assert b >= 2 * g.nphase * 8
+    p.precision = I.PREC_G_FP32
+    assert api.mm_device_bytes(g, p) < b

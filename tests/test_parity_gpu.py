@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA path (through the C ABI) against the plain FP64 CPU oracle.
+
+Macro fields must agree to 1e-12 in the per-component metric of helpers.q_rel_err; g and the
+heat flux are compared too.  Cases span several CTAs and ragged sizes (odd cell counts, velocity
+meshes whose v1 size does not fill whole warps), every boundary kind, anisotropic pressure
+tensors and non-zero initial g, the full 1D-2V shock-tube run, and the full 256^2 x 32^2
+specular workload through sampled one-step windows.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+from helpers import q_rel_err, rel_max
+from oracle import oracle as O
+from paper_2509_21832_gb300 import api
+from paper_2509_21832_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_Q = 1e-12
+ULP = 2.220446049250313e-16
+
+
+def g_floor(Q, eps):
+    """Absolute rounding floor of g: g carries (G - M)/eps, so a few-ulp difference in the two
+    Gaussians (evaluated in different but equivalent forms on each side) is amplified by 1/eps."""
+    rho = Q[0]
+    T = (Q[3] + Q[5] - (Q[1] ** 2 + Q[2] ** 2) / rho) / (2 * rho)
+    return 64 * ULP * np.max(rho / (2 * np.pi * T)) / eps
+
+
+def h_floor(Q):
+    """Absolute rounding floor of H = eps dv^2 sum c^3 g: the same few-ulp Gaussian differences,
+    times eps/eps, weighted by |c|^3 (E|c|^3 = 3.76 T^1.5 for the 2D Maxwellian)."""
+    rho = Q[0]
+    T = (Q[3] + Q[5] - (Q[1] ** 2 + Q[2] ** 2) / rho) / (2 * rho)
+    return 64 * ULP * 4.0 * np.max(rho * T ** 1.5)
+
+
+def run_gpu(grid, params, Q, G, dt, eps, nsteps):
+    with api.Solver(grid, params) as s:
+        s.set_state(Q, G)
+        s.step(dt, eps, nsteps)
+        s.sync()
+        Qg, Hg = s.get_moments()
+        Gg = s.get_g()
+    return Qg, Gg, Hg
+
+
+def check(grid, params, Q, G, dt, eps, nsteps, tol_q=TOL_Q, tol_g=1e-11):
+    Qg, Gg, Hg = run_gpu(grid, params, Q, G, dt, eps, nsteps)
+    Qo, Go, Ho = O.step(grid, params, Q, G, dt, eps, nsteps)
+    eq = q_rel_err(Qg, Qo)
+    assert np.all(eq <= tol_q), eq
+    gtol = max(tol_g * np.max(np.abs(Go)), g_floor(Qo, eps))
+    assert np.max(np.abs(Gg - Go)) <= gtol, (np.max(np.abs(Gg - Go)), gtol)
+    htol = max(tol_g * np.max(np.abs(Ho)), h_floor(Qo))
+    assert np.max(np.abs(Hg - Ho)) <= htol, (np.max(np.abs(Hg - Ho)), htol)
+    return eq
+
+
+def test_sod_1d2v_full_run():
+    pr = I.sod_1d2v()
+    eq = check(pr.grid, pr.params, pr.Q, pr.G, pr.dt, pr.eps, pr.nsteps)
+    print("sod 1d2v: max rel err", eq.max())
+
+
+CASES = [
+    # name, grid kwargs, bc, extra params
+    ("periodic_24", dict(nx=13, ny=11, nv1=24, nv2=24), (I.PERIODIC,) * 4, {}),
+    ("extrap_16", dict(nx=9, ny=14, nv1=16, nv2=16), (I.EXTRAP,) * 4, {}),
+    ("specular_32", dict(nx=10, ny=7, nv1=32, nv2=32), (I.SPECULAR,) * 4, {}),
+    ("mixed_diffuse_24", dict(nx=12, ny=9, nv1=24, nv2=24),
+     (I.EXTRAP, I.EXTRAP, I.DIFFUSE, I.EXTRAP), dict(wall_T=(1.0, 1.0, 1.1, 1.0))),
+    ("cavity_20", dict(nx=8, ny=8, nv1=20, nv2=20, v1min=-5, v1max=5, v2min=-5, v2max=5),
+     (I.DIFFUSE,) * 4, dict(wall_T=(1.0,) * 4, wall_U=(0.0, 0.0, 0.0, 0.16), nu=-1.0,
+                             tau_model=I.TAU_HARDSPHERE2D)),
+    ("cavity_literal_14", dict(nx=7, ny=6, nv1=14, nv2=14, v1min=-5, v1max=5, v2min=-5, v2max=5),
+     (I.DIFFUSE,) * 4, dict(wall_T=(0.9, 1.1, 1.0, 1.0), wall_U=(0.05, -0.1, 0.0, 0.2),
+                             wall_keep_es_term=0)),
+    ("odd_mesh_17x15", dict(nx=6, ny=5, nv1=17, nv2=15, v1min=-6, v1max=6, v2min=-6, v2max=6),
+     (I.PERIODIC, I.PERIODIC, I.SPECULAR, I.DIFFUSE), dict(tau_model=I.TAU_PRESSURE, nu=0.3)),
+    ("asym_mesh_extrap", dict(nx=5, ny=6, nv1=12, nv2=22, v1min=-5, v1max=7, v2min=-7, v2max=6),
+     (I.EXTRAP,) * 4, dict(tau_model=I.TAU_CONST, tau0=0.8)),
+]
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-1, 5.0])
+@pytest.mark.parametrize("name,gk,bc,extra", CASES, ids=[c[0] for c in CASES])
+def test_small_cases(name, gk, bc, extra, eps):
+    grid = I.Grid(**gk)
+    params = I.Params(bc=bc, **extra)
+    Q = I.smooth_state(grid, seed=zlib.crc32(name.encode()) % 1000, umax=0.25, aniso=0.08)
+    G = I.seeded_g(grid, seed=7, amp=0.02)
+    dt = O.dt_for_cfl(grid, 0.5, 0.0, I.CFL_SUM)[0]
+    check(grid, params, Q, G, dt, eps, 12)
+
+
+def test_one_cell_and_one_row():
+    g = I.Grid(nx=1, ny=1, nv1=8, nv2=8)
+    p = I.Params(bc=(I.PERIODIC,) * 4)
+    Q = I.q_from_prims(np.full((1, 1), 1.1), 0.2, -0.1, 0.9, 0.05, 0.02)
+    check(g, p, Q, I.seeded_g(g, 3), 1e-3, 0.05, 5)
+    g = I.Grid(nx=9, ny=1, nv1=8, nv2=8)
+    p = I.Params(bc=(I.SPECULAR, I.DIFFUSE, I.PERIODIC, I.PERIODIC))
+    Q = I.smooth_state(g, seed=5)
+    check(g, p, Q, I.seeded_g(g, 4), 5e-3, 0.05, 5)
+
+
+def test_long_velocity_mesh_large_shared_tables():
+    """nv2 = 600: the y kernel's shared tables exceed 48 KB."""
+    g = I.Grid(nx=3, ny=4, nv1=2, nv2=600, v1min=-6, v1max=6, v2min=-10, v2max=10)
+    p = I.Params(bc=(I.PERIODIC,) * 4)
+    Q = I.smooth_state(g, seed=9, umax=0.2)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    check(g, p, Q, I.seeded_g(g, 8), dt, 0.1, 3)
+
+
+def test_zero_steps_is_identity():
+    g = I.Grid(nx=5, ny=4, nv1=8, nv2=8)
+    p = I.Params(bc=(I.PERIODIC,) * 4)
+    Q = I.smooth_state(g, seed=1)
+    G = I.seeded_g(g, 2)
+    Qg, Gg, _ = run_gpu(g, p, Q, G, 1e-3, 0.1, 0)
+    assert np.array_equal(Qg, Q) and np.array_equal(Gg, G)
+
+
+def test_checkpoint_resume_bitwise():
+    g = I.Grid(nx=11, ny=9, nv1=16, nv2=16)
+    p = I.Params(bc=(I.SPECULAR, I.SPECULAR, I.EXTRAP, I.DIFFUSE))
+    Q = I.smooth_state(g, seed=17)
+    G = I.seeded_g(g, 18)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    Qa, Ga, Ha = run_gpu(g, p, Q, G, dt, 0.02, 10)
+    Q5, G5, _ = run_gpu(g, p, Q, G, dt, 0.02, 5)
+    Qb, Gb, Hb = run_gpu(g, p, Q5, G5, dt, 0.02, 5)
+    assert np.array_equal(Qa, Qb) and np.array_equal(Ga, Gb) and np.array_equal(Ha, Hb)
+
+
+def test_nonphysical_state_is_reported():
+    g = I.Grid(nx=6, ny=5, nv1=8, nv2=8)
+    p = I.Params(bc=(I.PERIODIC,) * 4)
+    Q = I.smooth_state(g, seed=1)
+    Q[0, 2, 3] = -1.0
+    with api.Solver(g, p) as s:
+        s.set_state(Q)
+        s.step(1e-3, 0.1, 1)
+        with pytest.raises(api.MMError) as e:
+            s.sync()
+        assert e.value.status == api.MM_ERR_NONPHYSICAL
+
+
+def test_step_before_state_and_bad_dt():
+    g = I.Grid(nx=4, ny=4, nv1=8, nv2=8)
+    with api.Solver(g, I.Params()) as s:
+        with pytest.raises(api.MMError) as e:
+            s.step(1e-3, 0.1, 1)
+        assert e.value.status == api.MM_ERR_STATE
+        s.set_state(I.smooth_state(g, 1))
+        for dt, eps in ((0.0, 0.1), (1e-3, -1.0), (float("nan"), 0.1)):
+            with pytest.raises(api.MMError) as e:
+                s.step(dt, eps, 1)
+            assert e.value.status == api.MM_ERR_INVALID_ARG
+
+
+def test_conservation_periodic_gpu():
+    g = I.Grid(nx=64, ny=48, nv1=24, nv2=24)
+    p = I.Params(bc=(I.PERIODIC,) * 4)
+    Q = I.smooth_state(g, seed=3)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    Qg, _, _ = run_gpu(g, p, Q, I.seeded_g(g, 4), dt, 0.01, 50)
+    for m in (0, 1, 2):
+        assert abs(Qg[m].sum() - Q[m].sum()) <= 1e-13 * Q[0].sum() * 1
+    assert abs((Qg[3] + Qg[5]).sum() - (Q[3] + Q[5]).sum()) <= 1e-13 * (Q[3] + Q[5]).sum()
+
+
+# ---------------------------------------------------------------------------------------------
+# full-size 256^2 x 32^2 specular workload: sampled one-step windows against the oracle
+# ---------------------------------------------------------------------------------------------
+def _window(pr, Q, G, i0, j0, w):
+    g = pr.grid
+    dx, dy = (g.x1 - g.x0) / g.nx, (g.y1 - g.y0) / g.ny
+    i0c, j0c = max(0, i0), max(0, j0)
+    i1c, j1c = min(g.nx, i0 + w), min(g.ny, j0 + w)
+    sub = I.Grid(nx=i1c - i0c, ny=j1c - j0c, x0=g.x0 + i0c * dx, x1=g.x0 + i1c * dx,
+                 y0=g.y0 + j0c * dy, y1=g.y0 + j1c * dy, nv1=g.nv1, nv2=g.nv2, v1min=g.v1min,
+                 v1max=g.v1max, v2min=g.v2min, v2max=g.v2max)
+    bc = list(pr.params.bc)
+    if i0c > 0:
+        bc[0] = I.EXTRAP
+    if i1c < g.nx:
+        bc[1] = I.EXTRAP
+    if j0c > 0:
+        bc[2] = I.EXTRAP
+    if j1c < g.ny:
+        bc[3] = I.EXTRAP
+    p = I.Params(**{**pr.params.__dict__, "bc": tuple(bc)})
+    return sub, p, np.ascontiguousarray(Q[:, j0c:j1c, i0c:i1c]), \
+        np.ascontiguousarray(G[j0c:j1c, i0c:i1c]), (i0c, j0c)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-1])
+def test_full_size_bump_specular_sampled(eps):
+    pr = I.bump_specular(eps=eps, seed=0)
+    with api.Solver(pr.grid, pr.params) as s:
+        s.set_state(pr.Q, pr.G)
+        s.step(pr.dt, pr.eps, 8)
+        Q8, _ = s.get_moments()
+        G8 = s.get_g()
+        s.step(pr.dt, pr.eps, 1)
+        Q9, H9 = s.get_moments()
+        G9 = s.get_g()
+    x0, y0 = pr.meta["x0"]
+    ic, jc = int(x0 * pr.grid.nx), int(y0 * pr.grid.ny)
+    targets = [(0, 0), (255, 0), (0, 255), (255, 255), (128, 0), (0, 77), (ic, jc),
+               (ic + 9, jc - 5), (200, 31)]
+    w = 7
+    gtol = max(1e-11 * np.max(np.abs(G9)), g_floor(Q9, pr.eps))
+    htol = max(1e-11 * np.max(np.abs(H9)), h_floor(Q9))
+    for (ti, tj) in targets:
+        sub, p, Qw, Gw, (oi, oj) = _window(pr, Q8, G8, ti - w // 2, tj - w // 2, w)
+        Qo, Go, Ho = O.step(sub, p, Qw, Gw, pr.dt, pr.eps, 1)
+        li, lj = ti - oi, tj - oj
+        qg, qo = Q9[:, tj, ti], Qo[:, lj, li]
+        scale = max(np.max(np.abs(Qo[0])), 1.0)
+        assert np.max(np.abs(qg - qo)) <= TOL_Q * scale, (ti, tj, qg - qo)
+        # g and H errors relative to the field's global scale (far from the bump g is round-off)
+        assert np.max(np.abs(G9[tj, ti] - Go[lj, li])) <= gtol, (ti, tj)
+        assert np.max(np.abs(H9[:, tj, ti] - Ho[:, lj, li])) <= htol, (ti, tj)
+    # properties that hold at any size: specular walls conserve mass and energy to round-off
+    assert abs(Q9[0].sum() - pr.Q[0].sum()) <= 1e-13 * pr.Q[0].sum()
+    assert abs((Q9[3] + Q9[5]).sum() - (pr.Q[3] + pr.Q[5]).sum()) <= 1e-13 * (pr.Q[3] + pr.Q[5]).sum()
