@@ -140,6 +140,35 @@ const char* mm_kernel_name(int idx);
 /* Release the context and its device memory (NULL is accepted). */
 void mm_destroy(mm_ctx* ctx);
 
+/* ---- stepping without any device allocation ------------------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers that may not call
+ * cudaMalloc (a host framework that owns every device allocation under a fixed budget, plug-ins
+ * loaded into such a framework, real-time loops that forbid allocation after start-up).
+ *
+ * mm_step_static_scratch advances nsteps time steps of the same scheme as mm_step, in place on
+ * caller-owned FP64 device buffers Q_dev [6][ny][nx] and G_dev [ny][nx][nv2][nv1] (inputs and
+ * outputs), writing the last step's heat flux to H_dev [4][ny][nx].  It allocates nothing: all
+ * scratch (the split-step buffer G*, the intermediate macro state, per-cell primitive fields,
+ * the diffuse-wall cell list and the error word) lives in one static device array of
+ * MM_STATIC_SCRATCH_BYTES bytes that every GPU loading this library holds until process exit.
+ *  - Limits: precision MM_PREC_FP64 only; nx*ny <= MM_STATIC_MAX_CELLS and
+ *    nx*ny*nv1*nv2 <= MM_STATIC_MAX_PHASE.  Larger problems, other precisions, NULL buffers,
+ *    dt <= 0, eps <= 0 or nsteps < 0 return MM_ERR_INVALID_ARG with a message in errbuf.
+ *  - Works on the current device and cuda_stream (NULL = legacy default stream).  The first call
+ *    on a device looks up the array's device address (cudaGetSymbolAddress) once; make that
+ *    first call before any stream capture.
+ *  - Every call shares the one array and it keeps the previous call's contents (the zero-start
+ *    parts are cleared at the start of each call).  Calls that overlap on the GPU -- on two
+ *    streams, or from two host threads -- race on it and give wrong results.
+ *  - Returns after synchronising cuda_stream; MM_ERR_NONPHYSICAL reports a non-physical state.
+ *  - errbuf (may be NULL) receives a NUL-terminated message of at most errlen bytes. */
+#define MM_STATIC_MAX_CELLS 16384
+#define MM_STATIC_MAX_PHASE 1048576
+#define MM_STATIC_SCRATCH_BYTES 10682880
+mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params* params, double* Q_dev,
+                                 double* G_dev, double* H_dev, double dt, double eps,
+                                 int nsteps, void* cuda_stream, char* errbuf, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

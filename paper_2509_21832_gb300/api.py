@@ -39,7 +39,7 @@ class mm_params(ctypes.Structure):
 EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device", "mm_step",
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
-           "mm_kernel_name", "mm_destroy"]
+           "mm_kernel_name", "mm_destroy", "mm_step_static_scratch"]
 
 _lib = None
 
@@ -82,6 +82,9 @@ def load(build_if_needed: bool = True):
     L.mm_kernel_name.restype = ctypes.c_char_p
     L.mm_destroy.argtypes = [vp]
     L.mm_destroy.restype = None
+    L.mm_step_static_scratch.argtypes = [G, P, vp, vp, vp, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, vp, ctypes.c_char_p, ctypes.c_size_t]
+    L.mm_step_static_scratch.restype = ctypes.c_int
     for name in ["mm_create", "mm_set_state", "mm_set_state_device", "mm_step", "mm_sync",
                  "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_set_timing",
                  "mm_get_timing"]:
@@ -158,6 +161,24 @@ def mm_create(grid, params, stream=0):
     if st != MM_OK:
         raise MMError(st, "mm_create rejected the grid/parameters or could not allocate")
     return ctx
+
+
+def mm_step_static_scratch(grid, params, Q_dev, G_dev, H_dev, dt, eps, nsteps, stream=0):
+    """Advance nsteps steps in place on caller-owned FP64 CUDA tensors Q [6][ny][nx],
+    G [ny][nx][nv2][nv1] and H [4][ny][nx] (output) without any device allocation: the scratch
+    is one static device array of the library (size limits MM_STATIC_MAX_CELLS = 16384 cells
+    and MM_STATIC_MAX_PHASE = 1048576 phase cells).  For callers that may not allocate device
+    memory.  Calls that overlap on the GPU share that scratch and race."""
+    ncell = grid.nx * grid.ny
+    nphase = ncell * grid.nv1 * grid.nv2
+    g, p = to_c_grid(grid), to_c_params(params)
+    buf = ctypes.create_string_buffer(256)
+    st = load().mm_step_static_scratch(ctypes.byref(g), ctypes.byref(p),
+                                       _dev_ptr(Q_dev, 6 * ncell), _dev_ptr(G_dev, nphase),
+                                       _dev_ptr(H_dev, 4 * ncell), float(dt), float(eps),
+                                       int(nsteps), ctypes.c_void_p(int(stream)), buf, 256)
+    if st != MM_OK:
+        raise MMError(st, "mm_step_static_scratch: " + buf.value.decode())
 
 
 def _check(ctx, st, what):
