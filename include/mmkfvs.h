@@ -140,6 +140,13 @@ const char* mm_kernel_name(int idx);
 /* Release the context and its device memory (NULL is accepted). */
 void mm_destroy(mm_ctx* ctx);
 
+/* Diagnostic: evaluate the table-driven exponential used by the phase-space kernels (Tang's
+ * method, see the micro kernels) and the CUDA library exp on n FP64 device values x_dev, into
+ * caller-owned device arrays; synchronises cuda_stream.  Used to test the kernels' exp against
+ * the library exp. */
+mm_status mm_diag_exp(const double* x_dev, double* y_fast_dev, double* y_lib_dev, size_t n,
+                      void* cuda_stream);
+
 /* ---- stepping without any device allocation ------------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers that may not call
  * cudaMalloc (a host framework that owns every device allocation under a fixed budget, plug-ins
@@ -164,7 +171,7 @@ void mm_destroy(mm_ctx* ctx);
  *  - errbuf (may be NULL) receives a NUL-terminated message of at most errlen bytes. */
 #define MM_STATIC_MAX_CELLS 16384
 #define MM_STATIC_MAX_PHASE 1048576
-#define MM_STATIC_SCRATCH_BYTES 10682880
+#define MM_STATIC_SCRATCH_BYTES 12780032
 mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params* params, double* Q_dev,
                                  double* G_dev, double* H_dev, double dt, double eps,
                                  int nsteps, void* cuda_stream, char* errbuf, size_t errlen);

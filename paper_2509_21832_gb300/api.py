@@ -39,7 +39,7 @@ class mm_params(ctypes.Structure):
 EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device", "mm_step",
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
-           "mm_kernel_name", "mm_destroy", "mm_step_static_scratch"]
+           "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp"]
 
 _lib = None
 
@@ -82,6 +82,8 @@ def load(build_if_needed: bool = True):
     L.mm_kernel_name.restype = ctypes.c_char_p
     L.mm_destroy.argtypes = [vp]
     L.mm_destroy.restype = None
+    L.mm_diag_exp.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
+    L.mm_diag_exp.restype = ctypes.c_int
     L.mm_step_static_scratch.argtypes = [G, P, vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, vp, ctypes.c_char_p, ctypes.c_size_t]
     L.mm_step_static_scratch.restype = ctypes.c_int
@@ -179,6 +181,17 @@ def mm_step_static_scratch(grid, params, Q_dev, G_dev, H_dev, dt, eps, nsteps, s
                                        int(nsteps), ctypes.c_void_p(int(stream)), buf, 256)
     if st != MM_OK:
         raise MMError(st, "mm_step_static_scratch: " + buf.value.decode())
+
+
+def mm_diag_exp(x_dev, stream=0):
+    """(fast, library) exponentials of a CUDA float64 tensor, computed on the device."""
+    import torch
+    yf, yl = torch.empty_like(x_dev), torch.empty_like(x_dev)
+    st = load().mm_diag_exp(x_dev.data_ptr(), yf.data_ptr(), yl.data_ptr(), x_dev.numel(),
+                            ctypes.c_void_p(int(stream)))
+    if st != MM_OK:
+        raise MMError(st, "mm_diag_exp")
+    return yf, yl
 
 
 def _check(ctx, st, what):

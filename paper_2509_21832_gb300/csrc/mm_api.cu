@@ -167,7 +167,7 @@ void enqueue_step(mm_ctx* c, double dt, double eps) {
   const KGrid& g = c->kg;
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
-  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, g, p, c->err, s); });
+  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, g, p, dt, eps, c->err, s); });
   timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
   timed(c, T_MICRO_Y, [&] { launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s); });
   if (c->n_wall > 0)
@@ -261,6 +261,8 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
   kg.nv2 = grid->nv2;
   kg.dx = (grid->x1 - grid->x0) / grid->nx;
   kg.dy = (grid->y1 - grid->y0) / grid->ny;
+  kg.idx = 1.0 / kg.dx;
+  kg.idy = 1.0 / kg.dy;
   kg.v1min = grid->v1min;
   kg.v2min = grid->v2min;
   kg.dv1 = (grid->v1max - grid->v1min) / grid->nv1;

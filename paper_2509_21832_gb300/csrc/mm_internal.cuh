@@ -11,6 +11,7 @@ namespace mmk {
 struct KGrid {
   int nx, ny, nv1, nv2;
   double dx, dy, v1min, v2min, dv1, dv2;
+  double idx, idy;  // 1/dx, 1/dy
 };
 
 // Physical parameters used on the device.
@@ -22,12 +23,23 @@ struct KParams {
   int keep_es;
 };
 
-// Per-cell primitive fields produced by the prims kernel, SoA [NPRIM][ny][nx].
+// Per-cell fields produced by the prims kernel, SoA [NPRIM][ny][nx]: primitive variables of
+// Q^n, then per-cell coefficients of the micro step (they depend on dt, eps and, through the
+// discrete strain and temperature gradient of Eq. 5-97more, on the neighbours), computed once
+// per cell so that the phase-space kernels never divide or repeat per-cell work in every lane.
 enum PrimField {
   P_RHO = 0, P_U1, P_U2, P_T, P_TAU,
   P_TI11, P_TI12, P_TI22,  // inverse of the ES tensor Tcal (Eq. 2-19)
   P_KG,                    // rho / (2 pi sqrt(det Tcal)): normalisation of the ES Gaussian
   P_TH11, P_TH22,          // diagonal of the temperature tensor P / rho
+  P_IT, P_INV2T,           // 1/T, 1/(2T)
+  P_KAP,                   // dt dv1 dv2 / (2 pi T): Zhat = kap/dt e1 e2 (projection polynomial)
+  P_OM1, P_OM1KAP,         // eps/(eps + dt tau), and times kap
+  P_GAM0,                  // om2/eps * KG: prefactor of the ES Gaussian in the relaxation
+  P_OME,                   // om2 mu / eps, mu = rho/(2 pi T)
+  // om2 mu / tau times the coefficients of B:sigma + C.grad T as a cubic in c2 (Eq. 5-69):
+  // p0 = c1 (w01 + c1 (w02 + c1 w03)), p1 = w10 + c1 (w11 + c1 w12), p2 = w20 + c1 w21, p3 = w30
+  P_W01, P_W02, P_W03, P_W10, P_W11, P_W12, P_W20, P_W21, P_W30,
   NPRIM
 };
 
@@ -45,8 +57,8 @@ MicroShape micro_shape(int nv1, int nv2);
 // Kernel kinds, for per-kernel timing.
 enum KernelKind { KK_PRIMS = 0, KK_MICRO_X, KK_MICRO_Y, KK_MACRO_X, KK_MACRO_Y, KK_COUNT };
 
-void launch_prims(const double* Q, double* prim, const KGrid& g, const KParams& p, int* err,
-                  cudaStream_t s);
+void launch_prims(const double* Q, double* prim, const KGrid& g, const KParams& p, double dt,
+                  double eps, int* err, cudaStream_t s);
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s);
@@ -62,6 +74,7 @@ void launch_macro_x(const double* Qn, const double* H, double* Q2, const KGrid& 
                     const KParams& p, double dt, double eps, int* err, cudaStream_t s);
 void launch_macro_y(const double* Q2, const double* H, double* Qn, const KGrid& g,
                     const KParams& p, double dt, double eps, int* err, cudaStream_t s);
+void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s);
 void launch_convert_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
 

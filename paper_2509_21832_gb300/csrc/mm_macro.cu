@@ -206,11 +206,50 @@ __device__ __forceinline__ double boundary_H(const KParams& p, double hc, double
   }
 }
 
+// (u1, u2, T) of cell c from its moments.
+__device__ __forceinline__ void uT_of(const double* Q, int nc, int c, double& u1, double& u2,
+                                      double& T) {
+  const double rho = Q[c];
+  u1 = Q[nc + c] / rho;
+  u2 = Q[2 * nc + c] / rho;
+  const double P11 = Q[3 * nc + c] - rho * u1 * u1;
+  const double P22 = Q[5 * nc + c] - rho * u2 * u2;
+  T = (P11 + P22) / (2.0 * rho);
+}
+
+// (u1, u2, T) across side s of cell (i, j) for the centred differences of Eq. (5-97more): the
+// neighbour (periodic wrap), the cell itself (extrapolation; diffuse-wall cells do not use these
+// values), or the mirrored ghost (specular: normal velocity negated).
+__device__ __forceinline__ void side_uT(const double* Q, const KGrid& g, const KParams& p, int nc,
+                                        int i, int j, int s, double cu1, double cu2, double cT,
+                                        double& u1, double& u2, double& T) {
+  int ni = i + (s == 0 ? -1 : s == 1 ? 1 : 0);
+  int nj = j + (s == 2 ? -1 : s == 3 ? 1 : 0);
+  bool inside = ni >= 0 && ni < g.nx && nj >= 0 && nj < g.ny;
+  if (!inside && p.bc[s] == MM_BC_PERIODIC) {
+    ni = (ni + g.nx) % g.nx;
+    nj = (nj + g.ny) % g.ny;
+    inside = true;
+  }
+  if (inside) {
+    uT_of(Q, nc, nj * g.nx + ni, u1, u2, T);
+  } else if (p.bc[s] == MM_BC_SPECULAR) {
+    u1 = s < 2 ? -cu1 : cu1;
+    u2 = s < 2 ? cu2 : -cu2;
+    T = cT;
+  } else {
+    u1 = cu1;
+    u2 = cu2;
+    T = cT;
+  }
+}
+
 __global__ void k_prims(const double* __restrict__ Q, double* __restrict__ prim, KGrid g,
-                        KParams p, int* __restrict__ err) {
+                        KParams p, double dt, double eps, int* __restrict__ err) {
   const int nc = g.nx * g.ny;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
+  const int i = c % g.nx, j = c / g.nx;
   double q[6];
   load_q(Q, nc, c, q);
   double rho, u1, u2, P11, P12, P22;
@@ -223,17 +262,59 @@ __global__ void k_prims(const double* __restrict__ Q, double* __restrict__ prim,
   const double det = s11 * s22 - s12 * s12;
   ok = ok && det > 0.0 && T > 0.0;
   if (!ok) atomicOr(err, ERR_NONPHYS_PRIM);
+  const double tau = tau_of(p, rho, T);
+  const double KG = rho / sqrt(4.0 * kPi * kPi * det);
   prim[P_RHO * nc + c] = rho;
   prim[P_U1 * nc + c] = u1;
   prim[P_U2 * nc + c] = u2;
   prim[P_T * nc + c] = T;
-  prim[P_TAU * nc + c] = tau_of(p, rho, T);
+  prim[P_TAU * nc + c] = tau;
   prim[P_TI11 * nc + c] = s22 / det;
   prim[P_TI12 * nc + c] = -s12 / det;
   prim[P_TI22 * nc + c] = s11 / det;
-  prim[P_KG * nc + c] = rho / sqrt(4.0 * kPi * kPi * det);
+  prim[P_KG * nc + c] = KG;
   prim[P_TH11 * nc + c] = P11 / rho;
   prim[P_TH22 * nc + c] = P22 / rho;
+
+  // discrete strain and temperature gradient, Eqs. (5-97), (5-97more)
+  double uL1, uL2, TL, uR1, uR2, TR, uB1, uB2, TB, uT1, uT2, TT;
+  side_uT(Q, g, p, nc, i, j, 0, u1, u2, T, uL1, uL2, TL);
+  side_uT(Q, g, p, nc, i, j, 1, u1, u2, T, uR1, uR2, TR);
+  side_uT(Q, g, p, nc, i, j, 2, u1, u2, T, uB1, uB2, TB);
+  side_uT(Q, g, p, nc, i, j, 3, u1, u2, T, uT1, uT2, TT);
+  const double dTdx = (0.5 * (TR + T) - 0.5 * (T + TL)) / g.dx;
+  const double dTdy = (0.5 * (TT + T) - 0.5 * (T + TB)) / g.dy;
+  const double Dxu1 = (uR1 - uL1) / 2.0, Dxu2 = (uR2 - uL2) / 2.0;
+  const double Dyu1 = (uT1 - uB1) / 2.0, Dyu2 = (uT2 - uB2) / 2.0;
+  const double sg11 = Dxu1 / g.dx - Dyu2 / g.dy;
+  const double sg12 = Dyu1 / g.dy + Dxu2 / g.dx;
+
+  const double iT = 1.0 / T;
+  const double kap = dt * g.dv1 * g.dv2 / (2.0 * kPi * T);
+  const double om1 = eps / (eps + dt * tau);
+  const double om2 = dt * tau / (eps + dt * tau);
+  const double mu = rho / (2.0 * kPi * T);
+  const double wt = om2 * mu / tau;
+  const double h2T2 = 0.5 * iT * iT;
+  prim[P_IT * nc + c] = iT;
+  prim[P_INV2T * nc + c] = 0.5 / T;
+  prim[P_KAP * nc + c] = kap;
+  prim[P_OM1 * nc + c] = om1;
+  prim[P_OM1KAP * nc + c] = om1 * kap;
+  prim[P_GAM0 * nc + c] = om2 / eps * KG;
+  prim[P_OME * nc + c] = om2 * mu / eps;
+  // B:sigma + C.grad T = p0 + p1 c2 + p2 c2^2 + p3 c2^3 (Eq. 5-69) with
+  // p0 = (s11/2T) c1^2 + (Tx/2T^2) c1^3 - (2Tx/T) c1, p1 = (s12/T) c1 + (Ty/2T^2) c1^2 - 2Ty/T,
+  // p2 = -s11/2T + (Tx/2T^2) c1, p3 = Ty/2T^2; stored times om2 mu / tau
+  prim[P_W01 * nc + c] = wt * (-2.0 * dTdx * iT);
+  prim[P_W02 * nc + c] = wt * (0.5 * sg11 * iT);
+  prim[P_W03 * nc + c] = wt * (h2T2 * dTdx);
+  prim[P_W10 * nc + c] = wt * (-2.0 * dTdy * iT);
+  prim[P_W11 * nc + c] = wt * (sg12 * iT);
+  prim[P_W12 * nc + c] = wt * (h2T2 * dTdy);
+  prim[P_W20 * nc + c] = wt * (-0.5 * sg11 * iT);
+  prim[P_W21 * nc + c] = wt * (h2T2 * dTdx);
+  prim[P_W30 * nc + c] = wt * (h2T2 * dTdy);
 }
 
 // Collision half step with tau^n, then x transport (Eq. 5-103, first line): Q^n -> Q**.
@@ -334,10 +415,10 @@ __global__ void k_macro_y(const double* __restrict__ Q2, const double* __restric
 
 }  // namespace
 
-void launch_prims(const double* Q, double* prim, const KGrid& g, const KParams& p, int* err,
-                  cudaStream_t s) {
+void launch_prims(const double* Q, double* prim, const KGrid& g, const KParams& p, double dt,
+                  double eps, int* err, cudaStream_t s) {
   const int nc = g.nx * g.ny;
-  k_prims<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, g, p, err);
+  k_prims<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, g, p, dt, eps, err);
 }
 
 void launch_macro_x(const double* Qn, const double* H, double* Q2, const KGrid& g,

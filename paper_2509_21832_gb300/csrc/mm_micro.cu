@@ -12,6 +12,7 @@
 // order of its rows, then combined across the CTA with warp shuffles and shared memory.
 #include <cmath>
 
+#include "mm_exp.cuh"
 #include "mm_internal.cuh"
 
 namespace mmk {
@@ -95,41 +96,14 @@ __device__ __forceinline__ bool diffuse_wall_cell(const KGrid& g, const KParams&
          (j == 0 && p.bc[2] == MM_BC_DIFFUSE) || (j == g.ny - 1 && p.bc[3] == MM_BC_DIFFUSE);
 }
 
-// (u1, u2, T) across side s of cell (i, j) for the centred differences of Eq. (5-97more):
-// neighbour (periodic wrap), the cell itself (extrapolation), or the mirrored ghost (specular).
-__device__ __forceinline__ void side_uT(const KGrid& g, const KParams& p, const double* prim,
-                                        int nc, int i, int j, int s, double c_u1, double c_u2,
-                                        double c_T, double& u1, double& u2, double& T) {
-  int ni = i + (s == 0 ? -1 : s == 1 ? 1 : 0);
-  int nj = j + (s == 2 ? -1 : s == 3 ? 1 : 0);
-  bool inside = ni >= 0 && ni < g.nx && nj >= 0 && nj < g.ny;
-  if (!inside && p.bc[s] == MM_BC_PERIODIC) {
-    ni = (ni + g.nx) % g.nx;
-    nj = (nj + g.ny) % g.ny;
-    inside = true;
-  }
-  if (inside) {
-    const int c = nj * g.nx + ni;
-    u1 = prim[P_U1 * nc + c];
-    u2 = prim[P_U2 * nc + c];
-    T = prim[P_T * nc + c];
-  } else if (p.bc[s] == MM_BC_SPECULAR) {
-    u1 = s < 2 ? -c_u1 : c_u1;
-    u2 = s < 2 ? c_u2 : -c_u2;
-    T = c_T;
-  } else {
-    u1 = c_u1;
-    u2 = c_u2;
-    T = c_T;
-  }
-}
-
 // ------------------------------------------------------------------------------------------
 // x sweep: Eqs. (zmicrox), (coeffs-2D-xdir), (zhat-2D-xdir), (update-micro-2D-xdir)
 // ------------------------------------------------------------------------------------------
 template <typename Tg>
-__global__ void __launch_bounds__(512, 1) k_micro_x(const Tg* __restrict__ Gin, Tg* __restrict__ Gout,
-                          const double* __restrict__ prim, KGrid g, KParams p, double dt, int R) {
+__global__ void __launch_bounds__(512, 1) k_micro_x(const Tg* __restrict__ Gin,
+                                                    Tg* __restrict__ Gout,
+                                                    const double* __restrict__ prim, KGrid g,
+                                                    KParams p, double dtidx, int R) {
   extern __shared__ double sm[];
   const int nv1 = g.nv1, nv2 = g.nv2;
   double* red = sm;
@@ -145,24 +119,23 @@ __global__ void __launch_bounds__(512, 1) k_micro_x(const Tg* __restrict__ Gin, 
   const int k = t % nv1, r = t / nv1;
   const bool active = r < R;
 
-  const double rho = prim[P_RHO * nc + cell];
   const double u1 = prim[P_U1 * nc + cell], u2 = prim[P_U2 * nc + cell];
-  const double T = prim[P_T * nc + cell];
-  (void)rho;
-  const double inv2T = 0.5 / T, iT = 1.0 / T;
+  const double inv2T = prim[P_INV2T * nc + cell], iT = prim[P_IT * nc + cell];
+  const double kap = prim[P_KAP * nc + cell];
 
   for (int l = t; l < nv2; l += blockDim.x) {
-    const double c2 = g.v2min + (l + 0.5) * g.dv2 - u2;
+    const double c2 = fma(l + 0.5, g.dv2, g.v2min) - u2;
+    const double q = c2 * c2;
     c2t[l] = c2;
-    c2q[l] = c2 * c2;
-    e2t[l] = exp(-c2 * c2 * inv2T);
+    c2q[l] = q;
+    e2t[l] = expd(-q * inv2T);
   }
 
-  const double v1 = g.v1min + (k + 0.5) * g.dv1;
+  const double v1 = fma(k + 0.5, g.dv1, g.v1min);
   const double c1 = v1 - u1;
   const double av = fabs(v1);
-  const double sig = -av / g.dx;     // Z = sig * (G_up - G)
-  const double lam = dt * av / g.dx; // -dt Z = lam * (G_up - G)
+  const double sig = -av * g.idx;  // Z = sig * (G_up - G)
+  const double lam = av * dtidx;   // -dt Z = lam * (G_up - G)
   const Upwind up = upwind_x(g, p, i, j, v1 > 0.0 ? 0 : 1);
   const int ku = up.mirror ? nv1 - 1 - k : k;
   const size_t nv = (size_t)nv1 * nv2;
@@ -182,16 +155,16 @@ __global__ void __launch_bounds__(512, 1) k_micro_x(const Tg* __restrict__ Gin, 
       D2 = fma(c2q[l], d, D2);
     }
   }
-  double S[4] = {sig * D0, sig * c1 * D0, sig * D1, sig * fma(c1 * c1, D0, D2)};
+  const double sD0 = sig * D0;
+  double S[4] = {sD0, c1 * sD0, sig * D1, fma(c1 * c1, sD0, sig * D2)};
   block_sum4(S, red);
 
   // projection coefficients: Zhat = (dv1 dv2 / (2 pi T)) e1 e2 (b0 + b1 c1 + b2 c2 + gm |c|^2)
-  const double b0 = 2.0 * S[0] - S[3] * inv2T;
+  const double b0 = fma(-S[3], inv2T, 2.0 * S[0]);
   const double b1 = S[1] * iT, b2 = S[2] * iT;
-  const double gm = 0.25 * S[3] * iT * iT - S[0] * inv2T;
-  const double kap = dt * g.dv1 * g.dv2 / (2.0 * kPi * T);
+  const double gm = fma(0.25 * S[3], iT * iT, -S[0] * inv2T);
   for (int l = t; l < nv2; l += blockDim.x) qet[l] = e2t[l] * fma(b2, c2t[l], gm * c2q[l]);
-  const double e1 = exp(-c1 * c1 * inv2T);
+  const double e1 = expd(-c1 * c1 * inv2T);
   const double bk = kap * e1;
   const double ak = bk * fma(gm * c1, c1, fma(b1, c1, b0));
   __syncthreads();
@@ -218,9 +191,12 @@ __global__ void __launch_bounds__(512, 1) k_micro_x(const Tg* __restrict__ Gin, 
 constexpr int kYTables = 13;
 
 template <typename Tg>
-__global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs, Tg* __restrict__ Gout,
-                          double* __restrict__ Hout, const double* __restrict__ prim, KGrid g,
-                          KParams p, double dt, double eps, int R, int* __restrict__ err) {
+__global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs,
+                                                    Tg* __restrict__ Gout,
+                                                    double* __restrict__ Hout,
+                                                    const double* __restrict__ prim, KGrid g,
+                                                    KParams p, double dtidy, double hscale, int R,
+                                                    int* __restrict__ err) {
   extern __shared__ double sm[];
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;
@@ -248,51 +224,34 @@ __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs, T
   const int k = t % nv1, r = t / nv1;
   const bool active = r < R;
 
-  const double rho = prim[P_RHO * nc + cell];
   const double u1 = prim[P_U1 * nc + cell], u2 = prim[P_U2 * nc + cell];
-  const double T = prim[P_T * nc + cell];
-  const double tau = prim[P_TAU * nc + cell];
+  const double inv2T = prim[P_INV2T * nc + cell], iT = prim[P_IT * nc + cell];
   const double Ti11 = prim[P_TI11 * nc + cell], Ti12 = prim[P_TI12 * nc + cell];
   const double Ti22 = prim[P_TI22 * nc + cell];
-  const double KG = prim[P_KG * nc + cell];
-  const double inv2T = 0.5 / T, iT = 1.0 / T;
-  const double om1 = eps / (eps + dt * tau);
-  const double om2 = dt * tau / (eps + dt * tau);
+  const double om1 = prim[P_OM1 * nc + cell], om1kap = prim[P_OM1KAP * nc + cell];
+  const double gam0 = prim[P_GAM0 * nc + cell], ome = prim[P_OME * nc + cell];
 
   for (int l = t; l < nv2; l += blockDim.x) {
-    const double v2 = g.v2min + (l + 0.5) * g.dv2;
+    const double v2 = fma(l + 0.5, g.dv2, g.v2min);
     const double c2 = v2 - u2;
     const double q = c2 * c2;
-    const double e2 = exp(-q * inv2T);
+    const double e2 = expd(-q * inv2T);
     const double av = fabs(v2);
-    const double sg = -av / g.dy;
+    const double sg = -av * g.idy;
     c2t[l] = c2;
     c2q[l] = q;
     c2c[l] = q * c2;
     e2t[l] = e2;
-    g2t[l] = exp(-0.5 * Ti22 * q);
+    g2t[l] = expd(-0.5 * Ti22 * q);
     v2t[l] = v2;
     s0t[l] = sg;
     s1t[l] = sg * c2;
     s2t[l] = sg * q;
-    wlt[l] = om1 * (dt * av / g.dy);
+    wlt[l] = om1 * (av * dtidy);
     E1t[l] = e2 * c2;
     E2t[l] = e2 * q;
     E3t[l] = e2 * q * c2;
   }
-
-  // discrete strain and temperature gradient of Eqs. (5-97), (5-97more)
-  double uL1, uL2, TL, uR1, uR2, TR, uB1, uB2, TB, uT1, uT2, TT;
-  side_uT(g, p, prim, nc, i, j, 0, u1, u2, T, uL1, uL2, TL);
-  side_uT(g, p, prim, nc, i, j, 1, u1, u2, T, uR1, uR2, TR);
-  side_uT(g, p, prim, nc, i, j, 2, u1, u2, T, uB1, uB2, TB);
-  side_uT(g, p, prim, nc, i, j, 3, u1, u2, T, uT1, uT2, TT);
-  const double dTdx = (0.5 * (TR + T) - 0.5 * (T + TL)) / g.dx;
-  const double dTdy = (0.5 * (TT + T) - 0.5 * (T + TB)) / g.dy;
-  const double Dxu1 = (uR1 - uL1) / 2.0, Dxu2 = (uR2 - uL2) / 2.0;
-  const double Dyu1 = (uT1 - uB1) / 2.0, Dyu2 = (uT2 - uB2) / 2.0;
-  const double s11 = Dxu1 / g.dx - Dyu2 / g.dy;
-  const double s12 = Dyu1 / g.dy + Dxu2 / g.dx;
 
   const Upwind ub = upwind_y(g, p, i, j, 2);  // upwind for v2 > 0
   const Upwind ut = upwind_y(g, p, i, j, 3);  // upwind for v2 < 0
@@ -301,8 +260,9 @@ __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs, T
   const Tg* Gb = Gs + (size_t)ub.cell * nv + k;
   const Tg* Gt = Gs + (size_t)ut.cell * nv + k;
 
-  const double v1 = g.v1min + (k + 0.5) * g.dv1;
+  const double v1 = fma(k + 0.5, g.dv1, g.v1min);
   const double c1 = v1 - u1;
+  const double c1q = c1 * c1;
   __syncthreads();
 
   // pass 1: velocity moments of Z*
@@ -321,32 +281,28 @@ __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs, T
       E2 = fma(s2t[l], d, E2);
     }
   }
-  double S[4] = {E0, c1 * E0, E1, fma(c1 * c1, E0, E2)};
+  double S[4] = {E0, c1 * E0, E1, fma(c1q, E0, E2)};
   block_sum4(S, red);
 
-  const double b0 = 2.0 * S[0] - S[3] * inv2T;
+  const double b0 = fma(-S[3], inv2T, 2.0 * S[0]);
   const double b1 = S[1] * iT, b2 = S[2] * iT;
-  const double gm = 0.25 * S[3] * iT * iT - S[0] * inv2T;
-  const double kap = dt * g.dv1 * g.dv2 / (2.0 * kPi * T);
-  const double mu = rho / (2.0 * kPi * T);
-  const double wt = om2 * mu / tau;
-
-  // Ghat's transport polynomial B:sigma + C.grad T = p0 + p1 c2 + p2 c2^2 + p3 c2^3 (Eq. 5-69)
-  const double h2T2 = 0.5 * iT * iT;
-  const double p0 = 0.5 * s11 * iT * c1 * c1 + h2T2 * c1 * c1 * c1 * dTdx - 2.0 * c1 * dTdx * iT;
-  const double p1 = s12 * iT * c1 + h2T2 * c1 * c1 * dTdy - 2.0 * dTdy * iT;
-  const double p2 = -0.5 * s11 * iT + h2T2 * c1 * dTdx;
-  const double p3 = h2T2 * dTdy;
-  const double C0 = om1 * kap * fma(gm * c1, c1, fma(b1, c1, b0)) - wt * p0 - om2 * mu / eps;
-  const double C1 = om1 * kap * b2 - wt * p1;
-  const double C2 = om1 * kap * gm - wt * p2;
-  const double C3 = -wt * p3;
-  const double e1 = exp(-c1 * c1 * inv2T);
+  const double gm = fma(0.25 * S[3], iT * iT, -S[0] * inv2T);
+  // om1 dt Zhat* and om2 Ghat's Maxwellian part as one cubic in c2 times e1 e2
+  const double w01 = prim[P_W01 * nc + cell], w02 = prim[P_W02 * nc + cell];
+  const double w03 = prim[P_W03 * nc + cell], w10 = prim[P_W10 * nc + cell];
+  const double w11 = prim[P_W11 * nc + cell], w12 = prim[P_W12 * nc + cell];
+  const double w20 = prim[P_W20 * nc + cell], w21 = prim[P_W21 * nc + cell];
+  const double w30 = prim[P_W30 * nc + cell];
+  const double C0 = om1kap * fma(gm, c1q, fma(b1, c1, b0)) - c1 * fma(c1, fma(c1, w03, w02), w01) - ome;
+  const double C1 = fma(om1kap, b2, -fma(c1, fma(c1, w12, w11), w10));
+  const double C2 = fma(om1kap, gm, -fma(c1, w21, w20));
+  const double C3 = -w30;
+  const double e1 = expd(-c1q * inv2T);
   const double A0 = e1 * C0, A1 = e1 * C1, A2 = e1 * C2, A3 = e1 * C3;
-  const double gam1 = om2 / eps * KG * exp(-0.5 * Ti11 * c1 * c1);
-  const double c2r = g.v2min + (r + 0.5) * g.dv2 - u2;
-  double x = exp(-Ti12 * c1 * c2r);
-  const double rat = exp(-Ti12 * c1 * (R * g.dv2));
+  const double gam1 = gam0 * expd(-0.5 * Ti11 * c1q);
+  const double c2r = fma(r + 0.5, g.dv2, g.v2min) - u2;
+  double x = expd(-Ti12 * c1 * c2r);
+  const double rat = expd(-Ti12 * c1 * (R * g.dv2));
 
   // pass 2: G^{n+1} = om1 (G* - dt Z* + dt Zhat*) + om2 Ghat, and its heat-flux moments
   double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0;
@@ -376,13 +332,12 @@ __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs, T
       H3 = fma(c2c[l], ov, H3);
     }
   }
-  double Hs[4] = {c1 * c1 * c1 * H0, c1 * c1 * H1, c1 * H2, H3};
+  double Hs[4] = {c1q * c1 * H0, c1q * H1, c1 * H2, H3};
   block_sum4(Hs, red);
   if (t == 0) {
-    const double f = eps * g.dv1 * g.dv2;
     bool ok = true;
     for (int m = 0; m < 4; ++m) {
-      Hout[m * nc + cell] = f * Hs[m];
+      Hout[m * nc + cell] = hscale * Hs[m];
       ok = ok && isfinite(Hs[m]);
     }
     if (!ok) atomicOr(err, ERR_NONFINITE_G);
@@ -573,6 +528,15 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_wall(const Tg* __restrict__ 
   }
 }
 
+__global__ void k_diag_exp(const double* __restrict__ x, double* __restrict__ yf,
+                           double* __restrict__ yl, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x) {
+    yf[q] = expd(x[q]);
+    yl[q] = exp(x[q]);
+  }
+}
+
 __global__ void k_f64_to_f32(const double* __restrict__ in, float* __restrict__ out, size_t n) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
        q += (size_t)gridDim.x * blockDim.x)
@@ -612,7 +576,7 @@ void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s) {
   if (ms.smem_x > 48 * 1024)
     cudaFuncSetAttribute(k_micro_x<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_x);
-  k_micro_x<Tg><<<g.nx * g.ny, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt, ms.R);
+  k_micro_x<Tg><<<g.nx * g.ny, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R);
 }
 
 template <typename Tg>
@@ -621,8 +585,8 @@ void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const
                     cudaStream_t s) {
   if (ms.smem_y > 48 * 1024)
     cudaFuncSetAttribute(k_micro_y<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_y);
-  k_micro_y<Tg><<<g.nx * g.ny, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt, eps,
-                                                           ms.R, err);
+  k_micro_y<Tg><<<g.nx * g.ny, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
+                                                           eps * g.dv1 * g.dv2, ms.R, err);
 }
 
 template <typename Tg>
@@ -651,6 +615,10 @@ template void launch_micro_y_wall<float>(const float*, float*, double*, const do
                                          const int*, int, const KGrid&, const KParams&, double,
                                          double, const MicroShape&, int*, cudaStream_t);
 
+void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s) {
+  k_diag_exp<<<152 * 4, 256, 0, s>>>(x, yf, yl, n);
+}
+
 void launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s) {
   k_f64_to_f32<<<152 * 8, 256, 0, s>>>(in, out, n);
 }
@@ -659,3 +627,14 @@ void launch_convert_f32_to_f64(const float* in, double* out, size_t n, cudaStrea
 }
 
 }  // namespace mmk
+
+extern "C" mm_status mm_diag_exp(const double* x_dev, double* y_fast_dev, double* y_lib_dev,
+                                 size_t n, void* cuda_stream) {
+  if (!x_dev || !y_fast_dev || !y_lib_dev) return MM_ERR_INVALID_ARG;
+  if (n == 0) return MM_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  mmk::launch_diag_exp(x_dev, y_fast_dev, y_lib_dev, n, s);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+}

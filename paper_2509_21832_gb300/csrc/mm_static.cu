@@ -114,6 +114,8 @@ extern "C" mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params
   kg.nv2 = grid->nv2;
   kg.dx = (grid->x1 - grid->x0) / grid->nx;
   kg.dy = (grid->y1 - grid->y0) / grid->ny;
+  kg.idx = 1.0 / kg.dx;
+  kg.idy = 1.0 / kg.dy;
   kg.v1min = grid->v1min;
   kg.v2min = grid->v2min;
   kg.dv1 = (grid->v1max - grid->v1min) / grid->nv1;
@@ -151,7 +153,7 @@ extern "C" mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params
   if (n_wall > 0)
     k_wall_list<<<(int)((ncell + 127) / 128), 128, 0, s>>>(wall, count, kg, kp);
   for (int n = 0; n < nsteps; ++n) {
-    launch_prims(Q_dev, prim, kg, kp, err, s);
+    launch_prims(Q_dev, prim, kg, kp, dt, eps, err, s);
     launch_micro_x<double>(G_dev, Gs, prim, kg, kp, dt, ms, s);
     launch_micro_y<double>(Gs, G_dev, H_dev, prim, kg, kp, dt, eps, ms, err, s);
     launch_micro_y_wall<double>(Gs, G_dev, H_dev, prim, wall, n_wall, kg, kp, dt, eps, ms, err, s);
