@@ -165,6 +165,51 @@ def config_of(pr, args):
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
 
+def fp32_variant(args, stream):
+    """Four-quadrant Riemann data, diffuse bottom wall, 1024^2 x 24^2, g in FP32: throughput,
+    HBM fraction (8 algorithmic bytes per phase cell: one FP32 read and write of g) and the
+    relative L1 density error against the FP64 path after the same number of steps."""
+    import torch
+    from paper_2509_21832_gb300 import api
+    from paper_2509_21832_gb300 import inputs as I
+    pr = I.riemann4_diffuse(n=args.variant_n, nv=24, eps=1e-2, seed=0, nsteps=100)
+    out = {"workload": "riemann4_diffuse_%dx%dx24x24" % (pr.grid.nx, pr.grid.ny),
+           "eps": pr.eps, "steps": pr.nsteps, "dtype": "g f32, macro/moments f64"}
+    res = {}
+    for prec in (I.PREC_G_FP32, I.PREC_FP64):
+        params = I.Params(**{**pr.params.__dict__, "precision": prec})
+        s = api.Solver(pr.grid, params, stream=stream.cuda_stream)
+        s.set_state(pr.Q, None)
+        s.step(pr.dt, pr.eps, 3)
+        s.sync()
+        s.set_state(pr.Q, None)
+        s.set_timing(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(pr.dt, pr.eps, pr.nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kt = s.get_timing()
+        Q, _ = s.get_moments(with_H=False)
+        s.close()
+        res[prec] = (ms, kt, Q)
+    ms, kt, Q32 = res[I.PREC_G_FP32]
+    ms64, _, Q64 = res[I.PREC_FP64]
+    nph = pr.grid.nphase
+    peaks, src = measured_peaks()
+    hbm = (8.0 + 160.0 / 576.0) * nph * pr.nsteps / (ms * 1e-3) / 1e9
+    out.update({
+        "value": nph * pr.nsteps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / pr.nsteps,
+        "fp64_ms_per_step": ms64 / pr.nsteps, "speedup_vs_fp64": ms64 / ms,
+        "hbm_achieved_gbs": hbm, "hbm_frac": hbm / peaks["hbm_gbs"],
+        "l1_density_rel_err_vs_fp64": float(np.sum(np.abs(Q32[0] - Q64[0])) / np.sum(np.abs(Q64[0]))),
+        "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()}})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -177,6 +222,8 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant-n", type=int, default=1024)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -297,13 +344,17 @@ def main():
                "sample": "%d steps of the full %dx%d grid (%d phase cells), %.1f s"
                          % (n, sub.nx, sub.ny, sub.nphase, t)}
 
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = {"riemann4_diffuse_1024x1024x24x24_fp32g": fp32_variant(args, stream)}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic", "config": config_of(pr, args),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks}
+                "gpu_launches": launches, "clocks": clocks, "variants": variants}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

@@ -171,7 +171,7 @@ mm_status mm_diag_exp(const double* x_dev, double* y_fast_dev, double* y_lib_dev
  *  - errbuf (may be NULL) receives a NUL-terminated message of at most errlen bytes. */
 #define MM_STATIC_MAX_CELLS 16384
 #define MM_STATIC_MAX_PHASE 1048576
-#define MM_STATIC_SCRATCH_BYTES 12780032
+#define MM_STATIC_SCRATCH_BYTES 18285312
 mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params* params, double* Q_dev,
                                  double* G_dev, double* H_dev, double dt, double eps,
                                  int nsteps, void* cuda_stream, char* errbuf, size_t errlen);

@@ -14,10 +14,10 @@ using namespace mmk;
 
 namespace {
 
-const char* const kKernelNames[] = {"prims", "micro_x", "micro_y", "micro_y_wall", "macro_x",
-                                    "macro_y"};
-constexpr int kNumKernels = 6;
-enum { T_PRIMS = 0, T_MICRO_X, T_MICRO_Y, T_MICRO_YW, T_MACRO_X, T_MACRO_Y };
+const char* const kKernelNames[] = {"prims",    "micro_x",  "micro_y", "micro_y_wall",
+                                    "macro_x1", "macro_x2", "macro_y", "h_unpack"};
+constexpr int kNumKernels = 8;
+enum { T_PRIMS = 0, T_MICRO_X, T_MICRO_Y, T_MICRO_YW, T_MACRO_X1, T_MACRO_X2, T_MACRO_Y, T_HUNPACK };
 
 struct TimedLaunch {
   int kind;
@@ -39,9 +39,12 @@ struct mm_ctx {
   void* G = nullptr;   // G^n / G^{n+1}
   void* Gs = nullptr;  // G* (scratch)
   double* Q = nullptr;
-  double* Q2 = nullptr;  // Q** (scratch)
+  double* macro = nullptr;  // Q*, Q**, half fluxes, boundary fluxes (scratch)
+  MacroBufs mb{};
   double* H = nullptr;
+  float* Hf = nullptr;      // FP32-g heat flux as (hi, lo) pairs
   double* prim = nullptr;
+  float* primf = nullptr;  // FP32 copies of the per-cell coefficients (FP32-g path)
   int* err = nullptr;
   int* wall_cells = nullptr;
   int n_wall = 0;
@@ -167,16 +170,23 @@ void enqueue_step(mm_ctx* c, double dt, double eps) {
   const KGrid& g = c->kg;
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
-  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, g, p, dt, eps, c->err, s); });
-  timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
-  timed(c, T_MICRO_Y, [&] { launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s); });
+  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
+  if constexpr (sizeof(Tg) == sizeof(float)) {
+    timed(c, T_MICRO_X, [&] { launch_micro_x_f32(G, Gs, c->primf, g, p, dt, c->ms, s); });
+    timed(c, T_MICRO_Y, [&] { launch_micro_y_f32(Gs, G, c->Hf, c->primf, g, p, dt, c->ms, s); });
+    timed(c, T_HUNPACK, [&] { launch_h_unpack(c->Hf, c->H, g, eps, s); });
+  } else {
+    timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
+    timed(c, T_MICRO_Y, [&] { launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s); });
+  }
   if (c->n_wall > 0)
     timed(c, T_MICRO_YW, [&] {
       launch_micro_y_wall<Tg>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
                               c->ms, c->err, s);
     });
-  timed(c, T_MACRO_X, [&] { launch_macro_x(c->Q, c->H, c->Q2, g, p, dt, eps, c->err, s); });
-  timed(c, T_MACRO_Y, [&] { launch_macro_y(c->Q2, c->H, c->Q, g, p, dt, eps, c->err, s); });
+  timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
+  timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
+  timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
 }
 
 // Copy an FP64 array of n elements into the context's G (FP64 or FP32), staging through Gs.
@@ -236,8 +246,10 @@ size_t mm_device_bytes(const mm_grid* g, const mm_params* p) {
       if ((i == 0 && p->bc[0] == MM_BC_DIFFUSE) || (i == g->nx - 1 && p->bc[1] == MM_BC_DIFFUSE) ||
           (j == 0 && p->bc[2] == MM_BC_DIFFUSE) || (j == g->ny - 1 && p->bc[3] == MM_BC_DIFFUSE))
         ++nwall;
-  return 2 * np * gs + (6 + 6 + 4 + NPRIM) * nc * sizeof(double) + sizeof(int) +
-         nwall * sizeof(int);
+  const size_t pf =
+      p->precision == MM_PREC_G_FP32 ? (NPRIMF + 8) * nc * sizeof(float) : 0;
+  return 2 * np * gs + (6 + 4 + NPRIM) * nc * sizeof(double) +
+         macro_doubles(g->nx, g->ny) * sizeof(double) + pf + sizeof(int) + nwall * sizeof(int);
 }
 
 mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
@@ -287,9 +299,11 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
   alloc(&c->G, c->nphase * gsz);
   alloc(&c->Gs, c->nphase * gsz > 16 ? c->nphase * gsz : 16);  // also stages FP64 chunks
   alloc((void**)&c->Q, 6 * c->ncell * sizeof(double));
-  alloc((void**)&c->Q2, 6 * c->ncell * sizeof(double));
+  alloc((void**)&c->macro, macro_doubles(grid->nx, grid->ny) * sizeof(double));
   alloc((void**)&c->H, 4 * c->ncell * sizeof(double));
+  if (c->fp32) alloc((void**)&c->Hf, 8 * c->ncell * sizeof(float));
   alloc((void**)&c->prim, NPRIM * c->ncell * sizeof(double));
+  if (c->fp32) alloc((void**)&c->primf, NPRIMF * c->ncell * sizeof(float));
   alloc((void**)&c->err, sizeof(int));
   std::vector<int> walls;
   for (int j = 0; j < grid->ny; ++j)
@@ -304,6 +318,7 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA;
   }
+  c->mb = carve_macro(c->macro, grid->nx, grid->ny);
   if (c->n_wall > 0)
     e = cudaMemcpy(c->wall_cells, walls.data(), walls.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
@@ -470,9 +485,11 @@ void mm_destroy(mm_ctx* c) {
   cudaFree(c->G);
   cudaFree(c->Gs);
   cudaFree(c->Q);
-  cudaFree(c->Q2);
+  cudaFree(c->macro);
   cudaFree(c->H);
+  cudaFree(c->Hf);
   cudaFree(c->prim);
+  cudaFree(c->primf);
   cudaFree(c->err);
   cudaFree(c->wall_cells);
   delete c;

@@ -14,6 +14,11 @@ struct KGrid {
   double idx, idy;  // 1/dx, 1/dy
 };
 
+// FP32 copies of the grid quantities for the FP32-g kernels (rounded once on the host).
+struct KGridF {
+  float v1min, v2min, dv1, dv2, idx, idy;
+};
+
 // Physical parameters used on the device.
 struct KParams {
   double nu, tau0;
@@ -43,6 +48,15 @@ enum PrimField {
   NPRIM
 };
 
+// FP32 copies of the per-cell coefficients used by the FP32-g phase-space kernels, SoA
+// [NPRIMF][ny][nx] (rounded once per cell by the prims kernel).
+enum PrimFieldF {
+  F_U1 = 0, F_U2, F_INV2T, F_IT, F_KAP, F_OM1, F_OM1KAP, F_GAM0, F_OME,
+  F_TI11H, F_TI12, F_TI22H,  // Ti11/2, Ti12, Ti22/2
+  F_W01, F_W02, F_W03, F_W10, F_W11, F_W12, F_W20, F_W21, F_W30,
+  NPRIMF
+};
+
 // Bits of the device error word.
 enum { ERR_NONPHYS_PRIM = 1, ERR_NONPHYS_MACRO = 2, ERR_NONFINITE_G = 4 };
 
@@ -57,8 +71,18 @@ MicroShape micro_shape(int nv1, int nv2);
 // Kernel kinds, for per-kernel timing.
 enum KernelKind { KK_PRIMS = 0, KK_MICRO_X, KK_MICRO_Y, KK_MACRO_X, KK_MACRO_Y, KK_COUNT };
 
-void launch_prims(const double* Q, double* prim, const KGrid& g, const KParams& p, double dt,
-                  double eps, int* err, cudaStream_t s);
+void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
+                  double dt, double eps, int* err, cudaStream_t s);
+// FP32-g phase-space kernels: g stored and transported in FP32; velocity sums of each warp in
+// FP32, combined across warps and turned into projection coefficients in FP64.
+// Velocity sums of each warp are FP32; the warps' sums are added with compensated FP32
+// (Neumaier) summation by one thread; the heat flux leaves as (hi, lo) FP32 pairs Hf[8][ny][nx]
+// that launch_h_unpack combines in FP64.  No FP64 instruction runs in these kernels.
+void launch_micro_x_f32(const float* Gin, float* Gout, const float* primf, const KGrid& g,
+                        const KParams& p, double dt, const MicroShape& ms, cudaStream_t s);
+void launch_micro_y_f32(const float* Gs, float* Gout, float* Hf, const float* primf,
+                        const KGrid& g, const KParams& p, double dt, const MicroShape& ms,
+                        cudaStream_t s);
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s);
@@ -70,10 +94,28 @@ template <typename Tg>
 void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
                          double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s);
-void launch_macro_x(const double* Qn, const double* H, double* Q2, const KGrid& g,
+// Buffers of the macro step: Q* and Q**, each cell's half fluxes along x (of Q*) and y (of Q**)
+// [Fp(6) Fm(6)][ny][nx], and the fluxes through the non-periodic boundary faces
+// BX [2 sides][6][ny], BY [2 sides][6][nx].
+struct MacroBufs {
+  double* Q1;
+  double* Q2;
+  double* FX;
+  double* FY;
+  double* BX;
+  double* BY;
+};
+constexpr size_t macro_doubles(int nx, int ny) {
+  return (size_t)nx * ny * (6 + 6 + 12 + 12) + 12 * (size_t)ny + 12 * (size_t)nx;
+}
+void launch_macro_x1(const double* Qn, const MacroBufs& mb, const KGrid& g, const KParams& p,
+                     double dt, double eps, int* err, cudaStream_t s);
+void launch_macro_x2(const double* H, const MacroBufs& mb, const KGrid& g, const KParams& p,
+                     double dt, int* err, cudaStream_t s);
+void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGrid& g,
                     const KParams& p, double dt, double eps, int* err, cudaStream_t s);
-void launch_macro_y(const double* Q2, const double* H, double* Qn, const KGrid& g,
-                    const KParams& p, double dt, double eps, int* err, cudaStream_t s);
+void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s);
+MacroBufs carve_macro(double* base, int nx, int ny);
 void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s);
 void launch_convert_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);

@@ -600,14 +600,9 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
 
 template void launch_micro_x<double>(const double*, double*, const double*, const KGrid&,
                                      const KParams&, double, const MicroShape&, cudaStream_t);
-template void launch_micro_x<float>(const float*, float*, const double*, const KGrid&,
-                                    const KParams&, double, const MicroShape&, cudaStream_t);
 template void launch_micro_y<double>(const double*, double*, double*, const double*,
                                      const KGrid&, const KParams&, double, double,
                                      const MicroShape&, int*, cudaStream_t);
-template void launch_micro_y<float>(const float*, float*, double*, const double*, const KGrid&,
-                                    const KParams&, double, double, const MicroShape&, int*,
-                                    cudaStream_t);
 template void launch_micro_y_wall<double>(const double*, double*, double*, const double*,
                                           const int*, int, const KGrid&, const KParams&, double,
                                           double, const MicroShape&, int*, cudaStream_t);

@@ -24,8 +24,11 @@ constexpr size_t round_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign;
 
 // Offsets of the regions carved from the static array (bytes, 256-byte aligned).
 constexpr size_t kOffGs = 0;
-constexpr size_t kOffQ2 = kOffGs + round_up(sizeof(double) * MM_STATIC_MAX_PHASE);
-constexpr size_t kOffPrim = kOffQ2 + round_up(sizeof(double) * 6 * MM_STATIC_MAX_CELLS);
+constexpr size_t kOffMacro = kOffGs + round_up(sizeof(double) * MM_STATIC_MAX_PHASE);
+// macro buffers: 36 doubles per cell plus 12 per boundary row/column (nx + ny <= cells + 1)
+constexpr size_t kOffPrim =
+    kOffMacro + round_up(sizeof(double) * (36 * (size_t)MM_STATIC_MAX_CELLS +
+                                           12 * ((size_t)MM_STATIC_MAX_CELLS + 1)));
 constexpr size_t kOffWall = kOffPrim + round_up(sizeof(double) * NPRIM * MM_STATIC_MAX_CELLS);
 constexpr size_t kOffCount = kOffWall + round_up(sizeof(int) * MM_STATIC_MAX_CELLS);
 constexpr size_t kOffErr = kOffCount + kAlign;
@@ -139,7 +142,7 @@ extern "C" mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params
   const MicroShape ms = micro_shape(grid->nv1, grid->nv2);
 
   double* Gs = reinterpret_cast<double*>(base + kOffGs);
-  double* Q2 = reinterpret_cast<double*>(base + kOffQ2);
+  const MacroBufs mb = carve_macro(reinterpret_cast<double*>(base + kOffMacro), grid->nx, grid->ny);
   double* prim = reinterpret_cast<double*>(base + kOffPrim);
   int* wall = reinterpret_cast<int*>(base + kOffWall);
   int* count = reinterpret_cast<int*>(base + kOffCount);
@@ -153,12 +156,13 @@ extern "C" mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params
   if (n_wall > 0)
     k_wall_list<<<(int)((ncell + 127) / 128), 128, 0, s>>>(wall, count, kg, kp);
   for (int n = 0; n < nsteps; ++n) {
-    launch_prims(Q_dev, prim, kg, kp, dt, eps, err, s);
+    launch_prims(Q_dev, prim, nullptr, kg, kp, dt, eps, err, s);
     launch_micro_x<double>(G_dev, Gs, prim, kg, kp, dt, ms, s);
     launch_micro_y<double>(Gs, G_dev, H_dev, prim, kg, kp, dt, eps, ms, err, s);
     launch_micro_y_wall<double>(Gs, G_dev, H_dev, prim, wall, n_wall, kg, kp, dt, eps, ms, err, s);
-    launch_macro_x(Q_dev, H_dev, Q2, kg, kp, dt, eps, err, s);
-    launch_macro_y(Q2, H_dev, Q_dev, kg, kp, dt, eps, err, s);
+    launch_macro_x1(Q_dev, mb, kg, kp, dt, eps, err, s);
+    launch_macro_x2(H_dev, mb, kg, kp, dt, err, s);
+    launch_macro_y(H_dev, mb, Q_dev, kg, kp, dt, eps, err, s);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return say(errbuf, errlen, MM_ERR_CUDA, cudaGetErrorString(e));

@@ -1,0 +1,68 @@
+"""FP32-g mixed precision (g stored and transported in FP32; projection coefficients, heat
+flux totals and the macro update in FP64) against the FP64 oracle and the FP64 GPU path."""
+import numpy as np
+import pytest
+
+from helpers import q_rel_err
+from oracle import oracle as O
+from paper_2509_21832_gb300 import api
+from paper_2509_21832_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+def run(grid, params, Q, G, dt, eps, n):
+    with api.Solver(grid, params) as s:
+        s.set_state(Q, G)
+        s.step(dt, eps, n)
+        Qg, Hg = s.get_moments()
+        Gg = s.get_g()
+    return Qg, Gg, Hg
+
+
+CASES = [
+    ("periodic_24", dict(nx=13, ny=11, nv1=24, nv2=24), (I.PERIODIC,) * 4, {}),
+    ("specular_32", dict(nx=10, ny=7, nv1=32, nv2=32), (I.SPECULAR,) * 4, {}),
+    ("mixed_diffuse_16", dict(nx=12, ny=9, nv1=16, nv2=16),
+     (I.EXTRAP, I.EXTRAP, I.DIFFUSE, I.EXTRAP), dict(wall_T=(1.0, 1.0, 1.1, 1.0))),
+    ("odd_17x15", dict(nx=6, ny=5, nv1=17, nv2=15, v1min=-6, v1max=6, v2min=-6, v2max=6),
+     (I.PERIODIC, I.PERIODIC, I.SPECULAR, I.EXTRAP), dict(nu=0.3)),
+]
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1.0])
+@pytest.mark.parametrize("name,gk,bc,extra", CASES, ids=[c[0] for c in CASES])
+def test_fp32g_against_oracle(name, gk, bc, extra, eps):
+    grid = I.Grid(**gk)
+    p64 = I.Params(bc=bc, **extra)
+    p32 = I.Params(bc=bc, precision=I.PREC_G_FP32, **extra)
+    Q = I.smooth_state(grid, seed=len(name), umax=0.25, aniso=0.08)
+    G = I.seeded_g(grid, seed=3, amp=0.02)
+    dt = O.dt_for_cfl(grid, 0.5, 0.0, I.CFL_SUM)[0]
+    n = 12
+    Qg, Gg, Hg = run(grid, p32, Q, G, dt, eps, n)
+    Qo, Go, Ho = O.step(grid, p64, Q, G, dt, eps, n)
+    # g carries FP32 rounding of each step's arithmetic (a few tens of ulp per step, relative to
+    # the Maxwellian scale, amplified by 1/eps through (G - M)/eps), macro fields see it through
+    # eps * sum c^3 g times dt/dx per step.
+    mscale = np.max(Qo[0]) / (2 * np.pi * 0.5)
+    gtol = n * 64 * U32 * max(np.max(np.abs(Go)), mscale / eps)
+    assert np.max(np.abs(Gg - Go)) <= gtol, (np.max(np.abs(Gg - Go)), gtol)
+    eq = q_rel_err(Qg, Qo)
+    assert np.all(eq <= n * 64 * U32), eq
+
+
+def test_fp32g_l1_density_error_vs_fp64_four_quadrant():
+    """Four-quadrant Riemann data with a diffuse bottom wall (reduced 128^2 x 24^2): the relative
+    L1 density error of FP32 g against the FP64 GPU run stays below 1e-3."""
+    pr = I.riemann4_diffuse(n=128, nv=24, eps=1e-2, seed=0, nsteps=60)
+    p64 = I.Params(**{**pr.params.__dict__, "precision": I.PREC_FP64})
+    p32 = I.Params(**{**pr.params.__dict__, "precision": I.PREC_G_FP32})
+    Q64, _, _ = run(pr.grid, p64, pr.Q, pr.G, pr.dt, pr.eps, pr.nsteps)
+    Q32, _, _ = run(pr.grid, p32, pr.Q, pr.G, pr.dt, pr.eps, pr.nsteps)
+    l1 = np.sum(np.abs(Q32[0] - Q64[0])) / np.sum(np.abs(Q64[0]))
+    print("relative L1 density error FP32-g vs FP64:", l1)
+    assert l1 <= 1e-3
+    assert l1 <= 1e-5  # what the arithmetic actually gives (FP32 round-off, not truncation)
