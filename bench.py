@@ -224,6 +224,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variant-n", type=int, default=1024)
+    ap.add_argument("--variant-only", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -233,6 +234,11 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, pr, world, rank)
+        return
+    if args.variant_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(fp32_variant(args, torch.cuda.Stream())), flush=True)
         return
 
     import torch

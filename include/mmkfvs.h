@@ -64,7 +64,7 @@ enum { MM_CFL_MIN = 0, MM_CFL_SUM = 1 };
 /* Storage of g: FP64, or FP32 with moments, projector coefficients, macro update and the
  * Gaussian tensor inverse in FP64 (the paper uses FP64 throughout; FP32 g is this library's
  * mixed-precision extension). */
-enum { MM_PREC_FP64 = 0, MM_PREC_G_FP32 = 1 };
+enum { MM_PREC_FP64 = 0, MM_PREC_G_FP32 = 1 };  /* MM_PREC_G_FP32 needs nv1 <= 32 */
 
 typedef struct {
   int nx, ny;                        /* spatial cells, >= 1 each (ny = 1: 1D-2V, y periodic) */

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mm_internal.cuh"
@@ -14,10 +15,13 @@ using namespace mmk;
 
 namespace {
 
-const char* const kKernelNames[] = {"prims",    "micro_x",  "micro_y", "micro_y_wall",
-                                    "macro_x1", "macro_x2", "macro_y", "h_unpack"};
-constexpr int kNumKernels = 8;
-enum { T_PRIMS = 0, T_MICRO_X, T_MICRO_Y, T_MICRO_YW, T_MACRO_X1, T_MACRO_X2, T_MACRO_Y, T_HUNPACK };
+const char* const kKernelNames[] = {"prims",    "micro_x",  "micro_y", "micro_y_wall", "macro_x1",
+                                    "macro_x2", "macro_y", "h_unpack", "micro_fused"};
+constexpr int kNumKernels = 9;
+enum {
+  T_PRIMS = 0, T_MICRO_X, T_MICRO_Y, T_MICRO_YW, T_MACRO_X1, T_MACRO_X2, T_MACRO_Y, T_HUNPACK,
+  T_MICRO_FUSED
+};
 
 struct TimedLaunch {
   int kind;
@@ -36,8 +40,10 @@ struct mm_ctx {
   int device = 0;
   bool fp32 = false;
   size_t nphase = 0, ncell = 0;
-  void* G = nullptr;   // G^n / G^{n+1}
-  void* Gs = nullptr;  // G* (scratch)
+  void* G = nullptr;     // G^n (and G^{n+1} after the step)
+  void* Gs = nullptr;    // FP64: G* (scratch); FP32: the other buffer of the ping-pong pair
+  void* Gexp = nullptr;  // FP32 with diffuse walls: G* exported for the wall kernel
+  int nseg = 1;          // FP32: row segments of the fused kernel
   double* Q = nullptr;
   double* macro = nullptr;  // Q*, Q**, half fluxes, boundary fluxes (scratch)
   MacroBufs mb{};
@@ -81,6 +87,7 @@ std::string validate(const mm_grid* g, const mm_params* p) {
        p->tau_model == MM_TAU_CONST) && !(p->tau0 > 0.0))
     return "tau0 must be > 0";
   if (p->precision != MM_PREC_FP64 && p->precision != MM_PREC_G_FP32) return "unknown precision";
+  if (p->precision == MM_PREC_G_FP32 && g->nv1 > 32) return "MM_PREC_G_FP32 needs nv1 <= 32";
   for (int s = 0; s < 4; ++s) {
     if (p->bc[s] < 0 || p->bc[s] > 3) return "unknown boundary kind";
     if (p->bc[s] == MM_BC_DIFFUSE && !(p->wall_T[s] > 0.0)) return "diffuse wall needs wall_T > 0";
@@ -172,18 +179,27 @@ void enqueue_step(mm_ctx* c, double dt, double eps) {
   cudaStream_t s = c->stream;
   timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
   if constexpr (sizeof(Tg) == sizeof(float)) {
-    timed(c, T_MICRO_X, [&] { launch_micro_x_f32(G, Gs, c->primf, g, p, dt, c->ms, s); });
-    timed(c, T_MICRO_Y, [&] { launch_micro_y_f32(Gs, G, c->Hf, c->primf, g, p, dt, c->ms, s); });
+    // fused streaming kernel: G -> Gs (ping-pong), wall cells from the exported G*
+    float* Ge = static_cast<float*>(c->Gexp);
+    timed(c, T_MICRO_FUSED, [&] {
+      launch_micro_fused_f32(G, Gs, Ge, c->Hf, c->primf, g, p, dt, c->ms, c->nseg, s);
+    });
     timed(c, T_HUNPACK, [&] { launch_h_unpack(c->Hf, c->H, g, eps, s); });
+    if (c->n_wall > 0)
+      timed(c, T_MICRO_YW, [&] {
+        launch_micro_y_wall<float>(Ge, Gs, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt,
+                                   eps, c->ms, c->err, s);
+      });
+    std::swap(c->G, c->Gs);
   } else {
     timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
     timed(c, T_MICRO_Y, [&] { launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s); });
+    if (c->n_wall > 0)
+      timed(c, T_MICRO_YW, [&] {
+        launch_micro_y_wall<Tg>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
+                                c->ms, c->err, s);
+      });
   }
-  if (c->n_wall > 0)
-    timed(c, T_MICRO_YW, [&] {
-      launch_micro_y_wall<Tg>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
-                              c->ms, c->err, s);
-    });
   timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
   timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
   timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
@@ -246,8 +262,11 @@ size_t mm_device_bytes(const mm_grid* g, const mm_params* p) {
       if ((i == 0 && p->bc[0] == MM_BC_DIFFUSE) || (i == g->nx - 1 && p->bc[1] == MM_BC_DIFFUSE) ||
           (j == 0 && p->bc[2] == MM_BC_DIFFUSE) || (j == g->ny - 1 && p->bc[3] == MM_BC_DIFFUSE))
         ++nwall;
-  const size_t pf =
-      p->precision == MM_PREC_G_FP32 ? (NPRIMF + 8) * nc * sizeof(float) : 0;
+  const bool diff = p->bc[0] == MM_BC_DIFFUSE || p->bc[1] == MM_BC_DIFFUSE ||
+                    p->bc[2] == MM_BC_DIFFUSE || p->bc[3] == MM_BC_DIFFUSE;
+  const size_t pf = p->precision == MM_PREC_G_FP32
+                        ? (NPRIMF + 8) * nc * sizeof(float) + (diff ? np * sizeof(float) : 0)
+                        : 0;
   return 2 * np * gs + (6 + 4 + NPRIM) * nc * sizeof(double) +
          macro_doubles(g->nx, g->ny) * sizeof(double) + pf + sizeof(int) + nwall * sizeof(int);
 }
@@ -302,6 +321,9 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
   alloc((void**)&c->macro, macro_doubles(grid->nx, grid->ny) * sizeof(double));
   alloc((void**)&c->H, 4 * c->ncell * sizeof(double));
   if (c->fp32) alloc((void**)&c->Hf, 8 * c->ncell * sizeof(float));
+  const bool any_diffuse = kp.bc[0] == MM_BC_DIFFUSE || kp.bc[1] == MM_BC_DIFFUSE ||
+                           kp.bc[2] == MM_BC_DIFFUSE || kp.bc[3] == MM_BC_DIFFUSE;
+  if (c->fp32 && any_diffuse) alloc(&c->Gexp, c->nphase * gsz);
   alloc((void**)&c->prim, NPRIM * c->ncell * sizeof(double));
   if (c->fp32) alloc((void**)&c->primf, NPRIMF * c->ncell * sizeof(float));
   alloc((void**)&c->err, sizeof(int));
@@ -319,6 +341,7 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
     return e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA;
   }
   c->mb = carve_macro(c->macro, grid->nx, grid->ny);
+  if (c->fp32) c->nseg = fused_segments_f32(kg, c->ms);
   if (c->n_wall > 0)
     e = cudaMemcpy(c->wall_cells, walls.data(), walls.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
@@ -484,6 +507,7 @@ void mm_destroy(mm_ctx* c) {
   destroy_events(c);
   cudaFree(c->G);
   cudaFree(c->Gs);
+  cudaFree(c->Gexp);
   cudaFree(c->Q);
   cudaFree(c->macro);
   cudaFree(c->H);

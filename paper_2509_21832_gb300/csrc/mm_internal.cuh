@@ -68,21 +68,8 @@ struct MicroShape {
 };
 MicroShape micro_shape(int nv1, int nv2);
 
-// Kernel kinds, for per-kernel timing.
-enum KernelKind { KK_PRIMS = 0, KK_MICRO_X, KK_MICRO_Y, KK_MACRO_X, KK_MACRO_Y, KK_COUNT };
-
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
                   double dt, double eps, int* err, cudaStream_t s);
-// FP32-g phase-space kernels: g stored and transported in FP32; velocity sums of each warp in
-// FP32, combined across warps and turned into projection coefficients in FP64.
-// Velocity sums of each warp are FP32; the warps' sums are added with compensated FP32
-// (Neumaier) summation by one thread; the heat flux leaves as (hi, lo) FP32 pairs Hf[8][ny][nx]
-// that launch_h_unpack combines in FP64.  No FP64 instruction runs in these kernels.
-void launch_micro_x_f32(const float* Gin, float* Gout, const float* primf, const KGrid& g,
-                        const KParams& p, double dt, const MicroShape& ms, cudaStream_t s);
-void launch_micro_y_f32(const float* Gs, float* Gout, float* Hf, const float* primf,
-                        const KGrid& g, const KParams& p, double dt, const MicroShape& ms,
-                        cudaStream_t s);
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s);
@@ -94,6 +81,16 @@ template <typename Tg>
 void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
                          double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s);
+// Fused FP32-g micro step (x sweep, y sweep, relaxation, heat flux) streaming over column
+// segments: reads Gin once and writes Gout (a different buffer); cells next to a diffuse wall are
+// left to the wall kernel, which reads the G* this kernel exports to Gexp.  One warp per cell
+// column (needs nv1 <= 32); no FP64 instruction runs in it: velocity sums are FP32 warp
+// butterflies and the heat flux leaves as (hi, lo) FP32 pairs Hf[8][ny][nx] that
+// launch_h_unpack combines in FP64.
+int fused_segments_f32(const KGrid& g, const MicroShape& ms);
+void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
+                            const float* primf, const KGrid& g, const KParams& p, double dt,
+                            const MicroShape& ms, int nseg, cudaStream_t s);
 // Buffers of the macro step: Q* and Q**, each cell's half fluxes along x (of Q*) and y (of Q**)
 // [Fp(6) Fm(6)][ny][nx], and the fluxes through the non-periodic boundary faces
 // BX [2 sides][6][ny], BY [2 sides][6][nx].

@@ -5,10 +5,9 @@
 // Precision split: no FP64 instruction runs here (the FP64 pipe of GB300 runs at 1/61 of FP32
 // and a warp instruction costs its full issue time even with one active lane, so an FP64
 // epilogue per cell would bound the kernel); per-cell coefficients come from the prims kernel,
-// computed in FP64 and rounded once; each warp's velocity sums are FP32 (per-thread partial sums
-// over its rows, then a pairwise butterfly); the warps' sums are combined with compensated
-// (Neumaier) FP32 summation; the heat flux leaves as (hi, lo) pairs that are combined in FP64 by
-// the per-cell unpack kernel.
+// computed in FP64 and rounded once; velocity sums are FP32 (per-lane partial sums over its
+// rows, then a pairwise warp butterfly); the heat flux leaves as (hi, lo) FP32 pairs (lo = 0
+// here) that the per-cell unpack kernel turns into FP64.
 #include <cmath>
 
 #include "mm_internal.cuh"
@@ -16,44 +15,6 @@
 namespace mmk {
 
 namespace {
-
-constexpr int kPartF = 128;  // floats: 32 warps x 4 partial sums
-constexpr int kHeadF = 136;  // floats before the tables: partials + 8 broadcast slots
-
-// Transposing butterfly over a warp for four floats; the warp's totals are written to
-// part[warp * 4 + m] by lanes 0, 8, 16, 24.
-__device__ __forceinline__ void warp_sum4f(const float v[4], float* part) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool h16 = lane & 16;
-  const float s0 = h16 ? v[0] : v[2];
-  const float s1 = h16 ? v[1] : v[3];
-  const float k0 = (h16 ? v[2] : v[0]) + __shfl_xor_sync(full, s0, 16);
-  const float k1 = (h16 ? v[3] : v[1]) + __shfl_xor_sync(full, s1, 16);
-  const bool h8 = lane & 8;
-  const float s = h8 ? k0 : k1;
-  float kk = (h8 ? k1 : k0) + __shfl_xor_sync(full, s, 8);
-  kk += __shfl_xor_sync(full, kk, 4);
-  kk += __shfl_xor_sync(full, kk, 2);
-  kk += __shfl_xor_sync(full, kk, 1);
-  if ((lane & 7) == 0) part[warp * 4 + (lane >> 3)] = kk;
-}
-
-// Compensated (Neumaier) sum of the warps' partial sums: value ~ hi + lo.
-__device__ __forceinline__ void sum_parts(const float* part, float hi[4], float lo[4]) {
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int m = 0; m < 4; ++m) {
-    float s = 0.f, c = 0.f;
-    for (int w = 0; w < nw; ++w) {
-      const float x = part[w * 4 + m];
-      const float t = s + x;
-      c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
-      s = t;
-    }
-    hi[m] = s;
-    lo[m] = c;
-  }
-}
 
 __device__ __forceinline__ bool diffuse_wall_cell(const KGrid& g, const KParams& p, int i, int j) {
   return (i == 0 && p.bc[0] == MM_BC_DIFFUSE) || (i == g.nx - 1 && p.bc[1] == MM_BC_DIFFUSE) ||
@@ -90,118 +51,155 @@ __device__ __forceinline__ UpwindF upwind_side(const KGrid& g, const KParams& p,
   return u;
 }
 
-// x sweep, Eqs. (zmicrox)-(update-micro-2D-xdir)
-__global__ void __launch_bounds__(512, 1) k_micro_x_f32(const float* __restrict__ Gin,
-                                                        float* __restrict__ Gout,
-                                                        const float* __restrict__ pf, KGrid g,
-                                                        KGridF gf, KParams p, float dtidx,
-                                                        int R) {
-  extern __shared__ float smf[];
-  const int nv1 = g.nv1, nv2 = g.nv2;
-  float* part = smf;
-  float* bco = smf + kPartF;
-  float* c2t = smf + kHeadF;
-  float* c2q = c2t + nv2;
-  float* e2t = c2q + nv2;
-  float* qet = e2t + nv2;
 
-  const int nc = g.nx * g.ny;
-  const int cell = blockIdx.x;
-  const int i = cell % g.nx, j = cell / g.nx;
-  const int t = threadIdx.x;
-  const int k = t % nv1, r = t / nv1;
-  const bool active = r < R;
+// ------------------------------------------------------------------------------------------
+// Fused streaming micro step (FP32 g), one warp per cell column.
+//
+// A warp owns the column of cells i and a segment of rows [j0, j1) and marches upward: the x
+// sweep of row j+1 goes into a three-row ring of split-step values G* in the warp's slice of
+// shared memory, then the y sweep, relaxation and heat flux of row j read rows j-1, j, j+1 from
+// the ring.  G* never goes to HBM: each step reads g once (the x neighbours' rows come through
+// L2, shared by the adjacent columns that march in step) and writes it once.  Lane t owns the v1
+// index k = t mod nv1 and the v2 rows l = t div nv1 + m R (R = 32 div nv1); every velocity sum
+// is a warp butterfly whose totals all lanes receive, so the warp never waits for other warps.
+// Cells next to a diffuse wall (and their y neighbours) also export G* to global memory for the
+// wall kernel, which finishes them afterwards.
+// ------------------------------------------------------------------------------------------
+struct FusedF32 {
+  const float* Gin;
+  float* Gout;
+  float* Gexp;  // G* export for the diffuse-wall kernel (NULL without diffuse walls)
+  float* Hf;
+  const float* pf;
+  KGrid g;
+  KGridF gf;
+  KParams p;
+  float dtidx, dtidy;
+  int R;         // rows per pass: 32 / nv1
+  int seg_rows;  // rows per segment
+  int nseg;
+};
 
-  const float u1 = pf[F_U1 * nc + cell], u2 = pf[F_U2 * nc + cell];
-  const float inv2T = pf[F_INV2T * nc + cell], iT = pf[F_IT * nc + cell];
-  const float kap = pf[F_KAP * nc + cell];
-  const float v1min = gf.v1min, v2min = gf.v2min, dv1 = gf.dv1, dv2 = gf.dv2;
+constexpr int kFusedWarps = 4;  // warps (columns) per CTA
 
-  for (int l = t; l < nv2; l += blockDim.x) {
-    const float c2 = fmaf(l + 0.5f, dv2, v2min) - u2;
+__device__ __forceinline__ bool exports_gstar(const KGrid& g, const KParams& p, int i, int j) {
+  return (p.bc[2] == MM_BC_DIFFUSE && j <= 1) || (p.bc[3] == MM_BC_DIFFUSE && j >= g.ny - 2) ||
+         (p.bc[0] == MM_BC_DIFFUSE && i == 0) || (p.bc[1] == MM_BC_DIFFUSE && i == g.nx - 1);
+}
+
+// Sum four floats over the warp; every lane receives the four totals.
+__device__ __forceinline__ void warp_allsum4(float v[4]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16;
+  const float s0 = h16 ? v[0] : v[2];
+  const float s1 = h16 ? v[1] : v[3];
+  const float k0 = (h16 ? v[2] : v[0]) + __shfl_xor_sync(full, s0, 16);
+  const float k1 = (h16 ? v[3] : v[1]) + __shfl_xor_sync(full, s1, 16);
+  const bool h8 = lane & 8;
+  const float s = h8 ? k0 : k1;
+  float kk = (h8 ? k1 : k0) + __shfl_xor_sync(full, s, 8);
+  kk += __shfl_xor_sync(full, kk, 4);
+  kk += __shfl_xor_sync(full, kk, 2);
+  kk += __shfl_xor_sync(full, kk, 1);
+  v[0] = __shfl_sync(full, kk, 0);
+  v[1] = __shfl_sync(full, kk, 8);
+  v[2] = __shfl_sync(full, kk, 16);
+  v[3] = __shfl_sync(full, kk, 24);
+}
+
+// x sweep of cell (i, j) into dst (the warp's shared-memory ring slot).
+__device__ __forceinline__ void wx_sweep(const FusedF32& a, int i, int j, float* dst, float* xt) {
+  const KGrid& g = a.g;
+  const int nv1 = g.nv1, nv2 = g.nv2, nc = g.nx * g.ny;
+  const int cell = j * g.nx + i;
+  float* c2t = xt;
+  float* c2q = xt + nv2;
+  float* e2t = xt + 2 * nv2;
+  float* qet = xt + 3 * nv2;
+  const int lane = threadIdx.x & 31, k = lane % nv1, r = lane / nv1;
+  const bool active = r < a.R;
+  const float u1 = __ldg(a.pf + F_U1 * nc + cell), u2 = __ldg(a.pf + F_U2 * nc + cell);
+  const float inv2T = __ldg(a.pf + F_INV2T * nc + cell), iT = __ldg(a.pf + F_IT * nc + cell);
+  const float kap = __ldg(a.pf + F_KAP * nc + cell);
+  for (int l = lane; l < nv2; l += 32) {
+    const float c2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
     const float q = c2 * c2;
     c2t[l] = c2;
     c2q[l] = q;
     e2t[l] = expf(-q * inv2T);
   }
-  const float v1 = fmaf(k + 0.5f, dv1, v1min);
+  const float v1 = fmaf(k + 0.5f, a.gf.dv1, a.gf.v1min);
   const float c1 = v1 - u1;
   const float av = fabsf(v1);
-  const float sig = -av * gf.idx;
-  const float lam = av * dtidx;
-  const UpwindF up = upwind_side(g, p, i, j, v1 > 0.f ? 0 : 1);
+  const float sig = -av * a.gf.idx;
+  const float lam = av * a.dtidx;
+  const UpwindF up = upwind_side(g, a.p, i, j, v1 > 0.f ? 0 : 1);
   const int ku = up.mirror ? nv1 - 1 - k : k;
   const size_t nv = (size_t)nv1 * nv2;
-  const float* Gc = Gin + (size_t)cell * nv + k;
-  const float* Gu = Gin + (size_t)up.cell * nv + ku;
-  __syncthreads();
-
+  const float* Gc = a.Gin + (size_t)cell * nv + k;
+  const float* Gu = a.Gin + (size_t)up.cell * nv + ku;
+  __syncwarp();
+  // pass 1: upwind differences and their moments; the loads of kChunk rows per lane are issued
+  // together so that many are in flight; dst keeps the upwind update G - dt Z = G + lam d
   float D0 = 0.f, D1 = 0.f, D2 = 0.f;
   if (active) {
-    for (int l = r; l < nv2; l += R) {
-      const float gv = Gc[l * nv1];
-      const float gu = up.zero ? 0.f : Gu[l * nv1];
-      const float d = gu - gv;
-      D0 += d;
-      D1 = fmaf(c2t[l], d, D1);
-      D2 = fmaf(c2q[l], d, D2);
+    constexpr int kChunk = 16;
+    for (int l0 = r; l0 < nv2; l0 += kChunk * a.R) {
+      float gv[kChunk], gu[kChunk];
+#pragma unroll
+      for (int m = 0; m < kChunk; ++m) {
+        const int l = l0 + m * a.R;
+        const bool in = l < nv2;
+        gv[m] = in ? __ldg(Gc + l * nv1) : 0.f;
+        gu[m] = (in && !up.zero) ? __ldg(Gu + l * nv1) : 0.f;
+      }
+#pragma unroll
+      for (int m = 0; m < kChunk; ++m) {
+        const int l = l0 + m * a.R;
+        if (l < nv2) {
+          const float d = gu[m] - gv[m];
+          dst[l * nv1 + k] = fmaf(lam, d, gv[m]);
+          D0 += d;
+          D1 = fmaf(c2t[l], d, D1);
+          D2 = fmaf(c2q[l], d, D2);
+        }
+      }
     }
   }
   const float sD0 = sig * D0;
-  const float S[4] = {sD0, c1 * sD0, sig * D1, fmaf(c1 * c1, sD0, sig * D2)};
-  warp_sum4f(S, part);
-  __syncthreads();
-  if (t == 0) {
-    float hi[4], lo[4];
-    sum_parts(part, hi, lo);
-    const float S0 = hi[0] + lo[0], S1 = hi[1] + lo[1], S2 = hi[2] + lo[2], S3 = hi[3] + lo[3];
-    bco[0] = fmaf(-S3, inv2T, 2.f * S0);
-    bco[1] = S1 * iT;
-    bco[2] = S2 * iT;
-    bco[3] = fmaf(0.25f * S3, iT * iT, -S0 * inv2T);
-  }
-  __syncthreads();
-  const float b0 = bco[0], b1 = bco[1], b2 = bco[2], gm = bco[3];
-  for (int l = t; l < nv2; l += blockDim.x) qet[l] = e2t[l] * fmaf(b2, c2t[l], gm * c2q[l]);
+  float S[4] = {sD0, c1 * sD0, sig * D1, fmaf(c1 * c1, sD0, sig * D2)};
+  warp_allsum4(S);
+  const float b0 = fmaf(-S[3], inv2T, 2.f * S[0]);
+  const float b1 = S[1] * iT, b2 = S[2] * iT;
+  const float gm = fmaf(0.25f * S[3], iT * iT, -S[0] * inv2T);
+  for (int l = lane; l < nv2; l += 32) qet[l] = e2t[l] * fmaf(b2, c2t[l], gm * c2q[l]);
   const float e1 = expf(-c1 * c1 * inv2T);
   const float bk = kap * e1;
   const float ak = bk * fmaf(gm * c1, c1, fmaf(b1, c1, b0));
-  __syncthreads();
-
+  __syncwarp();
+  // pass 2: G* = G - dt Z + dt Zhat, from shared memory only
+  const bool exp_ = a.Gexp != nullptr && exports_gstar(g, a.p, i, j);
   if (active) {
-    float* Go = Gout + (size_t)cell * nv + k;
-    for (int l = r; l < nv2; l += R) {
-      const float gv = Gc[l * nv1];
-      const float gu = up.zero ? 0.f : Gu[l * nv1];
-      const float d = gu - gv;
-      float o = fmaf(lam, d, gv);
+    float* Ge = a.Gexp + (size_t)cell * nv + k;
+    for (int l = r; l < nv2; l += a.R) {
+      float o = dst[l * nv1 + k];
       o = fmaf(ak, e2t[l], o);
       o = fmaf(bk, qet[l], o);
-      Go[l * nv1] = o;
+      dst[l * nv1 + k] = o;
+      if (exp_) Ge[l * nv1] = o;
     }
   }
+  __syncwarp();
 }
 
-constexpr int kYTablesF = 13;
-
-// y sweep + relaxation + heat flux (Eqs. zmicroy-update-micro-2D-ydir, 5-97, 5-98, 5-99) for
-// cells not adjacent to a diffuse wall
-__global__ void __launch_bounds__(512, 1) k_micro_y_f32(const float* __restrict__ Gs,
-                                                        float* __restrict__ Gout,
-                                                        float* __restrict__ Hf,
-                                                        const float* __restrict__ pf, KGrid g,
-                                                        KGridF gf, KParams p, float dtidy,
-                                                        int R) {
-  extern __shared__ float smf[];
-  const int nv1 = g.nv1, nv2 = g.nv2;
-  const int nc = g.nx * g.ny;
-  const int cell = blockIdx.x;
-  const int i = cell % g.nx, j = cell / g.nx;
-  if (diffuse_wall_cell(g, p, i, j)) return;
-
-  float* part = smf;
-  float* bco = smf + kPartF;
-  float* tb = smf + kHeadF;
+// y sweep + relaxation + heat flux of cell (i, j) from the G* rows in the warp's ring.
+__device__ __forceinline__ void wy_sweep(const FusedF32& a, int i, int j, const float* rc,
+                                         const float* srcb, bool mb, bool zb, const float* srct,
+                                         bool mt, bool zt, float* tb) {
+  const KGrid& g = a.g;
+  const int nv1 = g.nv1, nv2 = g.nv2, nc = g.nx * g.ny;
+  const int cell = j * g.nx + i;
   float* c2t = tb;
   float* c2q = tb + nv2;
   float* c2c = tb + 2 * nv2;
@@ -215,27 +213,22 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_f32(const float* __restrict_
   float* E1t = tb + 10 * nv2;
   float* E2t = tb + 11 * nv2;
   float* E3t = tb + 12 * nv2;
-
-  const int t = threadIdx.x;
-  const int k = t % nv1, r = t / nv1;
-  const bool active = r < R;
-
-  const float u1 = pf[F_U1 * nc + cell], u2 = pf[F_U2 * nc + cell];
-  const float inv2T = pf[F_INV2T * nc + cell], iT = pf[F_IT * nc + cell];
-  const float Ti11h = pf[F_TI11H * nc + cell], Ti12 = pf[F_TI12 * nc + cell];
-  const float Ti22h = pf[F_TI22H * nc + cell];
-  const float om1 = pf[F_OM1 * nc + cell], om1kap = pf[F_OM1KAP * nc + cell];
-  const float gam0 = pf[F_GAM0 * nc + cell], ome = pf[F_OME * nc + cell];
-  const float v1min = gf.v1min, v2min = gf.v2min, dv1 = gf.dv1, dv2 = gf.dv2;
-  const float idy = gf.idy;
-
-  for (int l = t; l < nv2; l += blockDim.x) {
-    const float v2 = fmaf(l + 0.5f, dv2, v2min);
+  const int lane = threadIdx.x & 31, k = lane % nv1, r = lane / nv1;
+  const bool active = r < a.R;
+  const float* pf = a.pf;
+  const float u1 = __ldg(pf + F_U1 * nc + cell), u2 = __ldg(pf + F_U2 * nc + cell);
+  const float inv2T = __ldg(pf + F_INV2T * nc + cell), iT = __ldg(pf + F_IT * nc + cell);
+  const float Ti11h = __ldg(pf + F_TI11H * nc + cell), Ti12 = __ldg(pf + F_TI12 * nc + cell);
+  const float Ti22h = __ldg(pf + F_TI22H * nc + cell);
+  const float om1 = __ldg(pf + F_OM1 * nc + cell), om1kap = __ldg(pf + F_OM1KAP * nc + cell);
+  const float gam0 = __ldg(pf + F_GAM0 * nc + cell), ome = __ldg(pf + F_OME * nc + cell);
+  for (int l = lane; l < nv2; l += 32) {
+    const float v2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min);
     const float c2 = v2 - u2;
     const float q = c2 * c2;
     const float e2 = expf(-q * inv2T);
     const float av = fabsf(v2);
-    const float sg = -av * idy;
+    const float sg = -av * a.gf.idy;
     c2t[l] = c2;
     c2q[l] = q;
     c2c[l] = q * c2;
@@ -245,57 +238,39 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_f32(const float* __restrict_
     s0t[l] = sg;
     s1t[l] = sg * c2;
     s2t[l] = sg * q;
-    wlt[l] = om1 * (av * dtidy);
+    wlt[l] = om1 * (av * a.dtidy);
     E1t[l] = e2 * c2;
     E2t[l] = e2 * q;
     E3t[l] = e2 * q * c2;
   }
-
-  const UpwindF ub = upwind_side(g, p, i, j, 2);
-  const UpwindF ut = upwind_side(g, p, i, j, 3);
-  const size_t nv = (size_t)nv1 * nv2;
-  const float* Gc = Gs + (size_t)cell * nv + k;
-  const float* Gb = Gs + (size_t)ub.cell * nv + k;
-  const float* Gt = Gs + (size_t)ut.cell * nv + k;
-  const float v1 = fmaf(k + 0.5f, dv1, v1min);
+  const float v1 = fmaf(k + 0.5f, a.gf.dv1, a.gf.v1min);
   const float c1 = v1 - u1;
   const float c1q = c1 * c1;
-  __syncthreads();
-
+  __syncwarp();
   float E0 = 0.f, E1 = 0.f, E2 = 0.f;
   if (active) {
-    for (int l = r; l < nv2; l += R) {
-      const float gv = Gc[l * nv1];
+    for (int l = r; l < nv2; l += a.R) {
+      const float gv = rc[l * nv1 + k];
       const bool top = v2t[l] < 0.f;
-      const UpwindF& u = top ? ut : ub;
-      const float* Gu = top ? Gt : Gb;
-      const int lu = u.mirror ? nv2 - 1 - l : l;
-      const float gu = u.zero ? 0.f : Gu[lu * nv1];
+      const float* src = top ? srct : srcb;
+      const int lu = (top ? mt : mb) ? nv2 - 1 - l : l;
+      const float gu = (top ? zt : zb) ? 0.f : src[lu * nv1 + k];
       const float d = gu - gv;
       E0 = fmaf(s0t[l], d, E0);
       E1 = fmaf(s1t[l], d, E1);
       E2 = fmaf(s2t[l], d, E2);
     }
   }
-  const float S[4] = {E0, c1 * E0, E1, fmaf(c1q, E0, E2)};
-  warp_sum4f(S, part);
-  __syncthreads();
-  if (t == 0) {
-    float hi[4], lo[4];
-    sum_parts(part, hi, lo);
-    const float S0 = hi[0] + lo[0], S1 = hi[1] + lo[1], S2 = hi[2] + lo[2], S3 = hi[3] + lo[3];
-    bco[0] = fmaf(-S3, inv2T, 2.f * S0);
-    bco[1] = S1 * iT;
-    bco[2] = S2 * iT;
-    bco[3] = fmaf(0.25f * S3, iT * iT, -S0 * inv2T);
-  }
-  __syncthreads();
-  const float b0 = bco[0], b1 = bco[1], b2 = bco[2], gm = bco[3];
-  const float w01 = pf[F_W01 * nc + cell], w02 = pf[F_W02 * nc + cell];
-  const float w03 = pf[F_W03 * nc + cell], w10 = pf[F_W10 * nc + cell];
-  const float w11 = pf[F_W11 * nc + cell], w12 = pf[F_W12 * nc + cell];
-  const float w20 = pf[F_W20 * nc + cell], w21 = pf[F_W21 * nc + cell];
-  const float w30 = pf[F_W30 * nc + cell];
+  float S[4] = {E0, c1 * E0, E1, fmaf(c1q, E0, E2)};
+  warp_allsum4(S);
+  const float b0 = fmaf(-S[3], inv2T, 2.f * S[0]);
+  const float b1 = S[1] * iT, b2 = S[2] * iT;
+  const float gm = fmaf(0.25f * S[3], iT * iT, -S[0] * inv2T);
+  const float w01 = __ldg(pf + F_W01 * nc + cell), w02 = __ldg(pf + F_W02 * nc + cell);
+  const float w03 = __ldg(pf + F_W03 * nc + cell), w10 = __ldg(pf + F_W10 * nc + cell);
+  const float w11 = __ldg(pf + F_W11 * nc + cell), w12 = __ldg(pf + F_W12 * nc + cell);
+  const float w20 = __ldg(pf + F_W20 * nc + cell), w21 = __ldg(pf + F_W21 * nc + cell);
+  const float w30 = __ldg(pf + F_W30 * nc + cell);
   const float C0 = om1kap * fmaf(gm, c1q, fmaf(b1, c1, b0)) - c1 * fmaf(c1, fmaf(c1, w03, w02), w01) - ome;
   const float C1 = fmaf(om1kap, b2, -fmaf(c1, fmaf(c1, w12, w11), w10));
   const float C2 = fmaf(om1kap, gm, -fmaf(c1, w21, w20));
@@ -303,20 +278,19 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_f32(const float* __restrict_
   const float e1 = expf(-c1q * inv2T);
   const float A0 = e1 * C0, A1 = e1 * C1, A2 = e1 * C2, A3 = e1 * C3;
   const float gam1 = gam0 * expf(-Ti11h * c1q);
-  const float c2r = fmaf(r + 0.5f, dv2, v2min) - u2;
+  const float c2r = fmaf(r + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
   float x = expf(-Ti12 * c1 * c2r);
-  const float rat = expf(-Ti12 * c1 * (R * dv2));
-
+  const float rat = expf(-Ti12 * c1 * (a.R * a.gf.dv2));
   float H0 = 0.f, H1 = 0.f, H2 = 0.f, H3 = 0.f;
   if (active) {
-    float* Go = Gout + (size_t)cell * nv + k;
-    for (int l = r; l < nv2; l += R) {
-      const float gv = Gc[l * nv1];
+    const size_t nv = (size_t)nv1 * nv2;
+    float* Go = a.Gout + (size_t)cell * nv + k;
+    for (int l = r; l < nv2; l += a.R) {
+      const float gv = rc[l * nv1 + k];
       const bool top = v2t[l] < 0.f;
-      const UpwindF& u = top ? ut : ub;
-      const float* Gu = top ? Gt : Gb;
-      const int lu = u.mirror ? nv2 - 1 - l : l;
-      const float gu = u.zero ? 0.f : Gu[lu * nv1];
+      const float* src = top ? srct : srcb;
+      const int lu = (top ? mt : mb) ? nv2 - 1 - l : l;
+      const float gu = (top ? zt : zb) ? 0.f : src[lu * nv1 + k];
       const float d = gu - gv;
       float o = fmaf(wlt[l], d, om1 * gv);
       o = fmaf(A0, e2t[l], o);
@@ -332,17 +306,51 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_f32(const float* __restrict_
       H3 = fmaf(c2c[l], o, H3);
     }
   }
-  const float Hs[4] = {c1q * c1 * H0, c1q * H1, c1 * H2, H3};
-  __syncthreads();  // the partial-sum slots are reused
-  warp_sum4f(Hs, part);
-  __syncthreads();
-  if (t == 0) {
-    float hi[4], lo[4];
-    sum_parts(part, hi, lo);
+  float Hs[4] = {c1q * c1 * H0, c1q * H1, c1 * H2, H3};
+  warp_allsum4(Hs);
+  if (lane == 0) {
     for (int m = 0; m < 4; ++m) {
-      Hf[(2 * m) * nc + cell] = hi[m];
-      Hf[(2 * m + 1) * nc + cell] = lo[m];
+      a.Hf[(2 * m) * nc + cell] = Hs[m];
+      a.Hf[(2 * m + 1) * nc + cell] = 0.f;
     }
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(32 * kFusedWarps) k_micro_fused_f32(FusedF32 a) {
+  extern __shared__ float smf[];
+  const KGrid& g = a.g;
+  const int nv = g.nv1 * g.nv2;
+  const int w = threadIdx.x >> 5;
+  const int per_warp = 3 * nv + 17 * g.nv2;
+  float* ring = smf + (size_t)w * per_warp;
+  float* xt = ring + 3 * nv;
+  float* yt = xt + 4 * g.nv2;
+  const int gw = blockIdx.x * kFusedWarps + w;
+  if (gw >= g.nx * a.nseg) return;  // whole warp leaves; no CTA-wide barrier is used below
+  const int i = gw % g.nx;
+  const int seg = gw / g.nx;
+  const int j0 = seg * a.seg_rows;
+  const int j1 = min(g.ny, j0 + a.seg_rows);
+  if (j0 >= j1) return;
+  const bool pery = a.p.bc[2] == MM_BC_PERIODIC;
+  // position p = j - j0 + 1 of a row in the march; its G* lives in ring slot p % 3
+  auto slot = [&](int pos) { return ring + (size_t)(pos % 3) * nv; };
+  if (j0 > 0 || pery) wx_sweep(a, i, j0 > 0 ? j0 - 1 : g.ny - 1, slot(0), xt);
+  wx_sweep(a, i, j0, slot(1), xt);
+  for (int j = j0; j < j1; ++j) {
+    const int pos = j - j0 + 1;
+    if (j + 1 < g.ny || pery) wx_sweep(a, i, j + 1 < g.ny ? j + 1 : 0, slot(pos + 1), xt);
+    if (diffuse_wall_cell(g, a.p, i, j)) continue;  // finished by the wall kernel
+    const float* rc = slot(pos);
+    const bool hasb = j > 0 || pery, hast = j < g.ny - 1 || pery;
+    const float* srcb = hasb ? slot(pos + 2) : rc;  // slot(pos - 1)
+    const float* srct = hast ? slot(pos + 1) : rc;
+    const bool mb = !hasb && a.p.bc[2] == MM_BC_SPECULAR;
+    const bool zb = !hasb && a.p.bc[2] == MM_BC_DIFFUSE;
+    const bool mt = !hast && a.p.bc[3] == MM_BC_SPECULAR;
+    const bool zt = !hast && a.p.bc[3] == MM_BC_DIFFUSE;
+    wy_sweep(a, i, j, rc, srcb, mb, zb, srct, mt, zt, yt);
   }
 }
 
@@ -353,23 +361,55 @@ KGridF grid_f32(const KGrid& g) {
                 (float)g.idy};
 }
 
-void launch_micro_x_f32(const float* Gin, float* Gout, const float* primf, const KGrid& g,
-                        const KParams& p, double dt, const MicroShape& ms, cudaStream_t s) {
-  const size_t smem = sizeof(float) * (kHeadF + 4 * (size_t)g.nv2);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_micro_x_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_micro_x_f32<<<g.nx * g.ny, ms.threads, smem, s>>>(Gin, Gout, primf, g, grid_f32(g), p,
-                                                      (float)(dt * g.idx), ms.R);
+static size_t fused_smem(const KGrid& g) {
+  return sizeof(float) * kFusedWarps * (3 * (size_t)g.nv1 * g.nv2 + 17 * (size_t)g.nv2);
 }
 
-void launch_micro_y_f32(const float* Gs, float* Gout, float* Hf, const float* primf,
-                        const KGrid& g, const KParams& p, double dt, const MicroShape& ms,
-                        cudaStream_t s) {
-  const size_t smem = sizeof(float) * (kHeadF + kYTablesF * (size_t)g.nv2);
+int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
+  (void)ms;
+  const size_t smem = fused_smem(g);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_micro_y_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_micro_y_f32<<<g.nx * g.ny, ms.threads, smem, s>>>(Gs, Gout, Hf, primf, g, grid_f32(g), p,
-                                                      (float)(dt * g.idy), ms.R);
+    cudaFuncSetAttribute(k_micro_fused_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_micro_fused_f32, 32 * kFusedWarps,
+                                                smem);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long resident = (long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * kFusedWarps;
+  // about four resident waves of columns, but at least 16 rows per segment
+  long nseg = (4 * resident + g.nx - 1) / g.nx;
+  const long max_seg = g.ny / 16 > 1 ? g.ny / 16 : 1;
+  if (nseg > max_seg) nseg = max_seg;
+  if (nseg < 1) nseg = 1;
+  return (int)nseg;
+}
+
+void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
+                            const float* primf, const KGrid& g, const KParams& p, double dt,
+                            const MicroShape& ms, int nseg, cudaStream_t s) {
+  (void)ms;
+  const size_t smem = fused_smem(g);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_micro_fused_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  FusedF32 a;
+  a.Gin = Gin;
+  a.Gout = Gout;
+  a.Gexp = Gexp;
+  a.Hf = Hf;
+  a.pf = primf;
+  a.g = g;
+  a.gf = grid_f32(g);
+  a.p = p;
+  a.dtidx = (float)(dt * g.idx);
+  a.dtidy = (float)(dt * g.idy);
+  a.R = 32 / g.nv1;
+  a.nseg = nseg;
+  a.seg_rows = (g.ny + nseg - 1) / nseg;
+  const int warps = g.nx * nseg;
+  k_micro_fused_f32<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, smem, s>>>(a);
 }
 
 }  // namespace mmk
