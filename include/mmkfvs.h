@@ -140,6 +140,36 @@ const char* mm_kernel_name(int idx);
 /* Release the context and its device memory (NULL is accepted). */
 void mm_destroy(mm_ctx* ctx);
 
+/* ---- batches of independent problems --------------------------------------------------------
+ * Many independent problems of uneven size and Knudsen number stepped together (FP64; nv1 <=
+ * 256).  Each phase of the step is one launch of a persistent kernel whose CTAs stride over the
+ * cells of all problems; one batch step is captured in a CUDA graph and replayed; the CTA and grid
+ * sizes of the phase-space kernels come from mm_batch_autotune (timed trial launches on the
+ * batch's own data, cached per process by the multiset of problem shapes).  Problem q's arrays
+ * have the single-problem layouts of this header. */
+typedef struct mm_batch mm_batch;
+/* grids[nprob], params[nprob]: as for mm_create, each validated the same way.  cuda_stream NULL:
+ * the batch creates its own non-blocking stream (graph capture needs a non-default stream). */
+mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* params,
+                          void* cuda_stream, mm_batch** out);
+/* State of problem q from host memory (G_host NULL: g = 0); synchronous. */
+mm_status mm_batch_set_state(mm_batch* b, int q, const double* Q_host, const double* G_host);
+/* nsteps steps of every problem, problem q with time step dt[q] and Knudsen number eps[q]
+ * (host arrays of nprob values); asynchronous. */
+mm_status mm_batch_step(mm_batch* b, const double* dt, const double* eps, int nsteps);
+/* Choose the CTA size and grid size of the phase-space kernels by timing trial launches (the
+ * state is not changed); best values written to the optional outputs.  Call after the first
+ * mm_batch_step (so that dt, eps are set). */
+mm_status mm_batch_autotune(mm_batch* b, int* threads_out, int* ctas_out);
+/* 1 (default): replay a captured CUDA graph of one batch step; 0: launch the kernels directly. */
+mm_status mm_batch_set_graph(mm_batch* b, int enable);
+/* Wait and report device errors (MM_ERR_NONPHYSICAL). */
+mm_status mm_batch_sync(mm_batch* b);
+mm_status mm_batch_get_moments(mm_batch* b, int q, double* Q_host, double* H_host);
+mm_status mm_batch_get_g(mm_batch* b, int q, double* G_host);
+const char* mm_batch_last_error(const mm_batch* b);
+void mm_batch_destroy(mm_batch* b);
+
 /* Diagnostic: evaluate the table-driven exponential used by the phase-space kernels (Tang's
  * method, see the micro kernels) and the CUDA library exp on n FP64 device values x_dev, into
  * caller-owned device arrays; synchronises cuda_stream.  Used to test the kernels' exp against

@@ -39,7 +39,10 @@ class mm_params(ctypes.Structure):
 EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device", "mm_step",
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
-           "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp"]
+           "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp",
+           "mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
+           "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments", "mm_batch_get_g",
+           "mm_batch_last_error", "mm_batch_destroy"]
 
 _lib = None
 
@@ -82,6 +85,22 @@ def load(build_if_needed: bool = True):
     L.mm_kernel_name.restype = ctypes.c_char_p
     L.mm_destroy.argtypes = [vp]
     L.mm_destroy.restype = None
+    L.mm_batch_create.argtypes = [ctypes.c_int, G, P, vp, ctypes.POINTER(vp)]
+    L.mm_batch_set_state.argtypes = [vp, ctypes.c_int, vp, vp]
+    L.mm_batch_step.argtypes = [vp, _dp, _dp, ctypes.c_int]
+    L.mm_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.mm_batch_set_graph.argtypes = [vp, ctypes.c_int]
+    L.mm_batch_sync.argtypes = [vp]
+    L.mm_batch_get_moments.argtypes = [vp, ctypes.c_int, vp, vp]
+    L.mm_batch_get_g.argtypes = [vp, ctypes.c_int, vp]
+    L.mm_batch_last_error.argtypes = [vp]
+    L.mm_batch_last_error.restype = ctypes.c_char_p
+    L.mm_batch_destroy.argtypes = [vp]
+    L.mm_batch_destroy.restype = None
+    for name in ["mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
+                 "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments",
+                 "mm_batch_get_g"]:
+        getattr(L, name).restype = ctypes.c_int
     L.mm_diag_exp.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
     L.mm_diag_exp.restype = ctypes.c_int
     L.mm_step_static_scratch.argtypes = [G, P, vp, vp, vp, ctypes.c_double, ctypes.c_double,
@@ -275,3 +294,81 @@ class Solver:
 
     def last_error(self):
         return self.L.mm_last_error(self.ctx).decode()
+
+
+class BatchSolver:
+    """Many independent problems stepped together (mm_batch_*)."""
+
+    def __init__(self, grids, params, stream=0):
+        self.L = load()
+        self.grids, self.params = list(grids), list(params)
+        n = len(self.grids)
+        G = (mm_grid * n)(*[to_c_grid(g) for g in self.grids])
+        P = (mm_params * n)(*[to_c_params(p) for p in self.params])
+        self.b = ctypes.c_void_p()
+        st = self.L.mm_batch_create(n, G, P, ctypes.c_void_p(int(stream)), ctypes.byref(self.b))
+        if st != MM_OK:
+            raise MMError(st, "mm_batch_create rejected the problems or could not allocate")
+        self.n = n
+
+    def _check(self, st, what):
+        if st != MM_OK:
+            raise MMError(st, "%s: %s" % (what, self.L.mm_batch_last_error(self.b).decode()))
+
+    def close(self):
+        if self.b:
+            self.L.mm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, q, Q, G=None):
+        g = self.grids[q]
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        G = None if G is None else np.ascontiguousarray(G, dtype=np.float64)
+        st = self.L.mm_batch_set_state(self.b, int(q), _host_ptr(Q, 6 * g.nx * g.ny),
+                                       _host_ptr(G, g.nx * g.ny * g.nv1 * g.nv2))
+        self._check(st, "mm_batch_set_state")
+
+    def step(self, dt, eps, nsteps=1):
+        dt = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, float), (self.n,)))
+        eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, float), (self.n,)))
+        st = self.L.mm_batch_step(self.b, dt.ctypes.data_as(_dp), eps.ctypes.data_as(_dp),
+                                  int(nsteps))
+        self._check(st, "mm_batch_step")
+
+    def autotune(self):
+        t, c = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.L.mm_batch_autotune(self.b, ctypes.byref(t), ctypes.byref(c)),
+                    "mm_batch_autotune")
+        return t.value, c.value
+
+    def set_graph(self, enable):
+        self._check(self.L.mm_batch_set_graph(self.b, int(enable)), "mm_batch_set_graph")
+
+    def sync(self):
+        self._check(self.L.mm_batch_sync(self.b), "mm_batch_sync")
+
+    def get_moments(self, q):
+        g = self.grids[q]
+        Q = np.empty((6, g.ny, g.nx))
+        H = np.empty((4, g.ny, g.nx))
+        self._check(self.L.mm_batch_get_moments(self.b, int(q), Q.ctypes.data, H.ctypes.data),
+                    "mm_batch_get_moments")
+        return Q, H
+
+    def get_g(self, q):
+        g = self.grids[q]
+        G = np.empty((g.ny, g.nx, g.nv2, g.nv1))
+        self._check(self.L.mm_batch_get_g(self.b, int(q), G.ctypes.data), "mm_batch_get_g")
+        return G

@@ -112,7 +112,17 @@ void launch_macro_x2(const double* H, const MacroBufs& mb, const KGrid& g, const
 void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGrid& g,
                     const KParams& p, double dt, double eps, int* err, cudaStream_t s);
 void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s);
-MacroBufs carve_macro(double* base, int nx, int ny);
+__host__ __device__ inline MacroBufs carve_macro(double* base, int nx, int ny) {
+  const size_t nc = (size_t)nx * ny;
+  MacroBufs mb;
+  mb.Q1 = base;
+  mb.Q2 = mb.Q1 + 6 * nc;
+  mb.FX = mb.Q2 + 6 * nc;
+  mb.FY = mb.FX + 12 * nc;
+  mb.BX = mb.FY + 12 * nc;
+  mb.BY = mb.BX + 12 * (size_t)ny;
+  return mb;
+}
 void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s);
 void launch_convert_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);

@@ -12,183 +12,22 @@
 // order of its rows, then combined across the CTA with warp shuffles and shared memory.
 #include <cmath>
 
-#include "mm_exp.cuh"
-#include "mm_internal.cuh"
+#include "mm_body_micro.cuh"
 
 namespace mmk {
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
-constexpr int kRed = 132;
-constexpr int kMaxThreads = 512;  // CTA size limit of the micro kernels (register budget)  // shared doubles reserved for block reductions (32 warps x 4 + 4)
+using namespace micro_body;
 
-// Sum four values over the CTA; every thread receives the four totals.  Within a warp the
-// values are reduced with a transposing butterfly (6 adds per lane instead of 20).
-__device__ __forceinline__ void block_sum4(double v[4], double* red) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool h16 = lane & 16;
-  double s0 = h16 ? v[0] : v[2];
-  double s1 = h16 ? v[1] : v[3];
-  double k0 = (h16 ? v[2] : v[0]) + __shfl_xor_sync(full, s0, 16);
-  double k1 = (h16 ? v[3] : v[1]) + __shfl_xor_sync(full, s1, 16);
-  const bool h8 = lane & 8;
-  double s = h8 ? k0 : k1;
-  double kk = (h8 ? k1 : k0) + __shfl_xor_sync(full, s, 8);
-  kk += __shfl_xor_sync(full, kk, 4);
-  kk += __shfl_xor_sync(full, kk, 2);
-  kk += __shfl_xor_sync(full, kk, 1);
-  if ((lane & 7) == 0) red[warp * 4 + (lane >> 3)] = kk;
-  __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  if (threadIdx.x < 4) {
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += red[w * 4 + threadIdx.x];
-    red[128 + threadIdx.x] = t;
-  }
-  __syncthreads();
-  v[0] = red[128];
-  v[1] = red[129];
-  v[2] = red[130];
-  v[3] = red[131];
-}
-
-// Upwind neighbour of cell (i, j) across side s, following the boundary rules of the micro
-// step: periodic wrap; extrapolation drops the outside difference (neighbour = the cell itself);
-// specular uses the cell itself at the mirrored velocity; diffuse sets the inflow of g to zero.
-struct Upwind {
-  int cell;     // neighbour cell index
-  bool mirror;  // read the mirrored velocity index
-  bool zero;    // inflow value is zero
-};
-
-__device__ __forceinline__ Upwind upwind_x(const KGrid& g, const KParams& p, int i, int j, int s) {
-  Upwind u{0, false, false};
-  int ni = s == 0 ? i - 1 : i + 1;
-  if (ni < 0 || ni >= g.nx) {
-    const int bc = p.bc[s];
-    if (bc == MM_BC_PERIODIC) ni = (ni + g.nx) % g.nx;
-    else if (bc == MM_BC_EXTRAP) ni = i;
-    else if (bc == MM_BC_SPECULAR) { ni = i; u.mirror = true; }
-    else { ni = i; u.zero = true; }
-  }
-  u.cell = j * g.nx + ni;
-  return u;
-}
-
-__device__ __forceinline__ Upwind upwind_y(const KGrid& g, const KParams& p, int i, int j, int s) {
-  Upwind u{0, false, false};
-  int nj = s == 2 ? j - 1 : j + 1;
-  if (nj < 0 || nj >= g.ny) {
-    const int bc = p.bc[s];
-    if (bc == MM_BC_PERIODIC) nj = (nj + g.ny) % g.ny;
-    else if (bc == MM_BC_EXTRAP) nj = j;
-    else if (bc == MM_BC_SPECULAR) { nj = j; u.mirror = true; }
-    else { nj = j; u.zero = true; }
-  }
-  u.cell = nj * g.nx + i;
-  return u;
-}
-
-__device__ __forceinline__ bool diffuse_wall_cell(const KGrid& g, const KParams& p, int i, int j) {
-  return (i == 0 && p.bc[0] == MM_BC_DIFFUSE) || (i == g.nx - 1 && p.bc[1] == MM_BC_DIFFUSE) ||
-         (j == 0 && p.bc[2] == MM_BC_DIFFUSE) || (j == g.ny - 1 && p.bc[3] == MM_BC_DIFFUSE);
-}
-
-// ------------------------------------------------------------------------------------------
-// x sweep: Eqs. (zmicrox), (coeffs-2D-xdir), (zhat-2D-xdir), (update-micro-2D-xdir)
-// ------------------------------------------------------------------------------------------
 template <typename Tg>
 __global__ void __launch_bounds__(512, 1) k_micro_x(const Tg* __restrict__ Gin,
                                                     Tg* __restrict__ Gout,
                                                     const double* __restrict__ prim, KGrid g,
                                                     KParams p, double dtidx, int R) {
   extern __shared__ double sm[];
-  const int nv1 = g.nv1, nv2 = g.nv2;
-  double* red = sm;
-  double* c2t = sm + kRed;
-  double* c2q = c2t + nv2;
-  double* e2t = c2q + nv2;
-  double* qet = e2t + nv2;
-
-  const int nc = g.nx * g.ny;
-  const int cell = blockIdx.x;
-  const int i = cell % g.nx, j = cell / g.nx;
-  const int t = threadIdx.x;
-  const int k = t % nv1, r = t / nv1;
-  const bool active = r < R;
-
-  const double u1 = prim[P_U1 * nc + cell], u2 = prim[P_U2 * nc + cell];
-  const double inv2T = prim[P_INV2T * nc + cell], iT = prim[P_IT * nc + cell];
-  const double kap = prim[P_KAP * nc + cell];
-
-  for (int l = t; l < nv2; l += blockDim.x) {
-    const double c2 = fma(l + 0.5, g.dv2, g.v2min) - u2;
-    const double q = c2 * c2;
-    c2t[l] = c2;
-    c2q[l] = q;
-    e2t[l] = expd(-q * inv2T);
-  }
-
-  const double v1 = fma(k + 0.5, g.dv1, g.v1min);
-  const double c1 = v1 - u1;
-  const double av = fabs(v1);
-  const double sig = -av * g.idx;  // Z = sig * (G_up - G)
-  const double lam = av * dtidx;   // -dt Z = lam * (G_up - G)
-  const Upwind up = upwind_x(g, p, i, j, v1 > 0.0 ? 0 : 1);
-  const int ku = up.mirror ? nv1 - 1 - k : k;
-  const size_t nv = (size_t)nv1 * nv2;
-  const Tg* Gc = Gin + (size_t)cell * nv + k;
-  const Tg* Gu = Gin + (size_t)up.cell * nv + ku;
-  __syncthreads();
-
-  // pass 1: velocity moments of Z
-  double D0 = 0.0, D1 = 0.0, D2 = 0.0;
-  if (active) {
-    for (int l = r; l < nv2; l += R) {
-      const double gv = (double)Gc[l * nv1];
-      const double gu = up.zero ? 0.0 : (double)Gu[l * nv1];
-      const double d = gu - gv;
-      D0 += d;
-      D1 = fma(c2t[l], d, D1);
-      D2 = fma(c2q[l], d, D2);
-    }
-  }
-  const double sD0 = sig * D0;
-  double S[4] = {sD0, c1 * sD0, sig * D1, fma(c1 * c1, sD0, sig * D2)};
-  block_sum4(S, red);
-
-  // projection coefficients: Zhat = (dv1 dv2 / (2 pi T)) e1 e2 (b0 + b1 c1 + b2 c2 + gm |c|^2)
-  const double b0 = fma(-S[3], inv2T, 2.0 * S[0]);
-  const double b1 = S[1] * iT, b2 = S[2] * iT;
-  const double gm = fma(0.25 * S[3], iT * iT, -S[0] * inv2T);
-  for (int l = t; l < nv2; l += blockDim.x) qet[l] = e2t[l] * fma(b2, c2t[l], gm * c2q[l]);
-  const double e1 = expd(-c1 * c1 * inv2T);
-  const double bk = kap * e1;
-  const double ak = bk * fma(gm * c1, c1, fma(b1, c1, b0));
-  __syncthreads();
-
-  // pass 2: G* = G - dt Z + dt Zhat
-  if (active) {
-    Tg* Go = Gout + (size_t)cell * nv + k;
-    for (int l = r; l < nv2; l += R) {
-      const double gv = (double)Gc[l * nv1];
-      const double gu = up.zero ? 0.0 : (double)Gu[l * nv1];
-      const double d = gu - gv;
-      double o = fma(lam, d, gv);
-      o = fma(ak, e2t[l], o);
-      o = fma(bk, qet[l], o);
-      Go[l * nv1] = (Tg)o;
-    }
-  }
+  micro_x_body<Tg>(Gin, Gout, prim, g, p, dtidx, R, blockIdx.x, sm);
 }
-
-// ------------------------------------------------------------------------------------------
-// y sweep + relaxation + heat flux for cells not adjacent to a diffuse wall:
-// Eqs. (zmicroy)-(update-micro-2D-ydir), (5-97), (5-97more), (5-98), (5-99)
-// ------------------------------------------------------------------------------------------
-constexpr int kYTables = 13;
 
 template <typename Tg>
 __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs,
@@ -198,334 +37,19 @@ __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs,
                                                     KParams p, double dtidy, double hscale, int R,
                                                     int* __restrict__ err) {
   extern __shared__ double sm[];
-  const int nv1 = g.nv1, nv2 = g.nv2;
-  const int nc = g.nx * g.ny;
-  const int cell = blockIdx.x;
-  const int i = cell % g.nx, j = cell / g.nx;
-  if (diffuse_wall_cell(g, p, i, j)) return;  // handled by k_micro_y_wall
-
-  double* red = sm;
-  double* tb = sm + kRed;
-  double* c2t = tb;
-  double* c2q = tb + nv2;
-  double* c2c = tb + 2 * nv2;
-  double* e2t = tb + 3 * nv2;
-  double* g2t = tb + 4 * nv2;
-  double* v2t = tb + 5 * nv2;
-  double* s0t = tb + 6 * nv2;
-  double* s1t = tb + 7 * nv2;
-  double* s2t = tb + 8 * nv2;
-  double* wlt = tb + 9 * nv2;
-  double* E1t = tb + 10 * nv2;
-  double* E2t = tb + 11 * nv2;
-  double* E3t = tb + 12 * nv2;
-
-  const int t = threadIdx.x;
-  const int k = t % nv1, r = t / nv1;
-  const bool active = r < R;
-
-  const double u1 = prim[P_U1 * nc + cell], u2 = prim[P_U2 * nc + cell];
-  const double inv2T = prim[P_INV2T * nc + cell], iT = prim[P_IT * nc + cell];
-  const double Ti11 = prim[P_TI11 * nc + cell], Ti12 = prim[P_TI12 * nc + cell];
-  const double Ti22 = prim[P_TI22 * nc + cell];
-  const double om1 = prim[P_OM1 * nc + cell], om1kap = prim[P_OM1KAP * nc + cell];
-  const double gam0 = prim[P_GAM0 * nc + cell], ome = prim[P_OME * nc + cell];
-
-  for (int l = t; l < nv2; l += blockDim.x) {
-    const double v2 = fma(l + 0.5, g.dv2, g.v2min);
-    const double c2 = v2 - u2;
-    const double q = c2 * c2;
-    const double e2 = expd(-q * inv2T);
-    const double av = fabs(v2);
-    const double sg = -av * g.idy;
-    c2t[l] = c2;
-    c2q[l] = q;
-    c2c[l] = q * c2;
-    e2t[l] = e2;
-    g2t[l] = expd(-0.5 * Ti22 * q);
-    v2t[l] = v2;
-    s0t[l] = sg;
-    s1t[l] = sg * c2;
-    s2t[l] = sg * q;
-    wlt[l] = om1 * (av * dtidy);
-    E1t[l] = e2 * c2;
-    E2t[l] = e2 * q;
-    E3t[l] = e2 * q * c2;
-  }
-
-  const Upwind ub = upwind_y(g, p, i, j, 2);  // upwind for v2 > 0
-  const Upwind ut = upwind_y(g, p, i, j, 3);  // upwind for v2 < 0
-  const size_t nv = (size_t)nv1 * nv2;
-  const Tg* Gc = Gs + (size_t)cell * nv + k;
-  const Tg* Gb = Gs + (size_t)ub.cell * nv + k;
-  const Tg* Gt = Gs + (size_t)ut.cell * nv + k;
-
-  const double v1 = fma(k + 0.5, g.dv1, g.v1min);
-  const double c1 = v1 - u1;
-  const double c1q = c1 * c1;
-  __syncthreads();
-
-  // pass 1: velocity moments of Z*
-  double E0 = 0.0, E1 = 0.0, E2 = 0.0;
-  if (active) {
-    for (int l = r; l < nv2; l += R) {
-      const double gv = (double)Gc[l * nv1];
-      const bool top = v2t[l] < 0.0;
-      const Upwind& u = top ? ut : ub;
-      const Tg* Gu = top ? Gt : Gb;
-      const int lu = u.mirror ? nv2 - 1 - l : l;
-      const double gu = u.zero ? 0.0 : (double)Gu[lu * nv1];
-      const double d = gu - gv;
-      E0 = fma(s0t[l], d, E0);
-      E1 = fma(s1t[l], d, E1);
-      E2 = fma(s2t[l], d, E2);
-    }
-  }
-  double S[4] = {E0, c1 * E0, E1, fma(c1q, E0, E2)};
-  block_sum4(S, red);
-
-  const double b0 = fma(-S[3], inv2T, 2.0 * S[0]);
-  const double b1 = S[1] * iT, b2 = S[2] * iT;
-  const double gm = fma(0.25 * S[3], iT * iT, -S[0] * inv2T);
-  // om1 dt Zhat* and om2 Ghat's Maxwellian part as one cubic in c2 times e1 e2
-  const double w01 = prim[P_W01 * nc + cell], w02 = prim[P_W02 * nc + cell];
-  const double w03 = prim[P_W03 * nc + cell], w10 = prim[P_W10 * nc + cell];
-  const double w11 = prim[P_W11 * nc + cell], w12 = prim[P_W12 * nc + cell];
-  const double w20 = prim[P_W20 * nc + cell], w21 = prim[P_W21 * nc + cell];
-  const double w30 = prim[P_W30 * nc + cell];
-  const double C0 = om1kap * fma(gm, c1q, fma(b1, c1, b0)) - c1 * fma(c1, fma(c1, w03, w02), w01) - ome;
-  const double C1 = fma(om1kap, b2, -fma(c1, fma(c1, w12, w11), w10));
-  const double C2 = fma(om1kap, gm, -fma(c1, w21, w20));
-  const double C3 = -w30;
-  const double e1 = expd(-c1q * inv2T);
-  const double A0 = e1 * C0, A1 = e1 * C1, A2 = e1 * C2, A3 = e1 * C3;
-  const double gam1 = gam0 * expd(-0.5 * Ti11 * c1q);
-  const double c2r = fma(r + 0.5, g.dv2, g.v2min) - u2;
-  double x = expd(-Ti12 * c1 * c2r);
-  const double rat = expd(-Ti12 * c1 * (R * g.dv2));
-
-  // pass 2: G^{n+1} = om1 (G* - dt Z* + dt Zhat*) + om2 Ghat, and its heat-flux moments
-  double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0;
-  if (active) {
-    Tg* Go = Gout + (size_t)cell * nv + k;
-    for (int l = r; l < nv2; l += R) {
-      const double gv = (double)Gc[l * nv1];
-      const bool top = v2t[l] < 0.0;
-      const Upwind& u = top ? ut : ub;
-      const Tg* Gu = top ? Gt : Gb;
-      const int lu = u.mirror ? nv2 - 1 - l : l;
-      const double gu = u.zero ? 0.0 : (double)Gu[lu * nv1];
-      const double d = gu - gv;
-      double o = fma(wlt[l], d, om1 * gv);
-      o = fma(A0, e2t[l], o);
-      o = fma(A1, E1t[l], o);
-      o = fma(A2, E2t[l], o);
-      o = fma(A3, E3t[l], o);
-      o = fma(gam1, g2t[l] * x, o);
-      x *= rat;
-      const Tg os = (Tg)o;
-      Go[l * nv1] = os;
-      const double ov = (double)os;
-      H0 += ov;
-      H1 = fma(c2t[l], ov, H1);
-      H2 = fma(c2q[l], ov, H2);
-      H3 = fma(c2c[l], ov, H3);
-    }
-  }
-  double Hs[4] = {c1q * c1 * H0, c1q * H1, c1 * H2, H3};
-  block_sum4(Hs, red);
-  if (t == 0) {
-    bool ok = true;
-    for (int m = 0; m < 4; ++m) {
-      Hout[m * nc + cell] = hscale * Hs[m];
-      ok = ok && isfinite(Hs[m]);
-    }
-    if (!ok) atomicOr(err, ERR_NONFINITE_G);
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// y sweep + relaxation + heat flux for cells adjacent to a diffuse wall (Section 6.3): Ghat is
-// -(1/tau)(I - Pi_M)[upwind v.grad M] with ghost wall Maxwellians, plus (G - M)/eps if kept.
-// ------------------------------------------------------------------------------------------
-struct SideM {
-  int kind;  // 0 neighbour/periodic, 1 extrapolation (the cell's own M), 2 specular, 3 diffuse
-  double rho, u1, u2, T;  // kind 0: neighbour prims; kind 3: wall density, velocity, temperature
-};
-
-__device__ __forceinline__ double maxw(double rho, double u1, double u2, double T, double v1,
-                                       double v2) {
-  const double a = v1 - u1, b = v2 - u2;
-  return rho / (2.0 * kPi * T) * exp(-(a * a + b * b) / (2.0 * T));
-}
-
-// Eq. (twodim_wall_densities_1)
-__device__ __forceinline__ double wall_R(double ua, double Taa, double Tw, double sgn) {
-  return sqrt(Taa / Tw) * exp(-ua * ua / (2.0 * Taa)) +
-         ua * sqrt(kPi / (2.0 * Tw)) * (erf(ua / sqrt(2.0 * Taa)) + sgn);
+  micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, blockIdx.x, sm);
 }
 
 template <typename Tg>
-__global__ void __launch_bounds__(512, 1) k_micro_y_wall(const Tg* __restrict__ Gs, Tg* __restrict__ Gout,
-                               double* __restrict__ Hout, const double* __restrict__ prim,
-                               const int* __restrict__ wall_cells, KGrid g, KParams p, double dt,
-                               double eps, int R, int* __restrict__ err) {
+__global__ void __launch_bounds__(512, 1) k_micro_y_wall(const Tg* __restrict__ Gs,
+                                                         Tg* __restrict__ Gout,
+                                                         double* __restrict__ Hout,
+                                                         const double* __restrict__ prim,
+                                                         const int* __restrict__ wall_cells,
+                                                         KGrid g, KParams p, double dt, double eps,
+                                                         int R, int* __restrict__ err) {
   extern __shared__ double sm[];
-  double* red = sm;
-  const int nv1 = g.nv1, nv2 = g.nv2;
-  const int nc = g.nx * g.ny;
-  const int cell = wall_cells[blockIdx.x];
-  const int i = cell % g.nx, j = cell / g.nx;
-  const int t = threadIdx.x;
-  const int k = t % nv1, r = t / nv1;
-  const bool active = r < R;
-
-  const double rho = prim[P_RHO * nc + cell];
-  const double u1 = prim[P_U1 * nc + cell], u2 = prim[P_U2 * nc + cell];
-  const double T = prim[P_T * nc + cell];
-  const double tau = prim[P_TAU * nc + cell];
-  const double Ti11 = prim[P_TI11 * nc + cell], Ti12 = prim[P_TI12 * nc + cell];
-  const double Ti22 = prim[P_TI22 * nc + cell];
-  const double KG = prim[P_KG * nc + cell];
-  const double Th11 = prim[P_TH11 * nc + cell], Th22 = prim[P_TH22 * nc + cell];
-  const double inv2T = 0.5 / T, iT = 1.0 / T;
-  const double om1 = eps / (eps + dt * tau);
-  const double om2 = dt * tau / (eps + dt * tau);
-
-  SideM sd[4];
-  for (int s = 0; s < 4; ++s) {
-    int ni = i + (s == 0 ? -1 : s == 1 ? 1 : 0);
-    int nj = j + (s == 2 ? -1 : s == 3 ? 1 : 0);
-    bool inside = ni >= 0 && ni < g.nx && nj >= 0 && nj < g.ny;
-    if (!inside && p.bc[s] == MM_BC_PERIODIC) {
-      ni = (ni + g.nx) % g.nx;
-      nj = (nj + g.ny) % g.ny;
-      inside = true;
-    }
-    if (inside) {
-      const int c = nj * g.nx + ni;
-      sd[s] = SideM{0, prim[P_RHO * nc + c], prim[P_U1 * nc + c], prim[P_U2 * nc + c],
-                    prim[P_T * nc + c]};
-    } else if (p.bc[s] == MM_BC_EXTRAP) {
-      sd[s] = SideM{1, 0, 0, 0, 0};
-    } else if (p.bc[s] == MM_BC_SPECULAR) {
-      sd[s] = SideM{2, 0, 0, 0, 0};
-    } else {
-      const double Tw = p.wall_T[s], U = p.wall_U[s];
-      const double sgn = (s == 0 || s == 2) ? -1.0 : 1.0;
-      const double rw = s < 2 ? rho * wall_R(u1, Th11, Tw, sgn) : rho * wall_R(u2, Th22, Tw, sgn);
-      sd[s] = SideM{3, rw, s < 2 ? 0.0 : U, s < 2 ? U : 0.0, Tw};
-    }
-  }
-
-  const Upwind ub = upwind_y(g, p, i, j, 2);
-  const Upwind ut = upwind_y(g, p, i, j, 3);
-  const size_t nv = (size_t)nv1 * nv2;
-  const Tg* Gc = Gs + (size_t)cell * nv + k;
-  const Tg* Gb = Gs + (size_t)ub.cell * nv + k;
-  const Tg* Gt = Gs + (size_t)ut.cell * nv + k;
-  const double v1 = g.v1min + (k + 0.5) * g.dv1;
-  const double v1m = g.v1min + (nv1 - 1 - k + 0.5) * g.dv1;  // mirrored v1
-  const double c1 = v1 - u1;
-
-  // upwind v . grad M at (k, l) with the ghost Maxwellians of each side
-  auto side_m = [&](int s, double m0, double va, double vb, double vmir) -> double {
-    const SideM& q = sd[s];
-    if (q.kind == 0) return maxw(q.rho, q.u1, q.u2, q.T, va, vb);
-    if (q.kind == 1) return m0;
-    if (q.kind == 2) return s < 2 ? maxw(rho, u1, u2, T, vmir, vb) : maxw(rho, u1, u2, T, va, vmir);
-    return maxw(q.rho, q.u1, q.u2, q.T, va, vb);
-  };
-  auto mup = [&](int l) -> double {
-    const double v2 = g.v2min + (l + 0.5) * g.dv2;
-    const double v2m = g.v2min + (nv2 - 1 - l + 0.5) * g.dv2;
-    const double m0 = maxw(rho, u1, u2, T, v1, v2);
-    double z = 0.0;
-    if (v1 > 0.0) z += v1 * ((m0 - side_m(0, m0, v1, v2, v1m)) / g.dx);
-    if (v1 < 0.0) z += v1 * ((side_m(1, m0, v1, v2, v1m) - m0) / g.dx);
-    if (v2 > 0.0) z += v2 * ((m0 - side_m(2, m0, v1, v2, v2m)) / g.dy);
-    if (v2 < 0.0) z += v2 * ((side_m(3, m0, v1, v2, v2m) - m0) / g.dy);
-    return z;
-  };
-
-  // pass 1: moments of Z* and of the upwind v.grad M
-  double E0 = 0, E1 = 0, E2 = 0, W0 = 0, W1 = 0, W2 = 0;
-  if (active) {
-    for (int l = r; l < nv2; l += R) {
-      const double v2 = g.v2min + (l + 0.5) * g.dv2;
-      const double c2 = v2 - u2;
-      const double gv = (double)Gc[l * nv1];
-      const bool top = v2 < 0.0;
-      const Upwind& u = top ? ut : ub;
-      const Tg* Gu = top ? Gt : Gb;
-      const int lu = u.mirror ? nv2 - 1 - l : l;
-      const double gu = u.zero ? 0.0 : (double)Gu[lu * nv1];
-      const double z = -fabs(v2) / g.dy * (gu - gv);
-      E0 += z;
-      E1 += c2 * z;
-      E2 += c2 * c2 * z;
-      const double mz = mup(l);
-      W0 += mz;
-      W1 += c2 * mz;
-      W2 += c2 * c2 * mz;
-    }
-  }
-  double S[4] = {E0, c1 * E0, E1, c1 * c1 * E0 + E2};
-  block_sum4(S, red);
-  double Wm[4] = {W0, c1 * W0, W1, c1 * c1 * W0 + W2};
-  block_sum4(Wm, red);
-
-  const double kap = g.dv1 * g.dv2 / (2.0 * kPi * T);
-  auto poly = [&](const double* s, double c2) -> double {
-    const double b0 = 2.0 * s[0] - s[3] * inv2T;
-    const double b1 = s[1] * iT, b2 = s[2] * iT;
-    const double gm = 0.25 * s[3] * iT * iT - s[0] * inv2T;
-    return b0 + b1 * c1 + b2 * c2 + gm * (c1 * c1 + c2 * c2);
-  };
-
-  double H0 = 0, H1 = 0, H2 = 0, H3 = 0;
-  if (active) {
-    Tg* Go = Gout + (size_t)cell * nv + k;
-    for (int l = r; l < nv2; l += R) {
-      const double v2 = g.v2min + (l + 0.5) * g.dv2;
-      const double c2 = v2 - u2;
-      const double gv = (double)Gc[l * nv1];
-      const bool top = v2 < 0.0;
-      const Upwind& u = top ? ut : ub;
-      const Tg* Gu = top ? Gt : Gb;
-      const int lu = u.mirror ? nv2 - 1 - l : l;
-      const double gu = u.zero ? 0.0 : (double)Gu[lu * nv1];
-      const double z = -fabs(v2) / g.dy * (gu - gv);
-      const double m = maxw(rho, u1, u2, T, v1, v2);
-      const double gstar2 = gv + dt * (kap * poly(S, c2) * (m / (rho / (2.0 * kPi * T))) - z);
-      const double mz = mup(l);
-      const double pim = kap * poly(Wm, c2) * (m / (rho / (2.0 * kPi * T)));
-      double gh = -(1.0 / tau) * (mz - pim);
-      if (p.keep_es) {
-        const double quad = Ti11 * c1 * c1 + 2.0 * Ti12 * c1 * c2 + Ti22 * c2 * c2;
-        gh += (KG * exp(-0.5 * quad) - m) / eps;
-      }
-      const double o = om1 * gstar2 + om2 * gh;
-      const Tg os = (Tg)o;
-      Go[l * nv1] = os;
-      const double ov = (double)os;
-      H0 += ov;
-      H1 += c2 * ov;
-      H2 += c2 * c2 * ov;
-      H3 += c2 * c2 * c2 * ov;
-    }
-  }
-  double Hs[4] = {c1 * c1 * c1 * H0, c1 * c1 * H1, c1 * H2, H3};
-  block_sum4(Hs, red);
-  if (t == 0) {
-    const double f = eps * g.dv1 * g.dv2;
-    bool ok = true;
-    for (int m = 0; m < 4; ++m) {
-      Hout[m * nc + cell] = f * Hs[m];
-      ok = ok && isfinite(Hs[m]);
-    }
-    if (!ok) atomicOr(err, ERR_NONFINITE_G);
-  }
+  micro_y_wall_body<Tg>(Gs, Gout, Hout, prim, g, p, dt, eps, R, err, wall_cells[blockIdx.x], sm);
 }
 
 __global__ void k_diag_exp(const double* __restrict__ x, double* __restrict__ yf,
@@ -555,7 +79,7 @@ MicroShape micro_shape(int nv1, int nv2) {
   double best = -1.0;
   for (int R = 1; R <= 32; ++R) {
     const int thr = R * nv1;
-    if (thr > kMaxThreads) break;
+    if (thr > micro_body::kMaxThreads) break;
     const int thr32 = (thr + 31) / 32 * 32;
     const int passes = (nv2 + R - 1) / R;
     const double u = (double)thr / thr32 * ((double)nv2 / (R * passes));
@@ -566,8 +90,8 @@ MicroShape micro_shape(int nv1, int nv2) {
     }
     if (R >= nv2) break;
   }
-  ms.smem_x = sizeof(double) * (kRed + 4 * (size_t)nv2);
-  ms.smem_y = sizeof(double) * (kRed + kYTables * (size_t)nv2);
+  ms.smem_x = sizeof(double) * (micro_body::kRed + 4 * (size_t)nv2);
+  ms.smem_y = sizeof(double) * (micro_body::kRed + micro_body::kYTables * (size_t)nv2);
   return ms;
 }
 
@@ -594,7 +118,7 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
                          double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s) {
   if (n_wall <= 0) return;
-  k_micro_y_wall<Tg><<<n_wall, ms.threads, sizeof(double) * kRed, s>>>(
+  k_micro_y_wall<Tg><<<n_wall, ms.threads, sizeof(double) * micro_body::kRed, s>>>(
       Gs, Gout, H, prim, wall_cells, g, p, dt, eps, ms.R, err);
 }
 
