@@ -668,8 +668,11 @@ static int check_args(const orc_grid* g, const orc_params* p) {
 /* ------------------------------------------------------------------------------------------ */
 /* one full time step, Section 5.3 (micro) then Section 5.4 (macro)                             */
 /* ------------------------------------------------------------------------------------------ */
-int orc_step(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H, double dt,
-             double eps, int nsteps) {
+/* One or more steps; with closure != NULL, cells with closure[c] != 0 take g^{n+1} = Ghat and
+ * the heat flux Hcl[m][c] in place of the relaxed micro solution and its moments. */
+static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
+                     double dt, double eps, int nsteps, const unsigned char* closure,
+                     const double* Hcl) {
   if (check_args(g, p) || !Q || !G || !H || !(dt > 0.0) || !(eps > 0.0) || nsteps < 0) return 1;
   const int nx = g->nx, ny = g->ny, nv1 = g->nv1, nv2 = g->nv2, nv = nv1 * nv2;
   const int nc = nx * ny;
@@ -713,6 +716,12 @@ int orc_step(const orc_grid* g, const orc_params* p, double* Q, double* G, doubl
         int i = c % nx, j = c / nx;
         const prim_t* pc = &P[c];
         ghat_cell(g, p, P, Mc, i, j, eps, gh, tmp);
+        if (closure && closure[c]) {
+          for (int l = 0; l < nv2; ++l)
+            for (int k = 0; k < nv1; ++k) G[gidx(g, i, j, k, l)] = gh[l * nv1 + k];
+          for (int m = 0; m < 4; ++m) H[m * nc + c] = Hcl[m * nc + c];
+          continue;
+        }
         double w1 = eps / (eps + dt * pc->tau);
         double w2 = dt * pc->tau / (eps + dt * pc->tau);
         double h111 = 0, h112 = 0, h122 = 0, h222 = 0;
@@ -804,6 +813,17 @@ int orc_step(const orc_grid* g, const orc_params* p, double* Q, double* G, doubl
   }
   free(P); free(Mc); free(Gs); free(Gss); free(Q1); free(Q2);
   return status;
+}
+
+int orc_step(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H, double dt,
+             double eps, int nsteps) {
+  return step_impl(g, p, Q, G, H, dt, eps, nsteps, NULL, NULL);
+}
+
+int orc_step_closure(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
+                     double dt, double eps, const unsigned char* closure, const double* Hcl) {
+  if (!closure || !Hcl) return 1;
+  return step_impl(g, p, Q, G, H, dt, eps, 1, closure, Hcl);
 }
 
 int orc_ghat(const orc_grid* g, const orc_params* p, const double* Q, double eps, double* Ghat) {
