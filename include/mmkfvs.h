@@ -170,6 +170,56 @@ mm_status mm_batch_get_g(mm_batch* b, int q, double* G_host);
 const char* mm_batch_last_error(const mm_batch* b);
 void mm_batch_destroy(mm_batch* b);
 
+/* ---- learned heat-flux closure ---------------------------------------------------------------
+ * The paper has no learned closure; this is the library's extension.  An MLP with MM_MLP_IN
+ * inputs, two GELU hidden layers of MM_MLP_HIDDEN and MM_MLP_OUT outputs, BF16 weights, FP32
+ * accumulation, maps local macro features of a cell to y = (H - H_CE) / (eps rho T^{3/2}), the
+ * dimensionless part of the heat-flux tensor of Eq. (5-99) beyond its Chapman-Enskog value H_CE
+ * (the moments of the transport part of Ghat, Eq. 5-97).  Parameters are one flat FP32 vector of
+ * MM_MLP_NPARAM values [W1 (64x38, row-major by output), b1, W2 (64x64), b2, W3 (4x64), b3];
+ * the normalisation vector holds [input mean (38), input 1/std (38), output mean (4), output
+ * std (4)].  Feature and target arrays are FP32 device arrays, sample-major [n][38], [n][4]. */
+#define MM_MLP_IN 38
+#define MM_MLP_HIDDEN 64
+#define MM_MLP_OUT 4
+#define MM_MLP_NPARAM 6916
+typedef struct mm_mlp mm_mlp;
+mm_status mm_mlp_create(void* cuda_stream, mm_mlp** out);
+/* Load FP32 parameters (rounded to BF16 for the kernels) and normalisation; resets Adam. */
+mm_status mm_mlp_set_params(mm_mlp* m, const float* params_host, const float* norm_host);
+/* FP32 master parameters and/or the BF16 parameters the kernels use (as FP32 values). */
+mm_status mm_mlp_get_params(mm_mlp* m, float* params_host, float* params_bf16_as_f32_host);
+/* Inference: Y[n][4] (de-standardised) from X[n][38]; asynchronous. */
+mm_status mm_mlp_forward(mm_mlp* m, const float* X_dev, float* Y_dev, int n);
+/* Gradient of the mean squared error of the standardised outputs with respect to the
+ * parameters (BF16 weights, FP32 accumulation), and the loss; synchronous if outputs given. */
+mm_status mm_mlp_grad(mm_mlp* m, const float* X_dev, const float* T_dev, int n, float* grad_host,
+                      float* loss_host);
+/* One Adam step (beta 0.9, 0.999) on a mini-batch; FP32 master weights, BF16 copies refreshed. */
+mm_status mm_mlp_train_step(mm_mlp* m, const float* X_dev, const float* T_dev, int n, float lr,
+                            float* loss_host);
+const char* mm_mlp_last_error(const mm_mlp* m);
+void mm_mlp_destroy(mm_mlp* m);
+
+/* Hybrid stepping with the closure (FP64 contexts).  While a network is set, every mm_step
+ * computes per cell the features of Q^n, the network's y and the indicator max_m |y_m|; a cell
+ * that touches no non-periodic boundary and whose indicator is <= threshold takes the closure:
+ * g^{n+1} = Ghat (the asymptotic-preserving limit of Eq. 5-98) and H = H_CE + eps rho T^{3/2} y,
+ * and skips the micro sweeps; every other cell takes the full micro update.  The context keeps
+ * the pointer: the network must outlive its use.  m = NULL switches the closure off.  Resets
+ * the statistics.  FP32-g contexts: MM_ERR_INVALID_ARG. */
+mm_status mm_set_closure(mm_ctx* c, const mm_mlp* m, double threshold);
+/* Features X_dev [nc][38] (FP32) of the current state and aux_dev [5][ny][nx] (FP64: H_CE of
+ * the four components, then the scale eps rho T^{3/2}); asynchronous. */
+mm_status mm_closure_features(mm_ctx* c, double dt, double eps, float* X_dev, double* aux_dev);
+/* Training data: the features of Q^n into X_dev [nc][38], then one plain (full micro) step, then
+ * the targets y = (H - H_CE) / (eps rho T^{3/2}) into Y_dev [nc][4]; asynchronous. */
+mm_status mm_closure_collect(mm_ctx* c, double dt, double eps, float* X_dev, float* Y_dev);
+/* Closure flags of the last hybrid step, [ny][nx] bytes (1 = closure). */
+mm_status mm_closure_flags(mm_ctx* c, unsigned char* flags_host);
+/* Closure cells summed over the hybrid steps since mm_set_closure, and cells x those steps. */
+mm_status mm_closure_stats(mm_ctx* c, long long* closure_cells, long long* cell_steps);
+
 /* Diagnostic: evaluate the table-driven exponential used by the phase-space kernels (Tang's
  * method, see the micro kernels) and the CUDA library exp on n FP64 device values x_dev, into
  * caller-owned device arrays; synchronises cuda_stream.  Used to test the kernels' exp against

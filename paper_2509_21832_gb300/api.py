@@ -42,7 +42,13 @@ EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device"
            "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp",
            "mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
            "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments", "mm_batch_get_g",
-           "mm_batch_last_error", "mm_batch_destroy"]
+           "mm_batch_last_error", "mm_batch_destroy",
+           "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_forward",
+           "mm_mlp_grad", "mm_mlp_train_step", "mm_mlp_last_error", "mm_mlp_destroy",
+           "mm_set_closure", "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
+           "mm_closure_stats"]
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 38, 64, 4, 6916
 
 _lib = None
 
@@ -106,9 +112,29 @@ def load(build_if_needed: bool = True):
     L.mm_step_static_scratch.argtypes = [G, P, vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, vp, ctypes.c_char_p, ctypes.c_size_t]
     L.mm_step_static_scratch.restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.mm_mlp_create.argtypes = [vp, ctypes.POINTER(vp)]
+    L.mm_mlp_set_params.argtypes = [vp, fp, fp]
+    L.mm_mlp_get_params.argtypes = [vp, fp, fp]
+    L.mm_mlp_forward.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.mm_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int, fp, fp]
+    L.mm_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, fp]
+    L.mm_mlp_last_error.argtypes = [vp]
+    L.mm_mlp_last_error.restype = ctypes.c_char_p
+    L.mm_mlp_destroy.argtypes = [vp]
+    L.mm_mlp_destroy.restype = None
+    L.mm_set_closure.argtypes = [vp, vp, ctypes.c_double]
+    L.mm_closure_features.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp]
+    L.mm_closure_collect.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp]
+    L.mm_closure_flags.argtypes = [vp, vp]
+    L.mm_closure_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)]
     for name in ["mm_create", "mm_set_state", "mm_set_state_device", "mm_step", "mm_sync",
                  "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_set_timing",
-                 "mm_get_timing"]:
+                 "mm_get_timing", "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params",
+                 "mm_mlp_forward", "mm_mlp_grad", "mm_mlp_train_step", "mm_set_closure",
+                 "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
+                 "mm_closure_stats"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -294,6 +320,117 @@ class Solver:
 
     def last_error(self):
         return self.L.mm_last_error(self.ctx).decode()
+
+    # ---- learned closure -------------------------------------------------------------------
+    def set_closure(self, mlp, threshold):
+        """Hybrid stepping with the network mlp (an MLP, or None to switch it off)."""
+        self._closure_mlp = mlp  # the context keeps the pointer: keep the network alive
+        h = None if mlp is None else mlp.h
+        _check(self.ctx, self.L.mm_set_closure(self.ctx, h, float(threshold)), "mm_set_closure")
+
+    def closure_features(self, dt, eps, X_dev, aux_dev):
+        """Features [nc][38] (float32 CUDA tensor) and [5][ny][nx] (float64: H_CE, scale)."""
+        _check(self.ctx, self.L.mm_closure_features(self.ctx, float(dt), float(eps),
+                                                   _f32_ptr(X_dev, self.ncell * MLP_IN),
+                                                   _dev_ptr(aux_dev, 5 * self.ncell)),
+               "mm_closure_features")
+
+    def closure_collect(self, dt, eps, X_dev, Y_dev):
+        """Features of Q^n, one plain step, targets (H - H_CE) / scale; float32 CUDA tensors."""
+        _check(self.ctx, self.L.mm_closure_collect(self.ctx, float(dt), float(eps),
+                                                  _f32_ptr(X_dev, self.ncell * MLP_IN),
+                                                  _f32_ptr(Y_dev, self.ncell * MLP_OUT)),
+               "mm_closure_collect")
+
+    def closure_flags(self):
+        f = np.zeros((self.grid.ny, self.grid.nx), dtype=np.uint8)
+        _check(self.ctx, self.L.mm_closure_flags(self.ctx, f.ctypes.data), "mm_closure_flags")
+        return f
+
+    def closure_stats(self):
+        a, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        _check(self.ctx, self.L.mm_closure_stats(self.ctx, ctypes.byref(a), ctypes.byref(b)),
+               "mm_closure_stats")
+        return a.value, b.value
+
+
+def _f32_ptr(t, n):
+    assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4
+    assert t.is_contiguous() and t.numel() == n, (t.numel(), n)
+    return t.data_ptr()
+
+
+def _host_f32(a, n):
+    assert isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    assert a.size == n, (a.size, n)
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class MLP:
+    """The closure network (mm_mlp_*): BF16 weights, FP32 accumulation, trained on the GPU."""
+
+    def __init__(self, params=None, norm=None, stream=0):
+        self.L = load()
+        self.h = ctypes.c_void_p()
+        st = self.L.mm_mlp_create(ctypes.c_void_p(int(stream)), ctypes.byref(self.h))
+        if st != MM_OK:
+            raise MMError(st, "mm_mlp_create")
+        if params is not None:
+            self.set_params(params, norm)
+
+    def _check(self, st, what):
+        if st != MM_OK:
+            raise MMError(st, "%s: %s" % (what, self.L.mm_mlp_last_error(self.h).decode()))
+
+    def close(self):
+        if self.h:
+            self.L.mm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params, norm):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        n = np.ascontiguousarray(norm, dtype=np.float32)
+        self._check(self.L.mm_mlp_set_params(self.h, _host_f32(p, MLP_NPARAM),
+                                             _host_f32(n, 2 * MLP_IN + 2 * MLP_OUT)),
+                    "mm_mlp_set_params")
+
+    def get_params(self):
+        """(FP32 master parameters, the BF16 parameters as FP32)."""
+        a = np.zeros(MLP_NPARAM, dtype=np.float32)
+        b = np.zeros(MLP_NPARAM, dtype=np.float32)
+        self._check(self.L.mm_mlp_get_params(self.h, _host_f32(a, MLP_NPARAM),
+                                             _host_f32(b, MLP_NPARAM)), "mm_mlp_get_params")
+        return a, b
+
+    def forward(self, X_dev, Y_dev):
+        n = X_dev.shape[0]
+        self._check(self.L.mm_mlp_forward(self.h, _f32_ptr(X_dev, n * MLP_IN),
+                                          _f32_ptr(Y_dev, n * MLP_OUT), n), "mm_mlp_forward")
+
+    def grad(self, X_dev, T_dev):
+        """(loss, gradient) of the mean squared error of the standardised outputs."""
+        n = X_dev.shape[0]
+        g = np.zeros(MLP_NPARAM, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        self._check(self.L.mm_mlp_grad(self.h, _f32_ptr(X_dev, n * MLP_IN),
+                                       _f32_ptr(T_dev, n * MLP_OUT), n, _host_f32(g, MLP_NPARAM),
+                                       _host_f32(loss, 1)), "mm_mlp_grad")
+        return float(loss[0]), g
+
+    def train_step(self, X_dev, T_dev, lr, want_loss=False):
+        n = X_dev.shape[0]
+        loss = np.zeros(1, dtype=np.float32)
+        self._check(self.L.mm_mlp_train_step(self.h, _f32_ptr(X_dev, n * MLP_IN),
+                                             _f32_ptr(T_dev, n * MLP_OUT), n, float(lr),
+                                             _host_f32(loss, 1) if want_loss else None),
+                    "mm_mlp_train_step")
+        return float(loss[0]) if want_loss else None
 
 
 class BatchSolver:

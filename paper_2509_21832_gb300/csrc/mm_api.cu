@@ -15,12 +15,14 @@ using namespace mmk;
 
 namespace {
 
-const char* const kKernelNames[] = {"prims",    "micro_x",  "micro_y", "micro_y_wall", "macro_x1",
-                                    "macro_x2", "macro_y", "h_unpack", "micro_fused"};
-constexpr int kNumKernels = 9;
+const char* const kKernelNames[] = {
+    "prims",    "micro_x",          "micro_y",   "micro_y_wall",   "macro_x1",
+    "macro_x2", "macro_y",          "h_unpack",  "micro_fused",    "closure_features",
+    "mlp_infer", "closure_decide",  "closure_lists", "closure_ghat"};
+constexpr int kNumKernels = 14;
 enum {
   T_PRIMS = 0, T_MICRO_X, T_MICRO_Y, T_MICRO_YW, T_MACRO_X1, T_MACRO_X2, T_MACRO_Y, T_HUNPACK,
-  T_MICRO_FUSED
+  T_MICRO_FUSED, T_CL_FEATURES, T_MLP, T_CL_DECIDE, T_CL_LISTS, T_CL_GHAT
 };
 
 struct TimedLaunch {
@@ -56,6 +58,18 @@ struct mm_ctx {
   int n_wall = 0;
   bool have_state = false;
   std::string last_error;
+  // learned closure (FP64 contexts): network, threshold and per-cell buffers
+  const mm_mlp* mlp = nullptr;
+  double closure_thr = 0.0;
+  float* cX = nullptr;                   // features [nc][38]
+  float* cY = nullptr;                   // network outputs [nc][4]
+  double* caux = nullptr;                // H_CE [4][nc], scale [nc]
+  unsigned char* cflags = nullptr;       // 1: closure cell in the last hybrid step
+  int* clists = nullptr;                 // x-sweep, y-sweep and closure cell lists [3][nc]
+  int* ccounts = nullptr;                // their lengths [3]
+  unsigned long long* cstat = nullptr;   // closure cells summed over hybrid steps
+  long long closure_steps = 0;
+  int blocks_x = 0, blocks_y = 0, blocks_g = 0;
   bool timing = false;
   std::vector<TimedLaunch> pending;
   std::vector<cudaEvent_t> free_events;
@@ -171,7 +185,7 @@ mm_status check_device_errors(mm_ctx* c) {
 }
 
 template <typename Tg>
-void enqueue_step(mm_ctx* c, double dt, double eps) {
+void enqueue_plain(mm_ctx* c, double dt, double eps) {
   Tg* G = static_cast<Tg*>(c->G);
   Tg* Gs = static_cast<Tg*>(c->Gs);
   const KGrid& g = c->kg;
@@ -203,6 +217,82 @@ void enqueue_step(mm_ctx* c, double dt, double eps) {
   timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
   timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
   timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
+}
+
+// Hybrid step with the learned closure (FP64): features and network on every cell, then the
+// micro sweeps on the micro cells (x sweep also on their y neighbours), Ghat on closure cells.
+void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
+  double* G = static_cast<double*>(c->G);
+  double* Gs = static_cast<double*>(c->Gs);
+  const KGrid& g = c->kg;
+  const KParams& p = c->kp;
+  cudaStream_t s = c->stream;
+  const int nc = (int)c->ncell;
+  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
+  timed(c, T_CL_FEATURES, [&] { launch_closure_features(c->Q, g, p, eps, dt, c->cX, c->caux, s); });
+  timed(c, T_MLP, [&] { mlp_forward_async(c->mlp, c->cX, c->cY, nc, s); });
+  timed(c, T_CL_DECIDE, [&] {
+    launch_closure_decide(c->cY, c->caux, c->closure_thr, g, p, c->cflags, c->H, c->cstat, s);
+  });
+  timed(c, T_CL_LISTS, [&] { launch_closure_lists(c->cflags, g, p, c->clists, c->ccounts, s); });
+  timed(c, T_MICRO_X, [&] {
+    launch_micro_x_list<double>(G, Gs, c->prim, g, p, dt, c->ms, c->clists, c->ccounts,
+                                c->blocks_x, s);
+  });
+  timed(c, T_MICRO_Y, [&] {
+    launch_micro_y_list<double>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err,
+                                c->clists + nc, c->ccounts + 1, c->blocks_y, s);
+  });
+  if (c->n_wall > 0)
+    timed(c, T_MICRO_YW, [&] {
+      launch_micro_y_wall<double>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
+                                  c->ms, c->err, s);
+    });
+  timed(c, T_CL_GHAT, [&] {
+    launch_closure_ghat(G, c->prim, g, dt, eps, c->ms, c->clists + 2 * nc, c->ccounts + 2,
+                        c->blocks_g, s);
+  });
+  timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
+  timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
+  timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
+  c->closure_steps += 1;
+}
+
+void enqueue_step(mm_ctx* c, double dt, double eps) {
+  if (c->fp32) enqueue_plain<float>(c, dt, eps);
+  else if (c->mlp) enqueue_hybrid(c, dt, eps);
+  else enqueue_plain<double>(c, dt, eps);
+}
+
+// Buffers of the closure, allocated on first use.
+mm_status ensure_closure(mm_ctx* c) {
+  if (c->caux) return MM_OK;
+  const size_t nc = c->ncell;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  alloc((void**)&c->cX, nc * MM_MLP_IN * sizeof(float));
+  alloc((void**)&c->cY, nc * MM_MLP_OUT * sizeof(float));
+  alloc((void**)&c->caux, 5 * nc * sizeof(double));
+  alloc((void**)&c->cflags, nc);
+  alloc((void**)&c->clists, 3 * nc * sizeof(int));
+  alloc((void**)&c->ccounts, 3 * sizeof(int));
+  alloc((void**)&c->cstat, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cstat, 0, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cflags, 0, nc, c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(c->cX); cudaFree(c->cY); cudaFree(c->caux); cudaFree(c->cflags);
+    cudaFree(c->clists); cudaFree(c->ccounts); cudaFree(c->cstat);
+    c->cX = c->cY = nullptr; c->caux = nullptr; c->cflags = nullptr; c->clists = c->ccounts = nullptr;
+    c->cstat = nullptr;
+    return e == cudaErrorMemoryAllocation ? fail(c, MM_ERR_OOM, "closure buffers")
+                                          : cuda_fail(c, e, "closure buffers");
+  }
+  c->blocks_x = micro_list_blocks(c->ms, false);
+  c->blocks_y = micro_list_blocks(c->ms, true);
+  c->blocks_g = closure_ghat_blocks(c->ms);
+  return MM_OK;
 }
 
 // Copy an FP64 array of n elements into the context's G (FP64 or FP32), staging through Gs.
@@ -397,10 +487,7 @@ mm_status mm_step(mm_ctx* c, double dt, double eps, int nsteps) {
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, MM_ERR_INVALID_ARG, "eps must be > 0");
   if (nsteps < 0) return fail(c, MM_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (!c->have_state) return fail(c, MM_ERR_STATE, "mm_step before mm_set_state");
-  for (int n = 0; n < nsteps; ++n) {
-    if (c->fp32) enqueue_step<float>(c, dt, eps);
-    else enqueue_step<double>(c, dt, eps);
-  }
+  for (int n = 0; n < nsteps; ++n) enqueue_step(c, dt, eps);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   return MM_OK;
@@ -468,6 +555,72 @@ double mm_dt_for_cfl(const mm_grid* g, double cfl, double t_final, int form, int
   return dt;
 }
 
+mm_status mm_set_closure(mm_ctx* c, const mm_mlp* m, double threshold) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!m) {
+    c->mlp = nullptr;
+    return MM_OK;
+  }
+  if (c->fp32) return fail(c, MM_ERR_INVALID_ARG, "the closure needs an FP64 context");
+  if (!(threshold >= 0.0) || !std::isfinite(threshold))
+    return fail(c, MM_ERR_INVALID_ARG, "threshold must be finite and >= 0");
+  mm_status st = ensure_closure(c);
+  if (st != MM_OK) return st;
+  cudaError_t e = cudaMemsetAsync(c->cstat, 0, sizeof(unsigned long long), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reset closure statistics");
+  c->mlp = m;
+  c->closure_thr = threshold;
+  c->closure_steps = 0;
+  return MM_OK;
+}
+
+mm_status mm_closure_features(mm_ctx* c, double dt, double eps, float* X_dev, double* aux_dev) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!X_dev || !aux_dev) return fail(c, MM_ERR_INVALID_ARG, "null output");
+  if (!(dt > 0.0) || !(eps > 0.0)) return fail(c, MM_ERR_INVALID_ARG, "dt and eps must be > 0");
+  if (!c->have_state) return fail(c, MM_ERR_STATE, "no state set");
+  launch_closure_features(c->Q, c->kg, c->kp, eps, dt, X_dev, aux_dev, c->stream);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "closure features");
+}
+
+mm_status mm_closure_collect(mm_ctx* c, double dt, double eps, float* X_dev, float* Y_dev) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!X_dev || !Y_dev) return fail(c, MM_ERR_INVALID_ARG, "null output");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !(eps > 0.0) || !std::isfinite(eps))
+    return fail(c, MM_ERR_INVALID_ARG, "dt and eps must be finite and > 0");
+  if (!c->have_state) return fail(c, MM_ERR_STATE, "no state set");
+  mm_status st = ensure_closure(c);
+  if (st != MM_OK) return st;
+  launch_closure_features(c->Q, c->kg, c->kp, eps, dt, X_dev, c->caux, c->stream);
+  if (c->fp32) enqueue_plain<float>(c, dt, eps);
+  else enqueue_plain<double>(c, dt, eps);
+  launch_closure_targets(c->H, c->caux, Y_dev, c->kg, c->stream);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "closure collect");
+}
+
+mm_status mm_closure_flags(mm_ctx* c, unsigned char* flags_host) {
+  if (!c || !flags_host) return MM_ERR_INVALID_ARG;
+  if (!c->cflags) return fail(c, MM_ERR_STATE, "no closure step has run");
+  cudaError_t e = cudaMemcpyAsync(flags_host, c->cflags, c->ncell, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "copy closure flags");
+}
+
+mm_status mm_closure_stats(mm_ctx* c, long long* closure_cells, long long* cell_steps) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  unsigned long long h = 0;
+  if (c->cstat) {
+    cudaError_t e = cudaMemcpyAsync(&h, c->cstat, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "closure statistics");
+  }
+  if (closure_cells) *closure_cells = (long long)h;
+  if (cell_steps) *cell_steps = c->closure_steps * (long long)c->ncell;
+  return MM_OK;
+}
+
 const char* mm_last_error(const mm_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
 
 mm_status mm_set_timing(mm_ctx* c, int enable) {
@@ -516,6 +669,13 @@ void mm_destroy(mm_ctx* c) {
   cudaFree(c->primf);
   cudaFree(c->err);
   cudaFree(c->wall_cells);
+  cudaFree(c->cX);
+  cudaFree(c->cY);
+  cudaFree(c->caux);
+  cudaFree(c->cflags);
+  cudaFree(c->clists);
+  cudaFree(c->ccounts);
+  cudaFree(c->cstat);
   delete c;
 }
 

@@ -1,0 +1,295 @@
+// Learned heat-flux closure on the FP64 path (an extension of the library; the paper has no
+// counterpart).  Per step, from Q^n:
+//  - k_closure_features: 38 features of every cell (the 3x3 stencil of rho, u, T relative to the
+//    cell, the pressure anisotropy, u / sqrt T, log10 eps and the relaxation weight omega1), the
+//    Chapman-Enskog heat flux H_CE (closed-form third central moments of the transport part of
+//    Ghat, Eq. 5-97: H111 = -3 eps p T_x / tau, H112 = -eps p T_y / tau, H122 = -eps p T_x / tau,
+//    H222 = -3 eps p T_y / tau with the discrete gradient of Eq. 5-97more) and the scale
+//    s = eps rho T^{3/2};
+//  - the network (mm_mlp.cu) predicts y = (H - H_CE) / s;
+//  - k_closure_decide: a cell takes the closure when max_m |y_m| <= threshold and it touches no
+//    non-periodic boundary; its heat flux becomes H_CE + s y;
+//  - k_closure_lists: work lists of the micro kernels: the y sweep runs on micro cells, the x sweep
+//    on micro cells and their y neighbours (whose G* the y sweep reads), the Ghat kernel on
+//    closure cells;
+//  - k_closure_ghat: g^{n+1} = Ghat in closure cells (the asymptotic-preserving limit of the
+//    relaxation, Eq. 5-98 with omega1 = 0), so that neighbouring micro cells read a defined g.
+// Collection of training data uses k_closure_features before and k_closure_targets after a
+// plain step.
+#include <cmath>
+
+#include "mm_body_macro.cuh"
+#include "mm_body_micro.cuh"
+
+namespace mmk {
+
+namespace {
+
+constexpr int kF = MM_MLP_IN;
+constexpr int kYo = MM_MLP_OUT;
+
+// Neighbour index along one axis and whether it is the mirror image at a specular wall.
+__device__ __forceinline__ int nb_index(int i, int d, int n, int bclo, int bchi, bool& mirror) {
+  const int k = i + d;
+  mirror = false;
+  if (k >= 0 && k < n) return k;
+  const int bc = k < 0 ? bclo : bchi;
+  if (bc == MM_BC_PERIODIC) return (k + n) % n;
+  mirror = bc == MM_BC_SPECULAR;
+  return i;
+}
+
+__device__ __forceinline__ bool boundary_cell(const KGrid& g, const KParams& p, int i, int j) {
+  return (i == 0 && p.bc[0] != MM_BC_PERIODIC) || (i == g.nx - 1 && p.bc[1] != MM_BC_PERIODIC) ||
+         (j == 0 && p.bc[2] != MM_BC_PERIODIC) || (j == g.ny - 1 && p.bc[3] != MM_BC_PERIODIC);
+}
+
+__global__ void k_closure_features(const double* __restrict__ Q, KGrid g, KParams p, double eps,
+                                   double dt, float* __restrict__ X, double* __restrict__ aux) {
+  const int nc = g.nx * g.ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int i = c % g.nx, j = c / g.nx;
+  const double rho = Q[c];
+  const double ir = 1.0 / rho;
+  const double u1 = Q[nc + c] * ir, u2 = Q[2 * nc + c] * ir;
+  const double P11 = Q[3 * nc + c] - rho * u1 * u1;
+  const double P12 = Q[4 * nc + c] - rho * u1 * u2;
+  const double P22 = Q[5 * nc + c] - rho * u2 * u2;
+  const double T = (P11 + P22) * (0.5 * ir);
+  const double iT = 1.0 / T;
+  const double sT = sqrt(T);
+  const double isT = 1.0 / sT;
+  const double tau = macro_body::tau_of(p, rho, T);
+  float* x = X + (size_t)c * kF;
+  int f = 0;
+  double TL = T, TR = T, TB = T, TT = T;
+  for (int dj = -1; dj <= 1; ++dj) {
+    bool my;
+    const int nj = nb_index(j, dj, g.ny, p.bc[2], p.bc[3], my);
+    for (int di = -1; di <= 1; ++di) {
+      if (di == 0 && dj == 0) continue;
+      bool mx;
+      const int ni = nb_index(i, di, g.nx, p.bc[0], p.bc[1], mx);
+      const int n = nj * g.nx + ni;
+      double a1, a2, Tn;
+      macro_body::uT_of(Q, nc, n, a1, a2, Tn);
+      if (mx) a1 = -a1;
+      if (my) a2 = -a2;
+      x[f++] = (float)(Q[n] * ir - 1.0);
+      x[f++] = (float)((a1 - u1) * isT);
+      x[f++] = (float)((a2 - u2) * isT);
+      x[f++] = (float)(Tn * iT - 1.0);
+      if (dj == 0) (di < 0 ? TL : TR) = Tn;
+      if (di == 0) (dj < 0 ? TB : TT) = Tn;
+    }
+  }
+  x[32] = (float)((P11 - P22) * (0.5 * ir) * iT);
+  x[33] = (float)(P12 * ir * iT);
+  x[34] = (float)(u1 * isT);
+  x[35] = (float)(u2 * isT);
+  x[36] = (float)log10(eps);
+  x[37] = (float)(eps / (eps + dt * tau));
+  // Chapman-Enskog heat flux with the discrete temperature gradient of Eq. (5-97more)
+  const double Tx = (0.5 * (TR + T) - 0.5 * (T + TL)) * g.idx;
+  const double Ty = (0.5 * (TT + T) - 0.5 * (T + TB)) * g.idy;
+  const double ep = eps * rho * T / tau;
+  aux[c] = -3.0 * ep * Tx;
+  aux[nc + c] = -ep * Ty;
+  aux[2 * nc + c] = -ep * Tx;
+  aux[3 * nc + c] = -3.0 * ep * Ty;
+  aux[4 * nc + c] = eps * rho * T * sT;
+}
+
+__global__ void k_closure_targets(const double* __restrict__ H, const double* __restrict__ aux,
+                                  float* __restrict__ Y, int nc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double is = 1.0 / aux[4 * nc + c];
+  for (int m = 0; m < kYo; ++m) Y[(size_t)c * kYo + m] = (float)((H[m * nc + c] - aux[m * nc + c]) * is);
+}
+
+__global__ void k_closure_decide(const float* __restrict__ Y, const double* __restrict__ aux,
+                                 float thr, KGrid g, KParams p, unsigned char* __restrict__ flags,
+                                 double* __restrict__ H, unsigned long long* __restrict__ nclosure) {
+  const int nc = g.nx * g.ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  bool cl = false;
+  if (c < nc) {
+    const int i = c % g.nx, j = c / g.nx;
+    float y[kYo];
+    float ind = 0.f;
+    for (int m = 0; m < kYo; ++m) {
+      y[m] = Y[(size_t)c * kYo + m];
+      ind = fmaxf(ind, fabsf(y[m]));
+    }
+    cl = !boundary_cell(g, p, i, j) && ind <= thr;  // NaN fails the test: micro solve
+    flags[c] = cl ? 1 : 0;
+    if (cl) {
+      const double s = aux[4 * nc + c];
+      for (int m = 0; m < kYo; ++m) H[m * nc + c] = fma(s, (double)y[m], aux[m * nc + c]);
+    }
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, cl);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(nclosure, (unsigned long long)__popc(b));
+}
+
+// Append the cells with pred set to list (warp-aggregated; the order within the list does not
+// matter: every cell's update is independent of the others').
+__device__ __forceinline__ void append(bool pred, int c, int* list, int* count) {
+  const unsigned full = 0xffffffffu;
+  const unsigned b = __ballot_sync(full, pred);
+  if (!b) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(b) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(b));
+  base = __shfl_sync(full, base, leader);
+  if (pred) list[base + __popc(b & ((1u << lane) - 1u))] = c;
+}
+
+__global__ void k_closure_lists(const unsigned char* __restrict__ flags, KGrid g, KParams p,
+                                int* __restrict__ xlist, int* __restrict__ ylist,
+                                int* __restrict__ clist, int* __restrict__ counts) {
+  const int nc = g.nx * g.ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  bool inx = false, iny = false, inc = false;
+  if (c < nc) {
+    const int i = c % g.nx, j = c / g.nx;
+    const bool micro = flags[c] == 0;
+    bool nb_micro = false;
+    for (int s = 2; s <= 3; ++s) {
+      int nj = s == 2 ? j - 1 : j + 1;
+      if (nj < 0 || nj >= g.ny) {
+        if (p.bc[s] != MM_BC_PERIODIC) continue;
+        nj = (nj + g.ny) % g.ny;
+      }
+      nb_micro = nb_micro || flags[nj * g.nx + i] == 0;
+    }
+    inx = micro || nb_micro;
+    iny = micro && !micro_body::diffuse_wall_cell(g, p, i, j);
+    inc = !micro;
+  }
+  append(inx, c, xlist, counts);
+  append(iny, c, ylist, counts + 1);
+  append(inc, c, clist, counts + 2);
+}
+
+// g^{n+1} = Ghat of Eq. (5-97) in the cells of clist, from the per-cell coefficients of the prims
+// kernel (stored there times omega2, hence the factor 1/omega2 = (eps + dt tau) / (dt tau)):
+// Ghat = (1/om2) [ -(p0 + p1 c2 + p2 c2^2 + p3 c2^3 + om2 mu / eps) e1 e2 + om2 KG / eps e^{-c.Tcal^{-1}c/2} ].
+// Thread t owns v1 index k = t % nv1 and rows l = t / nv1 + m R, as in the micro kernels.
+__global__ void __launch_bounds__(512, 1)
+    k_closure_ghat(double* __restrict__ G, const double* __restrict__ prim, KGrid g, double dt,
+                   double eps, int R, const int* __restrict__ clist, const int* __restrict__ count) {
+  extern __shared__ double sm[];
+  const int nv1 = g.nv1, nv2 = g.nv2;
+  const int nc = g.nx * g.ny;
+  double* e2t = sm;
+  double* E1t = sm + nv2;
+  double* E2t = sm + 2 * nv2;
+  double* E3t = sm + 3 * nv2;
+  double* g2t = sm + 4 * nv2;
+  const int t = threadIdx.x;
+  const int k = t % nv1, r = t / nv1;
+  const bool active = r < R;
+  const int n = *count;
+  const size_t nv = (size_t)nv1 * nv2;
+  for (int q = blockIdx.x; q < n; q += gridDim.x) {
+    const int cell = clist[q];
+    const double u1 = prim[P_U1 * nc + cell], u2 = prim[P_U2 * nc + cell];
+    const double inv2T = prim[P_INV2T * nc + cell];
+    const double Ti11 = prim[P_TI11 * nc + cell], Ti12 = prim[P_TI12 * nc + cell];
+    const double Ti22 = prim[P_TI22 * nc + cell];
+    const double gam0 = prim[P_GAM0 * nc + cell], ome = prim[P_OME * nc + cell];
+    const double dtt = dt * prim[P_TAU * nc + cell];
+    const double iom2 = (eps + dtt) / dtt;
+    for (int l = t; l < nv2; l += blockDim.x) {
+      const double c2 = fma(l + 0.5, g.dv2, g.v2min) - u2;
+      const double qq = c2 * c2;
+      const double e2 = expd(-qq * inv2T);
+      e2t[l] = e2;
+      E1t[l] = e2 * c2;
+      E2t[l] = e2 * qq;
+      E3t[l] = e2 * qq * c2;
+      g2t[l] = expd(-0.5 * Ti22 * qq);
+    }
+    const double c1 = fma(k + 0.5, g.dv1, g.v1min) - u1;
+    const double c1q = c1 * c1;
+    const double w01 = prim[P_W01 * nc + cell], w02 = prim[P_W02 * nc + cell];
+    const double w03 = prim[P_W03 * nc + cell], w10 = prim[P_W10 * nc + cell];
+    const double w11 = prim[P_W11 * nc + cell], w12 = prim[P_W12 * nc + cell];
+    const double w20 = prim[P_W20 * nc + cell], w21 = prim[P_W21 * nc + cell];
+    const double w30 = prim[P_W30 * nc + cell];
+    const double e1 = expd(-c1q * inv2T) * iom2;
+    const double A0 = -e1 * (c1 * fma(c1, fma(c1, w03, w02), w01) + ome);
+    const double A1 = -e1 * fma(c1, fma(c1, w12, w11), w10);
+    const double A2 = -e1 * fma(c1, w21, w20);
+    const double A3 = -e1 * w30;
+    const double gam1 = gam0 * iom2 * expd(-0.5 * Ti11 * c1q);
+    const double c2r = fma(r + 0.5, g.dv2, g.v2min) - u2;
+    double x = expd(-Ti12 * c1 * c2r);
+    const double rat = expd(-Ti12 * c1 * (R * g.dv2));
+    __syncthreads();
+    if (active) {
+      double* Go = G + (size_t)cell * nv + k;
+      for (int l = r; l < nv2; l += R) {
+        double o = A0 * e2t[l];
+        o = fma(A1, E1t[l], o);
+        o = fma(A2, E2t[l], o);
+        o = fma(A3, E3t[l], o);
+        o = fma(gam1, g2t[l] * x, o);
+        x *= rat;
+        Go[l * nv1] = o;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void launch_closure_features(const double* Q, const KGrid& g, const KParams& p, double eps,
+                             double dt, float* X, double* aux, cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  k_closure_features<<<(nc + 127) / 128, 128, 0, s>>>(Q, g, p, eps, dt, X, aux);
+}
+
+void launch_closure_targets(const double* H, const double* aux, float* Y, const KGrid& g,
+                            cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  k_closure_targets<<<(nc + 255) / 256, 256, 0, s>>>(H, aux, Y, nc);
+}
+
+void launch_closure_decide(const float* Y, const double* aux, double thr, const KGrid& g,
+                           const KParams& p, unsigned char* flags, double* H,
+                           unsigned long long* nclosure, cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  k_closure_decide<<<(nc + 255) / 256, 256, 0, s>>>(Y, aux, (float)thr, g, p, flags, H, nclosure);
+}
+
+void launch_closure_lists(const unsigned char* flags, const KGrid& g, const KParams& p,
+                          int* lists, int* counts, cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  cudaMemsetAsync(counts, 0, 3 * sizeof(int), s);
+  k_closure_lists<<<(nc + 255) / 256, 256, 0, s>>>(flags, g, p, lists, lists + nc, lists + 2 * nc,
+                                                   counts);
+}
+
+int closure_ghat_blocks(const MicroShape& ms) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_closure_ghat, ms.threads, ms.smem_ghat);
+  return (nsm > 0 ? nsm : 1) * (per > 0 ? per : 1);
+}
+
+void launch_closure_ghat(double* G, const double* prim, const KGrid& g, double dt, double eps,
+                         const MicroShape& ms, const int* clist, const int* count, int blocks,
+                         cudaStream_t s) {
+  if (ms.smem_ghat > 48 * 1024)
+    cudaFuncSetAttribute(k_closure_ghat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_ghat);
+  k_closure_ghat<<<blocks, ms.threads, ms.smem_ghat, s>>>(G, prim, g, dt, eps, ms.R, clist, count);
+}
+
+}  // namespace mmk

@@ -65,6 +65,7 @@ struct MicroShape {
   int R;
   int threads;
   size_t smem_x, smem_y;
+  size_t smem_ghat;  // closure Ghat kernel
 };
 MicroShape micro_shape(int nv1, int nv2);
 
@@ -123,6 +124,33 @@ __host__ __device__ inline MacroBufs carve_macro(double* base, int nx, int ny) {
   mb.BY = mb.BX + 12 * (size_t)ny;
   return mb;
 }
+// Micro sweeps over a device-resident cell list (persistent CTAs; count read on the device).
+template <typename Tg>
+void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
+                         const KParams& p, double dt, const MicroShape& ms, const int* list,
+                         const int* count, int blocks, cudaStream_t s);
+template <typename Tg>
+void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
+                         const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
+                         const int* list, const int* count, int blocks, cudaStream_t s);
+int micro_list_blocks(const MicroShape& ms, bool ysweep);
+// Learned closure (FP64 path): features + Chapman-Enskog flux + scale (aux [5][ny][nx]),
+// training targets, decision, work lists [x | y | closure][nc] with counts[3], Ghat write.
+void launch_closure_features(const double* Q, const KGrid& g, const KParams& p, double eps,
+                             double dt, float* X, double* aux, cudaStream_t s);
+void launch_closure_targets(const double* H, const double* aux, float* Y, const KGrid& g,
+                            cudaStream_t s);
+void launch_closure_decide(const float* Y, const double* aux, double thr, const KGrid& g,
+                           const KParams& p, unsigned char* flags, double* H,
+                           unsigned long long* nclosure, cudaStream_t s);
+void launch_closure_lists(const unsigned char* flags, const KGrid& g, const KParams& p,
+                          int* lists, int* counts, cudaStream_t s);
+int closure_ghat_blocks(const MicroShape& ms);
+void launch_closure_ghat(double* G, const double* prim, const KGrid& g, double dt, double eps,
+                         const MicroShape& ms, const int* clist, const int* count, int blocks,
+                         cudaStream_t s);
+// Network inference on the stream s (mm_mlp.cu).
+void mlp_forward_async(const mm_mlp* m, const float* X, float* Y, int n, cudaStream_t s);
 void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s);
 void launch_convert_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);

@@ -52,6 +52,39 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_wall(const Tg* __restrict__ 
   micro_y_wall_body<Tg>(Gs, Gout, Hout, prim, g, p, dt, eps, R, err, wall_cells[blockIdx.x], sm);
 }
 
+// The same sweeps over a list of cells: persistent CTAs take cells q = blockIdx.x + m gridDim.x.
+template <typename Tg>
+__global__ void __launch_bounds__(512, 1) k_micro_x_list(const Tg* __restrict__ Gin,
+                                                         Tg* __restrict__ Gout,
+                                                         const double* __restrict__ prim, KGrid g,
+                                                         KParams p, double dtidx, int R,
+                                                         const int* __restrict__ list,
+                                                         const int* __restrict__ count) {
+  extern __shared__ double sm[];
+  const int n = *count;
+  for (int q = blockIdx.x; q < n; q += gridDim.x) {
+    micro_x_body<Tg>(Gin, Gout, prim, g, p, dtidx, R, list[q], sm);
+    __syncthreads();
+  }
+}
+
+template <typename Tg>
+__global__ void __launch_bounds__(512, 1) k_micro_y_list(const Tg* __restrict__ Gs,
+                                                         Tg* __restrict__ Gout,
+                                                         double* __restrict__ Hout,
+                                                         const double* __restrict__ prim, KGrid g,
+                                                         KParams p, double dtidy, double hscale,
+                                                         int R, int* __restrict__ err,
+                                                         const int* __restrict__ list,
+                                                         const int* __restrict__ count) {
+  extern __shared__ double sm[];
+  const int n = *count;
+  for (int q = blockIdx.x; q < n; q += gridDim.x) {
+    micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, list[q], sm);
+    __syncthreads();
+  }
+}
+
 __global__ void k_diag_exp(const double* __restrict__ x, double* __restrict__ yf,
                            double* __restrict__ yl, size_t n) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
@@ -92,8 +125,50 @@ MicroShape micro_shape(int nv1, int nv2) {
   }
   ms.smem_x = sizeof(double) * (micro_body::kRed + 4 * (size_t)nv2);
   ms.smem_y = sizeof(double) * (micro_body::kRed + micro_body::kYTables * (size_t)nv2);
+  ms.smem_ghat = sizeof(double) * 5 * (size_t)nv2;
   return ms;
 }
+
+int micro_list_blocks(const MicroShape& ms, bool ysweep) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (ysweep) {
+    if (ms.smem_y > 48 * 1024)
+      cudaFuncSetAttribute(k_micro_y_list<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_y);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_micro_y_list<double>, ms.threads, ms.smem_y);
+  } else {
+    if (ms.smem_x > 48 * 1024)
+      cudaFuncSetAttribute(k_micro_x_list<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_x);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_micro_x_list<double>, ms.threads, ms.smem_x);
+  }
+  return (nsm > 0 ? nsm : 1) * (per > 0 ? per : 1);
+}
+
+template <typename Tg>
+void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
+                         const KParams& p, double dt, const MicroShape& ms, const int* list,
+                         const int* count, int blocks, cudaStream_t s) {
+  k_micro_x_list<Tg><<<blocks, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx,
+                                                           ms.R, list, count);
+}
+
+template <typename Tg>
+void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
+                         const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
+                         const int* list, const int* count, int blocks, cudaStream_t s) {
+  k_micro_y_list<Tg><<<blocks, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
+                                                           eps * g.dv1 * g.dv2, ms.R, err, list,
+                                                           count);
+}
+
+template void launch_micro_x_list<double>(const double*, double*, const double*, const KGrid&,
+                                          const KParams&, double, const MicroShape&, const int*,
+                                          const int*, int, cudaStream_t);
+template void launch_micro_y_list<double>(const double*, double*, double*, const double*,
+                                          const KGrid&, const KParams&, double, double,
+                                          const MicroShape&, int*, const int*, const int*, int,
+                                          cudaStream_t);
 
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,

@@ -1,0 +1,238 @@
+"""GPU tests of the learned closure through the C ABI: the network's forward pass, gradient and
+Adam step against the FP64 CPU reference (same BF16 weights), the features and Chapman-Enskog
+flux against the closure oracle, one hybrid step against the oracle's hybrid step, and the
+trained network's gain over the plain method (speed at a stated density error)."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import q_rel_err
+from oracle import closure_oracle as C
+from oracle import mlp_oracle as M
+from oracle import oracle as O
+from paper_2509_21832_gb300 import api
+from paper_2509_21832_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ULP = 2.220446049250313e-16
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _norm(seed, ystd=1.0):
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.standard_normal(38) * 0.1, np.exp(rng.uniform(-0.5, 0.5, 38)),
+                           rng.standard_normal(4) * 0.1 * ystd,
+                           ystd * np.exp(rng.uniform(-0.5, 0.5, 4))]).astype(np.float32)
+
+
+def _params(seed):
+    p = M.init_params(seed).astype(np.float64)
+    rng = np.random.default_rng(seed + 1)
+    p[M.OFF_B1:M.OFF_W2] = rng.standard_normal(64) * 0.1
+    p[M.OFF_B2:M.OFF_W3] = rng.standard_normal(64) * 0.1
+    p[M.OFF_B3:] = rng.standard_normal(4) * 0.1
+    return p.astype(np.float32)
+
+
+def test_mlp_forward_and_bf16_weights_match_oracle():
+    torch = _torch()
+    params, norm = _params(1), _norm(2)
+    mlp = api.MLP(params, norm)
+    master, wb = mlp.get_params()
+    assert np.array_equal(master, params)
+    assert np.array_equal(wb.astype(np.float64), M.bf16_round(params))  # RNE on both sides
+    for n in (1, 127, 1000, 4099):
+        X = (np.random.default_rng(n).standard_normal((n, 38)) * 1.3).astype(np.float32)
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        mlp.forward(Xd, Yd)
+        Y = Yd.cpu().numpy().astype(np.float64)
+        Yo = M.forward(M.bf16_round(params), norm.astype(np.float64), X.astype(np.float64))
+        tol = 2e-5 * (1.0 + np.max(np.abs(Yo)))
+        assert np.max(np.abs(Y - Yo)) <= tol, (n, np.max(np.abs(Y - Yo)), tol)
+    mlp.close()
+
+
+def test_mlp_gradient_matches_oracle():
+    torch = _torch()
+    params, norm = _params(3), _norm(4)
+    mlp = api.MLP(params, norm)
+    for n in (1, 333, 2048):
+        rng = np.random.default_rng(10 + n)
+        X = (rng.standard_normal((n, 38)) * 1.1).astype(np.float32)
+        T = rng.standard_normal((n, 4)).astype(np.float32)
+        L, g = mlp.grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+        Lo, go = M.loss_and_grad(M.bf16_round(params), norm.astype(np.float64),
+                                 X.astype(np.float64), T.astype(np.float64))
+        assert abs(L - Lo) <= 2e-5 * Lo, (n, L, Lo)
+        err = np.max(np.abs(g.astype(np.float64) - go))
+        assert err <= 1e-4 * np.max(np.abs(go)), (n, err, np.max(np.abs(go)))
+        # every layer's gradient is checked, not only the largest
+        for a, b in ((M.OFF_W1, M.OFF_B1), (M.OFF_W2, M.OFF_B2), (M.OFF_W3, M.OFF_B3)):
+            e = np.max(np.abs(g[a:b] - go[a:b]))
+            assert e <= 1e-4 * np.max(np.abs(go[a:b])) + 1e-9, (n, a, e)
+    mlp.close()
+
+
+def test_adam_step_matches_oracle():
+    torch = _torch()
+    params, norm = _params(5), _norm(6)
+    mlp = api.MLP(params, norm)
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((900, 38)).astype(np.float32)
+    T = rng.standard_normal((900, 4)).astype(np.float32)
+    lr = 1e-3
+    for t in (1, 2):
+        Lo, go = M.loss_and_grad(M.bf16_round(params if t == 1 else w_gpu), norm.astype(np.float64),
+                                 X.astype(np.float64), T.astype(np.float64))
+        if t == 1:
+            w_o, m1, m2 = M.adam_step(params.astype(np.float64), 0.0, 0.0, go, 1, lr)
+        else:
+            w_o, m1, m2 = M.adam_step(w_gpu.astype(np.float64), m1, m2, go, 2, lr)
+        mlp.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), lr)
+        w_gpu, wb = mlp.get_params()
+        sel = np.abs(go) > 1e-2 * np.max(np.abs(go))  # where FP32 and FP64 gradients agree in sign
+        err = np.abs(w_gpu.astype(np.float64) - w_o)[sel]
+        assert np.all(err <= 1e-2 * lr + 2.0 ** -22 * np.abs(w_o[sel])), (t, err.max())
+        assert np.array_equal(wb.astype(np.float64), M.bf16_round(w_gpu))
+    mlp.close()
+
+
+FEATURE_CASES = [
+    ("periodic", (I.PERIODIC,) * 4),
+    ("specular_extrap", (I.SPECULAR, I.EXTRAP, I.PERIODIC, I.PERIODIC)),
+    ("walls", (I.EXTRAP, I.SPECULAR, I.SPECULAR, I.DIFFUSE)),
+]
+
+
+@pytest.mark.parametrize("name,bc", FEATURE_CASES)
+def test_features_and_chapman_enskog_flux_match_oracle(name, bc):
+    torch = _torch()
+    g = I.Grid(nx=13, ny=11, nv1=8, nv2=8)
+    p = I.Params(nu=-0.5, bc=bc, tau_model=I.TAU_PRESSURE)
+    Q = I.smooth_state(g, 21, amp=0.25, umax=0.3, aniso=0.1)
+    eps, dt = 2e-2, 1e-3
+    X = torch.empty((g.ncell, 38), dtype=torch.float32, device="cuda")
+    aux = torch.empty((5, g.ny, g.nx), dtype=torch.float64, device="cuda")
+    with api.Solver(g, p) as s:
+        s.set_state(Q)
+        s.closure_features(dt, eps, X, aux)
+        s.sync()
+    Xo, Hce, scale = C.features(g, p, Q, eps, dt)
+    Xg = X.cpu().numpy().astype(np.float64)
+    # features are computed in FP64 and rounded once to FP32
+    assert np.all(np.abs(Xg - Xo) <= 2.0 ** -24 * np.abs(Xo) * 1.01 + 1e-14), name
+    A = aux.cpu().numpy()
+    assert np.max(np.abs(A[:4] - Hce)) <= 1e-13 * np.max(np.abs(Hce)), name
+    assert np.max(np.abs(A[4] - scale) / scale) <= 1e-15, name
+
+
+def _gap_threshold(ind, interior):
+    """A threshold in the widest gap of the middle half of the sorted indicator values, so that
+    FP32 and FP64 evaluations of the network decide every cell alike."""
+    v = np.sort(ind[interior])
+    lo, hi = len(v) // 4, 3 * len(v) // 4
+    k = lo + int(np.argmax(np.diff(v[lo:hi + 1])))
+    thr = 0.5 * (v[k] + v[k + 1])
+    return thr, (v[k + 1] - v[k]) / thr
+
+
+HYBRID_CASES = [
+    ("specular_16", dict(nx=14, ny=12, nv1=16, nv2=16), (I.SPECULAR,) * 4, 1e-2),
+    ("periodic_24", dict(nx=11, ny=13, nv1=24, nv2=24), (I.PERIODIC,) * 4, 1e-3),
+    ("mixed_20", dict(nx=12, ny=10, nv1=20, nv2=20), (I.EXTRAP, I.EXTRAP, I.PERIODIC, I.PERIODIC), 1e-1),
+]
+
+
+@pytest.mark.parametrize("name,gk,bc,eps", HYBRID_CASES)
+def test_hybrid_step_matches_oracle(name, gk, bc, eps):
+    g = I.Grid(**gk)
+    p = I.Params(nu=-0.5, bc=bc)
+    Q = I.smooth_state(g, 31, amp=0.2, umax=0.25, aniso=0.05)
+    G0 = I.seeded_g(g, 32, amp=0.02)
+    dt = 0.5 / (8.0 * g.nx + 8.0 * g.ny)
+    params, norm = _params(8), _norm(9)
+    wq = M.bf16_round(params)
+    net = lambda X: M.forward(wq, norm.astype(np.float64), X)
+    X, Hce, scale = C.features(g, p, Q, eps, dt)
+    ind = np.max(np.abs(net(X)), axis=1).reshape(g.ny, g.nx)
+    interior = ~C.boundary_cells(g, p)
+    thr, gap = _gap_threshold(ind, interior)
+    assert gap > 1e-3, gap
+    Qo, Go, Ho, fo, _ = C.hybrid_step(g, p, Q, G0, dt, eps, net, thr)
+    assert 0 < fo.sum() < interior.sum()
+    mlp = api.MLP(params, norm)
+    with api.Solver(g, p) as s:
+        s.set_state(Q, G0)
+        s.set_closure(mlp, thr)
+        s.step(dt, eps, 1)
+        s.sync()
+        Qg, Hg = s.get_moments()
+        Gg = s.get_g()
+        fg = s.closure_flags().astype(bool)
+        ncl, ncs = s.closure_stats()
+    assert np.array_equal(fg, fo), name
+    assert ncl == fo.sum() and ncs == g.ncell
+    rho = Q[0] if Q.ndim == 3 else Q.reshape(6, g.ny, g.nx)[0]
+    gfl = 64 * ULP * np.max(rho) / eps
+    gerr = np.max(np.abs(Gg - Go))
+    assert gerr <= max(1e-11 * np.max(np.abs(Go)), gfl), (name, gerr)
+    mic = ~fo
+    herr_m = np.max(np.abs(Hg[:, mic] - Ho[:, mic]))
+    assert herr_m <= max(1e-11 * np.max(np.abs(Ho)), 64 * ULP * 4.0 * np.max(rho) * 2), (name, herr_m)
+    # closure cells: H = H_CE + s y with y from the FP32 network
+    yo = net(X).T.reshape(4, g.ny, g.nx)
+    herr_c = np.max(np.abs(Hg[:, fo] - Ho[:, fo]))
+    tol_c = 2e-5 * np.max(scale) * (1.0 + np.max(np.abs(yo)))
+    assert herr_c <= tol_c, (name, herr_c, tol_c)
+    dH = max(herr_m, herr_c)
+    eq = q_rel_err(Qg, Qo)
+    rho_max = np.max(np.abs(Qo.reshape(6, -1)[0]))
+    tol_q = 1e-12 + 4.0 * dt * max(g.nx, g.ny) * dH / rho_max
+    assert np.all(eq <= tol_q), (name, eq, tol_q)
+    mlp.close()
+
+
+def test_hybrid_without_closure_cells_is_the_plain_step_bitwise():
+    g = I.Grid(nx=17, ny=9, nv1=24, nv2=24)
+    p = I.Params(nu=-0.5, bc=(I.SPECULAR, I.SPECULAR, I.PERIODIC, I.PERIODIC))
+    Q = I.smooth_state(g, 41)
+    G0 = I.seeded_g(g, 42, amp=0.02)
+    dt, eps = 1e-3, 1e-2
+    mlp = api.MLP(_params(10), _norm(11))
+    out = []
+    for thr in (None, 0.0):
+        with api.Solver(g, p) as s:
+            s.set_state(Q, G0)
+            if thr is not None:
+                s.set_closure(mlp, thr)  # max |y| <= 0 nowhere: every cell takes the micro path
+            s.step(dt, eps, 3)
+            s.sync()
+            out.append((s.get_moments(), s.get_g()))
+            if thr is not None:
+                assert s.closure_stats()[0] == 0
+    (Qa, Ha), Ga = out[0]
+    (Qb, Hb), Gb = out[1]
+    assert np.array_equal(Qa, Qb) and np.array_equal(Ha, Hb) and np.array_equal(Ga, Gb)
+    mlp.close()
+
+
+def test_closure_rejects_fp32_contexts_and_bad_thresholds():
+    g = I.Grid(nx=8, ny=8, nv1=16, nv2=16)
+    mlp = api.MLP(_params(12), _norm(13))
+    p32 = I.Params(precision=I.PREC_G_FP32)
+    with api.Solver(g, p32) as s:
+        with pytest.raises(api.MMError):
+            s.set_closure(mlp, 1e-3)
+    with api.Solver(g, I.Params()) as s:
+        for bad in (-1.0, float("nan"), float("inf")):
+            with pytest.raises(api.MMError):
+                s.set_closure(mlp, bad)
+        s.set_closure(None, 0.0)
+    mlp.close()
