@@ -176,20 +176,20 @@ void mm_batch_destroy(mm_batch* b);
  * accumulation, maps local macro features of a cell to y = (H - H_CE) / (eps rho T^{3/2}), the
  * dimensionless part of the heat-flux tensor of Eq. (5-99) beyond its Chapman-Enskog value H_CE
  * (the moments of the transport part of Ghat, Eq. 5-97).  Parameters are one flat FP32 vector of
- * MM_MLP_NPARAM values [W1 (64x38, row-major by output), b1, W2 (64x64), b2, W3 (4x64), b3];
- * the normalisation vector holds [input mean (38), input 1/std (38), output mean (4), output
- * std (4)].  Feature and target arrays are FP32 device arrays, sample-major [n][38], [n][4]. */
-#define MM_MLP_IN 38
+ * MM_MLP_NPARAM values [W1 (64x39, row-major by output), b1, W2 (64x64), b2, W3 (4x64), b3];
+ * the normalisation vector holds [input mean (39), input 1/std (39), output mean (4), output
+ * std (4)].  Feature and target arrays are FP32 device arrays, sample-major [n][39], [n][4]. */
+#define MM_MLP_IN 39
 #define MM_MLP_HIDDEN 64
 #define MM_MLP_OUT 4
-#define MM_MLP_NPARAM 6916
+#define MM_MLP_NPARAM 6980
 typedef struct mm_mlp mm_mlp;
 mm_status mm_mlp_create(void* cuda_stream, mm_mlp** out);
 /* Load FP32 parameters (rounded to BF16 for the kernels) and normalisation; resets Adam. */
 mm_status mm_mlp_set_params(mm_mlp* m, const float* params_host, const float* norm_host);
 /* FP32 master parameters and/or the BF16 parameters the kernels use (as FP32 values). */
 mm_status mm_mlp_get_params(mm_mlp* m, float* params_host, float* params_bf16_as_f32_host);
-/* Inference: Y[n][4] (de-standardised) from X[n][38]; asynchronous. */
+/* Inference: Y[n][4] (de-standardised) from X[n][39]; asynchronous. */
 mm_status mm_mlp_forward(mm_mlp* m, const float* X_dev, float* Y_dev, int n);
 /* Gradient of the mean squared error of the standardised outputs with respect to the
  * parameters (BF16 weights, FP32 accumulation), and the loss; synchronous if outputs given. */
@@ -204,15 +204,18 @@ void mm_mlp_destroy(mm_mlp* m);
 /* Hybrid stepping with the closure (FP64 contexts).  While a network is set, every mm_step
  * computes per cell the features of Q^n, the network's y and the indicator max_m |y_m|; a cell
  * that touches no non-periodic boundary and whose indicator is <= threshold takes the closure:
- * g^{n+1} = Ghat (the asymptotic-preserving limit of Eq. 5-98) and H = H_CE + eps rho T^{3/2} y,
- * and skips the micro sweeps; every other cell takes the full micro update.  The context keeps
- * the pointer: the network must outlive its use.  m = NULL switches the closure off.  Resets
- * the statistics.  FP32-g contexts: MM_ERR_INVALID_ARG. */
+ * H = H_CE + eps rho T^{3/2} y and no micro update; every other cell takes the full micro update.
+ * g is maintained where the micro sweeps read it: before the sweeps, every cell in the 3x3 block
+ * of a micro cell whose g^n was not produced by the previous step's micro update is reset to
+ * Ghat(Q^n) (the asymptotic-preserving limit of Eq. 5-98); elsewhere g of closure cells is left
+ * as it was (mm_get_g returns it as is).  The context keeps the pointer: the network must
+ * outlive its use.  m = NULL switches the closure off; the next step then first resets every
+ * non-current g to Ghat.  Resets the statistics.  FP32-g contexts: MM_ERR_INVALID_ARG. */
 mm_status mm_set_closure(mm_ctx* c, const mm_mlp* m, double threshold);
-/* Features X_dev [nc][38] (FP32) of the current state and aux_dev [5][ny][nx] (FP64: H_CE of
+/* Features X_dev [nc][39] (FP32) of the current state and aux_dev [5][ny][nx] (FP64: H_CE of
  * the four components, then the scale eps rho T^{3/2}); asynchronous. */
 mm_status mm_closure_features(mm_ctx* c, double dt, double eps, float* X_dev, double* aux_dev);
-/* Training data: the features of Q^n into X_dev [nc][38], then one plain (full micro) step, then
+/* Training data: the features of Q^n into X_dev [nc][39], then one plain (full micro) step, then
  * the targets y = (H - H_CE) / (eps rho T^{3/2}) into Y_dev [nc][4]; asynchronous. */
 mm_status mm_closure_collect(mm_ctx* c, double dt, double eps, float* X_dev, float* Y_dev);
 /* Closure flags of the last hybrid step, [ny][nx] bytes (1 = closure). */

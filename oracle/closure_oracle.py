@@ -16,14 +16,23 @@ cell it defines, from Q^n alone:
   (the strain terms and (Gcal - M)/eps have no odd central moments);
 * the scale s = eps rho T^{3/2} of the heat flux, and the network target
   y = (H - H_CE) / s, H being the heat flux of Eq. (5-99) from the micro step;
-* 38 features: for the 8 neighbours of the 3x3 stencil (rows j-1, j, j+1, columns i-1, i, i+1,
-  the centre skipped) rho_n/rho - 1, (u1_n - u1)/sqrt(T), (u2_n - u2)/sqrt(T), T_n/T - 1; then
-  (theta11 - theta22)/(2T), theta12/T with theta = P/rho, u1/sqrt(T), u2/sqrt(T), log10 eps and
-  the relaxation weight omega1 = eps / (eps + dt tau) of the micro step.  A neighbour outside
-  the box is the periodic image, or else the cell itself, with the normal velocity negated at a
-  specular wall;
+* 39 features: with the cell Knudsen number k = eps sqrt(T) / (tau h), h = min(dx, dy) (the
+  relaxation length over the mesh width, which makes differences between neighbours
+  resolution-independent), for the 8 neighbours of the 3x3 stencil (rows j-1, j, j+1, columns
+  i-1, i, i+1, the centre skipped) k (rho_n/rho - 1), k (u1_n - u1)/sqrt(T), k (u2_n - u2)/sqrt(T),
+  k (T_n/T - 1); then (theta11 - theta22)/(2T), theta12/T with theta = P/rho, u1/sqrt(T),
+  u2/sqrt(T), log10 eps, the relaxation weight omega1 = eps / (eps + dt tau) of the micro step
+  and log10 k.  A neighbour outside the box is the periodic image, or else the cell itself, with
+  the normal velocity negated at a specular wall;
 * the indicator max_m |y_m| of the network's prediction; a cell takes the closure when it is at
   most the threshold and the cell does not touch a non-periodic boundary.
+
+A closure cell skips the micro update and keeps its g, which nothing reads unless a micro cell
+needs it: the micro sweeps of a cell read g^n in its 3x3 block (the x sweep runs on the micro
+cells and on their y neighbours, whose G* the y sweep reads, and reads the x neighbours of
+those).  So at step n every cell in the 3x3 blocks of the micro cells whose g^n was not produced
+by the micro update of step n-1 is first reset to the asymptotic-preserving limit Ghat(Q^n)
+(Eq. 5-97): g is maintained exactly where it is read.
 """
 from __future__ import annotations
 
@@ -34,7 +43,7 @@ import numpy as np
 from oracle import oracle as O
 
 PERIODIC, SPECULAR = 0, 2
-N_FEAT = 38
+N_FEAT = 39
 
 
 def _cell_prims(grid, params, Q):
@@ -58,7 +67,7 @@ def _nb(i, d, n, bc_lo, bc_hi):
 
 
 def features(grid, params, Q, eps, dt):
-    """Features X [ny*nx][38], H_CE [4][ny][nx] and scale [ny][nx] of every cell."""
+    """Features X [ny*nx][39], H_CE [4][ny][nx] and scale [ny][nx] of every cell."""
     nx, ny = grid.nx, grid.ny
     dx = (grid.x1 - grid.x0) / nx
     dy = (grid.y1 - grid.y0) / ny
@@ -71,6 +80,7 @@ def features(grid, params, Q, eps, dt):
         for i in range(nx):
             rho, u1, u2, T, P11, P12, P22, tau = P[j, i]
             sT = math.sqrt(T)
+            k = eps * sT / (tau * min(dx, dy))
             f = []
             for dj in (-1, 0, 1):
                 nj, fy = _nb(j, dj, ny, bc[2], bc[3])
@@ -83,9 +93,10 @@ def features(grid, params, Q, eps, dt):
                         a1 = -a1
                     if fy:
                         a2 = -a2
-                    f += [r / rho - 1.0, (a1 - u1) / sT, (a2 - u2) / sT, Tn / T - 1.0]
+                    f += [k * (r / rho - 1.0), k * (a1 - u1) / sT, k * (a2 - u2) / sT,
+                          k * (Tn / T - 1.0)]
             f += [(P11 - P22) / (2.0 * rho * T), P12 / (rho * T), u1 / sT, u2 / sT,
-                  math.log10(eps), eps / (eps + dt * tau)]
+                  math.log10(eps), eps / (eps + dt * tau), math.log10(k)]
             X[j, i] = f
             # discrete temperature gradient of Eq. (5-97more): face temperatures (T_nb + T)/2
             iL, _ = _nb(i, -1, nx, bc[0], bc[1])
@@ -133,12 +144,45 @@ def decide(grid, params, y, Hce, scale, threshold):
     return flags, Hcl, ind
 
 
-def hybrid_step(grid, params, Q, G, dt, eps, y_of_features, threshold):
-    """One hybrid step: features of Q^n, the network's y (y_of_features(X) -> [n][4]), the
-    closure decision, then the step with g^{n+1} = Ghat and H = H_CE + s y in closure cells.
-    Returns (Q, G, H, flags, indicator)."""
-    X, Hce, scale = features(grid, params, Q, eps, dt)
-    y = y_of_features(X)
-    flags, Hcl, ind = decide(grid, params, y, Hce, scale, threshold)
-    Qn, Gn, Hn = O.step_closure(grid, params, Q, G, dt, eps, flags, Hcl)
-    return Qn, Gn, Hn, flags, ind
+def _dilate(mask, axis, periodic):
+    """Cells with a set neighbour along axis (or set themselves); periodic sides wrap."""
+    out = mask.copy()
+    n = mask.shape[axis]
+    for d in (-1, 1):
+        sh = np.roll(mask, d, axis=axis)
+        if not periodic:
+            idx = [slice(None)] * 2
+            idx[axis] = 0 if d == 1 else n - 1
+            sh[tuple(idx)] = False
+        out |= sh
+    return out
+
+
+def needed_cells(grid, params, micro):
+    """Cells whose g^n the micro sweeps of the micro cells read: their 3x3 blocks."""
+    yp = params.bc[2] == PERIODIC
+    xp = params.bc[0] == PERIODIC
+    return _dilate(_dilate(micro, 0, yp), 1, xp)
+
+
+def hybrid_run(grid, params, Q, G, dt, eps, y_of_features, threshold, nsteps=1, valid=None):
+    """nsteps hybrid steps: per step the features of Q^n, the network's y (y_of_features(X) ->
+    [n][4]), the closure decision, the refresh g^n = Ghat(Q^n) of needed cells whose g^n is not
+    current, then the step with H = H_CE + s y in closure cells.  valid [ny][nx]: cells whose
+    g is current at the start (default all).  Returns (Q, G, H, flags per step, indicator per
+    step, refresh per step)."""
+    valid = np.ones((grid.ny, grid.nx), dtype=bool) if valid is None else valid.copy()
+    flags_all, ind_all, ref_all = [], [], []
+    H = None
+    for _ in range(nsteps):
+        X, Hce, scale = features(grid, params, Q, eps, dt)
+        y = y_of_features(X)
+        flags, Hcl, ind = decide(grid, params, y, Hce, scale, threshold)
+        micro = ~flags
+        refresh = needed_cells(grid, params, micro) & ~valid
+        Q, G, H = O.step_closure(grid, params, Q, G, dt, eps, flags, refresh, Hcl)
+        valid = micro
+        flags_all.append(flags)
+        ind_all.append(ind)
+        ref_all.append(refresh)
+    return Q, G, H, flags_all, ind_all, ref_all

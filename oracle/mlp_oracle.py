@@ -4,9 +4,9 @@ TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the CP
 of the benchmark; the product path never uses it.  It shares no code with the CUDA library.
 
 The network is the library's extension (the paper has no learned closure): a multilayer
-perceptron with 38 inputs, two hidden layers of 64 GELU units and 4 outputs.  Parameters are one
-flat vector [W1 (64x38, row-major by output unit), b1 (64), W2 (64x64), b2 (64), W3 (4x64),
-b3 (4)] of 6916 values; the normalisation vector is [input mean (38), input 1/std (38), output
+perceptron with 39 inputs, two hidden layers of 64 GELU units and 4 outputs.  Parameters are one
+flat vector [W1 (64x39, row-major by output unit), b1 (64), W2 (64x64), b2 (64), W3 (4x64),
+b3 (4)] of 6980 values; the normalisation vector is [input mean (39), input 1/std (39), output
 mean (4), output std (4)].  With x' = (x - mean_x) / std_x,
 
     a1 = gelu(W1 x' + b1),  a2 = gelu(W2 a1 + b2),  y' = W3 a2 + b3,  y = y' std_y + mean_y,
@@ -23,7 +23,7 @@ import math
 import numpy as np
 from scipy.special import erf
 
-N_IN, N_HIDDEN, N_OUT = 38, 64, 4
+N_IN, N_HIDDEN, N_OUT = 39, 64, 4
 OFF_W1 = 0
 OFF_B1 = OFF_W1 + N_HIDDEN * N_IN
 OFF_W2 = OFF_B1 + N_HIDDEN
@@ -80,7 +80,7 @@ def _forward(params, norm, X):
 
 
 def forward(params, norm, X) -> np.ndarray:
-    """Network output y (de-standardised) for samples X [n][38]."""
+    """Network output y (de-standardised) for samples X [n][39]."""
     norm = np.asarray(norm, dtype=np.float64)
     ys = _forward(params, norm, X)[-1]
     return ys * norm[2 * N_IN + N_OUT:] + norm[2 * N_IN:2 * N_IN + N_OUT]

@@ -668,11 +668,12 @@ static int check_args(const orc_grid* g, const orc_params* p) {
 /* ------------------------------------------------------------------------------------------ */
 /* one full time step, Section 5.3 (micro) then Section 5.4 (macro)                             */
 /* ------------------------------------------------------------------------------------------ */
-/* One or more steps; with closure != NULL, cells with closure[c] != 0 take g^{n+1} = Ghat and
- * the heat flux Hcl[m][c] in place of the relaxed micro solution and its moments. */
+/* One or more steps; with closure != NULL (one step): cells with refresh[c] != 0 first take
+ * g^n = Ghat(Q^n); then cells with closure[c] != 0 keep g^n and take the heat flux Hcl[m][c] in
+ * place of the relaxed micro solution and its moments. */
 static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
                      double dt, double eps, int nsteps, const unsigned char* closure,
-                     const double* Hcl) {
+                     const unsigned char* refresh, const double* Hcl) {
   if (check_args(g, p) || !Q || !G || !H || !(dt > 0.0) || !(eps > 0.0) || nsteps < 0) return 1;
   const int nx = g->nx, ny = g->ny, nv1 = g->nv1, nv2 = g->nv2, nv = nv1 * nv2;
   const int nc = nx * ny;
@@ -702,6 +703,18 @@ static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* 
     }
     if (bad) { status = 4; break; }
 
+    /* closure: refreshed cells start the step from Ghat(Q^n) */
+    if (refresh) {
+#pragma omp parallel
+      {
+        double* tmp = (double*)malloc(sizeof(double) * nv);
+#pragma omp for schedule(static)
+        for (int c = 0; c < nc; ++c)
+          if (refresh[c]) ghat_cell(g, p, P, Mc, c % nx, c / nx, eps, G + (size_t)c * nv, tmp);
+        free(tmp);
+      }
+    }
+
     /* micro: x sweep (G^n -> G*), y sweep (G* -> G**) */
     micro_sweep(g, p, P, Mc, G, Gs, dt, 1);
     micro_sweep(g, p, P, Mc, Gs, Gss, dt, 2);
@@ -715,13 +728,11 @@ static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* 
       for (int c = 0; c < nc; ++c) {
         int i = c % nx, j = c / nx;
         const prim_t* pc = &P[c];
-        ghat_cell(g, p, P, Mc, i, j, eps, gh, tmp);
         if (closure && closure[c]) {
-          for (int l = 0; l < nv2; ++l)
-            for (int k = 0; k < nv1; ++k) G[gidx(g, i, j, k, l)] = gh[l * nv1 + k];
           for (int m = 0; m < 4; ++m) H[m * nc + c] = Hcl[m * nc + c];
           continue;
         }
+        ghat_cell(g, p, P, Mc, i, j, eps, gh, tmp);
         double w1 = eps / (eps + dt * pc->tau);
         double w2 = dt * pc->tau / (eps + dt * pc->tau);
         double h111 = 0, h112 = 0, h122 = 0, h222 = 0;
@@ -817,13 +828,14 @@ static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* 
 
 int orc_step(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H, double dt,
              double eps, int nsteps) {
-  return step_impl(g, p, Q, G, H, dt, eps, nsteps, NULL, NULL);
+  return step_impl(g, p, Q, G, H, dt, eps, nsteps, NULL, NULL, NULL);
 }
 
 int orc_step_closure(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
-                     double dt, double eps, const unsigned char* closure, const double* Hcl) {
-  if (!closure || !Hcl) return 1;
-  return step_impl(g, p, Q, G, H, dt, eps, 1, closure, Hcl);
+                     double dt, double eps, const unsigned char* closure,
+                     const unsigned char* refresh, const double* Hcl) {
+  if (!closure || !refresh || !Hcl) return 1;
+  return step_impl(g, p, Q, G, H, dt, eps, 1, closure, refresh, Hcl);
 }
 
 int orc_ghat(const orc_grid* g, const orc_params* p, const double* Q, double eps, double* Ghat) {

@@ -50,11 +50,13 @@ int orc_step(const orc_grid* g, const orc_params* p, double* Q, double* G, doubl
              double dt, double eps, int nsteps);
 
 /* One step of the hybrid scheme with a heat-flux closure (the library's learned-closure
- * extension; the paper has no counterpart): as orc_step, except that in cells with
- * closure[c] != 0 the micro solution is replaced by its asymptotic-preserving limit,
- * g^{n+1} = Ghat (Eq. 5-97), and the heat flux of the macro step by Hcl[4][ny][nx]. */
+ * extension; the paper has no counterpart).  Cells with refresh[c] != 0 first set g^n to its
+ * asymptotic-preserving limit Ghat(Q^n) (Eq. 5-97); then the step proceeds as orc_step, except
+ * that cells with closure[c] != 0 skip the micro update (they keep g^n) and feed the heat flux
+ * Hcl[4][ny][nx] to the macro step. */
 int orc_step_closure(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
-                     double dt, double eps, const unsigned char* closure, const double* Hcl);
+                     double dt, double eps, const unsigned char* closure,
+                     const unsigned char* refresh, const double* Hcl);
 /* Global time step (Eq. CFL-2D-part1/part2 and the 1D rule of Section 3.2). */
 double orc_dt_for_cfl(const orc_grid* g, double cfl, double t_final, int form, int* nsteps_out);
 

@@ -61,6 +61,7 @@ def lib():
         L.orc_trbdf2_W.restype = ctypes.c_double
         L.orc_step_closure.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
                                        ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_ubyte),
                                        ctypes.POINTER(ctypes.c_ubyte), _c_double_p]
         L.orc_step_closure.restype = ctypes.c_int
         L.orc_ghat.argtypes = [G, P, _c_double_p, ctypes.c_double, _c_double_p]
@@ -114,19 +115,23 @@ def step(grid, params, Q, G, dt, eps, nsteps=1):
     return Q, G, H
 
 
-def step_closure(grid, params, Q, G, dt, eps, closure, Hcl):
-    """One hybrid step: cells with closure != 0 take g^{n+1} = Ghat and the heat flux Hcl
-    [4][ny][nx]; returns (Q, G, H).  Inputs are not modified."""
+def step_closure(grid, params, Q, G, dt, eps, closure, refresh, Hcl):
+    """One hybrid step: cells with refresh != 0 first take g^n = Ghat(Q^n); cells with
+    closure != 0 then keep g^n and feed the heat flux Hcl [4][ny][nx] to the macro step; returns
+    (Q, G, H).  Inputs are not modified."""
     Q = np.array(Q, dtype=np.float64, order="C", copy=True)
     G = np.array(G, dtype=np.float64, order="C", copy=True)
     H = np.zeros((4, grid.ny, grid.nx), dtype=np.float64)
     fl = np.ascontiguousarray(np.asarray(closure).reshape(-1) != 0, dtype=np.uint8)
+    rf = np.ascontiguousarray(np.asarray(refresh).reshape(-1) != 0, dtype=np.uint8)
+    assert rf.size == fl.size
     Hc = np.ascontiguousarray(Hcl, dtype=np.float64).reshape(4, grid.ny, grid.nx)
     assert fl.size == grid.nx * grid.ny
     gg, pp = _grid(grid), _params(params)
     rc = lib().orc_step_closure(ctypes.byref(gg), ctypes.byref(pp), _ptr(Q), _ptr(G), _ptr(H),
                                 float(dt), float(eps),
-                                fl.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _ptr(Hc))
+                                fl.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                rf.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _ptr(Hc))
     if rc != 0:
         raise OracleError("orc_step_closure returned %d" % rc)
     return Q, G, H

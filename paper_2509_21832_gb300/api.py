@@ -48,7 +48,7 @@ EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device"
            "mm_set_closure", "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
            "mm_closure_stats"]
 
-MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 38, 64, 4, 6916
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 39, 64, 4, 6980
 
 _lib = None
 
@@ -329,7 +329,7 @@ class Solver:
         _check(self.ctx, self.L.mm_set_closure(self.ctx, h, float(threshold)), "mm_set_closure")
 
     def closure_features(self, dt, eps, X_dev, aux_dev):
-        """Features [nc][38] (float32 CUDA tensor) and [5][ny][nx] (float64: H_CE, scale)."""
+        """Features [nc][39] (float32 CUDA tensor) and [5][ny][nx] (float64: H_CE, scale)."""
         _check(self.ctx, self.L.mm_closure_features(self.ctx, float(dt), float(eps),
                                                    _f32_ptr(X_dev, self.ncell * MLP_IN),
                                                    _dev_ptr(aux_dev, 5 * self.ncell)),

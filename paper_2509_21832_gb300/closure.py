@@ -2,7 +2,7 @@
 closure network on the GPU with the library's own kernels (mm_mlp_*).
 
 The closure is an extension of the library (the paper has no learned closure).  The network maps
-38 local features of a cell (mm_closure_features) to y = (H - H_CE) / (eps rho T^{3/2}), the part
+39 local features of a cell (mm_closure_features) to y = (H - H_CE) / (eps rho T^{3/2}), the part
 of the heat flux of Eq. (5-99) beyond its Chapman-Enskog value.  Training data are (features of
 Q^n, target after one plain micro-macro step) pairs collected on the device by
 mm_closure_collect; the loss is the mean squared error of the standardised outputs and the
@@ -23,18 +23,22 @@ from . import inputs as I
 
 @dataclass
 class Dataset:
-    X: "torch.Tensor"   # [n][38] float32, CUDA
+    X: "torch.Tensor"   # [n][39] float32, CUDA
     Y: "torch.Tensor"   # [n][4] float32, CUDA
     seconds: float = 0.0
 
 
-def collect(problems, warm_steps: int, every: int, samples_per_problem: int, device="cuda"):
+def collect(problems, warm_steps: int, every: int, samples_per_problem: int, keep: float = 1.0,
+            seed: int = 0, device="cuda"):
     """Run each problem with the plain solver; after warm_steps, every `every` steps record the
-    features of Q^n and the target of the next step for all cells, samples_per_problem times.
+    features of Q^n and the target of the next step, samples_per_problem times, keeping a seeded
+    random fraction `keep` of the cells of each snapshot.
 
     problems: iterable of inputs.Problem (FP64).  Returns a Dataset on the device."""
     import torch
     Xs, Ys = [], []
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
     t0 = time.time()
     for pb in problems:
         nc = pb.grid.nx * pb.grid.ny
@@ -46,6 +50,9 @@ def collect(problems, warm_steps: int, every: int, samples_per_problem: int, dev
                 X = torch.empty((nc, api.MLP_IN), dtype=torch.float32, device=device)
                 Y = torch.empty((nc, api.MLP_OUT), dtype=torch.float32, device=device)
                 s.closure_collect(pb.dt, pb.eps, X, Y)
+                if keep < 1.0:
+                    idx = torch.randperm(nc, device=device, generator=gen)[:max(1, int(keep * nc))]
+                    X, Y = X.index_select(0, idx), Y.index_select(0, idx)
                 Xs.append(X)
                 Ys.append(Y)
                 if every > 1:
@@ -119,12 +126,13 @@ def train(ds: Dataset, epochs: int = 4, batch: int = 8192, lr: float = 2e-3, see
     return TrainResult(mlp, norm, losses, step, time.time() - t0)
 
 
-def training_problems(n: int = 128, nv: int = 32, eps_list=(1e-3, 3e-3, 1e-2, 3e-2, 1e-1),
-                      seeds=(11, 12)):
+def training_problems(n: int = 256, nv: int = 32, eps_list=(1e-3, 3e-3, 1e-2, 3e-2, 1e-1),
+                      cfls=(0.5, 0.25), seed: int = 11):
     """Bump problems with specular walls (the family the closure is applied to) over a range of
-    Knudsen numbers, as training runs."""
+    Knudsen numbers and two CFL numbers (so that the relaxation weight omega1 = eps/(eps + dt tau)
+    of finer meshes is covered), as training runs."""
     out = []
     for k, eps in enumerate(eps_list):
-        for sd in seeds:
-            out.append(I.bump_specular(n=n, nv=nv, eps=eps, seed=sd + 100 * k))
+        for m, cfl in enumerate(cfls):
+            out.append(I.bump_specular(n=n, nv=nv, eps=eps, seed=seed + 100 * k + m, cfl=cfl))
     return out

@@ -61,11 +61,13 @@ struct mm_ctx {
   // learned closure (FP64 contexts): network, threshold and per-cell buffers
   const mm_mlp* mlp = nullptr;
   double closure_thr = 0.0;
-  float* cX = nullptr;                   // features [nc][38]
+  float* cX = nullptr;                   // features [nc][39]
   float* cY = nullptr;                   // network outputs [nc][4]
   double* caux = nullptr;                // H_CE [4][nc], scale [nc]
   unsigned char* cflags = nullptr;       // 1: closure cell in the last hybrid step
-  int* clists = nullptr;                 // x-sweep, y-sweep and closure cell lists [3][nc]
+  unsigned char* cvalid = nullptr;       // 1: g of the cell is current (micro-updated last step)
+  bool cstale = false;                   // closure switched off: reset non-current g first
+  int* clists = nullptr;                 // x-sweep, y-sweep and refresh cell lists [3][nc]
   int* ccounts = nullptr;                // their lengths [3]
   unsigned long long* cstat = nullptr;   // closure cells summed over hybrid steps
   long long closure_steps = 0;
@@ -192,6 +194,15 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
   timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
+  if constexpr (sizeof(Tg) == sizeof(double)) {
+    if (c->cstale) {  // after hybrid steps: g of closure cells to Ghat(Q^n) before a full step
+      const int nc = (int)c->ncell;
+      launch_closure_stale(c->cvalid, g, c->clists + 2 * nc, c->ccounts + 2, s);
+      launch_closure_ghat(G, c->prim, g, dt, eps, c->ms, c->clists + 2 * nc, c->ccounts + 2,
+                          c->blocks_g, s);
+      c->cstale = false;
+    }
+  }
   if constexpr (sizeof(Tg) == sizeof(float)) {
     // fused streaming kernel: G -> Gs (ping-pong), wall cells from the exported G*
     float* Ge = static_cast<float*>(c->Gexp);
@@ -219,8 +230,9 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
 }
 
-// Hybrid step with the learned closure (FP64): features and network on every cell, then the
-// micro sweeps on the micro cells (x sweep also on their y neighbours), Ghat on closure cells.
+// Hybrid step with the learned closure (FP64): features and network on every cell, the decision
+// and work lists, g^n = Ghat(Q^n) on the cells the sweeps read whose g is not current, then the
+// micro sweeps on the micro cells (x sweep also on their y neighbours).
 void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   double* G = static_cast<double*>(c->G);
   double* Gs = static_cast<double*>(c->Gs);
@@ -234,7 +246,13 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   timed(c, T_CL_DECIDE, [&] {
     launch_closure_decide(c->cY, c->caux, c->closure_thr, g, p, c->cflags, c->H, c->cstat, s);
   });
-  timed(c, T_CL_LISTS, [&] { launch_closure_lists(c->cflags, g, p, c->clists, c->ccounts, s); });
+  timed(c, T_CL_LISTS, [&] {
+    launch_closure_lists(c->cflags, c->cvalid, g, p, c->clists, c->ccounts, s);
+  });
+  timed(c, T_CL_GHAT, [&] {
+    launch_closure_ghat(G, c->prim, g, dt, eps, c->ms, c->clists + 2 * nc, c->ccounts + 2,
+                        c->blocks_g, s);
+  });
   timed(c, T_MICRO_X, [&] {
     launch_micro_x_list<double>(G, Gs, c->prim, g, p, dt, c->ms, c->clists, c->ccounts,
                                 c->blocks_x, s);
@@ -248,10 +266,6 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
       launch_micro_y_wall<double>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
                                   c->ms, c->err, s);
     });
-  timed(c, T_CL_GHAT, [&] {
-    launch_closure_ghat(G, c->prim, g, dt, eps, c->ms, c->clists + 2 * nc, c->ccounts + 2,
-                        c->blocks_g, s);
-  });
   timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
   timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
   timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
@@ -276,15 +290,18 @@ mm_status ensure_closure(mm_ctx* c) {
   alloc((void**)&c->cY, nc * MM_MLP_OUT * sizeof(float));
   alloc((void**)&c->caux, 5 * nc * sizeof(double));
   alloc((void**)&c->cflags, nc);
+  alloc((void**)&c->cvalid, nc);
   alloc((void**)&c->clists, 3 * nc * sizeof(int));
   alloc((void**)&c->ccounts, 3 * sizeof(int));
   alloc((void**)&c->cstat, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cstat, 0, sizeof(unsigned long long), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cflags, 0, nc, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cvalid, 1, nc, c->stream);
   if (e != cudaSuccess) {
-    cudaFree(c->cX); cudaFree(c->cY); cudaFree(c->caux); cudaFree(c->cflags);
+    cudaFree(c->cX); cudaFree(c->cY); cudaFree(c->caux); cudaFree(c->cflags); cudaFree(c->cvalid);
     cudaFree(c->clists); cudaFree(c->ccounts); cudaFree(c->cstat);
-    c->cX = c->cY = nullptr; c->caux = nullptr; c->cflags = nullptr; c->clists = c->ccounts = nullptr;
+    c->cX = c->cY = nullptr; c->caux = nullptr; c->cflags = c->cvalid = nullptr;
+    c->clists = c->ccounts = nullptr;
     c->cstat = nullptr;
     return e == cudaErrorMemoryAllocation ? fail(c, MM_ERR_OOM, "closure buffers")
                                           : cuda_fail(c, e, "closure buffers");
@@ -458,6 +475,11 @@ mm_status mm_set_state(mm_ctx* c, const double* Q_host, const double* G_host) {
     e = cudaMemsetAsync(c->G, 0, c->nphase * (c->fp32 ? sizeof(float) : sizeof(double)), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "zero G");
   }
+  if (c->cvalid) {
+    e = cudaMemsetAsync(c->cvalid, 1, c->ncell, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reset closure validity");
+    c->cstale = false;
+  }
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set state");
   c->have_state = true;
@@ -476,6 +498,11 @@ mm_status mm_set_state_device(mm_ctx* c, const double* Q_dev, const double* G_de
   } else {
     e = cudaMemsetAsync(c->G, 0, c->nphase * (c->fp32 ? sizeof(float) : sizeof(double)), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "zero G");
+  }
+  if (c->cvalid) {
+    e = cudaMemsetAsync(c->cvalid, 1, c->ncell, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reset closure validity");
+    c->cstale = false;
   }
   c->have_state = true;
   return MM_OK;
@@ -558,6 +585,7 @@ double mm_dt_for_cfl(const mm_grid* g, double cfl, double t_final, int form, int
 mm_status mm_set_closure(mm_ctx* c, const mm_mlp* m, double threshold) {
   if (!c) return MM_ERR_INVALID_ARG;
   if (!m) {
+    if (c->mlp) c->cstale = true;  // the next plain step first resets non-current g to Ghat
     c->mlp = nullptr;
     return MM_OK;
   }
@@ -571,6 +599,7 @@ mm_status mm_set_closure(mm_ctx* c, const mm_mlp* m, double threshold) {
   c->mlp = m;
   c->closure_thr = threshold;
   c->closure_steps = 0;
+  c->cstale = false;
   return MM_OK;
 }
 
@@ -673,6 +702,7 @@ void mm_destroy(mm_ctx* c) {
   cudaFree(c->cY);
   cudaFree(c->caux);
   cudaFree(c->cflags);
+  cudaFree(c->cvalid);
   cudaFree(c->clists);
   cudaFree(c->ccounts);
   cudaFree(c->cstat);

@@ -1,7 +1,8 @@
 // Learned heat-flux closure on the FP64 path (an extension of the library; the paper has no
 // counterpart).  Per step, from Q^n:
-//  - k_closure_features: 38 features of every cell (the 3x3 stencil of rho, u, T relative to the
-//    cell, the pressure anisotropy, u / sqrt T, log10 eps and the relaxation weight omega1), the
+//  - k_closure_features: 39 features of every cell (the 3x3 stencil of rho, u, T relative to the
+//    cell times the cell Knudsen number k = eps sqrt(T) / (tau min(dx, dy)), the pressure
+//    anisotropy, u / sqrt T, log10 eps, the relaxation weight omega1 and log10 k), the
 //    Chapman-Enskog heat flux H_CE (closed-form third central moments of the transport part of
 //    Ghat, Eq. 5-97: H111 = -3 eps p T_x / tau, H112 = -eps p T_y / tau, H122 = -eps p T_x / tau,
 //    H222 = -3 eps p T_y / tau with the discrete gradient of Eq. 5-97more) and the scale
@@ -10,10 +11,12 @@
 //  - k_closure_decide: a cell takes the closure when max_m |y_m| <= threshold and it touches no
 //    non-periodic boundary; its heat flux becomes H_CE + s y;
 //  - k_closure_lists: work lists of the micro kernels: the y sweep runs on micro cells, the x sweep
-//    on micro cells and their y neighbours (whose G* the y sweep reads), the Ghat kernel on
-//    closure cells;
-//  - k_closure_ghat: g^{n+1} = Ghat in closure cells (the asymptotic-preserving limit of the
-//    relaxation, Eq. 5-98 with omega1 = 0), so that neighbouring micro cells read a defined g.
+//    on micro cells and their y neighbours (whose G* the y sweep reads); the refresh list holds
+//    the cells of the micro cells' 3x3 blocks (the g^n the sweeps read) whose g^n the previous
+//    step's micro update did not produce;
+//  - k_closure_ghat: g^n = Ghat(Q^n) on the refresh list, before the sweeps (the asymptotic-
+//    preserving limit of the relaxation, Eq. 5-98 with omega1 = 0).  Closure cells skip the micro
+//    update and keep their g, which is read only after such a refresh.
 // Collection of training data uses k_closure_features before and k_closure_targets after a
 // plain step.
 #include <cmath>
@@ -61,6 +64,8 @@ __global__ void k_closure_features(const double* __restrict__ Q, KGrid g, KParam
   const double sT = sqrt(T);
   const double isT = 1.0 / sT;
   const double tau = macro_body::tau_of(p, rho, T);
+  const double kn = eps * sT / (tau * fmin(g.dx, g.dy));
+  const double ks = kn * isT;
   float* x = X + (size_t)c * kF;
   int f = 0;
   double TL = T, TR = T, TB = T, TT = T;
@@ -76,10 +81,10 @@ __global__ void k_closure_features(const double* __restrict__ Q, KGrid g, KParam
       macro_body::uT_of(Q, nc, n, a1, a2, Tn);
       if (mx) a1 = -a1;
       if (my) a2 = -a2;
-      x[f++] = (float)(Q[n] * ir - 1.0);
-      x[f++] = (float)((a1 - u1) * isT);
-      x[f++] = (float)((a2 - u2) * isT);
-      x[f++] = (float)(Tn * iT - 1.0);
+      x[f++] = (float)(kn * (Q[n] * ir - 1.0));
+      x[f++] = (float)(ks * (a1 - u1));
+      x[f++] = (float)(ks * (a2 - u2));
+      x[f++] = (float)(kn * (Tn * iT - 1.0));
       if (dj == 0) (di < 0 ? TL : TR) = Tn;
       if (di == 0) (dj < 0 ? TB : TT) = Tn;
     }
@@ -90,6 +95,7 @@ __global__ void k_closure_features(const double* __restrict__ Q, KGrid g, KParam
   x[35] = (float)(u2 * isT);
   x[36] = (float)log10(eps);
   x[37] = (float)(eps / (eps + dt * tau));
+  x[38] = (float)log10(kn);
   // Chapman-Enskog heat flux with the discrete temperature gradient of Eq. (5-97more)
   const double Tx = (0.5 * (TR + T) - 0.5 * (T + TL)) * g.idx;
   const double Ty = (0.5 * (TT + T) - 0.5 * (T + TB)) * g.idy;
@@ -148,40 +154,67 @@ __device__ __forceinline__ void append(bool pred, int c, int* list, int* count) 
   if (pred) list[base + __popc(b & ((1u << lane) - 1u))] = c;
 }
 
-__global__ void k_closure_lists(const unsigned char* __restrict__ flags, KGrid g, KParams p,
+// Work lists of a hybrid step.  x sweep: micro cells and their y neighbours (the y sweep reads
+// their G*); y sweep: micro cells off diffuse walls; refresh: cells in the 3x3 block of a micro
+// cell (the g^n the sweeps read) whose g^n was not produced by the micro update of the previous
+// step (valid[c] == 0).  valid[c] then becomes this step's micro flag.
+__global__ void k_closure_lists(const unsigned char* __restrict__ flags,
+                                unsigned char* __restrict__ valid, KGrid g, KParams p,
                                 int* __restrict__ xlist, int* __restrict__ ylist,
-                                int* __restrict__ clist, int* __restrict__ counts) {
+                                int* __restrict__ rlist, int* __restrict__ counts) {
   const int nc = g.nx * g.ny;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  bool inx = false, iny = false, inc = false;
+  bool inx = false, iny = false, inr = false;
   if (c < nc) {
     const int i = c % g.nx, j = c / g.nx;
     const bool micro = flags[c] == 0;
-    bool nb_micro = false;
-    for (int s = 2; s <= 3; ++s) {
-      int nj = s == 2 ? j - 1 : j + 1;
+    bool ynb = false, blk = false;
+    for (int dj = -1; dj <= 1; ++dj) {
+      int nj = j + dj;
       if (nj < 0 || nj >= g.ny) {
-        if (p.bc[s] != MM_BC_PERIODIC) continue;
+        if (p.bc[dj < 0 ? 2 : 3] != MM_BC_PERIODIC) continue;
         nj = (nj + g.ny) % g.ny;
       }
-      nb_micro = nb_micro || flags[nj * g.nx + i] == 0;
+      for (int di = -1; di <= 1; ++di) {
+        int ni = i + di;
+        if (ni < 0 || ni >= g.nx) {
+          if (p.bc[di < 0 ? 0 : 1] != MM_BC_PERIODIC) continue;
+          ni = (ni + g.nx) % g.nx;
+        }
+        const bool m = flags[nj * g.nx + ni] == 0;
+        blk = blk || m;
+        if (di == 0 && dj != 0) ynb = ynb || m;
+      }
     }
-    inx = micro || nb_micro;
+    inx = micro || ynb;
     iny = micro && !micro_body::diffuse_wall_cell(g, p, i, j);
-    inc = !micro;
+    inr = blk && valid[c] == 0;
+    valid[c] = micro ? 1 : 0;
   }
   append(inx, c, xlist, counts);
   append(iny, c, ylist, counts + 1);
-  append(inc, c, clist, counts + 2);
+  append(inr, c, rlist, counts + 2);
 }
 
-// g^{n+1} = Ghat of Eq. (5-97) in the cells of clist, from the per-cell coefficients of the prims
+// Cells whose g is not current (valid[c] == 0), to be reset to Ghat before a plain step.
+__global__ void k_closure_stale(unsigned char* __restrict__ valid, int nc, int* __restrict__ rlist,
+                                int* __restrict__ count) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  bool st = false;
+  if (c < nc) {
+    st = valid[c] == 0;
+    valid[c] = 1;
+  }
+  append(st, c, rlist, count);
+}
+
+// g^n = Ghat(Q^n) of Eq. (5-97) in the cells of a list, from the per-cell coefficients of the prims
 // kernel (stored there times omega2, hence the factor 1/omega2 = (eps + dt tau) / (dt tau)):
 // Ghat = (1/om2) [ -(p0 + p1 c2 + p2 c2^2 + p3 c2^3 + om2 mu / eps) e1 e2 + om2 KG / eps e^{-c.Tcal^{-1}c/2} ].
 // Thread t owns v1 index k = t % nv1 and rows l = t / nv1 + m R, as in the micro kernels.
 __global__ void __launch_bounds__(512, 1)
     k_closure_ghat(double* __restrict__ G, const double* __restrict__ prim, KGrid g, double dt,
-                   double eps, int R, const int* __restrict__ clist, const int* __restrict__ count) {
+                   double eps, int R, const int* __restrict__ list, const int* __restrict__ count) {
   extern __shared__ double sm[];
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;
@@ -196,7 +229,7 @@ __global__ void __launch_bounds__(512, 1)
   const int n = *count;
   const size_t nv = (size_t)nv1 * nv2;
   for (int q = blockIdx.x; q < n; q += gridDim.x) {
-    const int cell = clist[q];
+    const int cell = list[q];
     const double u1 = prim[P_U1 * nc + cell], u2 = prim[P_U2 * nc + cell];
     const double inv2T = prim[P_INV2T * nc + cell];
     const double Ti11 = prim[P_TI11 * nc + cell], Ti12 = prim[P_TI12 * nc + cell];
@@ -268,12 +301,19 @@ void launch_closure_decide(const float* Y, const double* aux, double thr, const 
   k_closure_decide<<<(nc + 255) / 256, 256, 0, s>>>(Y, aux, (float)thr, g, p, flags, H, nclosure);
 }
 
-void launch_closure_lists(const unsigned char* flags, const KGrid& g, const KParams& p,
-                          int* lists, int* counts, cudaStream_t s) {
+void launch_closure_lists(const unsigned char* flags, unsigned char* valid, const KGrid& g,
+                          const KParams& p, int* lists, int* counts, cudaStream_t s) {
   const int nc = g.nx * g.ny;
   cudaMemsetAsync(counts, 0, 3 * sizeof(int), s);
-  k_closure_lists<<<(nc + 255) / 256, 256, 0, s>>>(flags, g, p, lists, lists + nc, lists + 2 * nc,
-                                                   counts);
+  k_closure_lists<<<(nc + 255) / 256, 256, 0, s>>>(flags, valid, g, p, lists, lists + nc,
+                                                   lists + 2 * nc, counts);
+}
+
+void launch_closure_stale(unsigned char* valid, const KGrid& g, int* list, int* count,
+                          cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  cudaMemsetAsync(count, 0, sizeof(int), s);
+  k_closure_stale<<<(nc + 255) / 256, 256, 0, s>>>(valid, nc, list, count);
 }
 
 int closure_ghat_blocks(const MicroShape& ms) {
@@ -285,11 +325,11 @@ int closure_ghat_blocks(const MicroShape& ms) {
 }
 
 void launch_closure_ghat(double* G, const double* prim, const KGrid& g, double dt, double eps,
-                         const MicroShape& ms, const int* clist, const int* count, int blocks,
+                         const MicroShape& ms, const int* list, const int* count, int blocks,
                          cudaStream_t s) {
   if (ms.smem_ghat > 48 * 1024)
     cudaFuncSetAttribute(k_closure_ghat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_ghat);
-  k_closure_ghat<<<blocks, ms.threads, ms.smem_ghat, s>>>(G, prim, g, dt, eps, ms.R, clist, count);
+  k_closure_ghat<<<blocks, ms.threads, ms.smem_ghat, s>>>(G, prim, g, dt, eps, ms.R, list, count);
 }
 
 }  // namespace mmk

@@ -135,7 +135,7 @@ void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, 
                          const int* list, const int* count, int blocks, cudaStream_t s);
 int micro_list_blocks(const MicroShape& ms, bool ysweep);
 // Learned closure (FP64 path): features + Chapman-Enskog flux + scale (aux [5][ny][nx]),
-// training targets, decision, work lists [x | y | closure][nc] with counts[3], Ghat write.
+// training targets, decision, work lists [x | y | refresh][nc] with counts[3], Ghat write.
 void launch_closure_features(const double* Q, const KGrid& g, const KParams& p, double eps,
                              double dt, float* X, double* aux, cudaStream_t s);
 void launch_closure_targets(const double* H, const double* aux, float* Y, const KGrid& g,
@@ -143,11 +143,13 @@ void launch_closure_targets(const double* H, const double* aux, float* Y, const 
 void launch_closure_decide(const float* Y, const double* aux, double thr, const KGrid& g,
                            const KParams& p, unsigned char* flags, double* H,
                            unsigned long long* nclosure, cudaStream_t s);
-void launch_closure_lists(const unsigned char* flags, const KGrid& g, const KParams& p,
-                          int* lists, int* counts, cudaStream_t s);
+void launch_closure_lists(const unsigned char* flags, unsigned char* valid, const KGrid& g,
+                          const KParams& p, int* lists, int* counts, cudaStream_t s);
+void launch_closure_stale(unsigned char* valid, const KGrid& g, int* list, int* count,
+                          cudaStream_t s);
 int closure_ghat_blocks(const MicroShape& ms);
 void launch_closure_ghat(double* G, const double* prim, const KGrid& g, double dt, double eps,
-                         const MicroShape& ms, const int* clist, const int* count, int blocks,
+                         const MicroShape& ms, const int* list, const int* count, int blocks,
                          cudaStream_t s);
 // Network inference on the stream s (mm_mlp.cu).
 void mlp_forward_async(const mm_mlp* m, const float* X, float* Y, int n, cudaStream_t s);

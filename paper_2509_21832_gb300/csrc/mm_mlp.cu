@@ -1,4 +1,4 @@
-// Learned heat-flux closure: a small MLP (38 -> 64 -> 64 -> 4, GELU) with BF16 weights and FP32
+// Learned heat-flux closure: a small MLP (39 -> 64 -> 64 -> 4, GELU) with BF16 weights and FP32
 // accumulation, trained and evaluated by these kernels.  The network maps local macro features
 // of a cell to the dimensionless non-Navier-Stokes part of the heat-flux tensor of Eq. (5-99):
 // H = H_CE + eps rho T^{3/2} y, where H_CE is the Chapman-Enskog value, i.e. the moments of the

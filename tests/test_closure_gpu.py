@@ -26,9 +26,20 @@ def _torch():
 
 def _norm(seed, ystd=1.0):
     rng = np.random.default_rng(seed)
-    return np.concatenate([rng.standard_normal(38) * 0.1, np.exp(rng.uniform(-0.5, 0.5, 38)),
+    return np.concatenate([rng.standard_normal(39) * 0.1, np.exp(rng.uniform(-0.5, 0.5, 39)),
                            rng.standard_normal(4) * 0.1 * ystd,
                            ystd * np.exp(rng.uniform(-0.5, 0.5, 4))]).astype(np.float32)
+
+
+def _data_norm(X, seed):
+    """Normalisation standardising the features of a case (as a trained network's does), with
+    outputs scaled to ~1e-6."""
+    # spreads floored at 1e-3 |mean|, so that the FP32 rounding of a feature moves its
+    # standardised value by at most ~6e-5
+    sx = np.maximum(X.std(axis=0), 1e-3 * np.abs(X.mean(axis=0)))
+    isx = np.where(sx > 1e-12, 1.0 / np.maximum(sx, 1e-12), 1.0)
+    n = _norm(seed, ystd=1e-6)
+    return np.concatenate([X.mean(axis=0), isx, n[78:]]).astype(np.float32)
 
 
 def _params(seed):
@@ -48,7 +59,7 @@ def test_mlp_forward_and_bf16_weights_match_oracle():
     assert np.array_equal(master, params)
     assert np.array_equal(wb.astype(np.float64), M.bf16_round(params))  # RNE on both sides
     for n in (1, 127, 1000, 4099):
-        X = (np.random.default_rng(n).standard_normal((n, 38)) * 1.3).astype(np.float32)
+        X = (np.random.default_rng(n).standard_normal((n, 39)) * 1.3).astype(np.float32)
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.empty((n, 4), dtype=torch.float32, device="cuda")
         mlp.forward(Xd, Yd)
@@ -65,7 +76,7 @@ def test_mlp_gradient_matches_oracle():
     mlp = api.MLP(params, norm)
     for n in (1, 333, 2048):
         rng = np.random.default_rng(10 + n)
-        X = (rng.standard_normal((n, 38)) * 1.1).astype(np.float32)
+        X = (rng.standard_normal((n, 39)) * 1.1).astype(np.float32)
         T = rng.standard_normal((n, 4)).astype(np.float32)
         L, g = mlp.grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
         Lo, go = M.loss_and_grad(M.bf16_round(params), norm.astype(np.float64),
@@ -85,7 +96,7 @@ def test_adam_step_matches_oracle():
     params, norm = _params(5), _norm(6)
     mlp = api.MLP(params, norm)
     rng = np.random.default_rng(7)
-    X = rng.standard_normal((900, 38)).astype(np.float32)
+    X = rng.standard_normal((900, 39)).astype(np.float32)
     T = rng.standard_normal((900, 4)).astype(np.float32)
     lr = 1e-3
     for t in (1, 2):
@@ -118,7 +129,7 @@ def test_features_and_chapman_enskog_flux_match_oracle(name, bc):
     p = I.Params(nu=-0.5, bc=bc, tau_model=I.TAU_PRESSURE)
     Q = I.smooth_state(g, 21, amp=0.25, umax=0.3, aniso=0.1)
     eps, dt = 2e-2, 1e-3
-    X = torch.empty((g.ncell, 38), dtype=torch.float32, device="cuda")
+    X = torch.empty((g.ncell, 39), dtype=torch.float32, device="cuda")
     aux = torch.empty((5, g.ny, g.nx), dtype=torch.float64, device="cuda")
     with api.Solver(g, p) as s:
         s.set_state(Q)
@@ -133,14 +144,19 @@ def test_features_and_chapman_enskog_flux_match_oracle(name, bc):
     assert np.max(np.abs(A[4] - scale) / scale) <= 1e-15, name
 
 
-def _gap_threshold(ind, interior):
-    """A threshold in the widest gap of the middle half of the sorted indicator values, so that
-    FP32 and FP64 evaluations of the network decide every cell alike."""
+def _gap_thresholds(ind, interior):
+    """Thresholds in the gaps of the middle half of the sorted indicator values, widest gap
+    first (relative width above 1e-3), so that FP32 and FP64 evaluations of the network decide
+    every cell alike."""
     v = np.sort(ind[interior])
     lo, hi = len(v) // 4, 3 * len(v) // 4
-    k = lo + int(np.argmax(np.diff(v[lo:hi + 1])))
-    thr = 0.5 * (v[k] + v[k + 1])
-    return thr, (v[k + 1] - v[k]) / thr
+    d = np.diff(v[lo:hi + 1])
+    out = []
+    for k in np.argsort(-d):
+        thr = 0.5 * (v[lo + k] + v[lo + k + 1])
+        if d[k] / thr > 1e-3:
+            out.append(thr)
+    return out
 
 
 HYBRID_CASES = [
@@ -151,51 +167,89 @@ HYBRID_CASES = [
 
 
 @pytest.mark.parametrize("name,gk,bc,eps", HYBRID_CASES)
-def test_hybrid_step_matches_oracle(name, gk, bc, eps):
+def test_hybrid_steps_match_oracle(name, gk, bc, eps):
+    """Two hybrid steps (the second one refreshes the g its sweeps read) against the oracle.  The
+    network's outputs are scaled to ~1e-6 so that the heat flux it contributes differs between
+    the FP32 kernels and the FP64 reference far below the macro-field tolerance; the threshold
+    sits in a gap of the indicator values of both steps."""
     g = I.Grid(**gk)
     p = I.Params(nu=-0.5, bc=bc)
     Q = I.smooth_state(g, 31, amp=0.2, umax=0.25, aniso=0.05)
     G0 = I.seeded_g(g, 32, amp=0.02)
     dt = 0.5 / (8.0 * g.nx + 8.0 * g.ny)
-    params, norm = _params(8), _norm(9)
+    X, _, _ = C.features(g, p, Q, eps, dt)
+    params, norm = _params(8), _data_norm(X, 9)
     wq = M.bf16_round(params)
     net = lambda X: M.forward(wq, norm.astype(np.float64), X)
-    X, Hce, scale = C.features(g, p, Q, eps, dt)
-    ind = np.max(np.abs(net(X)), axis=1).reshape(g.ny, g.nx)
     interior = ~C.boundary_cells(g, p)
-    thr, gap = _gap_threshold(ind, interior)
-    assert gap > 1e-3, gap
-    Qo, Go, Ho, fo, _ = C.hybrid_step(g, p, Q, G0, dt, eps, net, thr)
-    assert 0 < fo.sum() < interior.sum()
+    ind0 = np.max(np.abs(net(X)), axis=1).reshape(g.ny, g.nx)
+    ref = None
+    for thr in _gap_thresholds(ind0, interior):
+        Qo, Go, Ho, fo, io, ro = C.hybrid_run(g, p, Q, G0, dt, eps, net, thr, nsteps=2)
+        sep = min(np.min(np.abs(i[interior] - thr)) for i in io) / thr
+        if sep > 5e-4 and 0 < fo[1].sum() < interior.sum():
+            ref = (thr, Qo, Go, Ho, fo, ro)
+            break
+    assert ref is not None
+    thr, Qo, Go, Ho, fo, ro = ref
+    assert ro[1].sum() > 0  # the second step refreshes cells
     mlp = api.MLP(params, norm)
     with api.Solver(g, p) as s:
         s.set_state(Q, G0)
         s.set_closure(mlp, thr)
-        s.step(dt, eps, 1)
+        s.step(dt, eps, 2)
         s.sync()
         Qg, Hg = s.get_moments()
         Gg = s.get_g()
         fg = s.closure_flags().astype(bool)
         ncl, ncs = s.closure_stats()
-    assert np.array_equal(fg, fo), name
-    assert ncl == fo.sum() and ncs == g.ncell
-    rho = Q[0] if Q.ndim == 3 else Q.reshape(6, g.ny, g.nx)[0]
+    assert np.array_equal(fg, fo[1]), name
+    assert ncl == fo[0].sum() + fo[1].sum() and ncs == 2 * g.ncell
+    eq = q_rel_err(Qg, Qo)
+    assert np.all(eq <= 1e-12), (name, eq)
+    rho = np.asarray(Q).reshape(6, g.ny, g.nx)[0]
     gfl = 64 * ULP * np.max(rho) / eps
     gerr = np.max(np.abs(Gg - Go))
     assert gerr <= max(1e-11 * np.max(np.abs(Go)), gfl), (name, gerr)
-    mic = ~fo
-    herr_m = np.max(np.abs(Hg[:, mic] - Ho[:, mic]))
-    assert herr_m <= max(1e-11 * np.max(np.abs(Ho)), 64 * ULP * 4.0 * np.max(rho) * 2), (name, herr_m)
-    # closure cells: H = H_CE + s y with y from the FP32 network
-    yo = net(X).T.reshape(4, g.ny, g.nx)
-    herr_c = np.max(np.abs(Hg[:, fo] - Ho[:, fo]))
-    tol_c = 2e-5 * np.max(scale) * (1.0 + np.max(np.abs(yo)))
-    assert herr_c <= tol_c, (name, herr_c, tol_c)
-    dH = max(herr_m, herr_c)
-    eq = q_rel_err(Qg, Qo)
-    rho_max = np.max(np.abs(Qo.reshape(6, -1)[0]))
-    tol_q = 1e-12 + 4.0 * dt * max(g.nx, g.ny) * dH / rho_max
-    assert np.all(eq <= tol_q), (name, eq, tol_q)
+    herr = np.max(np.abs(Hg - Ho))
+    assert herr <= max(1e-11 * np.max(np.abs(Ho)), 64 * ULP * 8.0 * np.max(rho)), (name, herr)
+    mlp.close()
+
+
+def test_switching_the_closure_off_resets_stale_g():
+    """After hybrid steps, switching the closure off and stepping is the oracle's plain step from
+    the hybrid state with every non-current g reset to Ghat(Q^n)."""
+    g = I.Grid(nx=12, ny=10, nv1=16, nv2=16)
+    p = I.Params(nu=-0.5, bc=(I.SPECULAR,) * 4)
+    Q = I.smooth_state(g, 51, amp=0.2, umax=0.25, aniso=0.05)
+    G0 = I.seeded_g(g, 52, amp=0.02)
+    dt, eps = 0.5 / (16.0 * 12 + 16.0 * 10), 1e-2
+    X, _, _ = C.features(g, p, Q, eps, dt)
+    params, norm = _params(14), _data_norm(X, 15)
+    wq = M.bf16_round(params)
+    net = lambda X: M.forward(wq, norm.astype(np.float64), X)
+    interior = ~C.boundary_cells(g, p)
+    ind0 = np.max(np.abs(net(X)), axis=1).reshape(g.ny, g.nx)
+    for thr in _gap_thresholds(ind0, interior):
+        Q1, G1, H1, fo, io, ro = C.hybrid_run(g, p, Q, G0, dt, eps, net, thr, nsteps=2)
+        if min(np.min(np.abs(i[interior] - thr)) for i in io) / thr > 5e-4:
+            break
+    stale = fo[1]  # closure cells of the last hybrid step
+    none = np.zeros_like(stale)
+    Qo, Go, Ho = O.step_closure(g, p, Q1, G1, dt, eps, none, stale, np.zeros((4, g.ny, g.nx)))
+    mlp = api.MLP(params, norm)
+    with api.Solver(g, p) as s:
+        s.set_state(Q, G0)
+        s.set_closure(mlp, thr)
+        s.step(dt, eps, 2)
+        s.set_closure(None, 0.0)
+        s.step(dt, eps, 1)
+        s.sync()
+        Qg, Hg = s.get_moments()
+        Gg = s.get_g()
+    assert np.all(q_rel_err(Qg, Qo) <= 1e-12)
+    rho = np.asarray(Q).reshape(6, g.ny, g.nx)[0]
+    assert np.max(np.abs(Gg - Go)) <= max(1e-11 * np.max(np.abs(Go)), 64 * ULP * np.max(rho) / eps)
     mlp.close()
 
 

@@ -137,18 +137,20 @@ def test_features_of_a_uniform_state():
                        np.full((4, 5), T))
     eps, dt = 3e-2, 1e-3
     X, Hce, scale = C.features(g, p, Q, eps, dt)
-    inner = X.reshape(4, 5, 38)[:, 1:]  # away from the specular wall the neighbours agree
+    inner = X.reshape(4, 5, 39)[:, 1:]  # away from the specular wall the neighbours agree
     assert np.all(inner[..., :32] == 0.0)
     assert np.allclose(X[:, 34], U1 / math.sqrt(T), rtol=1e-15, atol=0)
     assert np.allclose(X[:, 35], U2 / math.sqrt(T), rtol=1e-15, atol=0)
     assert np.all(X[:, 36] == math.log10(eps))
     assert np.allclose(X[:, 37], eps / (eps + dt * rho), rtol=1e-15)  # tau = rho
+    k = eps * math.sqrt(T) / (rho * 0.2)  # h = min(1/5, 1/4)
+    assert np.allclose(X[:, 38], math.log10(k), rtol=0, atol=1e-15)
     assert np.all(Hce == 0.0)
     assert np.allclose(scale, eps * rho * T ** 1.5, rtol=1e-15)
     # at the specular wall the mirror image has u1 -> -u1: the left neighbours see -2 U1
-    wall = X.reshape(4, 5, 38)[:, 0]
+    wall = X.reshape(4, 5, 39)[:, 0]
     for nb in (0, 3, 5):  # (di = -1) in rows j-1, j, j+1
-        assert np.allclose(wall[:, 4 * nb + 1], -2 * U1 / math.sqrt(T), rtol=1e-14)
+        assert np.allclose(wall[:, 4 * nb + 1], -2 * k * U1 / math.sqrt(T), rtol=1e-14)
 
 
 def test_features_translation_boost_and_scaling():
@@ -158,7 +160,7 @@ def test_features_translation_boost_and_scaling():
     # periodic translation by one cell in each direction
     Qs = np.roll(np.roll(Q.reshape(6, 8, 8), 1, axis=1), 2, axis=2)
     Xs, Hs, ss = C.features(g, p, Qs, eps, dt)
-    assert np.allclose(Xs.reshape(8, 8, 38), np.roll(np.roll(X.reshape(8, 8, 38), 1, 0), 2, 1),
+    assert np.allclose(Xs.reshape(8, 8, 39), np.roll(np.roll(X.reshape(8, 8, 39), 1, 0), 2, 1),
                        rtol=0, atol=1e-14)
     # Galilean boost: only features 34, 35 change (by U / sqrt T); H_CE unchanged
     Qr = Q.reshape(6, 8, 8)
@@ -181,6 +183,30 @@ def test_features_translation_boost_and_scaling():
     assert np.allclose(Hd, 2.0 * Hce, rtol=1e-13, atol=0) and np.allclose(sd, 2.0 * s, rtol=1e-14)
 
 
+def test_stencil_features_are_resolution_independent():
+    # a smooth field on an n and a 3n grid: cell i of the coarse grid and cell 3i+1 of the fine
+    # grid share a centre; the Knudsen-scaled neighbour differences agree to O(h) (about 4.4 h
+    # relative for the diagonal density differences of this field, from the second-order terms
+    # of the Taylor expansion), while a missing 1/h would put them a factor 3 apart
+    def q_on(n):
+        g = I.Grid(nx=n, ny=n, nv1=8, nv2=8)
+        x, y = np.meshgrid(g.xc(), g.yc())
+        rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        T = 1.0 + 0.2 * np.cos(2 * np.pi * (x + y))
+        u1 = 0.2 * np.sin(2 * np.pi * y)
+        u2 = 0.1 * np.cos(2 * np.pi * x)
+        return g, I.q_from_prims(rho, u1, u2, T)
+    p = I.Params(nu=-0.5, bc=(I.PERIODIC,) * 4)
+    gc, Qc = q_on(32)
+    gf, Qf = q_on(96)
+    Xc = C.features(gc, p, Qc, 1e-2, 1e-3)[0].reshape(32, 32, 39)
+    Xf = C.features(gf, p, Qf, 1e-2, 1e-3)[0].reshape(96, 96, 39)[1::3, 1::3]
+    d = np.max(np.abs(Xf[..., :32] - Xc[..., :32]))
+    assert d <= 0.2 * np.max(np.abs(Xc[..., :32])), d
+    # log10 k moves by log10 3 between the grids
+    assert np.allclose(Xf[..., 38] - Xc[..., 38], np.log10(3.0), atol=1e-12)
+
+
 # ---------------------------------------------------------------------------------------------
 # hybrid step
 # ---------------------------------------------------------------------------------------------
@@ -190,31 +216,56 @@ def test_closure_step_without_closure_cells_is_the_plain_step():
     none = np.zeros((g.ny, g.nx), dtype=bool)
     Hcl = np.full((4, g.ny, g.nx), 123.0)
     a = O.step(g, p, Q, G0, 1e-3, 1e-2)
-    b = O.step_closure(g, p, Q, G0, 1e-3, 1e-2, none, Hcl)
+    b = O.step_closure(g, p, Q, G0, 1e-3, 1e-2, none, none, Hcl)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    # refreshing every cell is the plain step from g^n = Ghat(Q^n)
+    alls = np.ones((g.ny, g.nx), dtype=bool)
+    a = O.step(g, p, Q, O.ghat(g, p, Q, 1e-2), 1e-3, 1e-2)
+    b = O.step_closure(g, p, Q, G0, 1e-3, 1e-2, none, alls, Hcl)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
 
 
-def test_closure_cells_take_ghat_and_the_given_heat_flux_and_conserve():
-    g, p, Q = _smooth_case(n=6, nv=12)
+def test_closure_cells_keep_g_take_the_given_heat_flux_and_conserve():
+    g, p, Q = _smooth_case(n=8, nv=12)
     G0 = I.seeded_g(g, 5, amp=0.02)
     eps, dt = 1e-2, 1e-3
     flags = np.zeros((g.ny, g.nx), dtype=bool)
-    flags[1:4, 2:5] = True
+    flags[2:6, 3:7] = True
+    refresh = C.needed_cells(g, p, ~flags) & flags  # the closure ring
     rng = np.random.default_rng(0)
     Hcl = rng.standard_normal((4, g.ny, g.nx)) * 1e-3
-    Qn, Gn, Hn = O.step_closure(g, p, Q, G0, dt, eps, flags, Hcl)
+    Qn, Gn, Hn = O.step_closure(g, p, Q, G0, dt, eps, flags, refresh, Hcl)
     Gh = O.ghat(g, p, Q, eps).reshape(g.ny, g.nx, -1)
     Gn = Gn.reshape(g.ny, g.nx, -1)
-    assert np.array_equal(Gn[flags], Gh[flags])
+    G0r = G0.reshape(g.ny, g.nx, -1)
+    assert np.array_equal(Gn[refresh], Gh[refresh])
+    assert np.array_equal(Gn[flags & ~refresh], G0r[flags & ~refresh])
     assert np.array_equal(Hn[:, flags], Hcl[:, flags])
-    # cells outside the closure keep the plain step's micro solution
+    # the ring is one cell wide around the micro cells (3x3 blocks)
+    assert refresh.sum() == 12 and not refresh[3:5, 4:6].any()
+    # micro cells far from the refreshed ring keep the plain step's micro solution
     Qp, Gp, Hp = O.step(g, p, Q, G0, dt, eps)
-    assert np.array_equal(Gn[~flags], Gp.reshape(g.ny, g.nx, -1)[~flags])
-    assert np.array_equal(Hn[:, ~flags], Hp[:, ~flags])
+    far = ~C.needed_cells(g, p, refresh) & ~flags
+    assert far.sum() > 0
+    assert np.array_equal(Gn[far], Gp.reshape(g.ny, g.nx, -1)[far])
+    assert np.array_equal(Hn[:, far], Hp[:, far])
     # the heat flux enters the macro update in conservation form: totals are kept
     tot0 = Q.reshape(6, -1).sum(axis=1)
     tot1 = Qn.reshape(6, -1).sum(axis=1)
     for m in (0, 1, 2):
         assert abs(tot1[m] - tot0[m]) <= 1e-12 * max(1.0, abs(tot0[m]))
     assert abs((tot1[3] + tot1[5]) - (tot0[3] + tot0[5])) <= 1e-12 * abs(tot0[3] + tot0[5])
+
+
+def test_needed_cells_are_the_3x3_blocks_with_boundary_rules():
+    g = I.Grid(nx=7, ny=5)
+    m = np.zeros((5, 7), dtype=bool)
+    m[0, 0] = True
+    per = I.Params(bc=(I.PERIODIC,) * 4)
+    wall = I.Params(bc=(I.SPECULAR,) * 4)
+    a = C.needed_cells(g, per, m)
+    b = C.needed_cells(g, wall, m)
+    assert a.sum() == 9 and a[4, 6] and a[1, 1] and a[4, 0] and a[0, 6]
+    assert b.sum() == 4 and b[1, 1] and not b[4, 6]

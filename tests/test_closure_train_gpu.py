@@ -38,24 +38,24 @@ def _run(pb, nsteps, mlp=None, thr=None):
 
 
 def test_trained_closure_gain():
-    ds = closure.collect(closure.training_problems(n=128), warm_steps=10, every=12,
-                         samples_per_problem=8)
-    assert ds.X.shape[0] >= 10 * 8 * 128 * 128
+    # about 1.3e6 samples from 256^2 x 32^2 runs (five Knudsen numbers, two CFL numbers)
+    ds = closure.collect(closure.training_problems(n=256), warm_steps=10, every=12,
+                         samples_per_problem=8, keep=0.25)
+    assert ds.X.shape[0] >= 10 * 8 * 16384
     res = closure.train(ds, epochs=3, batch=8192, lr=2e-3, lr_final=1e-4, seed=0)
     first, last = res.losses[0][1], res.losses[-1][1]
     print("training: %d samples in %.2f s, %d steps in %.2f s, loss %.4g -> %.4g"
           % (ds.X.shape[0], ds.seconds, res.steps, res.seconds, first, last))
     assert last < 0.2 * first
-    pb = I.bump_specular(n=256, nv=32, eps=1e-2, seed=7)
-    nsteps = 100
+    # applied on a held-out problem of the 512^2 x 32^2 family
+    pb = I.bump_specular(n=512, nv=32, eps=1e-2, seed=7)
+    nsteps = 60
     Qp, tp, _ = _run(pb, nsteps)
     Qh, th, frac = _run(pb, nsteps, res.mlp, 1e-3)
-    Qn, tn, frac_n = _run(pb, nsteps, res.mlp, 1e30)  # every interior cell on the closure
-    l1 = lambda Q: np.sum(np.abs(Q[0] - Qp[0])) / np.sum(np.abs(Qp[0]))
-    print("plain %.2f ms/step; hybrid %.2f ms/step (x%.2f), closure fraction %.3f, L1 density "
-          "error %.3g; closure everywhere: L1 %.3g (fraction %.3f)"
-          % (tp / nsteps, th / nsteps, tp / th, frac, l1(Qh), l1(Qn), frac_n))
-    assert l1(Qh) <= 1e-3
+    l1 = np.sum(np.abs(Qh[0] - Qp[0])) / np.sum(np.abs(Qp[0]))
+    print("512^2 x 32^2, eps 1e-2: plain %.2f ms/step; hybrid %.2f ms/step (x%.2f), closure "
+          "fraction %.3f, L1 density error %.3g" % (tp / nsteps, th / nsteps, tp / th, frac, l1))
+    assert l1 <= 1e-3
     assert frac >= 0.3
     assert th < tp
     res.mlp.close()
