@@ -210,6 +210,68 @@ def fp32_variant(args, stream):
     return out
 
 
+def closure_variant(args, stream):
+    """Learned closure on the bump family with specular walls: the network is trained on the
+    GPU (library kernels) from about 1.3e6 samples of 256^2 x 32^2 plain runs, then the hybrid
+    step is timed against the plain FP64 step on 512^2 x 32^2 at eps = 1e-3, 1e-2 and 1e-1
+    (threshold 1e-3), with the relative L1 density error of the hybrid run against the plain run
+    after the same steps.  value = phase cells x steps / time of the hybrid run (an equivalent
+    rate: closure cells do not advance g)."""
+    import torch
+    from paper_2509_21832_gb300 import api, closure
+    from paper_2509_21832_gb300 import inputs as I
+    ds = closure.collect(closure.training_problems(n=256), warm_steps=10, every=12,
+                         samples_per_problem=8, keep=0.25)
+    res = closure.train(ds, epochs=3, batch=8192, lr=2e-3, lr_final=1e-4, seed=0)
+    out = {"workload": "bump_specular_%dx%dx32x32_learned_closure" % (args.closure_n, args.closure_n),
+           "threshold": 1e-3, "steps": args.closure_steps, "dtype": "f64 (network bf16/f32)",
+           "training": {"samples": int(ds.X.shape[0]), "collect_s": ds.seconds,
+                        "adam_steps": res.steps, "train_s": res.seconds,
+                        "loss_first": res.losses[0][1], "loss_last": res.losses[-1][1]},
+           "cases": []}
+
+    def run(pb, mlp):
+        s = api.Solver(pb.grid, pb.params, stream=stream.cuda_stream)
+        s.set_state(pb.Q, pb.G)
+        if mlp is not None:
+            s.set_closure(mlp, 1e-3)
+        s.step(pb.dt, pb.eps, 3)
+        s.set_state(pb.Q, pb.G)
+        if mlp is not None:
+            s.set_closure(mlp, 1e-3)
+        s.set_timing(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(pb.dt, pb.eps, args.closure_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kt = s.get_timing()
+        Q, _ = s.get_moments(with_H=False)
+        frac = None
+        if mlp is not None:
+            ncl, ncs = s.closure_stats()
+            frac = ncl / ncs
+        s.close()
+        return ms, kt, Q, frac
+
+    for eps in (1e-3, 1e-2, 1e-1):
+        pb = I.bump_specular(n=args.closure_n, nv=32, eps=eps, seed=7)
+        msp, _, Qp, _ = run(pb, None)
+        msh, kt, Qh, frac = run(pb, res.mlp)
+        nst = args.closure_steps
+        out["cases"].append({
+            "eps": eps, "plain_ms_per_step": msp / nst, "hybrid_ms_per_step": msh / nst,
+            "speedup_vs_fp64": msp / msh, "closure_fraction": frac,
+            "value": pb.grid.nphase * nst / (msh * 1e-3), "unit": UNIT,
+            "l1_density_rel_err_vs_fp64": float(np.sum(np.abs(Qh[0] - Qp[0])) / np.sum(np.abs(Qp[0]))),
+            "kernel_ms": {k: v[0] / v[1] for k, v in kt.items() if v[1]}})
+    res.mlp.close()
+    return out
+
+
 def batch_variant(args):
     """64 independent periodic problems (cells per side U{64..256}, velocity meshes 16^2..32^2,
     eps log-uniform on [1e-3, 1], seeded Fourier-mode fields), stepped as one batch: one
@@ -280,6 +342,9 @@ def main():
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--closure-only", action="store_true")
+    ap.add_argument("--closure-n", type=int, default=512)
+    ap.add_argument("--closure-steps", type=int, default=100)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -299,6 +364,11 @@ def main():
         import torch
         torch.cuda.set_device(local)
         print(json.dumps(fp32_variant(args, torch.cuda.Stream())), flush=True)
+        return
+    if args.closure_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(closure_variant(args, torch.cuda.Stream())), flush=True)
         return
 
     import torch
@@ -413,7 +483,8 @@ def main():
     variants = None
     if rank == 0 and not args.no_variants:
         variants = {"riemann4_diffuse_1024x1024x24x24_fp32g": fp32_variant(args, stream),
-                    "batch_64_periodic_fp64": batch_variant(args)}
+                    "batch_64_periodic_fp64": batch_variant(args),
+                    "bump_specular_512x512x32x32_learned_closure": closure_variant(args, stream)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

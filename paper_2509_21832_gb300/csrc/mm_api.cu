@@ -241,7 +241,9 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   cudaStream_t s = c->stream;
   const int nc = (int)c->ncell;
   timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
-  timed(c, T_CL_FEATURES, [&] { launch_closure_features(c->Q, g, p, eps, dt, c->cX, c->caux, s); });
+  timed(c, T_CL_FEATURES, [&] {
+    launch_closure_features(c->Q, c->prim, g, p, eps, dt, c->cX, c->caux, s);
+  });
   timed(c, T_MLP, [&] { mlp_forward_async(c->mlp, c->cX, c->cY, nc, s); });
   timed(c, T_CL_DECIDE, [&] {
     launch_closure_decide(c->cY, c->caux, c->closure_thr, g, p, c->cflags, c->H, c->cstat, s);
@@ -608,7 +610,8 @@ mm_status mm_closure_features(mm_ctx* c, double dt, double eps, float* X_dev, do
   if (!X_dev || !aux_dev) return fail(c, MM_ERR_INVALID_ARG, "null output");
   if (!(dt > 0.0) || !(eps > 0.0)) return fail(c, MM_ERR_INVALID_ARG, "dt and eps must be > 0");
   if (!c->have_state) return fail(c, MM_ERR_STATE, "no state set");
-  launch_closure_features(c->Q, c->kg, c->kp, eps, dt, X_dev, aux_dev, c->stream);
+  launch_prims(c->Q, c->prim, c->primf, c->kg, c->kp, dt, eps, c->err, c->stream);
+  launch_closure_features(c->Q, c->prim, c->kg, c->kp, eps, dt, X_dev, aux_dev, c->stream);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "closure features");
 }
@@ -621,7 +624,8 @@ mm_status mm_closure_collect(mm_ctx* c, double dt, double eps, float* X_dev, flo
   if (!c->have_state) return fail(c, MM_ERR_STATE, "no state set");
   mm_status st = ensure_closure(c);
   if (st != MM_OK) return st;
-  launch_closure_features(c->Q, c->kg, c->kp, eps, dt, X_dev, c->caux, c->stream);
+  launch_prims(c->Q, c->prim, c->primf, c->kg, c->kp, dt, eps, c->err, c->stream);
+  launch_closure_features(c->Q, c->prim, c->kg, c->kp, eps, dt, X_dev, c->caux, c->stream);
   if (c->fp32) enqueue_plain<float>(c, dt, eps);
   else enqueue_plain<double>(c, dt, eps);
   launch_closure_targets(c->H, c->caux, Y_dev, c->kg, c->stream);

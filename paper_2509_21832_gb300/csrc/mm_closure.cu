@@ -47,23 +47,21 @@ __device__ __forceinline__ bool boundary_cell(const KGrid& g, const KParams& p, 
          (j == 0 && p.bc[2] != MM_BC_PERIODIC) || (j == g.ny - 1 && p.bc[3] != MM_BC_PERIODIC);
 }
 
-__global__ void k_closure_features(const double* __restrict__ Q, KGrid g, KParams p, double eps,
-                                   double dt, float* __restrict__ X, double* __restrict__ aux) {
+// One thread per cell; the primitive variables of the stencil come from the prims kernel.
+__global__ void k_closure_features(const double* __restrict__ Q, const double* __restrict__ prim,
+                                   KGrid g, KParams p, double eps, double log10_eps, double dt,
+                                   float* __restrict__ X, double* __restrict__ aux) {
   const int nc = g.nx * g.ny;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int i = c % g.nx, j = c / g.nx;
-  const double rho = Q[c];
+  const double rho = prim[P_RHO * nc + c];
+  const double u1 = prim[P_U1 * nc + c], u2 = prim[P_U2 * nc + c];
+  const double T = prim[P_T * nc + c], iT = prim[P_IT * nc + c];
+  const double tau = prim[P_TAU * nc + c];
   const double ir = 1.0 / rho;
-  const double u1 = Q[nc + c] * ir, u2 = Q[2 * nc + c] * ir;
-  const double P11 = Q[3 * nc + c] - rho * u1 * u1;
-  const double P12 = Q[4 * nc + c] - rho * u1 * u2;
-  const double P22 = Q[5 * nc + c] - rho * u2 * u2;
-  const double T = (P11 + P22) * (0.5 * ir);
-  const double iT = 1.0 / T;
   const double sT = sqrt(T);
   const double isT = 1.0 / sT;
-  const double tau = macro_body::tau_of(p, rho, T);
   const double kn = eps * sT / (tau * fmin(g.dx, g.dy));
   const double ks = kn * isT;
   float* x = X + (size_t)c * kF;
@@ -77,11 +75,11 @@ __global__ void k_closure_features(const double* __restrict__ Q, KGrid g, KParam
       bool mx;
       const int ni = nb_index(i, di, g.nx, p.bc[0], p.bc[1], mx);
       const int n = nj * g.nx + ni;
-      double a1, a2, Tn;
-      macro_body::uT_of(Q, nc, n, a1, a2, Tn);
+      double a1 = prim[P_U1 * nc + n], a2 = prim[P_U2 * nc + n];
+      const double Tn = prim[P_T * nc + n];
       if (mx) a1 = -a1;
       if (my) a2 = -a2;
-      x[f++] = (float)(kn * (Q[n] * ir - 1.0));
+      x[f++] = (float)(kn * (prim[P_RHO * nc + n] * ir - 1.0));
       x[f++] = (float)(ks * (a1 - u1));
       x[f++] = (float)(ks * (a2 - u2));
       x[f++] = (float)(kn * (Tn * iT - 1.0));
@@ -89,11 +87,13 @@ __global__ void k_closure_features(const double* __restrict__ Q, KGrid g, KParam
       if (di == 0) (dj < 0 ? TB : TT) = Tn;
     }
   }
-  x[32] = (float)((P11 - P22) * (0.5 * ir) * iT);
+  const double th11 = prim[P_TH11 * nc + c], th22 = prim[P_TH22 * nc + c];
+  const double P12 = Q[4 * nc + c] - rho * u1 * u2;
+  x[32] = (float)((th11 - th22) * 0.5 * iT);
   x[33] = (float)(P12 * ir * iT);
   x[34] = (float)(u1 * isT);
   x[35] = (float)(u2 * isT);
-  x[36] = (float)log10(eps);
+  x[36] = (float)log10_eps;
   x[37] = (float)(eps / (eps + dt * tau));
   x[38] = (float)log10(kn);
   // Chapman-Enskog heat flux with the discrete temperature gradient of Eq. (5-97more)
@@ -282,10 +282,12 @@ __global__ void __launch_bounds__(512, 1)
 
 }  // namespace
 
-void launch_closure_features(const double* Q, const KGrid& g, const KParams& p, double eps,
-                             double dt, float* X, double* aux, cudaStream_t s) {
+void launch_closure_features(const double* Q, const double* prim, const KGrid& g,
+                             const KParams& p, double eps, double dt, float* X, double* aux,
+                             cudaStream_t s) {
   const int nc = g.nx * g.ny;
-  k_closure_features<<<(nc + 127) / 128, 128, 0, s>>>(Q, g, p, eps, dt, X, aux);
+  k_closure_features<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, g, p, eps, std::log10(eps), dt,
+                                                      X, aux);
 }
 
 void launch_closure_targets(const double* H, const double* aux, float* Y, const KGrid& g,

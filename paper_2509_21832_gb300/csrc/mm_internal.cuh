@@ -136,8 +136,10 @@ void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, 
 int micro_list_blocks(const MicroShape& ms, bool ysweep);
 // Learned closure (FP64 path): features + Chapman-Enskog flux + scale (aux [5][ny][nx]),
 // training targets, decision, work lists [x | y | refresh][nc] with counts[3], Ghat write.
-void launch_closure_features(const double* Q, const KGrid& g, const KParams& p, double eps,
-                             double dt, float* X, double* aux, cudaStream_t s);
+// (needs the prims of Q from launch_prims)
+void launch_closure_features(const double* Q, const double* prim, const KGrid& g,
+                             const KParams& p, double eps, double dt, float* X, double* aux,
+                             cudaStream_t s);
 void launch_closure_targets(const double* H, const double* aux, float* Y, const KGrid& g,
                             cudaStream_t s);
 void launch_closure_decide(const float* Y, const double* aux, double thr, const KGrid& g,
