@@ -35,6 +35,9 @@ UNIT = "phase-cell updates/s"
 FLOPS_MICRO_Y = 39.0
 FLOPS_STEP = 52.0
 BYTES_PER_PHASE_FP64 = 16.0 + 160.0 / 1024.0
+# DRAM traffic of k_micro_y per phase cell (32^2 velocity meshes), from the ncu capture in
+# profiles/k_micro_bump_specular_160x160x32x32_fp64.md: (214.0 + 172.7) MB / 26.2144 M.
+TRAFFIC_MICRO_Y_PER_PHASE_CELL = 386.7e6 / 26.2144e6
 
 
 def measured_peaks():
@@ -435,7 +438,12 @@ def main():
     achieved = FLOPS_MICRO_Y * nph / (ky_ms / ky_n * 1e-3) / 1e12
     hbm_gbs = BYTES_PER_PHASE_FP64 * nph * args.steps / (ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
+                "frac": achieved / fp64_peak,
+                # DRAM bytes per k_micro_y launch: ncu capture of the 160^2 x 32^2 case
+                # (read + write = 386.7 MB over 26.2 M phase cells), scaled by phase cells
+                "traffic": (TRAFFIC_MICRO_Y_PER_PHASE_CELL * nph
+                            if (pr.grid.nv1, pr.grid.nv2) == (32, 32) else None),
+                "traffic_unit": "bytes per launch",
                 "kernel": "micro_y", "peak_source": "FP64 peak from unit counts: 152 SMs x 4 "
                 "flop/clk x %.0f MHz" % sm_max,
                 "step_fp64_frac": FLOPS_STEP * nph * args.steps / (ms * 1e-3) / 1e12 / fp64_peak,
