@@ -117,6 +117,22 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(ms, pg, device):
+    """The slowest rank's time: every rank times the same K steps of its own replica."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, phase_cells, steps, ms):
+    """Whole-job rate of N independent replicas (weak scaling): all ranks' phase-cell updates
+    over the slowest rank's time."""
+    return world * phase_cells * steps / (ms * 1e-3)
+
+
 def cpu_baseline(pr, rows, steps):
     """Oracle (as it stands) on this host's cores over a strip of `rows` rows of the workload."""
     from oracle import oracle as O
@@ -422,13 +438,9 @@ def main():
     bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
     if set(clocks["reasons"]) & bad:
         ms, kt, clocks = timed_run(args.steps)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-
+    ms = max_over_ranks(ms, pg, "cuda")
     nph = pr.grid.nphase
-    value = world * nph * args.steps / (ms * 1e-3)
+    value = replica_value(world, nph, args.steps, ms)
     launches = sum(n for (_, n) in kt.values())
 
     peaks, peak_src = measured_peaks()
