@@ -91,7 +91,9 @@ __device__ __forceinline__ bool diffuse_wall_cell(const KGrid& g, const KParams&
 // ------------------------------------------------------------------------------------------
 // x sweep: Eqs. (zmicrox), (coeffs-2D-xdir), (zhat-2D-xdir), (update-micro-2D-xdir)
 // ------------------------------------------------------------------------------------------
-template <typename Tg>
+// NR > 0: every active thread owns exactly NR rows (nv2 == NR R); the upwind differences of pass
+// 1 stay in registers for pass 2.  NR = 0: any shape, differences recomputed in pass 2.
+template <typename Tg, int NR = 0>
 __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
                                                     Tg* __restrict__ Gout,
                                                     const double* __restrict__ prim, KGrid g,
@@ -135,14 +137,29 @@ __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
 
   // pass 1: velocity moments of Z
   double D0 = 0.0, D1 = 0.0, D2 = 0.0;
+  double dr[NR > 0 ? NR : 1];
   if (active) {
-    for (int l = r; l < nv2; l += R) {
-      const double gv = (double)Gc[l * nv1];
-      const double gu = up.zero ? 0.0 : (double)Gu[l * nv1];
-      const double d = gu - gv;
-      D0 += d;
-      D1 = fma(c2t[l], d, D1);
-      D2 = fma(c2q[l], d, D2);
+    if constexpr (NR > 0) {
+#pragma unroll
+      for (int m = 0; m < NR; ++m) {
+        const int l = r + m * R;
+        const double gv = (double)Gc[l * nv1];
+        const double gu = up.zero ? 0.0 : (double)Gu[l * nv1];
+        const double d = gu - gv;
+        dr[m] = d;
+        D0 += d;
+        D1 = fma(c2t[l], d, D1);
+        D2 = fma(c2q[l], d, D2);
+      }
+    } else {
+      for (int l = r; l < nv2; l += R) {
+        const double gv = (double)Gc[l * nv1];
+        const double gu = up.zero ? 0.0 : (double)Gu[l * nv1];
+        const double d = gu - gv;
+        D0 += d;
+        D1 = fma(c2t[l], d, D1);
+        D2 = fma(c2q[l], d, D2);
+      }
     }
   }
   const double sD0 = sig * D0;
@@ -162,14 +179,26 @@ __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
   // pass 2: G* = G - dt Z + dt Zhat
   if (active) {
     Tg* Go = Gout + (size_t)cell * nv + k;
-    for (int l = r; l < nv2; l += R) {
-      const double gv = (double)Gc[l * nv1];
-      const double gu = up.zero ? 0.0 : (double)Gu[l * nv1];
-      const double d = gu - gv;
-      double o = fma(lam, d, gv);
-      o = fma(ak, e2t[l], o);
-      o = fma(bk, qet[l], o);
-      Go[l * nv1] = (Tg)o;
+    if constexpr (NR > 0) {
+#pragma unroll
+      for (int m = 0; m < NR; ++m) {
+        const int l = r + m * R;
+        const double gv = (double)Gc[l * nv1];
+        double o = fma(lam, dr[m], gv);
+        o = fma(ak, e2t[l], o);
+        o = fma(bk, qet[l], o);
+        Go[l * nv1] = (Tg)o;
+      }
+    } else {
+      for (int l = r; l < nv2; l += R) {
+        const double gv = (double)Gc[l * nv1];
+        const double gu = up.zero ? 0.0 : (double)Gu[l * nv1];
+        const double d = gu - gv;
+        double o = fma(lam, d, gv);
+        o = fma(ak, e2t[l], o);
+        o = fma(bk, qet[l], o);
+        Go[l * nv1] = (Tg)o;
+      }
     }
   }
 }
@@ -199,7 +228,7 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
   double* c2c = tb + 2 * nv2;
   double* e2t = tb + 3 * nv2;
   double* g2t = tb + 4 * nv2;
-  double* v2t = tb + 5 * nv2;
+  double* w2t = tb + 5 * nv2;  // om1 - wlt: weight of the cell's own G* in the update
   double* s0t = tb + 6 * nv2;
   double* s1t = tb + 7 * nv2;
   double* s2t = tb + 8 * nv2;
@@ -219,26 +248,36 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
   const double om1 = prim[P_OM1 * nc + cell], om1kap = prim[P_OM1KAP * nc + cell];
   const double gam0 = prim[P_GAM0 * nc + cell], ome = prim[P_OME * nc + cell];
 
-  for (int l = t; l < nv2; l += blockDim.x) {
-    const double v2 = fma(l + 0.5, g.dv2, g.v2min);
-    const double c2 = v2 - u2;
-    const double q = c2 * c2;
-    const double e2 = expd(-q * inv2T);
-    const double av = fabs(v2);
-    const double sg = -av * g.idy;
-    c2t[l] = c2;
-    c2q[l] = q;
-    c2c[l] = q * c2;
-    e2t[l] = e2;
-    g2t[l] = expd(-0.5 * Ti22 * q);
-    v2t[l] = v2;
-    s0t[l] = sg;
-    s1t[l] = sg * c2;
-    s2t[l] = sg * q;
-    wlt[l] = om1 * (av * dtidy);
-    E1t[l] = e2 * c2;
-    E2t[l] = e2 * q;
-    E3t[l] = e2 * q * c2;
+  // l-dependent tables; nneg = number of rows with v2 < 0 (v2 increases with l), so that the
+  // upwind side of a row is an integer comparison
+  int nneg = 0;
+  for (int base = 0; base < nv2; base += blockDim.x) {
+    const int l = base + t;
+    bool neg = false;
+    if (l < nv2) {
+      const double v2 = fma(l + 0.5, g.dv2, g.v2min);
+      const double c2 = v2 - u2;
+      const double q = c2 * c2;
+      const double e2 = expd(-q * inv2T);
+      const double av = fabs(v2);
+      const double sg = -av * g.idy;
+      const double wl = om1 * (av * dtidy);
+      c2t[l] = c2;
+      c2q[l] = q;
+      c2c[l] = q * c2;
+      e2t[l] = e2;
+      g2t[l] = expd(-0.5 * Ti22 * q);
+      w2t[l] = om1 - wl;
+      s0t[l] = sg;
+      s1t[l] = sg * c2;
+      s2t[l] = sg * q;
+      wlt[l] = wl;
+      E1t[l] = e2 * c2;
+      E2t[l] = e2 * q;
+      E3t[l] = e2 * q * c2;
+      neg = v2 < 0.0;
+    }
+    nneg += __syncthreads_count(neg);
   }
 
   const Upwind ub = upwind_y(g, p, i, j, 2);  // upwind for v2 > 0
@@ -258,7 +297,7 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
   if (active) {
     for (int l = r; l < nv2; l += R) {
       const double gv = (double)Gc[l * nv1];
-      const bool top = v2t[l] < 0.0;
+      const bool top = l < nneg;
       const Upwind& u = top ? ut : ub;
       const Tg* Gu = top ? Gt : Gb;
       const int lu = u.mirror ? nv2 - 1 - l : l;
@@ -289,27 +328,28 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
   const double A0 = e1 * C0, A1 = e1 * C1, A2 = e1 * C2, A3 = e1 * C3;
   const double gam1 = gam0 * expd(-0.5 * Ti11 * c1q);
   const double c2r = fma(r + 0.5, g.dv2, g.v2min) - u2;
-  double x = expd(-Ti12 * c1 * c2r);
+  // gam1 times the cross factor exp(-Ti12 c1 c2) of row l, advanced by rat per row
+  double x = gam1 * expd(-Ti12 * c1 * c2r);
   const double rat = expd(-Ti12 * c1 * (R * g.dv2));
 
-  // pass 2: G^{n+1} = om1 (G* - dt Z* + dt Zhat*) + om2 Ghat, and its heat-flux moments
+  // pass 2: G^{n+1} = om1 (G* - dt Z* + dt Zhat*) + om2 Ghat, and its heat-flux moments;
+  // om1 G* - om1 dt Z* = wl G*_upwind + (om1 - wl) G*
   double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0;
   if (active) {
     Tg* Go = Gout + (size_t)cell * nv + k;
     for (int l = r; l < nv2; l += R) {
       const double gv = (double)Gc[l * nv1];
-      const bool top = v2t[l] < 0.0;
+      const bool top = l < nneg;
       const Upwind& u = top ? ut : ub;
       const Tg* Gu = top ? Gt : Gb;
       const int lu = u.mirror ? nv2 - 1 - l : l;
       const double gu = u.zero ? 0.0 : (double)Gu[lu * nv1];
-      const double d = gu - gv;
-      double o = fma(wlt[l], d, om1 * gv);
+      double o = fma(wlt[l], gu, w2t[l] * gv);
       o = fma(A0, e2t[l], o);
       o = fma(A1, E1t[l], o);
       o = fma(A2, E2t[l], o);
       o = fma(A3, E3t[l], o);
-      o = fma(gam1, g2t[l] * x, o);
+      o = fma(g2t[l], x, o);
       x *= rat;
       const Tg os = (Tg)o;
       Go[l * nv1] = os;

@@ -66,6 +66,7 @@ struct MicroShape {
   int threads;
   size_t smem_x, smem_y;
   size_t smem_ghat;  // closure Ghat kernel
+  int xrows;         // rows per thread of the register-resident x sweep (0: generic kernel)
 };
 MicroShape micro_shape(int nv1, int nv2);
 

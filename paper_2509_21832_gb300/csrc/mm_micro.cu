@@ -20,13 +20,13 @@ namespace {
 
 using namespace micro_body;
 
-template <typename Tg>
-__global__ void __launch_bounds__(512, 1) k_micro_x(const Tg* __restrict__ Gin,
+template <typename Tg, int NR>
+__global__ void __launch_bounds__(NR > 0 ? 256 : 512, 1) k_micro_x(const Tg* __restrict__ Gin,
                                                     Tg* __restrict__ Gout,
                                                     const double* __restrict__ prim, KGrid g,
                                                     KParams p, double dtidx, int R) {
   extern __shared__ double sm[];
-  micro_x_body<Tg>(Gin, Gout, prim, g, p, dtidx, R, blockIdx.x, sm);
+  micro_x_body<Tg, NR>(Gin, Gout, prim, g, p, dtidx, R, blockIdx.x, sm);
 }
 
 template <typename Tg>
@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_wall(const Tg* __restrict__ 
 }
 
 // The same sweeps over a list of cells: persistent CTAs take cells q = blockIdx.x + m gridDim.x.
-template <typename Tg>
-__global__ void __launch_bounds__(512, 1) k_micro_x_list(const Tg* __restrict__ Gin,
+template <typename Tg, int NR>
+__global__ void __launch_bounds__(NR > 0 ? 256 : 512, 1) k_micro_x_list(const Tg* __restrict__ Gin,
                                                          Tg* __restrict__ Gout,
                                                          const double* __restrict__ prim, KGrid g,
                                                          KParams p, double dtidx, int R,
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(512, 1) k_micro_x_list(const Tg* __restrict__ 
   extern __shared__ double sm[];
   const int n = *count;
   for (int q = blockIdx.x; q < n; q += gridDim.x) {
-    micro_x_body<Tg>(Gin, Gout, prim, g, p, dtidx, R, list[q], sm);
+    micro_x_body<Tg, NR>(Gin, Gout, prim, g, p, dtidx, R, list[q], sm);
     __syncthreads();
   }
 }
@@ -107,6 +107,8 @@ __global__ void k_f32_to_f64(const float* __restrict__ in, double* __restrict__ 
 
 }  // namespace
 
+int x_rows(const MicroShape& ms, int nv2);
+
 MicroShape micro_shape(int nv1, int nv2) {
   MicroShape ms{1, 32, 0, 0};
   double best = -1.0;
@@ -126,7 +128,36 @@ MicroShape micro_shape(int nv1, int nv2) {
   ms.smem_x = sizeof(double) * (micro_body::kRed + 4 * (size_t)nv2);
   ms.smem_y = sizeof(double) * (micro_body::kRed + micro_body::kYTables * (size_t)nv2);
   ms.smem_ghat = sizeof(double) * 5 * (size_t)nv2;
+  ms.xrows = x_rows(ms, nv2);
   return ms;
+}
+
+// Rows per thread when the x sweep keeps its upwind differences in registers (the shapes of the
+// common velocity meshes: 32^2 with R = 1, 16^2 with R = 2, 24^2 with R = 4; CTAs of at most
+// 256 threads, so that a thread may hold up to 255 registers), else 0.
+int x_rows(const MicroShape& ms, int nv2) {
+  const int nr = nv2 % ms.R == 0 ? nv2 / ms.R : 0;
+  return ms.threads <= 256 && (nr == 32 || nr == 8 || nr == 6) ? nr : 0;
+}
+
+template <typename Tg, typename F>
+void with_x_kernel(int nr, F&& f) {
+  switch (nr) {
+    case 32: f(k_micro_x<Tg, 32>); break;
+    case 8: f(k_micro_x<Tg, 8>); break;
+    case 6: f(k_micro_x<Tg, 6>); break;
+    default: f(k_micro_x<Tg, 0>); break;
+  }
+}
+
+template <typename Tg, typename F>
+void with_x_list_kernel(int nr, F&& f) {
+  switch (nr) {
+    case 32: f(k_micro_x_list<Tg, 32>); break;
+    case 8: f(k_micro_x_list<Tg, 8>); break;
+    case 6: f(k_micro_x_list<Tg, 6>); break;
+    default: f(k_micro_x_list<Tg, 0>); break;
+  }
 }
 
 int micro_list_blocks(const MicroShape& ms, bool ysweep) {
@@ -138,9 +169,11 @@ int micro_list_blocks(const MicroShape& ms, bool ysweep) {
       cudaFuncSetAttribute(k_micro_y_list<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_y);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_micro_y_list<double>, ms.threads, ms.smem_y);
   } else {
-    if (ms.smem_x > 48 * 1024)
-      cudaFuncSetAttribute(k_micro_x_list<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_x);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_micro_x_list<double>, ms.threads, ms.smem_x);
+    with_x_list_kernel<double>(ms.xrows, [&](auto kern) {
+      if (ms.smem_x > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_x);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, ms.threads, ms.smem_x);
+    });
   }
   return (nsm > 0 ? nsm : 1) * (per > 0 ? per : 1);
 }
@@ -149,8 +182,10 @@ template <typename Tg>
 void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                          const KParams& p, double dt, const MicroShape& ms, const int* list,
                          const int* count, int blocks, cudaStream_t s) {
-  k_micro_x_list<Tg><<<blocks, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx,
-                                                           ms.R, list, count);
+  with_x_list_kernel<Tg>(ms.xrows, [&](auto kern) {
+    kern<<<blocks, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R, list,
+                                              count);
+  });
 }
 
 template <typename Tg>
@@ -173,9 +208,11 @@ template void launch_micro_y_list<double>(const double*, double*, double*, const
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s) {
-  if (ms.smem_x > 48 * 1024)
-    cudaFuncSetAttribute(k_micro_x<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_x);
-  k_micro_x<Tg><<<g.nx * g.ny, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R);
+  with_x_kernel<Tg>(ms.xrows, [&](auto kern) {
+    if (ms.smem_x > 48 * 1024)
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_x);
+    kern<<<g.nx * g.ny, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R);
+  });
 }
 
 template <typename Tg>
