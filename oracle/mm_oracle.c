@@ -490,24 +490,87 @@ static void ghat_cell(const orc_grid* g, const orc_params* p, const prim_t* P, c
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* The 2D-2V manufactured solution of the convergence study (Section 6.1, "Method of           */
+/* Manufactured Solutions Example"): f = phi(v) F(t, x, y) with                                 */
+/*   phi = exp(-(v1-1)^2 - (v2-1)^2) + 2 exp(-(v1+1)^2 - (v2+1)^2),                            */
+/*   F   = 2 - sin(2 pi (t - x)) cos(2 pi (t - y)),                                            */
+/* whose moments are pi F (3, -1, -1, 9/2, 3, 9/2) (rho, rho u, E; the paper lists rho, rho u  */
+/* and P = (25/6, 8/3, 25/6) pi F), and the residual                                            */
+/*   S = f_t + v1 f_x + v2 f_y - (tau/eps)(Gcal[f] - f)                                         */
+/* with tau and the ES Gaussian Gcal of the exact moments.                                     */
+/* ------------------------------------------------------------------------------------------ */
+static double mms_F(double t, double x, double y) {
+  return 2.0 - sin(2.0 * ORC_PI * (t - x)) * cos(2.0 * ORC_PI * (t - y));
+}
+
+static double mms_phi(double v1, double v2) {
+  return exp(-(v1 - 1.0) * (v1 - 1.0) - (v2 - 1.0) * (v2 - 1.0)) +
+         2.0 * exp(-(v1 + 1.0) * (v1 + 1.0) - (v2 + 1.0) * (v2 + 1.0));
+}
+
+static void mms_q(double t, double x, double y, double q[6]) {
+  double pf = ORC_PI * mms_F(t, x, y);
+  q[0] = 3.0 * pf; q[1] = -pf; q[2] = -pf; q[3] = 4.5 * pf; q[4] = 3.0 * pf; q[5] = 4.5 * pf;
+}
+
+/* S at the velocity nodes of the cell centred at (x, y), time t; returns 0 or 4. */
+static int mms_source(const orc_grid* g, const orc_params* p, double eps, double t, double x,
+                      double y, double* S) {
+  const double w = 2.0 * ORC_PI;
+  const double s1 = sin(w * (t - x)), c1 = cos(w * (t - x));
+  const double s2 = sin(w * (t - y)), c2 = cos(w * (t - y));
+  const double F_t = -w * c1 * c2 + w * s1 * s2;  /* d/dt [2 - sin(w(t-x)) cos(w(t-y))] */
+  const double F_x = w * c1 * c2;
+  const double F_y = -w * s1 * s2;
+  const double F = 2.0 - s1 * c2;
+  double q[6];
+  mms_q(t, x, y, q);
+  prim_t e;
+  if (prim_of(p, q, &e)) return 4;
+  for (int l = 0; l < g->nv2; ++l)
+    for (int k = 0; k < g->nv1; ++k) {
+      const double v1 = vel1(g, k), v2 = vel2(g, l);
+      const double ph = mms_phi(v1, v2);
+      S[l * g->nv1 + k] = ph * (F_t + v1 * F_x + v2 * F_y) -
+                          (e.tau / eps) * (gauss_es(&e, v1, v2) - ph * F);
+    }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* macro helpers                                                                                */
 /* ------------------------------------------------------------------------------------------ */
 
 /* Collision half step of Section 5.4 with tau taken from q itself. */
+/* The step needs rho > 0 and T > 0 (tau); the pressure tensor of its input need not be
+ * positive definite (with a manufactured source the state before the last half step can leave
+ * that set; the relaxation brings it back). */
 static int coll_half(const orc_params* p, const double q[6], double eps, double dt, double out[6]) {
-  prim_t c;
-  int rc = prim_of(p, q, &c);
-  if (rc) return rc;
-  double W = orc_trbdf2_W(c.tau, p->nu, eps, dt);
-  double P11 = 0.5 * ((1.0 + W) * c.P11 + (1.0 - W) * c.P22);
-  double P12 = 0.5 * (2.0 * W * c.P12);
-  double P22 = 0.5 * ((1.0 - W) * c.P11 + (1.0 + W) * c.P22);
+  const double rho = q[0];
+  if (!(rho > 0.0) || !isfinite(rho)) return 4;
+  const double u1 = q[1] / rho, u2 = q[2] / rho;
+  const double P11 = q[3] - rho * u1 * u1;
+  const double P12 = q[4] - rho * u1 * u2;
+  const double P22 = q[5] - rho * u2 * u2;
+  const double T = (P11 + P22) / (2.0 * rho);
+  if (!(T > 0.0) || !isfinite(T) || !isfinite(P12) || !isfinite(u1) || !isfinite(u2)) return 4;
+  double tau;
+  switch (p->tau_model) {
+    case ORC_TAU_RHO: tau = p->tau0 * rho; break;
+    case ORC_TAU_HARDSPHERE2D: tau = 3.0 * ORC_PI * ORC_C25 * rho / (sqrt(2.0) * (1.0 - p->nu)); break;
+    case ORC_TAU_PRESSURE: tau = p->tau0 * rho * T; break;
+    default: tau = p->tau0; break;
+  }
+  double W = orc_trbdf2_W(tau, p->nu, eps, dt);
+  double n11 = 0.5 * ((1.0 + W) * P11 + (1.0 - W) * P22);
+  double n12 = 0.5 * (2.0 * W * P12);
+  double n22 = 0.5 * ((1.0 - W) * P11 + (1.0 + W) * P22);
   out[0] = q[0];
   out[1] = q[1];
   out[2] = q[2];
-  out[3] = c.rho * c.u1 * c.u1 + P11;
-  out[4] = c.rho * c.u1 * c.u2 + P12;
-  out[5] = c.rho * c.u2 * c.u2 + P22;
+  out[3] = rho * u1 * u1 + n11;
+  out[4] = rho * u1 * u2 + n12;
+  out[5] = rho * u2 * u2 + n22;
   return 0;
 }
 
@@ -670,10 +733,13 @@ static int check_args(const orc_grid* g, const orc_params* p) {
 /* ------------------------------------------------------------------------------------------ */
 /* One or more steps; with closure != NULL (one step): cells with refresh[c] != 0 first take
  * g^n = Ghat(Q^n); then cells with closure[c] != 0 keep g^n and take the heat flux Hcl[m][c] in
- * place of the relaxed micro solution and its moments. */
+ * place of the relaxed micro solution and its moments.  With mms != 0 the manufactured source
+ * S(t^n), t^n = t0 + n dt, enters Ghat as + (1/tau^n)(I - Pi_M)[S] and the macro update as
+ * Q*** += dt int (1, v, v (x) v) S dv between the y transport and the last collision half step
+ * (Section 6.1, Eq. macro2d-split3b). */
 static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
                      double dt, double eps, int nsteps, const unsigned char* closure,
-                     const unsigned char* refresh, const double* Hcl) {
+                     const unsigned char* refresh, const double* Hcl, int mms, double t0) {
   if (check_args(g, p) || !Q || !G || !H || !(dt > 0.0) || !(eps > 0.0) || nsteps < 0) return 1;
   const int nx = g->nx, ny = g->ny, nv1 = g->nv1, nv2 = g->nv2, nv = nv1 * nv2;
   const int nc = nx * ny;
@@ -722,7 +788,7 @@ static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* 
     /* micro: backward-Euler relaxation toward Ghat (Eq. 5-98), then H^{n+1} (Eq. 5-99) */
 #pragma omp parallel
     {
-      double* gh = (double*)malloc(sizeof(double) * nv);
+      double* gh = (double*)malloc(sizeof(double) * 2 * nv);  /* Ghat, then Pi_M[S] */
       double* tmp = (double*)malloc(sizeof(double) * nv);
 #pragma omp for schedule(static)
       for (int c = 0; c < nc; ++c) {
@@ -733,6 +799,14 @@ static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* 
           continue;
         }
         ghat_cell(g, p, P, Mc, i, j, eps, gh, tmp);
+        if (mms) {
+          const double dx = (g->x1 - g->x0) / nx, dy = (g->y1 - g->y0) / ny;
+          const double tn = t0 + step * dt;
+          if (mms_source(g, p, eps, tn, g->x0 + (i + 0.5) * dx, g->y0 + (j + 0.5) * dy, tmp) == 0) {
+            project(g, pc, tmp, gh + nv);
+            for (int id = 0; id < nv; ++id) gh[id] += (tmp[id] - gh[nv + id]) / pc->tau;
+          }
+        }
         double w1 = eps / (eps + dt * pc->tau);
         double w2 = dt * pc->tau / (eps + dt * pc->tau);
         double h111 = 0, h112 = 0, h122 = 0, h222 = 0;
@@ -812,6 +886,32 @@ static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* 
         Q1[m * nc + c] = v;
       }
     }
+    /* (3b) manufactured source: Q*** += dt int (1, v1, v2, v1^2, v1 v2, v2^2) S(t^n) dv */
+    if (mms) {
+      const double tn = t0 + step * dt;
+#pragma omp parallel
+      {
+        double* S = (double*)malloc(sizeof(double) * nv);
+#pragma omp for schedule(static) reduction(| : bad)
+        for (int c = 0; c < nc; ++c) {
+          int i = c % nx, j = c / nx;
+          if (mms_source(g, p, eps, tn, g->x0 + (i + 0.5) * dx, g->y0 + (j + 0.5) * dy, S)) {
+            bad = 1;
+            continue;
+          }
+          double m[6] = {0, 0, 0, 0, 0, 0};
+          for (int l = 0; l < nv2; ++l)
+            for (int k = 0; k < nv1; ++k) {
+              double v1 = vel1(g, k), v2 = vel2(g, l), sv = S[l * nv1 + k];
+              m[0] += sv; m[1] += v1 * sv; m[2] += v2 * sv;
+              m[3] += v1 * v1 * sv; m[4] += v1 * v2 * sv; m[5] += v2 * v2 * sv;
+            }
+          for (int q = 0; q < 6; ++q) Q1[q * nc + c] += dt * dv1 * dv2 * m[q];
+        }
+        free(S);
+      }
+      if (bad) { status = 4; break; }
+    }
     /* (4) collision half step with tau***: Q*** -> Q^{n+1} */
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (int c = 0; c < nc; ++c) {
@@ -828,14 +928,48 @@ static int step_impl(const orc_grid* g, const orc_params* p, double* Q, double* 
 
 int orc_step(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H, double dt,
              double eps, int nsteps) {
-  return step_impl(g, p, Q, G, H, dt, eps, nsteps, NULL, NULL, NULL);
+  return step_impl(g, p, Q, G, H, dt, eps, nsteps, NULL, NULL, NULL, 0, 0.0);
 }
 
 int orc_step_closure(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
                      double dt, double eps, const unsigned char* closure,
                      const unsigned char* refresh, const double* Hcl) {
   if (!closure || !refresh || !Hcl) return 1;
-  return step_impl(g, p, Q, G, H, dt, eps, 1, closure, refresh, Hcl);
+  return step_impl(g, p, Q, G, H, dt, eps, 1, closure, refresh, Hcl, 0, 0.0);
+}
+
+int orc_mms_source(const orc_grid* g, const orc_params* p, double eps, double t, double x,
+                   double y, double* S) {
+  if (check_args(g, p) || !S || !(eps > 0.0)) return 1;
+  return mms_source(g, p, eps, t, x, y, S);
+}
+
+int orc_step_mms(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
+                 double dt, double eps, int nsteps, double t0) {
+  return step_impl(g, p, Q, G, H, dt, eps, nsteps, NULL, NULL, NULL, 1, t0);
+}
+
+int orc_mms_exact(const orc_grid* g, const orc_params* p, double t, double eps, double* Q,
+                  double* G) {
+  if (check_args(g, p) || !Q || !G || !(eps > 0.0)) return 1;
+  const int nx = g->nx, ny = g->ny, nv1 = g->nv1, nv2 = g->nv2, nc = nx * ny;
+  const double dx = (g->x1 - g->x0) / nx, dy = (g->y1 - g->y0) / ny;
+  for (int c = 0; c < nc; ++c) {
+    const int i = c % nx, j = c / nx;
+    const double x = g->x0 + (i + 0.5) * dx, y = g->y0 + (j + 0.5) * dy;
+    double q[6];
+    mms_q(t, x, y, q);
+    for (int m = 0; m < 6; ++m) Q[m * nc + c] = q[m];
+    prim_t e;
+    if (prim_of(p, q, &e)) return 4;
+    const double F = mms_F(t, x, y);
+    for (int l = 0; l < nv2; ++l)
+      for (int k = 0; k < nv1; ++k) {
+        const double v1 = vel1(g, k), v2 = vel2(g, l);
+        G[gidx(g, i, j, k, l)] = (mms_phi(v1, v2) * F - maxwell(&e, v1, v2)) / eps;
+      }
+  }
+  return 0;
 }
 
 int orc_ghat(const orc_grid* g, const orc_params* p, const double* Q, double eps, double* Ghat) {

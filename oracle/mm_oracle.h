@@ -57,6 +57,20 @@ int orc_step(const orc_grid* g, const orc_params* p, double* Q, double* G, doubl
 int orc_step_closure(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
                      double dt, double eps, const unsigned char* closure,
                      const unsigned char* refresh, const double* Hcl);
+/* The 2D-2V manufactured solution of the convergence study (Section 6.1): f = phi(v) F(t, x, y),
+ * phi = exp(-|v - (1,1)|^2) + 2 exp(-|v + (1,1)|^2), F = 2 - sin(2 pi (t-x)) cos(2 pi (t-y)).
+ * orc_step_mms: nsteps steps starting at time t0 with the residual source S = f_t + v.grad f
+ * - (tau/eps)(Gcal[f] - f) added to Ghat as (1/tau)(I - Pi_M)[S] and to the macro update as
+ * dt int (1, v, v (x) v) S dv after the y transport (Eq. macro2d-split3b).
+ * orc_mms_exact: the exact Q (cell-centre values) and g = (f - M[f])/eps at the nodes, time t.
+ * Both return 0, 4 (non-physical) or 1 (invalid arguments). */
+int orc_step_mms(const orc_grid* g, const orc_params* p, double* Q, double* G, double* H,
+                 double dt, double eps, int nsteps, double t0);
+int orc_mms_exact(const orc_grid* g, const orc_params* p, double t, double eps, double* Q,
+                  double* G);
+/* The residual S at the velocity nodes ([nv2][nv1]) of the point (x, y), time t. */
+int orc_mms_source(const orc_grid* g, const orc_params* p, double eps, double t, double x,
+                   double y, double* S);
 /* Global time step (Eq. CFL-2D-part1/part2 and the 1D rule of Section 3.2). */
 double orc_dt_for_cfl(const orc_grid* g, double cfl, double t_final, int form, int* nsteps_out);
 

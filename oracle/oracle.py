@@ -64,6 +64,16 @@ def lib():
                                        ctypes.POINTER(ctypes.c_ubyte),
                                        ctypes.POINTER(ctypes.c_ubyte), _c_double_p]
         L.orc_step_closure.restype = ctypes.c_int
+        L.orc_step_mms.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_double]
+        L.orc_step_mms.restype = ctypes.c_int
+        L.orc_mms_exact.argtypes = [G, P, ctypes.c_double, ctypes.c_double, _c_double_p,
+                                    _c_double_p]
+        L.orc_mms_exact.restype = ctypes.c_int
+        L.orc_mms_source.argtypes = [G, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, _c_double_p]
+        L.orc_mms_source.restype = ctypes.c_int
         L.orc_ghat.argtypes = [G, P, _c_double_p, ctypes.c_double, _c_double_p]
         L.orc_ghat.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
@@ -135,6 +145,42 @@ def step_closure(grid, params, Q, G, dt, eps, closure, refresh, Hcl):
     if rc != 0:
         raise OracleError("orc_step_closure returned %d" % rc)
     return Q, G, H
+
+
+def step_mms(grid, params, Q, G, dt, eps, nsteps, t0=0.0):
+    """nsteps steps of the manufactured-solution problem from time t0; returns (Q, G, H)."""
+    Q = np.array(Q, dtype=np.float64, order="C", copy=True)
+    G = np.array(G, dtype=np.float64, order="C", copy=True)
+    H = np.zeros((4, grid.ny, grid.nx), dtype=np.float64)
+    gg, pp = _grid(grid), _params(params)
+    rc = lib().orc_step_mms(ctypes.byref(gg), ctypes.byref(pp), _ptr(Q), _ptr(G), _ptr(H),
+                            float(dt), float(eps), int(nsteps), float(t0))
+    if rc != 0:
+        raise OracleError("orc_step_mms returned %d" % rc)
+    return Q, G, H
+
+
+def mms_exact(grid, params, t, eps):
+    """Exact (Q [6][ny][nx], g [ny][nx][nv2][nv1]) of the manufactured solution at time t."""
+    Q = np.zeros((6, grid.ny, grid.nx))
+    G = np.zeros((grid.ny, grid.nx, grid.nv2, grid.nv1))
+    gg, pp = _grid(grid), _params(params)
+    rc = lib().orc_mms_exact(ctypes.byref(gg), ctypes.byref(pp), float(t), float(eps), _ptr(Q),
+                             _ptr(G))
+    if rc != 0:
+        raise OracleError("orc_mms_exact returned %d" % rc)
+    return Q, G
+
+
+def mms_source(grid, params, eps, t, x, y):
+    """The manufactured residual S [nv2][nv1] at the point (x, y), time t."""
+    S = np.zeros((grid.nv2, grid.nv1))
+    gg, pp = _grid(grid), _params(params)
+    rc = lib().orc_mms_source(ctypes.byref(gg), ctypes.byref(pp), float(eps), float(t),
+                              float(x), float(y), _ptr(S))
+    if rc != 0:
+        raise OracleError("orc_mms_source returned %d" % rc)
+    return S
 
 
 def dt_for_cfl(grid, cfl, t_final, form):

@@ -44,12 +44,16 @@ __device__ __forceinline__ bool prim6(const double q[6], double& rho, double& u1
 }
 
 // Collision half step (Section 5.4): P <- (1/2)[[1+W,0,1-W],[0,2W,0],[1-W,0,1+W]] P with the
-// TR-BDF2 factor W of tau(q); rho and rho u unchanged; E = rho u (x) u + P.
+// TR-BDF2 factor W of tau(q); rho and rho u unchanged; E = rho u (x) u + P.  The step needs
+// rho > 0 and T > 0; the input's pressure tensor need not be positive definite (with a
+// manufactured source the state before the last half step can leave that set).
 __device__ __forceinline__ bool coll_half(const KParams& p, const double q[6], double eps,
                                           double dt, double o[6]) {
   double rho, u1, u2, P11, P12, P22;
-  const bool ok = prim6(q, rho, u1, u2, P11, P12, P22);
+  prim6(q, rho, u1, u2, P11, P12, P22);
   const double T = (P11 + P22) * 0.5 / rho;
+  const bool ok = rho > 0.0 && T > 0.0 && isfinite(T) && isfinite(u1) && isfinite(u2) &&
+                  isfinite(P12);
   const double a = tau_of(p, rho, T) * (1.0 - p.nu);
   const double W = (48.0 * eps * eps - 10.0 * a * eps * dt) /
                    (48.0 * eps * eps + 14.0 * a * eps * dt + (a * dt) * (a * dt));
