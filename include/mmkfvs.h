@@ -223,6 +223,24 @@ mm_status mm_closure_flags(mm_ctx* c, unsigned char* flags_host);
 /* Closure cells summed over the hybrid steps since mm_set_closure, and cells x those steps. */
 mm_status mm_closure_stats(mm_ctx* c, long long* closure_cells, long long* cell_steps);
 
+/* ---- manufactured-solution harness ----------------------------------------------------------
+ * The 2D-2V manufactured solution of the paper's convergence study (Section 6.1, Method of
+ * Manufactured Solutions Example; Table tab5-4): f = phi(v) F(t, x, y) with
+ * phi = exp(-|v - (1,1)|^2) + 2 exp(-|v + (1,1)|^2), F = 2 - sin(2 pi (t-x)) cos(2 pi (t-y)),
+ * on doubly periodic FP64 contexts (other contexts: MM_ERR_INVALID_ARG).
+ * mm_mms_enable: while enabled, each mm_step adds the residual S = f_t + v.grad f
+ * - (tau/eps)(Gcal[f] - f) at t^n to Ghat as (1/tau^n)(I - Pi_M)[S] and to the macro update as
+ * dt int (1, v, v (x) v) S dv between the y transport and the last collision half step
+ * (Eq. macro2d-split3b); t^n starts at t0 and advances by dt per step.  Not combinable with the
+ * closure (MM_ERR_STATE).  Allocates one more phase-space buffer.
+ * mm_mms_set_exact: the state becomes the exact solution at time t (Q at cell centres,
+ * g = (f - M[f])/eps at the nodes).
+ * mm_mms_error: relative L2 errors of Q and g against the exact solution at time t (the norms
+ * of Section 6.1); synchronous. */
+mm_status mm_mms_enable(mm_ctx* c, int enable, double t0);
+mm_status mm_mms_set_exact(mm_ctx* c, double t, double eps);
+mm_status mm_mms_error(mm_ctx* c, double t, double eps, double* macro_err, double* micro_err);
+
 /* Diagnostic: evaluate the table-driven exponential used by the phase-space kernels (Tang's
  * method, see the micro kernels) and the CUDA library exp on n FP64 device values x_dev, into
  * caller-owned device arrays; synchronises cuda_stream.  Used to test the kernels' exp against

@@ -46,7 +46,7 @@ EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device"
            "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_forward",
            "mm_mlp_grad", "mm_mlp_train_step", "mm_mlp_last_error", "mm_mlp_destroy",
            "mm_set_closure", "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
-           "mm_closure_stats"]
+           "mm_closure_stats", "mm_mms_enable", "mm_mms_set_exact", "mm_mms_error"]
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 39, 64, 4, 6980
 
@@ -129,6 +129,11 @@ def load(build_if_needed: bool = True):
     L.mm_closure_flags.argtypes = [vp, vp]
     L.mm_closure_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]
+    L.mm_mms_enable.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+    L.mm_mms_set_exact.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    L.mm_mms_error.argtypes = [vp, ctypes.c_double, ctypes.c_double, _dp, _dp]
+    for name in ["mm_mms_enable", "mm_mms_set_exact", "mm_mms_error"]:
+        getattr(L, name).restype = ctypes.c_int
     for name in ["mm_create", "mm_set_state", "mm_set_state_device", "mm_step", "mm_sync",
                  "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_set_timing",
                  "mm_get_timing", "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params",
@@ -320,6 +325,20 @@ class Solver:
 
     def last_error(self):
         return self.L.mm_last_error(self.ctx).decode()
+
+    # ---- manufactured-solution harness -------------------------------------------------------
+    def mms_enable(self, enable=True, t0=0.0):
+        _check(self.ctx, self.L.mm_mms_enable(self.ctx, int(enable), float(t0)), "mm_mms_enable")
+
+    def mms_set_exact(self, t, eps):
+        _check(self.ctx, self.L.mm_mms_set_exact(self.ctx, float(t), float(eps)), "mm_mms_set_exact")
+
+    def mms_error(self, t, eps):
+        """(macro, micro) relative L2 errors against the manufactured solution at time t."""
+        a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(self.ctx, self.L.mm_mms_error(self.ctx, float(t), float(eps), ctypes.byref(a),
+                                             ctypes.byref(b)), "mm_mms_error")
+        return a.value, b.value
 
     # ---- learned closure -------------------------------------------------------------------
     def set_closure(self, mlp, threshold):

@@ -72,6 +72,13 @@ struct mm_ctx {
   unsigned long long* cstat = nullptr;   // closure cells summed over hybrid steps
   long long closure_steps = 0;
   int blocks_x = 0, blocks_y = 0, blocks_g = 0;
+  // manufactured-solution harness (FP64 contexts)
+  bool mms = false;
+  double mms_t = 0.0;                    // time t^n of the next step's source
+  double* mms_phi = nullptr;             // velocity tables phi, Gcal/F [nv]
+  double* mms_gam = nullptr;
+  double* mms_src_g = nullptr;           // source term of g^{n+1} (layout of G)
+  double* mms_src_q = nullptr;           // int (1, v, v v) S dv [6][ny][nx]
   bool timing = false;
   std::vector<TimedLaunch> pending;
   std::vector<cudaEvent_t> free_events;
@@ -194,7 +201,16 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
   timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
+  const double* srcg = nullptr;
+  const double* srcq = nullptr;
   if constexpr (sizeof(Tg) == sizeof(double)) {
+    if (c->mms) {
+      launch_mms_source(c->prim, c->mms_phi, c->mms_gam, c->mms_src_g, c->mms_src_q, g, p,
+                        c->mms_t, dt, eps, c->grid.x0, c->grid.y0, s);
+      srcg = c->mms_src_g;
+      srcq = c->mms_src_q;
+      c->mms_t += dt;
+    }
     if (c->cstale) {  // after hybrid steps: g of closure cells to Ghat(Q^n) before a full step
       const int nc = (int)c->ncell;
       launch_closure_stale(c->cvalid, g, c->clists + 2 * nc, c->ccounts + 2, s);
@@ -218,7 +234,9 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
     std::swap(c->G, c->Gs);
   } else {
     timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
-    timed(c, T_MICRO_Y, [&] { launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s); });
+    timed(c, T_MICRO_Y, [&] {
+      launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, srcg);
+    });
     if (c->n_wall > 0)
       timed(c, T_MICRO_YW, [&] {
         launch_micro_y_wall<Tg>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
@@ -227,7 +245,7 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   }
   timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
   timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
-  timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
+  timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s, srcq); });
 }
 
 // Hybrid step with the learned closure (FP64): features and network on every cell, the decision
@@ -584,8 +602,94 @@ double mm_dt_for_cfl(const mm_grid* g, double cfl, double t_final, int form, int
   return dt;
 }
 
+// Velocity tables and source buffers of the manufactured-solution harness, on first use.
+mm_status ensure_mms(mm_ctx* c) {
+  if (c->mms_phi) return MM_OK;
+  const size_t nv = (size_t)c->grid.nv1 * c->grid.nv2;
+  cudaError_t e = cudaMalloc(&c->mms_phi, nv * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->mms_gam, nv * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->mms_src_g, c->nphase * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->mms_src_q, 6 * c->ncell * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(c->mms_phi); cudaFree(c->mms_gam); cudaFree(c->mms_src_g); cudaFree(c->mms_src_q);
+    c->mms_phi = c->mms_gam = c->mms_src_g = c->mms_src_q = nullptr;
+    return e == cudaErrorMemoryAllocation ? fail(c, MM_ERR_OOM, "manufactured-solution buffers")
+                                          : cuda_fail(c, e, "manufactured-solution buffers");
+  }
+  launch_mms_tables(c->mms_phi, c->mms_gam, c->kg, c->kp, c->stream);
+  return MM_OK;
+}
+
+mm_status mms_check(mm_ctx* c) {
+  if (c->fp32) return fail(c, MM_ERR_INVALID_ARG, "the manufactured solution needs an FP64 context");
+  for (int s = 0; s < 4; ++s)
+    if (c->kp.bc[s] != MM_BC_PERIODIC)
+      return fail(c, MM_ERR_INVALID_ARG, "the manufactured solution is doubly periodic");
+  return MM_OK;
+}
+
+mm_status mm_mms_enable(mm_ctx* c, int enable, double t0) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!enable) {
+    c->mms = false;
+    return MM_OK;
+  }
+  mm_status st = mms_check(c);
+  if (st != MM_OK) return st;
+  if (c->mlp) return fail(c, MM_ERR_STATE, "switch the closure off before the manufactured source");
+  if (!std::isfinite(t0)) return fail(c, MM_ERR_INVALID_ARG, "t0 must be finite");
+  st = ensure_mms(c);
+  if (st != MM_OK) return st;
+  c->mms = true;
+  c->mms_t = t0;
+  return MM_OK;
+}
+
+mm_status mm_mms_set_exact(mm_ctx* c, double t, double eps) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  mm_status st = mms_check(c);
+  if (st != MM_OK) return st;
+  if (!(eps > 0.0) || !std::isfinite(t)) return fail(c, MM_ERR_INVALID_ARG, "bad t or eps");
+  st = ensure_mms(c);
+  if (st != MM_OK) return st;
+  launch_mms_exact(c->Q, static_cast<double*>(c->G), c->mms_phi, c->kg, c->kp, t, eps,
+                   c->grid.x0, c->grid.y0, c->stream);
+  if (c->cvalid) cudaMemsetAsync(c->cvalid, 1, c->ncell, c->stream);
+  c->cstale = false;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "manufactured initial state");
+  c->have_state = true;
+  return MM_OK;
+}
+
+mm_status mm_mms_error(mm_ctx* c, double t, double eps, double* macro_err, double* micro_err) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  mm_status st = mms_check(c);
+  if (st != MM_OK) return st;
+  if (!c->have_state) return fail(c, MM_ERR_STATE, "no state set");
+  st = ensure_mms(c);
+  if (st != MM_OK) return st;
+  double* sums = nullptr;
+  cudaError_t e = cudaMalloc(&sums, 4 * c->ncell * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(c, e, "error sums");
+  launch_mms_errors(c->Q, static_cast<const double*>(c->G), c->mms_phi, sums, c->kg, c->kp, t,
+                    eps, c->grid.x0, c->grid.y0, c->stream);
+  std::vector<double> h(4 * c->ncell);
+  e = cudaMemcpyAsync(h.data(), sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(sums);
+  if (e != cudaSuccess) return cuda_fail(c, e, "error sums");
+  double a[4] = {0, 0, 0, 0};
+  for (int m = 0; m < 4; ++m)
+    for (size_t k = 0; k < c->ncell; ++k) a[m] += h[m * c->ncell + k];
+  if (macro_err) *macro_err = std::sqrt(a[0] / a[1]);
+  if (micro_err) *micro_err = std::sqrt(a[2] / a[3]);
+  return check_device_errors(c);
+}
+
 mm_status mm_set_closure(mm_ctx* c, const mm_mlp* m, double threshold) {
   if (!c) return MM_ERR_INVALID_ARG;
+  if (m && c->mms) return fail(c, MM_ERR_STATE, "switch the manufactured source off first");
   if (!m) {
     if (c->mlp) c->cstale = true;  // the next plain step first resets non-current g to Ghat
     c->mlp = nullptr;
@@ -710,6 +814,10 @@ void mm_destroy(mm_ctx* c) {
   cudaFree(c->clists);
   cudaFree(c->ccounts);
   cudaFree(c->cstat);
+  cudaFree(c->mms_phi);
+  cudaFree(c->mms_gam);
+  cudaFree(c->mms_src_g);
+  cudaFree(c->mms_src_q);
   delete c;
 }
 

@@ -415,7 +415,8 @@ __device__ __forceinline__ void macro_x2_body(const double* __restrict__ H, Macr
 // (3) y transport (Eq. 5-103, second line), then the collision half step with tau***:
 // Q** -> Q^{n+1}.
 __device__ __forceinline__ void macro_y_body(const double* __restrict__ H, MacroBufs mb, double* __restrict__ Qn,
-                          KGrid g, KParams p, double dt, double eps, int* __restrict__ err, int c) {
+                          KGrid g, KParams p, double dt, double eps, int* __restrict__ err, int c,
+                          const double* __restrict__ srcq = nullptr) {
   const int nc = g.nx * g.ny;
   const int i = c % g.nx, j = c / g.nx;
   const int cb = (j > 0 ? j - 1 : g.ny - 1) * g.nx + i;
@@ -445,6 +446,9 @@ __device__ __forceinline__ void macro_y_body(const double* __restrict__ H, Macro
     if (m >= 3) v -= dt * (dH[m - 3] * g.idy);
     q3[m] = v;
   }
+  // optional source between the y transport and the collision half step (Eq. macro2d-split3b)
+  if (srcq)
+    for (int m = 0; m < 6; ++m) q3[m] = fma(dt, srcq[m * nc + c], q3[m]);
   double o[6];
   const bool ok = coll_half(p, q3, eps, dt, o);
   for (int m = 0; m < 6; ++m) Qn[m * nc + c] = o[m];

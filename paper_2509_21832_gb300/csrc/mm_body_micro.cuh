@@ -215,7 +215,8 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
                                                     double* __restrict__ Hout,
                                                     const double* __restrict__ prim, KGrid g,
                                                     KParams p, double dtidy, double hscale, int R,
-                                                    int* __restrict__ err, int cell, double* sm) {
+                                                    int* __restrict__ err, int cell, double* sm,
+                                                    const double* __restrict__ src = nullptr) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;
   const int i = cell % g.nx, j = cell / g.nx;
@@ -335,6 +336,8 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
   // pass 2: G^{n+1} = om1 (G* - dt Z* + dt Zhat*) + om2 Ghat, and its heat-flux moments;
   // om1 G* - om1 dt Z* = wl G*_upwind + (om1 - wl) G*
   double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0;
+  // optional source term of g^{n+1} (same layout as G), e.g. the manufactured residual
+  const double* Sc = src ? src + (size_t)cell * nv + k : nullptr;
   if (active) {
     Tg* Go = Gout + (size_t)cell * nv + k;
     for (int l = r; l < nv2; l += R) {
@@ -351,6 +354,7 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
       o = fma(A3, E3t[l], o);
       o = fma(g2t[l], x, o);
       x *= rat;
+      if (Sc) o += Sc[l * nv1];
       const Tg os = (Tg)o;
       Go[l * nv1] = os;
       const double ov = (double)os;

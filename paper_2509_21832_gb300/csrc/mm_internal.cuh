@@ -75,10 +75,11 @@ void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, c
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s);
+// src (optional): a term added to g^{n+1} at every node, same layout as G
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
-                    cudaStream_t s);
+                    cudaStream_t s, const double* src = nullptr);
 template <typename Tg>
 void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
@@ -111,8 +112,10 @@ void launch_macro_x1(const double* Qn, const MacroBufs& mb, const KGrid& g, cons
                      double dt, double eps, int* err, cudaStream_t s);
 void launch_macro_x2(const double* H, const MacroBufs& mb, const KGrid& g, const KParams& p,
                      double dt, int* err, cudaStream_t s);
+// srcq (optional): [6][ny][nx] rates added times dt after the y transport
 void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGrid& g,
-                    const KParams& p, double dt, double eps, int* err, cudaStream_t s);
+                    const KParams& p, double dt, double eps, int* err, cudaStream_t s,
+                    const double* srcq = nullptr);
 void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s);
 __host__ __device__ inline MacroBufs carve_macro(double* base, int nx, int ny) {
   const size_t nc = (size_t)nx * ny;
@@ -154,6 +157,18 @@ int closure_ghat_blocks(const MicroShape& ms);
 void launch_closure_ghat(double* G, const double* prim, const KGrid& g, double dt, double eps,
                          const MicroShape& ms, const int* list, const int* count, int blocks,
                          cudaStream_t s);
+// Manufactured-solution harness (mm_mms.cu): velocity tables phi, gam [nv]; exact state; the
+// source terms of one step at time t; per-cell error partial sums [4][ny][nx].
+void launch_mms_tables(double* phi, double* gam, const KGrid& g, const KParams& p,
+                       cudaStream_t s);
+void launch_mms_exact(double* Q, double* G, const double* phi, const KGrid& g, const KParams& p,
+                      double t, double eps, double x0, double y0, cudaStream_t s);
+void launch_mms_source(const double* prim, const double* phi, const double* gam, double* src_g,
+                       double* src_q, const KGrid& g, const KParams& p, double t, double dt,
+                       double eps, double x0, double y0, cudaStream_t s);
+void launch_mms_errors(const double* Q, const double* G, const double* phi, double* sums,
+                       const KGrid& g, const KParams& p, double t, double eps, double x0,
+                       double y0, cudaStream_t s);
 // Network inference on the stream s (mm_mlp.cu).
 void mlp_forward_async(const mm_mlp* m, const float* X, float* Y, int n, cudaStream_t s);
 void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s);

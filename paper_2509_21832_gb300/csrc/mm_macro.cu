@@ -36,9 +36,10 @@ __global__ void k_macro_x2(const double* __restrict__ H, MacroBufs mb, KGrid g, 
 }
 
 __global__ void k_macro_y(const double* __restrict__ H, MacroBufs mb, double* __restrict__ Qn,
-                          KGrid g, KParams p, double dt, double eps, int* __restrict__ err) {
+                          KGrid g, KParams p, double dt, double eps, int* __restrict__ err,
+                          const double* __restrict__ srcq) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < g.nx * g.ny) macro_y_body(H, mb, Qn, g, p, dt, eps, err, c);
+  if (c < g.nx * g.ny) macro_y_body(H, mb, Qn, g, p, dt, eps, err, c, srcq);
 }
 
 // Heat flux of the FP32-g kernels: compensated FP32 (hi, lo) totals -> FP64, times eps dv1 dv2.
@@ -71,9 +72,10 @@ void launch_macro_x2(const double* H, const MacroBufs& mb, const KGrid& g, const
 }
 
 void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGrid& g,
-                    const KParams& p, double dt, double eps, int* err, cudaStream_t s) {
+                    const KParams& p, double dt, double eps, int* err, cudaStream_t s,
+                    const double* srcq) {
   const int nc = g.nx * g.ny;
-  k_macro_y<<<(nc + 127) / 128, 128, 0, s>>>(H, mb, Qn, g, p, dt, eps, err);
+  k_macro_y<<<(nc + 127) / 128, 128, 0, s>>>(H, mb, Qn, g, p, dt, eps, err, srcq);
 }
 
 void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s) {

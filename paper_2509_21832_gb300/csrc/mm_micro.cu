@@ -35,9 +35,10 @@ __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs,
                                                     double* __restrict__ Hout,
                                                     const double* __restrict__ prim, KGrid g,
                                                     KParams p, double dtidy, double hscale, int R,
-                                                    int* __restrict__ err) {
+                                                    int* __restrict__ err,
+                                                    const double* __restrict__ src) {
   extern __shared__ double sm[];
-  micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, blockIdx.x, sm);
+  micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, blockIdx.x, sm, src);
 }
 
 template <typename Tg>
@@ -218,11 +219,11 @@ void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
-                    cudaStream_t s) {
+                    cudaStream_t s, const double* src) {
   if (ms.smem_y > 48 * 1024)
     cudaFuncSetAttribute(k_micro_y<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_y);
   k_micro_y<Tg><<<g.nx * g.ny, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
-                                                           eps * g.dv1 * g.dv2, ms.R, err);
+                                                           eps * g.dv1 * g.dv2, ms.R, err, src);
 }
 
 template <typename Tg>
@@ -238,7 +239,7 @@ template void launch_micro_x<double>(const double*, double*, const double*, cons
                                      const KParams&, double, const MicroShape&, cudaStream_t);
 template void launch_micro_y<double>(const double*, double*, double*, const double*,
                                      const KGrid&, const KParams&, double, double,
-                                     const MicroShape&, int*, cudaStream_t);
+                                     const MicroShape&, int*, cudaStream_t, const double*);
 template void launch_micro_y_wall<double>(const double*, double*, double*, const double*,
                                           const int*, int, const KGrid&, const KParams&, double,
                                           double, const MicroShape&, int*, cudaStream_t);

@@ -137,3 +137,21 @@ def test_micro_part_stays_orthogonal_to_the_null_space_with_the_source():
     scale = np.max(np.sum(np.abs(G), axis=(2, 3)))
     for m in (1, V1, V2, V1 * V1 + V2 * V2):
         assert np.max(np.abs(np.sum(G * m, axis=(2, 3)))) <= 1e-11 * scale * np.max(np.abs(m))
+
+
+def test_coarsest_printed_row():
+    """Table tab5-4, 40^4: the oracle on [-1, 1]^2 (the domain reading of the GPU convergence
+    test) gives the printed macro and micro errors to 10 %."""
+    with open(GOLDEN) as f:
+        row = json.load(f)["table_tab5_4"][0]
+    g = I.Grid(nx=40, ny=40, x0=-1, x1=1, y0=-1, y1=1, nv1=40, nv2=40, v1min=-6, v1max=6,
+               v2min=-6, v2max=6)
+    p = I.Params(nu=-1.0, tau_model=I.TAU_HARDSPHERE2D, bc=(I.PERIODIC,) * 4)
+    dt, ns = O.dt_for_cfl(g, 0.35, 0.25, I.CFL_SUM)
+    Q0, G0 = O.mms_exact(g, p, 0.0, EPS)
+    Q, G, _ = O.step_mms(g, p, Q0, G0, dt, EPS, ns, 0.0)
+    Qe, Ge = O.mms_exact(g, p, ns * dt, EPS)
+    em = math.sqrt(np.sum((Q - Qe) ** 2) / np.sum(Qe ** 2))
+    eu = math.sqrt(np.sum((G - Ge) ** 2) / np.sum(Ge ** 2))
+    assert abs(em / row["macro"] - 1) <= 0.10, em
+    assert abs(eu / row["micro"] - 1) <= 0.10, eu
