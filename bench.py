@@ -36,8 +36,8 @@ FLOPS_MICRO_Y = 39.0
 FLOPS_STEP = 52.0
 BYTES_PER_PHASE_FP64 = 16.0 + 160.0 / 1024.0
 # DRAM traffic of k_micro_y per phase cell (32^2 velocity meshes), from the ncu capture in
-# profiles/k_micro_bump_specular_160x160x32x32_fp64.md: (214.0 + 172.7) MB / 26.2144 M.
-TRAFFIC_MICRO_Y_PER_PHASE_CELL = 386.7e6 / 26.2144e6
+# profiles/k_micro_bump_specular_160x160x32x32_fp64.md: (213.9 + 173.0) MB / 26.2144 M.
+TRAFFIC_MICRO_Y_PER_PHASE_CELL = 386.9e6 / 26.2144e6
 
 
 def measured_peaks():
@@ -452,7 +452,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak,
                 # DRAM bytes per k_micro_y launch: ncu capture of the 160^2 x 32^2 case
-                # (read + write = 386.7 MB over 26.2 M phase cells), scaled by phase cells
+                # (read + write = 386.9 MB over 26.2 M phase cells), scaled by phase cells
                 "traffic": (TRAFFIC_MICRO_Y_PER_PHASE_CELL * nph
                             if (pr.grid.nv1, pr.grid.nv2) == (32, 32) else None),
                 "traffic_unit": "bytes per launch",
