@@ -35,8 +35,8 @@ UNIT = "phase-cell updates/s"
 FLOPS_MICRO_Y = 39.0
 FLOPS_STEP = 52.0
 BYTES_PER_PHASE_FP64 = 16.0 + 160.0 / 1024.0
-# DRAM traffic of k_micro_y per phase cell (32^2 velocity meshes), from the ncu capture in
-# profiles/k_micro_bump_specular_160x160x32x32_fp64.md: (213.9 + 173.0) MB / 26.2144 M.
+# DRAM traffic of k_micro_y per phase cell (32^2 velocity meshes), from an ncu capture of the
+# 160^2 x 32^2 bump case: (213.9 MB read + 173.0 MB written) / 26.2144 M phase cells.
 TRAFFIC_MICRO_Y_PER_PHASE_CELL = 386.9e6 / 26.2144e6
 
 
