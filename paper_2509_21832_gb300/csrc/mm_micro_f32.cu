@@ -108,26 +108,50 @@ __device__ __forceinline__ void warp_allsum4(float v[4]) {
   v[3] = __shfl_sync(full, kk, 24);
 }
 
+// Per-cell FP32 coefficients of one cell, loaded by one instruction (lane f reads field f) and
+// handed out by warp shuffles.
+__device__ __forceinline__ float load_fields(const float* __restrict__ pf, int nc, int cell) {
+  const int lane = threadIdx.x & 31;
+  return lane < NPRIMF ? __ldg(pf + (size_t)lane * nc + cell) : 0.f;
+}
+__device__ __forceinline__ float field(float fv, int f) { return __shfl_sync(0xffffffffu, fv, f); }
+
+// Velocity shape: compile-time for the common meshes (NV1 > 0: nv1 = NV1, nv2 = NV2, every
+// active lane owns exactly NR = NV2 / R rows), runtime otherwise (NV1 = 0).
+template <int NV1, int NV2>
+struct VShape {
+  static constexpr bool fixed = NV1 > 0;
+  static constexpr int RC = NV1 > 0 ? 32 / NV1 : 1;
+  static constexpr int NRC = NV1 > 0 ? NV2 / RC : 0;
+  int nv1, nv2, R, nr;
+  __device__ __forceinline__ VShape(const KGrid& g, int Rrt) {
+    nv1 = fixed ? NV1 : g.nv1;
+    nv2 = fixed ? NV2 : g.nv2;
+    R = fixed ? RC : Rrt;
+    nr = fixed ? NRC : (g.nv2 + Rrt - 1) / Rrt;
+  }
+};
+
 // x sweep of cell (i, j) into dst (the warp's shared-memory ring slot).
+template <int NV1, int NV2>
 __device__ __forceinline__ void wx_sweep(const FusedF32& a, int i, int j, float* dst, float* xt) {
   const KGrid& g = a.g;
-  const int nv1 = g.nv1, nv2 = g.nv2, nc = g.nx * g.ny;
+  const VShape<NV1, NV2> vs(g, a.R);
+  const int nv1 = vs.nv1, nv2 = vs.nv2, R = vs.R, nc = g.nx * g.ny;
   const int cell = j * g.nx + i;
-  float* c2t = xt;
-  float* c2q = xt + nv2;
-  float* e2t = xt + 2 * nv2;
-  float* qet = xt + 3 * nv2;
+  // row tables as pairs, one shared load each: X1 = (c2, c2^2), X2 = (e2, projection term)
+  float2* X1 = reinterpret_cast<float2*>(xt);
+  float2* X2 = X1 + nv2;
   const int lane = threadIdx.x & 31, k = lane % nv1, r = lane / nv1;
-  const bool active = r < a.R;
-  const float u1 = __ldg(a.pf + F_U1 * nc + cell), u2 = __ldg(a.pf + F_U2 * nc + cell);
-  const float inv2T = __ldg(a.pf + F_INV2T * nc + cell), iT = __ldg(a.pf + F_IT * nc + cell);
-  const float kap = __ldg(a.pf + F_KAP * nc + cell);
+  const bool active = r < R;
+  const float fv = load_fields(a.pf, nc, cell);
+  const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
+  const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT), kap = field(fv, F_KAP);
   for (int l = lane; l < nv2; l += 32) {
     const float c2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
     const float q = c2 * c2;
-    c2t[l] = c2;
-    c2q[l] = q;
-    e2t[l] = expf(-q * inv2T);
+    X1[l] = make_float2(c2, q);
+    X2[l] = make_float2(expf(-q * inv2T), 0.f);
   }
   const float v1 = fmaf(k + 0.5f, a.gf.dv1, a.gf.v1min);
   const float c1 = v1 - u1;
@@ -140,29 +164,51 @@ __device__ __forceinline__ void wx_sweep(const FusedF32& a, int i, int j, float*
   const float* Gc = a.Gin + (size_t)cell * nv + k;
   const float* Gu = a.Gin + (size_t)up.cell * nv + ku;
   __syncwarp();
-  // pass 1: upwind differences and their moments; the loads of kChunk rows per lane are issued
-  // together so that many are in flight; dst keeps the upwind update G - dt Z = G + lam d
+  // pass 1: upwind differences and their moments; dst keeps the upwind update G + lam d
   float D0 = 0.f, D1 = 0.f, D2 = 0.f;
   if (active) {
-    constexpr int kChunk = 16;
-    for (int l0 = r; l0 < nv2; l0 += kChunk * a.R) {
-      float gv[kChunk], gu[kChunk];
+    if constexpr (VShape<NV1, NV2>::fixed) {
+      constexpr int NR = VShape<NV1, NV2>::NRC;
+      constexpr int RR = VShape<NV1, NV2>::RC;
+      float gv[NR], gu[NR];
 #pragma unroll
-      for (int m = 0; m < kChunk; ++m) {
-        const int l = l0 + m * a.R;
-        const bool in = l < nv2;
-        gv[m] = in ? __ldg(Gc + l * nv1) : 0.f;
-        gu[m] = (in && !up.zero) ? __ldg(Gu + l * nv1) : 0.f;
+      for (int m = 0; m < NR; ++m) {
+        const int l = r + m * RR;
+        gv[m] = __ldg(Gc + l * NV1);
+        gu[m] = up.zero ? 0.f : __ldg(Gu + l * NV1);
       }
 #pragma unroll
-      for (int m = 0; m < kChunk; ++m) {
-        const int l = l0 + m * a.R;
-        if (l < nv2) {
-          const float d = gu[m] - gv[m];
-          dst[l * nv1 + k] = fmaf(lam, d, gv[m]);
-          D0 += d;
-          D1 = fmaf(c2t[l], d, D1);
-          D2 = fmaf(c2q[l], d, D2);
+      for (int m = 0; m < NR; ++m) {
+        const int l = r + m * RR;
+        const float d = gu[m] - gv[m];
+        const float2 cq = X1[l];
+        dst[l * NV1 + k] = fmaf(lam, d, gv[m]);
+        D0 += d;
+        D1 = fmaf(cq.x, d, D1);
+        D2 = fmaf(cq.y, d, D2);
+      }
+    } else {
+      constexpr int kChunk = 16;
+      for (int l0 = r; l0 < nv2; l0 += kChunk * R) {
+        float gv[kChunk], gu[kChunk];
+#pragma unroll
+        for (int m = 0; m < kChunk; ++m) {
+          const int l = l0 + m * R;
+          const bool in = l < nv2;
+          gv[m] = in ? __ldg(Gc + l * nv1) : 0.f;
+          gu[m] = (in && !up.zero) ? __ldg(Gu + l * nv1) : 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < kChunk; ++m) {
+          const int l = l0 + m * R;
+          if (l < nv2) {
+            const float d = gu[m] - gv[m];
+            const float2 cq = X1[l];
+            dst[l * nv1 + k] = fmaf(lam, d, gv[m]);
+            D0 += d;
+            D1 = fmaf(cq.x, d, D1);
+            D2 = fmaf(cq.y, d, D2);
+          }
         }
       }
     }
@@ -173,7 +219,10 @@ __device__ __forceinline__ void wx_sweep(const FusedF32& a, int i, int j, float*
   const float b0 = fmaf(-S[3], inv2T, 2.f * S[0]);
   const float b1 = S[1] * iT, b2 = S[2] * iT;
   const float gm = fmaf(0.25f * S[3], iT * iT, -S[0] * inv2T);
-  for (int l = lane; l < nv2; l += 32) qet[l] = e2t[l] * fmaf(b2, c2t[l], gm * c2q[l]);
+  for (int l = lane; l < nv2; l += 32) {
+    const float2 cq = X1[l];
+    X2[l].y = X2[l].x * fmaf(b2, cq.x, gm * cq.y);
+  }
   const float e1 = expf(-c1 * c1 * inv2T);
   const float bk = kap * e1;
   const float ak = bk * fmaf(gm * c1, c1, fmaf(b1, c1, b0));
@@ -182,10 +231,14 @@ __device__ __forceinline__ void wx_sweep(const FusedF32& a, int i, int j, float*
   const bool exp_ = a.Gexp != nullptr && exports_gstar(g, a.p, i, j);
   if (active) {
     float* Ge = a.Gexp + (size_t)cell * nv + k;
-    for (int l = r; l < nv2; l += a.R) {
+#pragma unroll
+    for (int m = 0; m < vs.nr; ++m) {
+      const int l = r + m * R;
+      if (!VShape<NV1, NV2>::fixed && l >= nv2) break;
+      const float2 eq = X2[l];
       float o = dst[l * nv1 + k];
-      o = fmaf(ak, e2t[l], o);
-      o = fmaf(bk, qet[l], o);
+      o = fmaf(ak, eq.x, o);
+      o = fmaf(bk, eq.y, o);
       dst[l * nv1 + k] = o;
       if (exp_) Ge[l * nv1] = o;
     }
@@ -194,54 +247,53 @@ __device__ __forceinline__ void wx_sweep(const FusedF32& a, int i, int j, float*
 }
 
 // y sweep + relaxation + heat flux of cell (i, j) from the G* rows in the warp's ring.
+template <int NV1, int NV2>
 __device__ __forceinline__ void wy_sweep(const FusedF32& a, int i, int j, const float* rc,
                                          const float* srcb, bool mb, bool zb, const float* srct,
                                          bool mt, bool zt, float* tb) {
   const KGrid& g = a.g;
-  const int nv1 = g.nv1, nv2 = g.nv2, nc = g.nx * g.ny;
+  const VShape<NV1, NV2> vs(g, a.R);
+  const int nv1 = vs.nv1, nv2 = vs.nv2, R = vs.R, nc = g.nx * g.ny;
   const int cell = j * g.nx + i;
-  float* c2t = tb;
-  float* c2q = tb + nv2;
-  float* c2c = tb + 2 * nv2;
-  float* e2t = tb + 3 * nv2;
-  float* g2t = tb + 4 * nv2;
-  float* v2t = tb + 5 * nv2;
-  float* s0t = tb + 6 * nv2;
-  float* s1t = tb + 7 * nv2;
-  float* s2t = tb + 8 * nv2;
-  float* wlt = tb + 9 * nv2;
-  float* E1t = tb + 10 * nv2;
-  float* E2t = tb + 11 * nv2;
-  float* E3t = tb + 12 * nv2;
+  // row tables grouped for 16-byte shared loads: TS = (s0, s1, s2) for the moments of Z*;
+  // TA = (e2, e2 c2, e2 c2^2, e2 c2^3), TB = (wl, om1 - wl, g2, c2), TC = (c2^2, c2^3) for the
+  // update and the heat flux
+  float4* TS = reinterpret_cast<float4*>(tb);
+  float4* TA = TS + nv2;
+  float4* TB = TA + nv2;
+  float2* TC = reinterpret_cast<float2*>(TB + nv2);
   const int lane = threadIdx.x & 31, k = lane % nv1, r = lane / nv1;
-  const bool active = r < a.R;
-  const float* pf = a.pf;
-  const float u1 = __ldg(pf + F_U1 * nc + cell), u2 = __ldg(pf + F_U2 * nc + cell);
-  const float inv2T = __ldg(pf + F_INV2T * nc + cell), iT = __ldg(pf + F_IT * nc + cell);
-  const float Ti11h = __ldg(pf + F_TI11H * nc + cell), Ti12 = __ldg(pf + F_TI12 * nc + cell);
-  const float Ti22h = __ldg(pf + F_TI22H * nc + cell);
-  const float om1 = __ldg(pf + F_OM1 * nc + cell), om1kap = __ldg(pf + F_OM1KAP * nc + cell);
-  const float gam0 = __ldg(pf + F_GAM0 * nc + cell), ome = __ldg(pf + F_OME * nc + cell);
-  for (int l = lane; l < nv2; l += 32) {
-    const float v2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min);
-    const float c2 = v2 - u2;
-    const float q = c2 * c2;
-    const float e2 = expf(-q * inv2T);
-    const float av = fabsf(v2);
-    const float sg = -av * a.gf.idy;
-    c2t[l] = c2;
-    c2q[l] = q;
-    c2c[l] = q * c2;
-    e2t[l] = e2;
-    g2t[l] = expf(-Ti22h * q);
-    v2t[l] = v2;
-    s0t[l] = sg;
-    s1t[l] = sg * c2;
-    s2t[l] = sg * q;
-    wlt[l] = om1 * (av * a.dtidy);
-    E1t[l] = e2 * c2;
-    E2t[l] = e2 * q;
-    E3t[l] = e2 * q * c2;
+  const bool active = r < R;
+  const float fv = load_fields(a.pf, nc, cell);
+  const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
+  const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT);
+  const float Ti11h = field(fv, F_TI11H), Ti12 = field(fv, F_TI12), Ti22h = field(fv, F_TI22H);
+  const float om1 = field(fv, F_OM1), om1kap = field(fv, F_OM1KAP);
+  const float gam0 = field(fv, F_GAM0), ome = field(fv, F_OME);
+  const float w01 = field(fv, F_W01), w02 = field(fv, F_W02), w03 = field(fv, F_W03);
+  const float w10 = field(fv, F_W10), w11 = field(fv, F_W11), w12 = field(fv, F_W12);
+  const float w20 = field(fv, F_W20), w21 = field(fv, F_W21), w30 = field(fv, F_W30);
+  // tables; nneg = rows with v2 < 0 (v2 increases with l): the upwind side of a row is an
+  // integer comparison
+  int nneg = 0;
+  for (int l0 = 0; l0 < nv2; l0 += 32) {
+    const int l = l0 + lane;
+    bool neg = false;
+    if (l < nv2) {
+      const float v2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min);
+      const float c2 = v2 - u2;
+      const float q = c2 * c2;
+      const float e2 = expf(-q * inv2T);
+      const float av = fabsf(v2);
+      const float sg = -av * a.gf.idy;
+      const float wl = om1 * (av * a.dtidy);
+      TS[l] = make_float4(sg, sg * c2, sg * q, 0.f);
+      TA[l] = make_float4(e2, e2 * c2, e2 * q, e2 * q * c2);
+      TB[l] = make_float4(wl, om1 - wl, expf(-Ti22h * q), c2);
+      TC[l] = make_float2(q, q * c2);
+      neg = v2 < 0.f;
+    }
+    nneg += __popc(__ballot_sync(0xffffffffu, neg));
   }
   const float v1 = fmaf(k + 0.5f, a.gf.dv1, a.gf.v1min);
   const float c1 = v1 - u1;
@@ -249,16 +301,20 @@ __device__ __forceinline__ void wy_sweep(const FusedF32& a, int i, int j, const 
   __syncwarp();
   float E0 = 0.f, E1 = 0.f, E2 = 0.f;
   if (active) {
-    for (int l = r; l < nv2; l += a.R) {
+#pragma unroll
+    for (int m = 0; m < vs.nr; ++m) {
+      const int l = r + m * R;
+      if (!VShape<NV1, NV2>::fixed && l >= nv2) break;
       const float gv = rc[l * nv1 + k];
-      const bool top = v2t[l] < 0.f;
+      const bool top = l < nneg;
       const float* src = top ? srct : srcb;
       const int lu = (top ? mt : mb) ? nv2 - 1 - l : l;
       const float gu = (top ? zt : zb) ? 0.f : src[lu * nv1 + k];
       const float d = gu - gv;
-      E0 = fmaf(s0t[l], d, E0);
-      E1 = fmaf(s1t[l], d, E1);
-      E2 = fmaf(s2t[l], d, E2);
+      const float4 ts = TS[l];
+      E0 = fmaf(ts.x, d, E0);
+      E1 = fmaf(ts.y, d, E1);
+      E2 = fmaf(ts.z, d, E2);
     }
   }
   float S[4] = {E0, c1 * E0, E1, fmaf(c1q, E0, E2)};
@@ -266,65 +322,62 @@ __device__ __forceinline__ void wy_sweep(const FusedF32& a, int i, int j, const 
   const float b0 = fmaf(-S[3], inv2T, 2.f * S[0]);
   const float b1 = S[1] * iT, b2 = S[2] * iT;
   const float gm = fmaf(0.25f * S[3], iT * iT, -S[0] * inv2T);
-  const float w01 = __ldg(pf + F_W01 * nc + cell), w02 = __ldg(pf + F_W02 * nc + cell);
-  const float w03 = __ldg(pf + F_W03 * nc + cell), w10 = __ldg(pf + F_W10 * nc + cell);
-  const float w11 = __ldg(pf + F_W11 * nc + cell), w12 = __ldg(pf + F_W12 * nc + cell);
-  const float w20 = __ldg(pf + F_W20 * nc + cell), w21 = __ldg(pf + F_W21 * nc + cell);
-  const float w30 = __ldg(pf + F_W30 * nc + cell);
   const float C0 = om1kap * fmaf(gm, c1q, fmaf(b1, c1, b0)) - c1 * fmaf(c1, fmaf(c1, w03, w02), w01) - ome;
   const float C1 = fmaf(om1kap, b2, -fmaf(c1, fmaf(c1, w12, w11), w10));
   const float C2 = fmaf(om1kap, gm, -fmaf(c1, w21, w20));
   const float C3 = -w30;
   const float e1 = expf(-c1q * inv2T);
   const float A0 = e1 * C0, A1 = e1 * C1, A2 = e1 * C2, A3 = e1 * C3;
-  const float gam1 = gam0 * expf(-Ti11h * c1q);
   const float c2r = fmaf(r + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
-  float x = expf(-Ti12 * c1 * c2r);
-  const float rat = expf(-Ti12 * c1 * (a.R * a.gf.dv2));
+  // gam0 exp(-Ti11 c1^2 / 2) times the cross factor exp(-Ti12 c1 c2) of row l
+  float x = gam0 * expf(-Ti11h * c1q - Ti12 * c1 * c2r);
+  const float rat = expf(-Ti12 * c1 * (R * a.gf.dv2));
   float H0 = 0.f, H1 = 0.f, H2 = 0.f, H3 = 0.f;
   if (active) {
     const size_t nv = (size_t)nv1 * nv2;
     float* Go = a.Gout + (size_t)cell * nv + k;
-    for (int l = r; l < nv2; l += a.R) {
+#pragma unroll
+    for (int m = 0; m < vs.nr; ++m) {
+      const int l = r + m * R;
+      if (!VShape<NV1, NV2>::fixed && l >= nv2) break;
       const float gv = rc[l * nv1 + k];
-      const bool top = v2t[l] < 0.f;
+      const bool top = l < nneg;
       const float* src = top ? srct : srcb;
       const int lu = (top ? mt : mb) ? nv2 - 1 - l : l;
       const float gu = (top ? zt : zb) ? 0.f : src[lu * nv1 + k];
-      const float d = gu - gv;
-      float o = fmaf(wlt[l], d, om1 * gv);
-      o = fmaf(A0, e2t[l], o);
-      o = fmaf(A1, E1t[l], o);
-      o = fmaf(A2, E2t[l], o);
-      o = fmaf(A3, E3t[l], o);
-      o = fmaf(gam1, g2t[l] * x, o);
+      const float4 ta = TA[l];
+      const float4 tb4 = TB[l];
+      const float2 tc = TC[l];
+      float o = fmaf(tb4.x, gu, tb4.y * gv);
+      o = fmaf(A0, ta.x, o);
+      o = fmaf(A1, ta.y, o);
+      o = fmaf(A2, ta.z, o);
+      o = fmaf(A3, ta.w, o);
+      o = fmaf(tb4.z, x, o);
       x *= rat;
       Go[l * nv1] = o;
       H0 += o;
-      H1 = fmaf(c2t[l], o, H1);
-      H2 = fmaf(c2q[l], o, H2);
-      H3 = fmaf(c2c[l], o, H3);
+      H1 = fmaf(tb4.w, o, H1);
+      H2 = fmaf(tc.x, o, H2);
+      H3 = fmaf(tc.y, o, H3);
     }
   }
   float Hs[4] = {c1q * c1 * H0, c1q * H1, c1 * H2, H3};
   warp_allsum4(Hs);
-  if (lane == 0) {
-    for (int m = 0; m < 4; ++m) {
-      a.Hf[(2 * m) * nc + cell] = Hs[m];
-      a.Hf[(2 * m + 1) * nc + cell] = 0.f;
-    }
-  }
+  if (lane < 8) a.Hf[lane * nc + cell] = (lane & 1) ? 0.f : Hs[lane >> 1];
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(32 * kFusedWarps) k_micro_fused_f32(FusedF32 a) {
+template <int NV1, int NV2>
+__global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_fused_f32(FusedF32 a) {
   extern __shared__ float smf[];
   const KGrid& g = a.g;
   const int nv = g.nv1 * g.nv2;
   const int w = threadIdx.x >> 5;
-  const int per_warp = 3 * nv + 17 * g.nv2;
+  const int ring_f = (3 * nv + 3) / 4 * 4;
+  const int per_warp = ring_f + 18 * g.nv2 + (g.nv2 & 1) * 2;
   float* ring = smf + (size_t)w * per_warp;
-  float* xt = ring + 3 * nv;
+  float* xt = ring + ring_f;
   float* yt = xt + 4 * g.nv2;
   const int gw = blockIdx.x * kFusedWarps + w;
   if (gw >= g.nx * a.nseg) return;  // whole warp leaves; no CTA-wide barrier is used below
@@ -336,11 +389,11 @@ __global__ void __launch_bounds__(32 * kFusedWarps) k_micro_fused_f32(FusedF32 a
   const bool pery = a.p.bc[2] == MM_BC_PERIODIC;
   // position p = j - j0 + 1 of a row in the march; its G* lives in ring slot p % 3
   auto slot = [&](int pos) { return ring + (size_t)(pos % 3) * nv; };
-  if (j0 > 0 || pery) wx_sweep(a, i, j0 > 0 ? j0 - 1 : g.ny - 1, slot(0), xt);
-  wx_sweep(a, i, j0, slot(1), xt);
+  if (j0 > 0 || pery) wx_sweep<NV1, NV2>(a, i, j0 > 0 ? j0 - 1 : g.ny - 1, slot(0), xt);
+  wx_sweep<NV1, NV2>(a, i, j0, slot(1), xt);
   for (int j = j0; j < j1; ++j) {
     const int pos = j - j0 + 1;
-    if (j + 1 < g.ny || pery) wx_sweep(a, i, j + 1 < g.ny ? j + 1 : 0, slot(pos + 1), xt);
+    if (j + 1 < g.ny || pery) wx_sweep<NV1, NV2>(a, i, j + 1 < g.ny ? j + 1 : 0, slot(pos + 1), xt);
     if (diffuse_wall_cell(g, a.p, i, j)) continue;  // finished by the wall kernel
     const float* rc = slot(pos);
     const bool hasb = j > 0 || pery, hast = j < g.ny - 1 || pery;
@@ -350,8 +403,17 @@ __global__ void __launch_bounds__(32 * kFusedWarps) k_micro_fused_f32(FusedF32 a
     const bool zb = !hasb && a.p.bc[2] == MM_BC_DIFFUSE;
     const bool mt = !hast && a.p.bc[3] == MM_BC_SPECULAR;
     const bool zt = !hast && a.p.bc[3] == MM_BC_DIFFUSE;
-    wy_sweep(a, i, j, rc, srcb, mb, zb, srct, mt, zt, yt);
+    wy_sweep<NV1, NV2>(a, i, j, rc, srcb, mb, zb, srct, mt, zt, yt);
   }
+}
+
+// The kernel instantiation for a velocity mesh: compile-time shapes for 32^2, 24^2 and 16^2.
+template <typename F>
+void with_fused_kernel(const KGrid& g, F&& f) {
+  if (g.nv1 == 32 && g.nv2 == 32) f(k_micro_fused_f32<32, 32>);
+  else if (g.nv1 == 24 && g.nv2 == 24) f(k_micro_fused_f32<24, 24>);
+  else if (g.nv1 == 16 && g.nv2 == 16) f(k_micro_fused_f32<16, 16>);
+  else f(k_micro_fused_f32<0, 0>);
 }
 
 }  // namespace
@@ -361,19 +423,24 @@ KGridF grid_f32(const KGrid& g) {
                 (float)g.idy};
 }
 
+// Shared memory per CTA: per warp a three-row ring of G* (rounded up to 16 bytes), the x-sweep
+// tables (2 float2 per row) and the y-sweep tables (3 float4 + 1 float2 per row), the whole
+// padded to a multiple of 16 bytes so that every warp's float4 tables stay aligned.
 static size_t fused_smem(const KGrid& g) {
-  return sizeof(float) * kFusedWarps * (3 * (size_t)g.nv1 * g.nv2 + 17 * (size_t)g.nv2);
+  const size_t nv = (size_t)g.nv1 * g.nv2;
+  const size_t per_warp = (3 * nv + 3) / 4 * 4 + 18 * (size_t)g.nv2 + (g.nv2 & 1) * 2;
+  return sizeof(float) * kFusedWarps * per_warp;
 }
 
 int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
   (void)ms;
   const size_t smem = fused_smem(g);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_micro_fused_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_micro_fused_f32, 32 * kFusedWarps,
-                                                smem);
+  with_fused_kernel(g, [&](auto kern) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kFusedWarps, smem);
+  });
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -391,9 +458,6 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
                             const MicroShape& ms, int nseg, cudaStream_t s) {
   (void)ms;
   const size_t smem = fused_smem(g);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_micro_fused_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
   FusedF32 a;
   a.Gin = Gin;
   a.Gout = Gout;
@@ -409,7 +473,11 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
   a.nseg = nseg;
   a.seg_rows = (g.ny + nseg - 1) / nseg;
   const int warps = g.nx * nseg;
-  k_micro_fused_f32<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, smem, s>>>(a);
+  with_fused_kernel(g, [&](auto kern) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, smem, s>>>(a);
+  });
 }
 
 }  // namespace mmk
