@@ -12,14 +12,14 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    src = os.path.join(HERE, "mm_oracle.c")
+    srcs = [os.path.join(HERE, "mm_oracle.c"), os.path.join(HERE, "mm_oracle1d.c")]
     hdr = os.path.join(HERE, "mm_oracle.h")
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in srcs + [hdr])):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-Wall", "-o", tmp, src, "-lm"]
+           "-Wall", "-o", tmp] + srcs + ["-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

@@ -71,6 +71,30 @@ int orc_mms_exact(const orc_grid* g, const orc_params* p, double t, double eps, 
 /* The residual S at the velocity nodes ([nv2][nv1]) of the point (x, y), time t. */
 int orc_mms_source(const orc_grid* g, const orc_params* p, double eps, double t, double x,
                    double y, double* S);
+/* ---- 1D-1V micro-macro scheme for Boltzmann-BGK (Sections 3 and 4) ------------------------
+ * Q[3][nx] = (rho, rho u, E), E = rho T / 2 + rho u^2 / 2; G[nx][nv]; H[nx] = (eps/2) dv sum v^3 G.
+ * Boundary kinds ORC_BC_PERIODIC or ORC_BC_EXTRAP on sides 0 (left) and 1 (right). */
+typedef struct {
+  int nx;
+  double x0, x1;
+  int nv;
+  double vmin, vmax;
+} orc1d_grid;
+enum { ORC1D_TAU_HARDSPHERE = 0, ORC1D_TAU_CONST = 1 };
+typedef struct {
+  int bc[2];
+  int tau_model; /* ORC1D_TAU_HARDSPHERE: tau = (16/5) sqrt(T / (2 pi)) (Eq. collision_parameter_1d) */
+  double tau0;   /* ORC1D_TAU_CONST */
+} orc1d_params;
+/* nsteps steps (Eqs. 5-19 ... 5-27); with mms != 0 the manufactured source of Section 4.1 at
+ * t^n = t0 + n dt enters Ghat as (1/tau)(I - Pi_M)[S] and the macro update as the printed
+ * dt pi^{3/2} cos(2 pi (x - t^n)) (-8, 11, -7).  Returns 0, 4 (non-physical) or 1. */
+int orc1d_step(const orc1d_grid* g, const orc1d_params* p, double* Q, double* G, double* H,
+               double dt, double eps, int nsteps, int mms, double t0);
+/* Exact Q and g of the 1D manufactured solution at time t. */
+int orc1d_mms_exact(const orc1d_grid* g, double t, double eps, double* Q, double* G);
+/* dt = CFL dx / max|v|, N = ceil(t_final / dt), dt reset to t_final / N (Section 3.2). */
+double orc1d_dt(const orc1d_grid* g, double cfl, double t_final, int* nsteps_out);
 /* Global time step (Eq. CFL-2D-part1/part2 and the 1D rule of Section 3.2). */
 double orc_dt_for_cfl(const orc_grid* g, double cfl, double t_final, int form, int* nsteps_out);
 

@@ -30,6 +30,17 @@ class OrcParams(ctypes.Structure):
                 ("wall_U", ctypes.c_double * 4), ("wall_keep_es_term", ctypes.c_int)]
 
 
+class Orc1dGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("nv", ctypes.c_int), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double)]
+
+
+class Orc1dParams(ctypes.Structure):
+    _fields_ = [("bc", ctypes.c_int * 2), ("tau_model", ctypes.c_int), ("tau0", ctypes.c_double)]
+
+
+TAU1D_HARDSPHERE, TAU1D_CONST = 0, 1
+
 _lib = None
 
 
@@ -74,6 +85,15 @@ def lib():
         L.orc_mms_source.argtypes = [G, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, _c_double_p]
         L.orc_mms_source.restype = ctypes.c_int
+        G1, P1 = ctypes.POINTER(Orc1dGrid), ctypes.POINTER(Orc1dParams)
+        L.orc1d_step.argtypes = [G1, P1, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.orc1d_step.restype = ctypes.c_int
+        L.orc1d_mms_exact.argtypes = [G1, ctypes.c_double, ctypes.c_double, _c_double_p,
+                                      _c_double_p]
+        L.orc1d_mms_exact.restype = ctypes.c_int
+        L.orc1d_dt.argtypes = [G1, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+        L.orc1d_dt.restype = ctypes.c_double
         L.orc_ghat.argtypes = [G, P, _c_double_p, ctypes.c_double, _c_double_p]
         L.orc_ghat.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
@@ -181,6 +201,42 @@ def mms_source(grid, params, eps, t, x, y):
     if rc != 0:
         raise OracleError("orc_mms_source returned %d" % rc)
     return S
+
+
+def _g1(nx, nv, x0, x1, vmin, vmax):
+    return Orc1dGrid(int(nx), float(x0), float(x1), int(nv), float(vmin), float(vmax))
+
+
+def step1d(nx, nv, Q, G, dt, eps, nsteps, bc=(0, 0), tau_model=TAU1D_HARDSPHERE, tau0=1.0,
+           x0=0.0, x1=1.0, vmin=-6.5, vmax=6.5, mms=False, t0=0.0):
+    """1D-1V BGK micro-macro steps; returns (Q [3][nx], G [nx][nv], H [nx])."""
+    Q = np.array(Q, dtype=np.float64, order="C", copy=True)
+    G = np.array(G, dtype=np.float64, order="C", copy=True)
+    H = np.zeros(nx)
+    g = _g1(nx, nv, x0, x1, vmin, vmax)
+    p = Orc1dParams((ctypes.c_int * 2)(*bc), int(tau_model), float(tau0))
+    rc = lib().orc1d_step(ctypes.byref(g), ctypes.byref(p), _ptr(Q), _ptr(G), _ptr(H),
+                          float(dt), float(eps), int(nsteps), int(bool(mms)), float(t0))
+    if rc != 0:
+        raise OracleError("orc1d_step returned %d" % rc)
+    return Q, G, H
+
+
+def mms1d_exact(nx, nv, t, eps, x0=0.0, x1=1.0, vmin=-6.5, vmax=6.5):
+    Q = np.zeros((3, nx))
+    G = np.zeros((nx, nv))
+    g = _g1(nx, nv, x0, x1, vmin, vmax)
+    rc = lib().orc1d_mms_exact(ctypes.byref(g), float(t), float(eps), _ptr(Q), _ptr(G))
+    if rc != 0:
+        raise OracleError("orc1d_mms_exact returned %d" % rc)
+    return Q, G
+
+
+def dt1d(nx, nv, cfl, t_final, x0=0.0, x1=1.0, vmin=-6.5, vmax=6.5):
+    n = ctypes.c_int(0)
+    g = _g1(nx, nv, x0, x1, vmin, vmax)
+    dt = lib().orc1d_dt(ctypes.byref(g), float(cfl), float(t_final), ctypes.byref(n))
+    return dt, n.value
 
 
 def dt_for_cfl(grid, cfl, t_final, form):

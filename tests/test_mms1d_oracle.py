@@ -1,0 +1,115 @@
+"""Pins of the 1D-1V BGK oracle (Sections 3 and 4): the exact manufactured state against the
+formulas printed in Section 4.1, the printed closed-form macro source against the moments of
+the residual, conservation and preserved equilibria of the plain scheme, the AP limit, and
+Table tab5-2 of the 1D convergence study."""
+import json
+import math
+import os
+
+import numpy as np
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mms_1d.json")
+
+
+def _errors(n, eps=0.1):
+    dt, ns = O.dt1d(n, n, 0.95, 0.9351)
+    Q0, G0 = O.mms1d_exact(n, n, 0.0, eps)
+    Q, G, _ = O.step1d(n, n, Q0, G0, dt, eps, ns, mms=True)
+    Qe, Ge = O.mms1d_exact(n, n, ns * dt, eps)
+    W = np.array([1.0, 1.0, 2.0])[:, None]  # (rho, rho u, int v^2 f)
+    return (math.sqrt(np.sum((W * (Q - Qe)) ** 2) / np.sum((W * Qe) ** 2)),
+            math.sqrt(np.sum((G - Ge) ** 2) / np.sum(Ge ** 2)), ns)
+
+
+def test_exact_state_matches_the_printed_formulas():
+    n = 12
+    Q, G = O.mms1d_exact(n, 30, 0.3, 0.1)
+    x = (np.arange(n) + 0.5) / n
+    F = 2 + np.sin(2 * np.pi * (x - 0.3))
+    rho = 3 * math.sqrt(math.pi) * F
+    assert np.allclose(Q[0], rho, rtol=1e-14)
+    assert np.allclose(Q[1] / Q[0], -1 / 3, rtol=1e-14)
+    T = 2 * Q[2] / Q[0] - (Q[1] / Q[0]) ** 2
+    assert np.allclose(T, 25 / 18, rtol=1e-13)
+    v = -6.5 + (np.arange(30) + 0.5) * 13 / 30
+    g = (np.exp(-(v - 1) ** 2) + 2 * np.exp(-(v + 1) ** 2) - 1.8 * np.exp(-0.04 * (3 * v + 1) ** 2))
+    assert np.allclose(G, g[None] * F[:, None] / 0.1, rtol=1e-13, atol=1e-15)
+    # the printed Maxwellian 1.8 exp(-0.04 (3v+1)^2) is M[f] for rho = 3 sqrt(pi), u = -1/3,
+    # T = 25/18 (F = 1)
+    M = 3 * math.sqrt(math.pi) / math.sqrt(2 * math.pi * 25 / 18) * np.exp(-(v + 1 / 3) ** 2 / (2 * 25 / 18))
+    assert np.allclose(M, 1.8 * np.exp(-0.04 * (3 * v + 1) ** 2), rtol=1e-14)
+
+
+def test_printed_macro_source_equals_the_moments_of_the_residual():
+    # int (1, v, v^2/2) S dv = d/dt (rho, rho u, E) + d/dx (flux), by Gauss-Hermite-free quadrature
+    # on a fine wide mesh; compared with pi^{3/2} cos(2 pi (x - t)) (-8, 11, -7)
+    v = np.linspace(-12, 12, 48001)
+    dv = v[1] - v[0]
+    phi = np.exp(-(v - 1) ** 2) + 2 * np.exp(-(v + 1) ** 2)
+    M = 1.8 * np.exp(-0.04 * (3 * v + 1) ** 2)
+    for (t, x) in ((0.0, 0.1), (0.4, 0.77)):
+        F = 2 + np.sin(2 * np.pi * (x - t))
+        Fx = 2 * np.pi * np.cos(2 * np.pi * (x - t))
+        tau = 16 / 5 * math.sqrt(25 / 18 / (2 * math.pi))
+        S = phi * (-Fx + v * Fx) - (tau / 0.1) * (M - phi) * F
+        mom = [np.sum(S * m) * dv for m in (1, v, 0.5 * v * v)]
+        want = math.pi ** 1.5 * math.cos(2 * math.pi * (x - t)) * np.array([-8, 11, -7])
+        assert np.allclose(mom, want, rtol=0, atol=1e-9 * np.max(np.abs(want)))
+
+
+def test_plain_scheme_conserves_and_keeps_equilibria():
+    n, nv = 24, 40
+    x = (np.arange(n) + 0.5) / n
+    rho = 1 + 0.3 * np.sin(2 * np.pi * x)
+    u = 0.2 * np.cos(2 * np.pi * x)
+    T = 1 + 0.2 * np.sin(4 * np.pi * x)
+    Q0 = np.array([rho, rho * u, 0.5 * rho * T + 0.5 * rho * u * u])
+    Q, G, H = O.step1d(n, nv, Q0, np.zeros((n, nv)), 2e-3, 0.05, 20, vmin=-8, vmax=8)
+    assert np.allclose(Q.sum(axis=1), Q0.sum(axis=1), rtol=1e-13, atol=1e-13)
+    # a global Maxwellian stays put with g = 0
+    one = np.ones(n)
+    Qm = np.array([1.3 * one, 1.3 * 0.1 * one, 0.5 * 1.3 * 0.8 + 0.5 * 1.3 * 0.01 * one])
+    Qq, Gq, Hq = O.step1d(n, nv, Qm, np.zeros((n, nv)), 2e-3, 0.05, 10, vmin=-8, vmax=8)
+    assert np.max(np.abs(Qq - Qm)) <= 1e-13 and np.max(np.abs(Gq)) <= 1e-13
+
+
+def test_asymptotic_preserving_limit():
+    # eps -> 0: G^{n+1} -> Ghat^n (Eq. 5-25), for any G^n
+    n, nv = 16, 32
+    x = (np.arange(n) + 0.5) / n
+    rho = 1 + 0.2 * np.sin(2 * np.pi * x)
+    T = 1 + 0.1 * np.cos(2 * np.pi * x)
+    Q0 = np.array([rho, 0 * rho, 0.5 * rho * T])
+    G0 = np.random.default_rng(0).standard_normal((n, nv)) * 0.01
+    _, Ga, _ = O.step1d(n, nv, Q0, G0, 1e-3, 1e-12, 1, vmin=-8, vmax=8)
+    _, Gb, _ = O.step1d(n, nv, Q0, 0 * G0, 1e-3, 1e-12, 1, vmin=-8, vmax=8)
+    assert np.max(np.abs(Ga - Gb)) <= 1e-9 * np.max(np.abs(Gb))
+    # and Ghat is the printed closed form -(1/tau)((v-u)^3/(2T) - 3(v-u)/2) (T_x/T) M
+    v = -8 + (np.arange(nv) + 0.5) * 16 / nv
+    dx = 1 / n
+    Tf = 0.5 * (np.roll(T, -1) + T)
+    Tx = (Tf - np.roll(Tf, 1)) / (dx * T)
+    tau = 16 / 5 * np.sqrt(T / (2 * np.pi))
+    M = rho[:, None] / np.sqrt(2 * np.pi * T[:, None]) * np.exp(-v[None] ** 2 / (2 * T[:, None]))
+    gh = -(1 / tau)[:, None] * (v[None] ** 3 / (2 * T[:, None]) - 1.5 * v[None]) * Tx[:, None] * M
+    # (up to the weight dt tau / (eps + dt tau) = 1 - O(1e-9) at eps = 1e-12)
+    assert np.allclose(Gb, gh, rtol=0, atol=1e-8 * np.max(np.abs(gh)))
+
+
+def test_convergence_table():
+    """Table tab5-2 up to N = 160 (the finer rows run on the GPU).  The macro error in the
+    (rho, rho u, int v^2 f) convention reproduces the printed values to 3 %; the micro error lies
+    7-22 % below the printed one; the printed step count 4095 at N = 640 is checked by the rule."""
+    with open(GOLDEN) as f:
+        table = {r["n"]: r for r in json.load(f)["table_tab5_2"]}
+    assert O.dt1d(640, 640, 0.95, 0.9351)[1] == 4095
+    prev = None
+    for n in (10, 20, 40, 80, 160):
+        em, eu, _ = _errors(n)
+        assert abs(em / table[n]["macro"] - 1) <= 0.03, (n, em)
+        assert 0.75 <= eu / table[n]["micro"] <= 1.0, (n, eu)
+        if prev is not None:
+            assert abs(math.log2(prev[0] / em) - table[n]["macro_rate"]) <= 0.05
+        prev = (em, eu)
