@@ -241,6 +241,44 @@ mm_status mm_mms_enable(mm_ctx* c, int enable, double t0);
 mm_status mm_mms_set_exact(mm_ctx* c, double t, double eps);
 mm_status mm_mms_error(mm_ctx* c, double t, double eps, double* macro_err, double* micro_err);
 
+/* ---- 1D-1V micro-macro scheme for Boltzmann-BGK (Sections 3 and 4) --------------------------
+ * Q [3][nx] = (rho, rho u, E) with E = rho T / 2 + rho u^2 / 2 (Eq. 5-11), G [nx][nv] (FP64,
+ * host arrays), H [nx] = (eps/2) dv sum_k v_k^3 G_k (Eq. 5-26).  One step: Ghat (Eq. 5-19), the
+ * upwind Z and its projection (Eqs. 5-20, 5-24, 5-21), the update of Eq. (5-25), the heat flux,
+ * then the KFVS macro update of Eq. (5-27) with the fluxes of Eq. (flux1d_1/2).  Boundaries:
+ * MM_BC_PERIODIC (both sides) or MM_BC_EXTRAP (Eqs. 1d_extrap_micro_1/2, 1d_extrap_macro_1/2).
+ * tau: MM1D_TAU_HARDSPHERE = (16/5) sqrt(T / (2 pi)) (Eq. collision_parameter_1d) or
+ * MM1D_TAU_CONST = tau0.  1 <= nv <= 65536, nx >= 2; other arguments: MM_ERR_INVALID_ARG. */
+#define MM1D_TAU_HARDSPHERE 0
+#define MM1D_TAU_CONST 1
+typedef struct {
+  int nx;
+  double x0, x1;
+  int nv;
+  double vmin, vmax;
+} mm1d_grid;
+typedef struct {
+  int bc[2];
+  int tau_model;
+  double tau0;
+} mm1d_params;
+typedef struct mm1d_ctx mm1d_ctx;
+mm_status mm1d_create(const mm1d_grid* grid, const mm1d_params* params, void* cuda_stream,
+                      mm1d_ctx** out);
+/* G_host NULL: g = 0.  Synchronous. */
+mm_status mm1d_set_state(mm1d_ctx* c, const double* Q_host, const double* G_host);
+/* Asynchronous; non-physical states are reported by mm1d_get_state. */
+mm_status mm1d_step(mm1d_ctx* c, double dt, double eps, int nsteps);
+/* Any of the outputs may be NULL; synchronous; MM_ERR_NONPHYSICAL after a bad state. */
+mm_status mm1d_get_state(mm1d_ctx* c, double* Q_host, double* G_host, double* H_host);
+/* The 1D manufactured solution of Section 4.1 (periodic contexts): while enabled, each step adds
+ * (1/tau)(I - Pi_M)[S] at t^n to Ghat and dt pi^{3/2} cos(2 pi (x - t^n)) (-8, 11, -7) to the
+ * macro update; t^n starts at t0.  mm1d_mms_set_exact sets the exact state at time t. */
+mm_status mm1d_mms_enable(mm1d_ctx* c, int enable, double t0);
+mm_status mm1d_mms_set_exact(mm1d_ctx* c, double t, double eps);
+const char* mm1d_last_error(const mm1d_ctx* c);
+void mm1d_destroy(mm1d_ctx* c);
+
 /* Diagnostic: evaluate the table-driven exponential used by the phase-space kernels (Tang's
  * method, see the micro kernels) and the CUDA library exp on n FP64 device values x_dev, into
  * caller-owned device arrays; synchronises cuda_stream.  Used to test the kernels' exp against

@@ -36,6 +36,18 @@ class mm_params(ctypes.Structure):
                 ("precision", ctypes.c_int)]
 
 
+class mm1d_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("nv", ctypes.c_int), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double)]
+
+
+class mm1d_params(ctypes.Structure):
+    _fields_ = [("bc", ctypes.c_int * 2), ("tau_model", ctypes.c_int), ("tau0", ctypes.c_double)]
+
+
+TAU1D_HARDSPHERE, TAU1D_CONST = 0, 1
+
+
 EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device", "mm_step",
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
@@ -46,7 +58,9 @@ EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device"
            "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_forward",
            "mm_mlp_grad", "mm_mlp_train_step", "mm_mlp_last_error", "mm_mlp_destroy",
            "mm_set_closure", "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
-           "mm_closure_stats", "mm_mms_enable", "mm_mms_set_exact", "mm_mms_error"]
+           "mm_closure_stats", "mm_mms_enable", "mm_mms_set_exact", "mm_mms_error",
+           "mm1d_create", "mm1d_set_state", "mm1d_step", "mm1d_get_state", "mm1d_mms_enable",
+           "mm1d_mms_set_exact", "mm1d_last_error", "mm1d_destroy"]
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 39, 64, 4, 6980
 
@@ -129,6 +143,20 @@ def load(build_if_needed: bool = True):
     L.mm_closure_flags.argtypes = [vp, vp]
     L.mm_closure_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]
+    G1, P1 = ctypes.POINTER(mm1d_grid), ctypes.POINTER(mm1d_params)
+    L.mm1d_create.argtypes = [G1, P1, vp, ctypes.POINTER(vp)]
+    L.mm1d_set_state.argtypes = [vp, vp, vp]
+    L.mm1d_step.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.mm1d_get_state.argtypes = [vp, vp, vp, vp]
+    L.mm1d_mms_enable.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+    L.mm1d_mms_set_exact.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    L.mm1d_last_error.argtypes = [vp]
+    L.mm1d_last_error.restype = ctypes.c_char_p
+    L.mm1d_destroy.argtypes = [vp]
+    L.mm1d_destroy.restype = None
+    for name in ["mm1d_create", "mm1d_set_state", "mm1d_step", "mm1d_get_state",
+                 "mm1d_mms_enable", "mm1d_mms_set_exact"]:
+        getattr(L, name).restype = ctypes.c_int
     L.mm_mms_enable.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     L.mm_mms_set_exact.argtypes = [vp, ctypes.c_double, ctypes.c_double]
     L.mm_mms_error.argtypes = [vp, ctypes.c_double, ctypes.c_double, _dp, _dp]
@@ -450,6 +478,66 @@ class MLP:
                                              _host_f32(loss, 1) if want_loss else None),
                     "mm_mlp_train_step")
         return float(loss[0]) if want_loss else None
+
+
+class Solver1D:
+    """The 1D-1V BGK micro-macro scheme (mm1d_*)."""
+
+    def __init__(self, nx, nv, x0=0.0, x1=1.0, vmin=-6.5, vmax=6.5, bc=(0, 0),
+                 tau_model=TAU1D_HARDSPHERE, tau0=1.0, stream=0):
+        self.nx, self.nv = nx, nv
+        self.L = load()
+        g = mm1d_grid(int(nx), float(x0), float(x1), int(nv), float(vmin), float(vmax))
+        p = mm1d_params((ctypes.c_int * 2)(*bc), int(tau_model), float(tau0))
+        self.ctx = ctypes.c_void_p()
+        st = self.L.mm1d_create(ctypes.byref(g), ctypes.byref(p), ctypes.c_void_p(int(stream)),
+                                ctypes.byref(self.ctx))
+        if st != MM_OK:
+            raise MMError(st, "mm1d_create rejected the grid/parameters or could not allocate")
+
+    def _check(self, st, what):
+        if st != MM_OK:
+            raise MMError(st, "%s: %s" % (what, self.L.mm1d_last_error(self.ctx).decode()))
+
+    def close(self):
+        if self.ctx:
+            self.L.mm1d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, Q, G=None):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        G = None if G is None else np.ascontiguousarray(G, dtype=np.float64)
+        self._check(self.L.mm1d_set_state(self.ctx, _host_ptr(Q, 3 * self.nx),
+                                          _host_ptr(G, self.nx * self.nv)), "mm1d_set_state")
+
+    def step(self, dt, eps, nsteps=1):
+        self._check(self.L.mm1d_step(self.ctx, float(dt), float(eps), int(nsteps)), "mm1d_step")
+
+    def get_state(self):
+        Q = np.empty((3, self.nx))
+        G = np.empty((self.nx, self.nv))
+        H = np.empty(self.nx)
+        self._check(self.L.mm1d_get_state(self.ctx, Q.ctypes.data, G.ctypes.data, H.ctypes.data),
+                    "mm1d_get_state")
+        return Q, G, H
+
+    def mms_enable(self, enable=True, t0=0.0):
+        self._check(self.L.mm1d_mms_enable(self.ctx, int(enable), float(t0)), "mm1d_mms_enable")
+
+    def mms_set_exact(self, t, eps):
+        self._check(self.L.mm1d_mms_set_exact(self.ctx, float(t), float(eps)), "mm1d_mms_set_exact")
 
 
 class BatchSolver:

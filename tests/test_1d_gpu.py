@@ -1,0 +1,86 @@
+"""The 1D-1V BGK scheme on the GPU (mm1d_*) against the oracle: plain steps with periodic and
+extrapolation boundaries, manufactured-source steps, and Table tab5-2 on all printed meshes
+N = 10 ... 640."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_21832_gb300 import api
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mms_1d.json")
+
+
+def _state(n, seed):
+    rng = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    rho = 1 + 0.3 * np.sin(2 * np.pi * x + rng.uniform(0, 6))
+    u = 0.2 * np.cos(2 * np.pi * x + rng.uniform(0, 6))
+    T = 1 + 0.2 * np.sin(4 * np.pi * x + rng.uniform(0, 6))
+    return np.array([rho, rho * u, 0.5 * rho * T + 0.5 * rho * u * u])
+
+
+CASES = [("periodic", (0, 0), 1e-2, 37, 45), ("extrap", (1, 1), 1e-1, 50, 33),
+         ("periodic_const_tau", (0, 0), 1.0, 20, 300)]
+
+
+@pytest.mark.parametrize("name,bc,eps,nx,nv", CASES)
+def test_plain_steps_match_the_oracle(name, bc, eps, nx, nv):
+    Q0 = _state(nx, nx)
+    G0 = np.random.default_rng(nv).standard_normal((nx, nv)) * 0.01
+    kw = dict(vmin=-8, vmax=8, bc=bc)
+    tau_model = api.TAU1D_CONST if "const" in name else api.TAU1D_HARDSPHERE
+    dt = 0.5 * (1 / nx) / 8
+    Qo, Go, Ho = O.step1d(nx, nv, Q0, G0, dt, eps, 7, tau_model=tau_model, tau0=0.7, **kw)
+    with api.Solver1D(nx, nv, tau_model=tau_model, tau0=0.7, **kw) as s:
+        s.set_state(Q0, G0)
+        s.step(dt, eps, 7)
+        Q, G, H = s.get_state()
+    scale = np.max(np.abs(Qo), axis=1)
+    assert np.all(np.max(np.abs(Q - Qo), axis=1) <= 1e-12 * np.maximum(scale, np.max(Qo[0])))
+    assert np.max(np.abs(G - Go)) <= 1e-11 * np.max(np.abs(Go)) + 1e-13 / eps
+    assert np.max(np.abs(H - Ho)) <= 1e-11 * np.max(np.abs(Ho)) + 1e-15
+
+
+def test_source_steps_match_the_oracle():
+    n, nv, eps = 30, 42, 0.1
+    dt, _ = O.dt1d(n, nv, 0.95, 0.9351)
+    Q0, G0 = O.mms1d_exact(n, nv, 0.2, eps)
+    Qo, Go, Ho = O.step1d(n, nv, Q0, G0, dt, eps, 9, mms=True, t0=0.2)
+    with api.Solver1D(n, nv) as s:
+        s.mms_set_exact(0.2, eps)
+        s.mms_enable(True, 0.2)
+        s.step(dt, eps, 9)
+        Q, G, H = s.get_state()
+    assert np.max(np.abs(Q - Qo)) <= 1e-12 * np.max(np.abs(Qo))
+    assert np.max(np.abs(G - Go)) <= 1e-11 * np.max(np.abs(Go))
+
+
+def test_convergence_table_on_all_printed_meshes():
+    with open(GOLDEN) as f:
+        table = {r["n"]: r for r in json.load(f)["table_tab5_2"]}
+    prev = None
+    for n in (10, 20, 40, 80, 160, 320, 640):
+        dt, ns = O.dt1d(n, n, 0.95, 0.9351)
+        with api.Solver1D(n, n) as s:
+            s.mms_set_exact(0.0, 0.1)
+            s.mms_enable(True, 0.0)
+            s.step(dt, 0.1, ns)
+            Q, G, _ = s.get_state()
+        Qe, Ge = O.mms1d_exact(n, n, ns * dt, 0.1)
+        W = np.array([1.0, 1.0, 2.0])[:, None]
+        em = math.sqrt(np.sum((W * (Q - Qe)) ** 2) / np.sum((W * Qe) ** 2))
+        eu = math.sqrt(np.sum((G - Ge) ** 2) / np.sum(Ge ** 2))
+        print("N=%d (%d steps): macro %.6e (paper %.6e)  micro %.6e (paper %.6e)"
+              % (n, ns, em, table[n]["macro"], eu, table[n]["micro"]))
+        assert abs(em / table[n]["macro"] - 1) <= 0.03
+        assert 0.75 <= eu / table[n]["micro"] <= 1.0
+        if prev is not None:
+            assert abs(math.log2(prev / em) - table[n]["macro_rate"]) <= 0.05
+        prev = em
+    assert ns == 4095
