@@ -190,6 +190,9 @@ size_t smem_x(const mm_batch* b) {
 size_t smem_y(const mm_batch* b) {
   return sizeof(double) * (micro_body::kRed + micro_body::kYTables * (size_t)b->max_nv2);
 }
+size_t smem_wall(const mm_batch* b) {
+  return sizeof(double) * micro_body::wall_smem_doubles(b->max_nv1, b->max_nv2);
+}
 
 void apply_tune(mm_batch* b, const Tune& t) {
   b->tune = t;
@@ -210,7 +213,7 @@ void enqueue_batch_step(mm_batch* b) {
   k_batch_micro_y<<<C, T, smem_y(b), s>>>(b->Gs, b->G, b->H, b->prim, b->d_prob, b->d_start,
                                           b->nprob, cells, b->err);
   if (b->nwall > 0)
-    k_batch_micro_y_wall<<<std::min(b->nwall, C), T, sizeof(double) * micro_body::kRed, s>>>(
+    k_batch_micro_y_wall<<<std::min(b->nwall, C), T, smem_wall(b), s>>>(
         b->Gs, b->G, b->H, b->prim, b->walls, b->d_prob, b->d_wstart, b->nprob, b->nwall, b->err);
   for (int ph = 0; ph < 3; ++ph)
     k_batch_macro<<<cgrid, tb, 0, s>>>(ph, b->Q, b->H, b->mac, b->d_prob, b->d_start, b->nprob,
@@ -349,6 +352,9 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
     cudaFuncSetAttribute(k_batch_micro_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(k_batch_micro_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   }
+  if (smem_wall(b) > 48 * 1024)
+    cudaFuncSetAttribute(k_batch_micro_y_wall, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_wall(b));
   // default launch shape until the autotuner runs: whole warps covering the widest v1 mesh
   Tune t0{std::max(32, (b->max_nv1 + 31) / 32 * 32), 152 * 8};
   {

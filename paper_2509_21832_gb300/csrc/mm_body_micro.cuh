@@ -385,10 +385,11 @@ struct SideM {
   double rho, u1, u2, T;  // kind 0: neighbour prims; kind 3: wall density, velocity, temperature
 };
 
-__device__ __forceinline__ double maxw(double rho, double u1, double u2, double T, double v1,
-                                       double v2) {
-  const double a = v1 - u1, b = v2 - u2;
-  return rho / (2.0 * kPi * T) * exp(-(a * a + b * b) / (2.0 * T));
+
+// Shared memory of the wall body: reduction scratch, the x and y factors of five Maxwellians and
+// their prefactors.
+__host__ __device__ constexpr size_t wall_smem_doubles(int nv1, int nv2) {
+  return kRed + 5 * ((size_t)nv1 + (size_t)nv2) + 8;
 }
 
 // Eq. (twodim_wall_densities_1)
@@ -455,28 +456,63 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
   const Tg* Gb = Gs + (size_t)ub.cell * nv + k;
   const Tg* Gt = Gs + (size_t)ut.cell * nv + k;
   const double v1 = g.v1min + (k + 0.5) * g.dv1;
-  const double v1m = g.v1min + (nv1 - 1 - k + 0.5) * g.dv1;  // mirrored v1
   const double c1 = v1 - u1;
 
-  // upwind v . grad M at (k, l) with the ghost Maxwellians of each side
-  auto side_m = [&](int s, double m0, double va, double vb, double vmir) -> double {
-    const SideM& q = sd[s];
-    if (q.kind == 0) return maxw(q.rho, q.u1, q.u2, q.T, va, vb);
-    if (q.kind == 1) return m0;
-    if (q.kind == 2) return s < 2 ? maxw(rho, u1, u2, T, vmir, vb) : maxw(rho, u1, u2, T, va, vmir);
-    return maxw(q.rho, q.u1, q.u2, q.T, va, vb);
+  // The Maxwellians of the four sides (neighbour or wall ghost) and of the cell (index 4) are
+  // separable: rho/(2 pi T) X_q(v1) Y_q(v2).  Their factors are tabulated once per cell, so the
+  // upwind v . grad M needs no exponential per velocity.
+  double* Xt = sm + kRed;         // [5][nv1]
+  double* Yt = Xt + 5 * nv1;      // [5][nv2]
+  double* pfq = Yt + 5 * nv2;     // [5]
+  auto par = [&](int q, double& pu1, double& pu2, double& pT, double& prho) {
+    if (q < 4 && (sd[q].kind == 0 || sd[q].kind == 3)) {
+      pu1 = sd[q].u1; pu2 = sd[q].u2; pT = sd[q].T; prho = sd[q].rho;
+    } else {
+      pu1 = u1; pu2 = u2; pT = T; prho = rho;
+    }
   };
-  auto mup = [&](int l) -> double {
+  for (int e = t; e < 5 * nv1; e += blockDim.x) {
+    const int q = e / nv1, kk = e % nv1;
+    double a1, a2, aT, ar;
+    par(q, a1, a2, aT, ar);
+    const double d = g.v1min + (kk + 0.5) * g.dv1 - a1;
+    Xt[e] = exp(-d * d / (2.0 * aT));
+  }
+  for (int e = t; e < 5 * nv2; e += blockDim.x) {
+    const int q = e / nv2, ll = e % nv2;
+    double a1, a2, aT, ar;
+    par(q, a1, a2, aT, ar);
+    const double d = g.v2min + (ll + 0.5) * g.dv2 - a2;
+    Yt[e] = exp(-d * d / (2.0 * aT));
+  }
+  if (t < 5) {
+    double a1, a2, aT, ar;
+    par(t, a1, a2, aT, ar);
+    pfq[t] = ar / (2.0 * kPi * aT);
+  }
+  __syncthreads();
+
+  // upwind v . grad M at (k, l) with the ghost Maxwellians of each side
+  const int km = nv1 - 1 - k;
+  auto side_m = [&](int s, double m0, int l) -> double {
+    const SideM& q = sd[s];
+    if (q.kind == 1) return m0;
+    if (q.kind == 2)
+      return s < 2 ? pfq[4] * Xt[4 * nv1 + km] * Yt[4 * nv2 + l]
+                   : pfq[4] * Xt[4 * nv1 + k] * Yt[4 * nv2 + (nv2 - 1 - l)];
+    return pfq[s] * Xt[s * nv1 + k] * Yt[s * nv2 + l];
+  };
+  auto mup = [&](int l, double m0) -> double {
     const double v2 = g.v2min + (l + 0.5) * g.dv2;
-    const double v2m = g.v2min + (nv2 - 1 - l + 0.5) * g.dv2;
-    const double m0 = maxw(rho, u1, u2, T, v1, v2);
     double z = 0.0;
-    if (v1 > 0.0) z += v1 * ((m0 - side_m(0, m0, v1, v2, v1m)) / g.dx);
-    if (v1 < 0.0) z += v1 * ((side_m(1, m0, v1, v2, v1m) - m0) / g.dx);
-    if (v2 > 0.0) z += v2 * ((m0 - side_m(2, m0, v1, v2, v2m)) / g.dy);
-    if (v2 < 0.0) z += v2 * ((side_m(3, m0, v1, v2, v2m) - m0) / g.dy);
+    if (v1 > 0.0) z += v1 * ((m0 - side_m(0, m0, l)) / g.dx);
+    if (v1 < 0.0) z += v1 * ((side_m(1, m0, l) - m0) / g.dx);
+    if (v2 > 0.0) z += v2 * ((m0 - side_m(2, m0, l)) / g.dy);
+    if (v2 < 0.0) z += v2 * ((side_m(3, m0, l) - m0) / g.dy);
     return z;
   };
+  const double x4 = pfq[4] * Xt[4 * nv1 + k];
+  auto mcell = [&](int l) -> double { return x4 * Yt[4 * nv2 + l]; };
 
   // pass 1: moments of Z* and of the upwind v.grad M
   double E0 = 0, E1 = 0, E2 = 0, W0 = 0, W1 = 0, W2 = 0;
@@ -494,7 +530,7 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
       E0 += z;
       E1 += c2 * z;
       E2 += c2 * c2 * z;
-      const double mz = mup(l);
+      const double mz = mup(l, mcell(l));
       W0 += mz;
       W1 += c2 * mz;
       W2 += c2 * c2 * mz;
@@ -526,9 +562,9 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
       const int lu = u.mirror ? nv2 - 1 - l : l;
       const double gu = u.zero ? 0.0 : (double)Gu[lu * nv1];
       const double z = -fabs(v2) / g.dy * (gu - gv);
-      const double m = maxw(rho, u1, u2, T, v1, v2);
+      const double m = mcell(l);
       const double gstar2 = gv + dt * (kap * poly(S, c2) * (m / (rho / (2.0 * kPi * T))) - z);
-      const double mz = mup(l);
+      const double mz = mup(l, m);
       const double pim = kap * poly(Wm, c2) * (m / (rho / (2.0 * kPi * T)));
       double gh = -(1.0 / tau) * (mz - pim);
       if (p.keep_es) {

@@ -231,7 +231,10 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
                          double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s) {
   if (n_wall <= 0) return;
-  k_micro_y_wall<Tg><<<n_wall, ms.threads, sizeof(double) * micro_body::kRed, s>>>(
+  const size_t smem = sizeof(double) * micro_body::wall_smem_doubles(g.nv1, g.nv2);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_micro_y_wall<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_micro_y_wall<Tg><<<n_wall, ms.threads, smem, s>>>(
       Gs, Gout, H, prim, wall_cells, g, p, dt, eps, ms.R, err);
 }
 
