@@ -43,45 +43,106 @@ __device__ __forceinline__ void stage(const __nv_bfloat16* __restrict__ w, const
   __syncthreads();
 }
 
-// Inference of one sample: standardised output y (layer 2 is folded into layer 3 so that only
-// the first hidden layer is held in registers).
-__device__ __forceinline__ void infer1(const float* sw, const float* sn, const float* x, float* y) {
-  float xn[kIn];
+// Inference layout in shared memory: W1 rows padded to 40 inputs, W3 transposed to [kH][4], so
+// that every weight load is a 16-byte vector load.
+constexpr int kInP = 40;
+constexpr int kIW1 = 0, kIB1 = kIW1 + kH * kInP, kIW2 = kIB1 + kH, kIB2 = kIW2 + kH * kH,
+              kIW3 = kIB2 + kH, kIB3 = kIW3 + kH * kOut, kINP = kIB3 + kOut;
+static_assert(kInP % 4 == 0 && kIn < kInP && kOut == 4, "inference layout");
+static_assert(kIB1 % 4 == 0 && kIW2 % 4 == 0 && kIW3 % 4 == 0 && kIB3 % 4 == 0, "alignment");
+constexpr int kInferThreads = 128;
+
+__device__ __forceinline__ void stage_infer(const __nv_bfloat16* __restrict__ w,
+                                            const float* __restrict__ norm, float* sw,
+                                            float* sn) {
+  for (int q = threadIdx.x; q < kH * kInP; q += blockDim.x) {
+    const int o = q / kInP, i = q % kInP;
+    sw[kIW1 + q] = i < kIn ? __bfloat162float(w[kW1 + o * kIn + i]) : 0.f;
+  }
+  for (int q = threadIdx.x; q < kH; q += blockDim.x) {
+    sw[kIB1 + q] = __bfloat162float(w[kB1 + q]);
+    sw[kIB2 + q] = __bfloat162float(w[kB2 + q]);
+    for (int o = 0; o < kOut; ++o) sw[kIW3 + q * kOut + o] = __bfloat162float(w[kW3 + o * kH + q]);
+  }
+  for (int q = threadIdx.x; q < kH * kH; q += blockDim.x) sw[kIW2 + q] = __bfloat162float(w[kW2 + q]);
+  for (int q = threadIdx.x; q < kOut; q += blockDim.x) sw[kIB3 + q] = __bfloat162float(w[kB3 + q]);
+  for (int q = threadIdx.x; q < 2 * kIn + 2 * kOut; q += blockDim.x) sn[q] = norm[q];
+  __syncthreads();
+}
+
+// Inference of one sample from its standardised inputs: standardised output y (layer 2 is folded
+// into layer 3 so that only the first hidden layer is held in registers).  The products are
+// accumulated in the order of the inputs, as in the training kernels.
+__device__ __forceinline__ void infer1(const float* sw, const float xn[kInP], float y[kOut]) {
+  const float4* W1 = reinterpret_cast<const float4*>(sw + kIW1);
+  const float4* W2 = reinterpret_cast<const float4*>(sw + kIW2);
+  const float4* W3 = reinterpret_cast<const float4*>(sw + kIW3);
+  float a1[kH];  // fully unrolled loops keep a1 in registers
 #pragma unroll
-  for (int i = 0; i < kIn; ++i) xn[i] = (x[i] - sn[i]) * sn[kIn + i];
-  float a1[kH];
-#pragma unroll 4
   for (int o = 0; o < kH; ++o) {
-    float acc = sw[kB1 + o];
+    float acc = sw[kIB1 + o];
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) acc = fmaf(sw[kW1 + o * kIn + i], xn[i], acc);
+    for (int q = 0; q < kInP / 4; ++q) {
+      const float4 wv = W1[o * (kInP / 4) + q];
+      acc = fmaf(wv.x, xn[4 * q], acc);
+      acc = fmaf(wv.y, xn[4 * q + 1], acc);
+      acc = fmaf(wv.z, xn[4 * q + 2], acc);
+      acc = fmaf(wv.w, xn[4 * q + 3], acc);
+    }
     a1[o] = gelu(acc);
   }
-#pragma unroll
-  for (int o = 0; o < kOut; ++o) y[o] = sw[kB3 + o];
+  y[0] = sw[kIB3];
+  y[1] = sw[kIB3 + 1];
+  y[2] = sw[kIB3 + 2];
+  y[3] = sw[kIB3 + 3];
   for (int o2 = 0; o2 < kH; ++o2) {
-    float acc = sw[kB2 + o2];
+    float acc = sw[kIB2 + o2];
 #pragma unroll
-    for (int i = 0; i < kH; ++i) acc = fmaf(sw[kW2 + o2 * kH + i], a1[i], acc);
+    for (int q = 0; q < kH / 4; ++q) {
+      const float4 wv = W2[o2 * (kH / 4) + q];
+      acc = fmaf(wv.x, a1[4 * q], acc);
+      acc = fmaf(wv.y, a1[4 * q + 1], acc);
+      acc = fmaf(wv.z, a1[4 * q + 2], acc);
+      acc = fmaf(wv.w, a1[4 * q + 3], acc);
+    }
     const float a2 = gelu(acc);
-#pragma unroll
-    for (int o = 0; o < kOut; ++o) y[o] = fmaf(sw[kW3 + o * kH + o2], a2, y[o]);
+    const float4 w3 = W3[o2];
+    y[0] = fmaf(w3.x, a2, y[0]);
+    y[1] = fmaf(w3.y, a2, y[1]);
+    y[2] = fmaf(w3.z, a2, y[2]);
+    y[3] = fmaf(w3.w, a2, y[3]);
   }
 }
 
-__global__ void k_mlp_infer(const __nv_bfloat16* __restrict__ w, const float* __restrict__ norm,
-                            const float* __restrict__ X, float* __restrict__ Y, int n) {
-  __shared__ float sw[kNP];
+// One thread per sample; a CTA stages its samples' inputs through shared memory with coalesced
+// loads.
+__global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const __nv_bfloat16* __restrict__ w,
+                                                             const float* __restrict__ norm,
+                                                             const float* __restrict__ X,
+                                                             float* __restrict__ Y, int n) {
+  __shared__ __align__(16) float sw[kINP];
   __shared__ float sn[2 * kIn + 2 * kOut];
-  stage(w, norm, sw, sn);
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    float x[kIn], y[kOut];
+  __shared__ float sx[kInferThreads * kIn];
+  stage_infer(w, norm, sw, sn);
+  for (int s0 = blockIdx.x * kInferThreads; s0 < n; s0 += gridDim.x * kInferThreads) {
+    const int cnt = min(kInferThreads, n - s0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt * kIn; q += kInferThreads) sx[q] = X[(size_t)s0 * kIn + q];
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      float xn[kInP];
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) x[i] = X[(size_t)s * kIn + i];
-    infer1(sw, sn, x, y);
-#pragma unroll
-    for (int o = 0; o < kOut; ++o)
-      Y[(size_t)s * kOut + o] = y[o] * sn[2 * kIn + kOut + o] + sn[2 * kIn + o];
+      for (int i = 0; i < kIn; ++i) xn[i] = (sx[threadIdx.x * kIn + i] - sn[i]) * sn[kIn + i];
+      xn[kIn] = 0.f;
+      float y[kOut];
+      infer1(sw, xn, y);
+      float4 o;
+      o.x = y[0] * sn[2 * kIn + kOut] + sn[2 * kIn];
+      o.y = y[1] * sn[2 * kIn + kOut + 1] + sn[2 * kIn + 1];
+      o.z = y[2] * sn[2 * kIn + kOut + 2] + sn[2 * kIn + 2];
+      o.w = y[3] * sn[2 * kIn + kOut + 3] + sn[2 * kIn + 3];
+      reinterpret_cast<float4*>(Y)[s0 + threadIdx.x] = o;
+    }
   }
 }
 
@@ -238,8 +299,8 @@ mm_status ensure_work(mm_mlp* m, int n) {
 namespace mmk {
 void mlp_forward_async(const mm_mlp* m, const float* X, float* Y, int n, cudaStream_t s) {
   if (n <= 0) return;
-  const int blocks = std::min((n + 127) / 128, 152 * 8);
-  k_mlp_infer<<<blocks, 128, 0, s>>>(m->wb, m->norm, X, Y, n);
+  const int blocks = std::min((n + kInferThreads - 1) / kInferThreads, 152 * 8);
+  k_mlp_infer<<<blocks, kInferThreads, 0, s>>>(m->wb, m->norm, X, Y, n);
 }
 }  // namespace mmk
 
@@ -298,8 +359,8 @@ mm_status mm_mlp_get_params(mm_mlp* m, float* params_host, float* params_bf16_as
 mm_status mm_mlp_forward(mm_mlp* m, const float* X_dev, float* Y_dev, int n) {
   if (!m || !X_dev || !Y_dev || n < 0) return MM_ERR_INVALID_ARG;
   if (n == 0) return MM_OK;
-  const int blocks = std::min((n + 127) / 128, 152 * 8);
-  k_mlp_infer<<<blocks, 128, 0, m->stream>>>(m->wb, m->norm, X_dev, Y_dev, n);
+  const int blocks = std::min((n + kInferThreads - 1) / kInferThreads, 152 * 8);
+  k_mlp_infer<<<blocks, kInferThreads, 0, m->stream>>>(m->wb, m->norm, X_dev, Y_dev, n);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MM_OK : mfail(m, e, "mlp forward");
 }
