@@ -79,3 +79,22 @@ def test_device_bytes():
     assert b >= 2 * g.nphase * 8
     p.precision = I.PREC_G_FP32
     assert api.mm_device_bytes(g, p) < b
+
+
+def test_header_is_plain_c():
+    """include/mmkfvs.h compiles as C99 (pedantic) and as C++: a C ABI usable from both."""
+    import shutil
+    import subprocess
+    import tempfile
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    inc = os.path.join(ROOT, "include")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "use.c")
+        with open(src, "w") as f:
+            f.write('#include "mmkfvs.h"\nint main(void) { mm_grid g; (void)g; return 0; }\n')
+        subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                               "-fsyntax-only", "-I" + inc, src])
+        if shutil.which("g++"):
+            subprocess.check_call(["g++", "-x", "c++", "-std=c++17", "-Wall", "-Werror",
+                                   "-fsyntax-only", "-I" + inc, src])
