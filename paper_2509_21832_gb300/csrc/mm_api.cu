@@ -18,11 +18,11 @@ namespace {
 const char* const kKernelNames[] = {
     "prims",    "micro_x",          "micro_y",   "micro_y_wall",   "macro_x1",
     "macro_x2", "macro_y",          "h_unpack",  "micro_fused",    "closure_features",
-    "mlp_infer", "closure_decide",  "closure_lists", "closure_ghat"};
-constexpr int kNumKernels = 14;
+    "mlp_infer", "closure_decide",  "closure_lists", "closure_ghat", "closure_predict"};
+constexpr int kNumKernels = 15;
 enum {
   T_PRIMS = 0, T_MICRO_X, T_MICRO_Y, T_MICRO_YW, T_MACRO_X1, T_MACRO_X2, T_MACRO_Y, T_HUNPACK,
-  T_MICRO_FUSED, T_CL_FEATURES, T_MLP, T_CL_DECIDE, T_CL_LISTS, T_CL_GHAT
+  T_MICRO_FUSED, T_CL_FEATURES, T_MLP, T_CL_DECIDE, T_CL_LISTS, T_CL_GHAT, T_CL_PREDICT
 };
 
 struct TimedLaunch {
@@ -248,9 +248,9 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s, srcq); });
 }
 
-// Hybrid step with the learned closure (FP64): features and network on every cell, the decision
-// and work lists, g^n = Ghat(Q^n) on the cells the sweeps read whose g is not current, then the
-// micro sweeps on the micro cells (x sweep also on their y neighbours).
+// Hybrid step with the learned closure (FP64): features, network and decision on every cell (one
+// fused kernel), the work lists, g^n = Ghat(Q^n) on the cells the sweeps read whose g is not
+// current, then the micro sweeps on the micro cells (x sweep also on their y neighbours).
 void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   double* G = static_cast<double*>(c->G);
   double* Gs = static_cast<double*>(c->Gs);
@@ -259,12 +259,9 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   cudaStream_t s = c->stream;
   const int nc = (int)c->ncell;
   timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
-  timed(c, T_CL_FEATURES, [&] {
-    launch_closure_features(c->Q, c->prim, g, p, eps, dt, c->cX, c->caux, s);
-  });
-  timed(c, T_MLP, [&] { mlp_forward_async(c->mlp, c->cX, c->cY, nc, s); });
-  timed(c, T_CL_DECIDE, [&] {
-    launch_closure_decide(c->cY, c->caux, c->closure_thr, g, p, c->cflags, c->H, c->cstat, s);
+  timed(c, T_CL_PREDICT, [&] {
+    launch_closure_predict(c->Q, c->prim, c->mlp, g, p, eps, dt, c->closure_thr, c->cflags, c->H,
+                           c->caux, c->cstat, s);
   });
   timed(c, T_CL_LISTS, [&] {
     launch_closure_lists(c->cflags, c->cvalid, g, p, c->clists, c->ccounts, s);

@@ -4,6 +4,7 @@
 
 #include <cmath>
 
+#include "mm_exp.cuh"
 #include "mm_internal.cuh"
 
 namespace mmk {
@@ -85,7 +86,7 @@ __device__ __forceinline__ void abJK(const double q[6], int dir, double& a, doub
   const double iPn = 1.0 / Pn;
   const double s2 = 2.0 * Pn * ir;  // 2 th
   const double h = rsqrt(s2);       // 1 / sqrt(2 th)
-  a = kInvSqrtPi * (s2 * h) * exp(-(un * h) * (un * h));
+  a = kInvSqrtPi * (s2 * h) * expd(-(un * h) * (un * h));
   b = erf(un * h);
   if (dir == 1) {
     J[0] = rho;

@@ -19,10 +19,12 @@
 //    update and keep their g, which is read only after such a refresh.
 // Collection of training data uses k_closure_features before and k_closure_targets after a
 // plain step.
+#include <algorithm>
 #include <cmath>
 
 #include "mm_body_macro.cuh"
 #include "mm_body_micro.cuh"
+#include "mm_body_mlp.cuh"
 
 namespace mmk {
 
@@ -47,13 +49,13 @@ __device__ __forceinline__ bool boundary_cell(const KGrid& g, const KParams& p, 
          (j == 0 && p.bc[2] != MM_BC_PERIODIC) || (j == g.ny - 1 && p.bc[3] != MM_BC_PERIODIC);
 }
 
-// One thread per cell; the primitive variables of the stencil come from the prims kernel.
-__global__ void k_closure_features(const double* __restrict__ Q, const double* __restrict__ prim,
-                                   KGrid g, KParams p, double eps, double log10_eps, double dt,
-                                   float* __restrict__ X, double* __restrict__ aux) {
+// Features x[39] and (H_CE[4], scale) of cell c; the primitive variables of the stencil come from
+// the prims kernel.
+__device__ __forceinline__ void cell_features(const double* __restrict__ Q,
+                                              const double* __restrict__ prim, const KGrid& g,
+                                              const KParams& p, double eps, double log10_eps,
+                                              double dt, int c, float* x, double aux5[5]) {
   const int nc = g.nx * g.ny;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
   const int i = c % g.nx, j = c / g.nx;
   const double rho = prim[P_RHO * nc + c];
   const double u1 = prim[P_U1 * nc + c], u2 = prim[P_U2 * nc + c];
@@ -64,12 +66,13 @@ __global__ void k_closure_features(const double* __restrict__ Q, const double* _
   const double isT = 1.0 / sT;
   const double kn = eps * sT / (tau * fmin(g.dx, g.dy));
   const double ks = kn * isT;
-  float* x = X + (size_t)c * kF;
   int f = 0;
   double TL = T, TR = T, TB = T, TT = T;
+#pragma unroll
   for (int dj = -1; dj <= 1; ++dj) {
     bool my;
     const int nj = nb_index(j, dj, g.ny, p.bc[2], p.bc[3], my);
+#pragma unroll
     for (int di = -1; di <= 1; ++di) {
       if (di == 0 && dj == 0) continue;
       bool mx;
@@ -100,11 +103,71 @@ __global__ void k_closure_features(const double* __restrict__ Q, const double* _
   const double Tx = (0.5 * (TR + T) - 0.5 * (T + TL)) * g.idx;
   const double Ty = (0.5 * (TT + T) - 0.5 * (T + TB)) * g.idy;
   const double ep = eps * rho * T / tau;
-  aux[c] = -3.0 * ep * Tx;
-  aux[nc + c] = -ep * Ty;
-  aux[2 * nc + c] = -ep * Tx;
-  aux[3 * nc + c] = -3.0 * ep * Ty;
-  aux[4 * nc + c] = eps * rho * T * sT;
+  aux5[0] = -3.0 * ep * Tx;
+  aux5[1] = -ep * Ty;
+  aux5[2] = -ep * Tx;
+  aux5[3] = -3.0 * ep * Ty;
+  aux5[4] = eps * rho * T * sT;
+}
+
+__global__ void k_closure_features(const double* __restrict__ Q, const double* __restrict__ prim,
+                                   KGrid g, KParams p, double eps, double log10_eps, double dt,
+                                   float* __restrict__ X, double* __restrict__ aux) {
+  const int nc = g.nx * g.ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  float x[kF];
+  double a5[5];
+  cell_features(Q, prim, g, p, eps, log10_eps, dt, c, x, a5);
+  float* xo = X + (size_t)c * kF;
+#pragma unroll
+  for (int f = 0; f < kF; ++f) xo[f] = x[f];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) aux[m * nc + c] = a5[m];
+}
+
+// Features, network and decision of the hybrid step in one pass over the cells (persistent
+// CTAs, the network's weights staged once per CTA): the same arithmetic as k_closure_features,
+// k_mlp_infer and k_closure_decide in sequence, without the feature and output arrays.
+__global__ void __launch_bounds__(mlp_body::kInferThreads)
+    k_closure_predict(const double* __restrict__ Q, const double* __restrict__ prim,
+                      const __nv_bfloat16* __restrict__ w, const float* __restrict__ norm,
+                      KGrid g, KParams p, double eps, double log10_eps, double dt, float thr,
+                      unsigned char* __restrict__ flags, double* __restrict__ H,
+                      unsigned long long* __restrict__ nclosure) {
+  using namespace mlp_body;
+  __shared__ __align__(16) float sw[kINP];
+  __shared__ float sn[2 * kIn + 2 * kOut];
+  stage_infer(w, norm, sw, sn);
+  const int nc = g.nx * g.ny;
+  for (int base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {
+    const int c = base + threadIdx.x;
+    bool cl = false;
+    if (c < nc) {
+      float x[kF];
+      double a5[5];
+      cell_features(Q, prim, g, p, eps, log10_eps, dt, c, x, a5);
+      float xn[kInP];
+#pragma unroll
+      for (int i = 0; i < kIn; ++i) xn[i] = (x[i] - sn[i]) * sn[kIn + i];
+      xn[kIn] = 0.f;
+      float y[kOut];
+      infer1(sw, xn, y);
+      float ind = 0.f;
+#pragma unroll
+      for (int o = 0; o < kOut; ++o) {
+        y[o] = destandardise(y[o], sn, o);
+        ind = fmaxf(ind, fabsf(y[o]));
+      }
+      const int i = c % g.nx, j = c / g.nx;
+      cl = !boundary_cell(g, p, i, j) && ind <= thr;  // NaN fails the test: micro solve
+      flags[c] = cl ? 1 : 0;
+      if (cl)
+        for (int m = 0; m < kOut; ++m) H[m * nc + c] = fma(a5[4], (double)y[m], a5[m]);
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, cl);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(nclosure, (unsigned long long)__popc(b));
+  }
 }
 
 __global__ void k_closure_targets(const double* __restrict__ H, const double* __restrict__ aux,
@@ -288,6 +351,25 @@ void launch_closure_features(const double* Q, const double* prim, const KGrid& g
   const int nc = g.nx * g.ny;
   k_closure_features<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, g, p, eps, std::log10(eps), dt,
                                                       X, aux);
+}
+
+void launch_closure_predict(const double* Q, const double* prim, const mm_mlp* m,
+                            const KGrid& g, const KParams& p, double eps, double dt, double thr,
+                            unsigned char* flags, double* H, double* aux,
+                            unsigned long long* nclosure, cudaStream_t s) {
+  (void)aux;
+  const __nv_bfloat16* w;
+  const float* norm;
+  mlp_device_params(m, &w, &norm);
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_closure_predict, mlp_body::kInferThreads, 0);
+  const int nc = g.nx * g.ny;
+  const int need = (nc + mlp_body::kInferThreads - 1) / mlp_body::kInferThreads;
+  const int blocks = std::max(1, std::min(need, (nsm > 0 ? nsm : 1) * (per > 0 ? per : 1)));
+  k_closure_predict<<<blocks, mlp_body::kInferThreads, 0, s>>>(
+      Q, prim, w, norm, g, p, eps, std::log10(eps), dt, (float)thr, flags, H, nclosure);
 }
 
 void launch_closure_targets(const double* H, const double* aux, float* Y, const KGrid& g,

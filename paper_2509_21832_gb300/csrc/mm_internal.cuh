@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libmmkfvs (not part of the ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "mmkfvs.h"
@@ -169,8 +170,15 @@ void launch_mms_source(const double* prim, const double* phi, const double* gam,
 void launch_mms_errors(const double* Q, const double* G, const double* phi, double* sums,
                        const KGrid& g, const KParams& p, double t, double eps, double x0,
                        double y0, cudaStream_t s);
-// Network inference on the stream s (mm_mlp.cu).
+// Network inference on the stream s (mm_mlp.cu), and the network's device parameters (BF16
+// weights, FP32 normalisation) for kernels that evaluate it inline.
 void mlp_forward_async(const mm_mlp* m, const float* X, float* Y, int n, cudaStream_t s);
+void mlp_device_params(const mm_mlp* m, const __nv_bfloat16** w, const float** norm);
+// Fused features + network + decision of the hybrid step (one thread per cell, persistent CTAs).
+void launch_closure_predict(const double* Q, const double* prim, const mm_mlp* m,
+                            const KGrid& g, const KParams& p, double eps, double dt, double thr,
+                            unsigned char* flags, double* H, double* aux,
+                            unsigned long long* nclosure, cudaStream_t s);
 void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* in, float* out, size_t n, cudaStream_t s);
 void launch_convert_f32_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
