@@ -136,23 +136,38 @@ __global__ void __launch_bounds__(mlp_body::kInferThreads)
                       unsigned char* __restrict__ flags, double* __restrict__ H,
                       unsigned long long* __restrict__ nclosure) {
   using namespace mlp_body;
-  __shared__ __align__(16) float sw[kINP];
-  __shared__ float sn[2 * kIn + 2 * kOut];
+  extern __shared__ __align__(16) float smi[];
+  float* sw = smi;
+  float* sn = smi + kINP;
+  float* tile = smi + kINP + 88 + (threadIdx.x >> 5) * kTile;
   stage_infer(w, norm, sw, sn);
   const int nc = g.nx * g.ny;
+  const int lane = threadIdx.x & 31;
   for (int base = blockIdx.x * blockDim.x; base < nc; base += gridDim.x * blockDim.x) {
     const int c = base + threadIdx.x;
+    float x[kF];
+    double a5[5] = {0, 0, 0, 0, 1};
+    if (c < nc) {
+      cell_features(Q, prim, g, p, eps, log10_eps, dt, c, x, a5);
+    } else {
+#pragma unroll
+      for (int f = 0; f < kF; ++f) x[f] = sn[f];  // standardises to zero
+    }
+    float y[kOut];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if ((lane >> 4) == h) put_row(tile, lane & 15, x, sn);
+      __syncwarp();
+      infer16(sw, tile);
+      if ((lane >> 4) == h) {
+        const float* yr = tile + kTileY + (lane & 15) * 4;
+#pragma unroll
+        for (int o = 0; o < kOut; ++o) y[o] = yr[o];
+      }
+      __syncwarp();
+    }
     bool cl = false;
     if (c < nc) {
-      float x[kF];
-      double a5[5];
-      cell_features(Q, prim, g, p, eps, log10_eps, dt, c, x, a5);
-      float xn[kInP];
-#pragma unroll
-      for (int i = 0; i < kIn; ++i) xn[i] = (x[i] - sn[i]) * sn[kIn + i];
-      xn[kIn] = 0.f;
-      float y[kOut];
-      infer1(sw, xn, y);
       float ind = 0.f;
 #pragma unroll
       for (int o = 0; o < kOut; ++o) {
@@ -166,7 +181,7 @@ __global__ void __launch_bounds__(mlp_body::kInferThreads)
         for (int m = 0; m < kOut; ++m) H[m * nc + c] = fma(a5[4], (double)y[m], a5[m]);
     }
     const unsigned b = __ballot_sync(0xffffffffu, cl);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(nclosure, (unsigned long long)__popc(b));
+    if (lane == 0 && b) atomicAdd(nclosure, (unsigned long long)__popc(b));
   }
 }
 
@@ -364,11 +379,14 @@ void launch_closure_predict(const double* Q, const double* prim, const mm_mlp* m
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_closure_predict, mlp_body::kInferThreads, 0);
+  const size_t smem = mlp_body::infer_smem_bytes();
+  cudaFuncSetAttribute(k_closure_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_closure_predict, mlp_body::kInferThreads,
+                                                smem);
   const int nc = g.nx * g.ny;
   const int need = (nc + mlp_body::kInferThreads - 1) / mlp_body::kInferThreads;
   const int blocks = std::max(1, std::min(need, (nsm > 0 ? nsm : 1) * (per > 0 ? per : 1)));
-  k_closure_predict<<<blocks, mlp_body::kInferThreads, 0, s>>>(
+  k_closure_predict<<<blocks, mlp_body::kInferThreads, smem, s>>>(
       Q, prim, w, norm, g, p, eps, std::log10(eps), dt, (float)thr, flags, H, nclosure);
 }
 

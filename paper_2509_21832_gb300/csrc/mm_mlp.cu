@@ -24,34 +24,37 @@ using namespace mmk::mlp_body;
 
 namespace {
 
-// One thread per sample; a CTA stages its samples' inputs through shared memory with coalesced
-// loads.
+// Inference, 32 samples per warp pass (two m16 tiles); weights staged once per CTA.
 __global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const __nv_bfloat16* __restrict__ w,
                                                              const float* __restrict__ norm,
                                                              const float* __restrict__ X,
                                                              float* __restrict__ Y, int n) {
-  __shared__ __align__(16) float sw[kINP];
-  __shared__ float sn[2 * kIn + 2 * kOut];
-  __shared__ float sx[kInferThreads * kIn];
+  extern __shared__ __align__(16) float smi[];
+  float* sw = smi;
+  float* sn = smi + kINP;
+  float* tile = smi + kINP + 88 + (threadIdx.x >> 5) * kTile;
   stage_infer(w, norm, sw, sn);
-  for (int s0 = blockIdx.x * kInferThreads; s0 < n; s0 += gridDim.x * kInferThreads) {
-    const int cnt = min(kInferThreads, n - s0);
-    __syncthreads();
-    for (int q = threadIdx.x; q < cnt * kIn; q += kInferThreads) sx[q] = X[(size_t)s0 * kIn + q];
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-      float xn[kInP];
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * kInferThreads; base < n; base += gridDim.x * kInferThreads) {
+    const int s = base + threadIdx.x;  // this lane's sample
+    float x[kIn];
 #pragma unroll
-      for (int i = 0; i < kIn; ++i) xn[i] = (sx[threadIdx.x * kIn + i] - sn[i]) * sn[kIn + i];
-      xn[kIn] = 0.f;
-      float y[kOut];
-      infer1(sw, xn, y);
-      float4 o;
-      o.x = destandardise(y[0], sn, 0);
-      o.y = destandardise(y[1], sn, 1);
-      o.z = destandardise(y[2], sn, 2);
-      o.w = destandardise(y[3], sn, 3);
-      reinterpret_cast<float4*>(Y)[s0 + threadIdx.x] = o;
+    for (int i = 0; i < kIn; ++i) x[i] = s < n ? X[(size_t)s * kIn + i] : 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if ((lane >> 4) == h) put_row(tile, lane & 15, x, sn);
+      __syncwarp();
+      infer16(sw, tile);
+      if ((lane >> 4) == h && s < n) {
+        const float* yr = tile + kTileY + (lane & 15) * 4;
+        float4 o;
+        o.x = destandardise(yr[0], sn, 0);
+        o.y = destandardise(yr[1], sn, 1);
+        o.z = destandardise(yr[2], sn, 2);
+        o.w = destandardise(yr[3], sn, 3);
+        reinterpret_cast<float4*>(Y)[s] = o;
+      }
+      __syncwarp();
     }
   }
 }
@@ -215,7 +218,9 @@ void mlp_device_params(const mm_mlp* m, const __nv_bfloat16** w, const float** n
 void mlp_forward_async(const mm_mlp* m, const float* X, float* Y, int n, cudaStream_t s) {
   if (n <= 0) return;
   const int blocks = std::min((n + kInferThreads - 1) / kInferThreads, 152 * 8);
-  k_mlp_infer<<<blocks, kInferThreads, 0, s>>>(m->wb, m->norm, X, Y, n);
+  cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)infer_smem_bytes());
+  k_mlp_infer<<<blocks, kInferThreads, infer_smem_bytes(), s>>>(m->wb, m->norm, X, Y, n);
 }
 }  // namespace mmk
 
@@ -275,7 +280,10 @@ mm_status mm_mlp_forward(mm_mlp* m, const float* X_dev, float* Y_dev, int n) {
   if (!m || !X_dev || !Y_dev || n < 0) return MM_ERR_INVALID_ARG;
   if (n == 0) return MM_OK;
   const int blocks = std::min((n + kInferThreads - 1) / kInferThreads, 152 * 8);
-  k_mlp_infer<<<blocks, kInferThreads, 0, m->stream>>>(m->wb, m->norm, X_dev, Y_dev, n);
+  cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)infer_smem_bytes());
+  k_mlp_infer<<<blocks, kInferThreads, infer_smem_bytes(), m->stream>>>(m->wb, m->norm, X_dev,
+                                                                        Y_dev, n);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MM_OK : mfail(m, e, "mlp forward");
 }
