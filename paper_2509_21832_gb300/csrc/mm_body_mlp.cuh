@@ -43,8 +43,9 @@ constexpr int kIW1 = 0, kIB1 = kIW1 + kH * kS1, kIW2 = kIB1 + kH, kIB2 = kIW2 + 
 static_assert(kIn < 40 && kS1 >= 40 && kOut == 4 && kH == 64, "inference layout");
 static_assert(kIB1 % 4 == 0 && kIW2 % 4 == 0 && kIW3 % 4 == 0 && kIB3 % 4 == 0, "alignment");
 constexpr int kInferThreads = 128;
-// per-warp scratch: inputs [16][kS1], hidden activations [16][kS2], outputs [16][4]
-constexpr int kTileX = 0, kTileA = 16 * kS1, kTileY = kTileA + 16 * kS2, kTile = kTileY + 64;
+// per-warp scratch: inputs [16][kS1] and hidden activations [16][kS2] in the same place (a layer
+// reads all its input fragments before it writes), outputs [16][4]
+constexpr int kTileX = 0, kTileA = 0, kTileY = 16 * kS2, kTile = kTileY + 64;
 constexpr int kNormF = 2 * kIn + 2 * kOut;
 // dynamic shared memory of an inference CTA: weights, normalisation, one tile per warp
 constexpr size_t infer_smem_bytes() {
@@ -99,37 +100,40 @@ __device__ __forceinline__ void mma_tf32(float d[4], const unsigned a[4], unsign
 // of stride SW.  Fragment layout of m16n8k8 (lane = 4 group + t): A holds (row group, col t),
 // (row group + 8, col t), (row group, col t + 4), (row group + 8, col t + 4); B holds (k t, n group)
 // and (k t + 4, n group); D holds (row group, cols 2t, 2t + 1) and (row group + 8, same cols).
-// in may alias out: all A fragments are read before any output is written.
+// The k slices are the outer loop with the eight 16 x 8 output tiles accumulating in registers,
+// so in may alias out: every input is read before any output is written.
 template <int K, int SIN, int SW>
 __device__ __forceinline__ void hidden16(const float* in, const float* W, const float* bias,
                                          float* out) {
   const int lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
-  unsigned ah[K / 8][4], al[K / 8][4];
+  float d[kH / 8][4];
+#pragma unroll
+  for (int nt = 0; nt < kH / 8; ++nt) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.f;
 #pragma unroll
   for (int ks = 0; ks < K / 8; ++ks) {
     const int c = ks * 8 + t;
-    split_tf32(in[gq * SIN + c], ah[ks][0], al[ks][0]);
-    split_tf32(in[(gq + 8) * SIN + c], ah[ks][1], al[ks][1]);
-    split_tf32(in[gq * SIN + c + 4], ah[ks][2], al[ks][2]);
-    split_tf32(in[(gq + 8) * SIN + c + 4], ah[ks][3], al[ks][3]);
+    unsigned ah[4], al[4];
+    split_tf32(in[gq * SIN + c], ah[0], al[0]);
+    split_tf32(in[(gq + 8) * SIN + c], ah[1], al[1]);
+    split_tf32(in[gq * SIN + c + 4], ah[2], al[2]);
+    split_tf32(in[(gq + 8) * SIN + c + 4], ah[3], al[3]);
+#pragma unroll
+    for (int nt = 0; nt < kH / 8; ++nt) {
+      const float* Wr = W + (nt * 8 + gq) * SW + c;
+      const unsigned b0 = __float_as_uint(Wr[0]);
+      const unsigned b1 = __float_as_uint(Wr[4]);
+      mma_tf32(d[nt], ah, b0, b1);
+      mma_tf32(d[nt], al, b0, b1);
+    }
   }
   __syncwarp();
 #pragma unroll
   for (int nt = 0; nt < kH / 8; ++nt) {
-    float d[4] = {0.f, 0.f, 0.f, 0.f};
-    const float* Wr = W + (nt * 8 + gq) * SW + t;
-#pragma unroll
-    for (int ks = 0; ks < K / 8; ++ks) {
-      const unsigned b0 = __float_as_uint(Wr[ks * 8]);
-      const unsigned b1 = __float_as_uint(Wr[ks * 8 + 4]);
-      mma_tf32(d, ah[ks], b0, b1);
-      mma_tf32(d, al[ks], b0, b1);
-    }
     const int col = nt * 8 + 2 * t;
-    out[gq * kS2 + col] = gelu(d[0] + bias[col]);
-    out[gq * kS2 + col + 1] = gelu(d[1] + bias[col + 1]);
-    out[(gq + 8) * kS2 + col] = gelu(d[2] + bias[col]);
-    out[(gq + 8) * kS2 + col + 1] = gelu(d[3] + bias[col + 1]);
+    out[gq * kS2 + col] = gelu(d[nt][0] + bias[col]);
+    out[gq * kS2 + col + 1] = gelu(d[nt][1] + bias[col + 1]);
+    out[(gq + 8) * kS2 + col] = gelu(d[nt][2] + bias[col]);
+    out[(gq + 8) * kS2 + col + 1] = gelu(d[nt][3] + bias[col + 1]);
   }
 }
 

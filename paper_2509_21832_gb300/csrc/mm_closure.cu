@@ -55,17 +55,20 @@ __device__ __forceinline__ void cell_features(const double* __restrict__ Q,
                                               const double* __restrict__ prim, const KGrid& g,
                                               const KParams& p, double eps, double log10_eps,
                                               double dt, int c, float* x, double aux5[5]) {
+  // Differences of neighbouring FP64 fields are formed in FP64 (they cancel) and rounded once;
+  // the scalings that multiply them, and the features that are not differences, are FP32: every
+  // feature is within a few FP32 ulp of its FP64 value, which is all an FP32 network input can
+  // carry, and the FP64 pipe (1/64 of the FP32 rate) keeps only the subtractions and H_CE.
   const int nc = g.nx * g.ny;
   const int i = c % g.nx, j = c / g.nx;
   const double rho = prim[P_RHO * nc + c];
   const double u1 = prim[P_U1 * nc + c], u2 = prim[P_U2 * nc + c];
-  const double T = prim[P_T * nc + c], iT = prim[P_IT * nc + c];
+  const double T = prim[P_T * nc + c];
   const double tau = prim[P_TAU * nc + c];
-  const double ir = 1.0 / rho;
-  const double sT = sqrt(T);
-  const double isT = 1.0 / sT;
-  const double kn = eps * sT / (tau * fmin(g.dx, g.dy));
-  const double ks = kn * isT;
+  const float rhof = (float)rho, Tf = (float)T, tauf = (float)tau, epsf = (float)eps;
+  const float sTf = sqrtf(Tf);
+  const float kn = epsf * sTf / (tauf * (float)fmin(g.dx, g.dy));
+  const float sr = kn / rhof, su = kn / sTf, sT = kn / Tf;
   int f = 0;
   double TL = T, TR = T, TB = T, TT = T;
 #pragma unroll
@@ -78,28 +81,27 @@ __device__ __forceinline__ void cell_features(const double* __restrict__ Q,
       bool mx;
       const int ni = nb_index(i, di, g.nx, p.bc[0], p.bc[1], mx);
       const int n = nj * g.nx + ni;
-      double a1 = prim[P_U1 * nc + n], a2 = prim[P_U2 * nc + n];
+      const double a1 = prim[P_U1 * nc + n], a2 = prim[P_U2 * nc + n];
       const double Tn = prim[P_T * nc + n];
-      if (mx) a1 = -a1;
-      if (my) a2 = -a2;
-      x[f++] = (float)(kn * (prim[P_RHO * nc + n] * ir - 1.0));
-      x[f++] = (float)(ks * (a1 - u1));
-      x[f++] = (float)(ks * (a2 - u2));
-      x[f++] = (float)(kn * (Tn * iT - 1.0));
+      x[f++] = sr * (float)(prim[P_RHO * nc + n] - rho);
+      x[f++] = su * (float)(mx ? -a1 - u1 : a1 - u1);
+      x[f++] = su * (float)(my ? -a2 - u2 : a2 - u2);
+      x[f++] = sT * (float)(Tn - T);
       if (dj == 0) (di < 0 ? TL : TR) = Tn;
       if (di == 0) (dj < 0 ? TB : TT) = Tn;
     }
   }
   const double th11 = prim[P_TH11 * nc + c], th22 = prim[P_TH22 * nc + c];
   const double P12 = Q[4 * nc + c] - rho * u1 * u2;
-  x[32] = (float)((th11 - th22) * 0.5 * iT);
-  x[33] = (float)(P12 * ir * iT);
-  x[34] = (float)(u1 * isT);
-  x[35] = (float)(u2 * isT);
+  const float iTf = 1.f / Tf;
+  x[32] = (float)(th11 - th22) * (0.5f * iTf);
+  x[33] = (float)P12 * (iTf / rhof);
+  x[34] = (float)u1 / sTf;
+  x[35] = (float)u2 / sTf;
   x[36] = (float)log10_eps;
-  x[37] = (float)(eps / (eps + dt * tau));
-  x[38] = (float)log10(kn);
-  // Chapman-Enskog heat flux with the discrete temperature gradient of Eq. (5-97more)
+  x[37] = epsf / fmaf((float)dt, tauf, epsf);
+  x[38] = log10f(kn);
+  // Chapman-Enskog heat flux with the discrete temperature gradient of Eq. (5-97more), FP64
   const double Tx = (0.5 * (TR + T) - 0.5 * (T + TL)) * g.idx;
   const double Ty = (0.5 * (TT + T) - 0.5 * (T + TB)) * g.idy;
   const double ep = eps * rho * T / tau;
@@ -107,7 +109,7 @@ __device__ __forceinline__ void cell_features(const double* __restrict__ Q,
   aux5[1] = -ep * Ty;
   aux5[2] = -ep * Tx;
   aux5[3] = -3.0 * ep * Ty;
-  aux5[4] = eps * rho * T * sT;
+  aux5[4] = eps * rho * T * sqrt(T);
 }
 
 __global__ void k_closure_features(const double* __restrict__ Q, const double* __restrict__ prim,
@@ -129,7 +131,7 @@ __global__ void k_closure_features(const double* __restrict__ Q, const double* _
 // Features, network and decision of the hybrid step in one pass over the cells (persistent
 // CTAs, the network's weights staged once per CTA): the same arithmetic as k_closure_features,
 // k_mlp_infer and k_closure_decide in sequence, without the feature and output arrays.
-__global__ void __launch_bounds__(mlp_body::kInferThreads)
+__global__ void __launch_bounds__(mlp_body::kInferThreads, 4)
     k_closure_predict(const double* __restrict__ Q, const double* __restrict__ prim,
                       const __nv_bfloat16* __restrict__ w, const float* __restrict__ norm,
                       KGrid g, KParams p, double eps, double log10_eps, double dt, float thr,

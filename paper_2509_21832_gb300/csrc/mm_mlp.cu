@@ -25,7 +25,7 @@ using namespace mmk::mlp_body;
 namespace {
 
 // Inference, 32 samples per warp pass (two m16 tiles); weights staged once per CTA.
-__global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const __nv_bfloat16* __restrict__ w,
+__global__ void __launch_bounds__(kInferThreads, 4) k_mlp_infer(const __nv_bfloat16* __restrict__ w,
                                                              const float* __restrict__ norm,
                                                              const float* __restrict__ X,
                                                              float* __restrict__ Y, int n) {
