@@ -407,13 +407,353 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_fused_f32(FusedF3
   }
 }
 
-// The kernel instantiation for a velocity mesh: compile-time shapes for 32^2, 24^2 and 16^2.
-template <typename F>
-void with_fused_kernel(const KGrid& g, F&& f) {
-  if (g.nv1 == 32 && g.nv2 == 32) f(k_micro_fused_f32<32, 32>);
-  else if (g.nv1 == 24 && g.nv2 == 24) f(k_micro_fused_f32<24, 24>);
-  else if (g.nv1 == 16 && g.nv2 == 16) f(k_micro_fused_f32<16, 16>);
-  else f(k_micro_fused_f32<0, 0>);
+// ------------------------------------------------------------------------------------------
+// Flat-mapped variant for the compile-time meshes (nv a multiple of 32, v2 mesh symmetric about
+// zero).  The same march, ring and arithmetic, but lane L owns the flat velocity indices
+// q = L + 32 m, m < nv / 32, so every lane is busy whatever nv1 is: with nv1 = 24 a lane owns
+// P = 3 columns k_s = (L + 32 s) mod nv1 and, in each, every ST = 4th row from
+// l_s = (L + 32 s) div nv1.  Each phase-space access is a contiguous 128-byte warp row; the rows
+// with v2 < 0 (upwind from above) are exactly the first half, so the upwind source of every
+// element is fixed at compile time; a specular y wall is served by a mirrored copy of the cell's
+// G* in the ring slot the missing neighbour would use; a diffuse x wall reads a zero row.  The
+// upwind differences stay in registers between the two passes of each sweep.
+// ------------------------------------------------------------------------------------------
+__device__ float kZeroRowF[1024];  // zero upwind values behind a diffuse wall (nv <= 1024)
+
+constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+
+template <int NV1, int NV2>
+struct FlatShape {
+  static constexpr int NV = NV1 * NV2;
+  static constexpr int M = NV / 32;                 // elements per lane
+  static constexpr int P = NV1 / cgcd(NV1, 32);     // v1 columns per lane
+  static constexpr int ST = 32 / cgcd(NV1, 32);     // row stride within a column
+  static constexpr int TOP = NV2 / (2 * ST);        // visits t < TOP are rows with v2 < 0
+  static constexpr int PER_WARP = 3 * NV + 14 * NV2;  // ring + tables, floats
+  static_assert(NV % 32 == 0 && M % P == 0 && (M / P) * ST == NV2, "flat shape");
+  static_assert((NV2 / 2) % ST == 0 && NV <= 1024 && NV2 % 2 == 0, "flat shape");
+};
+
+// x sweep of cell (i, j) into the ring slot dst (flat mapping).
+template <int NV1, int NV2>
+__device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float* dst, float* xt) {
+  using S = FlatShape<NV1, NV2>;
+  const KGrid& g = a.g;
+  const int nc = g.nx * g.ny, cell = j * g.nx + i;
+  const int lane = threadIdx.x & 31;
+  float2* X1 = reinterpret_cast<float2*>(xt);  // (c2, c2^2)
+  float2* X2 = X1 + NV2;                        // (e2, projection term)
+  const float fv = load_fields(a.pf, nc, cell);
+  const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
+  const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT), kap = field(fv, F_KAP);
+  for (int l = lane; l < NV2; l += 32) {
+    const float c2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
+    const float q = c2 * c2;
+    X1[l] = make_float2(c2, q);
+    X2[l] = make_float2(expf(-q * inv2T), 0.f);
+  }
+  const UpwindF upl = upwind_side(g, a.p, i, j, 0), upr = upwind_side(g, a.p, i, j, 1);
+  float c1[S::P], sig[S::P], lam[S::P];
+  const float* Gu[S::P];
+  int l0[S::P];
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) {
+    const int q0 = lane + 32 * s, k = q0 % NV1;
+    l0[s] = q0 / NV1;
+    const float v1 = fmaf(k + 0.5f, a.gf.dv1, a.gf.v1min);
+    c1[s] = v1 - u1;
+    const float av = fabsf(v1);
+    sig[s] = -av * a.gf.idx;
+    lam[s] = av * a.dtidx;
+    const UpwindF up = v1 > 0.f ? upl : upr;
+    Gu[s] = up.zero ? kZeroRowF + q0
+                    : a.Gin + (size_t)up.cell * S::NV + q0 + (up.mirror ? NV1 - 1 - 2 * k : 0);
+  }
+  const float* Gc = a.Gin + (size_t)cell * S::NV + lane;
+  __syncwarp();
+  // pass 1: upwind differences, their moments and the upwind update (kept in registers)
+  float ue[S::M];
+  float D0[S::P], D1[S::P], D2[S::P];
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) D0[s] = D1[s] = D2[s] = 0.f;
+  {
+    float gv[S::M], gu[S::M];
+#pragma unroll
+    for (int m = 0; m < S::M; ++m) {
+      gv[m] = __ldg(Gc + 32 * m);
+      gu[m] = __ldg(Gu[m % S::P] + 32 * S::P * (m / S::P));
+    }
+#pragma unroll
+    for (int m = 0; m < S::M; ++m) {
+      const int s = m % S::P, t = m / S::P;
+      const float d = gu[m] - gv[m];
+      const float2 cq = X1[l0[s] + S::ST * t];
+      ue[m] = fmaf(lam[s], d, gv[m]);
+      D0[s] += d;
+      D1[s] = fmaf(cq.x, d, D1[s]);
+      D2[s] = fmaf(cq.y, d, D2[s]);
+    }
+  }
+  float Sx[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) {
+    const float sD0 = sig[s] * D0[s];
+    Sx[0] += sD0;
+    Sx[1] = fmaf(c1[s], sD0, Sx[1]);
+    Sx[2] = fmaf(sig[s], D1[s], Sx[2]);
+    Sx[3] += fmaf(c1[s] * c1[s], sD0, sig[s] * D2[s]);
+  }
+  warp_allsum4(Sx);
+  const float b0 = fmaf(-Sx[3], inv2T, 2.f * Sx[0]);
+  const float b1 = Sx[1] * iT, b2 = Sx[2] * iT;
+  const float gm = fmaf(0.25f * Sx[3], iT * iT, -Sx[0] * inv2T);
+  for (int l = lane; l < NV2; l += 32) {
+    const float2 cq = X1[l];
+    X2[l].y = X2[l].x * fmaf(b2, cq.x, gm * cq.y);
+  }
+  float ak[S::P], bk[S::P];
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) {
+    bk[s] = kap * expf(-c1[s] * c1[s] * inv2T);
+    ak[s] = bk[s] * fmaf(gm * c1[s], c1[s], fmaf(b1, c1[s], b0));
+  }
+  __syncwarp();
+  // pass 2: G* = G - dt Z + dt Zhat
+#pragma unroll
+  for (int m = 0; m < S::M; ++m) {
+    const int s = m % S::P, t = m / S::P;
+    const float2 eq = X2[l0[s] + S::ST * t];
+    float o = fmaf(ak[s], eq.x, ue[m]);
+    o = fmaf(bk[s], eq.y, o);
+    dst[lane + 32 * m] = o;
+  }
+  if (a.Gexp != nullptr && exports_gstar(g, a.p, i, j)) {
+    float* Ge = a.Gexp + (size_t)cell * S::NV + lane;
+#pragma unroll
+    for (int m = 0; m < S::M; ++m) Ge[32 * m] = dst[lane + 32 * m];
+  }
+  __syncwarp();
+}
+
+// y sweep + relaxation + heat flux of cell (i, j) from the ring rows below (rb), at (rc) and
+// above (rt) the cell (flat mapping).
+template <int NV1, int NV2>
+__device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const float* rb,
+                                         const float* rc, const float* rt, float* tb) {
+  using S = FlatShape<NV1, NV2>;
+  const KGrid& g = a.g;
+  const int nc = g.nx * g.ny, cell = j * g.nx + i;
+  const int lane = threadIdx.x & 31;
+  // row tables: TS = (s0, s0 c2, s0 c2^2) for the moments of Z*; TA = (wl, e2, c2, g2) and
+  // TC = (c2^2, c2^3) for the update and the heat flux
+  float4* TS = reinterpret_cast<float4*>(tb);
+  float4* TA = TS + NV2;
+  float2* TC = reinterpret_cast<float2*>(TA + NV2);
+  const float fv = load_fields(a.pf, nc, cell);
+  const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
+  const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT);
+  const float Ti11h = field(fv, F_TI11H), Ti12 = field(fv, F_TI12), Ti22h = field(fv, F_TI22H);
+  const float om1 = field(fv, F_OM1), om1kap = field(fv, F_OM1KAP);
+  const float gam0 = field(fv, F_GAM0), ome = field(fv, F_OME);
+  const float w01 = field(fv, F_W01), w02 = field(fv, F_W02), w03 = field(fv, F_W03);
+  const float w10 = field(fv, F_W10), w11 = field(fv, F_W11), w12 = field(fv, F_W12);
+  const float w20 = field(fv, F_W20), w21 = field(fv, F_W21), w30 = field(fv, F_W30);
+  for (int l = lane; l < NV2; l += 32) {
+    const float v2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min);
+    const float c2 = v2 - u2;
+    const float q = c2 * c2;
+    const float av = fabsf(v2);
+    const float sg = -av * a.gf.idy;
+    TS[l] = make_float4(sg, sg * c2, sg * q, 0.f);
+    TA[l] = make_float4(om1 * (av * a.dtidy), expf(-q * inv2T), c2, expf(-Ti22h * q));
+    TC[l] = make_float2(q, q * c2);
+  }
+  float c1[S::P], c1q[S::P];
+  int l0[S::P];
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) {
+    const int q0 = lane + 32 * s, k = q0 % NV1;
+    l0[s] = q0 / NV1;
+    c1[s] = fmaf(k + 0.5f, a.gf.dv1, a.gf.v1min) - u1;
+    c1q[s] = c1[s] * c1[s];
+  }
+  __syncwarp();
+  // pass 1: upwind differences and the moments of Z*; G* and the differences stay in registers
+  float gvr[S::M], dr[S::M];
+  float E0[S::P], E1[S::P], E2[S::P];
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) E0[s] = E1[s] = E2[s] = 0.f;
+#pragma unroll
+  for (int m = 0; m < S::M; ++m) {
+    const int s = m % S::P, t = m / S::P;
+    const float gv = rc[lane + 32 * m];
+    const float gu = (t < S::TOP ? rt : rb)[lane + 32 * m];
+    const float d = gu - gv;
+    gvr[m] = gv;
+    dr[m] = d;
+    const float4 ts = TS[l0[s] + S::ST * t];
+    E0[s] = fmaf(ts.x, d, E0[s]);
+    E1[s] = fmaf(ts.y, d, E1[s]);
+    E2[s] = fmaf(ts.z, d, E2[s]);
+  }
+  float Sy[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) {
+    Sy[0] += E0[s];
+    Sy[1] = fmaf(c1[s], E0[s], Sy[1]);
+    Sy[2] += E1[s];
+    Sy[3] += fmaf(c1q[s], E0[s], E2[s]);
+  }
+  warp_allsum4(Sy);
+  const float b0 = fmaf(-Sy[3], inv2T, 2.f * Sy[0]);
+  const float b1 = Sy[1] * iT, b2 = Sy[2] * iT;
+  const float gm = fmaf(0.25f * Sy[3], iT * iT, -Sy[0] * inv2T);
+  // per column: the polynomial coefficients of Ghat in c2 (times e1) and the ES Gaussian's
+  // cross factor with its row ratio
+  float A0[S::P], A1[S::P], A2[S::P], A3[S::P], x[S::P], rat[S::P];
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) {
+    const float c = c1[s], cq = c1q[s];
+    const float C0 = om1kap * fmaf(gm, cq, fmaf(b1, c, b0)) - c * fmaf(c, fmaf(c, w03, w02), w01) - ome;
+    const float C1 = fmaf(om1kap, b2, -fmaf(c, fmaf(c, w12, w11), w10));
+    const float C2 = fmaf(om1kap, gm, -fmaf(c, w21, w20));
+    const float e1 = expf(-cq * inv2T);
+    A0[s] = e1 * C0;
+    A1[s] = e1 * C1;
+    A2[s] = e1 * C2;
+    A3[s] = -e1 * w30;
+    const float c2r = fmaf(l0[s] + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
+    x[s] = gam0 * expf(-Ti11h * cq - Ti12 * c * c2r);
+    rat[s] = expf(-Ti12 * c * (S::ST * a.gf.dv2));
+  }
+  // pass 2: G^{n+1} = om1 G* + wl (G*_up - G*) + Ghat + gamma exp(...), and the heat flux sums
+  float H0[S::P], H1[S::P], H2[S::P], H3[S::P];
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) H0[s] = H1[s] = H2[s] = H3[s] = 0.f;
+  float* Go = a.Gout + (size_t)cell * S::NV + lane;
+#pragma unroll
+  for (int m = 0; m < S::M; ++m) {
+    const int s = m % S::P, t = m / S::P;
+    const int l = l0[s] + S::ST * t;
+    const float4 ta = TA[l];
+    const float2 tc = TC[l];
+    float o = fmaf(ta.x, dr[m], om1 * gvr[m]);
+    const float pc = fmaf(fmaf(fmaf(A3[s], ta.z, A2[s]), ta.z, A1[s]), ta.z, A0[s]);
+    o = fmaf(ta.y, pc, o);
+    o = fmaf(ta.w, x[s], o);
+    x[s] *= rat[s];
+    Go[32 * m] = o;
+    H0[s] += o;
+    H1[s] = fmaf(ta.z, o, H1[s]);
+    H2[s] = fmaf(tc.x, o, H2[s]);
+    H3[s] = fmaf(tc.y, o, H3[s]);
+  }
+  float Hs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) {
+    Hs[0] = fmaf(c1q[s] * c1[s], H0[s], Hs[0]);
+    Hs[1] = fmaf(c1q[s], H1[s], Hs[1]);
+    Hs[2] = fmaf(c1[s], H2[s], Hs[2]);
+    Hs[3] += H3[s];
+  }
+  warp_allsum4(Hs);
+  if (lane < 8) a.Hf[lane * nc + cell] = (lane & 1) ? 0.f : Hs[lane >> 1];
+  __syncwarp();
+}
+
+// dst[(k, l)] = src[(k, nv2 - 1 - l)]: the specular image of a cell's G* rows.
+template <int NV1, int NV2>
+__device__ __forceinline__ void mirror_rows(const float* src, float* dst) {
+  using S = FlatShape<NV1, NV2>;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < S::M; ++m) {
+    const int q = lane + 32 * m, l = q / NV1, k = q % NV1;
+    dst[q] = src[(NV2 - 1 - l) * NV1 + k];
+  }
+  __syncwarp();
+}
+
+template <int NV1, int NV2>
+__global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_flat_f32(FusedF32 a) {
+  using S = FlatShape<NV1, NV2>;
+  extern __shared__ __align__(16) float smf[];
+  const KGrid& g = a.g;
+  const int w = threadIdx.x >> 5;
+  float* ring = smf + (size_t)w * S::PER_WARP;
+  float* xt = ring + 3 * S::NV;
+  float* yt = xt + 4 * NV2;
+  const int gw = blockIdx.x * kFusedWarps + w;
+  if (gw >= g.nx * a.nseg) return;  // whole warp leaves; no CTA-wide barrier is used below
+  const int i = gw % g.nx;
+  const int seg = gw / g.nx;
+  const int j0 = seg * a.seg_rows;
+  const int j1 = min(g.ny, j0 + a.seg_rows);
+  if (j0 >= j1) return;
+  const bool pery = a.p.bc[2] == MM_BC_PERIODIC;
+  auto slot = [&](int pos) { return ring + (size_t)(pos % 3) * S::NV; };
+  if (j0 > 0 || pery) fx_sweep<NV1, NV2>(a, i, j0 > 0 ? j0 - 1 : g.ny - 1, slot(0), xt);
+  fx_sweep<NV1, NV2>(a, i, j0, slot(1), xt);
+  for (int j = j0; j < j1; ++j) {
+    const int pos = j - j0 + 1;
+    if (j + 1 < g.ny || pery) fx_sweep<NV1, NV2>(a, i, j + 1 < g.ny ? j + 1 : 0, slot(pos + 1), xt);
+    if (diffuse_wall_cell(g, a.p, i, j)) continue;  // finished by the wall kernel
+    const float* rc = slot(pos);
+    const bool hasb = j > 0 || pery, hast = j < g.ny - 1 || pery;
+    // a missing neighbour's slot is free: it takes the specular image of the cell's rows
+    const float* rb = rc;
+    if (hasb) rb = slot(pos + 2);
+    else if (a.p.bc[2] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 2)); rb = slot(pos + 2); }
+    const float* rt = rc;
+    if (hast) rt = slot(pos + 1);
+    else if (a.p.bc[3] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 1)); rt = slot(pos + 1); }
+    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt);
+  }
+}
+
+// The kernel for a velocity mesh and its shared memory per CTA.  Flat-mapped kernels for the
+// 32^2, 24^2 and 16^2 meshes when the v2 mesh is symmetric (the rows with v2 < 0, evaluated in
+// FP32 as on the device, are exactly the first half); otherwise the column-mapped kernel
+// (compile-time shape where it has one).
+struct FusedPick {
+  void (*kern)(FusedF32);
+  size_t smem;
+};
+
+static bool v2_symmetric_f32(const KGrid& g) {
+  const float dv2 = (float)g.dv2, v2min = (float)g.v2min;  // as rounded for the FP32 kernels
+  if (g.nv2 % 2) return false;
+  int nneg = 0;
+  for (int l = 0; l < g.nv2; ++l) nneg += std::fmaf(l + 0.5f, dv2, v2min) < 0.f ? 1 : 0;
+  return nneg == g.nv2 / 2;
+}
+
+// Shared memory per CTA of the column-mapped kernel: per warp a three-row ring of G* (rounded up
+// to 16 bytes), the x-sweep tables (2 float2 per row) and the y-sweep tables (3 float4 + 1 float2
+// per row), the whole padded to a multiple of 16 bytes so that every warp's float4 tables stay
+// aligned.
+static size_t column_smem(const KGrid& g) {
+  const size_t nv = (size_t)g.nv1 * g.nv2;
+  const size_t per_warp = (3 * nv + 3) / 4 * 4 + 18 * (size_t)g.nv2 + (g.nv2 & 1) * 2;
+  return sizeof(float) * kFusedWarps * per_warp;
+}
+
+template <int NV1, int NV2>
+static FusedPick flat_pick() {
+  return FusedPick{k_micro_flat_f32<NV1, NV2>,
+                   sizeof(float) * kFusedWarps * (size_t)FlatShape<NV1, NV2>::PER_WARP};
+}
+
+static FusedPick pick_fused(const KGrid& g) {
+  const bool sym = v2_symmetric_f32(g);
+  if (sym && g.nv1 == 32 && g.nv2 == 32) return flat_pick<32, 32>();
+  if (sym && g.nv1 == 24 && g.nv2 == 24) return flat_pick<24, 24>();
+  if (sym && g.nv1 == 16 && g.nv2 == 16) return flat_pick<16, 16>();
+  const size_t smem = column_smem(g);
+  if (g.nv1 == 32 && g.nv2 == 32) return FusedPick{k_micro_fused_f32<32, 32>, smem};
+  if (g.nv1 == 24 && g.nv2 == 24) return FusedPick{k_micro_fused_f32<24, 24>, smem};
+  if (g.nv1 == 16 && g.nv2 == 16) return FusedPick{k_micro_fused_f32<16, 16>, smem};
+  return FusedPick{k_micro_fused_f32<0, 0>, smem};
 }
 
 }  // namespace
@@ -423,24 +763,13 @@ KGridF grid_f32(const KGrid& g) {
                 (float)g.idy};
 }
 
-// Shared memory per CTA: per warp a three-row ring of G* (rounded up to 16 bytes), the x-sweep
-// tables (2 float2 per row) and the y-sweep tables (3 float4 + 1 float2 per row), the whole
-// padded to a multiple of 16 bytes so that every warp's float4 tables stay aligned.
-static size_t fused_smem(const KGrid& g) {
-  const size_t nv = (size_t)g.nv1 * g.nv2;
-  const size_t per_warp = (3 * nv + 3) / 4 * 4 + 18 * (size_t)g.nv2 + (g.nv2 & 1) * 2;
-  return sizeof(float) * kFusedWarps * per_warp;
-}
-
 int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
   (void)ms;
-  const size_t smem = fused_smem(g);
+  const FusedPick f = pick_fused(g);
   int per_sm = 0;
-  with_fused_kernel(g, [&](auto kern) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kFusedWarps, smem);
-  });
+  if (f.smem > 48 * 1024)
+    cudaFuncSetAttribute(f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f.kern, 32 * kFusedWarps, f.smem);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -457,7 +786,7 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
                             const float* primf, const KGrid& g, const KParams& p, double dt,
                             const MicroShape& ms, int nseg, cudaStream_t s) {
   (void)ms;
-  const size_t smem = fused_smem(g);
+  const FusedPick f = pick_fused(g);
   FusedF32 a;
   a.Gin = Gin;
   a.Gout = Gout;
@@ -473,11 +802,9 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
   a.nseg = nseg;
   a.seg_rows = (g.ny + nseg - 1) / nseg;
   const int warps = g.nx * nseg;
-  with_fused_kernel(g, [&](auto kern) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, smem, s>>>(a);
-  });
+  if (f.smem > 48 * 1024)
+    cudaFuncSetAttribute(f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
+  f.kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, f.smem, s>>>(a);
 }
 
 }  // namespace mmk

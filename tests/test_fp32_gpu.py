@@ -29,6 +29,13 @@ CASES = [
      (I.EXTRAP, I.EXTRAP, I.DIFFUSE, I.EXTRAP), dict(wall_T=(1.0, 1.0, 1.1, 1.0))),
     ("odd_17x15", dict(nx=6, ny=5, nv1=17, nv2=15, v1min=-6, v1max=6, v2min=-6, v2max=6),
      (I.PERIODIC, I.PERIODIC, I.SPECULAR, I.EXTRAP), dict(nu=0.3)),
+    # three v1 columns per lane: mirrored x upwind at the specular side, a zero row behind the
+    # diffuse side, specular images of the bottom row
+    ("walls_24", dict(nx=9, ny=8, nv1=24, nv2=24),
+     (I.DIFFUSE, I.SPECULAR, I.SPECULAR, I.EXTRAP), dict(wall_T=(1.2, 1.0, 1.0, 1.0))),
+    # v2 mesh not symmetric about zero: the column-mapped kernel of the 24^2 shape
+    ("asym_24", dict(nx=8, ny=9, nv1=24, nv2=24, v2min=-7.0, v2max=9.0),
+     (I.EXTRAP, I.EXTRAP, I.PERIODIC, I.PERIODIC), {}),
 ]
 
 
