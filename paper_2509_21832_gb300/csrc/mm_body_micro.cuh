@@ -386,10 +386,10 @@ struct SideM {
 };
 
 
-// Shared memory of the wall body: reduction scratch, the x and y factors of five Maxwellians and
-// their prefactors.
+// Shared memory of the wall body: reduction scratch, the x and y factors of five Maxwellians,
+// their prefactors and the row factor of the ES Gaussian.
 __host__ __device__ constexpr size_t wall_smem_doubles(int nv1, int nv2) {
-  return kRed + 5 * ((size_t)nv1 + (size_t)nv2) + 8;
+  return kRed + 5 * ((size_t)nv1 + (size_t)nv2) + 8 + (size_t)nv2;
 }
 
 // Eq. (twodim_wall_densities_1)
@@ -490,10 +490,20 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
     par(t, a1, a2, aT, ar);
     pfq[t] = ar / (2.0 * kPi * aT);
   }
+  // ES Gaussian exp(-c.Tcal^{-1}c/2) = exp(-Ti11 c1^2/2) exp(-Ti22 c2^2/2) exp(-Ti12 c1 c2): the
+  // row factor tabulated, the column factor per thread, the cross factor by a recurrence
+  double* Et = pfq + 8;  // [nv2]
+  if (p.keep_es)
+    for (int l = t; l < nv2; l += blockDim.x) {
+      const double c2 = g.v2min + (l + 0.5) * g.dv2 - u2;
+      Et[l] = exp(-0.5 * Ti22 * c2 * c2);
+    }
   __syncthreads();
 
-  // upwind v . grad M at (k, l) with the ghost Maxwellians of each side
+  // upwind v . grad M at (k, l) with the ghost Maxwellians of each side (reciprocals of dx, dy,
+  // tau and of the cell's Maxwellian prefactor hoisted out of the velocity loops)
   const int km = nv1 - 1 - k;
+  const double idx = g.idx, idy = g.idy;
   auto side_m = [&](int s, double m0, int l) -> double {
     const SideM& q = sd[s];
     if (q.kind == 1) return m0;
@@ -502,17 +512,16 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
                    : pfq[4] * Xt[4 * nv1 + k] * Yt[4 * nv2 + (nv2 - 1 - l)];
     return pfq[s] * Xt[s * nv1 + k] * Yt[s * nv2 + l];
   };
-  auto mup = [&](int l, double m0) -> double {
-    const double v2 = g.v2min + (l + 0.5) * g.dv2;
+  auto mup = [&](int l, double v2, double m0) -> double {
     double z = 0.0;
-    if (v1 > 0.0) z += v1 * ((m0 - side_m(0, m0, l)) / g.dx);
-    if (v1 < 0.0) z += v1 * ((side_m(1, m0, l) - m0) / g.dx);
-    if (v2 > 0.0) z += v2 * ((m0 - side_m(2, m0, l)) / g.dy);
-    if (v2 < 0.0) z += v2 * ((side_m(3, m0, l) - m0) / g.dy);
+    if (v1 > 0.0) z += v1 * ((m0 - side_m(0, m0, l)) * idx);
+    if (v1 < 0.0) z += v1 * ((side_m(1, m0, l) - m0) * idx);
+    if (v2 > 0.0) z += v2 * ((m0 - side_m(2, m0, l)) * idy);
+    if (v2 < 0.0) z += v2 * ((side_m(3, m0, l) - m0) * idy);
     return z;
   };
-  const double x4 = pfq[4] * Xt[4 * nv1 + k];
-  auto mcell = [&](int l) -> double { return x4 * Yt[4 * nv2 + l]; };
+  const double xk = Xt[4 * nv1 + k];  // the cell's Maxwellian / (rho / (2 pi T)) = xk * Yt[l]
+  const double x4 = pfq[4] * xk;
 
   // pass 1: moments of Z* and of the upwind v.grad M
   double E0 = 0, E1 = 0, E2 = 0, W0 = 0, W1 = 0, W2 = 0;
@@ -526,11 +535,11 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
       const Tg* Gu = top ? Gt : Gb;
       const int lu = u.mirror ? nv2 - 1 - l : l;
       const double gu = u.zero ? 0.0 : (double)Gu[lu * nv1];
-      const double z = -fabs(v2) / g.dy * (gu - gv);
+      const double z = -fabs(v2) * idy * (gu - gv);
       E0 += z;
       E1 += c2 * z;
       E2 += c2 * c2 * z;
-      const double mz = mup(l, mcell(l));
+      const double mz = mup(l, v2, x4 * Yt[4 * nv2 + l]);
       W0 += mz;
       W1 += c2 * mz;
       W2 += c2 * c2 * mz;
@@ -542,12 +551,25 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
   block_sum4(Wm, red);
 
   const double kap = g.dv1 * g.dv2 / (2.0 * kPi * T);
-  auto poly = [&](const double* s, double c2) -> double {
-    const double b0 = 2.0 * s[0] - s[3] * inv2T;
-    const double b1 = s[1] * iT, b2 = s[2] * iT;
-    const double gm = 0.25 * s[3] * iT * iT - s[0] * inv2T;
-    return b0 + b1 * c1 + b2 * c2 + gm * (c1 * c1 + c2 * c2);
+  // the projection polynomials b0 + b1 c1 + b2 c2 + gm |c|^2 of Z* (S) and of v.grad M (Wm),
+  // times kap, as a0 + c2 (a1 + a2 c2) for this thread's c1
+  auto coeffs = [&](const double* sm4, double& a0, double& a1, double& a2) {
+    const double b0 = 2.0 * sm4[0] - sm4[3] * inv2T;
+    const double b1 = sm4[1] * iT, b2 = sm4[2] * iT;
+    const double gm = 0.25 * sm4[3] * iT * iT - sm4[0] * inv2T;
+    a0 = kap * (b0 + b1 * c1 + gm * c1 * c1);
+    a1 = kap * b2;
+    a2 = kap * gm;
   };
+  double sa0, sa1, sa2, wa0, wa1, wa2;
+  coeffs(S, sa0, sa1, sa2);
+  coeffs(Wm, wa0, wa1, wa2);
+  const double itau = 1.0 / tau;
+  const double ieps = 1.0 / eps;
+  // ES Gaussian at this thread's first row and the ratio of its cross factor between rows
+  const double c2r = g.v2min + (r + 0.5) * g.dv2 - u2;
+  double ex = p.keep_es ? KG * exp(-0.5 * Ti11 * c1 * c1 - Ti12 * c1 * c2r) : 0.0;
+  const double rat = p.keep_es ? exp(-Ti12 * c1 * (R * g.dv2)) : 0.0;
 
   double H0 = 0, H1 = 0, H2 = 0, H3 = 0;
   if (active) {
@@ -561,15 +583,16 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
       const Tg* Gu = top ? Gt : Gb;
       const int lu = u.mirror ? nv2 - 1 - l : l;
       const double gu = u.zero ? 0.0 : (double)Gu[lu * nv1];
-      const double z = -fabs(v2) / g.dy * (gu - gv);
-      const double m = mcell(l);
-      const double gstar2 = gv + dt * (kap * poly(S, c2) * (m / (rho / (2.0 * kPi * T))) - z);
-      const double mz = mup(l, m);
-      const double pim = kap * poly(Wm, c2) * (m / (rho / (2.0 * kPi * T)));
-      double gh = -(1.0 / tau) * (mz - pim);
+      const double z = -fabs(v2) * idy * (gu - gv);
+      const double ml = xk * Yt[4 * nv2 + l];  // M / (rho / (2 pi T))
+      const double m = pfq[4] * ml;
+      const double gstar2 = gv + dt * ((sa0 + c2 * (sa1 + sa2 * c2)) * ml - z);
+      const double mz = mup(l, v2, m);
+      const double pim = (wa0 + c2 * (wa1 + wa2 * c2)) * ml;
+      double gh = -itau * (mz - pim);
       if (p.keep_es) {
-        const double quad = Ti11 * c1 * c1 + 2.0 * Ti12 * c1 * c2 + Ti22 * c2 * c2;
-        gh += (KG * exp(-0.5 * quad) - m) / eps;
+        gh += (ex * Et[l] - m) * ieps;
+        ex *= rat;
       }
       const double o = om1 * gstar2 + om2 * gh;
       const Tg os = (Tg)o;
