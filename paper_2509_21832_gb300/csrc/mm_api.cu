@@ -183,6 +183,8 @@ mm_status check_device_errors(mm_ctx* c) {
   cudaError_t e = cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "device error check");
+  if (h & ERR_WAIT_TIMEOUT)
+    return fail(c, MM_ERR_TIMEOUT, "a bounded device wait ran out (bulk copy into shared memory)");
   if (h) {
     char buf[160];
     std::snprintf(buf, sizeof buf,
@@ -223,7 +225,7 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
     // fused streaming kernel: G -> Gs (ping-pong), wall cells from the exported G*
     float* Ge = static_cast<float*>(c->Gexp);
     timed(c, T_MICRO_FUSED, [&] {
-      launch_micro_fused_f32(G, Gs, Ge, c->Hf, c->primf, g, p, dt, c->ms, c->nseg, s);
+      launch_micro_fused_f32(G, Gs, Ge, c->Hf, c->primf, g, p, dt, c->ms, c->nseg, c->err, s);
     });
     timed(c, T_HUNPACK, [&] { launch_h_unpack(c->Hf, c->H, g, eps, s); });
     if (c->n_wall > 0)

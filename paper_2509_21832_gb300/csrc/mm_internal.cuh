@@ -59,7 +59,7 @@ enum PrimFieldF {
 };
 
 // Bits of the device error word.
-enum { ERR_NONPHYS_PRIM = 1, ERR_NONPHYS_MACRO = 2, ERR_NONFINITE_G = 4 };
+enum { ERR_NONPHYS_PRIM = 1, ERR_NONPHYS_MACRO = 2, ERR_NONFINITE_G = 4, ERR_WAIT_TIMEOUT = 8 };
 
 // Launch shape of the micro kernels: R rows of v2 per pass, threads = R * nv1 rounded up to 32.
 struct MicroShape {
@@ -94,7 +94,7 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
 int fused_segments_f32(const KGrid& g, const MicroShape& ms);
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
-                            const MicroShape& ms, int nseg, cudaStream_t s);
+                            const MicroShape& ms, int nseg, int* err, cudaStream_t s);
 // Buffers of the macro step: Q* and Q**, each cell's half fluxes along x (of Q*) and y (of Q**)
 // [Fp(6) Fm(6)][ny][nx], and the fluxes through the non-periodic boundary faces
 // BX [2 sides][6][ny], BY [2 sides][6][nx].

@@ -9,6 +9,7 @@
 // rows, then a pairwise warp butterfly); the heat flux leaves as (hi, lo) FP32 pairs (lo = 0
 // here) that the per-cell unpack kernel turns into FP64.
 #include <cmath>
+#include <cstdint>
 
 #include "mm_internal.cuh"
 
@@ -78,6 +79,7 @@ struct FusedF32 {
   int R;         // rows per pass: 32 / nv1
   int seg_rows;  // rows per segment
   int nseg;
+  int* err;      // device error word (ERR_WAIT_TIMEOUT from a bounded wait)
 };
 
 constexpr int kFusedWarps = 4;  // warps (columns) per CTA
@@ -418,7 +420,12 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_fused_f32(FusedF3
 // G* in the ring slot the missing neighbour would use; a diffuse x wall reads a zero row.  The
 // upwind differences stay in registers between the two passes of each sweep.
 // ------------------------------------------------------------------------------------------
-__device__ float kZeroRowF[1024];  // zero upwind values behind a diffuse wall (nv <= 1024)
+__device__ __align__(16) float kZeroRowF[1024];
+
+// Bulk prefetch of bytes (a multiple of 16) at a 16-byte aligned global address into L2.
+__device__ __forceinline__ void l2_prefetch_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}  // zero upwind values behind a diffuse wall (nv <= 1024)
 
 constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 
@@ -434,9 +441,14 @@ struct FlatShape {
   static_assert((NV2 / 2) % ST == 0 && NV <= 1024 && NV2 % 2 == 0, "flat shape");
 };
 
-// x sweep of cell (i, j) into the ring slot dst (flat mapping).
-template <int NV1, int NV2>
-__device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float* dst, float* xt) {
+// x sweep of cell (i, j) into the ring slot dst (flat mapping).  Gc is the cell's g block, Gl and
+// Gr the blocks upwind on the left and right (the cell's own block for extrapolation and specular
+// sides, mirrored in v1 when mirl / mirr, a zero row behind a diffuse side): global memory read
+// through the read-only path, or the shared-memory stage (STAGED).
+template <int NV1, int NV2, bool STAGED>
+__device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float* dst, float* xt,
+                                         const float* Gcb, const float* Gl, const float* Gr,
+                                         bool mirl, bool mirr) {
   using S = FlatShape<NV1, NV2>;
   const KGrid& g = a.g;
   const int nc = g.nx * g.ny, cell = j * g.nx + i;
@@ -452,7 +464,6 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
     X1[l] = make_float2(c2, q);
     X2[l] = make_float2(expf(-q * inv2T), 0.f);
   }
-  const UpwindF upl = upwind_side(g, a.p, i, j, 0), upr = upwind_side(g, a.p, i, j, 1);
   float c1[S::P], sig[S::P], lam[S::P];
   const float* Gu[S::P];
   int l0[S::P];
@@ -465,11 +476,11 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
     const float av = fabsf(v1);
     sig[s] = -av * a.gf.idx;
     lam[s] = av * a.dtidx;
-    const UpwindF up = v1 > 0.f ? upl : upr;
-    Gu[s] = up.zero ? kZeroRowF + q0
-                    : a.Gin + (size_t)up.cell * S::NV + q0 + (up.mirror ? NV1 - 1 - 2 * k : 0);
+    const bool left = v1 > 0.f;
+    Gu[s] = (left ? Gl : Gr) + q0 + ((left ? mirl : mirr) ? NV1 - 1 - 2 * k : 0);
   }
-  const float* Gc = a.Gin + (size_t)cell * S::NV + lane;
+  const float* Gc = Gcb + lane;
+  auto ld = [](const float* q) { return STAGED ? *q : __ldg(q); };
   __syncwarp();
   // pass 1: upwind differences, their moments and the upwind update (kept in registers)
   float ue[S::M];
@@ -480,8 +491,8 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
     float gv[S::M], gu[S::M];
 #pragma unroll
     for (int m = 0; m < S::M; ++m) {
-      gv[m] = __ldg(Gc + 32 * m);
-      gu[m] = __ldg(Gu[m % S::P] + 32 * S::P * (m / S::P));
+      gv[m] = ld(Gc + 32 * m);
+      gu[m] = ld(Gu[m % S::P] + 32 * S::P * (m / S::P));
     }
 #pragma unroll
     for (int m = 0; m < S::M; ++m) {
@@ -692,15 +703,187 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_flat_f32(FusedF32
   if (j0 >= j1) return;
   const bool pery = a.p.bc[2] == MM_BC_PERIODIC;
   auto slot = [&](int pos) { return ring + (size_t)(pos % 3) * S::NV; };
-  if (j0 > 0 || pery) fx_sweep<NV1, NV2>(a, i, j0 > 0 ? j0 - 1 : g.ny - 1, slot(0), xt);
-  fx_sweep<NV1, NV2>(a, i, j0, slot(1), xt);
+  // the g block of the cell two rows ahead goes to L2 while this row is swept, so that the x
+  // sweep's loads of the next-but-one iteration wait on L2 rather than on HBM
+  auto prefetch = [&](int jj) {
+    if ((threadIdx.x & 31) == 0 && jj < g.ny)
+      l2_prefetch_bulk(a.Gin + (size_t)(jj * g.nx + i) * S::NV, (unsigned)(S::NV * sizeof(float)));
+  };
+  auto xsweep = [&](int jj, float* dst) {
+    const UpwindF ul = upwind_side(g, a.p, i, jj, 0), ur = upwind_side(g, a.p, i, jj, 1);
+    const float* Gl = ul.zero ? kZeroRowF : a.Gin + (size_t)ul.cell * S::NV;
+    const float* Gr = ur.zero ? kZeroRowF : a.Gin + (size_t)ur.cell * S::NV;
+    fx_sweep<NV1, NV2, false>(a, i, jj, dst, xt, a.Gin + (size_t)(jj * g.nx + i) * S::NV, Gl, Gr,
+                              ul.mirror, ur.mirror);
+  };
+  prefetch(j0 + 1);
+  if (j0 > 0 || pery) xsweep(j0 > 0 ? j0 - 1 : g.ny - 1, slot(0));
+  xsweep(j0, slot(1));
   for (int j = j0; j < j1; ++j) {
     const int pos = j - j0 + 1;
-    if (j + 1 < g.ny || pery) fx_sweep<NV1, NV2>(a, i, j + 1 < g.ny ? j + 1 : 0, slot(pos + 1), xt);
+    prefetch(j + 2);
+    if (j + 1 < g.ny || pery) xsweep(j + 1 < g.ny ? j + 1 : 0, slot(pos + 1));
     if (diffuse_wall_cell(g, a.p, i, j)) continue;  // finished by the wall kernel
     const float* rc = slot(pos);
     const bool hasb = j > 0 || pery, hast = j < g.ny - 1 || pery;
     // a missing neighbour's slot is free: it takes the specular image of the cell's rows
+    const float* rb = rc;
+    if (hasb) rb = slot(pos + 2);
+    else if (a.p.bc[2] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 2)); rb = slot(pos + 2); }
+    const float* rt = rc;
+    if (hast) rt = slot(pos + 1);
+    else if (a.p.bc[3] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 1)); rt = slot(pos + 1); }
+    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Staged variant: the warps of a CTA sweep W adjacent columns in step, and the g blocks that the
+// x sweeps of the next-but-one row read (the W cells and one halo cell on each side) arrive in a
+// shared-memory stage by bulk asynchronous copies while the current row is swept in y.  One
+// thread issues the copies and an mbarrier counts their bytes; every wait on it is bounded and a
+// wait that runs out sets ERR_WAIT_TIMEOUT and ends the CTA.
+// ------------------------------------------------------------------------------------------
+constexpr int kWaitSpins = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kWaitSpins; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <int NV1, int NV2>
+struct StagedShape {
+  using S = FlatShape<NV1, NV2>;
+  static constexpr int W = kFusedWarps;
+  static constexpr int STAGE = (W + 2) * S::NV;  // floats: the g blocks of columns i0-1 .. i0+W
+  static constexpr int RING = 3 * S::NV;          // per warp
+  static constexpr int TABLES = 14 * NV2;         // per warp
+  static constexpr int FLOATS = STAGE + W * (RING + TABLES) + 4;  // + the mbarrier (8 bytes)
+};
+
+// Source of stage slot sigma (column c = i0 - 1 + sigma) for row jj: the column's block; beyond
+// a side the block the x sweep treats as upwind there (periodic partner, the edge cell itself for
+// extrapolation and specular sides, the zero row for a diffuse side); NULL past the right halo.
+__device__ __forceinline__ const float* stage_source(const FusedF32& a, int c, int jj, int nv) {
+  const KGrid& g = a.g;
+  if (c < -1 || c > g.nx) return nullptr;
+  if (c == -1 || c == g.nx) {
+    const int side = c < 0 ? 0 : 1;
+    const int bc = a.p.bc[side];
+    if (bc == MM_BC_DIFFUSE) return kZeroRowF;
+    if (bc == MM_BC_PERIODIC) c = side == 0 ? g.nx - 1 : 0;
+    else c = side == 0 ? 0 : g.nx - 1;
+  }
+  return a.Gin + (size_t)(jj * g.nx + c) * nv;
+}
+
+template <int NV1, int NV2>
+__global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF32 a) {
+  using S = FlatShape<NV1, NV2>;
+  using T = StagedShape<NV1, NV2>;
+  constexpr int W = T::W;
+  extern __shared__ __align__(16) float smf[];
+  const KGrid& g = a.g;
+  const int w = threadIdx.x >> 5;
+  float* stage = smf;
+  float* ring = smf + T::STAGE + w * (T::RING + T::TABLES);
+  float* xt = ring + T::RING;
+  float* yt = xt + 4 * NV2;
+  const uint32_t bar = smem_addr(smf + T::STAGE + W * (T::RING + T::TABLES));
+  const int ncx = (g.nx + W - 1) / W;
+  const int cx = blockIdx.x % ncx, seg = blockIdx.x / ncx;
+  const int i0 = cx * W, i = i0 + w;
+  const bool col = i < g.nx;  // warps past the last column only take part in the barriers
+  const int j0 = seg * a.seg_rows;
+  const int j1 = min(g.ny, j0 + a.seg_rows);
+  if (j0 >= j1) return;  // uniform over the CTA
+  const bool pery = a.p.bc[2] == MM_BC_PERIODIC;
+  const bool mirl = i == 0 && a.p.bc[0] == MM_BC_SPECULAR;
+  const bool mirr = i == g.nx - 1 && a.p.bc[1] == MM_BC_SPECULAR;
+  auto slot = [&](int pos) { return ring + (size_t)(pos % 3) * S::NV; };
+
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // bulk copies of row jj's blocks into the stage (thread 0)
+  auto issue = [&](int jj) {
+    if (threadIdx.x != 0) return;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const float* src[W + 2];
+    unsigned bytes = 0;
+#pragma unroll
+    for (int sg = 0; sg < W + 2; ++sg) {
+      src[sg] = stage_source(a, i0 - 1 + sg, jj, S::NV);
+      if (src[sg]) bytes += S::NV * sizeof(float);
+    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+#pragma unroll
+    for (int sg = 0; sg < W + 2; ++sg)
+      if (src[sg])
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(smem_addr(stage + sg * S::NV)),
+            "l"(src[sg]), "r"((unsigned)(S::NV * sizeof(float))), "r"(bar)
+            : "memory");
+  };
+  // the x sweeps of this segment, in order: the halo row below (if any), j0, then j0+1 .. j1
+  // (wrapping for periodic y; the last one only if it exists)
+  const bool halo = j0 > 0 || pery;
+  const int jlast = (j1 < g.ny || pery) ? j1 : j1 - 1;  // last x-swept row (before wrapping)
+  const int nx_rows = (halo ? 1 : 0) + (jlast - j0 + 1);
+  auto xrow = [&](int n) {  // the n-th x-swept row
+    int jj = (halo ? j0 - 1 : j0) + n;
+    if (jj < 0) jj += g.ny;
+    if (jj >= g.ny) jj -= g.ny;
+    return jj;
+  };
+  uint32_t parity = 0;
+  issue(xrow(0));
+  // x sweep number n into ring position pos, then the copy for sweep n + 1
+  auto xstep = [&](int n, int pos) -> bool {
+    // the sweep's warp shuffles need every lane: a warp sweeps only if all its lanes saw the copy
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
+    parity ^= 1u;
+    if (col && ok)
+      fx_sweep<NV1, NV2, true>(a, i, xrow(n), slot(pos), xt, stage + (w + 1) * S::NV,
+                               stage + w * S::NV, stage + (w + 2) * S::NV, mirl, mirr);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(a.err, ERR_WAIT_TIMEOUT);
+      mbar_wait_bounded(bar, parity ^ 1u);  // copies still in flight, bounded again
+      return false;
+    }
+    if (n + 1 < nx_rows) issue(xrow(n + 1));
+    return true;
+  };
+  int n = 0;
+  if (halo && !xstep(n++, 0)) return;
+  if (!xstep(n++, 1)) return;
+  for (int j = j0; j < j1; ++j) {
+    const int pos = j - j0 + 1;
+    if (j + 1 < g.ny || pery)
+      if (!xstep(n++, pos + 1)) return;
+    if (!col || diffuse_wall_cell(g, a.p, i, j)) continue;  // wall cells: the wall kernel
+    const float* rc = slot(pos);
+    const bool hasb = j > 0 || pery, hast = j < g.ny - 1 || pery;
     const float* rb = rc;
     if (hasb) rb = slot(pos + 2);
     else if (a.p.bc[2] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 2)); rb = slot(pos + 2); }
@@ -744,11 +927,17 @@ static FusedPick flat_pick() {
                    sizeof(float) * kFusedWarps * (size_t)FlatShape<NV1, NV2>::PER_WARP};
 }
 
+template <int NV1, int NV2>
+static FusedPick staged_pick() {
+  return FusedPick{k_micro_staged_f32<NV1, NV2>,
+                   sizeof(float) * (size_t)StagedShape<NV1, NV2>::FLOATS};
+}
+
 static FusedPick pick_fused(const KGrid& g) {
   const bool sym = v2_symmetric_f32(g);
   if (sym && g.nv1 == 32 && g.nv2 == 32) return flat_pick<32, 32>();
-  if (sym && g.nv1 == 24 && g.nv2 == 24) return flat_pick<24, 24>();
-  if (sym && g.nv1 == 16 && g.nv2 == 16) return flat_pick<16, 16>();
+  if (sym && g.nv1 == 24 && g.nv2 == 24) return staged_pick<24, 24>();
+  if (sym && g.nv1 == 16 && g.nv2 == 16) return staged_pick<16, 16>();
   const size_t smem = column_smem(g);
   if (g.nv1 == 32 && g.nv2 == 32) return FusedPick{k_micro_fused_f32<32, 32>, smem};
   if (g.nv1 == 24 && g.nv2 == 24) return FusedPick{k_micro_fused_f32<24, 24>, smem};
@@ -784,10 +973,11 @@ int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
 
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
-                            const MicroShape& ms, int nseg, cudaStream_t s) {
+                            const MicroShape& ms, int nseg, int* err, cudaStream_t s) {
   (void)ms;
   const FusedPick f = pick_fused(g);
   FusedF32 a;
+  a.err = err;
   a.Gin = Gin;
   a.Gout = Gout;
   a.Gexp = Gexp;
@@ -801,7 +991,8 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
   a.R = 32 / g.nv1;
   a.nseg = nseg;
   a.seg_rows = (g.ny + nseg - 1) / nseg;
-  const int warps = g.nx * nseg;
+  // one warp per column and segment; the staged kernels give a CTA kFusedWarps adjacent columns
+  const int warps = ((g.nx + kFusedWarps - 1) / kFusedWarps) * kFusedWarps * nseg;
   if (f.smem > 48 * 1024)
     cudaFuncSetAttribute(f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
   f.kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, f.smem, s>>>(a);
