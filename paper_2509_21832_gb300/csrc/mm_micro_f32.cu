@@ -448,14 +448,13 @@ struct FlatShape {
 template <int NV1, int NV2, bool STAGED>
 __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float* dst, float* xt,
                                          const float* Gcb, const float* Gl, const float* Gr,
-                                         bool mirl, bool mirr) {
+                                         bool mirl, bool mirr, float fv) {
   using S = FlatShape<NV1, NV2>;
   const KGrid& g = a.g;
   const int nc = g.nx * g.ny, cell = j * g.nx + i;
   const int lane = threadIdx.x & 31;
   float2* X1 = reinterpret_cast<float2*>(xt);  // (c2, c2^2)
   float2* X2 = X1 + NV2;                        // (e2, projection term)
-  const float fv = load_fields(a.pf, nc, cell);
   const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
   const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT), kap = field(fv, F_KAP);
   for (int l = lane; l < NV2; l += 32) {
@@ -466,11 +465,12 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
   }
   float c1[S::P], sig[S::P], lam[S::P];
   const float* Gu[S::P];
-  int l0[S::P];
+  int l0[S::P], kc[S::P];
 #pragma unroll
   for (int s = 0; s < S::P; ++s) {
     const int q0 = lane + 32 * s, k = q0 % NV1;
     l0[s] = q0 / NV1;
+    kc[s] = k;
     const float v1 = fmaf(k + 0.5f, a.gf.dv1, a.gf.v1min);
     c1[s] = v1 - u1;
     const float av = fabsf(v1);
@@ -522,12 +522,19 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
     const float2 cq = X1[l];
     X2[l].y = X2[l].x * fmaf(b2, cq.x, gm * cq.y);
   }
+  // kap e1 of each column: with several columns per lane, lane k evaluates column k's and the
+  // owners fetch it by shuffle
   float ak[S::P], bk[S::P];
+  if constexpr (S::P == 1) {
+    bk[0] = kap * expf(-c1[0] * c1[0] * inv2T);
+  } else {
+    const float ck = fmaf((lane < NV1 ? lane : 0) + 0.5f, a.gf.dv1, a.gf.v1min) - u1;
+    const float bown = kap * expf(-ck * ck * inv2T);
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) {
-    bk[s] = kap * expf(-c1[s] * c1[s] * inv2T);
-    ak[s] = bk[s] * fmaf(gm * c1[s], c1[s], fmaf(b1, c1[s], b0));
+    for (int s = 0; s < S::P; ++s) bk[s] = __shfl_sync(0xffffffffu, bown, kc[s]);
   }
+#pragma unroll
+  for (int s = 0; s < S::P; ++s) ak[s] = bk[s] * fmaf(gm * c1[s], c1[s], fmaf(b1, c1[s], b0));
   __syncwarp();
   // pass 2: G* = G - dt Z + dt Zhat
 #pragma unroll
@@ -550,7 +557,7 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
 // above (rt) the cell (flat mapping).
 template <int NV1, int NV2>
 __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const float* rb,
-                                         const float* rc, const float* rt, float* tb) {
+                                         const float* rc, const float* rt, float* tb, float fv) {
   using S = FlatShape<NV1, NV2>;
   const KGrid& g = a.g;
   const int nc = g.nx * g.ny, cell = j * g.nx + i;
@@ -560,7 +567,6 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
   float4* TS = reinterpret_cast<float4*>(tb);
   float4* TA = TS + NV2;
   float2* TC = reinterpret_cast<float2*>(TA + NV2);
-  const float fv = load_fields(a.pf, nc, cell);
   const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
   const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT);
   const float Ti11h = field(fv, F_TI11H), Ti12 = field(fv, F_TI12), Ti22h = field(fv, F_TI22H);
@@ -580,11 +586,12 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
     TC[l] = make_float2(q, q * c2);
   }
   float c1[S::P], c1q[S::P];
-  int l0[S::P];
+  int l0[S::P], kc[S::P];
 #pragma unroll
   for (int s = 0; s < S::P; ++s) {
     const int q0 = lane + 32 * s, k = q0 % NV1;
     l0[s] = q0 / NV1;
+    kc[s] = k;
     c1[s] = fmaf(k + 0.5f, a.gf.dv1, a.gf.v1min) - u1;
     c1q[s] = c1[s] * c1[s];
   }
@@ -622,20 +629,50 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
   // per column: the polynomial coefficients of Ghat in c2 (times e1) and the ES Gaussian's
   // cross factor with its row ratio
   float A0[S::P], A1[S::P], A2[S::P], A3[S::P], x[S::P], rat[S::P];
-#pragma unroll
-  for (int s = 0; s < S::P; ++s) {
-    const float c = c1[s], cq = c1q[s];
+  if constexpr (S::P == 1) {
+    const float c = c1[0], cq = c1q[0];
     const float C0 = om1kap * fmaf(gm, cq, fmaf(b1, c, b0)) - c * fmaf(c, fmaf(c, w03, w02), w01) - ome;
     const float C1 = fmaf(om1kap, b2, -fmaf(c, fmaf(c, w12, w11), w10));
     const float C2 = fmaf(om1kap, gm, -fmaf(c, w21, w20));
     const float e1 = expf(-cq * inv2T);
-    A0[s] = e1 * C0;
-    A1[s] = e1 * C1;
-    A2[s] = e1 * C2;
-    A3[s] = -e1 * w30;
-    const float c2r = fmaf(l0[s] + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
-    x[s] = gam0 * expf(-Ti11h * cq - Ti12 * c * c2r);
-    rat[s] = expf(-Ti12 * c * (S::ST * a.gf.dv2));
+    A0[0] = e1 * C0;
+    A1[0] = e1 * C1;
+    A2[0] = e1 * C2;
+    A3[0] = -e1 * w30;
+    const float c2r = fmaf(l0[0] + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
+    x[0] = gam0 * expf(-Ti11h * cq - Ti12 * c * c2r);
+    rat[0] = expf(-Ti12 * c * (S::ST * a.gf.dv2));
+  } else {
+    // lane k evaluates column k's coefficients, the Gaussian factor at row 0 and the ratio r of
+    // the cross factor between adjacent rows; the owners of column k fetch them by shuffle and
+    // advance the Gaussian factor to their first row l0 by r^l0 (l0 < ST, a power of two)
+    const float c = fmaf((lane < NV1 ? lane : 0) + 0.5f, a.gf.dv1, a.gf.v1min) - u1;
+    const float cq = c * c;
+    const float C0 = om1kap * fmaf(gm, cq, fmaf(b1, c, b0)) - c * fmaf(c, fmaf(c, w03, w02), w01) - ome;
+    const float C1 = fmaf(om1kap, b2, -fmaf(c, fmaf(c, w12, w11), w10));
+    const float C2 = fmaf(om1kap, gm, -fmaf(c, w21, w20));
+    const float e1 = expf(-cq * inv2T);
+    const float a0 = e1 * C0, a1 = e1 * C1, a2 = e1 * C2, a3 = -e1 * w30;
+    const float c2z = fmaf(0.5f, a.gf.dv2, a.gf.v2min) - u2;
+    const float x0 = gam0 * expf(-Ti11h * cq - Ti12 * c * c2z);
+    const float r1 = expf(-Ti12 * c * a.gf.dv2);
+    constexpr unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int s = 0; s < S::P; ++s) {
+      A0[s] = __shfl_sync(full, a0, kc[s]);
+      A1[s] = __shfl_sync(full, a1, kc[s]);
+      A2[s] = __shfl_sync(full, a2, kc[s]);
+      A3[s] = __shfl_sync(full, a3, kc[s]);
+      float r = __shfl_sync(full, r1, kc[s]);
+      float xs = __shfl_sync(full, x0, kc[s]);
+#pragma unroll
+      for (int b = 1; b < S::ST; b <<= 1) {
+        if (l0[s] & b) xs *= r;
+        r *= r;
+      }
+      x[s] = xs;
+      rat[s] = r;  // r1^ST
+    }
   }
   // pass 2: G^{n+1} = om1 G* + wl (G*_up - G*) + Ghat + gamma exp(...), and the heat flux sums
   float H0[S::P], H1[S::P], H2[S::P], H3[S::P];
@@ -714,7 +751,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_flat_f32(FusedF32
     const float* Gl = ul.zero ? kZeroRowF : a.Gin + (size_t)ul.cell * S::NV;
     const float* Gr = ur.zero ? kZeroRowF : a.Gin + (size_t)ur.cell * S::NV;
     fx_sweep<NV1, NV2, false>(a, i, jj, dst, xt, a.Gin + (size_t)(jj * g.nx + i) * S::NV, Gl, Gr,
-                              ul.mirror, ur.mirror);
+                              ul.mirror, ur.mirror, load_fields(a.pf, g.nx * g.ny, jj * g.nx + i));
   };
   prefetch(j0 + 1);
   if (j0 > 0 || pery) xsweep(j0 > 0 ? j0 - 1 : g.ny - 1, slot(0));
@@ -733,7 +770,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_flat_f32(FusedF32
     const float* rt = rc;
     if (hast) rt = slot(pos + 1);
     else if (a.p.bc[3] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 1)); rt = slot(pos + 1); }
-    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt);
+    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt, load_fields(a.pf, g.nx * g.ny, j * g.nx + i));
   }
 }
 
@@ -860,12 +897,14 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   issue(xrow(0));
   // x sweep number n into ring position pos, then the copy for sweep n + 1
   auto xstep = [&](int n, int pos) -> bool {
+    const int jj = xrow(n);
+    const float fvx = col ? load_fields(a.pf, g.nx * g.ny, jj * g.nx + i) : 0.f;
     // the sweep's warp shuffles need every lane: a warp sweeps only if all its lanes saw the copy
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
     parity ^= 1u;
     if (col && ok)
-      fx_sweep<NV1, NV2, true>(a, i, xrow(n), slot(pos), xt, stage + (w + 1) * S::NV,
-                               stage + w * S::NV, stage + (w + 2) * S::NV, mirl, mirr);
+      fx_sweep<NV1, NV2, true>(a, i, jj, slot(pos), xt, stage + (w + 1) * S::NV,
+                               stage + w * S::NV, stage + (w + 2) * S::NV, mirl, mirr, fvx);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicOr(a.err, ERR_WAIT_TIMEOUT);
       mbar_wait_bounded(bar, parity ^ 1u);  // copies still in flight, bounded again
@@ -879,6 +918,8 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   if (!xstep(n++, 1)) return;
   for (int j = j0; j < j1; ++j) {
     const int pos = j - j0 + 1;
+    // the y sweep's per-cell fields, in flight during this iteration's x sweep
+    const float fvy = col ? load_fields(a.pf, g.nx * g.ny, j * g.nx + i) : 0.f;
     if (j + 1 < g.ny || pery)
       if (!xstep(n++, pos + 1)) return;
     if (!col || diffuse_wall_cell(g, a.p, i, j)) continue;  // wall cells: the wall kernel
@@ -890,7 +931,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
     const float* rt = rc;
     if (hast) rt = slot(pos + 1);
     else if (a.p.bc[3] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 1)); rt = slot(pos + 1); }
-    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt);
+    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt, fvy);
   }
 }
 
