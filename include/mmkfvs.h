@@ -286,6 +286,14 @@ void mm1d_destroy(mm1d_ctx* c);
 mm_status mm_diag_exp(const double* x_dev, double* y_fast_dev, double* y_lib_dev, size_t n,
                       void* cuda_stream);
 
+/* Diagnostic of the bounded device waits (the FP32-g kernels wait on an mbarrier for their bulk
+ * copies, each wait giving up after a fixed number of attempts and setting an error bit that
+ * mm_sync reports as MM_ERR_TIMEOUT).  One warp arms an mbarrier for a 16-byte copy; with
+ * copy != 0 it issues that copy, else nothing completes the barrier and the wait gives up after
+ * `spins` attempts (1 <= spins).  Returns MM_OK when the wait completed, MM_ERR_TIMEOUT when it
+ * ran out (the device stays usable), MM_ERR_INVALID_ARG for spins < 1; synchronises cuda_stream. */
+mm_status mm_diag_bounded_wait(int copy, int spins, void* cuda_stream);
+
 /* ---- stepping without any device allocation ------------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers that may not call
  * cudaMalloc (a host framework that owns every device allocation under a fixed budget, plug-ins

@@ -52,6 +52,7 @@ EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device"
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
            "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp",
+           "mm_diag_bounded_wait",
            "mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
            "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments", "mm_batch_get_g",
            "mm_batch_last_error", "mm_batch_destroy",
@@ -123,6 +124,8 @@ def load(build_if_needed: bool = True):
         getattr(L, name).restype = ctypes.c_int
     L.mm_diag_exp.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
     L.mm_diag_exp.restype = ctypes.c_int
+    L.mm_diag_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int, vp]
+    L.mm_diag_bounded_wait.restype = ctypes.c_int
     L.mm_step_static_scratch.argtypes = [G, P, vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, vp, ctypes.c_char_p, ctypes.c_size_t]
     L.mm_step_static_scratch.restype = ctypes.c_int
@@ -270,6 +273,12 @@ def mm_diag_exp(x_dev, stream=0):
     if st != MM_OK:
         raise MMError(st, "mm_diag_exp")
     return yf, yl
+
+
+def mm_diag_bounded_wait(copy, spins=1 << 16, stream=0):
+    """Status of one bounded mbarrier wait on the device: MM_OK when the 16-byte bulk copy that
+    completes it was issued (copy=True), MM_ERR_TIMEOUT when nothing completes it."""
+    return load().mm_diag_bounded_wait(1 if copy else 0, int(spins), ctypes.c_void_p(int(stream)))
 
 
 def _check(ctx, st, what):

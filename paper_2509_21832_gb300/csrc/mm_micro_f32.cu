@@ -798,10 +798,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kWaitSpins; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  int spins = kWaitSpins) {
+  for (int it = 0; it < spins; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// Diagnostic of the bounded wait: one warp arms an mbarrier for 16 bytes and, when copy != 0,
+// issues the 16-byte bulk copy that completes it; otherwise nothing ever completes the phase and
+// the wait must run out after spins attempts.  *timed_out receives 1 if it did.
+__global__ void k_diag_bounded_wait(int copy, int spins, int* __restrict__ timed_out) {
+  __shared__ __align__(16) float buf[4];
+  __shared__ __align__(8) unsigned long long mb;
+  const uint32_t bar = smem_addr(&mb);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(16u)
+                 : "memory");
+    if (copy)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 16, "
+          "[%2];" ::"r"(smem_addr(buf)),
+          "l"(kZeroRowF), "r"(bar)
+          : "memory");
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, 0u, spins));
+  if (threadIdx.x == 0) *timed_out = ok ? 0 : 1;
 }
 
 template <int NV1, int NV2>
@@ -1040,3 +1065,20 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
 }
 
 }  // namespace mmk
+
+extern "C" mm_status mm_diag_bounded_wait(int copy, int spins, void* cuda_stream) {
+  if (spins < 1) return MM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int* d = nullptr;
+  int h = -1;
+  cudaError_t e = cudaMalloc((void**)&d, sizeof(int));
+  if (e == cudaSuccess) {
+    mmk::k_diag_bounded_wait<<<1, 32, 0, s>>>(copy, spins, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+  }
+  if (e != cudaSuccess) return MM_ERR_CUDA;
+  return h ? MM_ERR_TIMEOUT : MM_OK;
+}
