@@ -114,6 +114,19 @@ mm_status mm_sync(mm_ctx* ctx);
 /* Copy Q (and H unless H_host is NULL) to host memory; synchronises the stream. */
 mm_status mm_get_moments(mm_ctx* ctx, double* Q_host, double* H_host);
 
+/* One time step from host state to host moments: the same result, bit for bit, as
+ * mm_set_state(c, Q_host, G_host); mm_step(c, dt, eps, 1); mm_get_moments(c, Q_out, H_out), with
+ * the host-to-device copy of G_host overlapped with the step.  For plain FP64 contexts g is
+ * copied in row chunks on a second stream and the micro sweeps of each chunk start as soon as
+ * its rows (and those of its upper neighbour) are on the device; FP32-g, learned-closure and
+ * manufactured-solution contexts run the three calls in sequence.  Q_host [6][ny][nx] and
+ * G_host [ny][nx][nv2][nv1] are read (page-locked memory lets the copies run asynchronously);
+ * Q_out [6][ny][nx] and, if not NULL, H_out [4][ny][nx] receive Q^{n+1} and the heat flux.
+ * Synchronous; the context's state afterwards is that of the step.  Errors: MM_ERR_INVALID_ARG
+ * for NULL Q_host, G_host, Q_out or dt, eps not > 0; MM_ERR_NONPHYSICAL as mm_sync. */
+mm_status mm_step_host(mm_ctx* c, const double* Q_host, const double* G_host, double dt,
+                       double eps, double* Q_out, double* H_out);
+
 /* Copy Q (and H unless NULL) to caller-owned FP64 device memory; asynchronous. */
 mm_status mm_get_moments_device(mm_ctx* ctx, double* Q_dev, double* H_dev);
 

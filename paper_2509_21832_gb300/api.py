@@ -51,7 +51,7 @@ TAU1D_HARDSPHERE, TAU1D_CONST = 0, 1
 EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device", "mm_step",
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
-           "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp",
+           "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp", "mm_step_host",
            "mm_diag_bounded_wait",
            "mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
            "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments", "mm_batch_get_g",
@@ -91,6 +91,7 @@ def load(build_if_needed: bool = True):
     L.mm_step.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.mm_sync.argtypes = [vp]
     L.mm_get_moments.argtypes = [vp, vp, vp]
+    L.mm_step_host.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
     L.mm_get_moments_device.argtypes = [vp, vp, vp]
     L.mm_get_g.argtypes = [vp, vp]
     L.mm_dt_for_cfl.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -339,6 +340,19 @@ class Solver:
                                    _host_ptr(H, 4 * self.ncell))
         _check(self.ctx, st, "mm_get_moments")
         return Q, H
+
+    def step_host(self, Q, G, dt, eps, Q_out=None, H_out=None):
+        """One step from host (Q, G) to host (Q^{n+1}, H): mm_step_host, the copy of G overlapped
+        with the step (bitwise the result of set_state, step(dt, eps, 1), get_moments)."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        Qo = Q_out if Q_out is not None else np.empty((6, self.grid.ny, self.grid.nx))
+        Ho = H_out if H_out is not None else np.empty((4, self.grid.ny, self.grid.nx))
+        st = self.L.mm_step_host(self.ctx, _host_ptr(Q, 6 * self.ncell), _host_ptr(G, self.nphase),
+                                 float(dt), float(eps), _host_ptr(Qo, 6 * self.ncell),
+                                 _host_ptr(Ho, 4 * self.ncell))
+        _check(self.ctx, st, "mm_step_host")
+        return Qo, Ho
 
     def get_moments_device(self, Q_dev, H_dev=None):
         st = self.L.mm_get_moments_device(self.ctx, _dev_ptr(Q_dev, 6 * self.ncell),

@@ -79,6 +79,9 @@ struct mm_ctx {
   double* mms_gam = nullptr;
   double* mms_src_g = nullptr;           // source term of g^{n+1} (layout of G)
   double* mms_src_q = nullptr;           // int (1, v, v v) S dv [6][ny][nx]
+  // mm_step_host: streams for the row-chunk copies of g and for the x sweeps; events per chunk
+  cudaStream_t cstream = nullptr, xstream = nullptr;
+  std::vector<cudaEvent_t> chunk_events;
   bool timing = false;
   std::vector<TimedLaunch> pending;
   std::vector<cudaEvent_t> free_events;
@@ -295,6 +298,94 @@ void enqueue_step(mm_ctx* c, double dt, double eps) {
   if (c->fp32) enqueue_plain<float>(c, dt, eps);
   else if (c->mlp) enqueue_hybrid(c, dt, eps);
   else enqueue_plain<double>(c, dt, eps);
+}
+
+constexpr int kHostChunks = 16;  // row chunks of g in mm_step_host
+
+// One plain FP64 step whose g^n arrives from host memory while the micro sweeps run.  Three
+// streams: the copy stream brings Q, then g in row chunks; the x stream sweeps each chunk once
+// its rows have arrived; the context stream computes the per-cell fields, then sweeps each chunk
+// in y once the x sweeps of it and of its neighbour chunks are done (with periodic y the first
+// chunk's lower neighbour is the last chunk), then the walls and the macro update.  x sweeps of
+// later chunks run beside y sweeps of earlier ones.  Every cell is computed by the same kernels
+// as in enqueue_plain, so the result is the same bit for bit.
+mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* G_host,
+                                 double dt, double eps) {
+  const KGrid& g = c->kg;
+  const KParams& p = c->kp;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (!c->cstream) e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !c->xstream)
+    e = cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking);
+  const int nchunk = std::min(g.ny, kHostChunks);
+  // events: [0, n) chunk copied, [n, 2n) chunk x-swept, 2n entry, 2n+1 Q copied, 2n+2 fields
+  const int nev = 2 * nchunk + 3;
+  while (e == cudaSuccess && (int)c->chunk_events.size() < nev) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) c->chunk_events.push_back(ev);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy streams");
+  cudaEvent_t* copied = c->chunk_events.data();
+  cudaEvent_t* xswept = copied + nchunk;
+  cudaEvent_t entry = copied[2 * nchunk], qin = copied[2 * nchunk + 1],
+              fields = copied[2 * nchunk + 2];
+  double* G = static_cast<double*>(c->G);
+  double* Gs = static_cast<double*>(c->Gs);
+  const size_t row = (size_t)g.nx * g.nv1 * g.nv2;  // doubles of g per row of cells
+  auto row0 = [&](int r) { return (int)((long long)g.ny * r / nchunk); };
+  // the copies may overwrite Q and g only after the work already queued on the context stream;
+  // host-to-device copies are served in issue order, so Q (which the per-cell fields need
+  // first) goes ahead of the chunks of g
+  e = cudaEventRecord(entry, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cstream, entry, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->Q, Q_host, 6 * c->ncell * sizeof(double), cudaMemcpyHostToDevice,
+                        c->cstream);
+  if (e == cudaSuccess) e = cudaEventRecord(qin, c->cstream);
+  for (int r = 0; r < nchunk && e == cudaSuccess; ++r) {
+    const size_t off = row * row0(r), n = row * (row0(r + 1) - row0(r));
+    e = cudaMemcpyAsync(G + off, G_host + off, n * sizeof(double), cudaMemcpyHostToDevice,
+                        c->cstream);
+    if (e == cudaSuccess) e = cudaEventRecord(copied[r], c->cstream);
+  }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, qin, 0);
+  if (e == cudaSuccess && c->cvalid) e = cudaMemsetAsync(c->cvalid, 1, c->ncell, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy state in");
+  c->cstale = false;
+  c->have_state = true;
+  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
+  cudaEventRecord(fields, s);
+  cudaStreamWaitEvent(c->xstream, fields, 0);
+  for (int r = 0; r < nchunk; ++r) {
+    cudaStreamWaitEvent(c->xstream, copied[r], 0);
+    launch_micro_x<double>(G, Gs, c->prim, g, p, dt, c->ms, c->xstream, row0(r) * g.nx,
+                           (row0(r + 1) - row0(r)) * g.nx);
+    cudaEventRecord(xswept[r], c->xstream);
+  }
+  auto ysweep = [&](int r, int after) {
+    cudaStreamWaitEvent(s, xswept[after], 0);
+    timed(c, T_MICRO_Y, [&] {
+      launch_micro_y<double>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, nullptr,
+                             row0(r) * g.nx, (row0(r + 1) - row0(r)) * g.nx);
+    });
+  };
+  // x sweeps complete in chunk order, so waiting for chunk r+1 covers chunks 0..r+1
+  const bool pery = p.bc[2] == MM_BC_PERIODIC;
+  for (int r = pery && nchunk > 1 ? 1 : 0; r < nchunk; ++r) ysweep(r, std::min(r + 1, nchunk - 1));
+  if (pery && nchunk > 1) ysweep(0, nchunk - 1);
+  if (c->n_wall > 0)
+    timed(c, T_MICRO_YW, [&] {
+      launch_micro_y_wall<double>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
+                                  c->ms, c->err, s);
+    });
+  timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
+  timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
+  timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  return MM_OK;
 }
 
 // Buffers of the closure, allocated on first use.
@@ -559,6 +650,24 @@ mm_status mm_get_moments(mm_ctx* c, double* Q_host, double* H_host) {
   return check_device_errors(c);
 }
 
+mm_status mm_step_host(mm_ctx* c, const double* Q_host, const double* G_host, double dt,
+                       double eps, double* Q_out, double* H_out) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!Q_host || !G_host || !Q_out)
+    return fail(c, MM_ERR_INVALID_ARG, "Q_host, G_host and Q_out are required");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, MM_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, MM_ERR_INVALID_ARG, "eps must be > 0");
+  if (c->fp32 || c->mlp || c->mms) {  // not pipelined: the same three calls in sequence
+    mm_status st = mm_set_state(c, Q_host, G_host);
+    if (st == MM_OK) st = mm_step(c, dt, eps, 1);
+    if (st == MM_OK) st = mm_get_moments(c, Q_out, H_out);
+    return st;
+  }
+  mm_status st = enqueue_step_from_host(c, Q_host, G_host, dt, eps);
+  if (st != MM_OK) return st;
+  return mm_get_moments(c, Q_out, H_out);
+}
+
 mm_status mm_get_moments_device(mm_ctx* c, double* Q_dev, double* H_dev) {
   if (!c) return MM_ERR_INVALID_ARG;
   if (!Q_dev) return fail(c, MM_ERR_INVALID_ARG, "Q_dev is NULL");
@@ -794,6 +903,12 @@ void mm_destroy(mm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   destroy_events(c);
+  for (cudaStream_t t : {c->cstream, c->xstream})
+    if (t) {
+      cudaStreamSynchronize(t);
+      cudaStreamDestroy(t);
+    }
+  for (auto e : c->chunk_events) cudaEventDestroy(e);
   cudaFree(c->G);
   cudaFree(c->Gs);
   cudaFree(c->Gexp);

@@ -73,14 +73,17 @@ MicroShape micro_shape(int nv1, int nv2);
 
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
                   double dt, double eps, int* err, cudaStream_t s);
+// The sweeps over the cells [cell0, cell0 + ncells) (ncells < 0: every cell from cell0 = 0).
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
-                    const KParams& p, double dt, const MicroShape& ms, cudaStream_t s);
+                    const KParams& p, double dt, const MicroShape& ms, cudaStream_t s,
+                    int cell0 = 0, int ncells = -1);
 // src (optional): a term added to g^{n+1} at every node, same layout as G
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
-                    cudaStream_t s, const double* src = nullptr);
+                    cudaStream_t s, const double* src = nullptr, int cell0 = 0,
+                    int ncells = -1);
 template <typename Tg>
 void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,

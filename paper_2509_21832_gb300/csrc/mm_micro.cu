@@ -24,9 +24,9 @@ template <typename Tg, int NR>
 __global__ void __launch_bounds__(NR > 0 ? 256 : 512, 1) k_micro_x(const Tg* __restrict__ Gin,
                                                     Tg* __restrict__ Gout,
                                                     const double* __restrict__ prim, KGrid g,
-                                                    KParams p, double dtidx, int R) {
+                                                    KParams p, double dtidx, int R, int cell0) {
   extern __shared__ double sm[];
-  micro_x_body<Tg, NR>(Gin, Gout, prim, g, p, dtidx, R, blockIdx.x, sm);
+  micro_x_body<Tg, NR>(Gin, Gout, prim, g, p, dtidx, R, cell0 + (int)blockIdx.x, sm);
 }
 
 template <typename Tg>
@@ -36,9 +36,10 @@ __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs,
                                                     const double* __restrict__ prim, KGrid g,
                                                     KParams p, double dtidy, double hscale, int R,
                                                     int* __restrict__ err,
-                                                    const double* __restrict__ src) {
+                                                    const double* __restrict__ src, int cell0) {
   extern __shared__ double sm[];
-  micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, blockIdx.x, sm, src);
+  micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, cell0 + (int)blockIdx.x, sm,
+                   src);
 }
 
 template <typename Tg>
@@ -208,22 +209,27 @@ template void launch_micro_y_list<double>(const double*, double*, double*, const
 
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
-                    const KParams& p, double dt, const MicroShape& ms, cudaStream_t s) {
+                    const KParams& p, double dt, const MicroShape& ms, cudaStream_t s, int cell0,
+                    int ncells) {
+  const int n = ncells < 0 ? g.nx * g.ny : ncells;
+  if (n <= 0) return;
   with_x_kernel<Tg>(ms.xrows, [&](auto kern) {
     if (ms.smem_x > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_x);
-    kern<<<g.nx * g.ny, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R);
+    kern<<<n, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R, cell0);
   });
 }
 
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
-                    cudaStream_t s, const double* src) {
+                    cudaStream_t s, const double* src, int cell0, int ncells) {
+  const int n = ncells < 0 ? g.nx * g.ny : ncells;
+  if (n <= 0) return;
   if (ms.smem_y > 48 * 1024)
     cudaFuncSetAttribute(k_micro_y<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_y);
-  k_micro_y<Tg><<<g.nx * g.ny, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
-                                                           eps * g.dv1 * g.dv2, ms.R, err, src);
+  k_micro_y<Tg><<<n, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
+                                                 eps * g.dv1 * g.dv2, ms.R, err, src, cell0);
 }
 
 template <typename Tg>
@@ -239,10 +245,12 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
 }
 
 template void launch_micro_x<double>(const double*, double*, const double*, const KGrid&,
-                                     const KParams&, double, const MicroShape&, cudaStream_t);
+                                     const KParams&, double, const MicroShape&, cudaStream_t, int,
+                                     int);
 template void launch_micro_y<double>(const double*, double*, double*, const double*,
                                      const KGrid&, const KParams&, double, double,
-                                     const MicroShape&, int*, cudaStream_t, const double*);
+                                     const MicroShape&, int*, cudaStream_t, const double*, int,
+                                     int);
 template void launch_micro_y_wall<double>(const double*, double*, double*, const double*,
                                           const int*, int, const KGrid&, const KParams&, double,
                                           double, const MicroShape&, int*, cudaStream_t);
