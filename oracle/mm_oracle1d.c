@@ -61,16 +61,16 @@ static void kfvs1(double rho, double u, double T, double Fp[3], double Fm[3]) {
 
 /* ---- manufactured solution (Section 4.1) ----------------------------------------------------
  * f = (exp(-(v-1)^2) + 2 exp(-(v+1)^2)) (2 + sin(2 pi (x - t))), rho = 3 sqrt(pi) F, u = -1/3,
- * T = 25/18; S = f_t + v f_x - (tau/eps)(M - f) with tau and M of the exact state. */
+ * T = 25/18; S = f_t + v f_x - (tau/eps)(M - f) with M of the exact state and tau the cell's
+ * tau^n_i, the same tau as the Ghat that S enters (a reading: the passage writes only "tau"). */
 static double mms1_phi(double v) { return exp(-(v - 1.0) * (v - 1.0)) + 2.0 * exp(-(v + 1.0) * (v + 1.0)); }
 static double mms1_M(double v) { return 1.8 * exp(-0.04 * (3.0 * v + 1.0) * (3.0 * v + 1.0)); }
 
-static void mms1_source(const orc1d_grid* g, const orc1d_params* p, double eps, double t,
-                        double x, double* S) {
+static void mms1_source(const orc1d_grid* g, double tau, double eps, double t, double x,
+                        double* S) {
   const double F = 2.0 + sin(2.0 * PI1 * (x - t));
   const double Fx = 2.0 * PI1 * cos(2.0 * PI1 * (x - t));
   const double Ft = -Fx;
-  const double tau = tau1(p, 3.0 * sqrt(PI1) * F, 25.0 / 18.0);
   for (int k = 0; k < g->nv; ++k) {
     const double v = v_of(g, k), ph = mms1_phi(v);
     S[k] = ph * (Ft + v * Fx) - (tau / eps) * (mms1_M(v) - ph) * F;
@@ -146,7 +146,7 @@ int orc1d_step(const orc1d_grid* g, const orc1d_params* p, double* Q, double* G,
       }
       proj1(g, rho[i], u[i], T[i], Z, PZ);
       if (mms) {
-        mms1_source(g, p, eps, tn, g->x0 + (i + 0.5) * dx, S);
+        mms1_source(g, tau, eps, tn, g->x0 + (i + 0.5) * dx, S);
         proj1(g, rho[i], u[i], T[i], S, PS);
       }
       const double w1 = eps / (eps + dt * tau), w2 = dt * tau / (eps + dt * tau);

@@ -99,17 +99,19 @@ def test_asymptotic_preserving_limit():
 
 
 def test_convergence_table():
-    """Table tab5-2 up to N = 160 (the finer rows run on the GPU).  The macro error in the
-    (rho, rho u, int v^2 f) convention reproduces the printed values to 3 %; the micro error lies
-    7-22 % below the printed one; the printed step count 4095 at N = 640 is checked by the rule."""
+    """Table tab5-2 up to N = 160 (the finer rows run on the GPU).  With the residual's tau taken
+    as the cell's tau^n_i, the macro error in the (rho, rho u, int v^2 f) convention and the micro
+    error reproduce the printed values to 5 % (4 % measured) and the printed rates to 0.08; the
+    printed step count 4095 at N = 640 is checked by the rule."""
     with open(GOLDEN) as f:
         table = {r["n"]: r for r in json.load(f)["table_tab5_2"]}
     assert O.dt1d(640, 640, 0.95, 0.9351)[1] == 4095
     prev = None
     for n in (10, 20, 40, 80, 160):
         em, eu, _ = _errors(n)
-        assert abs(em / table[n]["macro"] - 1) <= 0.03, (n, em)
-        assert 0.75 <= eu / table[n]["micro"] <= 1.0, (n, eu)
+        assert abs(em / table[n]["macro"] - 1) <= 0.05, (n, em)
+        assert abs(eu / table[n]["micro"] - 1) <= 0.05, (n, eu)
         if prev is not None:
             assert abs(math.log2(prev[0] / em) - table[n]["macro_rate"]) <= 0.05
+            assert abs(math.log2(prev[1] / eu) - table[n]["micro_rate"]) <= 0.08
         prev = (em, eu)
