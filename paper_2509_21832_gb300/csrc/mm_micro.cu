@@ -10,6 +10,7 @@
 // ES Gaussian is K e^{-a c1^2/2} e^{-d c2^2/2} e^{-b c1 c2}, the last factor advanced along a
 // thread's rows by a multiplicative recurrence.  Velocity sums are accumulated per thread in the
 // order of its rows, then combined across the CTA with warp shuffles and shared memory.
+#include <algorithm>
 #include <cmath>
 
 #include "mm_body_micro.cuh"
@@ -114,7 +115,17 @@ int x_rows(const MicroShape& ms, int nv2);
 MicroShape micro_shape(int nv1, int nv2) {
   MicroShape ms{1, 32, 0, 0};
   double best = -1.0;
-  for (int R = 1; R <= 32; ++R) {
+  // nv1 <= 32: one warp per cell, R = 32 div nv1 rows per pass.  Measured on GB300 (FP64 step,
+  // 160^2 cells): against CTAs of several warps with full lanes it is 1.2x faster at 24^2 and
+  // 1.6-4x at 17^2 ... 22^2 -- no cross-warp reductions, and the per-cell work (tables, sums,
+  // coefficients) spread over the most rows per thread outweigh the idle lanes.
+  if (nv1 <= 32) {
+    ms.R = std::min(32 / nv1, nv2);
+    ms.threads = 32;
+    best = 2.0;
+  }
+  // wider meshes: the CTA size (whole warps, at most kMaxThreads) with the fewest idle lanes
+  for (int R = 1; R <= 32 && best < 2.0; ++R) {
     const int thr = R * nv1;
     if (thr > micro_body::kMaxThreads) break;
     const int thr32 = (thr + 31) / 32 * 32;
@@ -139,13 +150,14 @@ MicroShape micro_shape(int nv1, int nv2) {
 // 256 threads, so that a thread may hold up to 255 registers), else 0.
 int x_rows(const MicroShape& ms, int nv2) {
   const int nr = nv2 % ms.R == 0 ? nv2 / ms.R : 0;
-  return ms.threads <= 256 && (nr == 32 || nr == 8 || nr == 6) ? nr : 0;
+  return ms.threads <= 256 && (nr == 32 || nr == 24 || nr == 8 || nr == 6) ? nr : 0;
 }
 
 template <typename Tg, typename F>
 void with_x_kernel(int nr, F&& f) {
   switch (nr) {
     case 32: f(k_micro_x<Tg, 32>); break;
+    case 24: f(k_micro_x<Tg, 24>); break;
     case 8: f(k_micro_x<Tg, 8>); break;
     case 6: f(k_micro_x<Tg, 6>); break;
     default: f(k_micro_x<Tg, 0>); break;
@@ -156,6 +168,7 @@ template <typename Tg, typename F>
 void with_x_list_kernel(int nr, F&& f) {
   switch (nr) {
     case 32: f(k_micro_x_list<Tg, 32>); break;
+    case 24: f(k_micro_x_list<Tg, 24>); break;
     case 8: f(k_micro_x_list<Tg, 8>); break;
     case 6: f(k_micro_x_list<Tg, 6>); break;
     default: f(k_micro_x_list<Tg, 0>); break;
