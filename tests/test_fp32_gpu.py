@@ -33,6 +33,10 @@ CASES = [
     # diffuse side, specular images of the bottom row
     ("walls_24", dict(nx=9, ny=8, nv1=24, nv2=24),
      (I.DIFFUSE, I.SPECULAR, I.SPECULAR, I.EXTRAP), dict(wall_T=(1.2, 1.0, 1.0, 1.0))),
+    # 32^2 (the per-warp flat kernel): zero row behind a diffuse x side, G* exported for the
+    # wall kernel at the diffuse top wall
+    ("walls_32", dict(nx=7, ny=9, nv1=32, nv2=32),
+     (I.SPECULAR, I.DIFFUSE, I.EXTRAP, I.DIFFUSE), dict(wall_T=(1.0, 0.9, 1.0, 1.15))),
     # v2 mesh not symmetric about zero: the column-mapped kernel of the 24^2 shape
     ("asym_24", dict(nx=8, ny=9, nv1=24, nv2=24, v2min=-7.0, v2max=9.0),
      (I.EXTRAP, I.EXTRAP, I.PERIODIC, I.PERIODIC), {}),
