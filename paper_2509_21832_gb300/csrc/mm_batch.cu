@@ -56,7 +56,7 @@ __global__ void k_batch_prims(const double* __restrict__ Q, double* __restrict__
        item += gridDim.x * blockDim.x) {
     const BatchProb& b = pr[find_prob(start, nprob, item)];
     macro_body::prims_body(Q + 6 * (size_t)b.c_off, prim + NPRIM * (size_t)b.c_off, nullptr, b.g,
-                           b.p, b.dt, b.eps, err, item - b.c_off);
+                           b.p, b.dt, b.eps, 1.0 / b.eps, err, item - b.c_off);
   }
 }
 

@@ -32,9 +32,9 @@ __device__ __forceinline__ void load_q(const double* Q, int nc, int c, double q[
 
 // Primitive quantities of a moment vector; returns false for a non-physical state.
 __device__ __forceinline__ bool prim6(const double q[6], double& rho, double& u1, double& u2,
-                                      double& P11, double& P12, double& P22) {
+                                      double& P11, double& P12, double& P22, double& ir) {
   rho = q[0];
-  const double ir = 1.0 / rho;
+  ir = 1.0 / rho;
   u1 = q[1] * ir;
   u2 = q[2] * ir;
   P11 = q[3] - rho * u1 * u1;
@@ -49,9 +49,9 @@ __device__ __forceinline__ bool prim6(const double q[6], double& rho, double& u1
 // rho > 0 and T > 0; the input's pressure tensor need not be positive definite (with a
 // manufactured source the state before the last half step can leave that set).
 __device__ __forceinline__ bool coll_half(const KParams& p, const double q[6], double eps,
-                                          double dt, double o[6]) {
+                                          double dt, double o[6], double& ir) {
   double rho, u1, u2, P11, P12, P22;
-  prim6(q, rho, u1, u2, P11, P12, P22);
+  prim6(q, rho, u1, u2, P11, P12, P22, ir);
   const double T = (P11 + P22) * 0.5 / rho;
   const bool ok = rho > 0.0 && T > 0.0 && isfinite(T) && isfinite(u1) && isfinite(u2) &&
                   isfinite(P12);
@@ -72,11 +72,11 @@ __device__ __forceinline__ bool coll_half(const KParams& p, const double q[6], d
 
 // a, b, J, K of Eq. (flux-2D-1) (dir 1) / (flux-2D-2) (dir 2) for the Gaussian with moments q:
 // a = sqrt(2 th/pi) exp(-u^2/(2 th)), b = erf(u/sqrt(2 th)), th = P_nn/rho (the normal
-// temperature); written with one reciprocal of rho, one of P_nn and one reciprocal square root.
-__device__ __forceinline__ void abJK(const double q[6], int dir, double& a, double& b,
+// temperature); ir = 1/rho (from the caller, which has it already), one reciprocal of P_nn and
+// one reciprocal square root.
+__device__ __forceinline__ void abJK(const double q[6], double ir, int dir, double& a, double& b,
                                      double J[6], double K[6]) {
   const double rho = q[0];
-  const double ir = 1.0 / rho;
   const double u1 = q[1] * ir, u2 = q[2] * ir;
   const double P11 = q[3] - rho * u1 * u1;
   const double P12 = q[4] - rho * u1 * u2;
@@ -117,10 +117,10 @@ __device__ __forceinline__ void abJK(const double q[6], int dir, double& a, doub
   }
 }
 
-__device__ __forceinline__ void half_fluxes(const double q[6], int dir, double Fp[6],
+__device__ __forceinline__ void half_fluxes(const double q[6], double ir, int dir, double Fp[6],
                                             double Fm[6], double Kf[6]) {
   double a, b, J[6], K[6];
-  abJK(q, dir, a, b, J, K);
+  abJK(q, ir, dir, a, b, J, K);
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
     Fp[m] = 0.5 * (a * J[m] + (1.0 + b) * K[m]);
@@ -196,12 +196,26 @@ __device__ __forceinline__ void uT_of(const double* Q, int nc, int c, double& u1
   T = (P11 + P22) * (0.5 * ir);
 }
 
+// (u1, u2, T) of cell c into its per-cell fields (the values uT_of gives, bit for bit), so that
+// the prims of its neighbours read them instead of recomputing them.
+__device__ __forceinline__ void uT_body(const double* __restrict__ Q, double* __restrict__ prim,
+                                        int nc, int c) {
+  double u1, u2, T;
+  uT_of(Q, nc, c, u1, u2, T);
+  prim[P_U1 * nc + c] = u1;
+  prim[P_U2 * nc + c] = u2;
+  prim[P_T * nc + c] = T;
+}
+
 // (u1, u2, T) across side s of cell (i, j) for the centred differences of Eq. (5-97more): the
-// neighbour (periodic wrap), the cell itself (extrapolation; diffuse-wall cells do not use these
-// values), or the mirrored ghost (specular: normal velocity negated).
-__device__ __forceinline__ void side_uT(const double* Q, const KGrid& g, const KParams& p, int nc,
-                                        int i, int j, int s, double cu1, double cu2, double cT,
-                                        double& u1, double& u2, double& T) {
+// neighbour (periodic wrap; from its moments, or from its per-cell fields when FROM_PRIM), the
+// cell itself (extrapolation; diffuse-wall cells do not use these values), or the mirrored ghost
+// (specular: normal velocity negated).
+template <bool FROM_PRIM = false>
+__device__ __forceinline__ void side_uT(const double* Q, const double* prim, const KGrid& g,
+                                        const KParams& p, int nc, int i, int j, int s, double cu1,
+                                        double cu2, double cT, double& u1, double& u2,
+                                        double& T) {
   int ni = i + (s == 0 ? -1 : s == 1 ? 1 : 0);
   int nj = j + (s == 2 ? -1 : s == 3 ? 1 : 0);
   bool inside = ni >= 0 && ni < g.nx && nj >= 0 && nj < g.ny;
@@ -211,7 +225,14 @@ __device__ __forceinline__ void side_uT(const double* Q, const KGrid& g, const K
     inside = true;
   }
   if (inside) {
-    uT_of(Q, nc, nj * g.nx + ni, u1, u2, T);
+    const int n = nj * g.nx + ni;
+    if (FROM_PRIM) {
+      u1 = prim[P_U1 * nc + n];
+      u2 = prim[P_U2 * nc + n];
+      T = prim[P_T * nc + n];
+    } else {
+      uT_of(Q, nc, n, u1, u2, T);
+    }
   } else if (p.bc[s] == MM_BC_SPECULAR) {
     u1 = s < 2 ? -cu1 : cu1;
     u2 = s < 2 ? cu2 : -cu2;
@@ -223,18 +244,23 @@ __device__ __forceinline__ void side_uT(const double* Q, const KGrid& g, const K
   }
 }
 
+// Per-cell fields of cell c.  FROM_PRIM: the neighbours' (u1, u2, T) are already in prim (written
+// by uT_body over all cells); otherwise they are recomputed from Q.  ieps = 1/eps.
+template <bool FROM_PRIM = false>
 __device__ __forceinline__ void prims_body(const double* __restrict__ Q, double* __restrict__ prim,
                         float* __restrict__ primf, KGrid g, KParams p, double dt, double eps,
-                        int* __restrict__ err, int c) {
+                        double ieps, int* __restrict__ err, int c) {
   const int nc = g.nx * g.ny;
   const int i = c % g.nx, j = c / g.nx;
   const double rho = Q[c];
   const double ir = 1.0 / rho;
-  const double u1 = Q[nc + c] * ir, u2 = Q[2 * nc + c] * ir;
+  // the cell's own (u1, u2, T): as its neighbours see them
+  const double u1 = FROM_PRIM ? prim[P_U1 * nc + c] : Q[nc + c] * ir;
+  const double u2 = FROM_PRIM ? prim[P_U2 * nc + c] : Q[2 * nc + c] * ir;
   const double P11 = Q[3 * nc + c] - rho * u1 * u1;
   const double P12 = Q[4 * nc + c] - rho * u1 * u2;
   const double P22 = Q[5 * nc + c] - rho * u2 * u2;
-  const double T = (P11 + P22) * (0.5 * ir);
+  const double T = FROM_PRIM ? prim[P_T * nc + c] : (P11 + P22) * (0.5 * ir);
   const double nu = p.nu;
   const double t11 = P11 * ir, t12 = P12 * ir, t22 = P22 * ir;
   const double s11 = (1.0 - nu) * T + nu * t11;
@@ -249,9 +275,11 @@ __device__ __forceinline__ void prims_body(const double* __restrict__ Q, double*
   const double idet = 1.0 / det;
   const double KG = rho * kInv2Pi * rsqrt(det);
   prim[P_RHO * nc + c] = rho;
-  prim[P_U1 * nc + c] = u1;
-  prim[P_U2 * nc + c] = u2;
-  prim[P_T * nc + c] = T;
+  if (!FROM_PRIM) {  // else already there, read by the neighbours
+    prim[P_U1 * nc + c] = u1;
+    prim[P_U2 * nc + c] = u2;
+    prim[P_T * nc + c] = T;
+  }
   prim[P_TAU * nc + c] = tau;
   prim[P_TI11 * nc + c] = s22 * idet;
   prim[P_TI12 * nc + c] = -s12 * idet;
@@ -262,10 +290,10 @@ __device__ __forceinline__ void prims_body(const double* __restrict__ Q, double*
 
   // discrete strain and temperature gradient, Eqs. (5-97), (5-97more)
   double uL1, uL2, TL, uR1, uR2, TR, uB1, uB2, TB, uT1, uT2, TT;
-  side_uT(Q, g, p, nc, i, j, 0, u1, u2, T, uL1, uL2, TL);
-  side_uT(Q, g, p, nc, i, j, 1, u1, u2, T, uR1, uR2, TR);
-  side_uT(Q, g, p, nc, i, j, 2, u1, u2, T, uB1, uB2, TB);
-  side_uT(Q, g, p, nc, i, j, 3, u1, u2, T, uT1, uT2, TT);
+  side_uT<FROM_PRIM>(Q, prim, g, p, nc, i, j, 0, u1, u2, T, uL1, uL2, TL);
+  side_uT<FROM_PRIM>(Q, prim, g, p, nc, i, j, 1, u1, u2, T, uR1, uR2, TR);
+  side_uT<FROM_PRIM>(Q, prim, g, p, nc, i, j, 2, u1, u2, T, uB1, uB2, TB);
+  side_uT<FROM_PRIM>(Q, prim, g, p, nc, i, j, 3, u1, u2, T, uT1, uT2, TT);
   const double dTdx = (0.5 * (TR + T) - 0.5 * (T + TL)) * g.idx;
   const double dTdy = (0.5 * (TT + T) - 0.5 * (T + TB)) * g.idy;
   const double Dxu1 = (uR1 - uL1) * 0.5, Dxu2 = (uR2 - uL2) * 0.5;
@@ -280,7 +308,6 @@ __device__ __forceinline__ void prims_body(const double* __restrict__ Q, double*
   const double om2 = dt * tau * iden;
   const double mu = rho * kInv2Pi * iT;
   const double wt = dt * iden * mu;  // om2 mu / tau
-  const double ieps = 1.0 / eps;
   const double h2T2 = 0.5 * iT * iT;
   const double gam0 = om2 * ieps * KG;
   const double ome = om2 * mu * ieps;
@@ -327,7 +354,7 @@ __device__ __forceinline__ void boundary_face(const KParams& p, const double qc[
   double gq[6], Gp[6], Gm[6], GK[6];
   if (p.bc[s] == MM_BC_SPECULAR) mirror_q(qc, dir, gq);
   else wall_ghost(p, qc, s, gq);
-  half_fluxes(gq, dir, Gp, Gm, GK);
+  half_fluxes(gq, 1.0 / gq[0], dir, Gp, Gm, GK);
   const bool low = s == 0 || s == 2;  // the ghost is the left / bottom state
   for (int m = 0; m < 6; ++m) F[m] = low ? Gp[m] + Fm[m] : Fp[m] + Gm[m];
 }
@@ -340,9 +367,10 @@ __device__ __forceinline__ void macro_x1_body(const double* __restrict__ Qn, Mac
   const int i = c % g.nx, j = c / g.nx;
   double q[6], qs[6];
   load_q(Qn, nc, c, q);
-  const bool ok = coll_half(p, q, eps, dt, qs);
+  double ir;  // 1/rho: the collision half step leaves rho unchanged
+  const bool ok = coll_half(p, q, eps, dt, qs, ir);
   double Fp[6], Fm[6], K[6];
-  half_fluxes(qs, 1, Fp, Fm, K);
+  half_fluxes(qs, ir, 1, Fp, Fm, K);
   for (int m = 0; m < 6; ++m) {
     mb.Q1[m * nc + c] = qs[m];
     mb.FX[m * nc + c] = Fp[m];
@@ -393,10 +421,10 @@ __device__ __forceinline__ void macro_x2_body(const double* __restrict__ H, Macr
     q2[m] = v;
     mb.Q2[m * nc + c] = v;
   }
-  double r0, r1, r2, r3, r4, r5;
-  const bool ok = prim6(q2, r0, r1, r2, r3, r4, r5);
+  double r0, r1, r2, r3, r4, r5, ir;
+  const bool ok = prim6(q2, r0, r1, r2, r3, r4, r5, ir);
   double Fp[6], Fm[6], K[6];
-  half_fluxes(q2, 2, Fp, Fm, K);
+  half_fluxes(q2, ir, 2, Fp, Fm, K);
   for (int m = 0; m < 6; ++m) {
     mb.FY[m * nc + c] = Fp[m];
     mb.FY[(6 + m) * nc + c] = Fm[m];
@@ -450,8 +478,8 @@ __device__ __forceinline__ void macro_y_body(const double* __restrict__ H, Macro
   // optional source between the y transport and the collision half step (Eq. macro2d-split3b)
   if (srcq)
     for (int m = 0; m < 6; ++m) q3[m] = fma(dt, srcq[m * nc + c], q3[m]);
-  double o[6];
-  const bool ok = coll_half(p, q3, eps, dt, o);
+  double o[6], ir;
+  const bool ok = coll_half(p, q3, eps, dt, o, ir);
   for (int m = 0; m < 6; ++m) Qn[m * nc + c] = o[m];
   if (!ok) atomicOr(err, ERR_NONPHYS_MACRO);
 }

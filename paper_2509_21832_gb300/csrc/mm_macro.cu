@@ -16,11 +16,16 @@ namespace {
 
 using namespace macro_body;
 
+__global__ void k_prims_uT(const double* __restrict__ Q, double* __restrict__ prim, int nc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) uT_body(Q, prim, nc, c);
+}
+
 __global__ void k_prims(const double* __restrict__ Q, double* __restrict__ prim,
                         float* __restrict__ primf, KGrid g, KParams p, double dt, double eps,
-                        int* __restrict__ err) {
+                        double ieps, int* __restrict__ err) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < g.nx * g.ny) prims_body(Q, prim, primf, g, p, dt, eps, err, c);
+  if (c < g.nx * g.ny) prims_body<true>(Q, prim, primf, g, p, dt, eps, ieps, err, c);
 }
 
 __global__ void k_macro_x1(const double* __restrict__ Qn, MacroBufs mb, KGrid g, KParams p,
@@ -56,7 +61,9 @@ __global__ void k_h_unpack(const float* __restrict__ Hf, double* __restrict__ H,
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
                   double dt, double eps, int* err, cudaStream_t s) {
   const int nc = g.nx * g.ny;
-  k_prims<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, err);
+  // (u1, u2, T) of every cell first: each cell's prims then read those of its neighbours
+  k_prims_uT<<<(nc + 255) / 256, 256, 0, s>>>(Q, prim, nc);
+  k_prims<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, 1.0 / eps, err);
 }
 
 void launch_macro_x1(const double* Qn, const MacroBufs& mb, const KGrid& g, const KParams& p,
