@@ -18,11 +18,13 @@ namespace {
 const char* const kKernelNames[] = {
     "prims",    "micro_x",          "micro_y",   "micro_y_wall",   "macro_x1",
     "macro_x2", "macro_y",          "h_unpack",  "micro_fused",    "closure_features",
-    "mlp_infer", "closure_decide",  "closure_lists", "closure_ghat", "closure_predict"};
-constexpr int kNumKernels = 15;
+    "mlp_infer", "closure_decide",  "closure_lists", "closure_ghat", "closure_predict",
+    "prims_uT"};
+constexpr int kNumKernels = 16;
 enum {
   T_PRIMS = 0, T_MICRO_X, T_MICRO_Y, T_MICRO_YW, T_MACRO_X1, T_MACRO_X2, T_MACRO_Y, T_HUNPACK,
-  T_MICRO_FUSED, T_CL_FEATURES, T_MLP, T_CL_DECIDE, T_CL_LISTS, T_CL_GHAT, T_CL_PREDICT
+  T_MICRO_FUSED, T_CL_FEATURES, T_MLP, T_CL_DECIDE, T_CL_LISTS, T_CL_GHAT, T_CL_PREDICT,
+  T_PRIMS_UT
 };
 
 struct TimedLaunch {
@@ -181,6 +183,14 @@ void timed(mm_ctx* c, int kind, F&& launch) {
   c->pending.push_back(t);
 }
 
+// The per-cell fields of Q^n (two kernels, each timed).
+void enqueue_prims(mm_ctx* c, double dt, double eps, cudaStream_t s) {
+  timed(c, T_PRIMS_UT, [&] { launch_prims_uT(c->Q, c->prim, c->kg, s); });
+  timed(c, T_PRIMS, [&] {
+    launch_prims(c->Q, c->prim, c->primf, c->kg, c->kp, dt, eps, c->err, s);
+  });
+}
+
 mm_status check_device_errors(mm_ctx* c) {
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -205,7 +215,7 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   const KGrid& g = c->kg;
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
-  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
+  enqueue_prims(c, dt, eps, s);
   const double* srcg = nullptr;
   const double* srcq = nullptr;
   if constexpr (sizeof(Tg) == sizeof(double)) {
@@ -263,7 +273,7 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
   const int nc = (int)c->ncell;
-  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
+  enqueue_prims(c, dt, eps, s);
   timed(c, T_CL_PREDICT, [&] {
     launch_closure_predict(c->Q, c->prim, c->mlp, g, p, eps, dt, c->closure_thr, c->cflags, c->H,
                            c->caux, c->cstat, s);
@@ -355,7 +365,7 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
   if (e != cudaSuccess) return cuda_fail(c, e, "copy state in");
   c->cstale = false;
   c->have_state = true;
-  timed(c, T_PRIMS, [&] { launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, s); });
+  enqueue_prims(c, dt, eps, s);
   cudaEventRecord(fields, s);
   cudaStreamWaitEvent(c->xstream, fields, 0);
   for (int r = 0; r < nchunk; ++r) {
@@ -822,7 +832,7 @@ mm_status mm_closure_features(mm_ctx* c, double dt, double eps, float* X_dev, do
   if (!X_dev || !aux_dev) return fail(c, MM_ERR_INVALID_ARG, "null output");
   if (!(dt > 0.0) || !(eps > 0.0)) return fail(c, MM_ERR_INVALID_ARG, "dt and eps must be > 0");
   if (!c->have_state) return fail(c, MM_ERR_STATE, "no state set");
-  launch_prims(c->Q, c->prim, c->primf, c->kg, c->kp, dt, eps, c->err, c->stream);
+  enqueue_prims(c, dt, eps, c->stream);
   launch_closure_features(c->Q, c->prim, c->kg, c->kp, eps, dt, X_dev, aux_dev, c->stream);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "closure features");
@@ -836,7 +846,7 @@ mm_status mm_closure_collect(mm_ctx* c, double dt, double eps, float* X_dev, flo
   if (!c->have_state) return fail(c, MM_ERR_STATE, "no state set");
   mm_status st = ensure_closure(c);
   if (st != MM_OK) return st;
-  launch_prims(c->Q, c->prim, c->primf, c->kg, c->kp, dt, eps, c->err, c->stream);
+  enqueue_prims(c, dt, eps, c->stream);
   launch_closure_features(c->Q, c->prim, c->kg, c->kp, eps, dt, X_dev, c->caux, c->stream);
   if (c->fp32) enqueue_plain<float>(c, dt, eps);
   else enqueue_plain<double>(c, dt, eps);

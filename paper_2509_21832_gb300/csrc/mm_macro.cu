@@ -61,9 +61,12 @@ __global__ void k_h_unpack(const float* __restrict__ Hf, double* __restrict__ H,
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
                   double dt, double eps, int* err, cudaStream_t s) {
   const int nc = g.nx * g.ny;
-  // (u1, u2, T) of every cell first: each cell's prims then read those of its neighbours
-  k_prims_uT<<<(nc + 255) / 256, 256, 0, s>>>(Q, prim, nc);
   k_prims<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, 1.0 / eps, err);
+}
+
+void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s) {
+  const int nc = g.nx * g.ny;
+  k_prims_uT<<<(nc + 255) / 256, 256, 0, s>>>(Q, prim, nc);
 }
 
 void launch_macro_x1(const double* Qn, const MacroBufs& mb, const KGrid& g, const KParams& p,

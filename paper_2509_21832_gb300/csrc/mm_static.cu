@@ -156,6 +156,7 @@ extern "C" mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params
   if (n_wall > 0)
     k_wall_list<<<(int)((ncell + 127) / 128), 128, 0, s>>>(wall, count, kg, kp);
   for (int n = 0; n < nsteps; ++n) {
+    launch_prims_uT(Q_dev, prim, kg, s);
     launch_prims(Q_dev, prim, nullptr, kg, kp, dt, eps, err, s);
     launch_micro_x<double>(G_dev, Gs, prim, kg, kp, dt, ms, s);
     launch_micro_y<double>(Gs, G_dev, H_dev, prim, kg, kp, dt, eps, ms, err, s);
