@@ -37,6 +37,12 @@ CASES = [
     # wall kernel at the diffuse top wall
     ("walls_32", dict(nx=7, ny=9, nv1=32, nv2=32),
      (I.SPECULAR, I.DIFFUSE, I.EXTRAP, I.DIFFUSE), dict(wall_T=(1.0, 0.9, 1.0, 1.15))),
+    # grids smaller than a CTA's four columns: idle warps in the barriers, halo slots past the
+    # edge; one row (periodic y: the cell is its own y neighbour), one column
+    ("tiny_16", dict(nx=3, ny=2, nv1=16, nv2=16), (I.PERIODIC, I.PERIODIC, I.SPECULAR, I.SPECULAR), {}),
+    ("row_24", dict(nx=5, ny=1, nv1=24, nv2=24), (I.EXTRAP, I.SPECULAR, I.PERIODIC, I.PERIODIC), {}),
+    ("column_32", dict(nx=1, ny=6, nv1=32, nv2=32), (I.PERIODIC, I.PERIODIC, I.DIFFUSE, I.EXTRAP),
+     dict(wall_T=(1.0, 1.0, 1.1, 1.0))),
     # v2 mesh not symmetric about zero: the column-mapped kernel of the 24^2 shape
     ("asym_24", dict(nx=8, ny=9, nv1=24, nv2=24, v2min=-7.0, v2max=9.0),
      (I.EXTRAP, I.EXTRAP, I.PERIODIC, I.PERIODIC), {}),
