@@ -293,19 +293,21 @@ def closure_variant(args, stream):
     return out
 
 
-def batch_variant(args):
-    """64 independent periodic problems (cells per side U{64..256}, velocity meshes 16^2..32^2,
-    eps log-uniform on [1e-3, 1], seeded Fourier-mode fields), stepped as one batch: one
-    persistent launch per phase, the step replayed as a CUDA graph, autotuned CTA shape.  FP64.
-    Compared with stepping the same problems through separate single-problem contexts."""
+def batch_variant(args, count=None, nmin=64, nmax=256, steps=None):
+    """count independent periodic problems (cells per side U{nmin..nmax}, velocity meshes
+    16^2..32^2, eps log-uniform on [1e-3, 1], seeded Fourier-mode fields; by default the 64
+    problems of 64..256 cells per side), stepped as one batch: one persistent launch per phase,
+    the step replayed as a CUDA graph, autotuned CTA shape.  FP64.  Compared with stepping the
+    same problems through separate single-problem contexts, one after the other."""
     import torch
     from paper_2509_21832_gb300 import api
     from paper_2509_21832_gb300 import inputs as I
-    probs = I.batch_problems(count=args.batch_count, seed=0)
+    count = args.batch_count if count is None else count
+    probs = I.batch_problems(count=count, seed=0, nmin=nmin, nmax=nmax)
     nph = sum(p.grid.nphase for p in probs)
     dts = [p.dt for p in probs]
     epss = [p.eps for p in probs]
-    steps = args.batch_steps
+    steps = args.batch_steps if steps is None else steps
     b = api.BatchSolver([p.grid for p in probs], [p.params for p in probs])
     for q, p in enumerate(probs):
         b.set_state(q, p.Q, None)
@@ -338,7 +340,8 @@ def batch_variant(args):
     tsep = (time.perf_counter() - t0) / n_sep
     for s_ in ss:
         s_.close()
-    return {"workload": "batch_%d_periodic_problems" % len(probs), "phase_cells": nph,
+    return {"workload": "batch_%d_periodic_problems_%d_to_%d_cells_per_side"
+                        % (len(probs), nmin, nmax), "phase_cells": nph,
             "steps": steps, "dtype": "f64", "value": nph * steps / tb, "unit": UNIT,
             "ms_per_step": 1e3 * tb / steps, "autotuned": {"threads": threads, "ctas": ctas},
             "separate_contexts_ms_per_step": 1e3 * tsep,
@@ -380,6 +383,7 @@ def main():
         import torch
         torch.cuda.set_device(local)
         print(json.dumps(batch_variant(args)), flush=True)
+        print(json.dumps(batch_variant(args, count=256, nmin=16, nmax=48, steps=50)), flush=True)
         return
     if args.variant_only:
         import torch
@@ -503,6 +507,9 @@ def main():
     if rank == 0 and not args.no_variants:
         variants = {"riemann4_diffuse_1024x1024x24x24_fp32g": fp32_variant(args, stream),
                     "batch_64_periodic_fp64": batch_variant(args),
+                    # where batching matters: many problems too small to fill the GPU alone
+                    "batch_256_small_periodic_fp64": batch_variant(args, count=256, nmin=16,
+                                                                   nmax=48, steps=50),
                     "bump_specular_512x512x32x32_learned_closure": closure_variant(args, stream)}
 
     if rank == 0:
