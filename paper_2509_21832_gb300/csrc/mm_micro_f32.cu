@@ -8,6 +8,13 @@
 // computed in FP64 and rounded once; velocity sums are FP32 (per-lane partial sums over its
 // rows, then a pairwise warp butterfly); the heat flux leaves as (hi, lo) FP32 pairs (lo = 0
 // here) that the per-cell unpack kernel turns into FP64.
+//
+// Three kernels stream the same arithmetic, chosen on the host (pick_fused):
+//  - k_micro_staged_f32 (24^2 and 16^2 meshes symmetric in v2): flat lane mapping, the four
+//    warps of a CTA march four adjacent columns in step, g blocks staged by bulk copies;
+//  - k_micro_flat_f32 (32^2, symmetric in v2): flat lane mapping, one warp per column, g through
+//    the read-only path;
+//  - k_micro_fused_f32 (any mesh with nv1 <= 32): lane = v1 index, one warp per column.
 #include <cmath>
 #include <cstdint>
 
