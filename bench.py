@@ -30,10 +30,12 @@ METRIC = "phase-space updates/s & %HBM roofline; mixed/learned vs FP64 at set L1
 UNIT = "phase-cell updates/s"
 # Algorithmic FP64 flops per phase cell of the dominant kernel (y sweep 13, Ghat and blend 15,
 # heat-flux moments 8, Maxwellian/Gaussian from separable tables 3) and of the whole step
-# (plus the x sweep, 13); algorithmic bytes per phase cell and step: one read and one write of
-# g in FP64 plus the per-cell macro fields (6 + 6 + 4 + 4 doubles over nv = 1024 velocities).
+# (plus the x sweep, 7: the upwind difference, the upwind update and the two projection terms;
+# its velocity moments come from row sums of g left by the previous y sweep); algorithmic bytes
+# per phase cell and step: one read and one write of g in FP64 plus the per-cell macro fields
+# (6 + 6 + 4 + 4 doubles over nv = 1024 velocities).
 FLOPS_MICRO_Y = 39.0
-FLOPS_STEP = 52.0
+FLOPS_STEP = 46.0
 BYTES_PER_PHASE_FP64 = 16.0 + 160.0 / 1024.0
 # DRAM traffic of k_micro_y per phase cell (32^2 velocity meshes), from an ncu capture of the
 # 160^2 x 32^2 bump case: (213.9 MB read + 172.9 MB written) / 26.2144 M phase cells.

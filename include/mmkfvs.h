@@ -114,9 +114,12 @@ mm_status mm_sync(mm_ctx* ctx);
 /* Copy Q (and H unless H_host is NULL) to host memory; synchronises the stream. */
 mm_status mm_get_moments(mm_ctx* ctx, double* Q_host, double* H_host);
 
-/* One time step from host state to host moments: the same result, bit for bit, as
+/* One time step from host state to host moments: the result of
  * mm_set_state(c, Q_host, G_host); mm_step(c, dt, eps, 1); mm_get_moments(c, Q_out, H_out), with
- * the host-to-device copy of G_host overlapped with the step.  For plain FP64 contexts g is
+ * the host-to-device copy of G_host overlapped with the step (equal to rounding, relative 1e-13:
+ * the x sweep sums its velocity moments per velocity here, from row sums of g in mm_step, so the
+ * two differ in the order of additions; bitwise where the velocity mesh has no row sums, i.e.
+ * nv1 <= 16 or nv1 > 32).  For plain FP64 contexts g is
  * copied in row chunks on a second stream and the micro sweeps of each chunk start as soon as
  * its rows (and those of its upper neighbour) are on the device; FP32-g, learned-closure and
  * manufactured-solution contexts run the three calls in sequence.  Q_host [6][ny][nx] and

@@ -55,6 +55,9 @@ struct mm_ctx {
   float* Hf = nullptr;      // FP32-g heat flux as (hi, lo) pairs
   double* prim = nullptr;
   float* primf = nullptr;  // FP32 copies of the per-cell coefficients (FP32-g path)
+  // FP64 with one row per pass: raw row sums of G [cell][3][nv1], kept current with G (left by
+  // the y sweeps, formed whenever G is set otherwise) for the x sweep
+  double* rmom = nullptr;
   int* err = nullptr;
   int* wall_cells = nullptr;
   int n_wall = 0;
@@ -231,6 +234,8 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
       launch_closure_stale(c->cvalid, g, c->clists + 2 * nc, c->ccounts + 2, s);
       launch_closure_ghat(G, c->prim, g, dt, eps, c->ms, c->clists + 2 * nc, c->ccounts + 2,
                           c->blocks_g, s);
+      if (c->rmom)  // those cells' g changed: their row sums too
+        launch_row_sums_list(G, c->rmom, g, c->clists + 2 * nc, c->ccounts + 2, c->blocks_g, s);
       c->cstale = false;
     }
   }
@@ -248,14 +253,22 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
       });
     std::swap(c->G, c->Gs);
   } else {
-    timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
+    // the x sweep from the row sums of G (left by the previous y sweep, or formed when G was
+    // set), for one row per pass
+    if (c->rmom)
+      timed(c, T_MICRO_X, [&] {
+        launch_micro_x_rows<Tg>(G, Gs, c->prim, c->rmom, g, p, dt, c->ms, s);
+      });
+    else
+      timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
     timed(c, T_MICRO_Y, [&] {
-      launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, srcg);
+      launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, srcg, 0, -1,
+                         c->rmom);
     });
     if (c->n_wall > 0)
       timed(c, T_MICRO_YW, [&] {
         launch_micro_y_wall<Tg>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
-                                c->ms, c->err, s);
+                                c->ms, c->err, s, c->rmom);
       });
   }
   timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
@@ -285,18 +298,21 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
     launch_closure_ghat(G, c->prim, g, dt, eps, c->ms, c->clists + 2 * nc, c->ccounts + 2,
                         c->blocks_g, s);
   });
+  // the refreshed cells' new g needs new row sums (closure cells keep g and their sums)
+  if (c->rmom)
+    launch_row_sums_list(G, c->rmom, g, c->clists + 2 * nc, c->ccounts + 2, c->blocks_g, s);
   timed(c, T_MICRO_X, [&] {
     launch_micro_x_list<double>(G, Gs, c->prim, g, p, dt, c->ms, c->clists, c->ccounts,
-                                c->blocks_x, s);
+                                c->blocks_x, s, c->rmom);
   });
   timed(c, T_MICRO_Y, [&] {
     launch_micro_y_list<double>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err,
-                                c->clists + nc, c->ccounts + 1, c->blocks_y, s);
+                                c->clists + nc, c->ccounts + 1, c->blocks_y, s, c->rmom);
   });
   if (c->n_wall > 0)
     timed(c, T_MICRO_YW, [&] {
       launch_micro_y_wall<double>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
-                                  c->ms, c->err, s);
+                                  c->ms, c->err, s, c->rmom);
     });
   timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
   timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
@@ -370,15 +386,17 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
   cudaStreamWaitEvent(c->xstream, fields, 0);
   for (int r = 0; r < nchunk; ++r) {
     cudaStreamWaitEvent(c->xstream, copied[r], 0);
-    launch_micro_x<double>(G, Gs, c->prim, g, p, dt, c->ms, c->xstream, row0(r) * g.nx,
-                           (row0(r + 1) - row0(r)) * g.nx);
+    // the x sweep sums its moments per velocity here (g has just arrived, without row sums);
+    // the y sweeps leave the row sums of G^{n+1} for the steps that follow
+    const int c0 = row0(r) * g.nx, cn = (row0(r + 1) - row0(r)) * g.nx;
+    launch_micro_x<double>(G, Gs, c->prim, g, p, dt, c->ms, c->xstream, c0, cn);
     cudaEventRecord(xswept[r], c->xstream);
   }
   auto ysweep = [&](int r, int after) {
     cudaStreamWaitEvent(s, xswept[after], 0);
     timed(c, T_MICRO_Y, [&] {
       launch_micro_y<double>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, nullptr,
-                             row0(r) * g.nx, (row0(r + 1) - row0(r)) * g.nx);
+                             row0(r) * g.nx, (row0(r + 1) - row0(r)) * g.nx, c->rmom);
     });
   };
   // x sweeps complete in chunk order, so waiting for chunk r+1 covers chunks 0..r+1
@@ -388,7 +406,7 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
   if (c->n_wall > 0)
     timed(c, T_MICRO_YW, [&] {
       launch_micro_y_wall<double>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
-                                  c->ms, c->err, s);
+                                  c->ms, c->err, s, c->rmom);
     });
   timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
   timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
@@ -494,8 +512,13 @@ size_t mm_device_bytes(const mm_grid* g, const mm_params* p) {
   const size_t pf = p->precision == MM_PREC_G_FP32
                         ? (NPRIMF + 8) * nc * sizeof(float) + (diff ? np * sizeof(float) : 0)
                         : 0;
+  const MicroShape ms = micro_shape(g->nv1, g->nv2);
+  const size_t rows = p->precision == MM_PREC_FP64 && ms.R == 1 && ms.threads == 32
+                          ? 3 * nc * (size_t)g->nv1 * sizeof(double)
+                          : 0;
   return 2 * np * gs + (6 + 4 + NPRIM) * nc * sizeof(double) +
-         macro_doubles(g->nx, g->ny) * sizeof(double) + pf + sizeof(int) + nwall * sizeof(int);
+         macro_doubles(g->nx, g->ny) * sizeof(double) + pf + sizeof(int) + nwall * sizeof(int) +
+         rows;
 }
 
 mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
@@ -553,6 +576,9 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
   if (c->fp32 && any_diffuse) alloc(&c->Gexp, c->nphase * gsz);
   alloc((void**)&c->prim, NPRIM * c->ncell * sizeof(double));
   if (c->fp32) alloc((void**)&c->primf, NPRIMF * c->ncell * sizeof(float));
+  // row sums for the FP64 sweeps that run one warp per cell with one row per pass
+  if (!c->fp32 && c->ms.R == 1 && c->ms.threads == 32)
+    alloc((void**)&c->rmom, 3 * c->ncell * grid->nv1 * sizeof(double));
   alloc((void**)&c->err, sizeof(int));
   std::vector<int> walls;
   for (int j = 0; j < grid->ny; ++j)
@@ -600,6 +626,7 @@ mm_status mm_set_state(mm_ctx* c, const double* Q_host, const double* G_host) {
     if (e != cudaSuccess) return cuda_fail(c, e, "reset closure validity");
     c->cstale = false;
   }
+  if (c->rmom) launch_row_sums(static_cast<const double*>(c->G), c->rmom, c->kg, c->stream);
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set state");
   c->have_state = true;
@@ -624,6 +651,7 @@ mm_status mm_set_state_device(mm_ctx* c, const double* Q_dev, const double* G_de
     if (e != cudaSuccess) return cuda_fail(c, e, "reset closure validity");
     c->cstale = false;
   }
+  if (c->rmom) launch_row_sums(static_cast<const double*>(c->G), c->rmom, c->kg, c->stream);
   c->have_state = true;
   return MM_OK;
 }
@@ -772,6 +800,7 @@ mm_status mm_mms_set_exact(mm_ctx* c, double t, double eps) {
   if (st != MM_OK) return st;
   launch_mms_exact(c->Q, static_cast<double*>(c->G), c->mms_phi, c->kg, c->kp, t, eps,
                    c->grid.x0, c->grid.y0, c->stream);
+  if (c->rmom) launch_row_sums(static_cast<const double*>(c->G), c->rmom, c->kg, c->stream);
   if (c->cvalid) cudaMemsetAsync(c->cvalid, 1, c->ncell, c->stream);
   c->cstale = false;
   cudaError_t e = cudaGetLastError();
@@ -928,6 +957,7 @@ void mm_destroy(mm_ctx* c) {
   cudaFree(c->Hf);
   cudaFree(c->prim);
   cudaFree(c->primf);
+  cudaFree(c->rmom);
   cudaFree(c->err);
   cudaFree(c->wall_cells);
   cudaFree(c->cX);

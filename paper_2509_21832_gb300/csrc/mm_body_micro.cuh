@@ -88,6 +88,50 @@ __device__ __forceinline__ bool diffuse_wall_cell(const KGrid& g, const KParams&
          (j == 0 && p.bc[2] == MM_BC_DIFFUSE) || (j == g.ny - 1 && p.bc[3] == MM_BC_DIFFUSE);
 }
 
+// Raw row sums of the velocity column k of a cell's g block: Rm[(cell * 3 + j) * nv1 + k] =
+// sum_l v2(l)^j g(k, l), j = 0, 1, 2, accumulated over l in ascending order as
+// R0 += g, R1 = fma(v2, g, R1), R2 = fma(v2 v2, g, R2) with v2 = fma(l + 1/2, dv2, v2min): the y
+// sweep leaves them for G^{n+1} (they also give its heat-flux sums), row_sums_body forms them
+// for any g in exactly the same way, and the next x sweep takes the moments of its upwind
+// differences from two cells' sums instead of from every velocity.  Only for one row per pass
+// (R = 1: the thread of column k holds all its rows).
+__device__ __forceinline__ void store_row_sums(double* __restrict__ Rm, int cell, int nv1, int k,
+                                               double R0, double R1, double R2) {
+  double* o = Rm + (size_t)cell * 3 * nv1 + k;
+  o[0] = R0;
+  o[nv1] = R1;
+  o[2 * nv1] = R2;
+}
+
+// The row sums of cell `cell` of G (blockDim >= nv1; thread k = column k).
+template <typename Tg>
+__device__ __forceinline__ void row_sums_body(const Tg* __restrict__ G, double* __restrict__ Rm,
+                                              const KGrid& g, int cell) {
+  const int nv1 = g.nv1, nv2 = g.nv2;
+  const int k = threadIdx.x;
+  if (k >= nv1) return;
+  const Tg* Gc = G + (size_t)cell * nv1 * nv2 + k;
+  double R0 = 0.0, R1 = 0.0, R2 = 0.0;
+  for (int l = 0; l < nv2; ++l) {
+    const double v2 = fma(l + 0.5, g.dv2, g.v2min);
+    const double v2q = v2 * v2;
+    const double ov = (double)Gc[l * nv1];
+    R0 += ov;
+    R1 = fma(v2, ov, R1);
+    R2 = fma(v2q, ov, R2);
+  }
+  store_row_sums(Rm, cell, nv1, k, R0, R1, R2);
+}
+
+// Central heat-flux sums sum_l c2^j g (c2 = v2 - u2, j = 0..3) from the raw sums R_j.
+__device__ __forceinline__ void central_sums(double u2, double R0, double R1, double R2, double R3,
+                                             double& H0, double& H1, double& H2, double& H3) {
+  H0 = R0;
+  H1 = fma(-u2, R0, R1);
+  H2 = fma(u2, fma(u2, R0, -2.0 * R1), R2);
+  H3 = fma(u2, fma(u2, fma(-u2, R0, 3.0 * R1), -3.0 * R2), R3);
+}
+
 // ------------------------------------------------------------------------------------------
 // x sweep: Eqs. (zmicrox), (coeffs-2D-xdir), (zhat-2D-xdir), (update-micro-2D-xdir)
 // ------------------------------------------------------------------------------------------
@@ -203,6 +247,92 @@ __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
   }
 }
 
+// x sweep with the moments of Z from the row sums Rm of G^n (one row per pass, R = 1): with
+// d = G_up - G of column k, sum_l c2^j d for j = 0, 1, 2 follows from the differences of the two
+// cells' raw sums (c2 = v2 - u2), so one pass over the velocities forms
+// G* = G + lam d + ak e2 + bk qet (Eq. update-micro-2D-xdir) without accumulating per velocity.
+template <typename Tg>
+__device__ __forceinline__ void micro_x_rows_body(const Tg* __restrict__ Gin,
+                                                  Tg* __restrict__ Gout,
+                                                  const double* __restrict__ prim,
+                                                  const double* __restrict__ Rm, KGrid g,
+                                                  KParams p, double dtidx, int cell, double* sm) {
+  const int nv1 = g.nv1, nv2 = g.nv2;
+  double* red = sm;
+  double* c2t = sm + kRed;
+  double* c2q = c2t + nv2;
+  double* e2t = c2q + nv2;
+  double* qet = e2t + nv2;
+
+  const int nc = g.nx * g.ny;
+  const int i = cell % g.nx, j = cell / g.nx;
+  const int t = threadIdx.x;
+  const int k = t % nv1;
+  const bool active = t < nv1;
+
+  const double u1 = prim[P_U1 * nc + cell], u2 = prim[P_U2 * nc + cell];
+  const double inv2T = prim[P_INV2T * nc + cell], iT = prim[P_IT * nc + cell];
+  const double kap = prim[P_KAP * nc + cell];
+
+  for (int l = t; l < nv2; l += blockDim.x) {
+    const double c2 = fma(l + 0.5, g.dv2, g.v2min) - u2;
+    const double q = c2 * c2;
+    c2t[l] = c2;
+    c2q[l] = q;
+    e2t[l] = expd(-q * inv2T);
+  }
+
+  const double v1 = fma(k + 0.5, g.dv1, g.v1min);
+  const double c1 = v1 - u1;
+  const double av = fabs(v1);
+  const double sig = -av * g.idx;
+  const double lam = av * dtidx;
+  const Upwind up = upwind_x(g, p, i, j, v1 > 0.0 ? 0 : 1);
+  const int ku = up.mirror ? nv1 - 1 - k : k;
+  const size_t nv = (size_t)nv1 * nv2;
+  const Tg* Gc = Gin + (size_t)cell * nv + k;
+  const Tg* Gu = Gin + (size_t)up.cell * nv + ku;
+
+  // moments of the upwind differences: sum_l (1, c2, c2^2) d from the raw sums
+  double D0 = 0.0, D1 = 0.0, D2 = 0.0;
+  if (active) {
+    const double* Ro = Rm + (size_t)cell * 3 * nv1 + k;
+    const double* Ru = Rm + (size_t)up.cell * 3 * nv1 + ku;
+    const double r0 = (up.zero ? 0.0 : Ru[0]) - Ro[0];
+    const double r1 = (up.zero ? 0.0 : Ru[nv1]) - Ro[nv1];
+    const double r2 = (up.zero ? 0.0 : Ru[2 * nv1]) - Ro[2 * nv1];
+    D0 = r0;
+    D1 = fma(-u2, r0, r1);
+    D2 = fma(u2, fma(u2, r0, -2.0 * r1), r2);
+  }
+  __syncthreads();
+  const double sD0 = sig * D0;
+  double S[4] = {sD0, c1 * sD0, sig * D1, fma(c1 * c1, sD0, sig * D2)};
+  block_sum4(S, red);
+
+  const double b0 = fma(-S[3], inv2T, 2.0 * S[0]);
+  const double b1 = S[1] * iT, b2 = S[2] * iT;
+  const double gm = fma(0.25 * S[3], iT * iT, -S[0] * inv2T);
+  for (int l = t; l < nv2; l += blockDim.x) qet[l] = e2t[l] * fma(b2, c2t[l], gm * c2q[l]);
+  const double e1 = expd(-c1 * c1 * inv2T);
+  const double bk = kap * e1;
+  const double ak = bk * fma(gm * c1, c1, fma(b1, c1, b0));
+  __syncthreads();
+
+  // the single pass: G* = G - dt Z + dt Zhat
+  if (active) {
+    Tg* Go = Gout + (size_t)cell * nv + k;
+    for (int l = 0; l < nv2; ++l) {
+      const double gv = (double)Gc[l * nv1];
+      const double gu = up.zero ? 0.0 : (double)Gu[l * nv1];
+      double o = fma(lam, gu - gv, gv);
+      o = fma(ak, e2t[l], o);
+      o = fma(bk, qet[l], o);
+      Go[l * nv1] = (Tg)o;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // y sweep + relaxation + heat flux for cells not adjacent to a diffuse wall:
 // Eqs. (zmicroy)-(update-micro-2D-ydir), (5-97), (5-97more), (5-98), (5-99)
@@ -216,7 +346,8 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
                                                     const double* __restrict__ prim, KGrid g,
                                                     KParams p, double dtidy, double hscale, int R,
                                                     int* __restrict__ err, int cell, double* sm,
-                                                    const double* __restrict__ src = nullptr) {
+                                                    const double* __restrict__ src = nullptr,
+                                                    double* __restrict__ Rm = nullptr) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;
   const int i = cell % g.nx, j = cell / g.nx;
@@ -263,9 +394,9 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
       const double av = fabs(v2);
       const double sg = -av * g.idy;
       const double wl = om1 * (av * dtidy);
-      c2t[l] = c2;
-      c2q[l] = q;
-      c2c[l] = q * c2;
+      c2t[l] = v2;  // raw powers of v2 for the row sums (heat flux from central_sums)
+      c2q[l] = v2 * v2;
+      c2c[l] = v2 * v2 * v2;
       e2t[l] = e2;
       g2t[l] = expd(-0.5 * Ti22 * q);
       w2t[l] = om1 - wl;
@@ -335,7 +466,7 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
 
   // pass 2: G^{n+1} = om1 (G* - dt Z* + dt Zhat*) + om2 Ghat, and its heat-flux moments;
   // om1 G* - om1 dt Z* = wl G*_upwind + (om1 - wl) G*
-  double H0 = 0.0, H1 = 0.0, H2 = 0.0, H3 = 0.0;
+  double R0 = 0.0, R1 = 0.0, R2 = 0.0, R3 = 0.0;  // raw row sums of G^{n+1}
   // optional source term of g^{n+1} (same layout as G), e.g. the manufactured residual
   const double* Sc = src ? src + (size_t)cell * nv + k : nullptr;
   if (active) {
@@ -358,12 +489,15 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
       const Tg os = (Tg)o;
       Go[l * nv1] = os;
       const double ov = (double)os;
-      H0 += ov;
-      H1 = fma(c2t[l], ov, H1);
-      H2 = fma(c2q[l], ov, H2);
-      H3 = fma(c2c[l], ov, H3);
+      R0 += ov;
+      R1 = fma(c2t[l], ov, R1);
+      R2 = fma(c2q[l], ov, R2);
+      R3 = fma(c2c[l], ov, R3);
     }
+    if (Rm) store_row_sums(Rm, cell, nv1, k, R0, R1, R2);  // only with R = 1
   }
+  double H0, H1, H2, H3;
+  central_sums(u2, R0, R1, R2, R3, H0, H1, H2, H3);
   double Hs[4] = {c1q * c1 * H0, c1q * H1, c1 * H2, H3};
   block_sum4(Hs, red);
   if (t == 0) {
@@ -402,7 +536,8 @@ template <typename Tg>
 __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg* __restrict__ Gout,
                                double* __restrict__ Hout, const double* __restrict__ prim,
                                KGrid g, KParams p, double dt,
-                               double eps, int R, int* __restrict__ err, int cell, double* sm) {
+                               double eps, int R, int* __restrict__ err, int cell, double* sm,
+                               double* __restrict__ Rm = nullptr) {
   double* red = sm;
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;
@@ -571,7 +706,7 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
   double ex = p.keep_es ? KG * exp(-0.5 * Ti11 * c1 * c1 - Ti12 * c1 * c2r) : 0.0;
   const double rat = p.keep_es ? exp(-Ti12 * c1 * (R * g.dv2)) : 0.0;
 
-  double H0 = 0, H1 = 0, H2 = 0, H3 = 0;
+  double R0 = 0.0, R1 = 0.0, R2 = 0.0, R3 = 0.0;  // raw row sums of G^{n+1}
   if (active) {
     Tg* Go = Gout + (size_t)cell * nv + k;
     for (int l = r; l < nv2; l += R) {
@@ -598,12 +733,18 @@ __device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg*
       const Tg os = (Tg)o;
       Go[l * nv1] = os;
       const double ov = (double)os;
-      H0 += ov;
-      H1 += c2 * ov;
-      H2 += c2 * c2 * ov;
-      H3 += c2 * c2 * c2 * ov;
+      // the raw sums with v2 in the same form (and the same operations) as the other sweeps
+      const double v2r = fma(l + 0.5, g.dv2, g.v2min);
+      const double v2q = v2r * v2r;
+      R0 += ov;
+      R1 = fma(v2r, ov, R1);
+      R2 = fma(v2q, ov, R2);
+      R3 = fma(v2q * v2r, ov, R3);
     }
+    if (Rm) store_row_sums(Rm, cell, nv1, k, R0, R1, R2);  // only with R = 1
   }
+  double H0, H1, H2, H3;
+  central_sums(u2, R0, R1, R2, R3, H0, H1, H2, H3);
   double Hs[4] = {c1 * c1 * c1 * H0, c1 * c1 * H1, c1 * H2, H3};
   block_sum4(Hs, red);
   if (t == 0) {

@@ -82,15 +82,30 @@ void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s,
                     int cell0 = 0, int ncells = -1);
 // src (optional): a term added to g^{n+1} at every node, same layout as G
+// Rm (optional, used only with one row per pass, ms.R == 1): receives the raw row sums of
+// G^{n+1} [cell][3][nv1] for the next step's launch_micro_x_rows.
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
                     cudaStream_t s, const double* src = nullptr, int cell0 = 0,
-                    int ncells = -1);
+                    int ncells = -1, double* Rm = nullptr);
+// The x sweep from the row sums Rm of G^n left by the previous y sweep (needs ms.R == 1 and
+// every cell's sums current).
+template <typename Tg>
+void launch_micro_x_rows(const Tg* Gin, Tg* Gout, const double* prim, const double* Rm,
+                         const KGrid& g, const KParams& p, double dt, const MicroShape& ms,
+                         cudaStream_t s, int cell0 = 0, int ncells = -1);
+// The row sums of G for the cells [cell0, cell0 + ncells) (every cell for ncells < 0), or for a
+// list of cells: whenever G changes other than through a y sweep (needs ms.R == 1).
+void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s, int cell0 = 0,
+                     int ncells = -1);
+void launch_row_sums_list(const double* G, double* Rm, const KGrid& g, const int* list,
+                          const int* count, int blocks, cudaStream_t s);
 template <typename Tg>
 void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
-                         double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s);
+                         double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s,
+                         double* Rm = nullptr);
 // Fused FP32-g micro step (x sweep, y sweep, relaxation, heat flux) streaming over column
 // segments: reads Gin once and writes Gout (a different buffer); cells next to a diffuse wall are
 // left to the wall kernel, which reads the G* this kernel exports to Gexp.  One warp per cell
@@ -136,14 +151,17 @@ __host__ __device__ inline MacroBufs carve_macro(double* base, int nx, int ny) {
   return mb;
 }
 // Micro sweeps over a device-resident cell list (persistent CTAs; count read on the device).
+// Rm (optional, with ms.R == 1): the x sweep takes its moments from the row sums, the y sweep
+// leaves them for G^{n+1}.
 template <typename Tg>
 void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                          const KParams& p, double dt, const MicroShape& ms, const int* list,
-                         const int* count, int blocks, cudaStream_t s);
+                         const int* count, int blocks, cudaStream_t s, const double* Rm = nullptr);
 template <typename Tg>
 void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                          const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
-                         const int* list, const int* count, int blocks, cudaStream_t s);
+                         const int* list, const int* count, int blocks, cudaStream_t s,
+                         double* Rm = nullptr);
 int micro_list_blocks(const MicroShape& ms, bool ysweep);
 // Learned closure (FP64 path): features + Chapman-Enskog flux + scale (aux [5][ny][nx]),
 // training targets, decision, work lists [x | y | refresh][nc] with counts[3], Ghat write.

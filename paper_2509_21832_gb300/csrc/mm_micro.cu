@@ -31,16 +31,58 @@ __global__ void __launch_bounds__(NR > 0 ? 256 : 512, 1) k_micro_x(const Tg* __r
 }
 
 template <typename Tg>
+__global__ void __launch_bounds__(32) k_micro_x_rows(const Tg* __restrict__ Gin,
+                                                     Tg* __restrict__ Gout,
+                                                     const double* __restrict__ prim,
+                                                     const double* __restrict__ Rm, KGrid g,
+                                                     KParams p, double dtidx, int cell0) {
+  extern __shared__ double sm[];
+  micro_x_rows_body<Tg>(Gin, Gout, prim, Rm, g, p, dtidx, cell0 + (int)blockIdx.x, sm);
+}
+
+// The x sweep from the row sums over a list of cells (persistent CTAs of one warp).
+template <typename Tg>
+__global__ void __launch_bounds__(32) k_micro_x_rows_list(const Tg* __restrict__ Gin,
+                                                          Tg* __restrict__ Gout,
+                                                          const double* __restrict__ prim,
+                                                          const double* __restrict__ Rm,
+                                                          KGrid g, KParams p, double dtidx,
+                                                          const int* __restrict__ list,
+                                                          const int* __restrict__ count) {
+  extern __shared__ double sm[];
+  const int n = *count;
+  for (int q = blockIdx.x; q < n; q += gridDim.x) {
+    micro_x_rows_body<Tg>(Gin, Gout, prim, Rm, g, p, dtidx, list[q], sm);
+    __syncthreads();
+  }
+}
+
+// Row sums of the cells [cell0, cell0 + gridDim.x), or of a list of cells.
+__global__ void __launch_bounds__(32) k_row_sums(const double* __restrict__ G,
+                                                 double* __restrict__ Rm, KGrid g, int cell0) {
+  row_sums_body<double>(G, Rm, g, cell0 + (int)blockIdx.x);
+}
+
+__global__ void __launch_bounds__(32) k_row_sums_list(const double* __restrict__ G,
+                                                      double* __restrict__ Rm, KGrid g,
+                                                      const int* __restrict__ list,
+                                                      const int* __restrict__ count) {
+  const int n = *count;
+  for (int q = blockIdx.x; q < n; q += gridDim.x) row_sums_body<double>(G, Rm, g, list[q]);
+}
+
+template <typename Tg>
 __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs,
                                                     Tg* __restrict__ Gout,
                                                     double* __restrict__ Hout,
                                                     const double* __restrict__ prim, KGrid g,
                                                     KParams p, double dtidy, double hscale, int R,
                                                     int* __restrict__ err,
-                                                    const double* __restrict__ src, int cell0) {
+                                                    const double* __restrict__ src, int cell0,
+                                                    double* __restrict__ Rm) {
   extern __shared__ double sm[];
   micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, cell0 + (int)blockIdx.x, sm,
-                   src);
+                   src, Rm);
 }
 
 template <typename Tg>
@@ -50,9 +92,11 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_wall(const Tg* __restrict__ 
                                                          const double* __restrict__ prim,
                                                          const int* __restrict__ wall_cells,
                                                          KGrid g, KParams p, double dt, double eps,
-                                                         int R, int* __restrict__ err) {
+                                                         int R, int* __restrict__ err,
+                                                         double* __restrict__ Rm) {
   extern __shared__ double sm[];
-  micro_y_wall_body<Tg>(Gs, Gout, Hout, prim, g, p, dt, eps, R, err, wall_cells[blockIdx.x], sm);
+  micro_y_wall_body<Tg>(Gs, Gout, Hout, prim, g, p, dt, eps, R, err, wall_cells[blockIdx.x], sm,
+                        Rm);
 }
 
 // The same sweeps over a list of cells: persistent CTAs take cells q = blockIdx.x + m gridDim.x.
@@ -79,11 +123,13 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_list(const Tg* __restrict__ 
                                                          KParams p, double dtidy, double hscale,
                                                          int R, int* __restrict__ err,
                                                          const int* __restrict__ list,
-                                                         const int* __restrict__ count) {
+                                                         const int* __restrict__ count,
+                                                         double* __restrict__ Rm) {
   extern __shared__ double sm[];
   const int n = *count;
   for (int q = blockIdx.x; q < n; q += gridDim.x) {
-    micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, list[q], sm);
+    micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, list[q], sm, nullptr,
+                     Rm);
     __syncthreads();
   }
 }
@@ -196,7 +242,12 @@ int micro_list_blocks(const MicroShape& ms, bool ysweep) {
 template <typename Tg>
 void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                          const KParams& p, double dt, const MicroShape& ms, const int* list,
-                         const int* count, int blocks, cudaStream_t s) {
+                         const int* count, int blocks, cudaStream_t s, const double* Rm) {
+  if (Rm && ms.R == 1) {
+    k_micro_x_rows_list<Tg><<<blocks, 32, ms.smem_x, s>>>(Gin, Gout, prim, Rm, g, p,
+                                                          dt * g.idx, list, count);
+    return;
+  }
   with_x_list_kernel<Tg>(ms.xrows, [&](auto kern) {
     kern<<<blocks, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R, list,
                                               count);
@@ -206,19 +257,31 @@ void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGri
 template <typename Tg>
 void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                          const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
-                         const int* list, const int* count, int blocks, cudaStream_t s) {
+                         const int* list, const int* count, int blocks, cudaStream_t s,
+                         double* Rm) {
   k_micro_y_list<Tg><<<blocks, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
                                                            eps * g.dv1 * g.dv2, ms.R, err, list,
-                                                           count);
+                                                           count, ms.R == 1 ? Rm : nullptr);
+}
+
+void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s, int cell0,
+                     int ncells) {
+  const int n = ncells < 0 ? g.nx * g.ny : ncells;
+  if (n > 0) k_row_sums<<<n, 32, 0, s>>>(G, Rm, g, cell0);
+}
+
+void launch_row_sums_list(const double* G, double* Rm, const KGrid& g, const int* list,
+                          const int* count, int blocks, cudaStream_t s) {
+  k_row_sums_list<<<blocks, 32, 0, s>>>(G, Rm, g, list, count);
 }
 
 template void launch_micro_x_list<double>(const double*, double*, const double*, const KGrid&,
                                           const KParams&, double, const MicroShape&, const int*,
-                                          const int*, int, cudaStream_t);
+                                          const int*, int, cudaStream_t, const double*);
 template void launch_micro_y_list<double>(const double*, double*, double*, const double*,
                                           const KGrid&, const KParams&, double, double,
                                           const MicroShape&, int*, const int*, const int*, int,
-                                          cudaStream_t);
+                                          cudaStream_t, double*);
 
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
@@ -236,25 +299,39 @@ void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
-                    cudaStream_t s, const double* src, int cell0, int ncells) {
+                    cudaStream_t s, const double* src, int cell0, int ncells, double* Rm) {
   const int n = ncells < 0 ? g.nx * g.ny : ncells;
   if (n <= 0) return;
   if (ms.smem_y > 48 * 1024)
     cudaFuncSetAttribute(k_micro_y<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_y);
   k_micro_y<Tg><<<n, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
-                                                 eps * g.dv1 * g.dv2, ms.R, err, src, cell0);
+                                                 eps * g.dv1 * g.dv2, ms.R, err, src, cell0,
+                                                 ms.R == 1 ? Rm : nullptr);
+}
+
+template <typename Tg>
+void launch_micro_x_rows(const Tg* Gin, Tg* Gout, const double* prim, const double* Rm,
+                         const KGrid& g, const KParams& p, double dt, const MicroShape& ms,
+                         cudaStream_t s, int cell0, int ncells) {
+  const int n = ncells < 0 ? g.nx * g.ny : ncells;
+  if (n <= 0) return;
+  if (ms.smem_x > 48 * 1024)
+    cudaFuncSetAttribute(k_micro_x_rows<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ms.smem_x);
+  k_micro_x_rows<Tg><<<n, 32, ms.smem_x, s>>>(Gin, Gout, prim, Rm, g, p, dt * g.idx, cell0);
 }
 
 template <typename Tg>
 void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
-                         double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s) {
+                         double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s,
+                         double* Rm) {
   if (n_wall <= 0) return;
   const size_t smem = sizeof(double) * micro_body::wall_smem_doubles(g.nv1, g.nv2);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_micro_y_wall<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_micro_y_wall<Tg><<<n_wall, ms.threads, smem, s>>>(
-      Gs, Gout, H, prim, wall_cells, g, p, dt, eps, ms.R, err);
+      Gs, Gout, H, prim, wall_cells, g, p, dt, eps, ms.R, err, ms.R == 1 ? Rm : nullptr);
 }
 
 template void launch_micro_x<double>(const double*, double*, const double*, const KGrid&,
@@ -263,13 +340,16 @@ template void launch_micro_x<double>(const double*, double*, const double*, cons
 template void launch_micro_y<double>(const double*, double*, double*, const double*,
                                      const KGrid&, const KParams&, double, double,
                                      const MicroShape&, int*, cudaStream_t, const double*, int,
-                                     int);
+                                     int, double*);
+template void launch_micro_x_rows<double>(const double*, double*, const double*, const double*,
+                                          const KGrid&, const KParams&, double, const MicroShape&,
+                                          cudaStream_t, int, int);
 template void launch_micro_y_wall<double>(const double*, double*, double*, const double*,
                                           const int*, int, const KGrid&, const KParams&, double,
-                                          double, const MicroShape&, int*, cudaStream_t);
+                                          double, const MicroShape&, int*, cudaStream_t, double*);
 template void launch_micro_y_wall<float>(const float*, float*, double*, const double*,
                                          const int*, int, const KGrid&, const KParams&, double,
-                                         double, const MicroShape&, int*, cudaStream_t);
+                                         double, const MicroShape&, int*, cudaStream_t, double*);
 
 void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s) {
   k_diag_exp<<<152 * 4, 256, 0, s>>>(x, yf, yl, n);

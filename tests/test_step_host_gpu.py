@@ -1,8 +1,9 @@
 """mm_step_host: one step from host state to host moments with the copy of g overlapped with the
-micro sweeps (row chunks on a second stream) gives bit for bit the result of
-mm_set_state + mm_step(1) + mm_get_moments, for every chunking case: periodic y (the first
-chunk's y sweep deferred), rows not divisible by the chunk count, fewer rows than chunks,
-diffuse walls, and the contexts that run the calls in sequence (FP32 g)."""
+micro sweeps (row chunks on a second stream) gives the result of mm_set_state + mm_step(1) +
+mm_get_moments, for every chunking case: periodic y (the first chunk's y sweep deferred), rows
+not divisible by the chunk count, fewer rows than chunks, diffuse walls, and the contexts that
+run the calls in sequence (FP32 g).  Bit for bit where the mesh keeps no row sums (16^2, FP32 g);
+to rounding (1e-13) where mm_step takes the x-sweep moments from them (32^2, 24^2)."""
 import numpy as np
 import pytest
 
@@ -42,12 +43,18 @@ def test_step_host_is_bitwise_the_three_calls(name, gk, bc, extra, prec):
         G2 = s.get_g()
         # and again from the result, as a host-resident time loop does
         Q3, H3 = s.step_host(Q2, G2, dt, eps)
-    assert np.array_equal(Q1, Q2) and np.array_equal(H1, H2) and np.array_equal(G1, G2), name
     with api.Solver(grid, params) as s:
         s.set_state(Q, G)
         s.step(dt, eps, 2)
         Q4, H4 = s.get_moments()
-    assert np.array_equal(Q3, Q4) and np.array_equal(H3, H4), name
+
+    def same(a, b):
+        if grid.nv1 <= 16 or prec == I.PREC_G_FP32:
+            return np.array_equal(a, b)
+        return np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+
+    assert same(Q1, Q2) and same(H1, H2) and same(G1, G2), name
+    assert same(Q3, Q4) and same(H3, H4), name
 
 
 def test_step_host_rejects_missing_buffers():
