@@ -232,10 +232,9 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
     if (c->cstale) {  // after hybrid steps: g of closure cells to Ghat(Q^n) before a full step
       const int nc = (int)c->ncell;
       launch_closure_stale(c->cvalid, g, c->clists + 2 * nc, c->ccounts + 2, s);
+      // (with the row sums of the new g)
       launch_closure_ghat(G, c->prim, g, dt, eps, c->ms, c->clists + 2 * nc, c->ccounts + 2,
-                          c->blocks_g, s);
-      if (c->rmom)  // those cells' g changed: their row sums too
-        launch_row_sums_list(G, c->rmom, g, c->clists + 2 * nc, c->ccounts + 2, c->blocks_g, s);
+                          c->blocks_g, s, c->rmom);
       c->cstale = false;
     }
   }
@@ -294,13 +293,11 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   timed(c, T_CL_LISTS, [&] {
     launch_closure_lists(c->cflags, c->cvalid, g, p, c->clists, c->ccounts, s);
   });
+  // the refreshed cells' new g, with its row sums (closure cells keep g and their sums)
   timed(c, T_CL_GHAT, [&] {
     launch_closure_ghat(G, c->prim, g, dt, eps, c->ms, c->clists + 2 * nc, c->ccounts + 2,
-                        c->blocks_g, s);
+                        c->blocks_g, s, c->rmom);
   });
-  // the refreshed cells' new g needs new row sums (closure cells keep g and their sums)
-  if (c->rmom)
-    launch_row_sums_list(G, c->rmom, g, c->clists + 2 * nc, c->ccounts + 2, c->blocks_g, s);
   timed(c, T_MICRO_X, [&] {
     launch_micro_x_list<double>(G, Gs, c->prim, g, p, dt, c->ms, c->clists, c->ccounts,
                                 c->blocks_x, s, c->rmom);

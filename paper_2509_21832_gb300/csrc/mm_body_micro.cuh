@@ -112,13 +112,22 @@ __device__ __forceinline__ void row_sums_body(const Tg* __restrict__ G, double* 
   if (k >= nv1) return;
   const Tg* Gc = G + (size_t)cell * nv1 * nv2 + k;
   double R0 = 0.0, R1 = 0.0, R2 = 0.0;
-  for (int l = 0; l < nv2; ++l) {
-    const double v2 = fma(l + 0.5, g.dv2, g.v2min);
-    const double v2q = v2 * v2;
-    const double ov = (double)Gc[l * nv1];
-    R0 += ov;
-    R1 = fma(v2, ov, R1);
-    R2 = fma(v2q, ov, R2);
+  constexpr int kB = 8;  // loads issued ahead; the sums still run over l in ascending order
+  for (int l0 = 0; l0 < nv2; l0 += kB) {
+    double ov[kB];
+#pragma unroll
+    for (int m = 0; m < kB; ++m) ov[m] = l0 + m < nv2 ? (double)Gc[(l0 + m) * nv1] : 0.0;
+#pragma unroll
+    for (int m = 0; m < kB; ++m) {
+      const int l = l0 + m;
+      if (l < nv2) {
+        const double v2 = fma(l + 0.5, g.dv2, g.v2min);
+        const double v2q = v2 * v2;
+        R0 += ov[m];
+        R1 = fma(v2, ov[m], R1);
+        R2 = fma(v2q, ov[m], R2);
+      }
+    }
   }
   store_row_sums(Rm, cell, nv1, k, R0, R1, R2);
 }

@@ -294,7 +294,8 @@ __global__ void k_closure_stale(unsigned char* __restrict__ valid, int nc, int* 
 // Thread t owns v1 index k = t % nv1 and rows l = t / nv1 + m R, as in the micro kernels.
 __global__ void __launch_bounds__(512, 1)
     k_closure_ghat(double* __restrict__ G, const double* __restrict__ prim, KGrid g, double dt,
-                   double eps, int R, const int* __restrict__ list, const int* __restrict__ count) {
+                   double eps, int R, const int* __restrict__ list, const int* __restrict__ count,
+                   double* __restrict__ Rm) {
   extern __shared__ double sm[];
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;
@@ -346,6 +347,8 @@ __global__ void __launch_bounds__(512, 1)
     __syncthreads();
     if (active) {
       double* Go = G + (size_t)cell * nv + k;
+      // with Rm (one row per pass): the row sums of the new g, as row_sums_body forms them
+      double S0 = 0.0, S1 = 0.0, S2 = 0.0;
       for (int l = r; l < nv2; l += R) {
         double o = A0 * e2t[l];
         o = fma(A1, E1t[l], o);
@@ -354,7 +357,14 @@ __global__ void __launch_bounds__(512, 1)
         o = fma(gam1, g2t[l] * x, o);
         x *= rat;
         Go[l * nv1] = o;
+        if (Rm) {
+          const double v2 = fma(l + 0.5, g.dv2, g.v2min);
+          S0 += o;
+          S1 = fma(v2, o, S1);
+          S2 = fma(v2 * v2, o, S2);
+        }
       }
+      if (Rm) micro_body::store_row_sums(Rm, cell, nv1, k, S0, S1, S2);
     }
     __syncthreads();
   }
@@ -430,10 +440,11 @@ int closure_ghat_blocks(const MicroShape& ms) {
 
 void launch_closure_ghat(double* G, const double* prim, const KGrid& g, double dt, double eps,
                          const MicroShape& ms, const int* list, const int* count, int blocks,
-                         cudaStream_t s) {
+                         cudaStream_t s, double* Rm) {
   if (ms.smem_ghat > 48 * 1024)
     cudaFuncSetAttribute(k_closure_ghat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_ghat);
-  k_closure_ghat<<<blocks, ms.threads, ms.smem_ghat, s>>>(G, prim, g, dt, eps, ms.R, list, count);
+  k_closure_ghat<<<blocks, ms.threads, ms.smem_ghat, s>>>(G, prim, g, dt, eps, ms.R, list, count,
+                                                          ms.R == 1 ? Rm : nullptr);
 }
 
 }  // namespace mmk

@@ -95,12 +95,10 @@ template <typename Tg>
 void launch_micro_x_rows(const Tg* Gin, Tg* Gout, const double* prim, const double* Rm,
                          const KGrid& g, const KParams& p, double dt, const MicroShape& ms,
                          cudaStream_t s, int cell0 = 0, int ncells = -1);
-// The row sums of G for the cells [cell0, cell0 + ncells) (every cell for ncells < 0), or for a
-// list of cells: whenever G changes other than through a y sweep (needs ms.R == 1).
+// The row sums of G for the cells [cell0, cell0 + ncells) (every cell for ncells < 0): whenever
+// G is set other than by a sweep (needs ms.R == 1).
 void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s, int cell0 = 0,
                      int ncells = -1);
-void launch_row_sums_list(const double* G, double* Rm, const KGrid& g, const int* list,
-                          const int* count, int blocks, cudaStream_t s);
 template <typename Tg>
 void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
@@ -179,9 +177,10 @@ void launch_closure_lists(const unsigned char* flags, unsigned char* valid, cons
 void launch_closure_stale(unsigned char* valid, const KGrid& g, int* list, int* count,
                           cudaStream_t s);
 int closure_ghat_blocks(const MicroShape& ms);
+// Rm (optional, with ms.R == 1): the row sums of the new g of the listed cells.
 void launch_closure_ghat(double* G, const double* prim, const KGrid& g, double dt, double eps,
                          const MicroShape& ms, const int* list, const int* count, int blocks,
-                         cudaStream_t s);
+                         cudaStream_t s, double* Rm = nullptr);
 // Manufactured-solution harness (mm_mms.cu): velocity tables phi, gam [nv]; exact state; the
 // source terms of one step at time t; per-cell error partial sums [4][ny][nx].
 void launch_mms_tables(double* phi, double* gam, const KGrid& g, const KParams& p,

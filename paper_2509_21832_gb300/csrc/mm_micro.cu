@@ -57,19 +57,12 @@ __global__ void __launch_bounds__(32) k_micro_x_rows_list(const Tg* __restrict__
   }
 }
 
-// Row sums of the cells [cell0, cell0 + gridDim.x), or of a list of cells.
+// Row sums of the cells [cell0, cell0 + gridDim.x).
 __global__ void __launch_bounds__(32) k_row_sums(const double* __restrict__ G,
                                                  double* __restrict__ Rm, KGrid g, int cell0) {
   row_sums_body<double>(G, Rm, g, cell0 + (int)blockIdx.x);
 }
 
-__global__ void __launch_bounds__(32) k_row_sums_list(const double* __restrict__ G,
-                                                      double* __restrict__ Rm, KGrid g,
-                                                      const int* __restrict__ list,
-                                                      const int* __restrict__ count) {
-  const int n = *count;
-  for (int q = blockIdx.x; q < n; q += gridDim.x) row_sums_body<double>(G, Rm, g, list[q]);
-}
 
 template <typename Tg>
 __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs,
@@ -270,10 +263,6 @@ void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s
   if (n > 0) k_row_sums<<<n, 32, 0, s>>>(G, Rm, g, cell0);
 }
 
-void launch_row_sums_list(const double* G, double* Rm, const KGrid& g, const int* list,
-                          const int* count, int blocks, cudaStream_t s) {
-  k_row_sums_list<<<blocks, 32, 0, s>>>(G, Rm, g, list, count);
-}
 
 template void launch_micro_x_list<double>(const double*, double*, const double*, const KGrid&,
                                           const KParams&, double, const MicroShape&, const int*,
