@@ -9,8 +9,11 @@
 // that problem's grid, parameters, dt and eps read from a descriptor array in device memory.
 // One batch step is captured in a CUDA graph and replayed.  The CTA size and the grid size of
 // the phase-space kernels are chosen by a small autotuner (timed trial launches on the batch's
-// own data), cached per process by the multiset of problem shapes.  No kernel waits on another
-// CTA, so there are no spin-waits.
+// own data), cached per process by the multiset of problem shapes.  Problems that the tuned
+// shape runs as one warp per cell with one row per pass keep the row sums of g (sum over v2 of
+// v2^j g, j = 0..2, per v1 column) as the single-problem contexts do: the y sweep leaves them
+// for the next x sweep, which takes the moments of its upwind differences from them.  No kernel
+// waits on another CTA, so there are no spin-waits.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -33,11 +36,17 @@ struct BatchProb {
   double dt, eps, dtidx, dtidy, hscale;
   long long g_off;    // offset of the problem's phase-space block (elements)
   long long mac_off;  // offset of its macro buffers (doubles)
+  long long r_off;    // offset of its row sums (3 nv1 doubles per cell; nv1 <= 32 only)
   int c_off;          // first global cell index of the problem
   int w_off;          // first entry of its diffuse-wall cells in the wall list
   int n_wall;
   int R;              // rows per pass of the phase-space mapping for the tuned CTA size
+  int rows;           // 1: one warp per cell, R = 1, row sums kept (x sweep from them)
 };
+
+__device__ __forceinline__ double* rows_of(double* Rm, const BatchProb& b) {
+  return (Rm && b.rows) ? Rm + b.r_off : nullptr;
+}
 
 __device__ __forceinline__ int find_prob(const int* __restrict__ start, int nprob, int item) {
   int lo = 0, hi = nprob - 1;
@@ -61,34 +70,42 @@ __global__ void k_batch_prims(const double* __restrict__ Q, double* __restrict__
 }
 
 __global__ void k_batch_micro_x(const double* __restrict__ G, double* __restrict__ Gs,
-                                const double* __restrict__ prim, const BatchProb* __restrict__ pr,
-                                const int* __restrict__ start, int nprob, int total) {
+                                const double* __restrict__ prim, const double* __restrict__ Rm,
+                                const BatchProb* __restrict__ pr, const int* __restrict__ start,
+                                int nprob, int total) {
   extern __shared__ double sm[];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const BatchProb& b = pr[find_prob(start, nprob, item)];
-    micro_body::micro_x_body<double>(G + b.g_off, Gs + b.g_off, prim + NPRIM * (size_t)b.c_off,
-                                     b.g, b.p, b.dtidx, b.R, item - b.c_off, sm);
+    const double* pp = prim + NPRIM * (size_t)b.c_off;
+    if (b.rows)
+      micro_body::micro_x_rows_body<double>(G + b.g_off, Gs + b.g_off, pp, Rm + b.r_off, b.g,
+                                            b.p, b.dtidx, item - b.c_off, sm);
+    else
+      micro_body::micro_x_body<double>(G + b.g_off, Gs + b.g_off, pp, b.g, b.p, b.dtidx, b.R,
+                                       item - b.c_off, sm);
     __syncthreads();
   }
 }
 
 __global__ void k_batch_micro_y(const double* __restrict__ Gs, double* __restrict__ G,
                                 double* __restrict__ H, const double* __restrict__ prim,
-                                const BatchProb* __restrict__ pr, const int* __restrict__ start,
-                                int nprob, int total, int* __restrict__ err) {
+                                double* __restrict__ Rm, const BatchProb* __restrict__ pr,
+                                const int* __restrict__ start, int nprob, int total,
+                                int* __restrict__ err) {
   extern __shared__ double sm[];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const BatchProb& b = pr[find_prob(start, nprob, item)];
     micro_body::micro_y_body<double>(Gs + b.g_off, G + b.g_off, H + 4 * (size_t)b.c_off,
                                      prim + NPRIM * (size_t)b.c_off, b.g, b.p, b.dtidy, b.hscale,
-                                     b.R, err, item - b.c_off, sm);
+                                     b.R, err, item - b.c_off, sm, nullptr, rows_of(Rm, b));
     __syncthreads();
   }
 }
 
 __global__ void k_batch_micro_y_wall(const double* __restrict__ Gs, double* __restrict__ G,
                                      double* __restrict__ H, const double* __restrict__ prim,
-                                     const int* __restrict__ walls, const BatchProb* __restrict__ pr,
+                                     double* __restrict__ Rm, const int* __restrict__ walls,
+                                     const BatchProb* __restrict__ pr,
                                      const int* __restrict__ wstart, int nprob, int total,
                                      int* __restrict__ err) {
   extern __shared__ double sm[];
@@ -96,7 +113,7 @@ __global__ void k_batch_micro_y_wall(const double* __restrict__ Gs, double* __re
     const BatchProb& b = pr[find_prob(wstart, nprob, item)];
     micro_body::micro_y_wall_body<double>(Gs + b.g_off, G + b.g_off, H + 4 * (size_t)b.c_off,
                                           prim + NPRIM * (size_t)b.c_off, b.g, b.p, b.dt, b.eps,
-                                          b.R, err, walls[item], sm);
+                                          b.R, err, walls[item], sm, rows_of(Rm, b));
     __syncthreads();
   }
 }
@@ -160,6 +177,7 @@ struct mm_batch {
   double* H = nullptr;
   double* prim = nullptr;
   double* mac = nullptr;
+  double* Rm = nullptr;  // row sums of every problem with nv1 <= 32
   int* walls = nullptr;
   int* d_start = nullptr;
   int* d_wstart = nullptr;
@@ -196,7 +214,17 @@ size_t smem_wall(const mm_batch* b) {
 
 void apply_tune(mm_batch* b, const Tune& t) {
   b->tune = t;
-  for (auto& p : b->hp) p.R = best_R(p.g.nv1, p.g.nv2, t.threads);
+  for (auto& p : b->hp) {
+    p.R = best_R(p.g.nv1, p.g.nv2, t.threads);
+    p.rows = (t.threads == 32 && p.R == 1 && p.g.nv1 <= 32) ? 1 : 0;
+  }
+}
+
+// Row sums of problem q's g from G itself (after its g was set other than by a sweep, or
+// before a tuning that may switch the problem to the row-sum x sweep).
+void refresh_rows(mm_batch* b, int q) {
+  const BatchProb& d = b->hp[q];
+  if (d.g.nv1 <= 32) launch_row_sums(b->G + d.g_off, b->Rm + d.r_off, d.g, b->stream);
 }
 
 void enqueue_batch_step(mm_batch* b) {
@@ -208,13 +236,14 @@ void enqueue_batch_step(mm_batch* b) {
   const int cgrid = std::min((cells + tb - 1) / tb, 152 * 16);
   k_batch_prims<<<cgrid, tb, 0, s>>>(b->Q, b->prim, b->d_prob, b->d_start, b->nprob, cells,
                                       b->err);
-  k_batch_micro_x<<<C, T, smem_x(b), s>>>(b->G, b->Gs, b->prim, b->d_prob, b->d_start, b->nprob,
-                                          cells);
-  k_batch_micro_y<<<C, T, smem_y(b), s>>>(b->Gs, b->G, b->H, b->prim, b->d_prob, b->d_start,
-                                          b->nprob, cells, b->err);
+  k_batch_micro_x<<<C, T, smem_x(b), s>>>(b->G, b->Gs, b->prim, b->Rm, b->d_prob, b->d_start,
+                                          b->nprob, cells);
+  k_batch_micro_y<<<C, T, smem_y(b), s>>>(b->Gs, b->G, b->H, b->prim, b->Rm, b->d_prob,
+                                          b->d_start, b->nprob, cells, b->err);
   if (b->nwall > 0)
     k_batch_micro_y_wall<<<std::min(b->nwall, C), T, smem_wall(b), s>>>(
-        b->Gs, b->G, b->H, b->prim, b->walls, b->d_prob, b->d_wstart, b->nprob, b->nwall, b->err);
+        b->Gs, b->G, b->H, b->prim, b->Rm, b->walls, b->d_prob, b->d_wstart, b->nprob, b->nwall,
+        b->err);
   for (int ph = 0; ph < 3; ++ph)
     k_batch_macro<<<cgrid, tb, 0, s>>>(ph, b->Q, b->H, b->mac, b->d_prob, b->d_start, b->nprob,
                                         cells, b->err);
@@ -261,7 +290,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
   b->start.resize(nprob + 1);
   b->wstart.resize(nprob + 1);
   std::vector<int> walls;
-  size_t goff = 0, moff = 0;
+  size_t goff = 0, moff = 0, roff = 0;
   int coff = 0;
   char sig[64];
   std::vector<std::string> shapes;
@@ -293,6 +322,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
     d.p.keep_es = p.wall_keep_es_term ? 1 : 0;
     d.g_off = (long long)goff;
     d.mac_off = (long long)moff;
+    d.r_off = (long long)roff;
     d.c_off = coff;
     d.w_off = (int)walls.size();
     for (int j = 0; j < g.ny; ++j)
@@ -305,6 +335,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
     b->wstart[q] = d.w_off;
     goff += (size_t)g.nx * g.ny * g.nv1 * g.nv2;
     moff += macro_doubles(g.nx, g.ny);
+    if (g.nv1 <= 32) roff += (size_t)3 * g.nv1 * g.nx * g.ny;
     coff += g.nx * g.ny;
     b->max_nv1 = std::max(b->max_nv1, g.nv1);
     b->max_nv2 = std::max(b->max_nv2, g.nv2);
@@ -329,6 +360,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
   alloc((void**)&b->H, 4 * (size_t)coff * sizeof(double));
   alloc((void**)&b->prim, NPRIM * (size_t)coff * sizeof(double));
   alloc((void**)&b->mac, moff * sizeof(double));
+  alloc((void**)&b->Rm, roff * sizeof(double));
   alloc((void**)&b->walls, walls.size() * sizeof(int));
   alloc((void**)&b->d_start, (nprob + 1) * sizeof(int));
   alloc((void**)&b->d_wstart, (nprob + 1) * sizeof(int));
@@ -342,6 +374,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
     e = cudaMemcpy(b->d_wstart, b->wstart.data(), (nprob + 1) * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(b->G, 0, goff * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(b->Rm, 0, (roff > 0 ? roff : 2) * sizeof(double));
   if (e != cudaSuccess) {
     mm_batch_destroy(b);
     cudaGetLastError();
@@ -383,6 +416,10 @@ mm_status mm_batch_set_state(mm_batch* b, int q, const double* Q_host, const dou
     else
       e = cudaMemsetAsync(b->G + d.g_off, 0, np * sizeof(double), b->stream);
   }
+  if (e == cudaSuccess) {
+    refresh_rows(b, q);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   return e == cudaSuccess ? MM_OK : bcuda(b, e, "set state");
 }
@@ -408,6 +445,9 @@ mm_status mm_batch_autotune(mm_batch* b, int* threads_out, int* ctas_out) {
   cudaEventCreate(&e1);
   Tune best = b->tune;
   float best_ms = 1e30f;
+  // the row sums of every problem that a candidate shape may run as one warp per cell (they
+  // were not kept for it under the previous shape); the trial y sweeps store none
+  for (int q = 0; q < b->nprob; ++q) refresh_rows(b, q);
   // prims once so the coefficient fields are defined (uses the current dt, eps descriptors)
   k_batch_prims<<<std::min((b->ncell + 255) / 256, sms * 16), 256, 0, b->stream>>>(
       b->Q, b->prim, b->d_prob, b->d_start, b->nprob, b->ncell, b->err);
@@ -420,9 +460,10 @@ mm_status mm_batch_autotune(mm_batch* b, int* threads_out, int* ctas_out) {
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, b->stream);
         k_batch_micro_x<<<t.ctas, t.threads, smem_x(b), b->stream>>>(
-            b->G, b->Gs, b->prim, b->d_prob, b->d_start, b->nprob, b->ncell);
+            b->G, b->Gs, b->prim, b->Rm, b->d_prob, b->d_start, b->nprob, b->ncell);
         k_batch_micro_y<<<t.ctas, t.threads, smem_y(b), b->stream>>>(
-            b->Gs, tmp, b->H, b->prim, b->d_prob, b->d_start, b->nprob, b->ncell, b->err);
+            b->Gs, tmp, b->H, b->prim, nullptr, b->d_prob, b->d_start, b->nprob, b->ncell,
+            b->err);
         cudaEventRecord(e1, b->stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -550,6 +591,7 @@ void mm_batch_destroy(mm_batch* b) {
   cudaFree(b->H);
   cudaFree(b->prim);
   cudaFree(b->mac);
+  cudaFree(b->Rm);
   cudaFree(b->walls);
   cudaFree(b->d_start);
   cudaFree(b->d_wstart);
