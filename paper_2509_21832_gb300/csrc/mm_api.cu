@@ -58,6 +58,7 @@ struct mm_ctx {
   // FP64 with one row per pass: raw row sums of G [cell][3][nv1], kept current with G (left by
   // the y sweeps, formed whenever G is set otherwise) for the x sweep
   double* rmom = nullptr;
+  double* etab = nullptr;  // e1, e2 of every cell, from the x sweep to the y sweep (with rmom)
   int* err = nullptr;
   int* wall_cells = nullptr;
   int n_wall = 0;
@@ -256,13 +257,13 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
     // set), for one row per pass
     if (c->rmom)
       timed(c, T_MICRO_X, [&] {
-        launch_micro_x_rows<Tg>(G, Gs, c->prim, c->rmom, g, p, dt, c->ms, s);
+        launch_micro_x_rows<Tg>(G, Gs, c->prim, c->rmom, g, p, dt, c->ms, s, 0, -1, c->etab);
       });
     else
       timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
     timed(c, T_MICRO_Y, [&] {
       launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, srcg, 0, -1,
-                         c->rmom);
+                         c->rmom, c->rmom ? c->etab : nullptr);
     });
     if (c->n_wall > 0)
       timed(c, T_MICRO_YW, [&] {
@@ -300,11 +301,12 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   });
   timed(c, T_MICRO_X, [&] {
     launch_micro_x_list<double>(G, Gs, c->prim, g, p, dt, c->ms, c->clists, c->ccounts,
-                                c->blocks_x, s, c->rmom);
+                                c->blocks_x, s, c->rmom, c->etab);
   });
   timed(c, T_MICRO_Y, [&] {
     launch_micro_y_list<double>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err,
-                                c->clists + nc, c->ccounts + 1, c->blocks_y, s, c->rmom);
+                                c->clists + nc, c->ccounts + 1, c->blocks_y, s, c->rmom,
+                                c->etab);
   });
   if (c->n_wall > 0)
     timed(c, T_MICRO_YW, [&] {
@@ -511,7 +513,7 @@ size_t mm_device_bytes(const mm_grid* g, const mm_params* p) {
                         : 0;
   const MicroShape ms = micro_shape(g->nv1, g->nv2);
   const size_t rows = p->precision == MM_PREC_FP64 && ms.R == 1 && ms.threads == 32
-                          ? 3 * nc * (size_t)g->nv1 * sizeof(double)
+                          ? (3 * (size_t)g->nv1 + g->nv1 + g->nv2) * nc * sizeof(double)
                           : 0;
   return 2 * np * gs + (6 + 4 + NPRIM) * nc * sizeof(double) +
          macro_doubles(g->nx, g->ny) * sizeof(double) + pf + sizeof(int) + nwall * sizeof(int) +
@@ -574,8 +576,10 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
   alloc((void**)&c->prim, NPRIM * c->ncell * sizeof(double));
   if (c->fp32) alloc((void**)&c->primf, NPRIMF * c->ncell * sizeof(float));
   // row sums for the FP64 sweeps that run one warp per cell with one row per pass
-  if (!c->fp32 && c->ms.R == 1 && c->ms.threads == 32)
+  if (!c->fp32 && c->ms.R == 1 && c->ms.threads == 32) {
     alloc((void**)&c->rmom, 3 * c->ncell * grid->nv1 * sizeof(double));
+    alloc((void**)&c->etab, c->ncell * (grid->nv1 + grid->nv2) * sizeof(double));
+  }
   alloc((void**)&c->err, sizeof(int));
   std::vector<int> walls;
   for (int j = 0; j < grid->ny; ++j)
@@ -955,6 +959,7 @@ void mm_destroy(mm_ctx* c) {
   cudaFree(c->prim);
   cudaFree(c->primf);
   cudaFree(c->rmom);
+  cudaFree(c->etab);
   cudaFree(c->err);
   cudaFree(c->wall_cells);
   cudaFree(c->cX);

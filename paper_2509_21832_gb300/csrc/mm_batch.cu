@@ -78,8 +78,8 @@ __global__ void k_batch_micro_x(const double* __restrict__ G, double* __restrict
     const BatchProb& b = pr[find_prob(start, nprob, item)];
     const double* pp = prim + NPRIM * (size_t)b.c_off;
     if (b.rows)
-      micro_body::micro_x_rows_body<double>(G + b.g_off, Gs + b.g_off, pp, Rm + b.r_off, b.g,
-                                            b.p, b.dtidx, item - b.c_off, sm);
+      micro_body::micro_x_rows_body<double>(G + b.g_off, Gs + b.g_off, pp, Rm + b.r_off,
+                                            nullptr, b.g, b.p, b.dtidx, item - b.c_off, sm);
     else
       micro_body::micro_x_body<double>(G + b.g_off, Gs + b.g_off, pp, b.g, b.p, b.dtidx, b.R,
                                        item - b.c_off, sm);

@@ -260,12 +260,15 @@ __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
 // d = G_up - G of column k, sum_l c2^j d for j = 0, 1, 2 follows from the differences of the two
 // cells' raw sums (c2 = v2 - u2), so one pass over the velocities forms
 // G* = G + lam d + ak e2 + bk qet (Eq. update-micro-2D-xdir) without accumulating per velocity.
+// With Ee it also leaves the cell's Maxwellian factors for the y sweep, which needs the same
+// ones: Ee[cell (nv1 + nv2) + k] = e1(k), Ee[cell (nv1 + nv2) + nv1 + l] = e2(l).
 template <typename Tg>
 __device__ __forceinline__ void micro_x_rows_body(const Tg* __restrict__ Gin,
                                                   Tg* __restrict__ Gout,
                                                   const double* __restrict__ prim,
-                                                  const double* __restrict__ Rm, KGrid g,
-                                                  KParams p, double dtidx, int cell, double* sm) {
+                                                  const double* __restrict__ Rm,
+                                                  double* __restrict__ Ee, KGrid g, KParams p,
+                                                  double dtidx, int cell, double* sm) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   double* red = sm;
   double* c2t = sm + kRed;
@@ -283,12 +286,15 @@ __device__ __forceinline__ void micro_x_rows_body(const Tg* __restrict__ Gin,
   const double inv2T = prim[P_INV2T * nc + cell], iT = prim[P_IT * nc + cell];
   const double kap = prim[P_KAP * nc + cell];
 
+  double* Eec = Ee ? Ee + (size_t)cell * (nv1 + nv2) : nullptr;
   for (int l = t; l < nv2; l += blockDim.x) {
     const double c2 = fma(l + 0.5, g.dv2, g.v2min) - u2;
     const double q = c2 * c2;
+    const double e2 = expd(-q * inv2T);
     c2t[l] = c2;
     c2q[l] = q;
-    e2t[l] = expd(-q * inv2T);
+    e2t[l] = e2;
+    if (Eec) Eec[nv1 + l] = e2;
   }
 
   const double v1 = fma(k + 0.5, g.dv1, g.v1min);
@@ -324,6 +330,7 @@ __device__ __forceinline__ void micro_x_rows_body(const Tg* __restrict__ Gin,
   const double gm = fma(0.25 * S[3], iT * iT, -S[0] * inv2T);
   for (int l = t; l < nv2; l += blockDim.x) qet[l] = e2t[l] * fma(b2, c2t[l], gm * c2q[l]);
   const double e1 = expd(-c1 * c1 * inv2T);
+  if (Eec && active) Eec[k] = e1;
   const double bk = kap * e1;
   const double ak = bk * fma(gm * c1, c1, fma(b1, c1, b0));
   __syncthreads();
@@ -356,7 +363,8 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
                                                     KParams p, double dtidy, double hscale, int R,
                                                     int* __restrict__ err, int cell, double* sm,
                                                     const double* __restrict__ src = nullptr,
-                                                    double* __restrict__ Rm = nullptr) {
+                                                    double* __restrict__ Rm = nullptr,
+                                                    const double* __restrict__ Ee = nullptr) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;
   const int i = cell % g.nx, j = cell / g.nx;
@@ -399,7 +407,8 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
       const double v2 = fma(l + 0.5, g.dv2, g.v2min);
       const double c2 = v2 - u2;
       const double q = c2 * c2;
-      const double e2 = expd(-q * inv2T);
+      // e2 as the x sweep formed it (Ee), or formed here the same way
+      const double e2 = Ee ? Ee[(size_t)cell * (nv1 + nv2) + nv1 + l] : expd(-q * inv2T);
       const double av = fabs(v2);
       const double sg = -av * g.idy;
       const double wl = om1 * (av * dtidy);
@@ -465,12 +474,12 @@ __device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
   const double C1 = fma(om1kap, b2, -fma(c1, fma(c1, w12, w11), w10));
   const double C2 = fma(om1kap, gm, -fma(c1, w21, w20));
   const double C3 = -w30;
-  const double e1 = expd(-c1q * inv2T);
+  const double e1 = Ee ? Ee[(size_t)cell * (nv1 + nv2) + k] : expd(-c1q * inv2T);
   const double A0 = e1 * C0, A1 = e1 * C1, A2 = e1 * C2, A3 = e1 * C3;
-  const double gam1 = gam0 * expd(-0.5 * Ti11 * c1q);
   const double c2r = fma(r + 0.5, g.dv2, g.v2min) - u2;
-  // gam1 times the cross factor exp(-Ti12 c1 c2) of row l, advanced by rat per row
-  double x = gam1 * expd(-Ti12 * c1 * c2r);
+  // gam0 exp(-Ti11 c1^2 / 2 - Ti12 c1 c2) of row l (the factor of the ES Gaussian that depends on
+  // c1), advanced by rat per row
+  double x = gam0 * expd(-c1 * fma(0.5 * Ti11, c1, Ti12 * c2r));
   const double rat = expd(-Ti12 * c1 * (R * g.dv2));
 
   // pass 2: G^{n+1} = om1 (G* - dt Z* + dt Zhat*) + om2 Ghat, and its heat-flux moments;

@@ -84,17 +84,19 @@ void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
 // src (optional): a term added to g^{n+1} at every node, same layout as G
 // Rm (optional, used only with one row per pass, ms.R == 1): receives the raw row sums of
 // G^{n+1} [cell][3][nv1] for the next step's launch_micro_x_rows.
+// Ee (optional): the Maxwellian factors e1, e2 [cell][nv1 + nv2] that launch_micro_x_rows left
+// for every cell of this sweep in the same step (the values the sweep would form itself).
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
                     cudaStream_t s, const double* src = nullptr, int cell0 = 0,
-                    int ncells = -1, double* Rm = nullptr);
+                    int ncells = -1, double* Rm = nullptr, const double* Ee = nullptr);
 // The x sweep from the row sums Rm of G^n left by the previous y sweep (needs ms.R == 1 and
-// every cell's sums current).
+// every cell's sums current); with Ee it leaves each cell's e1, e2 for the y sweep.
 template <typename Tg>
 void launch_micro_x_rows(const Tg* Gin, Tg* Gout, const double* prim, const double* Rm,
                          const KGrid& g, const KParams& p, double dt, const MicroShape& ms,
-                         cudaStream_t s, int cell0 = 0, int ncells = -1);
+                         cudaStream_t s, int cell0 = 0, int ncells = -1, double* Ee = nullptr);
 // The row sums of G for the cells [cell0, cell0 + ncells) (every cell for ncells < 0): whenever
 // G is set other than by a sweep (needs ms.R == 1).
 void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s, int cell0 = 0,
@@ -154,12 +156,13 @@ __host__ __device__ inline MacroBufs carve_macro(double* base, int nx, int ny) {
 template <typename Tg>
 void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                          const KParams& p, double dt, const MicroShape& ms, const int* list,
-                         const int* count, int blocks, cudaStream_t s, const double* Rm = nullptr);
+                         const int* count, int blocks, cudaStream_t s, const double* Rm = nullptr,
+                         double* Ee = nullptr);
 template <typename Tg>
 void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                          const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
                          const int* list, const int* count, int blocks, cudaStream_t s,
-                         double* Rm = nullptr);
+                         double* Rm = nullptr, const double* Ee = nullptr);
 int micro_list_blocks(const MicroShape& ms, bool ysweep);
 // Learned closure (FP64 path): features + Chapman-Enskog flux + scale (aux [5][ny][nx]),
 // training targets, decision, work lists [x | y | refresh][nc] with counts[3], Ghat write.

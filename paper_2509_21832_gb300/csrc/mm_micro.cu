@@ -34,10 +34,11 @@ template <typename Tg>
 __global__ void __launch_bounds__(32) k_micro_x_rows(const Tg* __restrict__ Gin,
                                                      Tg* __restrict__ Gout,
                                                      const double* __restrict__ prim,
-                                                     const double* __restrict__ Rm, KGrid g,
-                                                     KParams p, double dtidx, int cell0) {
+                                                     const double* __restrict__ Rm,
+                                                     double* __restrict__ Ee, KGrid g, KParams p,
+                                                     double dtidx, int cell0) {
   extern __shared__ double sm[];
-  micro_x_rows_body<Tg>(Gin, Gout, prim, Rm, g, p, dtidx, cell0 + (int)blockIdx.x, sm);
+  micro_x_rows_body<Tg>(Gin, Gout, prim, Rm, Ee, g, p, dtidx, cell0 + (int)blockIdx.x, sm);
 }
 
 // The x sweep from the row sums over a list of cells (persistent CTAs of one warp).
@@ -46,13 +47,14 @@ __global__ void __launch_bounds__(32) k_micro_x_rows_list(const Tg* __restrict__
                                                           Tg* __restrict__ Gout,
                                                           const double* __restrict__ prim,
                                                           const double* __restrict__ Rm,
-                                                          KGrid g, KParams p, double dtidx,
+                                                          double* __restrict__ Ee, KGrid g,
+                                                          KParams p, double dtidx,
                                                           const int* __restrict__ list,
                                                           const int* __restrict__ count) {
   extern __shared__ double sm[];
   const int n = *count;
   for (int q = blockIdx.x; q < n; q += gridDim.x) {
-    micro_x_rows_body<Tg>(Gin, Gout, prim, Rm, g, p, dtidx, list[q], sm);
+    micro_x_rows_body<Tg>(Gin, Gout, prim, Rm, Ee, g, p, dtidx, list[q], sm);
     __syncthreads();
   }
 }
@@ -72,10 +74,11 @@ __global__ void __launch_bounds__(512, 1) k_micro_y(const Tg* __restrict__ Gs,
                                                     KParams p, double dtidy, double hscale, int R,
                                                     int* __restrict__ err,
                                                     const double* __restrict__ src, int cell0,
-                                                    double* __restrict__ Rm) {
+                                                    double* __restrict__ Rm,
+                                                    const double* __restrict__ Ee) {
   extern __shared__ double sm[];
   micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, cell0 + (int)blockIdx.x, sm,
-                   src, Rm);
+                   src, Rm, Ee);
 }
 
 template <typename Tg>
@@ -117,12 +120,13 @@ __global__ void __launch_bounds__(512, 1) k_micro_y_list(const Tg* __restrict__ 
                                                          int R, int* __restrict__ err,
                                                          const int* __restrict__ list,
                                                          const int* __restrict__ count,
-                                                         double* __restrict__ Rm) {
+                                                         double* __restrict__ Rm,
+                                                         const double* __restrict__ Ee) {
   extern __shared__ double sm[];
   const int n = *count;
   for (int q = blockIdx.x; q < n; q += gridDim.x) {
     micro_y_body<Tg>(Gs, Gout, Hout, prim, g, p, dtidy, hscale, R, err, list[q], sm, nullptr,
-                     Rm);
+                     Rm, Ee);
     __syncthreads();
   }
 }
@@ -235,9 +239,10 @@ int micro_list_blocks(const MicroShape& ms, bool ysweep) {
 template <typename Tg>
 void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                          const KParams& p, double dt, const MicroShape& ms, const int* list,
-                         const int* count, int blocks, cudaStream_t s, const double* Rm) {
+                         const int* count, int blocks, cudaStream_t s, const double* Rm,
+                         double* Ee) {
   if (Rm && ms.R == 1) {
-    k_micro_x_rows_list<Tg><<<blocks, 32, ms.smem_x, s>>>(Gin, Gout, prim, Rm, g, p,
+    k_micro_x_rows_list<Tg><<<blocks, 32, ms.smem_x, s>>>(Gin, Gout, prim, Rm, Ee, g, p,
                                                           dt * g.idx, list, count);
     return;
   }
@@ -251,10 +256,10 @@ template <typename Tg>
 void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                          const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
                          const int* list, const int* count, int blocks, cudaStream_t s,
-                         double* Rm) {
+                         double* Rm, const double* Ee) {
   k_micro_y_list<Tg><<<blocks, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
                                                            eps * g.dv1 * g.dv2, ms.R, err, list,
-                                                           count, ms.R == 1 ? Rm : nullptr);
+                                                           count, ms.R == 1 ? Rm : nullptr, Ee);
 }
 
 void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s, int cell0,
@@ -266,11 +271,11 @@ void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s
 
 template void launch_micro_x_list<double>(const double*, double*, const double*, const KGrid&,
                                           const KParams&, double, const MicroShape&, const int*,
-                                          const int*, int, cudaStream_t, const double*);
+                                          const int*, int, cudaStream_t, const double*, double*);
 template void launch_micro_y_list<double>(const double*, double*, double*, const double*,
                                           const KGrid&, const KParams&, double, double,
                                           const MicroShape&, int*, const int*, const int*, int,
-                                          cudaStream_t, double*);
+                                          cudaStream_t, double*, const double*);
 
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
@@ -288,26 +293,27 @@ void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,
-                    cudaStream_t s, const double* src, int cell0, int ncells, double* Rm) {
+                    cudaStream_t s, const double* src, int cell0, int ncells, double* Rm,
+                    const double* Ee) {
   const int n = ncells < 0 ? g.nx * g.ny : ncells;
   if (n <= 0) return;
   if (ms.smem_y > 48 * 1024)
     cudaFuncSetAttribute(k_micro_y<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_y);
   k_micro_y<Tg><<<n, ms.threads, ms.smem_y, s>>>(Gs, Gout, H, prim, g, p, dt * g.idy,
                                                  eps * g.dv1 * g.dv2, ms.R, err, src, cell0,
-                                                 ms.R == 1 ? Rm : nullptr);
+                                                 ms.R == 1 ? Rm : nullptr, Ee);
 }
 
 template <typename Tg>
 void launch_micro_x_rows(const Tg* Gin, Tg* Gout, const double* prim, const double* Rm,
                          const KGrid& g, const KParams& p, double dt, const MicroShape& ms,
-                         cudaStream_t s, int cell0, int ncells) {
+                         cudaStream_t s, int cell0, int ncells, double* Ee) {
   const int n = ncells < 0 ? g.nx * g.ny : ncells;
   if (n <= 0) return;
   if (ms.smem_x > 48 * 1024)
     cudaFuncSetAttribute(k_micro_x_rows<Tg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)ms.smem_x);
-  k_micro_x_rows<Tg><<<n, 32, ms.smem_x, s>>>(Gin, Gout, prim, Rm, g, p, dt * g.idx, cell0);
+  k_micro_x_rows<Tg><<<n, 32, ms.smem_x, s>>>(Gin, Gout, prim, Rm, Ee, g, p, dt * g.idx, cell0);
 }
 
 template <typename Tg>
@@ -329,10 +335,10 @@ template void launch_micro_x<double>(const double*, double*, const double*, cons
 template void launch_micro_y<double>(const double*, double*, double*, const double*,
                                      const KGrid&, const KParams&, double, double,
                                      const MicroShape&, int*, cudaStream_t, const double*, int,
-                                     int, double*);
+                                     int, double*, const double*);
 template void launch_micro_x_rows<double>(const double*, double*, const double*, const double*,
                                           const KGrid&, const KParams&, double, const MicroShape&,
-                                          cudaStream_t, int, int);
+                                          cudaStream_t, int, int, double*);
 template void launch_micro_y_wall<double>(const double*, double*, double*, const double*,
                                           const int*, int, const KGrid&, const KParams&, double,
                                           double, const MicroShape&, int*, cudaStream_t, double*);
