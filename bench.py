@@ -38,9 +38,9 @@ FLOPS_MICRO_Y = 39.0
 FLOPS_STEP = 46.0
 BYTES_PER_PHASE_FP64 = 16.0 + 160.0 / 1024.0
 # DRAM traffic of k_micro_y per phase cell (32^2 velocity meshes), from an ncu capture of the
-# 160^2 x 32^2 bump case: (213.9 MB read + 189.6 MB written, with the row sums) / 26.2144 M
-# phase cells.
-TRAFFIC_MICRO_Y_PER_PHASE_CELL = 403.5e6 / 26.2144e6
+# 160^2 x 32^2 bump case: (227.0 MB read, with the row sums and the x sweep's e1, e2, + 190.8 MB
+# written) / 26.2144 M phase cells.
+TRAFFIC_MICRO_Y_PER_PHASE_CELL = 417.8e6 / 26.2144e6
 
 
 def measured_peaks():
@@ -461,7 +461,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak,
                 # DRAM bytes per k_micro_y launch: ncu capture of the 160^2 x 32^2 case
-                # (read + write = 403.5 MB over 26.2 M phase cells), scaled by phase cells
+                # (read + write = 417.8 MB over 26.2 M phase cells), scaled by phase cells
                 "traffic": (TRAFFIC_MICRO_Y_PER_PHASE_CELL * nph
                             if (pr.grid.nv1, pr.grid.nv2) == (32, 32) else None),
                 "traffic_unit": "bytes per launch",
