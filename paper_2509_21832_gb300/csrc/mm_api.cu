@@ -58,7 +58,7 @@ struct mm_ctx {
   // FP64 with one row per pass: raw row sums of G [cell][3][nv1], kept current with G (left by
   // the y sweeps, formed whenever G is set otherwise) for the x sweep
   double* rmom = nullptr;
-  double* etab = nullptr;  // e1, e2 of every cell, from the x sweep to the y sweep (with rmom)
+  double* etab = nullptr;  // e1, e2 of every cell, from the x sweep to the y sweep (FP64 g)
   int* err = nullptr;
   int* wall_cells = nullptr;
   int n_wall = 0;
@@ -260,10 +260,12 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
         launch_micro_x_rows<Tg>(G, Gs, c->prim, c->rmom, g, p, dt, c->ms, s, 0, -1, c->etab);
       });
     else
-      timed(c, T_MICRO_X, [&] { launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s); });
+      timed(c, T_MICRO_X, [&] {
+        launch_micro_x<Tg>(G, Gs, c->prim, g, p, dt, c->ms, s, 0, -1, c->etab);
+      });
     timed(c, T_MICRO_Y, [&] {
       launch_micro_y<Tg>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, srcg, 0, -1,
-                         c->rmom, c->rmom ? c->etab : nullptr);
+                         c->rmom, c->etab);
     });
     if (c->n_wall > 0)
       timed(c, T_MICRO_YW, [&] {
@@ -388,14 +390,15 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
     // the x sweep sums its moments per velocity here (g has just arrived, without row sums);
     // the y sweeps leave the row sums of G^{n+1} for the steps that follow
     const int c0 = row0(r) * g.nx, cn = (row0(r + 1) - row0(r)) * g.nx;
-    launch_micro_x<double>(G, Gs, c->prim, g, p, dt, c->ms, c->xstream, c0, cn);
+    launch_micro_x<double>(G, Gs, c->prim, g, p, dt, c->ms, c->xstream, c0, cn, c->etab);
     cudaEventRecord(xswept[r], c->xstream);
   }
   auto ysweep = [&](int r, int after) {
     cudaStreamWaitEvent(s, xswept[after], 0);
     timed(c, T_MICRO_Y, [&] {
       launch_micro_y<double>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, nullptr,
-                             row0(r) * g.nx, (row0(r + 1) - row0(r)) * g.nx, c->rmom);
+                             row0(r) * g.nx, (row0(r + 1) - row0(r)) * g.nx, c->rmom,
+                             c->etab);
     });
   };
   // x sweeps complete in chunk order, so waiting for chunk r+1 covers chunks 0..r+1
@@ -513,11 +516,14 @@ size_t mm_device_bytes(const mm_grid* g, const mm_params* p) {
                         : 0;
   const MicroShape ms = micro_shape(g->nv1, g->nv2);
   const size_t rows = p->precision == MM_PREC_FP64 && ms.R == 1 && ms.threads == 32
-                          ? (3 * (size_t)g->nv1 + g->nv1 + g->nv2) * nc * sizeof(double)
+                          ? 3 * nc * (size_t)g->nv1 * sizeof(double)
+                          : 0;
+  const size_t etab = p->precision == MM_PREC_FP64
+                          ? ((size_t)g->nv1 + g->nv2) * nc * sizeof(double)
                           : 0;
   return 2 * np * gs + (6 + 4 + NPRIM) * nc * sizeof(double) +
          macro_doubles(g->nx, g->ny) * sizeof(double) + pf + sizeof(int) + nwall * sizeof(int) +
-         rows;
+         rows + etab;
 }
 
 mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
@@ -576,10 +582,10 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
   alloc((void**)&c->prim, NPRIM * c->ncell * sizeof(double));
   if (c->fp32) alloc((void**)&c->primf, NPRIMF * c->ncell * sizeof(float));
   // row sums for the FP64 sweeps that run one warp per cell with one row per pass
-  if (!c->fp32 && c->ms.R == 1 && c->ms.threads == 32) {
+  if (!c->fp32 && c->ms.R == 1 && c->ms.threads == 32)
     alloc((void**)&c->rmom, 3 * c->ncell * grid->nv1 * sizeof(double));
-    alloc((void**)&c->etab, c->ncell * (grid->nv1 + grid->nv2) * sizeof(double));
-  }
+  // the Maxwellian factors e1, e2 of every cell, formed by the x sweep, read by the y sweep
+  if (!c->fp32) alloc((void**)&c->etab, c->ncell * (grid->nv1 + grid->nv2) * sizeof(double));
   alloc((void**)&c->err, sizeof(int));
   std::vector<int> walls;
   for (int j = 0; j < grid->ny; ++j)

@@ -37,6 +37,7 @@ struct BatchProb {
   long long g_off;    // offset of the problem's phase-space block (elements)
   long long mac_off;  // offset of its macro buffers (doubles)
   long long r_off;    // offset of its row sums (3 nv1 doubles per cell; nv1 <= 32 only)
+  long long e_off;    // offset of its Maxwellian factors e1, e2 (nv1 + nv2 doubles per cell)
   int c_off;          // first global cell index of the problem
   int w_off;          // first entry of its diffuse-wall cells in the wall list
   int n_wall;
@@ -71,33 +72,34 @@ __global__ void k_batch_prims(const double* __restrict__ Q, double* __restrict__
 
 __global__ void k_batch_micro_x(const double* __restrict__ G, double* __restrict__ Gs,
                                 const double* __restrict__ prim, const double* __restrict__ Rm,
-                                const BatchProb* __restrict__ pr, const int* __restrict__ start,
-                                int nprob, int total) {
+                                double* __restrict__ Ee, const BatchProb* __restrict__ pr,
+                                const int* __restrict__ start, int nprob, int total) {
   extern __shared__ double sm[];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const BatchProb& b = pr[find_prob(start, nprob, item)];
     const double* pp = prim + NPRIM * (size_t)b.c_off;
     if (b.rows)
       micro_body::micro_x_rows_body<double>(G + b.g_off, Gs + b.g_off, pp, Rm + b.r_off,
-                                            nullptr, b.g, b.p, b.dtidx, item - b.c_off, sm);
+                                            Ee + b.e_off, b.g, b.p, b.dtidx, item - b.c_off, sm);
     else
       micro_body::micro_x_body<double>(G + b.g_off, Gs + b.g_off, pp, b.g, b.p, b.dtidx, b.R,
-                                       item - b.c_off, sm);
+                                       item - b.c_off, sm, Ee + b.e_off);
     __syncthreads();
   }
 }
 
 __global__ void k_batch_micro_y(const double* __restrict__ Gs, double* __restrict__ G,
                                 double* __restrict__ H, const double* __restrict__ prim,
-                                double* __restrict__ Rm, const BatchProb* __restrict__ pr,
-                                const int* __restrict__ start, int nprob, int total,
-                                int* __restrict__ err) {
+                                double* __restrict__ Rm, const double* __restrict__ Ee,
+                                const BatchProb* __restrict__ pr, const int* __restrict__ start,
+                                int nprob, int total, int* __restrict__ err) {
   extern __shared__ double sm[];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const BatchProb& b = pr[find_prob(start, nprob, item)];
     micro_body::micro_y_body<double>(Gs + b.g_off, G + b.g_off, H + 4 * (size_t)b.c_off,
                                      prim + NPRIM * (size_t)b.c_off, b.g, b.p, b.dtidy, b.hscale,
-                                     b.R, err, item - b.c_off, sm, nullptr, rows_of(Rm, b));
+                                     b.R, err, item - b.c_off, sm, nullptr, rows_of(Rm, b),
+                                     Ee + b.e_off);
     __syncthreads();
   }
 }
@@ -178,6 +180,7 @@ struct mm_batch {
   double* prim = nullptr;
   double* mac = nullptr;
   double* Rm = nullptr;  // row sums of every problem with nv1 <= 32
+  double* Ee = nullptr;  // e1, e2 of every cell, from the x sweep to the y sweep
   int* walls = nullptr;
   int* d_start = nullptr;
   int* d_wstart = nullptr;
@@ -236,9 +239,9 @@ void enqueue_batch_step(mm_batch* b) {
   const int cgrid = std::min((cells + tb - 1) / tb, 152 * 16);
   k_batch_prims<<<cgrid, tb, 0, s>>>(b->Q, b->prim, b->d_prob, b->d_start, b->nprob, cells,
                                       b->err);
-  k_batch_micro_x<<<C, T, smem_x(b), s>>>(b->G, b->Gs, b->prim, b->Rm, b->d_prob, b->d_start,
-                                          b->nprob, cells);
-  k_batch_micro_y<<<C, T, smem_y(b), s>>>(b->Gs, b->G, b->H, b->prim, b->Rm, b->d_prob,
+  k_batch_micro_x<<<C, T, smem_x(b), s>>>(b->G, b->Gs, b->prim, b->Rm, b->Ee, b->d_prob,
+                                          b->d_start, b->nprob, cells);
+  k_batch_micro_y<<<C, T, smem_y(b), s>>>(b->Gs, b->G, b->H, b->prim, b->Rm, b->Ee, b->d_prob,
                                           b->d_start, b->nprob, cells, b->err);
   if (b->nwall > 0)
     k_batch_micro_y_wall<<<std::min(b->nwall, C), T, smem_wall(b), s>>>(
@@ -290,7 +293,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
   b->start.resize(nprob + 1);
   b->wstart.resize(nprob + 1);
   std::vector<int> walls;
-  size_t goff = 0, moff = 0, roff = 0;
+  size_t goff = 0, moff = 0, roff = 0, eoff = 0;
   int coff = 0;
   char sig[64];
   std::vector<std::string> shapes;
@@ -323,6 +326,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
     d.g_off = (long long)goff;
     d.mac_off = (long long)moff;
     d.r_off = (long long)roff;
+    d.e_off = (long long)eoff;
     d.c_off = coff;
     d.w_off = (int)walls.size();
     for (int j = 0; j < g.ny; ++j)
@@ -336,6 +340,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
     goff += (size_t)g.nx * g.ny * g.nv1 * g.nv2;
     moff += macro_doubles(g.nx, g.ny);
     if (g.nv1 <= 32) roff += (size_t)3 * g.nv1 * g.nx * g.ny;
+    eoff += ((size_t)g.nv1 + g.nv2) * g.nx * g.ny;
     coff += g.nx * g.ny;
     b->max_nv1 = std::max(b->max_nv1, g.nv1);
     b->max_nv2 = std::max(b->max_nv2, g.nv2);
@@ -361,6 +366,7 @@ mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* para
   alloc((void**)&b->prim, NPRIM * (size_t)coff * sizeof(double));
   alloc((void**)&b->mac, moff * sizeof(double));
   alloc((void**)&b->Rm, roff * sizeof(double));
+  alloc((void**)&b->Ee, eoff * sizeof(double));
   alloc((void**)&b->walls, walls.size() * sizeof(int));
   alloc((void**)&b->d_start, (nprob + 1) * sizeof(int));
   alloc((void**)&b->d_wstart, (nprob + 1) * sizeof(int));
@@ -460,10 +466,10 @@ mm_status mm_batch_autotune(mm_batch* b, int* threads_out, int* ctas_out) {
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, b->stream);
         k_batch_micro_x<<<t.ctas, t.threads, smem_x(b), b->stream>>>(
-            b->G, b->Gs, b->prim, b->Rm, b->d_prob, b->d_start, b->nprob, b->ncell);
+            b->G, b->Gs, b->prim, b->Rm, b->Ee, b->d_prob, b->d_start, b->nprob, b->ncell);
         k_batch_micro_y<<<t.ctas, t.threads, smem_y(b), b->stream>>>(
-            b->Gs, tmp, b->H, b->prim, nullptr, b->d_prob, b->d_start, b->nprob, b->ncell,
-            b->err);
+            b->Gs, tmp, b->H, b->prim, nullptr, b->Ee, b->d_prob, b->d_start, b->nprob,
+            b->ncell, b->err);
         cudaEventRecord(e1, b->stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -592,6 +598,7 @@ void mm_batch_destroy(mm_batch* b) {
   cudaFree(b->prim);
   cudaFree(b->mac);
   cudaFree(b->Rm);
+  cudaFree(b->Ee);
   cudaFree(b->walls);
   cudaFree(b->d_start);
   cudaFree(b->d_wstart);

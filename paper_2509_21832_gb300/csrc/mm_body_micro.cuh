@@ -150,7 +150,8 @@ template <typename Tg, int NR = 0>
 __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
                                                     Tg* __restrict__ Gout,
                                                     const double* __restrict__ prim, KGrid g,
-                                                    KParams p, double dtidx, int R, int cell, double* sm) {
+                                                    KParams p, double dtidx, int R, int cell, double* sm,
+                                                    double* __restrict__ Ee = nullptr) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   double* red = sm;
   double* c2t = sm + kRed;
@@ -168,12 +169,17 @@ __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
   const double inv2T = prim[P_INV2T * nc + cell], iT = prim[P_IT * nc + cell];
   const double kap = prim[P_KAP * nc + cell];
 
+  // with Ee: the cell's Maxwellian factors for the y sweep, Ee[cell (nv1 + nv2) + k] = e1(k),
+  // Ee[cell (nv1 + nv2) + nv1 + l] = e2(l)
+  double* Eec = Ee ? Ee + (size_t)cell * (nv1 + nv2) : nullptr;
   for (int l = t; l < nv2; l += blockDim.x) {
     const double c2 = fma(l + 0.5, g.dv2, g.v2min) - u2;
     const double q = c2 * c2;
+    const double e2 = expd(-q * inv2T);
     c2t[l] = c2;
     c2q[l] = q;
-    e2t[l] = expd(-q * inv2T);
+    e2t[l] = e2;
+    if (Eec) Eec[nv1 + l] = e2;
   }
 
   const double v1 = fma(k + 0.5, g.dv1, g.v1min);
@@ -225,6 +231,7 @@ __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
   const double gm = fma(0.25 * S[3], iT * iT, -S[0] * inv2T);
   for (int l = t; l < nv2; l += blockDim.x) qet[l] = e2t[l] * fma(b2, c2t[l], gm * c2q[l]);
   const double e1 = expd(-c1 * c1 * inv2T);
+  if (Eec && t < nv1) Eec[k] = e1;
   const double bk = kap * e1;
   const double ak = bk * fma(gm * c1, c1, fma(b1, c1, b0));
   __syncthreads();

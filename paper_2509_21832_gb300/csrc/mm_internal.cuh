@@ -80,12 +80,13 @@ void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, c
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s,
-                    int cell0 = 0, int ncells = -1);
+                    int cell0 = 0, int ncells = -1, double* Ee = nullptr);
 // src (optional): a term added to g^{n+1} at every node, same layout as G
 // Rm (optional, used only with one row per pass, ms.R == 1): receives the raw row sums of
 // G^{n+1} [cell][3][nv1] for the next step's launch_micro_x_rows.
-// Ee (optional): the Maxwellian factors e1, e2 [cell][nv1 + nv2] that launch_micro_x_rows left
-// for every cell of this sweep in the same step (the values the sweep would form itself).
+// Ee (optional): the Maxwellian factors e1, e2 [cell][nv1 + nv2] that the x sweep
+// (launch_micro_x or launch_micro_x_rows with Ee) left for every cell of this sweep in the same
+// step (the values the sweep would form itself).
 template <typename Tg>
 void launch_micro_y(const Tg* Gs, Tg* Gout, double* H, const double* prim, const KGrid& g,
                     const KParams& p, double dt, double eps, const MicroShape& ms, int* err,

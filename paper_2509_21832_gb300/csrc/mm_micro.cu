@@ -25,9 +25,10 @@ template <typename Tg, int NR>
 __global__ void __launch_bounds__(NR > 0 ? 256 : 512, 1) k_micro_x(const Tg* __restrict__ Gin,
                                                     Tg* __restrict__ Gout,
                                                     const double* __restrict__ prim, KGrid g,
-                                                    KParams p, double dtidx, int R, int cell0) {
+                                                    KParams p, double dtidx, int R, int cell0,
+                                                    double* __restrict__ Ee) {
   extern __shared__ double sm[];
-  micro_x_body<Tg, NR>(Gin, Gout, prim, g, p, dtidx, R, cell0 + (int)blockIdx.x, sm);
+  micro_x_body<Tg, NR>(Gin, Gout, prim, g, p, dtidx, R, cell0 + (int)blockIdx.x, sm, Ee);
 }
 
 template <typename Tg>
@@ -102,11 +103,12 @@ __global__ void __launch_bounds__(NR > 0 ? 256 : 512, 1) k_micro_x_list(const Tg
                                                          const double* __restrict__ prim, KGrid g,
                                                          KParams p, double dtidx, int R,
                                                          const int* __restrict__ list,
-                                                         const int* __restrict__ count) {
+                                                         const int* __restrict__ count,
+                                                         double* __restrict__ Ee) {
   extern __shared__ double sm[];
   const int n = *count;
   for (int q = blockIdx.x; q < n; q += gridDim.x) {
-    micro_x_body<Tg, NR>(Gin, Gout, prim, g, p, dtidx, R, list[q], sm);
+    micro_x_body<Tg, NR>(Gin, Gout, prim, g, p, dtidx, R, list[q], sm, Ee);
     __syncthreads();
   }
 }
@@ -248,7 +250,7 @@ void launch_micro_x_list(const Tg* Gin, Tg* Gout, const double* prim, const KGri
   }
   with_x_list_kernel<Tg>(ms.xrows, [&](auto kern) {
     kern<<<blocks, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R, list,
-                                              count);
+                                              count, Ee);
   });
 }
 
@@ -280,13 +282,13 @@ template void launch_micro_y_list<double>(const double*, double*, double*, const
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
                     const KParams& p, double dt, const MicroShape& ms, cudaStream_t s, int cell0,
-                    int ncells) {
+                    int ncells, double* Ee) {
   const int n = ncells < 0 ? g.nx * g.ny : ncells;
   if (n <= 0) return;
   with_x_kernel<Tg>(ms.xrows, [&](auto kern) {
     if (ms.smem_x > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms.smem_x);
-    kern<<<n, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R, cell0);
+    kern<<<n, ms.threads, ms.smem_x, s>>>(Gin, Gout, prim, g, p, dt * g.idx, ms.R, cell0, Ee);
   });
 }
 
@@ -331,7 +333,7 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
 
 template void launch_micro_x<double>(const double*, double*, const double*, const KGrid&,
                                      const KParams&, double, const MicroShape&, cudaStream_t, int,
-                                     int);
+                                     int, double*);
 template void launch_micro_y<double>(const double*, double*, double*, const double*,
                                      const KGrid&, const KParams&, double, double,
                                      const MicroShape&, int*, cudaStream_t, const double*, int,
