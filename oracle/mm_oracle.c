@@ -86,6 +86,25 @@ static int prim_of(const orc_params* p, const double q[6], prim_t* o) {
   return 0;
 }
 
+/* Energy tensor E = rho (u (x) u + T I) (Section 2, ES-BGK operator), evaluated in that order
+ * and bracketing: E11 = rho (u1 u1 + T), E12 = rho (u1 u2), E22 = rho (u2 u2 + T). */
+int orc_q_from_prim(int ncell, const double* rho, const double* u1, const double* u2,
+                    const double* T, double* Q) {
+  for (int c = 0; c < ncell; ++c)
+    if (!(rho[c] > 0.0) || !(T[c] > 0.0) || !isfinite(rho[c]) || !isfinite(T[c]) ||
+        !isfinite(u1[c]) || !isfinite(u2[c]))
+      return -1;
+  for (int c = 0; c < ncell; ++c) {
+    Q[0 * ncell + c] = rho[c];
+    Q[1 * ncell + c] = rho[c] * u1[c];
+    Q[2 * ncell + c] = rho[c] * u2[c];
+    Q[3 * ncell + c] = rho[c] * (u1[c] * u1[c] + T[c]);
+    Q[4 * ncell + c] = rho[c] * (u1[c] * u2[c]);
+    Q[5 * ncell + c] = rho[c] * (u2[c] * u2[c] + T[c]);
+  }
+  return 0;
+}
+
 int orc_prims(const orc_params* p, const double q[6], double out[8]) {
   prim_t o;
   int rc = prim_of(p, q, &o);

@@ -98,6 +98,13 @@ double orc1d_dt(const orc1d_grid* g, double cfl, double t_final, int* nsteps_out
 /* Global time step (Eq. CFL-2D-part1/part2 and the 1D rule of Section 3.2). */
 double orc_dt_for_cfl(const orc_grid* g, double cfl, double t_final, int form, int* nsteps_out);
 
+/* Conservative state Q [6][ncell] from primitive fields rho, u1, u2, T [ncell] with an isotropic
+ * temperature tensor T I: Q = (rho, rho u1, rho u2, E11, E12, E22), E = rho (u (x) u + T I), the
+ * energy tensor of Section 2 (ES-BGK operator) as the paper's examples start (Section 6, g = 0).
+ * Returns -1 (Q untouched) if some rho or T is not positive and finite, or u is not finite. */
+int orc_q_from_prim(int ncell, const double* rho, const double* u1, const double* u2,
+                    const double* T, double* Q);
+
 /* ---- building blocks exposed for the pin tests ---- */
 
 /* Primitive variables of one cell: out = (rho, u1, u2, T, P11, P12, P22, tau). */

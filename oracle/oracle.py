@@ -58,6 +58,8 @@ def lib():
         L.orc_dt_for_cfl.restype = ctypes.c_double
         L.orc_prims.argtypes = [P, _c_double_p, _c_double_p]
         L.orc_prims.restype = ctypes.c_int
+        L.orc_q_from_prim.argtypes = [ctypes.c_int] + [_c_double_p] * 5
+        L.orc_q_from_prim.restype = ctypes.c_int
         L.orc_maxwellian_gauss.argtypes = [P, _c_double_p, ctypes.c_double, ctypes.c_double,
                                            _c_double_p, _c_double_p]
         L.orc_maxwellian_gauss.restype = None
@@ -245,6 +247,20 @@ def dt_for_cfl(grid, cfl, t_final, form):
     dt = lib().orc_dt_for_cfl(ctypes.byref(gg), float(cfl), float(t_final), int(form),
                               ctypes.byref(n))
     return dt, n.value
+
+
+def q_from_prim(rho, u1, u2, T):
+    """Q [6][...] from primitive fields of equal shape with an isotropic temperature tensor
+    (orc_q_from_prim)."""
+    fields = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, u1, u2, T)]
+    shape = fields[0].shape
+    if any(f.shape != shape for f in fields):
+        raise ValueError("rho, u1, u2, T must have the same shape")
+    n = int(np.prod(shape))
+    Q = np.zeros((6,) + shape)
+    if lib().orc_q_from_prim(n, *[_ptr(f) for f in fields], _ptr(Q)):
+        raise OracleError("non-physical primitive state")
+    return Q
 
 
 def prims(params, q):

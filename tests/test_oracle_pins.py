@@ -375,3 +375,46 @@ def test_euler_limit_sod():
         errs.append(np.mean(np.abs(Q[0, 0] - ex[0])))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 0.02
+
+
+def test_q_from_prim_printed_initial_states():
+    """The conservative initial states printed for the cylindrical Sod problem (Section 6.2) and
+    the lid-driven cavity (Section 6.3) follow from their primitive fields."""
+    gold = json.load(open(os.path.join(GOLDEN, "initial_states.json")))
+    for case in gold["cases"]:
+        rho, u1, u2, T = (np.array([v]) for v in case["prim"])
+        Q = O.q_from_prim(rho, u1, u2, T)[:, 0]
+        assert np.array_equal(Q, np.array(case["Q"])), case["name"]
+
+
+def test_q_from_prim_round_trip_and_energy():
+    """Q from (rho, u, T) gives back rho, u, T, an isotropic pressure tensor rho T I and the energy
+    (1/2) tr E = (1/2) rho (|u|^2 + 2 T) of Section 2 (d_v = 2); a swapped or dropped term in any
+    component breaks one of them."""
+    rng = np.random.default_rng(5)
+    n = 64
+    rho = rng.uniform(0.1, 3.0, n)
+    u1, u2 = rng.uniform(-2.0, 2.0, n), rng.uniform(-2.0, 2.0, n)
+    T = rng.uniform(0.2, 4.0, n)
+    Q = O.q_from_prim(rho, u1, u2, T)
+    p = I.Params()
+    for c in range(n):
+        out = O.prims(p, Q[:, c])
+        assert np.allclose(out[:4], [rho[c], u1[c], u2[c], T[c]], rtol=1e-13, atol=1e-13)
+        P = rho[c] * T[c]
+        assert np.allclose(out[4:7], [P, 0.0, P], rtol=1e-12, atol=1e-12 * P)
+    energy = 0.5 * (Q[3] + Q[5])
+    assert np.allclose(energy, 0.5 * rho * (u1 ** 2 + u2 ** 2 + 2.0 * T), rtol=1e-14)
+
+
+@pytest.mark.parametrize("bad", ["rho", "T", "u"])
+def test_q_from_prim_rejects_non_physical(bad):
+    rho, u1, u2, T = (np.ones(3) for _ in range(4))
+    if bad == "rho":
+        rho[1] = 0.0
+    elif bad == "T":
+        T[2] = -1.0
+    else:
+        u1[0] = np.nan
+    with pytest.raises(O.OracleError):
+        O.q_from_prim(rho, u1, u2, T)
