@@ -93,8 +93,30 @@ typedef struct mm_ctx mm_ctx;
 mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
                     mm_ctx** out);
 
-/* Device bytes mm_create allocates for this problem (state, scratch and flags). */
+/* Device bytes mm_create allocates for this problem (state, scratch and flags; the scratch
+ * pieces counted rounded up to 256 bytes).  0 for an invalid grid or parameters. */
 size_t mm_device_bytes(const mm_grid* grid, const mm_params* params);
+
+/* Bytes of caller scratch that mm_create_borrowed needs for this problem: every device buffer of
+ * a context except Q and G (split-step copy of g, macro scratch, heat flux, per-cell
+ * coefficients, row sums, Maxwellian factors, error word, diffuse-wall cell list), each rounded
+ * up to 256 bytes.  0 for an invalid grid or parameters. */
+size_t mm_scratch_bytes(const mm_grid* grid, const mm_params* params);
+
+/* Create a context on caller-owned device memory (e.g. the storage of framework tensors), which
+ * must outlive the context and which the context never frees:
+ *   Q_dev       [6][ny][nx] doubles, 16-byte aligned: the macro state, updated in place;
+ *   G_dev       [ny][nx][nv2][nv1] elements of the context's precision (double, or float for
+ *               MM_PREC_G_FP32), 256-byte aligned: g, which holds the state whenever mm_step or
+ *               a setter returns (FP32 g alternates between G_dev and a scratch copy inside
+ *               mm_step, which copies it back to G_dev at the end of the call when needed);
+ *   scratch_dev scratch_bytes >= mm_scratch_bytes(grid, params), 256-byte aligned.
+ * Optional features enabled later (learned closure, manufactured-solution harness, mm_step_host
+ * streams) allocate their own buffers, owned and freed by the context.  MM_ERR_INVALID_ARG for an
+ * invalid grid or parameters, a NULL or misaligned pointer or too little scratch. */
+mm_status mm_create_borrowed(const mm_grid* grid, const mm_params* params, void* cuda_stream,
+                             double* Q_dev, void* G_dev, void* scratch_dev, size_t scratch_bytes,
+                             mm_ctx** out);
 
 /* Copy the state in from host memory: Q_host [6][ny][nx], G_host [ny][nx][nv2][nv1] (NULL
  * means g = 0).  Synchronous with respect to the host buffers (they may be reused on return). */
@@ -102,6 +124,16 @@ mm_status mm_set_state(mm_ctx* ctx, const double* Q_host, const double* G_host);
 
 /* Same from caller-owned FP64 device memory; asynchronous on the context stream. */
 mm_status mm_set_state_device(mm_ctx* ctx, const double* Q_dev, const double* G_dev);
+
+/* Set the state from host primitive fields rho, u1, u2, T, each [ny][nx], with an isotropic
+ * temperature tensor and g = 0, as the paper's examples start (Section 6): Q = (rho, rho u1,
+ * rho u2, E11, E12, E22) with the energy tensor E = rho (u (x) u + T I) of Section 2 (ES-BGK
+ * operator), formed on the device as E11 = rho (u1 u1 + T), E12 = rho (u1 u2),
+ * E22 = rho (u2 u2 + T), each operation rounded once in that order.  Synchronous with respect to
+ * the host buffers.  MM_ERR_INVALID_ARG for a NULL field, rho or T not positive and finite, or u
+ * not finite (the state is then unchanged). */
+mm_status mm_set_state_prim(mm_ctx* ctx, const double* rho, const double* u1, const double* u2,
+                            const double* T);
 
 /* Advance nsteps time steps of size dt at Knudsen number eps (Section 5: micro x sweep, micro y
  * sweep, backward-Euler relaxation, heat-flux moments, then the Strang-split macro update).

@@ -48,7 +48,8 @@ class mm1d_params(ctypes.Structure):
 TAU1D_HARDSPHERE, TAU1D_CONST = 0, 1
 
 
-EXPORTS = ["mm_create", "mm_device_bytes", "mm_set_state", "mm_set_state_device", "mm_step",
+EXPORTS = ["mm_create", "mm_create_borrowed", "mm_scratch_bytes", "mm_device_bytes",
+           "mm_set_state", "mm_set_state_device", "mm_set_state_prim", "mm_step",
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
            "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp", "mm_step_host",
@@ -86,6 +87,10 @@ def load(build_if_needed: bool = True):
     L.mm_create.argtypes = [G, P, vp, ctypes.POINTER(vp)]
     L.mm_device_bytes.argtypes = [G, P]
     L.mm_device_bytes.restype = ctypes.c_size_t
+    L.mm_scratch_bytes.argtypes = [G, P]
+    L.mm_scratch_bytes.restype = ctypes.c_size_t
+    L.mm_create_borrowed.argtypes = [G, P, vp, vp, vp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.mm_set_state_prim.argtypes = [vp, vp, vp, vp, vp]
     L.mm_set_state.argtypes = [vp, vp, vp]
     L.mm_set_state_device.argtypes = [vp, vp, vp]
     L.mm_step.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
@@ -247,6 +252,24 @@ def mm_create(grid, params, stream=0):
     return ctx
 
 
+def mm_scratch_bytes(grid, params):
+    g, p = to_c_grid(grid), to_c_params(params)
+    return load().mm_scratch_bytes(ctypes.byref(g), ctypes.byref(p))
+
+
+def mm_create_borrowed(grid, params, Q_ptr, G_ptr, scratch_ptr, scratch_bytes, stream=0):
+    """A context on caller-owned device memory given as integer addresses (mm_create_borrowed);
+    returns (status, ctx)."""
+    L = load()
+    g, p = to_c_grid(grid), to_c_params(params)
+    ctx = ctypes.c_void_p()
+    st = L.mm_create_borrowed(ctypes.byref(g), ctypes.byref(p), ctypes.c_void_p(int(stream)),
+                              ctypes.c_void_p(int(Q_ptr)), ctypes.c_void_p(int(G_ptr)),
+                              ctypes.c_void_p(int(scratch_ptr)), int(scratch_bytes),
+                              ctypes.byref(ctx))
+    return st, ctx
+
+
 def mm_step_static_scratch(grid, params, Q_dev, G_dev, H_dev, dt, eps, nsteps, stream=0):
     """Advance nsteps steps in place on caller-owned FP64 CUDA tensors Q [6][ny][nx],
     G [ny][nx][nv2][nv1] and H [4][ny][nx] (output) without any device allocation: the scratch
@@ -290,12 +313,29 @@ def _check(ctx, st, what):
 class Solver:
     """One device context: state (Q, G, H) of a problem on the GPU."""
 
-    def __init__(self, grid, params, stream=0):
+    def __init__(self, grid, params, stream=0, borrow=None):
+        """borrow = (Q, G, scratch): CUDA tensors that the context works in instead of its own
+        allocations (mm_create_borrowed): Q float64 [6][ny][nx], G [ny][nx][nv2][nv1] float64 (or
+        float32 for FP32 g), scratch a byte tensor of at least mm_scratch_bytes(grid, params);
+        they must outlive the context."""
         self.grid, self.params = grid, params
         self.ncell = grid.nx * grid.ny
         self.nphase = self.ncell * grid.nv1 * grid.nv2
-        self.ctx = mm_create(grid, params, stream)
         self.L = load()
+        self.borrow = borrow
+        if borrow is None:
+            self.ctx = mm_create(grid, params, stream)
+        else:
+            Q, G, S = borrow
+            assert Q.is_cuda and Q.dtype.itemsize == 8 and Q.is_contiguous()
+            assert Q.numel() == 6 * self.ncell
+            assert G.is_cuda and G.is_contiguous() and G.numel() == self.nphase
+            assert S.is_cuda and S.is_contiguous()
+            st, ctx = mm_create_borrowed(grid, params, Q.data_ptr(), G.data_ptr(), S.data_ptr(),
+                                         S.numel() * S.element_size(), stream)
+            if st != MM_OK:
+                raise MMError(st, "mm_create_borrowed rejected the grid/parameters or buffers")
+            self.ctx = ctx
 
     def close(self):
         if self.ctx:
@@ -325,6 +365,13 @@ class Solver:
             st = self.L.mm_set_state(self.ctx, _host_ptr(Q, 6 * self.ncell),
                                      _host_ptr(G, self.nphase))
         _check(self.ctx, st, "mm_set_state")
+
+    def set_state_prim(self, rho, u1, u2, T):
+        """State from host primitive fields [ny][nx] with an isotropic temperature tensor and
+        g = 0 (mm_set_state_prim)."""
+        f = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, u1, u2, T)]
+        st = self.L.mm_set_state_prim(self.ctx, *[_host_ptr(a, self.ncell) for a in f])
+        _check(self.ctx, st, "mm_set_state_prim")
 
     def step(self, dt, eps, nsteps=1):
         _check(self.ctx, self.L.mm_step(self.ctx, float(dt), float(eps), int(nsteps)), "mm_step")

@@ -2,7 +2,9 @@
 // one time step (Section 5 of Rossmanith & Sar, arXiv 2509.21832: prims of Q^n, micro x sweep,
 // micro y sweep + relaxation + heat flux, macro collision/x transport, macro y transport/
 // collision), per-kernel event timing and error latching.
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -63,6 +65,10 @@ struct mm_ctx {
   int* wall_cells = nullptr;
   int n_wall = 0;
   bool have_state = false;
+  // mm_create_borrowed: Q, G and the scratch buffers belong to the caller; user_G is the caller's
+  // g buffer, which holds the state whenever a call returns (FP32 g ping-pongs inside mm_step)
+  bool borrowed = false;
+  void* user_G = nullptr;
   std::string last_error;
   // learned closure (FP64 contexts): network, threshold and per-cell buffers
   const mm_mlp* mlp = nullptr;
@@ -494,49 +500,12 @@ mm_status copy_g_out(mm_ctx* c, double* dst) {
   return MM_OK;
 }
 
-}  // namespace
 
-extern "C" {
-
-size_t mm_device_bytes(const mm_grid* g, const mm_params* p) {
-  if (!validate(g, p).empty()) return 0;
-  const size_t nc = (size_t)g->nx * g->ny;
-  const size_t np = nc * g->nv1 * g->nv2;
-  const size_t gs = p->precision == MM_PREC_G_FP32 ? sizeof(float) : sizeof(double);
-  size_t nwall = 0;
-  for (int j = 0; j < g->ny; ++j)
-    for (int i = 0; i < g->nx; ++i)
-      if ((i == 0 && p->bc[0] == MM_BC_DIFFUSE) || (i == g->nx - 1 && p->bc[1] == MM_BC_DIFFUSE) ||
-          (j == 0 && p->bc[2] == MM_BC_DIFFUSE) || (j == g->ny - 1 && p->bc[3] == MM_BC_DIFFUSE))
-        ++nwall;
-  const bool diff = p->bc[0] == MM_BC_DIFFUSE || p->bc[1] == MM_BC_DIFFUSE ||
-                    p->bc[2] == MM_BC_DIFFUSE || p->bc[3] == MM_BC_DIFFUSE;
-  const size_t pf = p->precision == MM_PREC_G_FP32
-                        ? (NPRIMF + 8) * nc * sizeof(float) + (diff ? np * sizeof(float) : 0)
-                        : 0;
-  const MicroShape ms = micro_shape(g->nv1, g->nv2);
-  const size_t rows = p->precision == MM_PREC_FP64 && ms.R == 1 && ms.threads == 32
-                          ? 3 * nc * (size_t)g->nv1 * sizeof(double)
-                          : 0;
-  const size_t etab = p->precision == MM_PREC_FP64
-                          ? ((size_t)g->nv1 + g->nv2) * nc * sizeof(double)
-                          : 0;
-  return 2 * np * gs + (6 + 4 + NPRIM) * nc * sizeof(double) +
-         macro_doubles(g->nx, g->ny) * sizeof(double) + pf + sizeof(int) + nwall * sizeof(int) +
-         rows + etab;
-}
-
-mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
-                    mm_ctx** out) {
-  if (!out) return MM_ERR_INVALID_ARG;
-  *out = nullptr;
-  const std::string v = validate(grid, params);
-  if (!v.empty()) return MM_ERR_INVALID_ARG;
-  mm_ctx* c = new mm_ctx();
+// Everything of a context but its device buffers: grid and parameters in kernel form, launch
+// shape, sizes and the diffuse-wall cell list.
+void init_shape(mm_ctx* c, const mm_grid* grid, const mm_params* params, std::vector<int>& walls) {
   c->grid = *grid;
   c->params = *params;
-  c->stream = static_cast<cudaStream_t>(cuda_stream);
-  cudaGetDevice(&c->device);
   c->fp32 = params->precision == MM_PREC_G_FP32;
   c->ncell = (size_t)grid->nx * grid->ny;
   c->nphase = c->ncell * grid->nv1 * grid->nv2;
@@ -564,46 +533,87 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
   }
   kp.keep_es = params->wall_keep_es_term ? 1 : 0;
   c->ms = micro_shape(grid->nv1, grid->nv2);
-
-  const size_t gsz = c->fp32 ? sizeof(float) : sizeof(double);
-  cudaError_t e = cudaSuccess;
-  auto alloc = [&](void** ptr, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes > 0 ? bytes : 1);
-  };
-  alloc(&c->G, c->nphase * gsz);
-  alloc(&c->Gs, c->nphase * gsz > 16 ? c->nphase * gsz : 16);  // also stages FP64 chunks
-  alloc((void**)&c->Q, 6 * c->ncell * sizeof(double));
-  alloc((void**)&c->macro, macro_doubles(grid->nx, grid->ny) * sizeof(double));
-  alloc((void**)&c->H, 4 * c->ncell * sizeof(double));
-  if (c->fp32) alloc((void**)&c->Hf, 8 * c->ncell * sizeof(float));
-  const bool any_diffuse = kp.bc[0] == MM_BC_DIFFUSE || kp.bc[1] == MM_BC_DIFFUSE ||
-                           kp.bc[2] == MM_BC_DIFFUSE || kp.bc[3] == MM_BC_DIFFUSE;
-  if (c->fp32 && any_diffuse) alloc(&c->Gexp, c->nphase * gsz);
-  alloc((void**)&c->prim, NPRIM * c->ncell * sizeof(double));
-  if (c->fp32) alloc((void**)&c->primf, NPRIMF * c->ncell * sizeof(float));
-  // row sums for the FP64 sweeps that run one warp per cell with one row per pass
-  if (!c->fp32 && c->ms.R == 1 && c->ms.threads == 32)
-    alloc((void**)&c->rmom, 3 * c->ncell * grid->nv1 * sizeof(double));
-  // the Maxwellian factors e1, e2 of every cell, formed by the x sweep, read by the y sweep
-  if (!c->fp32) alloc((void**)&c->etab, c->ncell * (grid->nv1 + grid->nv2) * sizeof(double));
-  alloc((void**)&c->err, sizeof(int));
-  std::vector<int> walls;
+  walls.clear();
   for (int j = 0; j < grid->ny; ++j)
     for (int i = 0; i < grid->nx; ++i)
       if ((i == 0 && kp.bc[0] == MM_BC_DIFFUSE) || (i == grid->nx - 1 && kp.bc[1] == MM_BC_DIFFUSE) ||
           (j == 0 && kp.bc[2] == MM_BC_DIFFUSE) || (j == grid->ny - 1 && kp.bc[3] == MM_BC_DIFFUSE))
         walls.push_back(j * grid->nx + i);
   c->n_wall = (int)walls.size();
-  if (c->n_wall > 0) alloc((void**)&c->wall_cells, walls.size() * sizeof(int));
+}
+
+// Every device buffer of a context except Q and G, in a fixed order: mm_create allocates them,
+// mm_create_borrowed carves them from the caller's scratch and mm_scratch_bytes adds up their
+// sizes, so the three agree by construction.
+template <typename F>
+void scratch_plan(mm_ctx* c, F&& take) {
+  const size_t gsz = c->fp32 ? sizeof(float) : sizeof(double);
+  const KParams& kp = c->kp;
+  const bool any_diffuse = kp.bc[0] == MM_BC_DIFFUSE || kp.bc[1] == MM_BC_DIFFUSE ||
+                           kp.bc[2] == MM_BC_DIFFUSE || kp.bc[3] == MM_BC_DIFFUSE;
+  take(&c->Gs, std::max<size_t>(c->nphase * gsz, 16));  // also stages FP64 chunks
+  take((void**)&c->macro, macro_doubles(c->kg.nx, c->kg.ny) * sizeof(double));
+  take((void**)&c->H, 4 * c->ncell * sizeof(double));
+  if (c->fp32) take((void**)&c->Hf, 8 * c->ncell * sizeof(float));
+  if (c->fp32 && any_diffuse) take(&c->Gexp, c->nphase * gsz);
+  take((void**)&c->prim, NPRIM * c->ncell * sizeof(double));
+  if (c->fp32) take((void**)&c->primf, NPRIMF * c->ncell * sizeof(float));
+  // row sums for the FP64 sweeps that run one warp per cell with one row per pass
+  if (!c->fp32 && c->ms.R == 1 && c->ms.threads == 32)
+    take((void**)&c->rmom, 3 * c->ncell * c->kg.nv1 * sizeof(double));
+  // the Maxwellian factors e1, e2 of every cell, formed by the x sweep, read by the y sweep
+  if (!c->fp32) take((void**)&c->etab, c->ncell * (c->kg.nv1 + c->kg.nv2) * sizeof(double));
+  take((void**)&c->err, sizeof(int));
+  if (c->n_wall > 0) take((void**)&c->wall_cells, (size_t)c->n_wall * sizeof(int));
+}
+
+constexpr size_t kCarveAlign = 256;
+
+size_t carve_round(size_t bytes) { return (bytes + kCarveAlign - 1) / kCarveAlign * kCarveAlign; }
+
+struct Borrowed {
+  double* Q;
+  void* G;
+  char* scratch;
+  size_t bytes;
+};
+
+mm_status create_ctx(const mm_grid* grid, const mm_params* params, void* cuda_stream,
+                     const Borrowed* bw, mm_ctx** out) {
+  mm_ctx* c = new mm_ctx();
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&c->device);
+  std::vector<int> walls;
+  init_shape(c, grid, params, walls);
+  const size_t gsz = c->fp32 ? sizeof(float) : sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (!bw) {
+    auto alloc = [&](void** ptr, size_t bytes) {
+      if (e == cudaSuccess) e = cudaMalloc(ptr, bytes > 0 ? bytes : 1);
+    };
+    alloc(&c->G, c->nphase * gsz);
+    alloc((void**)&c->Q, 6 * c->ncell * sizeof(double));
+    scratch_plan(c, alloc);
+  } else {
+    c->borrowed = true;
+    c->G = c->user_G = bw->G;
+    c->Q = bw->Q;
+    size_t off = 0;
+    scratch_plan(c, [&](void** ptr, size_t bytes) {
+      *ptr = bw->scratch + off;
+      off += carve_round(bytes);
+    });
+  }
   if (e != cudaSuccess) {
     mm_destroy(c);
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA;
   }
   c->mb = carve_macro(c->macro, grid->nx, grid->ny);
-  if (c->fp32) c->nseg = fused_segments_f32(kg, c->ms);
+  if (c->fp32) c->nseg = fused_segments_f32(c->kg, c->ms);
   if (c->n_wall > 0)
-    e = cudaMemcpy(c->wall_cells, walls.data(), walls.size() * sizeof(int), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(c->wall_cells, walls.data(), walls.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->H, 0, 4 * c->ncell * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -615,14 +625,11 @@ mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_str
   return MM_OK;
 }
 
-mm_status mm_set_state(mm_ctx* c, const double* Q_host, const double* G_host) {
-  if (!c) return MM_ERR_INVALID_ARG;
-  if (!Q_host) return fail(c, MM_ERR_INVALID_ARG, "Q_host is NULL");
-  cudaError_t e = cudaMemcpyAsync(c->Q, Q_host, 6 * c->ncell * sizeof(double),
-                                  cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "copy Q in");
-  if (G_host) {
-    mm_status s = copy_g_in(c, G_host, cudaMemcpyHostToDevice);
+// g from G_src (or zero), then the closure validity and the row sums: the tail of the setters
+mm_status set_g(mm_ctx* c, const double* G_src, cudaMemcpyKind kind) {
+  cudaError_t e = cudaSuccess;
+  if (G_src) {
+    mm_status s = copy_g_in(c, G_src, kind);
     if (s != MM_OK) return s;
   } else {
     e = cudaMemsetAsync(c->G, 0, c->nphase * (c->fp32 ? sizeof(float) : sizeof(double)), c->stream);
@@ -634,8 +641,89 @@ mm_status mm_set_state(mm_ctx* c, const double* Q_host, const double* G_host) {
     c->cstale = false;
   }
   if (c->rmom) launch_row_sums(static_cast<const double*>(c->G), c->rmom, c->kg, c->stream);
+  return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
+                    mm_ctx** out) {
+  if (!out) return MM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!validate(grid, params).empty()) return MM_ERR_INVALID_ARG;
+  return create_ctx(grid, params, cuda_stream, nullptr, out);
+}
+
+// G and Q plus every other buffer of the plan (each counted rounded up to the carve alignment)
+size_t mm_device_bytes(const mm_grid* grid, const mm_params* params) {
+  if (!validate(grid, params).empty()) return 0;
+  const size_t nc = (size_t)grid->nx * grid->ny;
+  const size_t gs = params->precision == MM_PREC_G_FP32 ? sizeof(float) : sizeof(double);
+  return nc * grid->nv1 * grid->nv2 * gs + 6 * nc * sizeof(double) +
+         mm_scratch_bytes(grid, params);
+}
+
+size_t mm_scratch_bytes(const mm_grid* grid, const mm_params* params) {
+  if (!validate(grid, params).empty()) return 0;
+  mm_ctx c;
+  std::vector<int> walls;
+  init_shape(&c, grid, params, walls);
+  size_t total = 0;
+  scratch_plan(&c, [&](void**, size_t bytes) { total += carve_round(bytes); });
+  return total;
+}
+
+mm_status mm_create_borrowed(const mm_grid* grid, const mm_params* params, void* cuda_stream,
+                             double* Q_dev, void* G_dev, void* scratch_dev, size_t scratch_bytes,
+                             mm_ctx** out) {
+  if (!out) return MM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!validate(grid, params).empty()) return MM_ERR_INVALID_ARG;
+  if (!Q_dev || !G_dev || !scratch_dev) return MM_ERR_INVALID_ARG;
+  if ((uintptr_t)Q_dev % 16 != 0 || (uintptr_t)G_dev % kCarveAlign != 0 ||
+      (uintptr_t)scratch_dev % kCarveAlign != 0)
+    return MM_ERR_INVALID_ARG;
+  if (scratch_bytes < mm_scratch_bytes(grid, params)) return MM_ERR_INVALID_ARG;
+  const Borrowed bw{Q_dev, G_dev, static_cast<char*>(scratch_dev), scratch_bytes};
+  return create_ctx(grid, params, cuda_stream, &bw, out);
+}
+
+mm_status mm_set_state(mm_ctx* c, const double* Q_host, const double* G_host) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!Q_host) return fail(c, MM_ERR_INVALID_ARG, "Q_host is NULL");
+  cudaError_t e = cudaMemcpyAsync(c->Q, Q_host, 6 * c->ncell * sizeof(double),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy Q in");
+  mm_status st = set_g(c, G_host, cudaMemcpyHostToDevice);
+  if (st != MM_OK) return st;
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set state");
+  c->have_state = true;
+  return MM_OK;
+}
+
+mm_status mm_set_state_prim(mm_ctx* c, const double* rho, const double* u1, const double* u2,
+                            const double* T) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!rho || !u1 || !u2 || !T) return fail(c, MM_ERR_INVALID_ARG, "rho, u1, u2 and T are required");
+  for (size_t i = 0; i < c->ncell; ++i)
+    if (!(rho[i] > 0.0) || !(T[i] > 0.0) || !std::isfinite(rho[i]) || !std::isfinite(T[i]) ||
+        !std::isfinite(u1[i]) || !std::isfinite(u2[i]))
+      return fail(c, MM_ERR_INVALID_ARG, "rho and T must be positive and finite, u finite");
+  // the four fields go through the per-cell coefficient buffer, which the next step rewrites
+  const double* f[4] = {rho, u1, u2, T};
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < 4 && e == cudaSuccess; ++m)
+    e = cudaMemcpyAsync(c->prim + m * c->ncell, f[m], c->ncell * sizeof(double),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy primitive fields in");
+  launch_q_from_prim(c->prim, c->Q, (int)c->ncell, c->stream);
+  mm_status st = set_g(c, nullptr, cudaMemcpyHostToDevice);  // g = 0
+  if (st != MM_OK) return st;
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set state from primitive fields");
   c->have_state = true;
   return MM_OK;
 }
@@ -646,19 +734,8 @@ mm_status mm_set_state_device(mm_ctx* c, const double* Q_dev, const double* G_de
   cudaError_t e = cudaMemcpyAsync(c->Q, Q_dev, 6 * c->ncell * sizeof(double),
                                   cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "copy Q in");
-  if (G_dev) {
-    mm_status s = copy_g_in(c, G_dev, cudaMemcpyDeviceToDevice);
-    if (s != MM_OK) return s;
-  } else {
-    e = cudaMemsetAsync(c->G, 0, c->nphase * (c->fp32 ? sizeof(float) : sizeof(double)), c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "zero G");
-  }
-  if (c->cvalid) {
-    e = cudaMemsetAsync(c->cvalid, 1, c->ncell, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "reset closure validity");
-    c->cstale = false;
-  }
-  if (c->rmom) launch_row_sums(static_cast<const double*>(c->G), c->rmom, c->kg, c->stream);
+  mm_status st = set_g(c, G_dev, cudaMemcpyDeviceToDevice);
+  if (st != MM_OK) return st;
   c->have_state = true;
   return MM_OK;
 }
@@ -670,6 +747,12 @@ mm_status mm_step(mm_ctx* c, double dt, double eps, int nsteps) {
   if (nsteps < 0) return fail(c, MM_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (!c->have_state) return fail(c, MM_ERR_STATE, "mm_step before mm_set_state");
   for (int n = 0; n < nsteps; ++n) enqueue_step(c, dt, eps);
+  if (c->borrowed && c->G != c->user_G) {
+    // FP32 g ping-pongs between G and the scratch copy: leave the state in the caller's buffer
+    cudaMemcpyAsync(c->user_G, c->G, c->nphase * sizeof(float), cudaMemcpyDeviceToDevice,
+                    c->stream);
+    std::swap(c->G, c->Gs);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   return MM_OK;
@@ -955,6 +1038,12 @@ void mm_destroy(mm_ctx* c) {
       cudaStreamDestroy(t);
     }
   for (auto e : c->chunk_events) cudaEventDestroy(e);
+  if (c->borrowed) {  // Q, G and the scratch pieces belong to the caller
+    c->G = c->Gs = c->Gexp = nullptr;
+    c->Q = c->macro = c->H = c->prim = c->rmom = c->etab = nullptr;
+    c->Hf = c->primf = nullptr;
+    c->err = c->wall_cells = nullptr;
+  }
   cudaFree(c->G);
   cudaFree(c->Gs);
   cudaFree(c->Gexp);

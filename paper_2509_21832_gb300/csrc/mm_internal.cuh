@@ -74,6 +74,8 @@ MicroShape micro_shape(int nv1, int nv2);
 // Per-cell fields: launch_prims_uT writes every cell's (u1, u2, T) into prim, then
 // launch_prims the rest (it reads the neighbours' (u1, u2, T) there): always in this order.
 void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s);
+// Q [6][nc] from primitive fields P4 [4][nc] = (rho, u1, u2, T), isotropic temperature tensor
+void launch_q_from_prim(const double* P4, double* Q, int nc, cudaStream_t s);
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
                   double dt, double eps, int* err, cudaStream_t s);
 // The sweeps over the cells [cell0, cell0 + ncells) (ncells < 0: every cell from cell0 = 0).

@@ -6,6 +6,7 @@
 //    with the boundary rules of Sections 5.4.1, 5.4.2 and 6.3.
 // One thread per spatial cell.  A face flux is evaluated by both cells that share the face, from
 // the same operands in the same order, so both see bitwise the same value.
+#include <algorithm>
 #include <cmath>
 
 #include "mm_body_macro.cuh"
@@ -56,12 +57,32 @@ __global__ void k_h_unpack(const float* __restrict__ Hf, double* __restrict__ H,
     H[m * nc + c] = hscale * ((double)Hf[(2 * m) * nc + c] + (double)Hf[(2 * m + 1) * nc + c]);
 }
 
+// Q = (rho, rho u1, rho u2, E11, E12, E22) from primitive fields staged as P4 [4][nc] = (rho, u1,
+// u2, T) with an isotropic temperature tensor: E = rho (u (x) u + T I) (Section 2, ES-BGK
+// operator), as E11 = rho (u1 u1 + T), E12 = rho (u1 u2), E22 = rho (u2 u2 + T), every product
+// and sum rounded once in that order (no contraction).
+__global__ void k_q_from_prim(const double* __restrict__ P4, double* __restrict__ Q, int nc) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    const double rho = P4[c], u1 = P4[nc + c], u2 = P4[2 * nc + c], T = P4[3 * nc + c];
+    Q[c] = rho;
+    Q[nc + c] = __dmul_rn(rho, u1);
+    Q[2 * nc + c] = __dmul_rn(rho, u2);
+    Q[3 * nc + c] = __dmul_rn(rho, __dadd_rn(__dmul_rn(u1, u1), T));
+    Q[4 * nc + c] = __dmul_rn(rho, __dmul_rn(u1, u2));
+    Q[5 * nc + c] = __dmul_rn(rho, __dadd_rn(__dmul_rn(u2, u2), T));
+  }
+}
+
 }  // namespace
 
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
                   double dt, double eps, int* err, cudaStream_t s) {
   const int nc = g.nx * g.ny;
   k_prims<<<(nc + 127) / 128, 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, 1.0 / eps, err);
+}
+
+void launch_q_from_prim(const double* P4, double* Q, int nc, cudaStream_t s) {
+  if (nc > 0) k_q_from_prim<<<std::min((nc + 255) / 256, 152 * 8), 256, 0, s>>>(P4, Q, nc);
 }
 
 void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s) {

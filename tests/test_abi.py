@@ -98,3 +98,36 @@ def test_header_is_plain_c():
         if shutil.which("g++"):
             subprocess.check_call(["g++", "-x", "c++", "-std=c++17", "-Wall", "-Werror",
                                    "-fsyntax-only", "-I" + inc, src])
+
+
+def test_scratch_bytes_bookkeeping():
+    """mm_device_bytes = g + Q + mm_scratch_bytes; every scratch piece is rounded to 256 bytes; an
+    invalid problem needs 0."""
+    for g, p, gsz in [(I.Grid(nx=20, ny=12, nv1=32, nv2=32), I.Params(bc=(I.SPECULAR,) * 4), 8),
+                      (I.Grid(nx=9, ny=18, nv1=24, nv2=24),
+                       I.Params(bc=(I.EXTRAP, I.EXTRAP, I.DIFFUSE, I.EXTRAP),
+                                precision=I.PREC_G_FP32), 4)]:
+        nc = g.nx * g.ny
+        s = api.mm_scratch_bytes(g, p)
+        assert s > 0 and s % 256 == 0
+        assert api.mm_device_bytes(g, p) == nc * g.nv1 * g.nv2 * gsz + 6 * nc * 8 + s
+        # at least the split-step copy of g, the heat flux and the per-cell coefficients
+        assert s >= nc * g.nv1 * g.nv2 * gsz + 4 * nc * 8
+    bad = I.Grid(nx=0, ny=4)
+    assert api.mm_scratch_bytes(bad, I.Params()) == 0
+
+
+def test_create_borrowed_rejects_bad_buffers_without_gpu_work():
+    """Argument checks of mm_create_borrowed come before any device call: NULL pointers,
+    misalignment and too little scratch are MM_ERR_INVALID_ARG."""
+    g, p = I.Grid(nx=8, ny=8, nv1=16, nv2=16), I.Params()
+    need = api.mm_scratch_bytes(g, p)
+    base = 1 << 20  # never dereferenced: every case fails its checks first
+    cases = [(0, base, base, need), (base, 0, base, need), (base, base, 0, need),
+             (base + 8, base, base, need), (base, base + 8, base, need),
+             (base, base, base + 128, need), (base, base, base, need - 1)]
+    for q, gg, sc, nb in cases:
+        st, _ = api.mm_create_borrowed(g, p, q, gg, sc, nb)
+        assert st == api.MM_ERR_INVALID_ARG, (q, gg, sc, nb)
+    st, _ = api.mm_create_borrowed(I.Grid(nx=0, ny=8), p, base, base, base, need)
+    assert st == api.MM_ERR_INVALID_ARG
