@@ -92,7 +92,7 @@ struct mm_ctx {
   double* mms_src_g = nullptr;           // source term of g^{n+1} (layout of G)
   double* mms_src_q = nullptr;           // int (1, v, v v) S dv [6][ny][nx]
   // mm_step_host: streams for the row-chunk copies of g and for the x sweeps; events per chunk
-  cudaStream_t cstream = nullptr, xstream = nullptr;
+  cudaStream_t cstream = nullptr, xstream = nullptr, ystream = nullptr;
   std::vector<cudaEvent_t> chunk_events;
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -176,21 +176,27 @@ void drain_timing(mm_ctx* c) {
   c->pending.clear();
 }
 
+// A launch timed by events on the stream it runs on (the context stream unless given).
 template <typename F>
-void timed(mm_ctx* c, int kind, F&& launch) {
+void timed_on(mm_ctx* c, int kind, cudaStream_t st, F&& launch) {
   if (!c->timing) {
     launch();
     return;
   }
   if (c->pending.size() > 50000) {
-    cudaStreamSynchronize(c->stream);
+    cudaDeviceSynchronize();
     drain_timing(c);
   }
   TimedLaunch t{kind, take_event(c), take_event(c)};
-  cudaEventRecord(t.a, c->stream);
+  cudaEventRecord(t.a, st);
   launch();
-  cudaEventRecord(t.b, c->stream);
+  cudaEventRecord(t.b, st);
   c->pending.push_back(t);
+}
+
+template <typename F>
+void timed(mm_ctx* c, int kind, F&& launch) {
+  timed_on(c, kind, c->stream, launch);
 }
 
 // The per-cell fields of Q^n (two kernels, each timed).
@@ -351,9 +357,12 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
   if (!c->cstream) e = cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking);
   if (e == cudaSuccess && !c->xstream)
     e = cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !c->ystream)
+    e = cudaStreamCreateWithFlags(&c->ystream, cudaStreamNonBlocking);
   const int nchunk = std::min(g.ny, kHostChunks);
-  // events: [0, n) chunk copied, [n, 2n) chunk x-swept, 2n entry, 2n+1 Q copied, 2n+2 fields
-  const int nev = 2 * nchunk + 3;
+  // events: [0, n) chunk copied, [n, 2n) chunk x-swept, 2n entry, 2n+1 Q copied, 2n+2 fields,
+  // 2n+3 the y sweeps of the second stream done
+  const int nev = 2 * nchunk + 4;
   while (e == cudaSuccess && (int)c->chunk_events.size() < nev) {
     cudaEvent_t ev;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -363,7 +372,7 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
   cudaEvent_t* copied = c->chunk_events.data();
   cudaEvent_t* xswept = copied + nchunk;
   cudaEvent_t entry = copied[2 * nchunk], qin = copied[2 * nchunk + 1],
-              fields = copied[2 * nchunk + 2];
+              fields = copied[2 * nchunk + 2], ydone = copied[2 * nchunk + 3];
   double* G = static_cast<double*>(c->G);
   double* Gs = static_cast<double*>(c->Gs);
   const size_t row = (size_t)g.nx * g.nv1 * g.nv2;  // doubles of g per row of cells
@@ -399,10 +408,14 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
     launch_micro_x<double>(G, Gs, c->prim, g, p, dt, c->ms, c->xstream, c0, cn, c->etab);
     cudaEventRecord(xswept[r], c->xstream);
   }
+  // the y sweeps of consecutive chunks alternate between the context stream and a second
+  // stream: they write disjoint rows (of g, H and the row sums) and read only x-swept rows, so
+  // one chunk's last wave of CTAs can share the GPU with the next chunk's first
   auto ysweep = [&](int r, int after) {
-    cudaStreamWaitEvent(s, xswept[after], 0);
-    timed(c, T_MICRO_Y, [&] {
-      launch_micro_y<double>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, s, nullptr,
+    cudaStream_t ys = (r & 1) ? c->ystream : s;
+    cudaStreamWaitEvent(ys, xswept[after], 0);
+    timed_on(c, T_MICRO_Y, ys, [&] {
+      launch_micro_y<double>(Gs, G, c->H, c->prim, g, p, dt, eps, c->ms, c->err, ys, nullptr,
                              row0(r) * g.nx, (row0(r + 1) - row0(r)) * g.nx, c->rmom,
                              c->etab);
     });
@@ -411,6 +424,9 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
   const bool pery = p.bc[2] == MM_BC_PERIODIC;
   for (int r = pery && nchunk > 1 ? 1 : 0; r < nchunk; ++r) ysweep(r, std::min(r + 1, nchunk - 1));
   if (pery && nchunk > 1) ysweep(0, nchunk - 1);
+  // the second stream's sweeps (the last of them waited for every x sweep) before the rest
+  cudaEventRecord(ydone, c->ystream);
+  cudaStreamWaitEvent(s, ydone, 0);
   if (c->n_wall > 0)
     timed(c, T_MICRO_YW, [&] {
       launch_micro_y_wall<double>(Gs, G, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
@@ -1032,7 +1048,7 @@ void mm_destroy(mm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   destroy_events(c);
-  for (cudaStream_t t : {c->cstream, c->xstream})
+  for (cudaStream_t t : {c->cstream, c->xstream, c->ystream})
     if (t) {
       cudaStreamSynchronize(t);
       cudaStreamDestroy(t);
