@@ -205,8 +205,9 @@ def exchange_local(blocks, copies, states):
 
 def exchange(blocks, copies, rank, Q, G, group=None):
     """Refresh the halos of block `rank` (torch tensors Q, G of its extended grid) from its
-    neighbours and send them the cells they need: one isend and one irecv per neighbouring block,
-    Q and g of the face cells packed in one message, all posted before any is waited on."""
+    neighbours and send them the cells they need: per neighbouring block one message of Q and one
+    of g (each in its own dtype, so FP32 g travels as FP32) each way, all posted before any is
+    waited on."""
     import torch
     import torch.distributed as dist
     b = blocks[rank]
@@ -221,17 +222,18 @@ def exchange(blocks, copies, rank, Q, G, group=None):
             Gf[di] = Gf.index_select(0, si)
         elif s == rank:
             si = torch.as_tensor(src, device=Q.device)
-            msg = torch.cat([Qf.index_select(1, si).t().reshape(-1),
-                             Gf.index_select(0, si).reshape(-1)]).contiguous()
-            reqs.append(dist.isend(msg, dst=r, group=group))
+            for msg in (Qf.index_select(1, si).contiguous(), Gf.index_select(0, si).contiguous()):
+                reqs.append(dist.isend(msg, dst=r, group=group))
         elif r == rank:
-            buf = torch.empty(len(dst) * (6 + nv), dtype=Q.dtype, device=Q.device)
-            reqs.append(dist.irecv(buf, src=s, group=group))
-            recvs.append((dst, buf))
+            m = len(dst)
+            qb = torch.empty((6, m), dtype=Q.dtype, device=Q.device)
+            gb = torch.empty((m, nv), dtype=G.dtype, device=G.device)
+            reqs.append(dist.irecv(qb, src=s, group=group))
+            reqs.append(dist.irecv(gb, src=s, group=group))
+            recvs.append((dst, qb, gb))
     for q in reqs:
         q.wait()
-    for dst, buf in recvs:
-        m = len(dst)
+    for dst, qb, gb in recvs:
         di = torch.as_tensor(dst, device=Q.device)
-        Qf[:, di] = buf[:6 * m].reshape(m, 6).t()
-        Gf[di] = buf[6 * m:].reshape(m, nv)
+        Qf[:, di] = qb
+        Gf[di] = gb

@@ -14,16 +14,18 @@ from paper_2509_21832_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 CASES = [
-    ("periodic_32", 32, (I.PERIODIC,) * 4, 2, 2),
-    ("specular_diffuse_16", 16, (I.PERIODIC, I.PERIODIC, I.SPECULAR, I.DIFFUSE), 3, 2),
-    ("extrap_specular_32", 32, (I.EXTRAP, I.SPECULAR, I.PERIODIC, I.PERIODIC), 2, 2),
+    ("periodic_32", 32, (I.PERIODIC,) * 4, 2, 2, I.PREC_FP64),
+    ("specular_diffuse_16", 16, (I.PERIODIC, I.PERIODIC, I.SPECULAR, I.DIFFUSE), 3, 2, I.PREC_FP64),
+    ("extrap_specular_32", 32, (I.EXTRAP, I.SPECULAR, I.PERIODIC, I.PERIODIC), 2, 2, I.PREC_FP64),
+    ("fp32_g_specular_diffuse_24", 24, (I.PERIODIC, I.PERIODIC, I.DIFFUSE, I.SPECULAR), 2, 2,
+     I.PREC_G_FP32),
 ]
 
 
-@pytest.mark.parametrize("name,nv,bc,px,py", CASES, ids=[c[0] for c in CASES])
-def test_blocks_on_one_gpu_reproduce_the_undivided_step(name, nv, bc, px, py):
+@pytest.mark.parametrize("name,nv,bc,px,py,prec", CASES, ids=[c[0] for c in CASES])
+def test_blocks_on_one_gpu_reproduce_the_undivided_step(name, nv, bc, px, py, prec):
     grid = I.Grid(nx=24, ny=16, x0=0.0, x1=1.5, y0=0.0, y1=1.0, nv1=nv, nv2=nv)
-    params = I.Params(bc=bc)
+    params = I.Params(bc=bc, precision=prec)
     Q = I.smooth_state(grid, seed=31, umax=0.25, aniso=0.06)
     G = I.seeded_g(grid, seed=32, amp=0.02)
     dt = 0.4 / (8.0 * grid.nx + 8.0 * grid.ny)
@@ -35,8 +37,10 @@ def test_blocks_on_one_gpu_reproduce_the_undivided_step(name, nv, bc, px, py):
         Gu = s.get_g()
     blocks = halo.decompose(grid, params, px, py, w=2)
     copies = halo.plan(blocks)
+    gdt = torch.float32 if prec == I.PREC_G_FP32 else torch.float64
+    Gsrc = torch.from_numpy(G).to(gdt)
     states = [(Qb.cuda(), Gb.cuda()) for Qb, Gb in
-              halo.scatter(blocks, torch.from_numpy(Q), torch.from_numpy(G))]
+              halo.scatter(blocks, torch.from_numpy(Q), Gsrc)]
     solvers = []
     for b, (Qb, Gb) in zip(blocks, states):
         S = torch.empty(api.mm_scratch_bytes(b.grid, b.params), dtype=torch.uint8, device="cuda")
@@ -48,12 +52,14 @@ def test_blocks_on_one_gpu_reproduce_the_undivided_step(name, nv, bc, px, py):
             if n:
                 halo.exchange_local(blocks, copies, states)
             for sv, (Qb, Gb) in zip(solvers, states):
-                sv.set_state(Qb.clone(), Gb.clone())  # halos in, row sums re-formed
+                # halos in (row sums re-formed); FP32 g goes in through its FP64 image, which
+                # rounds back to the same FP32 values
+                sv.set_state(Qb.clone(), Gb.double())
                 sv.step(dt, eps, 1)
         for sv in solvers:
             sv.sync()
         Qs, Gs = torch.zeros(Q.shape, dtype=torch.float64), torch.zeros(G.shape, dtype=torch.float64)
-        halo.gather(blocks, [(Qb.cpu(), Gb.cpu()) for Qb, Gb in states], Qs, Gs)
+        halo.gather(blocks, [(Qb.cpu(), Gb.cpu().double()) for Qb, Gb in states], Qs, Gs)
     finally:
         for sv in solvers:
             sv.close()
