@@ -153,6 +153,28 @@ def cpu_baseline(pr, rows, steps):
     return sub.nphase * steps / t, t, O.num_threads(), sub
 
 
+def cpu_single_thread(args, rows, steps):
+    """The same oracle timing with one OpenMP thread, in a child process (the thread count is
+    fixed when the library loads): phase-cell updates/s over `steps` steps of a strip of `rows`
+    rows of the workload, or None if the child fails."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "from paper_2509_21832_gb300 import inputs as I; "
+            "pr = I.bump_specular(n=%d, nv=%d, eps=%r, seed=0); "
+            "v, t, c, sub = bench.cpu_baseline(pr, %d, %d); "
+            "print(json.dumps([v, t, c, sub.nx, sub.ny, sub.nphase]))"
+            % (os.path.dirname(os.path.abspath(__file__)), args.n, args.nv, args.eps, rows, steps))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=300)
+        v, t, c, nx, ny, nph = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return {"value": v, "cores": c,
+            "sample": "%d steps of a %dx%d-row strip (%d phase cells), %.1f s"
+                      % (steps, nx, ny, nph, t)}
+
+
 def run_reference(args, pr, world, rank):
     if rank != 0:
         return
@@ -504,7 +526,8 @@ def main():
         v, t, cores, sub = cpu_baseline(pr, pr.grid.ny, n)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d steps of the full %dx%d grid (%d phase cells), %.1f s"
-                         % (n, sub.nx, sub.ny, sub.nphase, t)}
+                         % (n, sub.nx, sub.ny, sub.nphase, t),
+               "single_thread": cpu_single_thread(args, 32, 4)}
 
     variants = None
     if rank == 0 and not args.no_variants:
