@@ -33,7 +33,7 @@ namespace {
 struct BatchProb {
   KGrid g;
   KParams p;
-  double dt, eps, dtidx, dtidy, hscale;
+  double dt, eps, ieps, dtidx, dtidy, hscale;  // ieps = 1/eps, formed on the host
   long long g_off;    // offset of the problem's phase-space block (elements)
   long long mac_off;  // offset of its macro buffers (doubles)
   long long r_off;    // offset of its row sums (3 nv1 doubles per cell; nv1 <= 32 only)
@@ -59,14 +59,28 @@ __device__ __forceinline__ int find_prob(const int* __restrict__ start, int npro
   return lo;
 }
 
+// Per-cell fields in the two passes of the single-problem step (every cell's (u1, u2, T) first,
+// then the rest reading its neighbours' from there), so that every problem of a batch is stepped
+// bit for bit as by its own context.
+__global__ void k_batch_prims_uT(const double* __restrict__ Q, double* __restrict__ prim,
+                                 const BatchProb* __restrict__ pr, const int* __restrict__ start,
+                                 int nprob, int total) {
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total;
+       item += gridDim.x * blockDim.x) {
+    const BatchProb& b = pr[find_prob(start, nprob, item)];
+    macro_body::uT_body(Q + 6 * (size_t)b.c_off, prim + NPRIM * (size_t)b.c_off,
+                        b.g.nx * b.g.ny, item - b.c_off);
+  }
+}
+
 __global__ void k_batch_prims(const double* __restrict__ Q, double* __restrict__ prim,
                               const BatchProb* __restrict__ pr, const int* __restrict__ start,
                               int nprob, int total, int* __restrict__ err) {
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total;
        item += gridDim.x * blockDim.x) {
     const BatchProb& b = pr[find_prob(start, nprob, item)];
-    macro_body::prims_body(Q + 6 * (size_t)b.c_off, prim + NPRIM * (size_t)b.c_off, nullptr, b.g,
-                           b.p, b.dt, b.eps, 1.0 / b.eps, err, item - b.c_off);
+    macro_body::prims_body<true>(Q + 6 * (size_t)b.c_off, prim + NPRIM * (size_t)b.c_off, nullptr,
+                                 b.g, b.p, b.dt, b.eps, b.ieps, err, item - b.c_off);
   }
 }
 
@@ -237,6 +251,7 @@ void enqueue_batch_step(mm_batch* b) {
   const int cells = b->ncell;
   const int tb = 256;
   const int cgrid = std::min((cells + tb - 1) / tb, 152 * 16);
+  k_batch_prims_uT<<<cgrid, tb, 0, s>>>(b->Q, b->prim, b->d_prob, b->d_start, b->nprob, cells);
   k_batch_prims<<<cgrid, tb, 0, s>>>(b->Q, b->prim, b->d_prob, b->d_start, b->nprob, cells,
                                       b->err);
   k_batch_micro_x<<<C, T, smem_x(b), s>>>(b->G, b->Gs, b->prim, b->Rm, b->Ee, b->d_prob,
@@ -455,6 +470,8 @@ mm_status mm_batch_autotune(mm_batch* b, int* threads_out, int* ctas_out) {
   // were not kept for it under the previous shape); the trial y sweeps store none
   for (int q = 0; q < b->nprob; ++q) refresh_rows(b, q);
   // prims once so the coefficient fields are defined (uses the current dt, eps descriptors)
+  k_batch_prims_uT<<<std::min((b->ncell + 255) / 256, sms * 16), 256, 0, b->stream>>>(
+      b->Q, b->prim, b->d_prob, b->d_start, b->nprob, b->ncell);
   k_batch_prims<<<std::min((b->ncell + 255) / 256, sms * 16), 256, 0, b->stream>>>(
       b->Q, b->prim, b->d_prob, b->d_start, b->nprob, b->ncell, b->err);
   for (int T : tcands)
@@ -519,6 +536,7 @@ mm_status mm_batch_step(mm_batch* b, const double* dt, const double* eps, int ns
       BatchProb& d = b->hp[q];
       d.dt = dt[q];
       d.eps = eps[q];
+      d.ieps = 1.0 / eps[q];
       d.dtidx = dt[q] * d.g.idx;
       d.dtidy = dt[q] * d.g.idy;
       d.hscale = eps[q] * d.g.dv1 * d.g.dv2;

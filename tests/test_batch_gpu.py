@@ -80,3 +80,35 @@ def test_autotune_keeps_state_and_results():
     for (g, p, eps, Q, G, dt), (Qb, Hb, Gb) in zip(probs, tuned):
         Qo, Go, Ho = O.step(g, p, Q, G, dt, eps, 4)
         assert np.all(q_rel_err(Qb, Qo) <= 1e-12)
+
+
+def test_full_size_batch_matches_single_contexts():
+    """The benchmark's batch (64 periodic problems of 64-256 cells per side, 16^2 ... 32^2
+    velocity meshes, eps log-uniform on [1e-3, 1]; about 9.4e8 phase cells), autotuned as the
+    benchmark runs it: after two steps every problem's Q, H and g equal those of a single-problem
+    context bit for bit (the same device bodies run per cell; the single contexts are checked
+    against the oracle at full size in tests/test_parity_gpu.py)."""
+    probs = I.batch_problems(count=64, seed=0, nmin=64, nmax=256)
+    dts = [p.dt for p in probs]
+    epss = [p.eps for p in probs]
+    with api.BatchSolver([p.grid for p in probs], [p.params for p in probs]) as b:
+        for q, p in enumerate(probs):
+            b.set_state(q, p.Q, None)
+        b.step(dts, epss, 1)
+        for q, p in enumerate(probs):
+            b.set_state(q, p.Q, None)
+        b.autotune()
+        b.step(dts, epss, 2)
+        b.sync()
+        got = {}
+        for q in range(0, len(probs), 7):  # every 7th problem: all mesh sizes and eps decades
+            got[q] = b.get_moments(q) + (b.get_g(q),)
+    for q, (Qb, Hb, Gb) in got.items():
+        p = probs[q]
+        with api.Solver(p.grid, p.params) as s:
+            s.set_state(p.Q, None)
+            s.step(p.dt, p.eps, 2)
+            Qs, Hs = s.get_moments()
+            Gs = s.get_g()
+        assert np.array_equal(Qb, Qs) and np.array_equal(Hb, Hs) and np.array_equal(Gb, Gs), \
+            (q, p.grid.nx, p.grid.ny, p.grid.nv1, p.eps)
