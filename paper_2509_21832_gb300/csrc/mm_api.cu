@@ -359,7 +359,18 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
     e = cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking);
   if (e == cudaSuccess && !c->ystream)
     e = cudaStreamCreateWithFlags(&c->ystream, cudaStreamNonBlocking);
-  const int nchunk = std::min(g.ny, kHostChunks);
+  // row chunks of about ny / kHostChunks rows, the first two a quarter and a half of that: the
+  // sweeps start as soon as the first small chunk has arrived
+  std::vector<int> bounds{0};
+  {
+    const int full = std::max(1, (g.ny + kHostChunks - 1) / kHostChunks);
+    int rows = std::max(1, full / 4);
+    while (bounds.back() < g.ny) {
+      bounds.push_back(std::min(g.ny, bounds.back() + rows));
+      rows = std::min(full, 2 * rows);
+    }
+  }
+  const int nchunk = (int)bounds.size() - 1;
   // events: [0, n) chunk copied, [n, 2n) chunk x-swept, 2n entry, 2n+1 Q copied, 2n+2 fields,
   // 2n+3 the y sweeps of the second stream done
   const int nev = 2 * nchunk + 4;
@@ -376,7 +387,7 @@ mm_status enqueue_step_from_host(mm_ctx* c, const double* Q_host, const double* 
   double* G = static_cast<double*>(c->G);
   double* Gs = static_cast<double*>(c->Gs);
   const size_t row = (size_t)g.nx * g.nv1 * g.nv2;  // doubles of g per row of cells
-  auto row0 = [&](int r) { return (int)((long long)g.ny * r / nchunk); };
+  auto row0 = [&](int r) { return bounds[r]; };
   // the copies may overwrite Q and g only after the work already queued on the context stream;
   // host-to-device copies are served in issue order, so Q (which the per-cell fields need
   // first) goes ahead of the chunks of g
