@@ -62,3 +62,29 @@ def test_step_host_rejects_missing_buffers():
     with api.Solver(grid, I.Params()) as s:
         st = s.L.mm_step_host(s.ctx, None, None, 1e-3, 1e-2, None, None)
         assert st == api.MM_ERR_INVALID_ARG
+
+
+def test_step_host_full_size_benchmark_workload():
+    """The benchmark's end-to-end path at full size (256^2 x 32^2 bump, specular walls: 18 ramped
+    row chunks, y sweeps on two streams) against mm_set_state + mm_step + mm_get_moments: equal
+    to rounding (the x sweep sums per velocity here, from row sums there), twice in a row."""
+    pr = I.bump_specular(n=256, nv=32, eps=0.1, seed=0)
+    G = I.seeded_g(pr.grid, seed=5, amp=0.02)
+    with api.Solver(pr.grid, pr.params) as s:
+        s.set_state(pr.Q, G)
+        s.step(pr.dt, pr.eps, 1)
+        Q1, H1 = s.get_moments()
+        G1 = s.get_g()
+        s.step(pr.dt, pr.eps, 1)
+        Q2, H2 = s.get_moments()
+    with api.Solver(pr.grid, pr.params) as s:
+        s.set_state(pr.Q, None)
+        Qa, Ha = s.step_host(pr.Q, G, pr.dt, pr.eps)
+        Ga = s.get_g()
+        Qb, Hb = s.step_host(Qa, Ga, pr.dt, pr.eps)
+
+    def close(a, b):
+        return np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+
+    assert close(Qa, Q1) and close(Ha, H1) and close(Ga, G1)
+    assert close(Qb, Q2) and close(Hb, H2)
