@@ -231,3 +231,62 @@ def test_full_size_bump_specular_sampled(eps):
     # properties that hold at any size: specular walls conserve mass and energy to round-off
     assert abs(Q9[0].sum() - pr.Q[0].sum()) <= 1e-13 * pr.Q[0].sum()
     assert abs((Q9[3] + Q9[5]).sum() - (pr.Q[3] + pr.Q[5]).sum()) <= 1e-13 * (pr.Q[3] + pr.Q[5]).sum()
+
+
+def test_beyond_32bit_phase_offsets_sampled():
+    """More than 2^31 phase cells (the bump at 1536^2 x 32^2: 2.4e9 phase cells, about 40 GB on
+    the device, in the benchmark's launch configuration): one-step windows against the oracle,
+    among them cells in the top rows whose phase-space offsets exceed 2^31, plus mass and energy
+    conservation.  The state lives in CUDA tensors (mm_create_borrowed), so only the windows
+    cross to the host."""
+    import torch
+    pr = I.bump_specular(n=1536, nv=32, eps=1e-1, seed=0)
+    g = pr.grid
+    nc, nv = g.nx * g.ny, g.nv1 * g.nv2
+    assert nc * nv > 2 ** 31
+    Qt = torch.empty(6 * nc, dtype=torch.float64, device="cuda")
+    Gt = torch.empty(nc * nv, dtype=torch.float64, device="cuda")
+    St = torch.empty(api.mm_scratch_bytes(g, pr.params), dtype=torch.uint8, device="cuda")
+    Gv = Gt.view(g.ny, g.nx, g.nv2, g.nv1)
+    x0, y0 = pr.meta["x0"]
+    ic, jc = int(x0 * g.nx), int(y0 * g.ny)
+    targets = [(0, 0), (g.nx - 1, g.ny - 1), (g.nx - 1, 0), (0, g.ny - 1), (ic, jc),
+               (700, 1500), (1200, 1420), (g.nx // 2, g.ny - 1)]
+    w = 7
+    with api.Solver(g, pr.params, borrow=(Qt, Gt, St)) as s:
+        s.set_state(pr.Q, None)
+        s.step(pr.dt, pr.eps, 8)
+        s.sync()
+        Q8 = Qt.view(6, g.ny, g.nx).cpu().numpy()
+        wins = {}
+        for (ti, tj) in targets:
+            i0, j0 = max(0, ti - w // 2), max(0, tj - w // 2)
+            i1, j1 = min(g.nx, ti - w // 2 + w), min(g.ny, tj - w // 2 + w)
+            wins[(ti, tj)] = (i0, j0, i1, j1, Gv[j0:j1, i0:i1].cpu().numpy())
+        s.step(pr.dt, pr.eps, 1)
+        Q9, H9 = s.get_moments()
+        torch.cuda.synchronize()
+        gmax = max(float(Gt[k:k + (1 << 27)].abs().max()) for k in range(0, nc * nv, 1 << 27))
+        G9w = {t: Gv[t[1], t[0]].cpu().numpy() for t in targets}
+    gtol = max(1e-11 * gmax, g_floor(Q9, pr.eps))
+    htol = max(1e-11 * np.max(np.abs(H9)), h_floor(Q9))
+    dx, dy = (g.x1 - g.x0) / g.nx, (g.y1 - g.y0) / g.ny
+    for (ti, tj), (i0, j0, i1, j1, Gw) in wins.items():
+        sub = I.Grid(nx=i1 - i0, ny=j1 - j0, x0=g.x0 + i0 * dx, x1=g.x0 + i1 * dx,
+                     y0=g.y0 + j0 * dy, y1=g.y0 + j1 * dy, nv1=g.nv1, nv2=g.nv2,
+                     v1min=g.v1min, v1max=g.v1max, v2min=g.v2min, v2max=g.v2max)
+        bc = list(pr.params.bc)
+        bc[0] = bc[0] if i0 == 0 else I.EXTRAP
+        bc[1] = bc[1] if i1 == g.nx else I.EXTRAP
+        bc[2] = bc[2] if j0 == 0 else I.EXTRAP
+        bc[3] = bc[3] if j1 == g.ny else I.EXTRAP
+        p = I.Params(**{**pr.params.__dict__, "bc": tuple(bc)})
+        Qo, Go, Ho = O.step(sub, p, np.ascontiguousarray(Q8[:, j0:j1, i0:i1]), Gw, pr.dt,
+                            pr.eps, 1)
+        li, lj = ti - i0, tj - j0
+        scale = max(np.max(np.abs(Qo[0])), 1.0)
+        assert np.max(np.abs(Q9[:, tj, ti] - Qo[:, lj, li])) <= TOL_Q * scale, (ti, tj)
+        assert np.max(np.abs(G9w[(ti, tj)] - Go[lj, li])) <= gtol, (ti, tj)
+        assert np.max(np.abs(H9[:, tj, ti] - Ho[:, lj, li])) <= htol, (ti, tj)
+    assert abs(Q9[0].sum() - pr.Q[0].sum()) <= 1e-13 * pr.Q[0].sum()
+    assert abs((Q9[3] + Q9[5]).sum() - (pr.Q[3] + pr.Q[5]).sum()) <= 1e-13 * (pr.Q[3] + pr.Q[5]).sum()
