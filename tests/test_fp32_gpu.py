@@ -106,3 +106,25 @@ def test_fp32g_full_size_four_quadrant_vs_fp64():
     l1 = np.sum(np.abs(Q32[0] - Q64[0])) / np.sum(np.abs(Q64[0]))
     print("full size: relative L1 density error FP32-g vs FP64:", l1)
     assert l1 <= 1e-7
+
+
+def test_fp32g_beyond_32bit_phase_offsets_vs_fp64():
+    """The four-quadrant problem at 2048^2 x 24^2 (2.4e9 phase cells: offsets beyond 2^31 in the
+    staged FP32-g kernel, its wall export and the FP64 path) after 10 steps: every density finite
+    and positive and the relative L1 density error against the FP64 path at round-off level."""
+    pr = I.riemann4_diffuse(n=2048, nv=24, eps=1e-2, seed=0, nsteps=10)
+    assert pr.grid.nphase > 2 ** 31
+    p64 = I.Params(**{**pr.params.__dict__, "precision": I.PREC_FP64})
+    p32 = I.Params(**{**pr.params.__dict__, "precision": I.PREC_G_FP32})
+
+    def moments(params):
+        with api.Solver(pr.grid, params) as s:
+            s.set_state(pr.Q, None)
+            s.step(pr.dt, pr.eps, pr.nsteps)
+            return s.get_moments(with_H=False)[0]
+
+    Q64, Q32 = moments(p64), moments(p32)
+    assert np.all(np.isfinite(Q64)) and np.all(np.isfinite(Q32)) and np.all(Q32[0] > 0.0)
+    l1 = np.sum(np.abs(Q32[0] - Q64[0])) / np.sum(np.abs(Q64[0]))
+    print("2048^2 x 24^2: relative L1 density error FP32-g vs FP64:", l1)
+    assert l1 <= 1e-7
