@@ -283,6 +283,38 @@ def test_specular_mirror_symmetry():
     assert np.max(np.abs(G - G[:, ::-1, :, ::-1])) < 1e-12 * max(1e-300, np.max(np.abs(G)))
 
 
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_diffuse_walls_mirror_symmetry(axis):
+    """Two equal diffuse walls facing each other (same temperature; the same tangential speed for
+    walls normal to y, zero for walls normal to x) keep a mirror-symmetric state mirror-symmetric,
+    with and without the ES term of the wall-cell Ghat: the two sides of the wall treatment
+    (ghost Maxwellians, wall densities, upwind inflow, heat-flux faces) are mirror images of each
+    other.  A sign or index error on one side breaks it."""
+    g = I.Grid(nx=10, ny=8, nv1=12, nv2=12)
+    x, y = np.meshgrid(g.xc(), g.yc())
+    if axis == "x":
+        bc, wT, wU = (I.DIFFUSE, I.DIFFUSE, I.PERIODIC, I.PERIODIC), (1.2, 1.2, 1, 1), (0, 0, 0, 0)
+        rho = 1 + 0.3 * np.cos(2 * np.pi * x) + 0.1 * np.cos(2 * np.pi * y)
+        u1, u2 = 0.2 * np.sin(2 * np.pi * x), 0.05 * np.cos(2 * np.pi * y)
+        sgn = np.array([1, -1, 1, 1, -1, 1])[:, None, None]
+        mirror = lambda a: a[..., ::-1]  # noqa: E731
+        gmirror = lambda G: G[:, ::-1, :, ::-1]  # noqa: E731
+    else:
+        bc, wT, wU = (I.PERIODIC, I.PERIODIC, I.DIFFUSE, I.DIFFUSE), (1, 1, 0.9, 0.9), (0, 0, 0.2, 0.2)
+        rho = 1 + 0.3 * np.cos(2 * np.pi * y) + 0.1 * np.cos(2 * np.pi * x)
+        u1, u2 = 0.05 * np.cos(2 * np.pi * x), 0.2 * np.sin(2 * np.pi * y)
+        sgn = np.array([1, 1, -1, 1, -1, 1])[:, None, None]
+        mirror = lambda a: a[..., ::-1, :]  # noqa: E731
+        gmirror = lambda G: G[::-1, :, ::-1, :]  # noqa: E731
+    Q0 = I.q_from_prims(rho, u1, u2, 1.0)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    for keep in (1, 0):
+        p = I.Params(nu=-0.5, bc=bc, wall_T=wT, wall_U=wU, wall_keep_es_term=keep)
+        Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, 1e-2, 12)
+        assert np.max(np.abs(Q - sgn * mirror(Q))) < 1e-12, (axis, keep)
+        assert np.max(np.abs(G - gmirror(G))) < 1e-11 * np.max(np.abs(G)), (axis, keep)
+
+
 @pytest.mark.parametrize("bc,u", [((I.PERIODIC,) * 4, (0.4, -0.3)), ((I.SPECULAR,) * 4, (0.0, 0.0)),
                                   ((I.EXTRAP,) * 4, (0.3, 0.2)), ((I.DIFFUSE,) * 4, (0.0, 0.0))])
 def test_global_maxwellian_is_preserved(bc, u):
