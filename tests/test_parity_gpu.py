@@ -290,3 +290,31 @@ def test_beyond_32bit_phase_offsets_sampled():
         assert np.max(np.abs(H9[:, tj, ti] - Ho[:, lj, li])) <= htol, (ti, tj)
     assert abs(Q9[0].sum() - pr.Q[0].sum()) <= 1e-13 * pr.Q[0].sum()
     assert abs((Q9[3] + Q9[5]).sum() - (pr.Q[3] + pr.Q[5]).sum()) <= 1e-13 * (pr.Q[3] + pr.Q[5]).sum()
+
+
+@pytest.mark.parametrize("bc,u,nv,prec", [
+    ((I.PERIODIC,) * 4, (0.4, -0.3), 32, I.PREC_FP64),
+    ((I.SPECULAR,) * 4, (0.0, 0.0), 32, I.PREC_FP64),
+    ((I.EXTRAP,) * 4, (0.3, 0.2), 24, I.PREC_FP64),
+    ((I.DIFFUSE,) * 4, (0.0, 0.0), 16, I.PREC_FP64),
+    ((I.SPECULAR, I.SPECULAR, I.PERIODIC, I.PERIODIC), (0.0, 0.1), 24, I.PREC_G_FP32),
+    ((I.DIFFUSE,) * 4, (0.0, 0.0), 24, I.PREC_G_FP32),
+])
+def test_global_maxwellian_is_preserved_gpu(bc, u, nv, prec):
+    """A global Maxwellian (uniform rho, u, T; g = 0; walls at rest at the gas temperature) is a
+    fixed point of the scheme: on the GPU, Q stays put to round-off and g stays at round-off, for
+    every boundary kind that admits it, in both precisions of g (Sections 5.3-5.4: Z = 0 and
+    Zhat = 0 for an exact Maxwellian, Ghat = 0 without gradients, the KFVS faces cancel)."""
+    g = I.Grid(nx=14, ny=11, nv1=nv, nv2=nv)
+    p = I.Params(nu=-0.5, bc=bc, wall_T=(0.8,) * 4, precision=prec)
+    Q0 = I.q_from_prims(np.full((11, 14), 1.3), u[0], u[1], 0.8)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    with api.Solver(g, p) as s:
+        s.set_state(Q0, None)
+        s.step(dt, 1e-2, 25)
+        Q, _ = s.get_moments()
+        G = s.get_g()
+    tol_q = 1e-13 if prec == I.PREC_FP64 else 1e-6
+    assert np.max(np.abs(Q - Q0)) < tol_q, np.max(np.abs(Q - Q0))
+    # g of an exact equilibrium is round-off: FP64 sums, or FP32 storage of round-off
+    assert np.max(np.abs(G)) < (1e-11 if prec == I.PREC_FP64 else 1e-5), np.max(np.abs(G))
