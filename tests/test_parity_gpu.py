@@ -318,3 +318,19 @@ def test_global_maxwellian_is_preserved_gpu(bc, u, nv, prec):
     assert np.max(np.abs(Q - Q0)) < tol_q, np.max(np.abs(Q - Q0))
     # g of an exact equilibrium is round-off: FP64 sums, or FP32 storage of round-off
     assert np.max(np.abs(G)) < (1e-11 if prec == I.PREC_FP64 else 1e-5), np.max(np.abs(G))
+
+
+@pytest.mark.parametrize("eps", [1e-8, 1e30])
+@pytest.mark.parametrize("name,gk,bc,extra", [CASES[0], CASES[2], CASES[3]],
+                         ids=[CASES[0][0], CASES[2][0], CASES[3][0]])
+def test_extreme_knudsen_numbers(name, gk, bc, extra, eps):
+    """The asymptotic-preserving end (eps = 1e-8: g^{n+1} is Ghat^n up to O(eps), the relaxation
+    weights are 0 and 1 to within 1e-8) and free streaming (eps = 1e30: the collision weights are
+    exactly 1 and 0 in FP64, as in the paper's collisionless check, which starts from g = 0:
+    f = M + eps g, so a g of order one would be a non-physical f there) against the oracle."""
+    grid = I.Grid(**gk)
+    params = I.Params(bc=bc, **extra)
+    Q = I.smooth_state(grid, seed=zlib.crc32(name.encode()) % 1000, umax=0.25, aniso=0.08)
+    G = I.seeded_g(grid, seed=7, amp=0.02) if eps < 1.0 else I.zero_g(grid)
+    dt = O.dt_for_cfl(grid, 0.5, 0.0, I.CFL_SUM)[0]
+    check(grid, params, Q, G, dt, eps, 12)
