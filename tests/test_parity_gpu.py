@@ -334,3 +334,19 @@ def test_extreme_knudsen_numbers(name, gk, bc, extra, eps):
     G = I.seeded_g(grid, seed=7, amp=0.02) if eps < 1.0 else I.zero_g(grid)
     dt = O.dt_for_cfl(grid, 0.5, 0.0, I.CFL_SUM)[0]
     check(grid, params, Q, G, dt, eps, 12)
+
+
+@pytest.mark.parametrize("nv1,nv2,bc", [
+    (512, 4, (I.SPECULAR,) * 4),      # the widest v1 mesh: 512-thread CTAs, 16-warp reductions
+    (1, 1024, (I.PERIODIC,) * 4),     # one v1 column, the longest v2 mesh: 107 KB of y tables
+    (1, 1024, (I.SPECULAR, I.SPECULAR, I.DIFFUSE, I.EXTRAP)),
+])
+def test_velocity_mesh_limits(nv1, nv2, bc):
+    """The ends of the accepted velocity meshes (nv1 in 1..512, nv2 in 1..1024) against the
+    oracle on a 3 x 2 grid."""
+    grid = I.Grid(nx=3, ny=2, nv1=nv1, nv2=nv2)
+    params = I.Params(bc=bc, wall_T=(1.0, 1.0, 1.05, 1.0))
+    Q = I.smooth_state(grid, seed=nv1 + nv2, umax=0.2, aniso=0.05)
+    G = I.seeded_g(grid, seed=3, amp=0.02)
+    dt = O.dt_for_cfl(grid, 0.5, 0.0, I.CFL_SUM)[0]
+    check(grid, params, Q, G, dt, 1e-2, 4)
