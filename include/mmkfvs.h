@@ -89,7 +89,8 @@ typedef struct mm_ctx mm_ctx;
 /* Create a context and allocate its device state (owned by the context).  cuda_stream is a
  * cudaStream_t (NULL for the legacy default stream).  Validates the grid and parameters
  * (MM_ERR_INVALID_ARG), e.g. unpaired periodic sides, nu outside [-1, 1), a velocity mesh that is
- * not symmetric where a specular wall needs it. */
+ * not symmetric where a specular wall needs it, or (FP32 g) a velocity mesh whose fused kernel
+ * would need more shared memory than a CTA can have (three rows of G* per warp). */
 mm_status mm_create(const mm_grid* grid, const mm_params* params, void* cuda_stream,
                     mm_ctx** out);
 

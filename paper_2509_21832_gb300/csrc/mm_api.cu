@@ -126,6 +126,16 @@ std::string validate(const mm_grid* g, const mm_params* p) {
     return "tau0 must be > 0";
   if (p->precision != MM_PREC_FP64 && p->precision != MM_PREC_G_FP32) return "unknown precision";
   if (p->precision == MM_PREC_G_FP32 && g->nv1 > 32) return "MM_PREC_G_FP32 needs nv1 <= 32";
+  if (p->precision == MM_PREC_G_FP32) {
+    // the fused kernel keeps three rows of G* per warp in shared memory
+    KGrid kg{};
+    kg.nv1 = g->nv1;
+    kg.nv2 = g->nv2;
+    kg.v2min = g->v2min;
+    kg.dv2 = (g->v2max - g->v2min) / g->nv2;
+    if (fused_smem_f32(kg) > kMaxSmemPerCta)
+      return "MM_PREC_G_FP32: the velocity mesh is too large for the fused kernel's shared memory";
+  }
   for (int s = 0; s < 4; ++s) {
     if (p->bc[s] < 0 || p->bc[s] > 3) return "unknown boundary kind";
     if (p->bc[s] == MM_BC_DIFFUSE && !(p->wall_T[s] > 0.0)) return "diffuse wall needs wall_T > 0";

@@ -116,6 +116,10 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
 // butterflies and the heat flux leaves as (hi, lo) FP32 pairs Hf[8][ny][nx] that
 // launch_h_unpack combines in FP64.
 int fused_segments_f32(const KGrid& g, const MicroShape& ms);
+// Shared memory per CTA of the FP32-g kernel chosen for this mesh (bytes)
+size_t fused_smem_f32(const KGrid& g);
+// Opt-in shared memory per CTA of the target GPU (sm_103a)
+constexpr size_t kMaxSmemPerCta = 227 * 1024;
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
                             const MicroShape& ms, int nseg, int* err, cudaStream_t s);

@@ -1020,6 +1020,8 @@ static FusedPick pick_fused(const KGrid& g) {
 
 }  // namespace
 
+size_t fused_smem_f32(const KGrid& g) { return pick_fused(g).smem; }
+
 KGridF grid_f32(const KGrid& g) {
   return KGridF{(float)g.v1min, (float)g.v2min, (float)g.dv1, (float)g.dv2, (float)g.idx,
                 (float)g.idy};

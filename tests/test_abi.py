@@ -131,3 +131,15 @@ def test_create_borrowed_rejects_bad_buffers_without_gpu_work():
         assert st == api.MM_ERR_INVALID_ARG, (q, gg, sc, nb)
     st, _ = api.mm_create_borrowed(I.Grid(nx=0, ny=8), p, base, base, base, need)
     assert st == api.MM_ERR_INVALID_ARG
+
+
+def test_fp32_g_meshes_beyond_shared_memory_are_rejected():
+    """FP32 g keeps three rows of G* per warp in shared memory: velocity meshes whose kernel would
+    need more than the 227 KB a CTA can have are rejected when the problem is validated (before
+    any device work), the others accepted."""
+    p32 = I.Params(precision=I.PREC_G_FP32, bc=(I.PERIODIC,) * 4)
+    assert api.mm_device_bytes(I.Grid(nx=8, ny=8, nv1=32, nv2=100), p32) > 0
+    assert api.mm_device_bytes(I.Grid(nx=8, ny=8, nv1=32, nv2=128), p32) == 0
+    assert api.mm_device_bytes(I.Grid(nx=8, ny=8, nv1=32, nv2=1024), p32) == 0
+    # the FP64 kernels fit at every accepted mesh
+    assert api.mm_device_bytes(I.Grid(nx=8, ny=8, nv1=32, nv2=1024), I.Params()) > 0
