@@ -103,10 +103,12 @@ __device__ __forceinline__ void store_row_sums(double* __restrict__ Rm, int cell
   o[2 * nv1] = R2;
 }
 
-// The row sums of cell `cell` of G (blockDim >= nv1; thread k = column k).
+// The row sums of cell `cell` of G (blockDim >= nv1; thread k = column k); vt holds v2 and v2^2
+// of every row ([2][nv2], formed as fma(l + 1/2, dv2, v2min) and its square).
 template <typename Tg>
 __device__ __forceinline__ void row_sums_body(const Tg* __restrict__ G, double* __restrict__ Rm,
-                                              const KGrid& g, int cell) {
+                                              const KGrid& g, int cell,
+                                              const double* __restrict__ vt) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int k = threadIdx.x;
   if (k >= nv1) return;
@@ -121,11 +123,9 @@ __device__ __forceinline__ void row_sums_body(const Tg* __restrict__ G, double* 
     for (int m = 0; m < kB; ++m) {
       const int l = l0 + m;
       if (l < nv2) {
-        const double v2 = fma(l + 0.5, g.dv2, g.v2min);
-        const double v2q = v2 * v2;
         R0 += ov[m];
-        R1 = fma(v2, ov[m], R1);
-        R2 = fma(v2q, ov[m], R2);
+        R1 = fma(vt[l], ov[m], R1);
+        R2 = fma(vt[nv2 + l], ov[m], R2);
       }
     }
   }

@@ -60,10 +60,20 @@ __global__ void __launch_bounds__(32) k_micro_x_rows_list(const Tg* __restrict__
   }
 }
 
-// Row sums of the cells [cell0, cell0 + gridDim.x).
+// Row sums of the cells [cell0, cell0 + ncells): persistent one-warp CTAs, each tabulating v2 and
+// v2^2 of the rows once in shared memory.
 __global__ void __launch_bounds__(32) k_row_sums(const double* __restrict__ G,
-                                                 double* __restrict__ Rm, KGrid g, int cell0) {
-  row_sums_body<double>(G, Rm, g, cell0 + (int)blockIdx.x);
+                                                 double* __restrict__ Rm, KGrid g, int cell0,
+                                                 int ncells) {
+  extern __shared__ double vt[];
+  for (int l = threadIdx.x; l < g.nv2; l += 32) {
+    const double v2 = fma(l + 0.5, g.dv2, g.v2min);
+    vt[l] = v2;
+    vt[g.nv2 + l] = v2 * v2;
+  }
+  __syncwarp();
+  for (int q = blockIdx.x; q < ncells; q += gridDim.x)
+    row_sums_body<double>(G, Rm, g, cell0 + q, vt);
 }
 
 
@@ -267,7 +277,9 @@ void launch_micro_y_list(const Tg* Gs, Tg* Gout, double* H, const double* prim, 
 void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s, int cell0,
                      int ncells) {
   const int n = ncells < 0 ? g.nx * g.ny : ncells;
-  if (n > 0) k_row_sums<<<n, 32, 0, s>>>(G, Rm, g, cell0);
+  if (n > 0)
+    k_row_sums<<<std::min(n, 152 * 32), 32, 2 * (size_t)g.nv2 * sizeof(double), s>>>(G, Rm, g,
+                                                                                     cell0, n);
 }
 
 
