@@ -75,16 +75,26 @@ def _split(n, p):
     return edges
 
 
-def _exact_extent(lo, n, d):
-    """hi near lo + n d with (hi - lo) / n == d exactly (the library and the oracle both take the
-    cell size as (hi - lo) / n)."""
-    hi0 = lo + n * d
-    cand = hi0
-    for _ in range(4096):
-        if (cand - lo) / n == d:
-            return cand
-        cand = np.nextafter(cand, np.inf if (cand - lo) / n < d else -np.inf)
-    raise ValueError("no block extent reproduces the cell size %r exactly" % d)
+def _ulps(x, k):
+    """x moved by k units in the last place (down for k < 0)."""
+    for _ in range(abs(k)):
+        x = np.nextafter(x, np.inf if k > 0 else -np.inf)
+    return x
+
+
+def _exact_extent(lo0, n, d, span=48):
+    """(lo, hi) near (lo0, lo0 + n d) with (hi - lo) / n == d exactly (the library and the oracle
+    both take the cell size as (hi - lo) / n; positions enter neither's plain step), or None: not
+    every cell count admits one when d is not a dyadic fraction."""
+    for a in range(2 * span + 1):
+        lo = _ulps(lo0, (a + 1) // 2 * (1 if a % 2 else -1))  # lo0, +1, -1, +2, -2 ... ulps
+        hi = lo + n * d
+        for _ in range(span):
+            q = (hi - lo) / n
+            if q == d:
+                return float(lo), float(hi)
+            hi = np.nextafter(hi, np.inf if q < d else -np.inf)
+    return None
 
 
 def decompose(grid, params, px, py, w=2):
@@ -111,12 +121,35 @@ def decompose(grid, params, px, py, w=2):
                     continue  # a domain side with its own rule
                 halo[side] = w
                 bc[side] = I.EXTRAP  # placeholder beyond the halo
+            # along each axis: the block's extent with the undivided cell size to the last bit;
+            # where no extent of this cell count has it, one more halo cell at a time
+            ext = []
+            for (lo_side, hi_side, o0, o1, d, base) in ((0, 1, i0, i1, dx, grid.x0),
+                                                        (2, 3, j0, j1, dy, grid.y0)):
+                found = None
+                for extra in range(8):
+                    if extra and not (halo[lo_side] or halo[hi_side]):
+                        break  # the block spans the axis with its own rules: nothing to widen
+                    grow = hi_side if halo[hi_side] else lo_side
+                    h = list(halo)
+                    if extra:
+                        h[grow] += extra
+                    n = o1 - o0 + h[lo_side] + h[hi_side]
+                    if not (halo[lo_side] or halo[hi_side]):
+                        found = (h, (base, grid.x1 if lo_side == 0 else grid.y1))
+                        break
+                    lohi = _exact_extent(base + (o0 - h[lo_side]) * d, n, d)
+                    if lohi is not None:
+                        found = (h, lohi)
+                        break
+                if found is None:
+                    raise ValueError("no block extent reproduces the cell size %r exactly" % d)
+                halo[lo_side], halo[hi_side] = found[0][lo_side], found[0][hi_side]
+                ext.append(found[1])
             hl, hr, hb, ht = halo
             nxe, nye = i1 - i0 + hl + hr, j1 - j0 + hb + ht
-            x0e = grid.x0 + (i0 - hl) * dx
-            y0e = grid.y0 + (j0 - hb) * dy
-            g = replace(grid, nx=nxe, ny=nye, x0=x0e, x1=_exact_extent(x0e, nxe, dx),
-                        y0=y0e, y1=_exact_extent(y0e, nye, dy))
+            (x0e, x1e), (y0e, y1e) = ext
+            g = replace(grid, nx=nxe, ny=nye, x0=x0e, x1=x1e, y0=y0e, y1=y1e)
             assert (g.x1 - g.x0) / g.nx == dx and (g.y1 - g.y0) / g.ny == dy
             blocks.append(Block(by * px + bx, bx, by, i0, i1, j0, j1, hl, hr, hb, ht, g,
                                 replace(params, bc=tuple(bc)), grid.nx, grid.ny))

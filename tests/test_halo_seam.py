@@ -138,3 +138,76 @@ def test_stale_halos_change_the_result():
     Qs, Gs = np.zeros_like(Q), np.zeros_like(G)
     halo.gather(blocks, states, Qs, Gs)
     assert not np.array_equal(Qs, Qu) and not np.array_equal(Gs, Gu)
+
+
+@pytest.mark.parametrize("nx,ny,px,py,w", [(17, 13, 3, 2, 2), (16, 12, 2, 2, 3), (15, 9, 4, 1, 2)])
+def test_uneven_blocks_and_wider_halos(nx, ny, px, py, w):
+    """Block sizes that do not divide the grid (owned widths differ by one) and a halo wider than
+    needed give the undivided step as well; the extended grids keep the undivided cell sizes."""
+    grid = I.Grid(nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=0.8, nv1=8, nv2=8)
+    params = I.Params(bc=(I.PERIODIC, I.PERIODIC, I.SPECULAR, I.EXTRAP))
+    Q = I.smooth_state(grid, seed=41, umax=0.25, aniso=0.06)
+    G = I.seeded_g(grid, seed=42, amp=0.02)
+    dt = 0.4 / (8.0 * grid.nx + 8.0 * grid.ny)
+    Qu, Gu, _ = O.step(grid, params, Q, G, dt, 1e-2, STEPS)
+    blocks = halo.decompose(grid, params, px, py, w=w)
+    for b in blocks:
+        assert (b.grid.x1 - b.grid.x0) / b.grid.nx == (grid.x1 - grid.x0) / grid.nx
+        assert (b.grid.y1 - b.grid.y0) / b.grid.ny == (grid.y1 - grid.y0) / grid.ny
+    copies = halo.plan(blocks)
+    states = halo.scatter(blocks, Q, G)
+    for n in range(STEPS):
+        if n:
+            halo.exchange_local(blocks, copies, states)
+        states = [O.step(b.grid, b.params, Qb, Gb, dt, 1e-2, 1)[:2]
+                  for b, (Qb, Gb) in zip(blocks, states)]
+    Qs, Gs = np.zeros_like(Q), np.zeros_like(G)
+    halo.gather(blocks, states, Qs, Gs)
+    assert np.array_equal(Qs, Qu) and np.array_equal(Gs, Gu)
+
+
+def _rank2d(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+    from oracle import oracle as Orc
+    from paper_2509_21832_gb300 import halo as hl
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    grid, params, Q, G, dt, eps = problem((I.PERIODIC,) * 4)
+    blocks = hl.decompose(grid, params, 2, 2, w=2)
+    copies = hl.plan(blocks)
+    Qb, Gb = hl.scatter(blocks, Q, G)[rank]
+    b = blocks[rank]
+    for n in range(STEPS):
+        if n:
+            hl.exchange(blocks, copies, rank, torch.from_numpy(Qb), torch.from_numpy(Gb))
+        Qb, Gb, _ = Orc.step(b.grid, b.params, Qb, Gb, dt, eps, 1)
+    dist.barrier()
+    out.put((rank, Qb, Gb))
+    dist.destroy_process_group()
+
+
+def test_four_gloo_ranks_2x2_periodic():
+    """Four ranks in a 2 x 2 block grid, periodic in both directions: every rank exchanges faces
+    and corners with the other three (the corner cells of a halo come from the diagonal block)."""
+    import torch.multiprocessing as mp
+    grid, params, Q, G, dt, eps = problem((I.PERIODIC,) * 4)
+    Qu, Gu, _ = O.step(grid, params, Q, G, dt, eps, STEPS)
+    blocks = halo.decompose(grid, params, 2, 2, w=2)
+    peers = {r: {s for (s, rr) in halo.plan(blocks) if rr == r} for r in range(4)}
+    assert all(len(v) == 3 for v in peers.values())
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank2d, args=(r, 4, port, q)) for r in range(4)]
+    for p in ps:
+        p.start()
+    res = sorted((q.get(timeout=240) for _ in range(4)), key=lambda t: t[0])
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    Qs, Gs = np.zeros_like(Q), np.zeros_like(G)
+    halo.gather(blocks, [(Qb, Gb) for _, Qb, Gb in res], Qs, Gs)
+    assert np.array_equal(Qs, Qu) and np.array_equal(Gs, Gu)
