@@ -13,7 +13,6 @@ cores on a bounded sample of the same workload (a strip of rows per step).
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess

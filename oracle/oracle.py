@@ -6,7 +6,6 @@ nu, tau_model, tau0, bc, wall_T, wall_U, wall_keep_es_term) and numpy arrays in 
 Q[6][ny][nx], G[ny][nx][nv2][nv1], H[4][ny][nx].
 """
 import ctypes
-import os
 
 import numpy as np
 

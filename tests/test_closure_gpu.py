@@ -2,7 +2,6 @@
 Adam step against the FP64 CPU reference (same BF16 weights), the features and Chapman-Enskog
 flux against the closure oracle, one hybrid step against the oracle's hybrid step, and the
 trained network's gain over the plain method (speed at a stated density error)."""
-import math
 
 import numpy as np
 import pytest

@@ -5,7 +5,6 @@ quadrature, invariances of the features, and conservation of the hybrid step."""
 import math
 
 import numpy as np
-import pytest
 
 from oracle import closure_oracle as C
 from oracle import mlp_oracle as M

@@ -11,7 +11,7 @@ import zlib
 import numpy as np
 import pytest
 
-from helpers import q_rel_err, rel_max
+from helpers import q_rel_err
 from oracle import oracle as O
 from paper_2509_21832_gb300 import api
 from paper_2509_21832_gb300 import inputs as I
