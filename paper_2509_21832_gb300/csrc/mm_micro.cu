@@ -168,7 +168,7 @@ __global__ void k_f32_to_f64(const float* __restrict__ in, double* __restrict__ 
 int x_rows(const MicroShape& ms, int nv2);
 
 MicroShape micro_shape(int nv1, int nv2) {
-  MicroShape ms{1, 32, 0, 0};
+  MicroShape ms{1, 32, 0, 0, 0, 0};
   double best = -1.0;
   // nv1 <= 32: one warp per cell, R = 32 div nv1 rows per pass.  Measured on GB300 (FP64 step,
   // 160^2 cells): against CTAs of several warps with full lanes it is 1.2x faster at 24^2 and

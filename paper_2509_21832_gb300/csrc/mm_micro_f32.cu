@@ -458,7 +458,7 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
                                          bool mirl, bool mirr, float fv) {
   using S = FlatShape<NV1, NV2>;
   const KGrid& g = a.g;
-  const int nc = g.nx * g.ny, cell = j * g.nx + i;
+  const int cell = j * g.nx + i;
   const int lane = threadIdx.x & 31;
   float2* X1 = reinterpret_cast<float2*>(xt);  // (c2, c2^2)
   float2* X2 = X1 + NV2;                        // (e2, projection term)
