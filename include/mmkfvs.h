@@ -19,7 +19,9 @@
  * mm_last_error() gives a text for the last failure of a context.
  *
  * Threading: one context per CUDA stream; calls on one context are not thread-safe.  All work
- * of a context is enqueued on the stream given at creation (NULL = legacy default stream).
+ * of a context is ordered on the stream given at creation (NULL = legacy default stream);
+ * mm_step_host also runs its copies and sweeps on streams of its own, which wait for that stream
+ * before they start and are joined to it before the call returns.
  */
 #ifndef MMKFVS_H
 #define MMKFVS_H
