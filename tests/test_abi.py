@@ -143,3 +143,33 @@ def test_fp32_g_meshes_beyond_shared_memory_are_rejected():
     assert api.mm_device_bytes(I.Grid(nx=8, ny=8, nv1=32, nv2=1024), p32) == 0
     # the FP64 kernels fit at every accepted mesh
     assert api.mm_device_bytes(I.Grid(nx=8, ny=8, nv1=32, nv2=1024), I.Params()) > 0
+
+
+def test_missing_library_fails_loudly():
+    """Without the built library the binding raises instead of computing anything on the CPU."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r); "
+            "from paper_2509_21832_gb300 import build as b, api; "
+            "b.LIB = '/nonexistent/libmmkfvs.so'; api._lib = None\n"
+            "try:\n    api.load(build_if_needed=False)\n    print('loaded')\n"
+            "except ImportError as e:\n    print('ImportError', e)" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.stdout.startswith("ImportError"), r.stdout + r.stderr
+
+
+def test_product_package_never_imports_the_oracle():
+    """The oracle is test infrastructure: no module of the package imports it."""
+    import ast
+    pkg = os.path.join(ROOT, "paper_2509_21832_gb300")
+    for fn in sorted(os.listdir(pkg)):
+        if not fn.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, fn)).read())
+        for node in ast.walk(tree):
+            mods = []
+            if isinstance(node, ast.Import):
+                mods = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                mods = [node.module or ""]
+            assert not any(m == "oracle" or m.startswith("oracle.") for m in mods), (fn, mods)
