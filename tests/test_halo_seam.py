@@ -211,3 +211,49 @@ def test_four_gloo_ranks_2x2_periodic():
     Qs, Gs = np.zeros_like(Q), np.zeros_like(G)
     halo.gather(blocks, [(Qb, Gb) for _, Qb, Gb in res], Qs, Gs)
     assert np.array_equal(Qs, Qu) and np.array_equal(Gs, Gu)
+
+
+def _rank_exchange_dtypes(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+    from paper_2509_21832_gb300 import halo as hl
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    grid = I.Grid(nx=12, ny=6, nv1=4, nv2=3)
+    blocks = hl.decompose(grid, I.Params(bc=(I.PERIODIC,) * 4), world, 1, w=2)
+    copies = hl.plan(blocks)
+    b = blocks[rank]
+    gi = torch.as_tensor(b.global_index())
+    own = torch.as_tensor(b.owned_mask())
+    nc, nv = b.nx * b.ny, grid.nv1 * grid.nv2
+    # owned cells carry values made from their global index; halos start as NaN
+    Q = (gi[None, :].double() * 10 + torch.arange(6)[:, None]).clone()
+    G = (gi[:, None].float() * 100 + torch.arange(nv)[None, :]).clone()
+    Q[:, ~own] = float("nan")
+    G[~own] = float("nan")
+    hl.exchange(blocks, copies, rank, Q.view(6, b.ny, b.nx), G.view(b.ny, b.nx, 3, 4))
+    Qx = gi[None, :].double() * 10 + torch.arange(6)[:, None]
+    Gx = gi[:, None].float() * 100 + torch.arange(nv)[None, :]
+    ok = bool(torch.equal(Q, Qx) and torch.equal(G, Gx) and G.dtype == torch.float32)
+    dist.barrier()
+    out.put((rank, ok))
+    dist.destroy_process_group()
+
+
+def test_exchange_fills_every_halo_with_the_owners_values_in_their_dtypes():
+    """After one exchange every halo cell holds its owner's Q (float64) and g (float32, as FP32 g
+    travels), corners and the periodic wrap included."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank_exchange_dtypes, args=(r, 3, port, q)) for r in range(3)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in range(3))
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, ok in res), res
