@@ -358,10 +358,13 @@ mm_status mm_diag_bounded_wait(int copy, int spins, void* cuda_stream);
  * MM_STATIC_SCRATCH_BYTES bytes that every GPU loading this library holds until process exit.
  *  - Limits: precision MM_PREC_FP64 only; nx*ny <= MM_STATIC_MAX_CELLS and
  *    nx*ny*nv1*nv2 <= MM_STATIC_MAX_PHASE.  Larger problems, other precisions, NULL buffers,
- *    dt <= 0, eps <= 0 or nsteps < 0 return MM_ERR_INVALID_ARG with a message in errbuf.
- *  - Works on the current device and cuda_stream (NULL = legacy default stream).  The first call
- *    on a device looks up the array's device address (cudaGetSymbolAddress) once; make that
- *    first call before any stream capture.
+ *    Q_dev or H_dev not 16-byte aligned, G_dev not 256-byte aligned (the rules of
+ *    mm_create_borrowed), dt <= 0, eps <= 0 or nsteps < 0 return MM_ERR_INVALID_ARG with a
+ *    message in errbuf.
+ *  - Works on the current device and cuda_stream (NULL = legacy default stream).  Every call
+ *    looks up the array's device address in the current context (cudaGetSymbolAddress, which
+ *    allocates nothing); the first call on a device may load the library's device code there,
+ *    so make that first call before any stream capture.
  *  - Every call shares the one array and it keeps the previous call's contents (the zero-start
  *    parts are cleared at the start of each call).  Calls that overlap on the GPU -- on two
  *    streams, or from two host threads -- race on it and give wrong results.

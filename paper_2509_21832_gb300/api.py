@@ -211,16 +211,22 @@ def to_c_params(p) -> mm_params:
 def _host_ptr(a, n):
     if a is None:
         return None
-    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
-    assert a.size == n, (a.size, n)
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    if a.size != n:
+        raise ValueError("host array has %d elements, expected %d" % (a.size, n))
     return a.ctypes.data
 
 
 def _dev_ptr(t, n):
     if t is None:
         return None
-    assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8
-    assert t.is_contiguous() and t.numel() == n, (t.numel(), n)
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8):
+        raise TypeError("expected a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("device tensor must be contiguous")
+    if t.numel() != n:
+        raise ValueError("device tensor has %d elements, expected %d" % (t.numel(), n))
     return t.data_ptr()
 
 
@@ -327,10 +333,14 @@ class Solver:
             self.ctx = mm_create(grid, params, stream)
         else:
             Q, G, S = borrow
-            assert Q.is_cuda and Q.dtype.itemsize == 8 and Q.is_contiguous()
-            assert Q.numel() == 6 * self.ncell
-            assert G.is_cuda and G.is_contiguous() and G.numel() == self.nphase
-            assert S.is_cuda and S.is_contiguous()
+            _dev_ptr(Q, 6 * self.ncell)
+            gsize = 4 if int(getattr(params, "precision", 0)) == 1 else 8
+            if not (G.is_cuda and G.is_contiguous() and G.numel() == self.nphase
+                    and G.element_size() == gsize):
+                raise ValueError("borrowed g must be a contiguous CUDA tensor of %d elements of "
+                                 "%d bytes" % (self.nphase, gsize))
+            if not (S.is_cuda and S.is_contiguous()):
+                raise ValueError("borrowed scratch must be a contiguous CUDA tensor")
             st, ctx = mm_create_borrowed(grid, params, Q.data_ptr(), G.data_ptr(), S.data_ptr(),
                                          S.numel() * S.element_size(), stream)
             if st != MM_OK:
@@ -472,14 +482,20 @@ class Solver:
 
 
 def _f32_ptr(t, n):
-    assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4
-    assert t.is_contiguous() and t.numel() == n, (t.numel(), n)
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4):
+        raise TypeError("expected a float32 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("device tensor must be contiguous")
+    if t.numel() != n:
+        raise ValueError("device tensor has %d elements, expected %d" % (t.numel(), n))
     return t.data_ptr()
 
 
 def _host_f32(a, n):
-    assert isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
-    assert a.size == n, (a.size, n)
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("expected a C-contiguous float32 numpy array")
+    if a.size != n:
+        raise ValueError("host array has %d elements, expected %d" % (a.size, n))
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 

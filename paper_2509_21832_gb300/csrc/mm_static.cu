@@ -9,9 +9,9 @@
 // per-cell primitive fields, the diffuse-wall cell list and the error word) in ONE file-scope
 // static device array of fixed size.  Every GPU that loads this library holds that array until
 // the process exits.
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "mm_internal.cuh"
 
@@ -39,20 +39,14 @@ static_assert(kStaticBytes == MM_STATIC_SCRATCH_BYTES, "header size constant out
 // symbol: host code must use the address from cudaGetSymbolAddress, never the name.
 static __device__ __align__(256) unsigned char mm_static_scratch[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the static array on the current device, looked up once per device.
-cudaError_t scratch_address(int dev, unsigned char** out) {
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, mm_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+// Device address of the static array in the current context.  Looked up on every call: the
+// lookup allocates nothing, and an address kept from an earlier call could belong to a context
+// that has since been destroyed (cudaDeviceReset) or is not the caller's current one.
+cudaError_t scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, mm_static_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 
@@ -98,16 +92,15 @@ extern "C" mm_status mm_step_static_scratch(const mm_grid* grid, const mm_params
   }
   if (!Q_dev || !G_dev || !H_dev)
     return say(errbuf, errlen, MM_ERR_INVALID_ARG, "Q_dev, G_dev and H_dev are required");
+  // the same alignment that mm_create_borrowed asks of caller buffers
+  if ((uintptr_t)Q_dev % 16 != 0 || (uintptr_t)H_dev % 16 != 0 || (uintptr_t)G_dev % 256 != 0)
+    return say(errbuf, errlen, MM_ERR_INVALID_ARG,
+               "Q_dev and H_dev must be 16-byte aligned and G_dev 256-byte aligned");
   if (!(dt > 0.0) || !(eps > 0.0) || nsteps < 0)
     return say(errbuf, errlen, MM_ERR_INVALID_ARG, "need dt > 0, eps > 0, nsteps >= 0");
 
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return say(errbuf, errlen, MM_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices)
-    return say(errbuf, errlen, MM_ERR_INVALID_ARG, "device ordinal beyond 63");
   unsigned char* base = nullptr;
-  e = scratch_address(dev, &base);
+  cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return say(errbuf, errlen, MM_ERR_CUDA, cudaGetErrorString(e));
 
   KGrid kg;

@@ -175,9 +175,16 @@ def plan(blocks):
 
 
 def _flat(Q, G, b):
-    """Views Q [6][ncell] and G [ncell][nv] of a block's extended arrays."""
+    """Views Q [6][ncell] and G [ncell][nv] of a block's extended arrays.  The arrays must be
+    C-contiguous: a reshaped copy would take the halo writes and lose them."""
     nc = b.nx * b.ny
-    return Q.reshape(6, nc), G.reshape(nc, -1)
+    for a in (Q, G):
+        ok = a.is_contiguous() if hasattr(a, "is_contiguous") else a.flags["C_CONTIGUOUS"]
+        if not ok:
+            raise ValueError("block arrays must be C-contiguous (halo writes go through views)")
+    if hasattr(Q, "is_contiguous"):      # torch: view() never copies
+        return Q.view(6, nc), G.view(nc, -1)
+    return Q.reshape(6, nc), G.reshape(nc, -1)   # C-contiguous numpy: reshape is a view
 
 
 def scatter(blocks, Q, G):

@@ -71,6 +71,12 @@ def test_static_scratch_rejects_problems_beyond_its_limits():
         api.mm_step_static_scratch(grid, I.Params(precision=I.PREC_G_FP32), _Fake(6 * 64),
                                    _Fake(64 * 64), _Fake(4 * 64), 1e-3, 0.1, 1)
     assert e.value.status == api.MM_ERR_INVALID_ARG
+    # buffers off the alignment that mm_create_borrowed asks for are refused, not stepped
+    for q, g, h in ((4104, 4096, 4096), (4096, 4104, 4096), (4096, 4096, 4104), (4096, 4352 + 16, 4096)):
+        with pytest.raises(api.MMError) as e:
+            api.mm_step_static_scratch(grid, I.Params(), _Fake(6 * 64, q), _Fake(64 * 64, g),
+                                       _Fake(4 * 64, h), 1e-3, 0.1, 1)
+        assert e.value.status == api.MM_ERR_INVALID_ARG and "aligned" in str(e.value)
 
 
 class _Fake:
@@ -78,8 +84,9 @@ class _Fake:
 
     is_cuda = True
 
-    def __init__(self, n):
+    def __init__(self, n, ptr=4096):
         self.n = n
+        self.ptr = ptr
         import torch
         self.dtype = torch.float64
 
@@ -93,4 +100,4 @@ class _Fake:
         return self.n
 
     def data_ptr(self):
-        return 4096
+        return self.ptr
