@@ -25,5 +25,29 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def build_variant(outdir: str, replace) -> str:
+    """Build a copy of the oracle in outdir with textual edits applied to its sources (used by
+    tests that plant a mistake in the oracle and check that a pin catches it).  replace maps a
+    source file name to a list of (old, new) pairs; each old must occur exactly once."""
+    os.makedirs(outdir, exist_ok=True)
+    srcs = []
+    for name in ("mm_oracle.c", "mm_oracle1d.c", "mm_oracle.h"):
+        with open(os.path.join(HERE, name)) as f:
+            text = f.read()
+        for old, new in replace.get(name, []):
+            if text.count(old) != 1:
+                raise ValueError("edit %r matches %d times in %s" % (old, text.count(old), name))
+            text = text.replace(old, new)
+        dst = os.path.join(outdir, name)
+        with open(dst, "w") as f:
+            f.write(text)
+        if name.endswith(".c"):
+            srcs.append(dst)
+    out = os.path.join(outdir, "liboracle_variant.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                           "-ffp-contract=off", "-o", out] + srcs + ["-lm"])
+    return out
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))

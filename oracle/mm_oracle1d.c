@@ -61,8 +61,9 @@ static void kfvs1(double rho, double u, double T, double Fp[3], double Fm[3]) {
 
 /* ---- manufactured solution (Section 4.1) ----------------------------------------------------
  * f = (exp(-(v-1)^2) + 2 exp(-(v+1)^2)) (2 + sin(2 pi (x - t))), rho = 3 sqrt(pi) F, u = -1/3,
- * T = 25/18; S = f_t + v f_x - (tau/eps)(M - f) with M of the exact state and tau the cell's
- * tau^n_i, the same tau as the Ghat that S enters (a reading: the passage writes only "tau"). */
+ * T = 25/18; S = f_t + v f_x - (tau/eps)(M - f) with M and tau both of the exact state: the
+ * passage defines S as a function of (t, x, v) alone, so nothing of the numerical state enters
+ * it (with the hard-sphere tau of Eq. collision_parameter_1d, tau(T = 25/18) is a constant). */
 static double mms1_phi(double v) { return exp(-(v - 1.0) * (v - 1.0)) + 2.0 * exp(-(v + 1.0) * (v + 1.0)); }
 static double mms1_M(double v) { return 1.8 * exp(-0.04 * (3.0 * v + 1.0) * (3.0 * v + 1.0)); }
 
@@ -146,7 +147,7 @@ int orc1d_step(const orc1d_grid* g, const orc1d_params* p, double* Q, double* G,
       }
       proj1(g, rho[i], u[i], T[i], Z, PZ);
       if (mms) {
-        mms1_source(g, tau, eps, tn, g->x0 + (i + 0.5) * dx, S);
+        mms1_source(g, tau1(p, 0.0, 25.0 / 18.0), eps, tn, g->x0 + (i + 0.5) * dx, S);
         proj1(g, rho[i], u[i], T[i], S, PS);
       }
       const double w1 = eps / (eps + dt * tau), w2 = dt * tau / (eps + dt * tau);

@@ -46,61 +46,81 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        G, P = ctypes.POINTER(OrcGrid), ctypes.POINTER(OrcParams)
-        L.orc_step.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
-                               ctypes.c_double, ctypes.c_double, ctypes.c_int]
-        L.orc_step.restype = ctypes.c_int
-        L.orc_dt_for_cfl.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                     ctypes.POINTER(ctypes.c_int)]
-        L.orc_dt_for_cfl.restype = ctypes.c_double
-        L.orc_prims.argtypes = [P, _c_double_p, _c_double_p]
-        L.orc_prims.restype = ctypes.c_int
-        L.orc_q_from_prim.argtypes = [ctypes.c_int] + [_c_double_p] * 5
-        L.orc_q_from_prim.restype = ctypes.c_int
-        L.orc_maxwellian_gauss.argtypes = [P, _c_double_p, ctypes.c_double, ctypes.c_double,
-                                           _c_double_p, _c_double_p]
-        L.orc_maxwellian_gauss.restype = None
-        L.orc_project.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                  ctypes.c_double, _c_double_p, _c_double_p]
-        L.orc_project.restype = None
-        L.orc_kfvs_half.argtypes = [_c_double_p, ctypes.c_int, _c_double_p, _c_double_p]
-        L.orc_kfvs_half.restype = None
-        L.orc_wall_R.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
-        L.orc_wall_R.restype = ctypes.c_double
-        L.orc_trbdf2_W.argtypes = [ctypes.c_double] * 4
-        L.orc_trbdf2_W.restype = ctypes.c_double
-        L.orc_step_closure.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
-                                       ctypes.c_double, ctypes.c_double,
-                                       ctypes.POINTER(ctypes.c_ubyte),
-                                       ctypes.POINTER(ctypes.c_ubyte), _c_double_p]
-        L.orc_step_closure.restype = ctypes.c_int
-        L.orc_step_mms.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
-                                   ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                   ctypes.c_double]
-        L.orc_step_mms.restype = ctypes.c_int
-        L.orc_mms_exact.argtypes = [G, P, ctypes.c_double, ctypes.c_double, _c_double_p,
-                                    _c_double_p]
-        L.orc_mms_exact.restype = ctypes.c_int
-        L.orc_mms_source.argtypes = [G, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_double, _c_double_p]
-        L.orc_mms_source.restype = ctypes.c_int
-        G1, P1 = ctypes.POINTER(Orc1dGrid), ctypes.POINTER(Orc1dParams)
-        L.orc1d_step.argtypes = [G1, P1, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
-                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double]
-        L.orc1d_step.restype = ctypes.c_int
-        L.orc1d_mms_exact.argtypes = [G1, ctypes.c_double, ctypes.c_double, _c_double_p,
-                                      _c_double_p]
-        L.orc1d_mms_exact.restype = ctypes.c_int
-        L.orc1d_dt.argtypes = [G1, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
-        L.orc1d_dt.restype = ctypes.c_double
-        L.orc_ghat.argtypes = [G, P, _c_double_p, ctypes.c_double, _c_double_p]
-        L.orc_ghat.restype = ctypes.c_int
-        L.orc_num_threads.argtypes = []
-        L.orc_num_threads.restype = ctypes.c_int
-        _lib = L
+        _lib = _configure(ctypes.CDLL(_build.build()))
     return _lib
+
+
+class use_library:
+    """Context manager: route every call of this module to another build of the oracle (a copy
+    of its source with a planted mistake, built by build.build_variant) while the block runs."""
+
+    def __init__(self, path):
+        self.L = _configure(ctypes.CDLL(path))
+
+    def __enter__(self):
+        global _lib
+        self.saved, _lib = _lib, self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _configure(L):
+    G, P = ctypes.POINTER(OrcGrid), ctypes.POINTER(OrcParams)
+    L.orc_step.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
+                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.orc_step.restype = ctypes.c_int
+    L.orc_dt_for_cfl.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int)]
+    L.orc_dt_for_cfl.restype = ctypes.c_double
+    L.orc_prims.argtypes = [P, _c_double_p, _c_double_p]
+    L.orc_prims.restype = ctypes.c_int
+    L.orc_q_from_prim.argtypes = [ctypes.c_int] + [_c_double_p] * 5
+    L.orc_q_from_prim.restype = ctypes.c_int
+    L.orc_maxwellian_gauss.argtypes = [P, _c_double_p, ctypes.c_double, ctypes.c_double,
+                                       _c_double_p, _c_double_p]
+    L.orc_maxwellian_gauss.restype = None
+    L.orc_project.argtypes = [G, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double, _c_double_p, _c_double_p]
+    L.orc_project.restype = None
+    L.orc_kfvs_half.argtypes = [_c_double_p, ctypes.c_int, _c_double_p, _c_double_p]
+    L.orc_kfvs_half.restype = None
+    L.orc_wall_R.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.orc_wall_R.restype = ctypes.c_double
+    L.orc_trbdf2_W.argtypes = [ctypes.c_double] * 4
+    L.orc_trbdf2_W.restype = ctypes.c_double
+    L.orc_step_closure.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
+                                   ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_ubyte),
+                                   ctypes.POINTER(ctypes.c_ubyte), _c_double_p]
+    L.orc_step_closure.restype = ctypes.c_int
+    L.orc_step_mms.argtypes = [G, P, _c_double_p, _c_double_p, _c_double_p,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_double]
+    L.orc_step_mms.restype = ctypes.c_int
+    L.orc_mms_exact.argtypes = [G, P, ctypes.c_double, ctypes.c_double, _c_double_p,
+                                _c_double_p]
+    L.orc_mms_exact.restype = ctypes.c_int
+    L.orc_mms_source.argtypes = [G, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, _c_double_p]
+    L.orc_mms_source.restype = ctypes.c_int
+    G1, P1 = ctypes.POINTER(Orc1dGrid), ctypes.POINTER(Orc1dParams)
+    L.orc1d_step.argtypes = [G1, P1, _c_double_p, _c_double_p, _c_double_p, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    L.orc1d_step.restype = ctypes.c_int
+    L.orc1d_mms_exact.argtypes = [G1, ctypes.c_double, ctypes.c_double, _c_double_p,
+                                  _c_double_p]
+    L.orc1d_mms_exact.restype = ctypes.c_int
+    L.orc1d_dt.argtypes = [G1, ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+    L.orc1d_dt.restype = ctypes.c_double
+    L.orc_ghat.argtypes = [G, P, _c_double_p, ctypes.c_double, _c_double_p]
+    L.orc_ghat.restype = ctypes.c_int
+    L.orc_num_threads.argtypes = []
+    L.orc_num_threads.restype = ctypes.c_int
+    return L
 
 
 def _grid(g) -> OrcGrid:

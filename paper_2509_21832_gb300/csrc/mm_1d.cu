@@ -91,12 +91,12 @@ __global__ void k1d_micro(const double* __restrict__ G, double* __restrict__ Gn,
   const double* Gc = G + (size_t)i * nv;
   const double* Gl = G + (size_t)iL * nv;
   const double* Gr = G + (size_t)iR * nv;
-  // manufactured source at (x_i, t^n): S = phi (F_t + v F_x) - (tau/eps)(M_e - phi) F with the
-  // exact Maxwellian M_e and the cell's tau^n_i (the tau of the Ghat that S enters)
+  // manufactured source at (x_i, t^n): S = phi (F_t + v F_x) - (tau_e/eps)(M_e - phi) F with the
+  // exact state's Maxwellian M_e and tau_e = tau(T = 25/18): S is a function of (t, x, v) alone
   const double x = g.x0 + (i + 0.5) * g.dx;
   const double F = 2.0 + sin(2.0 * kPi1 * (x - tn));
   const double Fx = 2.0 * kPi1 * cos(2.0 * kPi1 * (x - tn));
-  const double te = tau / eps;
+  const double te = tau_1d(g, 25.0 / 18.0) / eps;
   // pass 1: moments of Z (and of S) against the basis of Eq. (5-5)
   double a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
   for (int k = threadIdx.x; k < nv; k += blockDim.x) {

@@ -76,34 +76,38 @@ def run_study(n, lo=-1.0, hi=1.0):
         return s.mms_error(ns * dt, EPS)
 
 
-def test_convergence_study_reproduces_the_printed_table():
-    """Table tab5-4 on the paper's meshes 40^4, 80^4, 160^4, t = 0.25, CFL 0.35.  Reading: the
-    runs behind the table used the square [-1, 1]^2 (the domain of the paper's other 2D
-    examples), not the [0, 1]^2 of its caption; on [0, 1]^2 every printed row is matched by the
-    next coarser mesh instead.  The printed errors are reproduced to 10 % at 40^4, 5 % at 80^4
-    and 2 % at 160^4 (the remaining difference shrinks with the mesh), and the printed orders of
-    convergence to 0.1."""
+def test_convergence_study_under_the_stated_domain():
+    """Table tab5-4 on the paper's meshes 40^4, 80^4, 160^4, t = 0.25, CFL 0.35, under the
+    readings taken from Section 6.1: the stated domain [0, 1]^2 and the tau of the exact state
+    in S.  Under them the errors come out at about half the printed ones (0.53-0.65 times: each
+    printed row is close to our next coarser mesh), with first-order convergence whose
+    pre-asymptotic orders run ahead of the printed ones by about one mesh.  The same meshes on
+    [-1, 1]^2, which is not the stated domain, are reported beside them: there the printed
+    errors come out to 10 % at 40^4, 5 % at 80^4 and 2 % at 160^4 and the printed orders to 0.1,
+    an observation about the paper's runs, not a reading the tests rely on."""
     with open(GOLDEN) as f:
         table = {r["n"]: r for r in json.load(f)["table_tab5_4"]}
-    tol = {40: 0.10, 80: 0.05, 160: 0.02}
-    errs = {n: run_study(n) for n in (40, 80, 160)}
-    for n, (em, eu) in errs.items():
-        print("%d^4: macro %.6e (paper %.6e)  micro %.6e (paper %.6e)"
-              % (n, em, table[n]["macro"], eu, table[n]["micro"]))
-        assert abs(em / table[n]["macro"] - 1) <= tol[n]
-        assert abs(eu / table[n]["micro"] - 1) <= tol[n]
+    stated = {n: run_study(n, 0.0, 1.0) for n in (40, 80, 160)}
+    other = {n: run_study(n) for n in (40, 80, 160)}
+    for n in (40, 80, 160):
+        (em, eu), (fm, fu) = stated[n], other[n]
+        print("%d^4: [0,1]^2 macro %.6e (%.3f of printed) micro %.6e (%.3f) | "
+              "[-1,1]^2 macro %.6e (%.3f) micro %.6e (%.3f)"
+              % (n, em, em / table[n]["macro"], eu, eu / table[n]["micro"],
+                 fm, fm / table[n]["macro"], fu, fu / table[n]["micro"]))
+        assert 0.45 <= em / table[n]["macro"] <= 0.75
+        assert 0.45 <= eu / table[n]["micro"] <= 0.75
+        tol = {40: 0.10, 80: 0.05, 160: 0.02}[n]
+        assert abs(fm / table[n]["macro"] - 1) <= tol
+        assert abs(fu / table[n]["micro"] - 1) <= tol
     for a, b in ((40, 80), (80, 160)):
-        rm = math.log2(errs[a][0] / errs[b][0])
-        ru = math.log2(errs[a][1] / errs[b][1])
-        print("%d -> %d: orders %.3f (paper %.3f), %.3f (paper %.3f)"
+        rm = math.log2(stated[a][0] / stated[b][0])
+        ru = math.log2(stated[a][1] / stated[b][1])
+        print("%d -> %d on [0,1]^2: orders %.3f (paper %.3f), %.3f (paper %.3f)"
               % (a, b, rm, table[b]["macro_rate"], ru, table[b]["micro_rate"]))
-        assert abs(rm - table[b]["macro_rate"]) <= 0.1
-        assert abs(ru - table[b]["micro_rate"]) <= 0.1
-
-
-def test_unit_square_matches_the_next_printed_row():
-    """On the caption's [0, 1]^2 the n^4 errors equal the printed (2n)^4 row to 5 %."""
-    with open(GOLDEN) as f:
-        table = {r["n"]: r for r in json.load(f)["table_tab5_4"]}
-    em, eu = run_study(80, 0.0, 1.0)
-    assert abs(em / table[160]["macro"] - 1) <= 0.05 and abs(eu / table[160]["micro"] - 1) <= 0.05
+        assert 0.6 <= rm <= 1.05 and 0.6 <= ru <= 1.05
+        assert rm >= table[b]["macro_rate"] - 0.05 and ru >= table[b]["micro_rate"] - 0.05
+        fm = math.log2(other[a][0] / other[b][0])
+        fu = math.log2(other[a][1] / other[b][1])
+        assert abs(fm - table[b]["macro_rate"]) <= 0.1
+        assert abs(fu - table[b]["micro_rate"]) <= 0.1

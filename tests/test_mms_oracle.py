@@ -139,19 +139,32 @@ def test_micro_part_stays_orthogonal_to_the_null_space_with_the_source():
         assert np.max(np.abs(np.sum(G * m, axis=(2, 3)))) <= 1e-11 * scale * np.max(np.abs(m))
 
 
-def test_coarsest_printed_row():
-    """Table tab5-4, 40^4: the oracle on [-1, 1]^2 (the domain reading of the GPU convergence
-    test) gives the printed macro and micro errors to 10 %."""
-    with open(GOLDEN) as f:
-        row = json.load(f)["table_tab5_4"][0]
-    g = I.Grid(nx=40, ny=40, x0=-1, x1=1, y0=-1, y1=1, nv1=40, nv2=40, v1min=-6, v1max=6,
+def _study_40(lo, hi):
+    g = I.Grid(nx=40, ny=40, x0=lo, x1=hi, y0=lo, y1=hi, nv1=40, nv2=40, v1min=-6, v1max=6,
                v2min=-6, v2max=6)
     p = I.Params(nu=-1.0, tau_model=I.TAU_HARDSPHERE2D, bc=(I.PERIODIC,) * 4)
     dt, ns = O.dt_for_cfl(g, 0.35, 0.25, I.CFL_SUM)
     Q0, G0 = O.mms_exact(g, p, 0.0, EPS)
     Q, G, _ = O.step_mms(g, p, Q0, G0, dt, EPS, ns, 0.0)
     Qe, Ge = O.mms_exact(g, p, ns * dt, EPS)
-    em = math.sqrt(np.sum((Q - Qe) ** 2) / np.sum(Qe ** 2))
-    eu = math.sqrt(np.sum((G - Ge) ** 2) / np.sum(Ge ** 2))
-    assert abs(em / row["macro"] - 1) <= 0.10, em
-    assert abs(eu / row["micro"] - 1) <= 0.10, eu
+    return (math.sqrt(np.sum((Q - Qe) ** 2) / np.sum(Qe ** 2)),
+            math.sqrt(np.sum((G - Ge) ** 2) / np.sum(Ge ** 2)))
+
+
+def test_coarsest_printed_row():
+    """Table tab5-4, 40^4, under the readings taken from Section 6.1: the domain [0, 1]^2 that
+    the caption and the text state, and the tau of the exact state in S (S is a function of
+    (t, x, v) alone).  Under them the oracle's errors are 0.61 (macro) and 0.64 (micro) times
+    the printed ones -- about the printed 80^4 row.  The same mesh on [-1, 1]^2, which is not
+    the stated domain, is reported beside it: there the printed row comes out to 10 %."""
+    with open(GOLDEN) as f:
+        row = json.load(f)["table_tab5_4"][0]
+    em, eu = _study_40(0.0, 1.0)
+    print("[0,1]^2: macro %.4e (%.3f of printed), micro %.4e (%.3f)"
+          % (em, em / row["macro"], eu, eu / row["micro"]))
+    assert 0.5 <= em / row["macro"] <= 0.75, em
+    assert 0.5 <= eu / row["micro"] <= 0.75, eu
+    em2, eu2 = _study_40(-1.0, 1.0)
+    print("[-1,1]^2: macro %.4e (%.3f of printed), micro %.4e (%.3f)"
+          % (em2, em2 / row["macro"], eu2, eu2 / row["micro"]))
+    assert abs(em2 / row["macro"] - 1) <= 0.10 and abs(eu2 / row["micro"] - 1) <= 0.10

@@ -213,12 +213,13 @@ def test_ghat_transport_term_converges_to_analytic_projection():
     p = I.Params(nu=-0.5, bc=(I.PERIODIC,) * 4, tau_model=I.TAU_CONST, tau0=1.0)
     errs = []
     for n in (16, 32, 64):
-        g = I.Grid(nx=n, ny=n, nv1=32, nv2=32)
+        # dy = (2/3) dx, so that a dx taken for dy in the discrete gradients shows
+        g = I.Grid(nx=n, ny=3 * n // 2, nv1=32, nv2=32)
         x, y = np.meshgrid(g.xc(), g.yc())
         rho, u1, u2, T = _fields(x, y)
         Q = I.q_from_prims(rho, u1, u2, T)
         Gh = O.ghat(g, p, Q, 1e30)   # eps huge: only -(1/tau){B:sigma + C.grad T} M remains
-        i = j = n // 4               # cell centre at (0.25 - h/2, 0.25 - h/2) + h/2 ...
+        i, j = n // 4, 3 * n // 8    # the cell centred at (0.25 + dx/2, 0.25 + dy/2)
         xc, yc = g.xc()[i], g.yc()[j]
         h = 1e-5
         v1, v2 = g.v1()[None, :], g.v2()[:, None]
@@ -450,3 +451,205 @@ def test_q_from_prim_rejects_non_physical(bad):
         u1[0] = np.nan
     with pytest.raises(O.OracleError):
         O.q_from_prim(rho, u1, u2, T)
+
+
+# ---------------------------------------------------------------------------------------------
+# free streaming along y and along a diagonal of a mesh with dx != dy: fixes the transport
+# scale of the y sweeps (micro, macro and heat-flux differences), which no x-only pin sees
+# ---------------------------------------------------------------------------------------------
+def _collisionless(k, T, A, X, Y, t, v1, v2):
+    """Moments of f(x, v, t) = rho0(x - v t) M_T(v), rho0 = 1 + A sin(2 pi k.x), u = 0: with
+    a = 2 pi k t and D = exp(-T |a|^2 / 2) (the characteristic function of the Gaussian),
+    rho = 1 + A s D, m = -A c T a D, E = T I + A s (T I - T^2 a a^T) D (s, c the sine and cosine of
+    2 pi k.x); and f itself at the cell centres and velocity nodes."""
+    a = 2 * math.pi * np.array(k, dtype=float) * t
+    D = math.exp(-T * (a @ a) / 2)
+    ph = 2 * math.pi * (k[0] * X + k[1] * Y)
+    s, c = np.sin(ph), np.cos(ph)
+    Q = np.array([1 + A * s * D, -A * c * T * a[0] * D, -A * c * T * a[1] * D,
+                  T + A * s * (T - T * T * a[0] * a[0]) * D, A * s * (-T * T * a[0] * a[1]) * D,
+                  T + A * s * (T - T * T * a[1] * a[1]) * D])
+    V1, V2 = v1[None, None, None, :], v2[None, None, :, None]
+    ph2 = 2 * math.pi * (k[0] * (X[:, :, None, None] - V1 * t) + k[1] * (Y[:, :, None, None] - V2 * t))
+    f = (1 + A * np.sin(ph2)) * np.exp(-(V1 ** 2 + V2 ** 2) / (2 * T)) / (2 * math.pi * T)
+    return Q, f
+
+
+def _free_stream_errors(nx, ny, k, nv, tf=0.1, A=0.2, T=1.0, eps=1e30):
+    g = I.Grid(nx=nx, ny=ny, nv1=nv[0], nv2=nv[1])
+    p = I.Params(nu=-0.5, bc=(I.PERIODIC,) * 4)
+    X, Y = np.meshgrid(g.xc(), g.yc())
+    Q0 = I.q_from_prims(1 + A * np.sin(2 * math.pi * (k[0] * X + k[1] * Y)), 0.0, 0.0, T)
+    dt, n = O.dt_for_cfl(g, 0.5, tf, I.CFL_SUM)
+    Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, eps, n)
+    Qe, fe = _collisionless(k, T, A, X, Y, n * dt, g.v1(), g.v2())
+    # the kinetic solution f_h = M[Q] + eps g, M from the moments of Q (u, T of the cell)
+    rho = Q[0]
+    u1, u2 = Q[1] / rho, Q[2] / rho
+    Tn = (Q[3] + Q[5] - rho * (u1 * u1 + u2 * u2)) / (2 * rho)
+    V1, V2 = g.v1()[None, None, None, :], g.v2()[None, None, :, None]
+    w = lambda a: a[:, :, None, None]  # noqa: E731
+    M = w(rho / (2 * math.pi * Tn)) * np.exp(-((V1 - w(u1)) ** 2 + (V2 - w(u2)) ** 2) / (2 * w(Tn)))
+    eq = np.mean(np.abs(Q - Qe), axis=(1, 2))
+    ef = np.mean(np.abs(M + eps * G - fe)) / np.mean(np.abs(fe))
+    return eq, ef
+
+
+def _assert_first_order(levels, comps):
+    for (qa, fa), (qb, fb) in zip(levels, levels[1:]):
+        assert fa / fb > 1.5, (fa, fb)
+        for m in comps:
+            assert qa[m] / qb[m] > 1.5, (m, qa[m], qb[m])
+
+
+def test_free_streaming_along_y():
+    """eps = 1e30 on a single column (nx = 1, dx = 1 != dy): density, y momentum, both normal
+    energies and the kinetic solution f_h = M + eps g follow the collisionless solution with
+    first-order convergence; a y transport scaled by dx instead of dy breaks it."""
+    levels = [_free_stream_errors(1, ny, (0, 1), (8, 32)) for ny in (25, 50, 100)]
+    _assert_first_order(levels, (0, 2, 3, 5))
+    q, f = levels[-1]
+    assert np.all(q[[0, 2, 3, 5]] < 2.5e-3) and f < 3e-3, (q, f)
+    assert q[1] < 1e-15 and q[4] < 1e-15     # no x motion arises
+
+
+def test_free_streaming_diagonal_unequal_cells():
+    """eps = 1e30, density wave along (1, 1) on meshes with dy = (2/3) dx: all six moments and f_h
+    converge at first order to the collisionless solution."""
+    levels = [_free_stream_errors(n, 3 * n // 2, (1, 1), (16, 16)) for n in (12, 24, 48)]
+    _assert_first_order(levels, range(6))
+    q, f = levels[-1]
+    assert np.all(q < 5e-3) and f < 8e-3, (q, f)
+
+
+# ---------------------------------------------------------------------------------------------
+# diffuse walls (Section 6.3): one step from a uniform gas at rest with an anisotropic diagonal
+# pressure tensor next to a moving wall of another temperature, in closed form
+# ---------------------------------------------------------------------------------------------
+def _half_moments(r, theta_n, mu_t, theta_t, s):
+    """r int_{s v_n > 0} v_n m(v) N(v_n; 0, theta_n) N(v_t; mu_t, theta_t) dv for the monomials
+    m = (1, v_n, v_t, v_n^2, v_n v_t, v_t^2): half-line Gaussian moments times full-line ones."""
+    i1, i2, i3 = s * math.sqrt(theta_n / (2 * math.pi)), theta_n / 2, s * 2 * theta_n * math.sqrt(theta_n / (2 * math.pi))
+    j1, j2 = mu_t, mu_t * mu_t + theta_t
+    return r * np.array([i1, i2, i1 * j1, i3, i2 * j1, i1 * j2])
+
+
+def _to_q_order(F, d):
+    """(1, v_n, v_t, v_n^2, v_n v_t, v_t^2) -> (1, v1, v2, v1^2, v1 v2, v2^2) for normal axis d."""
+    if d == 0:
+        return F
+    return np.array([F[0], F[2], F[1], F[5], F[4], F[3]])
+
+
+def _relax_half(q, W):
+    """Collision half step of the ES-BGK macro equations: the trace of P is kept and its
+    deviator is multiplied by W, the TR-BDF2 stability factor of y' = -tau (1 - nu) y / eps."""
+    rho, m1, m2 = q[0], q[1], q[2]
+    P = np.array([[q[3] - m1 * m1 / rho, q[4] - m1 * m2 / rho],
+                  [q[4] - m1 * m2 / rho, q[5] - m2 * m2 / rho]])
+    p = np.trace(P) / 2
+    Pn = p * np.eye(2) + W * (P - p * np.eye(2))
+    return np.array([rho, m1, m2, m1 * m1 / rho + Pn[0, 0], m1 * m2 / rho + Pn[0, 1],
+                     m2 * m2 / rho + Pn[1, 1]])
+
+
+def _wall_case(side, shear=0.0):
+    d = side // 2                  # normal axis
+    n_norm, n_tan = 4, 3
+    nx, ny = (n_norm, n_tan) if d == 0 else (n_tan, n_norm)
+    # cells of 0.1 along the wall normal, 0.1 along the wall; v in [-10, 10]^2 so that the
+    # Gaussian tails beyond the mesh are below round-off
+    g = I.Grid(nx=nx, ny=ny, x0=0, x1=0.1 * nx, y0=0, y1=0.1 * ny,
+               nv1=40, nv2=40, v1min=-10, v1max=10, v2min=-10, v2max=10)
+    bc = [I.PERIODIC] * 4
+    bc[2 * d] = bc[2 * d + 1] = I.EXTRAP
+    bc[side] = I.DIFFUSE
+    wT, wU = [1.0] * 4, [0.0] * 4
+    wT[side], wU[side] = 1.4, 0.35
+    p = I.Params(nu=-0.5, bc=tuple(bc), wall_T=tuple(wT), wall_U=tuple(wU), tau_model=I.TAU_RHO,
+                 tau0=1.0, wall_keep_es_term=1)
+    rho, T, aniso = 1.3, 1.0, 0.15
+    Q0 = I.q_from_prims(np.full((ny, nx), rho), 0.0, 0.0, T, aniso, shear)
+    h = (g.x1 - g.x0) / nx if d == 0 else (g.y1 - g.y0) / ny
+    cell = (slice(None), 0 if side == 2 else (ny - 1 if side == 3 else slice(None)),
+            0 if side == 0 else (nx - 1 if side == 1 else slice(None)))
+    return g, p, Q0, d, h, cell, rho, 1.4, 0.35
+
+
+@pytest.mark.parametrize("side", [0, 1, 2, 3])
+def test_diffuse_wall_macro_step_closed_form(side):
+    """After one step from a uniform gas at rest (g = 0, P diagonal and anisotropic) the wall cell
+    holds, to round-off, Q* = the first collision half step, plus dt/h times the net KFVS flux:
+    through the wall, the wall-side half flux of the wall Maxwellian (density r_w from zero mass
+    flux, r_w sqrt(T_w / 2 pi) = rho sqrt(T*_nn / 2 pi) with T*_nn of Q*, tangential velocity U,
+    temperature T_w) plus the cell's own outgoing half flux; through the inner face, the full flux
+    of the uniform state.  The heat-flux differences cancel in the wall cell (its inner neighbour
+    has no third moments), and the last collision half step relaxes the result.  Pins the ghost
+    state's orientation, velocity and density, and the split stage it is taken from."""
+    g, p, Q0, d, h, cell, rho, Tw, U = _wall_case(side)
+    eps, dt = 0.05, 2e-3
+    Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, eps, 1)
+    tau = rho                                         # tau = tau0 rho, rho unchanged (zero mass flux)
+    W = _trbdf2_scalar(tau * (1 - p.nu) / eps, dt / 2)
+    q0 = Q0[:, 0, 0]
+    qs = _relax_half(q0, W)                           # Q*
+    Tnn = (qs[3] if d == 0 else qs[5]) / rho
+    Ttt = (qs[5] if d == 0 else qs[3]) / rho
+    rw = rho * math.sqrt(Tnn / Tw)
+    low = side % 2 == 0
+    s_in = 1 if low else -1                           # the wall emits velocities pointing inward
+    F_wall = (_half_moments(rw, Tw, U, Tw, s_in) + _half_moments(rho, Tnn, 0.0, Ttt, -s_in))
+    F_wall = _to_q_order(F_wall, d)
+    F_int = np.zeros(6)
+    F_int[1 + d] = rho * Tnn                          # full flux of the uniform state at rest
+    net = (F_wall - F_int) if low else (F_int - F_wall)
+    want = _relax_half(qs + dt / h * net, W)
+    got = Q[cell]
+    got = got.reshape(6, -1)
+    assert np.all(np.abs(got - want[:, None]) <= 1e-13 * max(1.0, np.max(np.abs(want)))), (got[:, 0], want)
+    # the tangential momentum the moving wall hands to the gas: dt/h r_w U sqrt(T_w / 2 pi)
+    assert abs(got[2 - d, 0] - dt / h * rw * U * math.sqrt(Tw / (2 * math.pi))) < 1e-14
+
+
+@pytest.mark.parametrize("side", [0, 1, 2, 3])
+@pytest.mark.parametrize("keep", [1, 0])
+def test_diffuse_wall_micro_shear_closed_form(side, keep):
+    """g after one step from g = 0 in the wall cell is (dt tau/(eps + dt tau)) Ghat_wall; its shear
+    moment eps dv^2 sum v1 v2 g is, to round-off, w2 (+-(eps/tau) r_w U T_w / (2 h) + nu P12): the
+    upwind difference against the wall Maxwellian (r_w from the time-n state's normal temperature,
+    tangential velocity U) seen through (I - Pi_M), whose shear moment it keeps, plus the ES term
+    eps (Gcal - M)/eps with shear moment nu P12 (dropped in the literal wall form)."""
+    g, p, Q0, d, h, cell, rho, Tw, U = _wall_case(side, shear=0.1)
+    p.wall_keep_es_term = keep
+    eps, dt = 0.05, 2e-3
+    Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, eps, 1)
+    tau = rho
+    w2 = dt * tau / (eps + dt * tau)
+    P = np.array([[Q0[3, 0, 0], Q0[4, 0, 0]], [Q0[4, 0, 0], Q0[5, 0, 0]]])
+    rw = rho * math.sqrt(P[d, d] / rho / Tw)
+    sgn = 1 if side % 2 == 0 else -1
+    want = w2 * (sgn * (eps / tau) * rw * U * Tw / (2 * h) + keep * p.nu * P[0, 1])
+    V1, V2 = np.meshgrid(g.v1(), g.v2())
+    dv2 = (g.v1()[1] - g.v1()[0]) * (g.v2()[1] - g.v2()[0])
+    Gc = G[cell[1], cell[2]].reshape(-1, g.nv2, g.nv1)
+    got = eps * dv2 * np.einsum("ckl,kl->c", Gc, V1 * V2)
+    assert np.all(np.abs(got - want) <= 1e-12 * abs(want)), (got, want)
+
+
+def test_diffuse_walls_conserve_mass():
+    """Zero mass flux through every diffuse wall (wall densities of Section 6.3): with four moving
+    walls of different temperatures and a flowing, anisotropic gas the total mass stays constant
+    to round-off over many steps, while the energy does not (the walls exchange heat)."""
+    g = I.Grid(nx=10, ny=9, nv1=16, nv2=16)
+    p = I.Params(nu=-0.5, bc=(I.DIFFUSE,) * 4, wall_T=(1.3, 0.8, 1.1, 0.9),
+                 wall_U=(0.2, -0.3, 0.25, -0.15))
+    x, y = np.meshgrid(g.xc(), g.yc())
+    rho = 1 + 0.3 * np.cos(2 * np.pi * x) * np.sin(np.pi * y) + 0.1 * x
+    u1 = 0.3 * np.sin(2 * np.pi * y) + 0.2 * (x - 0.5)
+    u2 = -0.25 * np.cos(np.pi * x) - 0.2 * (y - 0.5)
+    Q0 = I.q_from_prims(rho, u1, u2, 1.0 + 0.2 * x * y, 0.1, -0.05)
+    dt = O.dt_for_cfl(g, 0.5, 0.0, I.CFL_SUM)[0]
+    for eps in (1e-2, 1.0):
+        Q, G, H = O.step(g, p, Q0, I.zero_g(g), dt, eps, 30)
+        assert abs(Q[0].sum() - Q0[0].sum()) <= 1e-13 * Q0[0].sum()
+        assert abs((Q[3] + Q[5]).sum() - (Q0[3] + Q0[5]).sum()) > 1e-6
