@@ -55,6 +55,27 @@ def fp64_peak_tflops(sm_max_mhz):
     return 152 * 4 * sm_max_mhz * 1e6 / 1e12
 
 
+def measure_fp64_peak(stream, reps=5):
+    """FP64 pipe throughput measured on this GPU: the library's FMA probe (8 independent chains
+    per thread, 8 CTAs of 256 threads per SM, about 0.1 s per launch), best of `reps` launches
+    timed with CUDA events on `stream`, in TFLOP/s."""
+    import torch
+    from paper_2509_21832_gb300 import api
+    ctas, iters = 152 * 8, 20000
+    out = torch.empty(ctas * 256, dtype=torch.float64, device="cuda")
+    best = 0.0
+    for r in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = api.mm_diag_fp64_fma(out, ctas, iters, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        if r > 0:   # the first launch is a warm-up
+            best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -152,28 +173,6 @@ def cpu_baseline(pr, rows, steps):
     return sub.nphase * steps / t, t, O.num_threads(), sub
 
 
-def cpu_single_thread(args, rows, steps):
-    """The same oracle timing with one OpenMP thread, in a child process (the thread count is
-    fixed when the library loads): phase-cell updates/s over `steps` steps of a strip of `rows`
-    rows of the workload, or None if the child fails."""
-    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
-            "from paper_2509_21832_gb300 import inputs as I; "
-            "pr = I.bump_specular(n=%d, nv=%d, eps=%r, seed=0); "
-            "v, t, c, sub = bench.cpu_baseline(pr, %d, %d); "
-            "print(json.dumps([v, t, c, sub.nx, sub.ny, sub.nphase]))"
-            % (os.path.dirname(os.path.abspath(__file__)), args.n, args.nv, args.eps, rows, steps))
-    env = dict(os.environ, OMP_NUM_THREADS="1")
-    try:
-        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                           timeout=300)
-        v, t, c, nx, ny, nph = json.loads(r.stdout.strip().splitlines()[-1])
-    except Exception:
-        return None
-    return {"value": v, "cores": c,
-            "sample": "%d steps of a %dx%d-row strip (%d phase cells), %.1f s"
-                      % (steps, nx, ny, nph, t)}
-
-
 def run_reference(args, pr, world, rank):
     if rank != 0:
         return
@@ -206,6 +205,46 @@ def config_of(pr, args):
             "seed": pr.meta.get("seed"),
             "l2": "inputs larger than L2: two %d MB FP64 phase-space buffers" % (g.nphase * 8 // 2**20),
             "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+def plain_variant(pr, stream, steps, oracle_rows, oracle_steps, name, compare=False):
+    """A plain FP64 workload other than the headline one: device-resident throughput over
+    `steps` steps (CUDA events on the context stream, per-kernel timing off), and the oracle as
+    it stands on this host's cores over `oracle_steps` steps of a strip of `oracle_rows` rows.
+    With compare, the oracle runs the same full problem and the line carries the largest
+    relative difference of the macro fields (max over cells of |Q_gpu - Q_oracle| over
+    max(max |Q_oracle,c|, max rho), per component)."""
+    import torch
+    from paper_2509_21832_gb300 import api
+    s = api.Solver(pr.grid, pr.params, stream=stream.cuda_stream)
+    s.set_state(pr.Q, pr.G)
+    s.step(pr.dt, pr.eps, 3)
+    s.sync()
+    s.set_state(pr.Q, pr.G)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(pr.dt, pr.eps, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    Qg, _ = s.get_moments(with_H=False)
+    s.close()
+    nph = pr.grid.nphase
+    cv, ct, cores, sub = cpu_baseline(pr, oracle_rows, oracle_steps)
+    out = {"variant": name, "eps": pr.eps, "steps": steps, "dtype": "f64",
+           "value": nph * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+           "phase_cells": nph,
+           "cpu_baseline": {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "%d steps of a %dx%d-row strip (%d phase cells), %.1f s"
+                                      % (oracle_steps, sub.nx, sub.ny, sub.nphase, ct)}}
+    if compare and sub.ny == pr.grid.ny and oracle_steps == steps:
+        from oracle import oracle as O
+        Qo, _, _ = O.step(pr.grid, pr.params, pr.Q, pr.G, pr.dt, pr.eps, steps)
+        scale = np.maximum(np.max(np.abs(Qo), axis=(1, 2)), np.max(Qo[0]))
+        out["max_rel_err_vs_oracle"] = float(np.max(np.max(np.abs(Qg - Qo), axis=(1, 2)) / scale))
+    return out
 
 
 def fp32_variant(args, stream):
@@ -372,6 +411,20 @@ def batch_variant(args, count=None, nmin=64, nmax=256, steps=None):
             "speedup_vs_separate_contexts": tsep / (tb / steps)}
 
 
+def summarize_variant(v):
+    """The headline line's short form of a variant (its full line is printed before it)."""
+    keep = ("value", "ms_per_step", "speedup_vs_fp64", "hbm_frac", "l1_density_rel_err_vs_fp64",
+            "speedup_vs_separate_contexts", "max_rel_err_vs_oracle", "steps", "eps")
+    out = {k: v[k] for k in keep if k in v}
+    if "cpu_baseline" in v:
+        out["cpu_baseline_value"] = v["cpu_baseline"]["value"]
+    if "cases" in v:
+        out["cases"] = [{k: c[k] for k in ("eps", "threshold", "speedup_vs_fp64",
+                                           "closure_fraction", "l1_density_rel_err_vs_fp64")}
+                        for c in v["cases"]]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -440,8 +493,8 @@ def main():
         solver.step(pr.dt, pr.eps, 1)
     solver.sync()
 
-    def timed_run(K):
-        solver.set_timing(True)
+    def timed_run(K, timing):
+        solver.set_timing(timing)
         sampler = ClockSampler(local)
         sampler.start()
         time.sleep(0.3)
@@ -460,22 +513,27 @@ def main():
         sampler.stop()
         solver.sync()
         ms = e0.elapsed_time(e1)
-        kt = solver.get_timing()
+        kt = solver.get_timing() if timing else None
         solver.set_timing(False)
         return ms, kt, sampler.summary()
 
-    ms, kt, clocks = timed_run(args.steps)
+    # the headline: K steps with the library's per-kernel events off
+    ms, _, clocks = timed_run(args.steps, False)
     bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
     if set(clocks["reasons"]) & bad:
-        ms, kt, clocks = timed_run(args.steps)
+        ms, _, clocks = timed_run(args.steps, False)
     ms = max_over_ranks(ms, pg, "cuda")
     nph = pr.grid.nphase
     value = replica_value(world, nph, args.steps, ms)
+    # the per-kernel split (and the roofline's kernel duration): the same K steps again with an
+    # event pair around every launch, on the context stream that the kernels run on
+    ms_split, kt, clocks_split = timed_run(args.steps, True)
     launches = sum(n for (_, n) in kt.values())
 
     peaks, peak_src = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = fp64_peak_tflops(sm_max)
+    fp64_units = fp64_peak_tflops(sm_max)
+    fp64_peak = measure_fp64_peak(stream)
     ky_ms, ky_n = kt["micro_y"]
     achieved = FLOPS_MICRO_Y * nph / (ky_ms / ky_n * 1e-3) / 1e12
     hbm_gbs = BYTES_PER_PHASE_FP64 * nph * args.steps / (ms * 1e-3) / 1e9
@@ -486,8 +544,11 @@ def main():
                 "traffic": (TRAFFIC_MICRO_Y_PER_PHASE_CELL * nph
                             if (pr.grid.nv1, pr.grid.nv2) == (32, 32) else None),
                 "traffic_unit": "bytes per launch",
-                "kernel": "micro_y", "peak_source": "FP64 peak from unit counts: 152 SMs x 4 "
-                "flop/clk x %.0f MHz" % sm_max,
+                "kernel": "micro_y",
+                "peak_source": "measured: FP64 FMA probe (mm_diag_fp64_fma), best of 5 launches "
+                               "on this GPU; unit counts give %.3f TFLOP/s (152 SMs x 4 flop/clk "
+                               "x %.0f MHz)" % (fp64_units, sm_max),
+                "split_run_ms_per_step": ms_split / args.steps,
                 "step_fp64_frac": FLOPS_STEP * nph * args.steps / (ms * 1e-3) / 1e12 / fp64_peak,
                 "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
                 "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_source": peak_src,
@@ -525,17 +586,28 @@ def main():
         v, t, cores, sub = cpu_baseline(pr, pr.grid.ny, n)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d steps of the full %dx%d grid (%d phase cells), %.1f s"
-                         % (n, sub.nx, sub.ny, sub.nphase, t),
-               "single_thread": cpu_single_thread(args, 32, 4)}
+                         % (n, sub.nx, sub.ny, sub.nphase, t)}
 
     variants = None
     if rank == 0 and not args.no_variants:
-        variants = {"riemann4_diffuse_1024x1024x24x24_fp32g": fp32_variant(args, stream),
-                    "batch_64_periodic_fp64": batch_variant(args),
-                    # where batching matters: many problems too small to fill the GPU alone
-                    "batch_256_small_periodic_fp64": batch_variant(args, count=256, nmin=16,
-                                                                   nmax=48, steps=50),
-                    "bump_specular_512x512x32x32_learned_closure": closure_variant(args, stream)}
+        full = {
+            # the 1D-2V Sod shock tube (200 x 24^2, 640 steps to t = 0.2), checked against the
+            # oracle's full run on this host
+            "sod_1d2v_200x24x24_fp64": plain_variant(I.sod_1d2v(), stream, 640, 1, 640,
+                                                      "sod_1d2v_200x24x24_fp64", compare=True),
+            # the headline workload at the other Knudsen number of its family
+            "bump_specular_256x256x32x32_eps1e-3_fp64": plain_variant(
+                I.bump_specular(n=args.n, nv=args.nv, eps=1e-3, seed=0), stream, args.steps, 32,
+                8, "bump_specular_256x256x32x32_eps1e-3_fp64"),
+            "riemann4_diffuse_1024x1024x24x24_fp32g": fp32_variant(args, stream),
+            "batch_64_periodic_fp64": batch_variant(args),
+            # where batching matters: many problems too small to fill the GPU alone
+            "batch_256_small_periodic_fp64": batch_variant(args, count=256, nmin=16, nmax=48,
+                                                           steps=50),
+            "bump_specular_512x512x32x32_learned_closure": closure_variant(args, stream)}
+        for k, v in full.items():
+            print(json.dumps(dict(v, variant=k)), flush=True)
+        variants = {k: summarize_variant(v) for k, v in full.items()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

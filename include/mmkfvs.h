@@ -337,6 +337,14 @@ void mm1d_destroy(mm1d_ctx* c);
 mm_status mm_diag_exp(const double* x_dev, double* y_fast_dev, double* y_lib_dev, size_t n,
                       void* cuda_stream);
 
+/* Diagnostic: the FP64 pipe's throughput.  Launches `ctas` CTAs of 256 threads on cuda_stream;
+ * each thread runs `iters` rounds of 8 independent FP64 fused multiply-adds d <- a d + b
+ * (a = 1 - 2^-20, b = 2^-30, d starting at 1 + lane/256) and writes the sum of its 8 chains to
+ * out_dev[thread] (caller-owned, ctas * 256 doubles).  The launch performs
+ * ctas * 256 * iters * 16 FP64 flops and is not synchronised, so that the caller can time it with
+ * events on cuda_stream.  MM_ERR_INVALID_ARG for ctas < 1, iters < 1 or out_dev NULL. */
+mm_status mm_diag_fp64_fma(double* out_dev, int ctas, int iters, void* cuda_stream);
+
 /* Diagnostic of the bounded device waits (the FP32-g kernels wait on an mbarrier for their bulk
  * copies, each wait giving up after a fixed number of attempts and setting an error bit that
  * mm_sync reports as MM_ERR_TIMEOUT).  One warp arms an mbarrier for a 16-byte copy; with

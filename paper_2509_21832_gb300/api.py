@@ -53,7 +53,7 @@ EXPORTS = ["mm_create", "mm_create_borrowed", "mm_scratch_bytes", "mm_device_byt
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
            "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp", "mm_step_host",
-           "mm_diag_bounded_wait",
+           "mm_diag_bounded_wait", "mm_diag_fp64_fma",
            "mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
            "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments", "mm_batch_get_g",
            "mm_batch_last_error", "mm_batch_destroy",
@@ -132,6 +132,8 @@ def load(build_if_needed: bool = True):
     L.mm_diag_exp.restype = ctypes.c_int
     L.mm_diag_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int, vp]
     L.mm_diag_bounded_wait.restype = ctypes.c_int
+    L.mm_diag_fp64_fma.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    L.mm_diag_fp64_fma.restype = ctypes.c_int
     L.mm_step_static_scratch.argtypes = [G, P, vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, vp, ctypes.c_char_p, ctypes.c_size_t]
     L.mm_step_static_scratch.restype = ctypes.c_int
@@ -303,6 +305,17 @@ def mm_diag_exp(x_dev, stream=0):
     if st != MM_OK:
         raise MMError(st, "mm_diag_exp")
     return yf, yl
+
+
+def mm_diag_fp64_fma(out_dev, ctas, iters, stream=0):
+    """Launch the FP64 FMA probe (ctas x 256 threads, iters rounds of 8 chains) on stream without
+    synchronising; out_dev is a float64 CUDA tensor of ctas * 256 elements.  Returns the flops."""
+    _dev_ptr(out_dev, ctas * 256)
+    st = load().mm_diag_fp64_fma(out_dev.data_ptr(), int(ctas), int(iters),
+                                 ctypes.c_void_p(int(stream)))
+    if st != MM_OK:
+        raise MMError(st, "mm_diag_fp64_fma")
+    return float(ctas) * 256 * iters * 16
 
 
 def mm_diag_bounded_wait(copy, spins=1 << 16, stream=0):

@@ -360,6 +360,25 @@ template void launch_micro_y_wall<float>(const float*, float*, double*, const do
                                          const int*, int, const KGrid&, const KParams&, double,
                                          double, const MicroShape&, int*, cudaStream_t, double*);
 
+// FP64 pipe probe: 8 independent FMA chains per thread, so that issue, not latency, bounds it.
+__global__ void k_diag_fp64_fma(double* __restrict__ out, int iters, double a, double b) {
+  double d[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) d[c] = 1.0 + (threadIdx.x + 32 * c) / 256.0;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) d[c] = fma(a, d[c], b);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) sum += d[c];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+void launch_diag_fp64_fma(double* out, int ctas, int iters, cudaStream_t s) {
+  k_diag_fp64_fma<<<ctas, 256, 0, s>>>(out, iters, 1.0 - 0x1p-20, 0x1p-30);
+}
+
 void launch_diag_exp(const double* x, double* yf, double* yl, size_t n, cudaStream_t s) {
   k_diag_exp<<<152 * 4, 256, 0, s>>>(x, yf, yl, n);
 }
@@ -372,6 +391,12 @@ void launch_convert_f32_to_f64(const float* in, double* out, size_t n, cudaStrea
 }
 
 }  // namespace mmk
+
+extern "C" mm_status mm_diag_fp64_fma(double* out_dev, int ctas, int iters, void* cuda_stream) {
+  if (!out_dev || ctas < 1 || iters < 1) return MM_ERR_INVALID_ARG;
+  mmk::launch_diag_fp64_fma(out_dev, ctas, iters, static_cast<cudaStream_t>(cuda_stream));
+  return cudaGetLastError() == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+}
 
 extern "C" mm_status mm_diag_exp(const double* x_dev, double* y_fast_dev, double* y_lib_dev,
                                  size_t n, void* cuda_stream) {

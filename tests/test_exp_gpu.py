@@ -24,3 +24,22 @@ def test_fast_exp_matches_library_exp_within_2_ulp():
     assert np.array_equal(yf[~fin], yl[~fin])
     # the exact values the paper-independent identities fix
     assert yf[-14] == 1.0 and yf[-13] == 1.0
+
+
+def test_fp64_fma_probe_computes_its_recurrence():
+    """The FP64-pipe probe that the benchmark times for its FP64 peak: each of a thread's 8
+    chains follows d <- a d + b, whose closed form is d_n = a^n d_0 + b (1 - a^n) / (1 - a)."""
+    import math
+    import torch
+    ctas, iters = 4, 1000
+    out = torch.empty(ctas * 256, dtype=torch.float64, device="cuda")
+    flops = api.mm_diag_fp64_fma(out, ctas, iters)
+    torch.cuda.synchronize()
+    assert flops == ctas * 256 * iters * 16
+    a, b = 1.0 - 2.0 ** -20, 2.0 ** -30
+    an = a ** iters
+    lane = np.arange(256)
+    want = sum(an * (1.0 + (lane + 32 * c) / 256.0) + b * (1 - an) / (1 - a) for c in range(8))
+    got = out.cpu().numpy().reshape(ctas, 256)
+    assert np.allclose(got, want[None, :], rtol=1e-12, atol=0)
+    assert math.isfinite(float(got.sum()))
