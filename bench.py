@@ -332,26 +332,29 @@ def closure_variant(args, stream):
         ms = e0.elapsed_time(e1)
         kt = s.get_timing()
         Q, _ = s.get_moments(with_H=False)
-        frac = None
+        frac, modes = None, None
         if mlp is not None:
             ncl, ncs = s.closure_stats()
             frac = ncl / ncs
+            modes = s.closure_steps()
         s.close()
-        return ms, kt, Q, frac
+        return ms, kt, Q, frac, modes
 
     for eps in (1e-3, 1e-2, 1e-1):
         pb = I.bump_specular(n=args.closure_n, nv=32, eps=eps, seed=7)
-        msp, _, Qp, _ = run(pb, None, 1e-3)
+        msp, ktp, Qp, _, _ = run(pb, None, 1e-3)
         for thr in (1e-3, 1e-2):
-            msh, kt, Qh, frac = run(pb, res.mlp, thr)
+            msh, kt, Qh, frac, modes = run(pb, res.mlp, thr)
             nst = args.closure_steps
             out["cases"].append({
                 "eps": eps, "threshold": thr, "plain_ms_per_step": msp / nst,
                 "hybrid_ms_per_step": msh / nst, "speedup_vs_fp64": msp / msh,
-                "closure_fraction": frac, "value": pb.grid.nphase * nst / (msh * 1e-3),
+                "closure_fraction": frac, "hybrid_steps": modes[0], "plain_fallback_steps": modes[1],
+                "value": pb.grid.nphase * nst / (msh * 1e-3),
                 "unit": UNIT,
                 "l1_density_rel_err_vs_fp64": float(np.sum(np.abs(Qh[0] - Qp[0])) / np.sum(np.abs(Qp[0]))),
-                "kernel_ms": {k: v[0] / v[1] for k, v in kt.items() if v[1]}})
+                "kernel_ms": {k: v[0] / v[1] for k, v in kt.items() if v[1]},
+                "plain_kernel_ms": {k: v[0] / v[1] for k, v in ktp.items() if v[1]}})
     res.mlp.close()
     return out
 
@@ -359,9 +362,10 @@ def closure_variant(args, stream):
 def batch_variant(args, count=None, nmin=64, nmax=256, steps=None):
     """count independent periodic problems (cells per side U{nmin..nmax}, velocity meshes
     16^2..32^2, eps log-uniform on [1e-3, 1], seeded Fourier-mode fields; by default the 64
-    problems of 64..256 cells per side), stepped as one batch: one persistent launch per phase,
-    the step replayed as a CUDA graph, autotuned CTA shape.  FP64.  Compared with stepping the
-    same problems through separate single-problem contexts, one after the other."""
+    problems of 64..256 cells per side), stepped as one batch: every call of K steps is one
+    persistent launch walking a work queue of (step, problem, phase, tile) items, replayed as a
+    CUDA graph, with autotuned tiles.  FP64.  Compared with stepping the same problems through
+    separate single-problem contexts, one after the other."""
     import torch
     from paper_2509_21832_gb300 import api
     from paper_2509_21832_gb300 import inputs as I
@@ -378,6 +382,7 @@ def batch_variant(args, count=None, nmin=64, nmax=256, steps=None):
     for q, p in enumerate(probs):
         b.set_state(q, p.Q, None)
     threads, ctas = b.autotune()
+    tiles = b.tiles()
     b.step(dts, epss, 2)
     b.sync()
     torch.cuda.synchronize()
@@ -406,7 +411,10 @@ def batch_variant(args, count=None, nmin=64, nmax=256, steps=None):
     return {"workload": "batch_%d_periodic_problems_%d_to_%d_cells_per_side"
                         % (len(probs), nmin, nmax), "phase_cells": nph,
             "steps": steps, "dtype": "f64", "value": nph * steps / tb, "unit": UNIT,
-            "ms_per_step": 1e3 * tb / steps, "autotuned": {"threads": threads, "ctas": ctas},
+            "ms_per_step": 1e3 * tb / steps,
+            "autotuned": {"threads": threads, "ctas": ctas, "cells_per_micro_item": tiles[0],
+                          "cells_per_cell_item": tiles[1]},
+            "launches_per_call": 1,
             "separate_contexts_ms_per_step": 1e3 * tsep,
             "speedup_vs_separate_contexts": tsep / (tb / steps)}
 
@@ -420,7 +428,8 @@ def summarize_variant(v):
         out["cpu_baseline_value"] = v["cpu_baseline"]["value"]
     if "cases" in v:
         out["cases"] = [{k: c[k] for k in ("eps", "threshold", "speedup_vs_fp64",
-                                           "closure_fraction", "l1_density_rel_err_vs_fp64")}
+                                           "closure_fraction", "plain_fallback_steps",
+                                           "l1_density_rel_err_vs_fp64")}
                         for c in v["cases"]]
     return out
 

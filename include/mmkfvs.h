@@ -193,28 +193,48 @@ void mm_destroy(mm_ctx* ctx);
 
 /* ---- batches of independent problems --------------------------------------------------------
  * Many independent problems of uneven size and Knudsen number stepped together (FP64; nv1 <=
- * 256).  Each phase of the step is one launch of a persistent kernel whose CTAs stride over the
- * cells of all problems; one batch step is captured in a CUDA graph and replayed; the CTA and grid
- * sizes of the phase-space kernels come from mm_batch_autotune (timed trial launches on the
- * batch's own data, cached per process by the multiset of problem shapes).  Problem q's arrays
- * have the single-problem layouts of this header. */
+ * 256), the batched form that the paper's MPI design has no counterpart of.  Every call of
+ * mm_batch_step is ONE launch of a persistent kernel for all of its steps: its CTAs take work
+ * items -- (step, problem, phase of the step of Section 5, tile of cells) -- from a queue in a
+ * fixed order and wait, before each item, until the phases it depends on are complete for the
+ * same problem.  Every wait is bounded (2 s); one that runs out ends the launch and is reported by
+ * mm_batch_sync as MM_ERR_TIMEOUT, with the device left usable.  The launch is captured in a CUDA
+ * graph (with the reset of its queue) and replayed.  The tile sizes (cells per item) come from
+ * mm_batch_autotune (timed trial steps on the batch's own state, cached per process by the
+ * multiset of problem shapes).  Problem q's arrays have the single-problem layouts of this
+ * header. */
 typedef struct mm_batch mm_batch;
 /* grids[nprob], params[nprob]: as for mm_create, each validated the same way.  cuda_stream NULL:
  * the batch creates its own non-blocking stream (graph capture needs a non-default stream). */
 mm_status mm_batch_create(int nprob, const mm_grid* grids, const mm_params* params,
                           void* cuda_stream, mm_batch** out);
-/* State of problem q from host memory (G_host NULL: g = 0); synchronous. */
+/* State of problem q from host memory (G_host NULL: g = 0); clears the device error word;
+ * synchronous. */
 mm_status mm_batch_set_state(mm_batch* b, int q, const double* Q_host, const double* G_host);
 /* nsteps steps of every problem, problem q with time step dt[q] and Knudsen number eps[q]
  * (host arrays of nprob values); asynchronous. */
 mm_status mm_batch_step(mm_batch* b, const double* dt, const double* eps, int nsteps);
-/* Choose the CTA size and grid size of the phase-space kernels by timing trial launches (the
- * state is not changed); best values written to the optional outputs.  Call after the first
- * mm_batch_step (so that dt, eps are set). */
+/* Choose the tile sizes of the work queue (cells per item of the phase-space phases: 1, 2, 4 or
+ * 8; of the per-cell phases: 1 or 4 CTAs' worth) by timing two-step trial launches on the batch's
+ * own state, which is saved before and restored after (the state is not changed; the batch
+ * temporarily holds a second copy of its g).  The CTA size (whole warps covering the widest v1
+ * mesh) and the persistent grid (every resident CTA) are written to the optional outputs.  Call
+ * after the first mm_batch_step (so that dt, eps are set). */
 mm_status mm_batch_autotune(mm_batch* b, int* threads_out, int* ctas_out);
-/* 1 (default): replay a captured CUDA graph of one batch step; 0: launch the kernels directly. */
+/* The current tile sizes: cells per item of the phase-space phases and of the per-cell ones. */
+mm_status mm_batch_tiles(const mm_batch* b, int* micro_cells, int* macro_cells);
+/* 1 (default): replay a captured CUDA graph of the launch; 0: launch the kernel directly. */
 mm_status mm_batch_set_graph(mm_batch* b, int enable);
-/* Wait and report device errors (MM_ERR_NONPHYSICAL). */
+/* Diagnostic of the bounded waits: with 0 <= q and 0 <= phase < 8 the following steps do not
+ * count the completed items of that phase of problem q (phases: 0 (u, T), 1 per-cell
+ * coefficients, 2 micro x, 3 micro y, 4 diffuse walls, 5 macro x half fluxes, 6 macro x
+ * transport, 7 macro y), so that the items that depend on it wait in vain and give up after
+ * wait_ms milliseconds (0 < wait_ms <= 60000); q < 0 or phase < 0 switches this off (waits back
+ * to 2 s).  The state is meaningless after such a step; mm_batch_set_state restores it and
+ * clears the error word. */
+mm_status mm_batch_diag_hold(mm_batch* b, int q, int phase, double wait_ms);
+/* Wait and report device errors: MM_ERR_TIMEOUT after a wait ran out, MM_ERR_NONPHYSICAL after
+ * a non-physical state. */
 mm_status mm_batch_sync(mm_batch* b);
 mm_status mm_batch_get_moments(mm_batch* b, int q, double* Q_host, double* H_host);
 mm_status mm_batch_get_g(mm_batch* b, int q, double* G_host);
@@ -263,6 +283,17 @@ void mm_mlp_destroy(mm_mlp* m);
  * outlive its use.  m = NULL switches the closure off; the next step then first resets every
  * non-current g to Ghat.  Resets the statistics.  FP32-g contexts: MM_ERR_INVALID_ARG. */
 mm_status mm_set_closure(mm_ctx* c, const mm_mlp* m, double threshold);
+/* Fallback of the hybrid step at low closure fractions (defaults: min_fraction 0.25, period
+ * 16).  With a closure set, every period-th step (counted from mm_set_closure or from this call)
+ * is a hybrid step whose number of closure cells is read back (mm_step waits for the device once
+ * there); when it is below min_fraction of the cells, the period - 1 steps that follow are plain
+ * steps (the full micro sweeps, the first one resetting the g of the closure cells to Ghat(Q^n)),
+ * else hybrid steps.  The choice depends only on the computed counts, so runs are reproducible.
+ * min_fraction 0 keeps every step hybrid; period 1 evaluates every step without reading back.
+ * MM_ERR_INVALID_ARG outside 0 <= min_fraction <= 1, period >= 1. */
+mm_status mm_set_closure_fallback(mm_ctx* c, double min_fraction, int period);
+/* Hybrid steps and plain fallback steps run since mm_set_closure. */
+mm_status mm_closure_steps(mm_ctx* c, long long* hybrid_steps, long long* plain_steps);
 /* Features X_dev [nc][39] (FP32) of the current state and aux_dev [5][ny][nx] (FP64: H_CE of
  * the four components, then the scale eps rho T^{3/2}); asynchronous. */
 mm_status mm_closure_features(mm_ctx* c, double dt, double eps, float* X_dev, double* aux_dev);

@@ -56,11 +56,12 @@ EXPORTS = ["mm_create", "mm_create_borrowed", "mm_scratch_bytes", "mm_device_byt
            "mm_diag_bounded_wait", "mm_diag_fp64_fma",
            "mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
            "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments", "mm_batch_get_g",
+           "mm_batch_tiles", "mm_batch_diag_hold",
            "mm_batch_last_error", "mm_batch_destroy",
            "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_forward",
            "mm_mlp_grad", "mm_mlp_train_step", "mm_mlp_last_error", "mm_mlp_destroy",
            "mm_set_closure", "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
-           "mm_closure_stats", "mm_mms_enable", "mm_mms_set_exact", "mm_mms_error",
+           "mm_closure_stats", "mm_set_closure_fallback", "mm_closure_steps", "mm_mms_enable", "mm_mms_set_exact", "mm_mms_error",
            "mm1d_create", "mm1d_set_state", "mm1d_step", "mm1d_get_state", "mm1d_mms_enable",
            "mm1d_mms_set_exact", "mm1d_last_error", "mm1d_destroy"]
 
@@ -117,6 +118,8 @@ def load(build_if_needed: bool = True):
     L.mm_batch_step.argtypes = [vp, _dp, _dp, ctypes.c_int]
     L.mm_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.mm_batch_set_graph.argtypes = [vp, ctypes.c_int]
+    L.mm_batch_tiles.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.mm_batch_diag_hold.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
     L.mm_batch_sync.argtypes = [vp]
     L.mm_batch_get_moments.argtypes = [vp, ctypes.c_int, vp, vp]
     L.mm_batch_get_g.argtypes = [vp, ctypes.c_int, vp]
@@ -126,7 +129,7 @@ def load(build_if_needed: bool = True):
     L.mm_batch_destroy.restype = None
     for name in ["mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
                  "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments",
-                 "mm_batch_get_g"]:
+                 "mm_batch_get_g", "mm_batch_tiles", "mm_batch_diag_hold"]:
         getattr(L, name).restype = ctypes.c_int
     L.mm_diag_exp.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
     L.mm_diag_exp.restype = ctypes.c_int
@@ -154,6 +157,9 @@ def load(build_if_needed: bool = True):
     L.mm_closure_flags.argtypes = [vp, vp]
     L.mm_closure_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]
+    L.mm_set_closure_fallback.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.mm_closure_steps.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)]
     G1, P1 = ctypes.POINTER(mm1d_grid), ctypes.POINTER(mm1d_params)
     L.mm1d_create.argtypes = [G1, P1, vp, ctypes.POINTER(vp)]
     L.mm1d_set_state.argtypes = [vp, vp, vp]
@@ -178,7 +184,7 @@ def load(build_if_needed: bool = True):
                  "mm_get_timing", "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params",
                  "mm_mlp_forward", "mm_mlp_grad", "mm_mlp_train_step", "mm_set_closure",
                  "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
-                 "mm_closure_stats"]:
+                 "mm_closure_stats", "mm_set_closure_fallback", "mm_closure_steps"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -493,6 +499,17 @@ class Solver:
                "mm_closure_stats")
         return a.value, b.value
 
+    def set_closure_fallback(self, min_fraction, period):
+        _check(self.ctx, self.L.mm_set_closure_fallback(self.ctx, float(min_fraction),
+                                                        int(period)), "mm_set_closure_fallback")
+
+    def closure_steps(self):
+        """(hybrid steps, plain fallback steps) since the closure was set."""
+        a, b = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        _check(self.ctx, self.L.mm_closure_steps(self.ctx, ctypes.byref(a), ctypes.byref(b)),
+               "mm_closure_steps")
+        return a.value, b.value
+
 
 def _f32_ptr(t, n):
     if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4):
@@ -698,6 +715,17 @@ class BatchSolver:
 
     def set_graph(self, enable):
         self._check(self.L.mm_batch_set_graph(self.b, int(enable)), "mm_batch_set_graph")
+
+    def tiles(self):
+        """(cells per item of the phase-space phases, cells per item of the per-cell phases)."""
+        a, c = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.L.mm_batch_tiles(self.b, ctypes.byref(a), ctypes.byref(c)),
+                    "mm_batch_tiles")
+        return a.value, c.value
+
+    def diag_hold(self, q, phase, wait_ms=50.0):
+        self._check(self.L.mm_batch_diag_hold(self.b, int(q), int(phase), float(wait_ms)),
+                    "mm_batch_diag_hold")
 
     def sync(self):
         self._check(self.L.mm_batch_sync(self.b), "mm_batch_sync")

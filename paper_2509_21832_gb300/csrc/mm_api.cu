@@ -83,6 +83,15 @@ struct mm_ctx {
   int* ccounts = nullptr;                // their lengths [3]
   unsigned long long* cstat = nullptr;   // closure cells summed over hybrid steps
   long long closure_steps = 0;
+  // fallback at low closure fractions: every cl_period-th step is a hybrid step whose closure
+  // count decides the next cl_period - 1 steps (plain when below cl_min_frac of the cells)
+  double cl_min_frac = 0.25;
+  int cl_period = 16;
+  int cl_left = 0;                        // steps before the next evaluation
+  bool cl_plain = false;                  // the steps until then run the plain step
+  unsigned long long cl_seen = 0;         // cstat at the last evaluation
+  unsigned long long* cl_host = nullptr;  // pinned copy of cstat
+  long long fallback_steps = 0;           // plain steps run in place of hybrid ones
   int blocks_x = 0, blocks_y = 0, blocks_g = 0;
   // manufactured-solution harness (FP64 contexts)
   bool mms = false;
@@ -343,10 +352,46 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   c->closure_steps += 1;
 }
 
-void enqueue_step(mm_ctx* c, double dt, double eps) {
+// A step with the closure set: an evaluation (hybrid) step every cl_period steps, whose closure
+// count (read back once, the one wait of the evaluation) decides whether the following
+// cl_period - 1 steps are hybrid or plain; a plain step after hybrid ones first resets the g of
+// the closure cells to Ghat(Q^n) (cstale).  The choice depends only on the computed counts, so
+// a run is reproducible.
+mm_status enqueue_closure_step(mm_ctx* c, double dt, double eps) {
+  if (c->cl_left > 0) {
+    --c->cl_left;
+    if (c->cl_plain) {
+      enqueue_plain<double>(c, dt, eps);
+      ++c->fallback_steps;
+    } else {
+      enqueue_hybrid(c, dt, eps);
+    }
+    return MM_OK;
+  }
+  enqueue_hybrid(c, dt, eps);
+  if (c->cl_period <= 1) return MM_OK;
+  if (!c->cl_host) {
+    cudaError_t e = cudaMallocHost((void**)&c->cl_host, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(c, e, "closure count buffer");
+  }
+  cudaError_t e = cudaMemcpyAsync(c->cl_host, c->cstat, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "closure count");
+  const unsigned long long now = *c->cl_host;
+  const double count = (double)(now - c->cl_seen);
+  c->cl_seen = now;
+  c->cl_plain = count < c->cl_min_frac * (double)c->ncell;
+  if (c->cl_plain) c->cstale = true;
+  c->cl_left = c->cl_period - 1;
+  return MM_OK;
+}
+
+mm_status enqueue_step(mm_ctx* c, double dt, double eps) {
   if (c->fp32) enqueue_plain<float>(c, dt, eps);
-  else if (c->mlp) enqueue_hybrid(c, dt, eps);
+  else if (c->mlp) return enqueue_closure_step(c, dt, eps);
   else enqueue_plain<double>(c, dt, eps);
+  return MM_OK;
 }
 
 constexpr int kHostChunks = 16;  // row chunks of g in mm_step_host
@@ -783,7 +828,10 @@ mm_status mm_step(mm_ctx* c, double dt, double eps, int nsteps) {
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, MM_ERR_INVALID_ARG, "eps must be > 0");
   if (nsteps < 0) return fail(c, MM_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (!c->have_state) return fail(c, MM_ERR_STATE, "mm_step before mm_set_state");
-  for (int n = 0; n < nsteps; ++n) enqueue_step(c, dt, eps);
+  for (int n = 0; n < nsteps; ++n) {
+    mm_status st = enqueue_step(c, dt, eps);
+    if (st != MM_OK) return st;
+  }
   if (c->borrowed && c->G != c->user_G) {
     // FP32 g ping-pongs between G and the scratch copy: leave the state in the caller's buffer
     cudaMemcpyAsync(c->user_G, c->G, c->nphase * sizeof(float), cudaMemcpyDeviceToDevice,
@@ -980,6 +1028,28 @@ mm_status mm_set_closure(mm_ctx* c, const mm_mlp* m, double threshold) {
   c->closure_thr = threshold;
   c->closure_steps = 0;
   c->cstale = false;
+  c->cl_left = 0;
+  c->cl_plain = false;
+  c->cl_seen = 0;
+  c->fallback_steps = 0;
+  return MM_OK;
+}
+
+mm_status mm_set_closure_fallback(mm_ctx* c, double min_fraction, int period) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (!(min_fraction >= 0.0 && min_fraction <= 1.0) || period < 1)
+    return fail(c, MM_ERR_INVALID_ARG, "need 0 <= min_fraction <= 1 and period >= 1");
+  c->cl_min_frac = min_fraction;
+  c->cl_period = period;
+  c->cl_left = 0;
+  c->cl_plain = false;
+  return MM_OK;
+}
+
+mm_status mm_closure_steps(mm_ctx* c, long long* hybrid_steps, long long* plain_steps) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (hybrid_steps) *hybrid_steps = c->closure_steps;
+  if (plain_steps) *plain_steps = c->fallback_steps;
   return MM_OK;
 }
 
@@ -1066,6 +1136,7 @@ const char* mm_kernel_name(int idx) {
 }
 
 void mm_destroy(mm_ctx* c) {
+  if (c && c->cl_host) cudaFreeHost(c->cl_host);
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   destroy_events(c);

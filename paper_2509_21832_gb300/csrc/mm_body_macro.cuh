@@ -7,6 +7,13 @@
 #include "mm_exp.cuh"
 #include "mm_internal.cuh"
 
+// Pointer qualifier of the device bodies: __restrict__ by default; a translation unit whose
+// kernel reads data that other CTAs of the same launch wrote defines MMK_R as empty before
+// including this header, so that no load of the bodies may take the non-coherent read-only path.
+#ifndef MMK_R
+#define MMK_R __restrict__
+#endif
+
 namespace mmk {
 namespace macro_body {
 
@@ -198,7 +205,7 @@ __device__ __forceinline__ void uT_of(const double* Q, int nc, int c, double& u1
 
 // (u1, u2, T) of cell c into its per-cell fields (the values uT_of gives, bit for bit), so that
 // the prims of its neighbours read them instead of recomputing them.
-__device__ __forceinline__ void uT_body(const double* __restrict__ Q, double* __restrict__ prim,
+__device__ __forceinline__ void uT_body(const double* MMK_R Q, double* MMK_R prim,
                                         int nc, int c) {
   double u1, u2, T;
   uT_of(Q, nc, c, u1, u2, T);
@@ -247,9 +254,9 @@ __device__ __forceinline__ void side_uT(const double* Q, const double* prim, con
 // Per-cell fields of cell c.  FROM_PRIM: the neighbours' (u1, u2, T) are already in prim (written
 // by uT_body over all cells); otherwise they are recomputed from Q.  ieps = 1/eps.
 template <bool FROM_PRIM = false>
-__device__ __forceinline__ void prims_body(const double* __restrict__ Q, double* __restrict__ prim,
-                        float* __restrict__ primf, KGrid g, KParams p, double dt, double eps,
-                        double ieps, int* __restrict__ err, int c) {
+__device__ __forceinline__ void prims_body(const double* MMK_R Q, double* MMK_R prim,
+                        float* MMK_R primf, KGrid g, KParams p, double dt, double eps,
+                        double ieps, int* MMK_R err, int c) {
   const int nc = g.nx * g.ny;
   const int i = c % g.nx, j = c / g.nx;
   const double rho = Q[c];
@@ -361,8 +368,8 @@ __device__ __forceinline__ void boundary_face(const KParams& p, const double qc[
 
 // (1) collision half step with tau^n: Q^n -> Q*, and the x half fluxes of Q* (plus the fluxes
 // through the non-periodic x boundary faces).
-__device__ __forceinline__ void macro_x1_body(const double* __restrict__ Qn, MacroBufs mb, KGrid g, KParams p,
-                           double dt, double eps, int* __restrict__ err, int c) {
+__device__ __forceinline__ void macro_x1_body(const double* MMK_R Qn, MacroBufs mb, KGrid g, KParams p,
+                           double dt, double eps, int* MMK_R err, int c) {
   const int nc = g.nx * g.ny;
   const int i = c % g.nx, j = c / g.nx;
   double q[6], qs[6];
@@ -389,8 +396,8 @@ __device__ __forceinline__ void macro_x1_body(const double* __restrict__ Qn, Mac
 }
 
 // (2) x transport (Eq. 5-103, first line): Q* -> Q**, then the y half fluxes of Q**.
-__device__ __forceinline__ void macro_x2_body(const double* __restrict__ H, MacroBufs mb, KGrid g, KParams p,
-                           double dt, int* __restrict__ err, int c) {
+__device__ __forceinline__ void macro_x2_body(const double* MMK_R H, MacroBufs mb, KGrid g, KParams p,
+                           double dt, int* MMK_R err, int c) {
   const int nc = g.nx * g.ny;
   const int i = c % g.nx, j = c / g.nx;
   const int cl = j * g.nx + (i > 0 ? i - 1 : g.nx - 1);
@@ -443,9 +450,9 @@ __device__ __forceinline__ void macro_x2_body(const double* __restrict__ H, Macr
 
 // (3) y transport (Eq. 5-103, second line), then the collision half step with tau***:
 // Q** -> Q^{n+1}.
-__device__ __forceinline__ void macro_y_body(const double* __restrict__ H, MacroBufs mb, double* __restrict__ Qn,
-                          KGrid g, KParams p, double dt, double eps, int* __restrict__ err, int c,
-                          const double* __restrict__ srcq = nullptr) {
+__device__ __forceinline__ void macro_y_body(const double* MMK_R H, MacroBufs mb, double* MMK_R Qn,
+                          KGrid g, KParams p, double dt, double eps, int* MMK_R err, int c,
+                          const double* MMK_R srcq = nullptr) {
   const int nc = g.nx * g.ny;
   const int i = c % g.nx, j = c / g.nx;
   const int cb = (j > 0 ? j - 1 : g.ny - 1) * g.nx + i;

@@ -7,6 +7,13 @@
 #include "mm_exp.cuh"
 #include "mm_internal.cuh"
 
+// Pointer qualifier of the device bodies: __restrict__ by default; a translation unit whose
+// kernel reads data that other CTAs of the same launch wrote defines MMK_R as empty before
+// including this header, so that no load of the bodies may take the non-coherent read-only path.
+#ifndef MMK_R
+#define MMK_R __restrict__
+#endif
+
 namespace mmk {
 namespace micro_body {
 
@@ -95,7 +102,7 @@ __device__ __forceinline__ bool diffuse_wall_cell(const KGrid& g, const KParams&
 // for any g in exactly the same way, and the next x sweep takes the moments of its upwind
 // differences from two cells' sums instead of from every velocity.  Only for one row per pass
 // (R = 1: the thread of column k holds all its rows).
-__device__ __forceinline__ void store_row_sums(double* __restrict__ Rm, int cell, int nv1, int k,
+__device__ __forceinline__ void store_row_sums(double* MMK_R Rm, int cell, int nv1, int k,
                                                double R0, double R1, double R2) {
   double* o = Rm + (size_t)cell * 3 * nv1 + k;
   o[0] = R0;
@@ -106,9 +113,9 @@ __device__ __forceinline__ void store_row_sums(double* __restrict__ Rm, int cell
 // The row sums of cell `cell` of G (blockDim >= nv1; thread k = column k); vt holds v2 and v2^2
 // of every row ([2][nv2], formed as fma(l + 1/2, dv2, v2min) and its square).
 template <typename Tg>
-__device__ __forceinline__ void row_sums_body(const Tg* __restrict__ G, double* __restrict__ Rm,
+__device__ __forceinline__ void row_sums_body(const Tg* MMK_R G, double* MMK_R Rm,
                                               const KGrid& g, int cell,
-                                              const double* __restrict__ vt) {
+                                              const double* MMK_R vt) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int k = threadIdx.x;
   if (k >= nv1) return;
@@ -147,11 +154,11 @@ __device__ __forceinline__ void central_sums(double u2, double R0, double R1, do
 // NR > 0: every active thread owns exactly NR rows (nv2 == NR R); the upwind differences of pass
 // 1 stay in registers for pass 2.  NR = 0: any shape, differences recomputed in pass 2.
 template <typename Tg, int NR = 0>
-__device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
-                                                    Tg* __restrict__ Gout,
-                                                    const double* __restrict__ prim, KGrid g,
+__device__ __forceinline__ void micro_x_body(const Tg* MMK_R Gin,
+                                                    Tg* MMK_R Gout,
+                                                    const double* MMK_R prim, KGrid g,
                                                     KParams p, double dtidx, int R, int cell, double* sm,
-                                                    double* __restrict__ Ee = nullptr) {
+                                                    double* MMK_R Ee = nullptr) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   double* red = sm;
   double* c2t = sm + kRed;
@@ -270,11 +277,11 @@ __device__ __forceinline__ void micro_x_body(const Tg* __restrict__ Gin,
 // With Ee it also leaves the cell's Maxwellian factors for the y sweep, which needs the same
 // ones: Ee[cell (nv1 + nv2) + k] = e1(k), Ee[cell (nv1 + nv2) + nv1 + l] = e2(l).
 template <typename Tg>
-__device__ __forceinline__ void micro_x_rows_body(const Tg* __restrict__ Gin,
-                                                  Tg* __restrict__ Gout,
-                                                  const double* __restrict__ prim,
-                                                  const double* __restrict__ Rm,
-                                                  double* __restrict__ Ee, KGrid g, KParams p,
+__device__ __forceinline__ void micro_x_rows_body(const Tg* MMK_R Gin,
+                                                  Tg* MMK_R Gout,
+                                                  const double* MMK_R prim,
+                                                  const double* MMK_R Rm,
+                                                  double* MMK_R Ee, KGrid g, KParams p,
                                                   double dtidx, int cell, double* sm) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   double* red = sm;
@@ -363,15 +370,15 @@ __device__ __forceinline__ void micro_x_rows_body(const Tg* __restrict__ Gin,
 constexpr int kYTables = 13;
 
 template <typename Tg>
-__device__ __forceinline__ void micro_y_body(const Tg* __restrict__ Gs,
-                                                    Tg* __restrict__ Gout,
-                                                    double* __restrict__ Hout,
-                                                    const double* __restrict__ prim, KGrid g,
+__device__ __forceinline__ void micro_y_body(const Tg* MMK_R Gs,
+                                                    Tg* MMK_R Gout,
+                                                    double* MMK_R Hout,
+                                                    const double* MMK_R prim, KGrid g,
                                                     KParams p, double dtidy, double hscale, int R,
-                                                    int* __restrict__ err, int cell, double* sm,
-                                                    const double* __restrict__ src = nullptr,
-                                                    double* __restrict__ Rm = nullptr,
-                                                    const double* __restrict__ Ee = nullptr) {
+                                                    int* MMK_R err, int cell, double* sm,
+                                                    const double* MMK_R src = nullptr,
+                                                    double* MMK_R Rm = nullptr,
+                                                    const double* MMK_R Ee = nullptr) {
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;
   const int i = cell % g.nx, j = cell / g.nx;
@@ -558,11 +565,11 @@ __device__ __forceinline__ double wall_R(double ua, double Taa, double Tw, doubl
 }
 
 template <typename Tg>
-__device__ __forceinline__ void micro_y_wall_body(const Tg* __restrict__ Gs, Tg* __restrict__ Gout,
-                               double* __restrict__ Hout, const double* __restrict__ prim,
+__device__ __forceinline__ void micro_y_wall_body(const Tg* MMK_R Gs, Tg* MMK_R Gout,
+                               double* MMK_R Hout, const double* MMK_R prim,
                                KGrid g, KParams p, double dt,
-                               double eps, int R, int* __restrict__ err, int cell, double* sm,
-                               double* __restrict__ Rm = nullptr) {
+                               double eps, int R, int* MMK_R err, int cell, double* sm,
+                               double* MMK_R Rm = nullptr) {
   double* red = sm;
   const int nv1 = g.nv1, nv2 = g.nv2;
   const int nc = g.nx * g.ny;

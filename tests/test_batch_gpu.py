@@ -112,3 +112,62 @@ def test_full_size_batch_matches_single_contexts():
             Gs = s.get_g()
         assert np.array_equal(Qb, Qs) and np.array_equal(Hb, Hs) and np.array_equal(Gb, Gs), \
             (q, p.grid.nx, p.grid.ny, p.grid.nv1, p.eps)
+
+
+def test_one_launch_for_many_steps_equals_launch_per_step():
+    """A call of several steps is one persistent launch whose queue holds every step's items;
+    its results equal those of one launch per step bit for bit (the queue only orders work)."""
+    probs = mixed_batch()
+    many = run_batch(probs, 5)
+    with api.BatchSolver([p[0] for p in probs], [p[1] for p in probs]) as b:
+        for q, (g, p, eps, Q, G, dt) in enumerate(probs):
+            b.set_state(q, Q, G)
+        for _ in range(5):
+            b.step([p[5] for p in probs], [p[2] for p in probs], 1)
+        b.sync()
+        one = [b.get_moments(q) + (b.get_g(q),) for q in range(len(probs))]
+    for (Qa, Ha, Ga), (Qb, Hb, Gb) in zip(many, one):
+        assert np.array_equal(Qa, Qb) and np.array_equal(Ga, Gb) and np.array_equal(Ha, Hb)
+
+
+@pytest.mark.parametrize("q,phase,nsteps", [(1, 2, 1), (3, 4, 1), (0, 7, 3)])
+def test_bounded_wait_runs_out_and_reports_timeout(q, phase, nsteps):
+    """A dependency that is never released (the completions of one phase of one problem are not
+    counted) makes the items waiting on it give up after the wait bound: mm_batch_sync reports
+    MM_ERR_TIMEOUT, the launch ends within a few wait bounds, no fault is raised, and after the
+    state is set again the batch steps exactly as a fresh one.  Holding the last phase of a
+    problem with three steps in the launch stalls the next step's first phases."""
+    import time
+    probs = mixed_batch()
+    ref = run_batch(probs, 2)
+    dts, epss = [p[5] for p in probs], [p[2] for p in probs]
+    with api.BatchSolver([p[0] for p in probs], [p[1] for p in probs]) as b:
+        for k, (g, p, eps, Q, G, dt) in enumerate(probs):
+            b.set_state(k, Q, G)
+        b.diag_hold(q, phase, 50.0)
+        t0 = time.perf_counter()
+        b.step(dts, epss, nsteps)
+        with pytest.raises(api.MMError) as e:
+            b.sync()
+        assert e.value.status == api.MM_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 10.0
+        b.diag_hold(-1, -1)
+        for k, (g, p, eps, Q, G, dt) in enumerate(probs):
+            b.set_state(k, Q, G)
+        b.step(dts, epss, 2)
+        b.sync()
+        got = [b.get_moments(k) + (b.get_g(k),) for k in range(len(probs))]
+    for (Qa, Ha, Ga), (Qb, Hb, Gb) in zip(ref, got):
+        assert np.array_equal(Qa, Qb) and np.array_equal(Ga, Gb) and np.array_equal(Ha, Hb)
+
+
+def test_autotuned_tiles_are_reported():
+    probs = mixed_batch()
+    with api.BatchSolver([p[0] for p in probs], [p[1] for p in probs]) as b:
+        for k, (g, p, eps, Q, G, dt) in enumerate(probs):
+            b.set_state(k, Q, G)
+        b.step([p[5] for p in probs], [p[2] for p in probs], 1)
+        threads, ctas = b.autotune()
+        tm, tc = b.tiles()
+        assert threads == 32 and ctas >= 152
+        assert tm in (1, 2, 4, 8) and tc in (threads, 4 * threads)

@@ -203,6 +203,7 @@ def test_hybrid_steps_match_oracle(name, gk, bc, eps):
     with api.Solver(g, p) as s:
         s.set_state(Q, G0)
         s.set_closure(mlp, thr)
+        s.set_closure_fallback(0.0, 1)  # both steps hybrid, as in the oracle's run
         s.step(dt, eps, 2)
         s.sync()
         Qg, Hg = s.get_moments()
@@ -247,6 +248,7 @@ def test_switching_the_closure_off_resets_stale_g():
     with api.Solver(g, p) as s:
         s.set_state(Q, G0)
         s.set_closure(mlp, thr)
+        s.set_closure_fallback(0.0, 1)
         s.step(dt, eps, 2)
         s.set_closure(None, 0.0)
         s.step(dt, eps, 1)
@@ -307,4 +309,44 @@ def test_closure_rejects_fp32_contexts_and_bad_thresholds():
             with pytest.raises(api.MMError):
                 s.set_closure(mlp, bad)
         s.set_closure(None, 0.0)
+    mlp.close()
+
+
+def test_low_closure_fraction_falls_back_to_plain_steps():
+    """Below the minimum closure fraction, the steps that follow an evaluation step are plain:
+    the first of them the oracle's plain step with the closure cells' g reset to Ghat(Q^n), the
+    next ones plain oracle steps; the next evaluation step is hybrid again."""
+    g = I.Grid(nx=12, ny=10, nv1=16, nv2=16)
+    p = I.Params(nu=-0.5, bc=(I.SPECULAR,) * 4)
+    Q = I.smooth_state(g, 51, amp=0.2, umax=0.25, aniso=0.05)
+    G0 = I.seeded_g(g, 52, amp=0.02)
+    dt, eps = 0.5 / (16.0 * 12 + 16.0 * 10), 1e-2
+    X, _, _ = C.features(g, p, Q, eps, dt)
+    params, norm = _params(14), _data_norm(X, 15)
+    wq = M.bf16_round(params)
+    net = lambda X: M.forward(wq, norm.astype(np.float64), X)
+    interior = ~C.boundary_cells(g, p)
+    ind0 = np.max(np.abs(net(X)), axis=1).reshape(g.ny, g.nx)
+    for thr in _gap_thresholds(ind0, interior):
+        Q1, G1, H1, fo, io, ro = C.hybrid_run(g, p, Q, G0, dt, eps, net, thr, nsteps=1)
+        if min(np.min(np.abs(i[interior] - thr)) for i in io) / thr > 5e-4 and fo[0].sum() > 0:
+            break
+    none = np.zeros_like(fo[0])
+    Q2, G2, H2 = O.step_closure(g, p, Q1, G1, dt, eps, none, fo[0], np.zeros((4, g.ny, g.nx)))
+    Qo, Go, Ho = O.step(g, p, Q2, G2, dt, eps, 1)
+    mlp = api.MLP(params, norm)
+    with api.Solver(g, p) as s:
+        s.set_state(Q, G0)
+        s.set_closure(mlp, thr)
+        s.set_closure_fallback(1.0, 4)  # any closure fraction is below 1: fall back
+        s.step(dt, eps, 3)
+        s.sync()
+        Qg, Hg = s.get_moments()
+        Gg = s.get_g()
+        assert s.closure_steps() == (1, 2)
+        s.step(dt, eps, 2)  # the fourth step is plain, the fifth an evaluation again
+        assert s.closure_steps() == (2, 3)
+    assert np.all(q_rel_err(Qg, Qo) <= 1e-12)
+    rho = np.asarray(Q).reshape(6, g.ny, g.nx)[0]
+    assert np.max(np.abs(Gg - Go)) <= max(1e-11 * np.max(np.abs(Go)), 64 * ULP * np.max(rho) / eps)
     mlp.close()
