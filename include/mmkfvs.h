@@ -138,6 +138,15 @@ mm_status mm_set_state_device(mm_ctx* ctx, const double* Q_dev, const double* G_
 mm_status mm_set_state_prim(mm_ctx* ctx, const double* rho, const double* u1, const double* u2,
                             const double* T);
 
+/* The caller changed g (in place, in the buffer of a context from mm_create_borrowed) in the
+ * cells [i0, i1) x [j0, j1) -- the halo cells of a block of a spatially decomposed problem after
+ * an exchange with its neighbours (Section 5.5 distributes the grid this way): the library
+ * re-forms what it keeps derived from g there (the row sums of g that FP64 contexts with one row
+ * per pass keep for the x sweep); nothing else is needed before the next mm_step.  Asynchronous
+ * on the context stream, which must be ordered after the caller's writes.  MM_ERR_INVALID_ARG for
+ * a region outside the grid. */
+mm_status mm_g_region_changed(mm_ctx* ctx, int i0, int i1, int j0, int j1);
+
 /* Advance nsteps time steps of size dt at Knudsen number eps (Section 5: micro x sweep, micro y
  * sweep, backward-Euler relaxation, heat-flux moments, then the Strang-split macro update).
  * Asynchronous on the context stream.  dt > 0, eps > 0, nsteps >= 0. */

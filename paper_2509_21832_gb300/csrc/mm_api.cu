@@ -102,6 +102,10 @@ struct mm_ctx {
   double* mms_src_q = nullptr;           // int (1, v, v v) S dv [6][ny][nx]
   // mm_step_host: streams for the row-chunk copies of g and for the x sweeps; events per chunk
   cudaStream_t cstream = nullptr, xstream = nullptr, ystream = nullptr;
+  // FP32 g: the collision half step and x half fluxes of Q^n run on mstream beside the
+  // phase-space kernel (they need only Q^n); ev_fork marks Q^n, ev_x1 their end
+  cudaStream_t mstream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_x1 = nullptr;
   std::vector<cudaEvent_t> chunk_events;
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -250,6 +254,25 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   const KGrid& g = c->kg;
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
+  bool x1_side = false;
+  if constexpr (sizeof(Tg) == sizeof(float)) {
+    // macro x1 (collision half step and x half fluxes of Q^n) beside the phase-space kernel
+    cudaError_t e = cudaSuccess;
+    if (!c->mstream) e = cudaStreamCreateWithFlags(&c->mstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->ev_fork)
+      e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !c->ev_x1)
+      e = cudaEventCreateWithFlags(&c->ev_x1, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->mstream, c->ev_fork, 0);
+    if (e == cudaSuccess) {
+      timed_on(c, T_MACRO_X1, c->mstream, [&] {
+        launch_macro_x1(c->Q, c->mb, c->kg, c->kp, dt, eps, c->err, c->mstream);
+      });
+      x1_side = cudaEventRecord(c->ev_x1, c->mstream) == cudaSuccess;
+    }
+    if (!x1_side) cudaGetLastError();  // side stream unavailable: macro x1 runs in order below
+  }
   enqueue_prims(c, dt, eps, s);
   const double* srcg = nullptr;
   const double* srcq = nullptr;
@@ -304,7 +327,8 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
                                 c->ms, c->err, s, c->rmom);
       });
   }
-  timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
+  if (x1_side) cudaStreamWaitEvent(s, c->ev_x1, 0);
+  else timed(c, T_MACRO_X1, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, s); });
   timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
   timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s, srcq); });
 }
@@ -822,6 +846,17 @@ mm_status mm_set_state_device(mm_ctx* c, const double* Q_dev, const double* G_de
   return MM_OK;
 }
 
+mm_status mm_g_region_changed(mm_ctx* c, int i0, int i1, int j0, int j1) {
+  if (!c) return MM_ERR_INVALID_ARG;
+  if (i0 < 0 || j0 < 0 || i1 > c->grid.nx || j1 > c->grid.ny || i0 > i1 || j0 > j1)
+    return fail(c, MM_ERR_INVALID_ARG, "region outside the grid");
+  if (c->rmom)
+    launch_row_sums_rect(static_cast<const double*>(c->G), c->rmom, c->kg, i0, i1, j0, j1,
+                         c->stream);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "row sums of a region");
+}
+
 mm_status mm_step(mm_ctx* c, double dt, double eps, int nsteps) {
   if (!c) return MM_ERR_INVALID_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, MM_ERR_INVALID_ARG, "dt must be > 0");
@@ -1136,11 +1171,13 @@ const char* mm_kernel_name(int idx) {
 }
 
 void mm_destroy(mm_ctx* c) {
-  if (c && c->cl_host) cudaFreeHost(c->cl_host);
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->cl_host) cudaFreeHost(c->cl_host);
   destroy_events(c);
-  for (cudaStream_t t : {c->cstream, c->xstream, c->ystream})
+  for (cudaEvent_t ev : {c->ev_fork, c->ev_x1})
+    if (ev) cudaEventDestroy(ev);
+  for (cudaStream_t t : {c->cstream, c->xstream, c->ystream, c->mstream})
     if (t) {
       cudaStreamSynchronize(t);
       cudaStreamDestroy(t);

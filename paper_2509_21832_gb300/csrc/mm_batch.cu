@@ -135,7 +135,10 @@ __device__ bool wait_deps(const MegaArgs& a, const unsigned* cur, const unsigned
 }
 
 // The whole of nsteps batch steps: persistent CTAs of blockDim.x threads take queue items.
-__global__ void k_batch_steps(MegaArgs a) {
+#ifndef MM_BATCH_MINB
+#define MM_BATCH_MINB 16
+#endif
+__global__ void __launch_bounds__(32, MM_BATCH_MINB) k_batch_steps(MegaArgs a) {
   extern __shared__ double sm[];
   __shared__ int s_item;
   const int t = threadIdx.x, T = blockDim.x;

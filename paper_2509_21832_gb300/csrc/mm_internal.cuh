@@ -102,6 +102,8 @@ void launch_micro_x_rows(const Tg* Gin, Tg* Gout, const double* prim, const doub
                          cudaStream_t s, int cell0 = 0, int ncells = -1, double* Ee = nullptr);
 // The row sums of G for the cells [cell0, cell0 + ncells) (every cell for ncells < 0): whenever
 // G is set other than by a sweep (needs ms.R == 1).
+void launch_row_sums_rect(const double* G, double* Rm, const KGrid& g, int i0, int i1, int j0,
+                          int j1, cudaStream_t s);
 void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s, int cell0 = 0,
                      int ncells = -1);
 template <typename Tg>

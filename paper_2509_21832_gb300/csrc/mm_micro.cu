@@ -283,6 +283,30 @@ void launch_row_sums(const double* G, double* Rm, const KGrid& g, cudaStream_t s
 }
 
 
+// Row sums of the cells of a rectangle [i0, i0 + wi) x [j0, j0 + n / wi): persistent one-warp
+// CTAs, as k_row_sums.
+__global__ void __launch_bounds__(32) k_row_sums_rect(const double* __restrict__ G,
+                                                      double* __restrict__ Rm, KGrid g, int i0,
+                                                      int wi, int j0, int n) {
+  extern __shared__ double vt[];
+  for (int l = threadIdx.x; l < g.nv2; l += 32) {
+    const double v2 = fma(l + 0.5, g.dv2, g.v2min);
+    vt[l] = v2;
+    vt[g.nv2 + l] = v2 * v2;
+  }
+  __syncwarp();
+  for (int q = blockIdx.x; q < n; q += gridDim.x)
+    row_sums_body<double>(G, Rm, g, (j0 + q / wi) * g.nx + i0 + q % wi, vt);
+}
+
+void launch_row_sums_rect(const double* G, double* Rm, const KGrid& g, int i0, int i1, int j0,
+                          int j1, cudaStream_t s) {
+  const int wi = i1 - i0, n = wi * (j1 - j0);
+  if (wi > 0 && n > 0)
+    k_row_sums_rect<<<std::min(n, 152 * 32), 32, 2 * (size_t)g.nv2 * sizeof(double), s>>>(
+        G, Rm, g, i0, wi, j0, n);
+}
+
 template void launch_micro_x_list<double>(const double*, double*, const double*, const KGrid&,
                                           const KParams&, double, const MicroShape&, const int*,
                                           const int*, int, cudaStream_t, const double*, double*);

@@ -862,8 +862,13 @@ __device__ __forceinline__ const float* stage_source(const FusedF32& a, int c, i
   return a.Gin + (size_t)(jj * g.nx + c) * nv;
 }
 
+// CTAs per SM the staged kernel is compiled for (its register bound)
+#ifndef MM_F32_MINB
+#define MM_F32_MINB 4
+#endif
+
 template <int NV1, int NV2>
-__global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF32 a) {
+__global__ void __launch_bounds__(32 * kFusedWarps, MM_F32_MINB) k_micro_staged_f32(FusedF32 a) {
   using S = FlatShape<NV1, NV2>;
   using T = StagedShape<NV1, NV2>;
   constexpr int W = T::W;
