@@ -419,6 +419,73 @@ def batch_variant(args, count=None, nmin=64, nmax=256, steps=None):
             "speedup_vs_separate_contexts": tsep / (tb / steps)}
 
 
+def run_blocks(pr, world, rank, steps, warmup, make_stepper, device, group=None):
+    """One problem split into px x py spatial blocks, one per rank (Section 5.5's decomposition):
+    each rank steps its block (owned cells and a halo of two cells on every side that borders
+    another block), refreshing the halos from their owners before every step with point-to-point
+    messages over torch.distributed (NCCL between GPUs, gloo on CPU; no collective).
+    make_stepper(pr, block, Q, G) returns step(regions) that advances the block's tensors one step
+    in place, told which regions of g the exchange rewrote.  Returns (block, Q, G, seconds of
+    the timed steps on this rank)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2509_21832_gb300 import halo
+    px, py = halo.block_shape(world)
+    blocks = halo.decompose(pr.grid, pr.params, px, py, w=2)
+    copies = halo.plan(blocks)
+    b = blocks[rank]
+    Qb, Gb = halo.scatter(blocks, pr.Q, pr.G)[rank]
+    Qt = torch.from_numpy(np.ascontiguousarray(Qb)).to(device)
+    Gt = torch.from_numpy(np.ascontiguousarray(Gb)).to(device)
+    step = make_stepper(pr, b, Qt, Gt)
+    regions = halo.halo_regions(b)
+    cuda = Qt.is_cuda
+
+    def one():
+        halo.exchange(blocks, copies, rank, Qt, Gt, group=group)
+        step(regions)
+
+    for _ in range(warmup):
+        one()
+    if cuda:
+        torch.cuda.synchronize()
+    dist.barrier(group=group)
+    t0 = time.perf_counter()
+    if cuda:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+    for _ in range(steps):
+        one()
+    if cuda:
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+    else:
+        sec = time.perf_counter() - t0
+    dist.barrier(group=group)
+    return b, Qt, Gt, sec
+
+
+def gpu_block_stepper(pr, b, Qt, Gt):
+    """The library on the block's own CUDA tensors (a borrowed context on torch's current
+    stream, which also carries the halo copies)."""
+    import torch
+    from paper_2509_21832_gb300 import api
+    S = torch.empty(api.mm_scratch_bytes(b.grid, b.params), dtype=torch.uint8, device=Qt.device)
+    s = api.Solver(b.grid, b.params, stream=torch.cuda.current_stream().cuda_stream,
+                   borrow=(Qt, Gt, S))
+    s.scratch = S
+    s.set_state(Qt.clone(), Gt.clone())
+
+    def step(regions):
+        for r in regions:
+            s.g_region_changed(*r)
+        s.step(pr.dt, pr.eps, 1)
+
+    step.solver = s
+    return step
+
+
 def summarize_variant(v):
     """The headline line's short form of a variant (its full line is printed before it)."""
     keep = ("value", "ms_per_step", "speedup_vs_fp64", "hbm_frac", "l1_density_rel_err_vs_fp64",
@@ -455,6 +522,9 @@ def main():
     ap.add_argument("--closure-only", action="store_true")
     ap.add_argument("--closure-n", type=int, default=512)
     ap.add_argument("--closure-steps", type=int, default=100)
+    ap.add_argument("--decompose", action="store_true",
+                    help="split the one problem into spatial blocks, one per rank (halo exchange "
+                         "between ranks every step) instead of running one replica per rank")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -491,6 +561,24 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
+
+    if args.decompose:
+        b, _, _, sec = run_blocks(pr, world, rank, args.steps, args.warmup, gpu_block_stepper,
+                                  torch.device("cuda", local))
+        ms = max_over_ranks(1e3 * sec, pg, "cuda")
+        if rank == 0:
+            from paper_2509_21832_gb300 import halo
+            px, py = halo.block_shape(world)
+            cfg = dict(config_of(pr, args), parallelism="spatial blocks %dx%d, halo 2" % (px, py))
+            print(json.dumps({
+                "metric": METRIC, "value": pr.grid.nphase * args.steps / (ms * 1e-3),
+                "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg}),
+                flush=True)
+        if pg:
+            pg.destroy_process_group()
+        return
 
     stream = torch.cuda.Stream()
     solver = api.Solver(pr.grid, pr.params, stream=stream.cuda_stream)

@@ -61,7 +61,8 @@ EXPORTS = ["mm_create", "mm_create_borrowed", "mm_scratch_bytes", "mm_device_byt
            "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_forward",
            "mm_mlp_grad", "mm_mlp_train_step", "mm_mlp_last_error", "mm_mlp_destroy",
            "mm_set_closure", "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
-           "mm_closure_stats", "mm_set_closure_fallback", "mm_closure_steps", "mm_mms_enable", "mm_mms_set_exact", "mm_mms_error",
+           "mm_closure_stats", "mm_set_closure_fallback", "mm_closure_steps",
+           "mm_g_region_changed", "mm_mms_enable", "mm_mms_set_exact", "mm_mms_error",
            "mm1d_create", "mm1d_set_state", "mm1d_step", "mm1d_get_state", "mm1d_mms_enable",
            "mm1d_mms_set_exact", "mm1d_last_error", "mm1d_destroy"]
 
@@ -158,6 +159,7 @@ def load(build_if_needed: bool = True):
     L.mm_closure_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]
     L.mm_set_closure_fallback.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.mm_g_region_changed.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.mm_closure_steps.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]
     G1, P1 = ctypes.POINTER(mm1d_grid), ctypes.POINTER(mm1d_params)
@@ -184,7 +186,8 @@ def load(build_if_needed: bool = True):
                  "mm_get_timing", "mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params",
                  "mm_mlp_forward", "mm_mlp_grad", "mm_mlp_train_step", "mm_set_closure",
                  "mm_closure_features", "mm_closure_collect", "mm_closure_flags",
-                 "mm_closure_stats", "mm_set_closure_fallback", "mm_closure_steps"]:
+                 "mm_closure_stats", "mm_set_closure_fallback", "mm_closure_steps",
+                 "mm_g_region_changed"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -498,6 +501,11 @@ class Solver:
         _check(self.ctx, self.L.mm_closure_stats(self.ctx, ctypes.byref(a), ctypes.byref(b)),
                "mm_closure_stats")
         return a.value, b.value
+
+    def g_region_changed(self, i0, i1, j0, j1):
+        """g was changed by the caller in cells [i0, i1) x [j0, j1) (borrowed buffers)."""
+        _check(self.ctx, self.L.mm_g_region_changed(self.ctx, int(i0), int(i1), int(j0),
+                                                    int(j1)), "mm_g_region_changed")
 
     def set_closure_fallback(self, min_fraction, period):
         _check(self.ctx, self.L.mm_set_closure_fallback(self.ctx, float(min_fraction),

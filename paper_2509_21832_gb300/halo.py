@@ -277,3 +277,23 @@ def exchange(blocks, copies, rank, Q, G, group=None):
         di = torch.as_tensor(dst, device=Q.device)
         Qf[:, di] = qb
         Gf[di] = gb
+
+
+def halo_regions(b):
+    """The halo cells of block b as rectangles (i0, i1, j0, j1) of its extended grid."""
+    out = []
+    if b.hl:
+        out.append((0, b.hl, 0, b.ny))
+    if b.hr:
+        out.append((b.nx - b.hr, b.nx, 0, b.ny))
+    if b.hb:
+        out.append((0, b.nx, 0, b.hb))
+    if b.ht:
+        out.append((0, b.nx, b.ny - b.ht, b.ny))
+    return out
+
+
+def block_shape(world):
+    """px x py blocks for `world` ranks: the factorisation closest to square, px >= py."""
+    py = max(p for p in range(1, int(world ** 0.5) + 1) if world % p == 0)
+    return world // py, py

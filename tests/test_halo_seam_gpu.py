@@ -65,3 +65,58 @@ def test_blocks_on_one_gpu_reproduce_the_undivided_step(name, nv, bc, px, py, pr
             sv.close()
     assert np.array_equal(Qs.numpy(), Qu), name
     assert np.array_equal(Gs.numpy(), Gu), name
+
+
+@pytest.mark.parametrize("name,nv,bc,px,py,prec", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_blocks_with_region_refresh_reproduce_the_undivided_step(name, nv, bc, px, py, prec):
+    """The same with the halo refresh that `bench.py --decompose` uses: after the exchange only
+    the halo rectangles' g is re-registered (mm_g_region_changed re-forms their row sums); the
+    state is set once."""
+    grid = I.Grid(nx=24, ny=16, x0=0.0, x1=1.5, y0=0.0, y1=1.0, nv1=nv, nv2=nv)
+    params = I.Params(bc=bc, precision=prec)
+    Q = I.smooth_state(grid, seed=41, umax=0.25, aniso=0.06)
+    G = I.seeded_g(grid, seed=42, amp=0.02)
+    dt = 0.4 / (8.0 * grid.nx + 8.0 * grid.ny)
+    eps, steps = 1e-2, 4
+    with api.Solver(grid, params) as s:
+        s.set_state(Q, G)
+        s.step(dt, eps, steps)
+        Qu, _ = s.get_moments()
+        Gu = s.get_g()
+    blocks = halo.decompose(grid, params, px, py, w=2)
+    copies = halo.plan(blocks)
+    states = [(Qb.cuda(), Gb.cuda()) for Qb, Gb in
+              halo.scatter(blocks, torch.from_numpy(Q), torch.from_numpy(G))]
+    solvers = []
+    for b, (Qb, Gb) in zip(blocks, states):
+        S = torch.empty(api.mm_scratch_bytes(b.grid, b.params), dtype=torch.uint8, device="cuda")
+        sv = api.Solver(b.grid, b.params, stream=torch.cuda.current_stream().cuda_stream,
+                        borrow=(Qb, Gb, S))
+        sv.scratch = S
+        sv.set_state(Qb.clone(), Gb.clone())
+        solvers.append(sv)
+    try:
+        for n in range(steps):
+            if n:
+                halo.exchange_local(blocks, copies, states)
+                for b, sv in zip(blocks, solvers):
+                    for r in halo.halo_regions(b):
+                        sv.g_region_changed(*r)
+            for sv in solvers:
+                sv.step(dt, eps, 1)
+        for sv in solvers:
+            sv.sync()
+        Qs, Gs = torch.zeros(Q.shape, dtype=torch.float64), torch.zeros(G.shape, dtype=torch.float64)
+        halo.gather(blocks, [(Qb.cpu(), Gb.cpu()) for Qb, Gb in states], Qs, Gs)
+    finally:
+        for sv in solvers:
+            sv.close()
+    assert np.array_equal(Qs.numpy(), Qu), name
+    assert np.array_equal(Gs.numpy(), Gu), name
+    with pytest.raises(api.MMError):
+        solvers_bad = api.Solver(grid, params)
+        try:
+            solvers_bad.set_state(Q, G)
+            solvers_bad.g_region_changed(0, grid.nx + 1, 0, 1)
+        finally:
+            solvers_bad.close()
