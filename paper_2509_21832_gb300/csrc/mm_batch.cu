@@ -136,7 +136,7 @@ __device__ bool wait_deps(const MegaArgs& a, const unsigned* cur, const unsigned
 
 // The whole of nsteps batch steps: persistent CTAs of blockDim.x threads take queue items.
 #ifndef MM_BATCH_MINB
-#define MM_BATCH_MINB 16
+#define MM_BATCH_MINB 24
 #endif
 __global__ void __launch_bounds__(32, MM_BATCH_MINB) k_batch_steps(MegaArgs a) {
   extern __shared__ double sm[];
