@@ -85,7 +85,8 @@ struct FusedF32 {
   float dtidx, dtidy;
   int R;         // rows per pass: 32 / nv1
   int seg_rows;  // rows per segment
-  int nseg;
+  int nseg;      // segments covered by this launch, from segment seg0 on
+  int seg0;
   int* err;      // device error word (ERR_WAIT_TIMEOUT from a bounded wait)
 };
 
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_fused_f32(FusedF3
   const int gw = blockIdx.x * kFusedWarps + w;
   if (gw >= g.nx * a.nseg) return;  // whole warp leaves; no CTA-wide barrier is used below
   const int i = gw % g.nx;
-  const int seg = gw / g.nx;
+  const int seg = a.seg0 + gw / g.nx;
   const int j0 = seg * a.seg_rows;
   const int j1 = min(g.ny, j0 + a.seg_rows);
   if (j0 >= j1) return;
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, MM_F32_FLAT_MINB) k_micro_fl
   const int gw = blockIdx.x * kFusedWarps + w;
   if (gw >= g.nx * a.nseg) return;  // whole warp leaves; no CTA-wide barrier is used below
   const int i = gw % g.nx;
-  const int seg = gw / g.nx;
+  const int seg = a.seg0 + gw / g.nx;
   const int j0 = seg * a.seg_rows;
   const int j1 = min(g.ny, j0 + a.seg_rows);
   if (j0 >= j1) return;
@@ -885,7 +886,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, MM_F32_MINB) k_micro_staged_
   float* yt = xt + 4 * NV2;
   const uint32_t bar = smem_addr(smf + T::STAGE + W * (T::RING + T::TABLES));
   const int ncx = (g.nx + W - 1) / W;
-  const int cx = blockIdx.x % ncx, seg = blockIdx.x / ncx;
+  const int cx = blockIdx.x % ncx, seg = a.seg0 + blockIdx.x / ncx;
   const int i0 = cx * W, i = i0 + w;
   const bool col = i < g.nx;  // warps past the last column only take part in the barriers
   const int j0 = seg * a.seg_rows;
@@ -1060,7 +1061,8 @@ int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
 
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
-                            const MicroShape& ms, int nseg, int* err, cudaStream_t s) {
+                            const MicroShape& ms, int nseg, int* err, cudaStream_t s, int seg0,
+                            int seg1) {
   (void)ms;
   const FusedPick f = pick_fused(g);
   FusedF32 a;
@@ -1076,10 +1078,13 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
   a.dtidx = (float)(dt * g.idx);
   a.dtidy = (float)(dt * g.idy);
   a.R = 32 / g.nv1;
-  a.nseg = nseg;
+  if (seg1 < 0 || seg1 > nseg) seg1 = nseg;
+  if (seg0 >= seg1) return;
   a.seg_rows = (g.ny + nseg - 1) / nseg;
+  a.seg0 = seg0;
+  a.nseg = seg1 - seg0;
   // one warp per column and segment; the staged kernels give a CTA kFusedWarps adjacent columns
-  const int warps = ((g.nx + kFusedWarps - 1) / kFusedWarps) * kFusedWarps * nseg;
+  const int warps = ((g.nx + kFusedWarps - 1) / kFusedWarps) * kFusedWarps * a.nseg;
   if (f.smem > 48 * 1024)
     cudaFuncSetAttribute(f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
   f.kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, f.smem, s>>>(a);
