@@ -260,11 +260,11 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
   bool x1_side = false;
-#ifdef MM_F32_FORK_AFTER_PRIMS
   enqueue_prims(c, dt, eps, s);
-#endif
   if constexpr (sizeof(Tg) == sizeof(float)) {
-    // macro x1 (collision half step and x half fluxes of Q^n) beside the phase-space kernel
+    // macro x1 (collision half step and x half fluxes of Q^n) beside the phase-space kernel:
+    // forked after the per-cell fields, so that it runs with the FP32 kernel rather than against
+    // the FP64-bound fields kernel
     cudaError_t e = cudaSuccess;
     if (!c->mstream) e = cudaStreamCreateWithFlags(&c->mstream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !c->ev_fork)
@@ -281,9 +281,6 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
     }
     if (!x1_side) cudaGetLastError();  // side stream unavailable: macro x1 runs in order below
   }
-#ifndef MM_F32_FORK_AFTER_PRIMS
-  enqueue_prims(c, dt, eps, s);
-#endif
   const double* srcg = nullptr;
   const double* srcq = nullptr;
   if constexpr (sizeof(Tg) == sizeof(double)) {
