@@ -115,6 +115,35 @@ def loss_and_grad(params, norm, X, T):
     return L, g
 
 
+def loss_and_grad_bf16(params, norm, X, T, rnd=None):
+    """Loss and gradient as the training kernels form them: the same chain rule as
+    loss_and_grad, with every operand of a tensor-core product rounded to BF16 where the kernels
+    round it -- the standardised inputs x', the activations a1, a2 and the back-propagated
+    pre-activation gradients d3, d2, d1 (each first as the FP32 value the kernels hold) -- and
+    the bias gradients summed from the rounded d (the kernels append a column of ones to a layer's
+    input).  rnd replaces the rounding (identity: the plain chain rule)."""
+    r = bf16_round if rnd is None else rnd
+    norm = np.asarray(norm, dtype=np.float64)
+    W1, b1, W2, b2, W3, b3 = unpack(params)
+    mx, isx = norm[:N_IN], norm[N_IN:2 * N_IN]
+    a0 = r((np.asarray(X, dtype=np.float64) - mx) * isx)
+    z1 = a0 @ W1.T + b1
+    a1 = r(gelu(z1))
+    z2 = a1 @ W2.T + b2
+    a2 = r(gelu(z2))
+    ys = a2 @ W3.T + b3
+    n = len(ys)
+    ts = (np.asarray(T, dtype=np.float64) - norm[2 * N_IN:2 * N_IN + N_OUT]) / norm[2 * N_IN + N_OUT:]
+    e = ys - ts
+    L = float(np.sum(e * e) / n)
+    d3 = r(2.0 * e / n)
+    d2 = r((d3 @ W3) * gelu_grad(z2))
+    d1 = r((d2 @ W2) * gelu_grad(z1))
+    g = np.concatenate([(d1.T @ a0).ravel(), d1.sum(axis=0), (d2.T @ a1).ravel(), d2.sum(axis=0),
+                        (d3.T @ a2).ravel(), d3.sum(axis=0)])
+    return L, g
+
+
 def adam_step(w, m1, m2, grad, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba 2015, Algorithm 1) of FP64 arrays; returns (w, m1, m2)."""
     m1 = b1 * m1 + (1.0 - b1) * grad

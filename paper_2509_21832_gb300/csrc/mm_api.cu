@@ -310,7 +310,7 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
     if (c->n_wall > 0)
       timed(c, T_MICRO_YW, [&] {
         launch_micro_y_wall<float>(Ge, Gs, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt,
-                                   eps, c->ms, c->err, s);
+                                   eps, wall_shape_f32(g.nv1, g.nv2), c->err, s);
       });
     std::swap(c->G, c->Gs);
   } else {
@@ -438,6 +438,13 @@ mm_status enqueue_f32_pipeline(mm_ctx* c, double dt, double eps, int nsteps) {
     return n;
   };
   float* Ge = static_cast<float*>(c->Gexp);
+  const MicroShape wshape = wall_shape_f32(g.nv1, g.nv2);
+  // CTAs of the phase-space kernel per SM in the pipeline: fewer than the kernel could hold
+  // leaves registers for the per-cell FP64 kernels that run beside it
+#ifndef MM_F32_PIPE_CTAS
+#define MM_F32_PIPE_CTAS 3
+#endif
+  const size_t smem_floor = MM_F32_PIPE_CTAS >= 4 ? 0 : 233472 / MM_F32_PIPE_CTAS - 2048;
   // fork the three streams from the context stream
   cudaEventRecord(c->ev_join[0], s);
   for (cudaStream_t t : {sm[0], sm[1], sf}) cudaStreamWaitEvent(t, c->ev_join[0], 0);
@@ -458,7 +465,7 @@ mm_status enqueue_f32_pipeline(mm_ctx* c, double dt, double eps, int nsteps) {
       if (b + 1 < K) cudaStreamWaitEvent(st, c->ev_band_p[b], 0);
       timed_on(c, T_MICRO_FUSED, st, [&] {
         launch_micro_fused_f32(Gin, Gout, Ge, c->Hf, c->primf, g, p, dt, c->ms, c->nseg, c->err,
-                               st, b, b + 1);
+                               st, b, b + 1, smem_floor);
       });
       cudaEventRecord(c->ev_band_m[b], st);
     }
@@ -496,7 +503,7 @@ mm_status enqueue_f32_pipeline(mm_ctx* c, double dt, double eps, int nsteps) {
       if (w1 > w0)
         timed_on(c, T_MICRO_YW, sf, [&] {
           launch_micro_y_wall<float>(Ge, Gout, c->H, c->prim, c->wall_cells + w0, w1 - w0, g, p,
-                                     dt, eps, c->ms, c->err, sf);
+                                     dt, eps, wshape, c->err, sf);
         });
       timed_on(c, T_MACRO_X2, sf, [&] {
         launch_macro_x2(c->H, c->mb, g, p, dt, c->err, sf, r0(b) * nx, r1(b) * nx);

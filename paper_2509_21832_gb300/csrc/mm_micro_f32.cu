@@ -15,6 +15,7 @@
 //  - k_micro_flat_f32 (32^2, symmetric in v2): flat lane mapping, one warp per column, g through
 //    the read-only path;
 //  - k_micro_fused_f32 (any mesh with nv1 <= 32): lane = v1 index, one warp per column.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -1062,7 +1063,7 @@ int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
                             const MicroShape& ms, int nseg, int* err, cudaStream_t s, int seg0,
-                            int seg1) {
+                            int seg1, size_t smem_floor) {
   (void)ms;
   const FusedPick f = pick_fused(g);
   FusedF32 a;
@@ -1085,9 +1086,11 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
   a.nseg = seg1 - seg0;
   // one warp per column and segment; the staged kernels give a CTA kFusedWarps adjacent columns
   const int warps = ((g.nx + kFusedWarps - 1) / kFusedWarps) * kFusedWarps * a.nseg;
-  if (f.smem > 48 * 1024)
-    cudaFuncSetAttribute(f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
-  f.kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, f.smem, s>>>(a);
+  // a floor above the kernel's own need caps the CTAs per SM (room for concurrent kernels)
+  const size_t smem = std::max(f.smem, std::min(smem_floor, kMaxSmemPerCta));
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  f.kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, smem, s>>>(a);
 }
 
 }  // namespace mmk

@@ -93,6 +93,25 @@ def test_gradient_closed_form_with_zero_output_layer():
                        (2.0 / len(X)) * (b3 - ts).T @ a2, atol=1e-13, rtol=0)
 
 
+def test_bf16_operand_gradient_reduces_to_the_chain_rule_and_stays_close():
+    """The training kernels' gradient with BF16 operands: with the rounding replaced by the
+    identity it is the plain chain-rule gradient (itself pinned by central differences above);
+    with BF16 rounding of the activations and back-propagated gradients it stays within a few
+    BF16 units (2^-8 relative) of it in every layer, and differs from it (the roundings act)."""
+    X, T, norm = _data(1)
+    p = M.bf16_round(M.init_params(3))
+    L0, g0 = M.loss_and_grad(p, norm, X, T)
+    Li, gi = M.loss_and_grad_bf16(p, norm, X, T, rnd=lambda a: a)
+    assert abs(Li - L0) <= 1e-14 * max(1.0, L0)
+    assert np.max(np.abs(gi - g0)) <= 1e-14 * np.max(np.abs(g0))
+    Lb, gb = M.loss_and_grad_bf16(p, norm, X, T)
+    assert abs(Lb - L0) <= 2.0 ** -6 * L0
+    for a, b in ((M.OFF_W1, M.OFF_B1), (M.OFF_W2, M.OFF_B2), (M.OFF_W3, M.OFF_B3)):
+        scale = np.max(np.abs(g0[a:b]))
+        err = np.max(np.abs(gb[a:b] - g0[a:b]))
+        assert 0.0 < err <= 2.0 ** -5 * scale, (a, err / scale)
+
+
 def test_first_adam_step_moves_by_lr_times_sign():
     g = np.array([3.0, -1e-3, 0.5, -7.0])
     w, m1, m2 = M.adam_step(np.zeros(4), np.zeros(4), np.zeros(4), g, 1, 1e-2)
