@@ -272,7 +272,11 @@ mm_status mm_mlp_get_params(mm_mlp* m, float* params_host, float* params_bf16_as
 /* Inference: Y[n][4] (de-standardised) from X[n][39]; asynchronous. */
 mm_status mm_mlp_forward(mm_mlp* m, const float* X_dev, float* Y_dev, int n);
 /* Gradient of the mean squared error of the standardised outputs with respect to the
- * parameters (BF16 weights, FP32 accumulation), and the loss; synchronous if outputs given. */
+ * parameters, and the loss; synchronous if outputs given.  Forward and backward run on the tensor
+ * cores (mma m16n8k16) with BF16 operands -- the BF16 weights, the standardised inputs, the
+ * activations and the back-propagated pre-activation gradients, each rounded to BF16 where it
+ * enters a product -- and FP32 accumulation; the weight gradients are summed over chunks of 128
+ * samples in a fixed order (deterministic).  Work buffer: about 680 bytes per sample. */
 mm_status mm_mlp_grad(mm_mlp* m, const float* X_dev, const float* T_dev, int n, float* grad_host,
                       float* loss_host);
 /* One Adam step (beta 0.9, 0.999) on a mini-batch; FP32 master weights, BF16 copies refreshed. */

@@ -5,13 +5,13 @@
 // transport part of Ghat (Eq. 5-97) for a Gaussian: H111 = -3 eps p Tx / tau, H112 = -eps p Ty /
 // tau, H122 = -eps p Tx / tau, H222 = -3 eps p Ty / tau (p = rho T).
 //
-// Kernels: features (one thread per cell), inference (one thread per sample, weights in shared
-// memory), training forward/backward per sample (activations and pre-activation gradients kept
-// in global memory), weight gradients as reductions over the batch (one thread per weight, fixed
-// order: deterministic), and Adam on FP32 master weights that refreshes the BF16 copies.
+// Kernels: inference (tensor cores, split-TF32 activations), training forward/backward and
+// weight gradients on the tensor cores with BF16 operands and FP32 accumulation (fixed-order
+// reductions: deterministic), and Adam on FP32 master weights that refreshes the BF16 copies.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -59,99 +59,304 @@ __global__ void __launch_bounds__(kInferThreads, 4) k_mlp_infer(const __nv_bfloa
   }
 }
 
-// Per-sample forward and backward of the loss L = (1/n) sum_s sum_o (y_so - t_so)^2, targets
-// standardised like the outputs.  The layer inputs A0 (standardised x), A1, A2, the
-// pre-activations Z1, Z2 and the pre-activation gradients D1, D2, D3 go to global memory (the
-// per-sample activations do not fit in registers) for the weight-gradient reductions.
-struct Work {
-  float *A0, *A1, *A2, *Z1, *Z2, *D1, *D2, *D3;
+// ---- training on the tensor cores -------------------------------------------------------------
+// Forward and backward of the loss L = (1/n) sum_s sum_o (y_so - t'_so)^2 (targets standardised
+// like the outputs) as tile contractions: mma.sync m16n8k16 with BF16 operands and FP32
+// accumulation.  A warp takes 16 samples: the layer products [16 x K] x [K x N] run with the
+// activations (and, backwards, the pre-activation gradients) as the A operand, rounded to BF16,
+// and the BF16 weights as the B operand from shared memory; a layer's FP32 accumulators, after
+// GELU and rounding, are the next layer's A fragments register for register.  The operands of
+// the weight gradients (the layer inputs with a column of ones appended for the bias, and the
+// pre-activation gradients, both BF16) go to global memory feature-major; a second kernel forms
+// dL/dW = D^T [A | 1] per chunk of 128 samples on the tensor cores, and a third sums the chunks
+// in a fixed order (deterministic).
+constexpr int kTrainThreads = 128;  // 4 warps, 16 samples each per pass
+constexpr int kChunk = 128;         // samples per weight-gradient partial
+// rows of the feature-major operand arrays: layer input + ones row, padded to whole n-tiles
+constexpr int kR0 = 48, kR1 = 72, kRD3 = 16;  // A0t rows (39 + 1 + pad), A1t/A2t rows, D3t rows
+// shared layouts of the weights (BF16, row strides that spread a fragment's 8 rows over banks)
+constexpr int kSW1 = 56, kSW2 = 72, kSW3 = 72, kSW3T = 24;
+
+struct TrainWork {
+  __nv_bfloat16 *A0t, *A1t, *A2t, *D1t, *D2t, *D3t;  // feature-major [rows][np]
+  float* part;                                      // weight-gradient partials [nchunk][kNP]
+  float* tile_loss;                                 // [np / 16]
+  int np;
 };
 
-__global__ void k_mlp_fwd_bwd(const __nv_bfloat16* __restrict__ w, const float* __restrict__ norm,
-                              const float* __restrict__ X, const float* __restrict__ T, int n,
-                              Work wk, float* __restrict__ loss) {
-  __shared__ float sw[kNP];
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half), .y = hi
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__global__ void __launch_bounds__(kTrainThreads) k_mlp_train(
+    const __nv_bfloat16* __restrict__ w, const float* __restrict__ norm,
+    const float* __restrict__ X, const float* __restrict__ T, int n, TrainWork wk) {
+  __shared__ __align__(16) __nv_bfloat16 sW1[kH * kSW1];
+  __shared__ __align__(16) __nv_bfloat16 sW2[kH * kSW2];
+  __shared__ __align__(16) __nv_bfloat16 sW2t[kH * kSW2];
+  __shared__ __align__(16) __nv_bfloat16 sW3[8 * kSW3];
+  __shared__ __align__(16) __nv_bfloat16 sW3t[kH * kSW3T];
+  __shared__ float sb[2 * kH + kOut];
   __shared__ float sn[2 * kIn + 2 * kOut];
-  stage(w, norm, sw, sn);
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    float* A0 = wk.A0 + (size_t)s * kIn;
-    float* A1 = wk.A1 + (size_t)s * kH;
-    float* A2 = wk.A2 + (size_t)s * kH;
-    float* Z1 = wk.Z1 + (size_t)s * kH;
-    float* Z2 = wk.Z2 + (size_t)s * kH;
-    float* D1 = wk.D1 + (size_t)s * kH;
-    float* D2 = wk.D2 + (size_t)s * kH;
-    float* D3 = wk.D3 + (size_t)s * kOut;
-    float xn[kIn];
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  for (int q = threadIdx.x; q < kH * kSW1; q += blockDim.x) {
+    const int o = q / kSW1, i = q % kSW1;
+    sW1[q] = i < kIn ? w[kW1 + o * kIn + i] : zero;
+  }
+  for (int q = threadIdx.x; q < kH * kSW2; q += blockDim.x) {
+    const int o = q / kSW2, i = q % kSW2;
+    sW2[q] = i < kH ? w[kW2 + o * kH + i] : zero;   // [o][j]
+    sW2t[q] = i < kH ? w[kW2 + i * kH + o] : zero;  // [j][o]
+  }
+  for (int q = threadIdx.x; q < 8 * kSW3; q += blockDim.x) {
+    const int o = q / kSW3, j = q % kSW3;
+    sW3[q] = (o < kOut && j < kH) ? w[kW3 + o * kH + j] : zero;
+  }
+  for (int q = threadIdx.x; q < kH * kSW3T; q += blockDim.x) {
+    const int j = q / kSW3T, o = q % kSW3T;
+    sW3t[q] = o < kOut ? w[kW3 + o * kH + j] : zero;
+  }
+  for (int q = threadIdx.x; q < kH; q += blockDim.x) {
+    sb[q] = __bfloat162float(w[kB1 + q]);
+    sb[kH + q] = __bfloat162float(w[kB2 + q]);
+  }
+  if (threadIdx.x < kOut) sb[2 * kH + threadIdx.x] = __bfloat162float(w[kB3 + threadIdx.x]);
+  for (int q = threadIdx.x; q < 2 * kIn + 2 * kOut; q += blockDim.x) sn[q] = norm[q];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  const int np = wk.np;
+  const int ntiles = np / 16;
+  const float inv_n = 1.f / n;
+  for (int tile = blockIdx.x * (kTrainThreads / 32) + (threadIdx.x >> 5); tile < ntiles;
+       tile += gridDim.x * (kTrainThreads / 32)) {
+    const int s0 = tile * 16;
+    const int sa = s0 + gq, sb8 = s0 + gq + 8;  // the two samples (rows) this lane holds
+    const bool va = sa < n, vb = sb8 < n;
+    auto put = [&](__nv_bfloat16* At, int row, int s, float v) {
+      At[(size_t)row * np + s] = __float2bfloat16_rn(v);
+    };
+    // ---- layer 1: x' (standardised, BF16) x W1^T + b1 ----
+    uint32_t A0[3][4];
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) {
-      xn[i] = (X[(size_t)s * kIn + i] - sn[i]) * sn[kIn + i];
-      A0[i] = xn[i];
+    for (int kt = 0; kt < 3; ++kt) {
+      float v[8];
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int col = 16 * kt + 2 * tq + (h & 1) + ((h & 4) ? 8 : 0);
+        const int s = (h & 2) ? sb8 : sa;
+        const bool ok = ((h & 2) ? vb : va) && col < kIn;
+        v[h] = ok ? (X[(size_t)s * kIn + col] - sn[col]) * sn[kIn + col] : 0.f;
+        // the weight-gradient operand: x' rows, and the ones row for the bias
+        const float out = col < kIn ? v[h] : (col == kIn && ((h & 2) ? vb : va) ? 1.f : 0.f);
+        put(wk.A0t, col, s, out);
+      }
+      A0[kt][0] = pack2(v[0], v[1]);
+      A0[kt][1] = pack2(v[2], v[3]);
+      A0[kt][2] = pack2(v[4], v[5]);
+      A0[kt][3] = pack2(v[6], v[7]);
     }
-    for (int o = 0; o < kH; ++o) {
-      float acc = sw[kB1 + o];
+    float acc[8][4];
+    float gg1[8][4];
+    uint32_t A1[4][4];
 #pragma unroll
-      for (int i = 0; i < kIn; ++i) acc = fmaf(sw[kW1 + o * kIn + i], xn[i], acc);
-      Z1[o] = acc;
-      A1[o] = gelu(acc);
+    for (int nt = 0; nt < 8; ++nt) {
+      acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+      for (int kt = 0; kt < 3; ++kt) {
+        const __nv_bfloat16* bp = sW1 + (nt * 8 + gq) * kSW1 + 16 * kt + 2 * tq;
+        mma16816(acc[nt], A0[kt], ld32(bp), ld32(bp + 8));
+      }
     }
-    float y[kOut];
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) y[o] = sw[kB3 + o];
-    for (int o2 = 0; o2 < kH; ++o2) {
-      float acc = sw[kB2 + o2];
-      for (int i = 0; i < kH; ++i) acc = fmaf(sw[kW2 + o2 * kH + i], A1[i], acc);
-      Z2[o2] = acc;
-      const float a2 = gelu(acc);
-      A2[o2] = a2;
+    for (int nt = 0; nt < 8; ++nt) {
+      float a[4];
 #pragma unroll
-      for (int o = 0; o < kOut; ++o) y[o] = fmaf(sw[kW3 + o * kH + o2], a2, y[o]);
+      for (int r = 0; r < 4; ++r) {
+        const int col = nt * 8 + 2 * tq + (r & 1);
+        const float z = acc[nt][r] + sb[col];
+        a[r] = gelu(z);
+        gg1[nt][r] = gelu_grad(z);
+        const bool ok = (r & 2) ? vb : va;
+        if (!ok) a[r] = 0.f;
+        put(wk.A1t, col, (r & 2) ? sb8 : sa, a[r]);
+      }
+      const int kt = nt >> 1, hi = nt & 1;
+      A1[kt][hi ? 2 : 0] = pack2(a[0], a[1]);
+      A1[kt][hi ? 3 : 1] = pack2(a[2], a[3]);
     }
-    float d3[kOut], l = 0.f;
-#pragma unroll
-    for (int o = 0; o < kOut; ++o) {
-      const float t = (T[(size_t)s * kOut + o] - sn[2 * kIn + o]) / sn[2 * kIn + kOut + o];
-      const float e = y[o] - t;
-      l += e * e;
-      d3[o] = 2.f * e / n;
-      D3[o] = d3[o];
+    if (tq == 0) {
+      put(wk.A1t, kH, sa, va ? 1.f : 0.f);
+      put(wk.A1t, kH, sb8, vb ? 1.f : 0.f);
     }
-    atomicAdd(loss, l / n);
-    for (int i = 0; i < kH; ++i) {
-      float acc = 0.f;
+    // ---- layer 2 ----
+    float gg2[8][4];
+    uint32_t A2[4][4];
 #pragma unroll
-      for (int o = 0; o < kOut; ++o) acc = fmaf(sw[kW3 + o * kH + i], d3[o], acc);
-      D2[i] = acc * gelu_grad(Z2[i]);
+    for (int nt = 0; nt < 8; ++nt) {
+      acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt) {
+        const __nv_bfloat16* bp = sW2 + (nt * 8 + gq) * kSW2 + 16 * kt + 2 * tq;
+        mma16816(acc[nt], A1[kt], ld32(bp), ld32(bp + 8));
+      }
     }
-    for (int i = 0; i < kH; ++i) {
-      float acc = 0.f;
-      for (int o = 0; o < kH; ++o) acc = fmaf(sw[kW2 + o * kH + i], D2[o], acc);
-      D1[i] = acc * gelu_grad(Z1[i]);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float a[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int col = nt * 8 + 2 * tq + (r & 1);
+        const float z = acc[nt][r] + sb[kH + col];
+        a[r] = gelu(z);
+        gg2[nt][r] = gelu_grad(z);
+        const bool ok = (r & 2) ? vb : va;
+        if (!ok) a[r] = 0.f;
+        put(wk.A2t, col, (r & 2) ? sb8 : sa, a[r]);
+      }
+      const int kt = nt >> 1, hi = nt & 1;
+      A2[kt][hi ? 2 : 0] = pack2(a[0], a[1]);
+      A2[kt][hi ? 3 : 1] = pack2(a[2], a[3]);
+    }
+    if (tq == 0) {
+      put(wk.A2t, kH, sa, va ? 1.f : 0.f);
+      put(wk.A2t, kH, sb8, vb ? 1.f : 0.f);
+    }
+    // ---- output layer and the loss gradient d3 = 2 (y' - t') / n ----
+    float y[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+      const __nv_bfloat16* bp = sW3 + gq * kSW3 + 16 * kt + 2 * tq;
+      mma16816(y, A2[kt], ld32(bp), ld32(bp + 8));
+    }
+    float d3[4], lsum = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int o = 2 * tq + (r & 1);
+      const int s = (r & 2) ? sb8 : sa;
+      const bool ok = o < kOut && ((r & 2) ? vb : va);
+      float e = 0.f;
+      if (ok) {
+        const float tt = (T[(size_t)s * kOut + o] - sn[2 * kIn + o]) / sn[2 * kIn + kOut + o];
+        e = y[r] + sb[2 * kH + o] - tt;
+      }
+      lsum += e * e;
+      d3[r] = 2.f * e * inv_n;
+      if (o < kRD3) put(wk.D3t, o, s, d3[r]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+    if (lane == 0) wk.tile_loss[tile] = lsum * inv_n;
+    // ---- backward: dA2 = d3 W3, d2 = dA2 gelu'(z2) ----
+    uint32_t D3f[4] = {pack2(d3[0], d3[1]), pack2(d3[2], d3[3]), 0u, 0u};
+    uint32_t D2f[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+      const __nv_bfloat16* bp = sW3t + (nt * 8 + gq) * kSW3T + 2 * tq;
+      mma16816(acc[nt], D3f, ld32(bp), ld32(bp + 8));
+      float d[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        d[r] = acc[nt][r] * gg2[nt][r];
+        put(wk.D2t, nt * 8 + 2 * tq + (r & 1), (r & 2) ? sb8 : sa, d[r]);
+      }
+      const int kt = nt >> 1, hi = nt & 1;
+      D2f[kt][hi ? 2 : 0] = pack2(d[0], d[1]);
+      D2f[kt][hi ? 3 : 1] = pack2(d[2], d[3]);
+    }
+    // ---- dA1 = d2 W2, d1 = dA1 gelu'(z1) ----
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt) {
+        const __nv_bfloat16* bp = sW2t + (nt * 8 + gq) * kSW2 + 16 * kt + 2 * tq;
+        mma16816(acc[nt], D2f[kt], ld32(bp), ld32(bp + 8));
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        put(wk.D1t, nt * 8 + 2 * tq + (r & 1), (r & 2) ? sb8 : sa, acc[nt][r] * gg1[nt][r]);
     }
   }
 }
 
-// dW[o][i] = sum_s D[s][o] A[s][i], db[o] = sum_s D[s][o]; one thread per parameter, samples in
-// order (deterministic).
-__global__ void k_mlp_wgrad(const float* __restrict__ A0, const float* __restrict__ A1,
-                            const float* __restrict__ A2, const float* __restrict__ D1,
-                            const float* __restrict__ D2, const float* __restrict__ D3, int n,
-                            float* __restrict__ grad) {
+// Weight-gradient partials of one chunk of kChunk samples: P[chunk][layer params] = D^T [A | 1]
+// over the chunk, M = the layer's outputs (warp w: rows 16 w .. 16 w + 15), N = its inputs and
+// the ones row, K = the samples; A fragments from D (feature-major: a pair of samples is one
+// 32-bit load), B fragments from [A | 1] (the same).
+__global__ void __launch_bounds__(kTrainThreads) k_mlp_wgrad_mma(TrainWork wk) {
+  const int chunk = blockIdx.x, layer = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  const __nv_bfloat16 *D, *A;
+  int mrows, nin, woff, boff;
+  if (layer == 0) { D = wk.D1t; A = wk.A0t; mrows = kH; nin = kIn; woff = kW1; boff = kB1; }
+  else if (layer == 1) { D = wk.D2t; A = wk.A1t; mrows = kH; nin = kH; woff = kW2; boff = kB2; }
+  else { D = wk.D3t; A = wk.A2t; mrows = kOut; nin = kH; woff = kW3; boff = kB3; }
+  if (16 * warp >= mrows) return;
+  const int ntn = (nin + 1 + 7) / 8;  // n-tiles: inputs and the ones row
+  const size_t np = wk.np;
+  const int s0 = chunk * kChunk;
+  float acc[9][4];
+#pragma unroll
+  for (int nt = 0; nt < 9; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+  for (int kt = 0; kt < kChunk / 16; ++kt) {
+    const int s = s0 + 16 * kt + 2 * tq;
+    const __nv_bfloat16* dr = D + (size_t)(16 * warp + gq) * np + s;
+    const uint32_t af[4] = {ld32(dr), ld32(dr + 8 * np), ld32(dr + 8), ld32(dr + 8 * np + 8)};
+#pragma unroll
+    for (int nt = 0; nt < 9; ++nt) {
+      if (nt < ntn) {
+        const __nv_bfloat16* ar = A + (size_t)(nt * 8 + gq) * np + s;
+        mma16816(acc[nt], af, ld32(ar), ld32(ar + 8));
+      }
+    }
+  }
+  float* P = wk.part + (size_t)chunk * kNP;
+#pragma unroll
+  for (int nt = 0; nt < 9; ++nt) {
+    if (nt >= ntn) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int o = 16 * warp + gq + ((r & 2) ? 8 : 0);
+      const int i = nt * 8 + 2 * tq + (r & 1);
+      if (o >= mrows) continue;
+      if (i < nin) P[woff + o * nin + i] = acc[nt][r];
+      else if (i == nin) P[boff + o] = acc[nt][r];
+    }
+  }
+}
+
+// grad[q] = sum of the chunks' partials in chunk order; the loss from the tiles' partial losses
+// in tile order.
+__global__ void k_mlp_reduce(const float* __restrict__ part, int nchunk,
+                             const float* __restrict__ tile_loss, int ntiles,
+                             float* __restrict__ grad, float* __restrict__ loss) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= kNP) return;
-  const float *D, *A;
-  int o, i, nin, nout;
-  bool bias = false;
-  if (q < kB1) { D = D1; A = A0; nin = kIn; nout = kH; o = q / kIn; i = q % kIn; }
-  else if (q < kW2) { D = D1; A = A0; nin = kIn; nout = kH; o = q - kB1; i = 0; bias = true; }
-  else if (q < kB2) { D = D2; A = A1; nin = kH; nout = kH; o = (q - kW2) / kH; i = (q - kW2) % kH; }
-  else if (q < kW3) { D = D2; A = A1; nin = kH; nout = kH; o = q - kB2; i = 0; bias = true; }
-  else if (q < kB3) { D = D3; A = A2; nin = kH; nout = kOut; o = (q - kW3) / kH; i = (q - kW3) % kH; }
-  else { D = D3; A = A2; nin = kH; nout = kOut; o = q - kB3; i = 0; bias = true; }
-  float acc = 0.f;
-  for (int s = 0; s < n; ++s)
-    acc = fmaf(D[(size_t)s * nout + o], bias ? 1.f : A[(size_t)s * nin + i], acc);
-  grad[q] = acc;
+  if (q < kNP) {
+    float acc = 0.f;
+    for (int c = 0; c < nchunk; ++c) acc += part[(size_t)c * kNP + q];
+    grad[q] = acc;
+  }
+  if (q == 0) {
+    float l = 0.f;
+    for (int t = 0; t < ntiles; ++t) l += tile_loss[t];
+    *loss = l;
+  }
 }
 
 __global__ void k_mlp_adam(float* __restrict__ wm, __nv_bfloat16* __restrict__ wb,
@@ -197,15 +402,36 @@ mm_status mfail(mm_mlp* m, cudaError_t e, const char* what) {
   if (m) m->last_error = std::string(what) + ": " + cudaGetErrorString(e);
   return MM_ERR_CUDA;
 }
+// Bytes of the training work buffer for n samples (padded to whole chunks): the feature-major
+// BF16 operands, the chunk partials and the tile losses.
+size_t work_bytes(int np) {
+  const size_t rows = (size_t)kR0 + 2 * kR1 + 2 * kH + kRD3;
+  return rows * np * sizeof(__nv_bfloat16) + (size_t)(np / kChunk) * kNP * sizeof(float) +
+         (size_t)(np / 16) * sizeof(float);
+}
 mm_status ensure_work(mm_mlp* m, int n) {
-  if (n <= m->work_n) return MM_OK;
+  const int np = (n + kChunk - 1) / kChunk * kChunk;
+  if (np <= m->work_n) return MM_OK;
   cudaFree(m->work);
   m->work = nullptr;
-  const size_t per = (size_t)kIn + 6 * (size_t)kH + (size_t)kOut;
-  cudaError_t e = cudaMalloc(&m->work, per * n * sizeof(float));
+  cudaError_t e = cudaMalloc(&m->work, work_bytes(np));
   if (e != cudaSuccess) return mfail(m, e, "mlp work buffer");
-  m->work_n = n;
+  m->work_n = np;
   return MM_OK;
+}
+TrainWork carve_work(mm_mlp* m, int np) {
+  TrainWork wk;
+  __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(m->work);
+  wk.A0t = b;
+  wk.A1t = wk.A0t + (size_t)kR0 * np;
+  wk.A2t = wk.A1t + (size_t)kR1 * np;
+  wk.D1t = wk.A2t + (size_t)kR1 * np;
+  wk.D2t = wk.D1t + (size_t)kH * np;
+  wk.D3t = wk.D2t + (size_t)kH * np;
+  wk.part = reinterpret_cast<float*>(wk.D3t + (size_t)kRD3 * np);
+  wk.tile_loss = wk.part + (size_t)(np / kChunk) * kNP;
+  wk.np = np;
+  return wk;
 }
 }  // namespace
 
@@ -293,20 +519,16 @@ mm_status mm_mlp_grad(mm_mlp* m, const float* X_dev, const float* T_dev, int n, 
   if (!m || !X_dev || !T_dev || n < 1) return MM_ERR_INVALID_ARG;
   mm_status st = ensure_work(m, n);
   if (st != MM_OK) return st;
-  Work wk;
-  wk.A0 = m->work;
-  wk.A1 = wk.A0 + (size_t)kIn * n;
-  wk.A2 = wk.A1 + (size_t)kH * n;
-  wk.Z1 = wk.A2 + (size_t)kH * n;
-  wk.Z2 = wk.Z1 + (size_t)kH * n;
-  wk.D1 = wk.Z2 + (size_t)kH * n;
-  wk.D2 = wk.D1 + (size_t)kH * n;
-  wk.D3 = wk.D2 + (size_t)kH * n;
-  cudaError_t e = cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream);
-  const int blocks = std::min((n + 127) / 128, 152 * 8);
-  k_mlp_fwd_bwd<<<blocks, 128, 0, m->stream>>>(m->wb, m->norm, X_dev, T_dev, n, wk, m->loss);
-  k_mlp_wgrad<<<(kNP + 127) / 128, 128, 0, m->stream>>>(wk.A0, wk.A1, wk.A2, wk.D1, wk.D2,
-                                                        wk.D3, n, m->grad);
+  const int np = (n + kChunk - 1) / kChunk * kChunk;
+  const TrainWork wk = carve_work(m, np);
+  // the padding rows and samples of the operands must read as zeros
+  cudaError_t e = cudaMemsetAsync(m->work, 0, work_bytes(np), m->stream);
+  const int ntiles = np / 16;
+  const int blocks = std::min((ntiles + 3) / 4, 152 * 4);
+  k_mlp_train<<<blocks, kTrainThreads, 0, m->stream>>>(m->wb, m->norm, X_dev, T_dev, n, wk);
+  k_mlp_wgrad_mma<<<dim3(np / kChunk, 3), kTrainThreads, 0, m->stream>>>(wk);
+  k_mlp_reduce<<<(kNP + 127) / 128, 128, 0, m->stream>>>(wk.part, np / kChunk, wk.tile_loss,
+                                                         ntiles, m->grad, m->loss);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess && grad_host)
     e = cudaMemcpyAsync(grad_host, m->grad, kNP * sizeof(float), cudaMemcpyDeviceToHost, m->stream);

@@ -78,15 +78,22 @@ def test_mlp_gradient_matches_oracle():
         X = (rng.standard_normal((n, 39)) * 1.1).astype(np.float32)
         T = rng.standard_normal((n, 4)).astype(np.float32)
         L, g = mlp.grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
-        Lo, go = M.loss_and_grad(M.bf16_round(params), norm.astype(np.float64),
-                                 X.astype(np.float64), T.astype(np.float64))
+        # the kernels' products take BF16 operands (activations, back-propagated gradients) with
+        # FP32 accumulation: the oracle rounds the same operands
+        Lo, go = M.loss_and_grad_bf16(M.bf16_round(params), norm.astype(np.float64),
+                                      X.astype(np.float64), T.astype(np.float64))
         assert abs(L - Lo) <= 2e-5 * Lo, (n, L, Lo)
         err = np.max(np.abs(g.astype(np.float64) - go))
         assert err <= 1e-4 * np.max(np.abs(go)), (n, err, np.max(np.abs(go)))
-        # every layer's gradient is checked, not only the largest
-        for a, b in ((M.OFF_W1, M.OFF_B1), (M.OFF_W2, M.OFF_B2), (M.OFF_W3, M.OFF_B3)):
+        # every layer's gradient (weights and biases) is checked, not only the largest
+        for a, b in ((M.OFF_W1, M.OFF_B1), (M.OFF_B1, M.OFF_W2), (M.OFF_W2, M.OFF_B2),
+                     (M.OFF_B2, M.OFF_W3), (M.OFF_W3, M.OFF_B3), (M.OFF_B3, M.N_PARAM)):
             e = np.max(np.abs(g[a:b] - go[a:b]))
             assert e <= 1e-4 * np.max(np.abs(go[a:b])) + 1e-9, (n, a, e)
+        # and the BF16 operands cost no more than a few BF16 units against the plain gradient
+        _, gx = M.loss_and_grad(M.bf16_round(params), norm.astype(np.float64),
+                                X.astype(np.float64), T.astype(np.float64))
+        assert np.max(np.abs(g - gx)) <= 2.0 ** -5 * np.max(np.abs(gx))
     mlp.close()
 
 
@@ -99,8 +106,9 @@ def test_adam_step_matches_oracle():
     T = rng.standard_normal((900, 4)).astype(np.float32)
     lr = 1e-3
     for t in (1, 2):
-        Lo, go = M.loss_and_grad(M.bf16_round(params if t == 1 else w_gpu), norm.astype(np.float64),
-                                 X.astype(np.float64), T.astype(np.float64))
+        Lo, go = M.loss_and_grad_bf16(M.bf16_round(params if t == 1 else w_gpu),
+                                      norm.astype(np.float64), X.astype(np.float64),
+                                      T.astype(np.float64))
         if t == 1:
             w_o, m1, m2 = M.adam_step(params.astype(np.float64), 0.0, 0.0, go, 1, lr)
         else:
