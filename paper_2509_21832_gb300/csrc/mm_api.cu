@@ -394,6 +394,9 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
 // kernels as in the step-by-step order, so the results are the same bit for bit.  Needs a
 // non-periodic y direction (a periodic one would tie the first band to the last).
 bool pipeline_f32_ok(const mm_ctx* c) {
+#ifdef MM_F32_NO_PIPELINE
+  return false;
+#endif
   return c->fp32 && c->kp.bc[2] != MM_BC_PERIODIC && c->nseg >= 2 && !c->mms;
 }
 
@@ -442,7 +445,7 @@ mm_status enqueue_f32_pipeline(mm_ctx* c, double dt, double eps, int nsteps) {
   // CTAs of the phase-space kernel per SM in the pipeline: fewer than the kernel could hold
   // leaves registers for the per-cell FP64 kernels that run beside it
 #ifndef MM_F32_PIPE_CTAS
-#define MM_F32_PIPE_CTAS 3
+#define MM_F32_PIPE_CTAS 4
 #endif
   const size_t smem_floor = MM_F32_PIPE_CTAS >= 4 ? 0 : 233472 / MM_F32_PIPE_CTAS - 2048;
   // fork the three streams from the context stream
