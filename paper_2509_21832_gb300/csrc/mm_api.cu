@@ -106,11 +106,6 @@ struct mm_ctx {
   // phase-space kernel (they need only Q^n); ev_fork marks Q^n, ev_x1 their end
   cudaStream_t mstream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_x1 = nullptr;
-  // FP32 g, several steps at once: two streams for the banded phase-space kernel, one event per
-  // band for "per-cell fields ready" and for "phase-space kernel done", and the join events
-  cudaStream_t bstream[2] = {nullptr, nullptr};
-  std::vector<cudaEvent_t> ev_band_p, ev_band_m;
-  cudaEvent_t ev_join[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> chunk_events;
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -310,7 +305,7 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
     if (c->n_wall > 0)
       timed(c, T_MICRO_YW, [&] {
         launch_micro_y_wall<float>(Ge, Gs, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt,
-                                   eps, wall_shape_f32(g.nv1, g.nv2), c->err, s);
+                                   eps, c->ms, c->err, s);
       });
     std::swap(c->G, c->Gs);
   } else {
@@ -381,147 +376,6 @@ void enqueue_hybrid(mm_ctx* c, double dt, double eps) {
   timed(c, T_MACRO_X2, [&] { launch_macro_x2(c->H, c->mb, g, p, dt, c->err, s); });
   timed(c, T_MACRO_Y, [&] { launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, s); });
   c->closure_steps += 1;
-}
-
-// FP32 g, nsteps >= 1 steps in one go, as a software pipeline over row bands (whole segments of
-// the fused kernel).  Band b's phase-space kernel runs on one of two streams as soon as the
-// per-cell fields of bands b-1..b+1 are ready; the per-cell FP64 work (heat-flux unpack, wall
-// cells, macro x2, macro y, then the next step's (u, T), macro x1 and coefficients) runs on a
-// third stream band by band, each task after the bands it reads: macro y of band b after
-// macro x2 of b-1..b+1, the next step's fields of band b after macro y of b, its coefficients
-// after the (u, T) of b-1..b+1, its phase-space kernel after those.  So the FP64 work of some
-// bands runs beside the FP32 phase-space kernel of others.  Every cell is computed by the same
-// kernels as in the step-by-step order, so the results are the same bit for bit.  Needs a
-// non-periodic y direction (a periodic one would tie the first band to the last).
-bool pipeline_f32_ok(const mm_ctx* c) {
-#ifdef MM_F32_NO_PIPELINE
-  return false;
-#endif
-  return c->fp32 && c->kp.bc[2] != MM_BC_PERIODIC && c->nseg >= 2 && !c->mms;
-}
-
-mm_status enqueue_f32_pipeline(mm_ctx* c, double dt, double eps, int nsteps) {
-  const KGrid& g = c->kg;
-  const KParams& p = c->kp;
-  const int nx = g.nx, ny = g.ny;
-  const int seg_rows = (ny + c->nseg - 1) / c->nseg;
-  const int K = (ny + seg_rows - 1) / seg_rows;  // bands: the nonempty segments
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
-    if (!c->bstream[k]) e = cudaStreamCreateWithFlags(&c->bstream[k], cudaStreamNonBlocking);
-  if (e == cudaSuccess && !c->mstream)
-    e = cudaStreamCreateWithFlags(&c->mstream, cudaStreamNonBlocking);
-  auto make = [&](std::vector<cudaEvent_t>& v) {
-    while (e == cudaSuccess && (int)v.size() < K) {
-      cudaEvent_t ev = nullptr;
-      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-      if (e == cudaSuccess) v.push_back(ev);
-    }
-  };
-  make(c->ev_band_p);
-  make(c->ev_band_m);
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-    if (!c->ev_join[k]) e = cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(c, e, "pipeline streams");
-
-  cudaStream_t s = c->stream, sf = c->mstream;
-  cudaStream_t sm[2] = {c->bstream[0], c->bstream[1]};
-  auto r0 = [&](int b) { return b * seg_rows; };
-  auto r1 = [&](int b) { return std::min(ny, (b + 1) * seg_rows); };
-  // wall cells (listed in cell order) in rows [0, r): rows fully on a diffuse bottom or top wall,
-  // else the diffuse x sides
-  const int sides = (p.bc[0] == MM_BC_DIFFUSE ? 1 : 0) + (p.bc[1] == MM_BC_DIFFUSE ? 1 : 0);
-  auto walls_before = [&](int r) {
-    int n = 0;
-    for (int j = 0; j < r; ++j) {
-      const bool full = (j == 0 && p.bc[2] == MM_BC_DIFFUSE) ||
-                        (j == ny - 1 && p.bc[3] == MM_BC_DIFFUSE);
-      n += full ? nx : std::min(sides, nx);
-    }
-    return n;
-  };
-  float* Ge = static_cast<float*>(c->Gexp);
-  const MicroShape wshape = wall_shape_f32(g.nv1, g.nv2);
-  // CTAs of the phase-space kernel per SM in the pipeline: fewer than the kernel could hold
-  // leaves registers for the per-cell FP64 kernels that run beside it
-#ifndef MM_F32_PIPE_CTAS
-#define MM_F32_PIPE_CTAS 4
-#endif
-  const size_t smem_floor = MM_F32_PIPE_CTAS >= 4 ? 0 : 233472 / MM_F32_PIPE_CTAS - 2048;
-  // fork the three streams from the context stream
-  cudaEventRecord(c->ev_join[0], s);
-  for (cudaStream_t t : {sm[0], sm[1], sf}) cudaStreamWaitEvent(t, c->ev_join[0], 0);
-  // the first step's per-cell fields, all bands at once
-  timed_on(c, T_PRIMS_UT, sf, [&] { launch_prims_uT(c->Q, c->prim, g, sf); });
-  timed_on(c, T_PRIMS, sf, [&] {
-    launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, sf);
-  });
-  for (int b = 0; b < K; ++b) cudaEventRecord(c->ev_band_p[b], sf);
-  timed_on(c, T_MACRO_X1, sf, [&] { launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, sf); });
-  for (int n = 0; n < nsteps; ++n) {
-    const bool last = n == nsteps - 1;
-    const float* Gin = static_cast<const float*>(c->G);
-    float* Gout = static_cast<float*>(c->Gs);
-    for (int b = 0; b < K; ++b) {
-      cudaStream_t st = sm[b & 1];
-      cudaStreamWaitEvent(st, c->ev_band_p[std::min(b + 1, K - 1)], 0);
-      if (b + 1 < K) cudaStreamWaitEvent(st, c->ev_band_p[b], 0);
-      timed_on(c, T_MICRO_FUSED, st, [&] {
-        launch_micro_fused_f32(Gin, Gout, Ge, c->Hf, c->primf, g, p, dt, c->ms, c->nseg, c->err,
-                               st, b, b + 1, smem_floor);
-      });
-      cudaEventRecord(c->ev_band_m[b], st);
-    }
-    int nY = 0, nU = 0, nX1 = 0, nP = 0;  // bands done of each next-step task
-    auto advance = [&](int nX2) {  // everything whose inputs are ready after nX2 bands of x2
-      for (; nY < K && nX2 >= std::min(nY + 2, K); ++nY)
-        timed_on(c, T_MACRO_Y, sf, [&] {
-          launch_macro_y(c->H, c->mb, c->Q, g, p, dt, eps, c->err, sf, nullptr, r0(nY) * nx,
-                         r1(nY) * nx);
-        });
-      if (last) return;
-      for (; nU < nY; ++nU)
-        timed_on(c, T_PRIMS_UT, sf, [&] {
-          launch_prims_uT(c->Q, c->prim, g, sf, r0(nU) * nx, r1(nU) * nx);
-        });
-      for (; nX1 < K && nY >= std::min(nX1 + 2, K); ++nX1)
-        timed_on(c, T_MACRO_X1, sf, [&] {
-          launch_macro_x1(c->Q, c->mb, g, p, dt, eps, c->err, sf, r0(nX1) * nx, r1(nX1) * nx);
-        });
-      for (; nP < K && nU >= std::min(nP + 2, K); ++nP) {
-        timed_on(c, T_PRIMS, sf, [&] {
-          launch_prims(c->Q, c->prim, c->primf, g, p, dt, eps, c->err, sf, r0(nP) * nx,
-                       r1(nP) * nx);
-        });
-        cudaEventRecord(c->ev_band_p[nP], sf);
-      }
-    };
-    for (int b = 0; b < K; ++b) {
-      cudaStreamWaitEvent(sf, c->ev_band_m[b], 0);
-      if (b + 1 < K) cudaStreamWaitEvent(sf, c->ev_band_m[b + 1], 0);
-      timed_on(c, T_HUNPACK, sf, [&] {
-        launch_h_unpack(c->Hf, c->H, g, eps, sf, r0(b) * nx, r1(b) * nx);
-      });
-      const int w0 = walls_before(r0(b)), w1 = walls_before(r1(b));
-      if (w1 > w0)
-        timed_on(c, T_MICRO_YW, sf, [&] {
-          launch_micro_y_wall<float>(Ge, Gout, c->H, c->prim, c->wall_cells + w0, w1 - w0, g, p,
-                                     dt, eps, wshape, c->err, sf);
-        });
-      timed_on(c, T_MACRO_X2, sf, [&] {
-        launch_macro_x2(c->H, c->mb, g, p, dt, c->err, sf, r0(b) * nx, r1(b) * nx);
-      });
-      advance(b + 1);
-    }
-    std::swap(c->G, c->Gs);
-  }
-  // join: the context stream continues after all three
-  cudaEventRecord(c->ev_join[0], sm[0]);
-  cudaEventRecord(c->ev_join[1], sm[1]);
-  cudaEventRecord(c->ev_join[2], sf);
-  for (int k = 0; k < 3; ++k) cudaStreamWaitEvent(s, c->ev_join[k], 0);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? MM_OK : cuda_fail(c, e, "pipelined FP32 steps");
 }
 
 // A step with the closure set: an evaluation (hybrid) step every cl_period steps, whose closure
@@ -1011,14 +865,9 @@ mm_status mm_step(mm_ctx* c, double dt, double eps, int nsteps) {
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(c, MM_ERR_INVALID_ARG, "eps must be > 0");
   if (nsteps < 0) return fail(c, MM_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (!c->have_state) return fail(c, MM_ERR_STATE, "mm_step before mm_set_state");
-  if (nsteps > 0 && pipeline_f32_ok(c)) {
-    mm_status st = enqueue_f32_pipeline(c, dt, eps, nsteps);
+  for (int n = 0; n < nsteps; ++n) {
+    mm_status st = enqueue_step(c, dt, eps);
     if (st != MM_OK) return st;
-  } else {
-    for (int n = 0; n < nsteps; ++n) {
-      mm_status st = enqueue_step(c, dt, eps);
-      if (st != MM_OK) return st;
-    }
   }
   if (c->borrowed && c->G != c->user_G) {
     // FP32 g ping-pongs between G and the scratch copy: leave the state in the caller's buffer
@@ -1328,12 +1177,9 @@ void mm_destroy(mm_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->cl_host) cudaFreeHost(c->cl_host);
   destroy_events(c);
-  for (cudaEvent_t ev : {c->ev_fork, c->ev_x1, c->ev_join[0], c->ev_join[1], c->ev_join[2]})
+  for (cudaEvent_t ev : {c->ev_fork, c->ev_x1})
     if (ev) cudaEventDestroy(ev);
-  for (cudaEvent_t ev : c->ev_band_p) cudaEventDestroy(ev);
-  for (cudaEvent_t ev : c->ev_band_m) cudaEventDestroy(ev);
-  for (cudaStream_t t : {c->cstream, c->xstream, c->ystream, c->mstream, c->bstream[0],
-                         c->bstream[1]})
+  for (cudaStream_t t : {c->cstream, c->xstream, c->ystream, c->mstream})
     if (t) {
       cudaStreamSynchronize(t);
       cudaStreamDestroy(t);

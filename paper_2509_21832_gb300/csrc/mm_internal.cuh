@@ -70,9 +70,6 @@ struct MicroShape {
   int xrows;         // rows per thread of the register-resident x sweep (0: generic kernel)
 };
 MicroShape micro_shape(int nv1, int nv2);
-// The diffuse-wall kernel's shape for FP32-g contexts (no row sums kept): several rows per pass
-// (about 128 threads), as there are few wall cells to spread over the GPU.
-MicroShape wall_shape_f32(int nv1, int nv2);
 
 // Per-cell fields: launch_prims_uT writes every cell's (u1, u2, T) into prim, then
 // launch_prims the rest (it reads the neighbours' (u1, u2, T) there): always in this order.
@@ -131,7 +128,7 @@ constexpr size_t kMaxSmemPerCta = 227 * 1024;
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
                             const MicroShape& ms, int nseg, int* err, cudaStream_t s,
-                            int seg0 = 0, int seg1 = -1, size_t smem_floor = 0);
+                            int seg0 = 0, int seg1 = -1);
 // Buffers of the macro step: Q* and Q**, each cell's half fluxes along x (of Q*) and y (of Q**)
 // [Fp(6) Fm(6)][ny][nx], and the fluxes through the non-periodic boundary faces
 // BX [2 sides][6][ny], BY [2 sides][6][nx].

@@ -167,16 +167,6 @@ __global__ void k_f32_to_f64(const float* __restrict__ in, double* __restrict__ 
 
 int x_rows(const MicroShape& ms, int nv2);
 
-MicroShape wall_shape_f32(int nv1, int nv2) {
-  MicroShape ms = micro_shape(nv1, nv2);
-  const int R = std::max(1, std::min(nv2, 128 / nv1));
-  if (R * nv1 > ms.R * nv1 && R * nv1 <= micro_body::kMaxThreads) {
-    ms.R = R;
-    ms.threads = (R * nv1 + 31) / 32 * 32;
-  }
-  return ms;
-}
-
 MicroShape micro_shape(int nv1, int nv2) {
   MicroShape ms{1, 32, 0, 0, 0, 0};
   double best = -1.0;

@@ -1063,7 +1063,7 @@ int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
                             const MicroShape& ms, int nseg, int* err, cudaStream_t s, int seg0,
-                            int seg1, size_t smem_floor) {
+                            int seg1) {
   (void)ms;
   const FusedPick f = pick_fused(g);
   FusedF32 a;
@@ -1086,11 +1086,9 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
   a.nseg = seg1 - seg0;
   // one warp per column and segment; the staged kernels give a CTA kFusedWarps adjacent columns
   const int warps = ((g.nx + kFusedWarps - 1) / kFusedWarps) * kFusedWarps * a.nseg;
-  // a floor above the kernel's own need caps the CTAs per SM (room for concurrent kernels)
-  const size_t smem = std::max(f.smem, std::min(smem_floor, kMaxSmemPerCta));
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  f.kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, smem, s>>>(a);
+  if (f.smem > 48 * 1024)
+    cudaFuncSetAttribute(f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
+  f.kern<<<(warps + kFusedWarps - 1) / kFusedWarps, 32 * kFusedWarps, f.smem, s>>>(a);
 }
 
 }  // namespace mmk

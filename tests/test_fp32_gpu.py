@@ -133,9 +133,9 @@ def test_fp32g_beyond_32bit_phase_offsets_vs_fp64():
 @pytest.mark.parametrize("bc", [(I.EXTRAP, I.EXTRAP, I.DIFFUSE, I.EXTRAP),
                                 (I.DIFFUSE, I.SPECULAR, I.SPECULAR, I.DIFFUSE)])
 def test_pipelined_steps_equal_single_steps(bc):
-    """Several FP32-g steps in one call run as a pipeline over row bands on three streams (the
-    per-cell FP64 work of some bands beside the phase-space kernel of others); the result equals
-    that of one call per step bit for bit, with diffuse walls on the bottom, top and x sides."""
+    """Several FP32-g steps in one call (macro x1 of each step on a side stream beside the
+    phase-space kernel) equal one call per step bit for bit, with diffuse walls on the bottom,
+    top and x sides."""
     g = I.Grid(nx=96, ny=256, nv1=24, nv2=24)
     p = I.Params(nu=-0.5, bc=bc, wall_T=(1.1, 1.0, 0.9, 1.2), wall_U=(0.1, 0.0, 0.2, -0.1),
                  precision=I.PREC_G_FP32)
