@@ -524,6 +524,8 @@ def main():
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--batch-nmin", type=int, default=64)
+    ap.add_argument("--batch-nmax", type=int, default=256)
     ap.add_argument("--closure-only", action="store_true")
     ap.add_argument("--closure-n", type=int, default=512)
     ap.add_argument("--closure-steps", type=int, default=100)
@@ -543,7 +545,8 @@ def main():
     if args.batch_only:
         import torch
         torch.cuda.set_device(local)
-        print(json.dumps(batch_variant(args)), flush=True)
+        print(json.dumps(batch_variant(args, nmin=args.batch_nmin, nmax=args.batch_nmax)),
+              flush=True)
         print(json.dumps(batch_variant(args, count=256, nmin=16, nmax=48, steps=50)), flush=True)
         return
     if args.variant_only:

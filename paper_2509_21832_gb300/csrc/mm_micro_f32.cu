@@ -849,7 +849,7 @@ struct StagedShape {
   static constexpr int STAGE = (W + 2) * S::NV;  // floats: the g blocks of columns i0-1 .. i0+W
   static constexpr int RING = 3 * S::NV;          // per warp
   static constexpr int TABLES = 14 * NV2;         // per warp
-  static constexpr int FLOATS = STAGE + W * (RING + TABLES) + 4;  // + the mbarrier (8 bytes)
+  static constexpr int FLOATS = STAGE + W * (RING + TABLES) + 6;  // + two mbarriers, a flag
 };
 
 // Source of stage slot sigma (column c = i0 - 1 + sigma) for row jj: the column's block; beyond
@@ -885,27 +885,34 @@ __global__ void __launch_bounds__(32 * kFusedWarps, MM_F32_MINB) k_micro_staged_
   float* ring = smf + T::STAGE + w * (T::RING + T::TABLES);
   float* xt = ring + T::RING;
   float* yt = xt + 4 * NV2;
-  const uint32_t bar = smem_addr(smf + T::STAGE + W * (T::RING + T::TABLES));
+  // full: the stage holds the next row (the bulk copies' bytes have landed); empty: every warp
+  // has finished reading the stage, so that it may be refilled
+  float* bars = smf + T::STAGE + W * (T::RING + T::TABLES);
+  const uint32_t bar = smem_addr(bars);
+  const uint32_t bar_empty = smem_addr(bars + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 4);
   const int ncx = (g.nx + W - 1) / W;
   const int cx = blockIdx.x % ncx, seg = a.seg0 + blockIdx.x / ncx;
   const int i0 = cx * W, i = i0 + w;
-  const bool col = i < g.nx;  // warps past the last column only take part in the barriers
+  const bool col = i < g.nx;  // warps past the last column only read nothing from the stage
   const int j0 = seg * a.seg_rows;
   const int j1 = min(g.ny, j0 + a.seg_rows);
   if (j0 >= j1) return;  // uniform over the CTA
   const bool pery = a.p.bc[2] == MM_BC_PERIODIC;
   const bool mirl = i == 0 && a.p.bc[0] == MM_BC_SPECULAR;
   const bool mirr = i == g.nx - 1 && a.p.bc[1] == MM_BC_SPECULAR;
+  const int lane = threadIdx.x & 31;
   auto slot = [&](int pos) { return ring + (size_t)(pos % 3) * S::NV; };
 
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_empty), "r"(W) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_flag = 0;
   }
   __syncthreads();
   // bulk copies of row jj's blocks into the stage (thread 0)
   auto issue = [&](int jj) {
-    if (threadIdx.x != 0) return;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     const float* src[W + 2];
     unsigned bytes = 0;
@@ -936,24 +943,51 @@ __global__ void __launch_bounds__(32 * kFusedWarps, MM_F32_MINB) k_micro_staged_
     if (jj >= g.ny) jj -= g.ny;
     return jj;
   };
-  uint32_t parity = 0;
-  issue(xrow(0));
-  // x sweep number n into ring position pos, then the copy for sweep n + 1
+  uint32_t parity = 0;        // phase of the full barrier awaited next
+  uint32_t eparity = 0;       // phase of the empty barrier (thread 0)
+  bool pending = true;        // thread 0: a copy issued whose completion no warp has seen yet
+  if (threadIdx.x == 0) issue(xrow(0));
+  // Give up after a wait ran out (here or in another warp): thread 0 first lets its copies land
+  // (bounded again), so that no bulk copy writes into the shared memory of a finished CTA.
+  auto give_up = [&]() {
+    if (lane == 0) {
+      atomicOr(a.err, ERR_WAIT_TIMEOUT);
+      *abort_flag = 1;
+    }
+    if (threadIdx.x == 0 && pending) mbar_wait_bounded(bar, parity);
+    return false;
+  };
+  // x sweep number n into ring position pos; the warp then releases the stage, and thread 0
+  // refills it with the next row as soon as every warp has released it (the other warps go on
+  // to their y sweeps meanwhile)
   auto xstep = [&](int n, int pos) -> bool {
+    if (*abort_flag) return give_up();
     const int jj = xrow(n);
     const float fvx = col ? load_fields(a.pf, g.nx * g.ny, jj * g.nx + i) : 0.f;
     // the sweep's warp shuffles need every lane: a warp sweeps only if all its lanes saw the copy
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
+    if (!ok) return give_up();
     parity ^= 1u;
-    if (col && ok)
+    if (threadIdx.x == 0) pending = false;
+    if (col)
       fx_sweep<NV1, NV2, true>(a, i, jj, slot(pos), xt, stage + (w + 1) * S::NV,
                                stage + w * S::NV, stage + (w + 2) * S::NV, mirl, mirr, fvx);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicOr(a.err, ERR_WAIT_TIMEOUT);
-      mbar_wait_bounded(bar, parity ^ 1u);  // copies still in flight, bounded again
-      return false;
+    __syncwarp();
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_empty) : "memory");
+    if (threadIdx.x == 0) {
+      const bool free = mbar_wait_bounded(bar_empty, eparity);
+      if (free && n + 1 < nx_rows) {
+        issue(xrow(n + 1));
+        pending = true;
+      }
+      if (!free) {
+        atomicOr(a.err, ERR_WAIT_TIMEOUT);
+        *abort_flag = 1;
+      }
     }
-    if (n + 1 < nx_rows) issue(xrow(n + 1));
+    eparity ^= 1u;
+    __syncwarp();
     return true;
   };
   int n = 0;
