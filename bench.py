@@ -448,11 +448,13 @@ def run_blocks(pr, world, rank, steps, warmup, make_stepper, device, group=None)
         halo.exchange(blocks, copies, rank, Qt, Gt, group=group)
         step(regions)
 
+    sync = dist.is_available() and dist.is_initialized()
     for _ in range(warmup):
         one()
     if cuda:
         torch.cuda.synchronize()
-    dist.barrier(group=group)
+    if sync:
+        dist.barrier(group=group)
     t0 = time.perf_counter()
     if cuda:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -465,7 +467,8 @@ def run_blocks(pr, world, rank, steps, warmup, make_stepper, device, group=None)
         sec = e0.elapsed_time(e1) * 1e-3
     else:
         sec = time.perf_counter() - t0
-    dist.barrier(group=group)
+    if sync:
+        dist.barrier(group=group)
     return b, Qt, Gt, sec
 
 

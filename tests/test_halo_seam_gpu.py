@@ -120,3 +120,22 @@ def test_blocks_with_region_refresh_reproduce_the_undivided_step(name, nv, bc, p
             solvers_bad.g_region_changed(0, grid.nx + 1, 0, 1)
         finally:
             solvers_bad.close()
+
+
+def test_decomposed_bench_stepper_on_one_block():
+    """The GPU stepper of `bench.py --decompose` (a borrowed context on the block's tensors) on a
+    single rank, where the one block is the whole grid: the same state as a plain context after
+    the same steps, bit for bit."""
+    import bench
+    pr = I.bump_specular(n=48, nv=32, eps=1e-2, seed=4)
+    b, Qt, Gt, sec = bench.run_blocks(pr, 1, 0, 3, 0, bench.gpu_block_stepper,
+                                      torch.device("cuda"))
+    torch.cuda.synchronize()
+    with api.Solver(pr.grid, pr.params) as s:
+        s.set_state(pr.Q, pr.G)
+        s.step(pr.dt, pr.eps, 3)
+        Qu, _ = s.get_moments()
+        Gu = s.get_g()
+    assert sec > 0
+    assert np.array_equal(Qt.cpu().numpy().reshape(Qu.shape), Qu)
+    assert np.array_equal(Gt.cpu().numpy().reshape(Gu.shape), Gu)
