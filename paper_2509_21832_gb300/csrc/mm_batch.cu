@@ -135,10 +135,9 @@ __device__ bool wait_deps(const MegaArgs& a, const unsigned* cur, const unsigned
 }
 
 // The whole of nsteps batch steps: persistent CTAs of blockDim.x threads take queue items.
-#ifndef MM_BATCH_MINB
-#define MM_BATCH_MINB 24
-#endif
-__global__ void __launch_bounds__(32, MM_BATCH_MINB) k_batch_steps(MegaArgs a) {
+// Compiled for 24 one-warp CTAs per SM (80 registers; the spills fall in the macro and wall
+// paths): measured faster than 16 (128 registers) or 20 (96).
+__global__ void __launch_bounds__(32, 24) k_batch_steps(MegaArgs a) {
   extern __shared__ double sm[];
   __shared__ int s_item;
   const int t = threadIdx.x, T = blockDim.x;
