@@ -288,7 +288,10 @@ def fp32_variant(args, stream):
         "fp64_ms_per_step": ms64 / pr.nsteps, "speedup_vs_fp64": ms64 / ms,
         "hbm_achieved_gbs": hbm, "hbm_frac": hbm / peaks["hbm_gbs"],
         "l1_density_rel_err_vs_fp64": float(np.sum(np.abs(Q32[0] - Q64[0])) / np.sum(np.abs(Q64[0]))),
-        "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()}})
+        # per step, summed over the launches of a kind (the phase-space kernel is launched once
+        # per group of row segments)
+        "kernel_ms_per_step": {k: v[0] / pr.nsteps for k, v in kt.items() if v[1]},
+        "launches_per_step": {k: v[1] / pr.nsteps for k, v in kt.items() if v[1]}})
     return out
 
 

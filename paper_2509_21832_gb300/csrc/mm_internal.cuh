@@ -152,7 +152,7 @@ void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGri
                     const KParams& p, double dt, double eps, int* err, cudaStream_t s,
                     const double* srcq = nullptr, int c0 = 0, int c1 = -1);
 void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s,
-                     int c0 = 0, int c1 = -1);
+                     int c0 = 0, int c1 = -1, const KParams* skip_walls = nullptr);
 __host__ __device__ inline MacroBufs carve_macro(double* base, int nx, int ny) {
   const size_t nc = (size_t)nx * ny;
   MacroBufs mb;

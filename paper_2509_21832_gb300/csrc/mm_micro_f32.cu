@@ -1075,7 +1075,8 @@ int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long resident = (long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1) * kFusedWarps;
-  // about four resident waves of columns, but at least 16 rows per segment
+  // about four resident waves of columns (three and four measured best of 2 ... 8), but at
+  // least 16 rows per segment
   long nseg = (4 * resident + g.nx - 1) / g.nx;
   const long max_seg = g.ny / 16 > 1 ? g.ny / 16 : 1;
   if (nseg > max_seg) nseg = max_seg;

@@ -43,6 +43,12 @@ CASES = [
     ("row_24", dict(nx=5, ny=1, nv1=24, nv2=24), (I.EXTRAP, I.SPECULAR, I.PERIODIC, I.PERIODIC), {}),
     ("column_32", dict(nx=1, ny=6, nv1=32, nv2=32), (I.PERIODIC, I.PERIODIC, I.DIFFUSE, I.EXTRAP),
      dict(wall_T=(1.0, 1.0, 1.1, 1.0))),
+    # tall enough for several row segments: with diffuse walls on the bottom and top only, the
+    # segments that export the wall rows' G* run first and the wall kernel runs beside the rest
+    ("walls_y_segments_24", dict(nx=8, ny=64, nv1=24, nv2=24),
+     (I.PERIODIC, I.PERIODIC, I.DIFFUSE, I.DIFFUSE), dict(wall_T=(1.0, 1.0, 1.1, 0.9))),
+    ("walls_y_segments_16", dict(nx=12, ny=50, nv1=16, nv2=16),
+     (I.EXTRAP, I.SPECULAR, I.DIFFUSE, I.DIFFUSE), dict(wall_T=(1.0, 1.0, 1.2, 1.0))),
     # v2 mesh not symmetric about zero: the column-mapped kernel of the 24^2 shape
     ("asym_24", dict(nx=8, ny=9, nv1=24, nv2=24, v2min=-7.0, v2max=9.0),
      (I.EXTRAP, I.EXTRAP, I.PERIODIC, I.PERIODIC), {}),
