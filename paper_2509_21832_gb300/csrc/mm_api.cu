@@ -298,46 +298,15 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   if constexpr (sizeof(Tg) == sizeof(float)) {
     // fused streaming kernel: G -> Gs (ping-pong), wall cells from the exported G*
     float* Ge = static_cast<float*>(c->Gexp);
-    const int nseg = c->nseg;
-    const int seg_rows = (g.ny + nseg - 1) / nseg;
-    const bool bot = p.bc[2] == MM_BC_DIFFUSE, top = p.bc[3] == MM_BC_DIFFUSE;
-    const bool xwall = p.bc[0] == MM_BC_DIFFUSE || p.bc[1] == MM_BC_DIFFUSE;
-    // G* of rows 0, 1 (ny-2, ny-1) is exported by the segments that own or border those rows:
-    // the ones holding rows 0..2 (ny-3..ny-1)
-    const int b1 = bot ? std::min(nseg, 2 / seg_rows + 1) : 0;
-    const int t0 = top ? std::max(0, g.ny - 3) / seg_rows : nseg;
-    if (x1_side && c->n_wall > 0 && !xwall && b1 < t0) {
-      // diffuse walls only at the bottom and top: the segments that export the wall rows' G*
-      // run first, then the wall kernel on the side stream beside the remaining segments
-      auto seg = [&](int s0, int s1) {
-        if (s1 > s0)
-          timed(c, T_MICRO_FUSED, [&] {
-            launch_micro_fused_f32(G, Gs, Ge, c->Hf, c->primf, g, p, dt, c->ms, nseg, c->err, s,
-                                   s0, s1);
-          });
-      };
-      seg(0, b1);
-      seg(t0, nseg);
-      cudaEventRecord(c->ev_fork, s);
-      cudaStreamWaitEvent(c->mstream, c->ev_fork, 0);
-      timed_on(c, T_MICRO_YW, c->mstream, [&] {
-        launch_micro_y_wall<float>(Ge, Gs, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt,
-                                   eps, c->ms, c->err, c->mstream);
+    timed(c, T_MICRO_FUSED, [&] {
+      launch_micro_fused_f32(G, Gs, Ge, c->Hf, c->primf, g, p, dt, c->ms, c->nseg, c->err, s);
+    });
+    timed(c, T_HUNPACK, [&] { launch_h_unpack(c->Hf, c->H, g, eps, s); });
+    if (c->n_wall > 0)
+      timed(c, T_MICRO_YW, [&] {
+        launch_wall_f32(Ge, Gs, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps, c->err,
+                        s);
       });
-      cudaEventRecord(c->ev_x1, c->mstream);  // macro x2 waits for macro x1 and the walls
-      seg(b1, t0);
-      timed(c, T_HUNPACK, [&] { launch_h_unpack(c->Hf, c->H, g, eps, s, 0, -1, &p); });
-    } else {
-      timed(c, T_MICRO_FUSED, [&] {
-        launch_micro_fused_f32(G, Gs, Ge, c->Hf, c->primf, g, p, dt, c->ms, nseg, c->err, s);
-      });
-      timed(c, T_HUNPACK, [&] { launch_h_unpack(c->Hf, c->H, g, eps, s); });
-      if (c->n_wall > 0)
-        timed(c, T_MICRO_YW, [&] {
-          launch_micro_y_wall<float>(Ge, Gs, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt,
-                                     eps, c->ms, c->err, s);
-        });
-    }
     std::swap(c->G, c->Gs);
   } else {
     // the x sweep from the row sums of G (left by the previous y sweep, or formed when G was

@@ -112,6 +112,12 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
                          double dt, double eps, const MicroShape& ms, int* err, cudaStream_t s,
                          double* Rm = nullptr);
+// Diffuse-wall cells of the FP32-g step from the G* the fused kernel exported (Gs): G^{n+1} of
+// those cells into Gout and their heat flux into H (FP64); one CTA per cell, per-velocity
+// arithmetic in FP32.
+void launch_wall_f32(const float* Gs, float* Gout, double* H, const double* prim,
+                     const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
+                     double dt, double eps, int* err, cudaStream_t s);
 // Fused FP32-g micro step (x sweep, y sweep, relaxation, heat flux) streaming over column
 // segments: reads Gin once and writes Gout (a different buffer); cells next to a diffuse wall are
 // left to the wall kernel, which reads the G* this kernel exports to Gexp.  One warp per cell
@@ -152,7 +158,7 @@ void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGri
                     const KParams& p, double dt, double eps, int* err, cudaStream_t s,
                     const double* srcq = nullptr, int c0 = 0, int c1 = -1);
 void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s,
-                     int c0 = 0, int c1 = -1, const KParams* skip_walls = nullptr);
+                     int c0 = 0, int c1 = -1);
 __host__ __device__ inline MacroBufs carve_macro(double* base, int nx, int ny) {
   const size_t nc = (size_t)nx * ny;
   MacroBufs mb;

@@ -51,17 +51,10 @@ __global__ void k_macro_y(const double* __restrict__ H, MacroBufs mb, double* __
 }
 
 // Heat flux of the FP32-g kernels: compensated FP32 (hi, lo) totals -> FP64, times eps dv1 dv2.
-// With skip set, cells next to a diffuse wall are left alone (the wall kernel writes their H).
 __global__ void k_h_unpack(const float* __restrict__ Hf, double* __restrict__ H, int nc,
-                           double hscale, int c0, int c1, KGrid g, KParams p, int skip) {
+                           double hscale, int c0, int c1) {
   const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= c1) return;
-  if (skip) {
-    const int i = c % g.nx, j = c / g.nx;
-    if ((i == 0 && p.bc[0] == MM_BC_DIFFUSE) || (i == g.nx - 1 && p.bc[1] == MM_BC_DIFFUSE) ||
-        (j == 0 && p.bc[2] == MM_BC_DIFFUSE) || (j == g.ny - 1 && p.bc[3] == MM_BC_DIFFUSE))
-      return;
-  }
   for (int m = 0; m < 4; ++m)
     H[m * nc + c] = hscale * ((double)Hf[(2 * m) * nc + c] + (double)Hf[(2 * m + 1) * nc + c]);
 }
@@ -130,13 +123,11 @@ void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGri
 }
 
 void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s,
-                     int c0, int c1, const KParams* skip_walls) {
+                     int c0, int c1) {
   c1 = end_of(g, c1);
   if (c1 > c0)
     k_h_unpack<<<blocks_of(c0, c1, 128), 128, 0, s>>>(Hf, H, g.nx * g.ny, eps * g.dv1 * g.dv2,
-                                                      c0, c1, g,
-                                                      skip_walls ? *skip_walls : KParams{},
-                                                      skip_walls ? 1 : 0);
+                                                      c0, c1);
 }
 
 }  // namespace mmk

@@ -380,9 +380,6 @@ template void launch_micro_x_rows<double>(const double*, double*, const double*,
 template void launch_micro_y_wall<double>(const double*, double*, double*, const double*,
                                           const int*, int, const KGrid&, const KParams&, double,
                                           double, const MicroShape&, int*, cudaStream_t, double*);
-template void launch_micro_y_wall<float>(const float*, float*, double*, const double*,
-                                         const int*, int, const KGrid&, const KParams&, double,
-                                         double, const MicroShape&, int*, cudaStream_t, double*);
 
 // FP64 pipe probe: 8 independent FMA chains per thread, so that issue, not latency, bounds it.
 __global__ void k_diag_fp64_fma(double* __restrict__ out, int iters, double a, double b) {

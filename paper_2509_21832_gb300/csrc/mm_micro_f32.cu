@@ -15,6 +15,9 @@
 //  - k_micro_flat_f32 (32^2, symmetric in v2): flat lane mapping, one warp per column, g through
 //    the read-only path;
 //  - k_micro_fused_f32 (any mesh with nv1 <= 32): lane = v1 index, one warp per column.
+// The flat-mapped sweeps update two elements per instruction (packed f32x2 arithmetic of
+// sm_100 and later).  k_wall_f32 then finishes the cells next to a diffuse wall from the G* the
+// streaming kernels export.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -450,6 +453,23 @@ struct FlatShape {
   static_assert((NV2 / 2) % ST == 0 && NV <= 1024 && NV2 % 2 == 0, "flat shape");
 };
 
+// Packed FP32 pairs: a lane updates the elements of visits t = 2u and 2u + 1 of one v1 column
+// (rows a = l0 + 2 ST u and b = a + ST) with one f32x2 instruction.  Their row factors share a
+// table slot, l0 + ST u, so that one shared load brings both.
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) {
+  return __fadd2_rn(x, make_float2(-y.x, -y.y));
+}
+
+template <int NV1, int NV2>
+__device__ __forceinline__ int pair_slot(int l, int& half) {
+  constexpr int ST = FlatShape<NV1, NV2>::ST;
+  const int r = l % (2 * ST);
+  half = r >= ST ? 1 : 0;
+  return r - half * ST + ST * (l / (2 * ST));
+}
+
 // x sweep of cell (i, j) into the ring slot dst (flat mapping).  Gc is the cell's g block, Gl and
 // Gr the blocks upwind on the left and right (the cell's own block for extrapolation and specular
 // sides, mirrored in v1 when mirl / mirr, a zero row behind a diffuse side): global memory read
@@ -459,24 +479,29 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
                                          const float* Gcb, const float* Gl, const float* Gr,
                                          bool mirl, bool mirr, float fv) {
   using S = FlatShape<NV1, NV2>;
+  constexpr int P = S::P, NU = S::M / S::P / 2, ST = S::ST;
   const KGrid& g = a.g;
   const int cell = j * g.nx + i;
   const int lane = threadIdx.x & 31;
-  float2* X1 = reinterpret_cast<float2*>(xt);  // (c2, c2^2)
-  float2* X2 = X1 + NV2;                        // (e2, projection term)
+  // per row pair: {c2_a, c2_b, c2_a^2, c2_b^2}, {e2_a, e2_b, projection term a, b}
+  float4* XP = reinterpret_cast<float4*>(xt);
   const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
   const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT), kap = field(fv, F_KAP);
   for (int l = lane; l < NV2; l += 32) {
+    int h;
+    const int p = pair_slot<NV1, NV2>(l, h);
     const float c2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
     const float q = c2 * c2;
-    X1[l] = make_float2(c2, q);
-    X2[l] = make_float2(expf(-q * inv2T), 0.f);
+    float* X = xt + 8 * p;
+    X[h] = c2;
+    X[2 + h] = q;
+    X[4 + h] = expf(-q * inv2T);
   }
-  float c1[S::P], sig[S::P], lam[S::P];
-  const float* Gu[S::P];
-  int l0[S::P], kc[S::P];
+  float c1[P], sig[P], lam[P];
+  const float* Gu[P];
+  int l0[P], kc[P];
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) {
+  for (int s = 0; s < P; ++s) {
     const int q0 = lane + 32 * s, k = q0 % NV1;
     l0[s] = q0 / NV1;
     kc[s] = k;
@@ -492,68 +517,78 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
   auto ld = [](const float* q) { return STAGED ? *q : __ldg(q); };
   __syncwarp();
   // pass 1: upwind differences, their moments and the upwind update (kept in registers)
-  float ue[S::M];
-  float D0[S::P], D1[S::P], D2[S::P];
+  float2 ue[P][NU];
+  float2 D0[P], D1[P], D2[P];
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) D0[s] = D1[s] = D2[s] = 0.f;
+  for (int s = 0; s < P; ++s) D0[s] = D1[s] = D2[s] = f2(0.f);
   {
-    float gv[S::M], gu[S::M];
+    float2 gv[P][NU], gu[P][NU];
 #pragma unroll
-    for (int m = 0; m < S::M; ++m) {
-      gv[m] = ld(Gc + 32 * m);
-      gu[m] = ld(Gu[m % S::P] + 32 * S::P * (m / S::P));
-    }
+    for (int u = 0; u < NU; ++u)
 #pragma unroll
-    for (int m = 0; m < S::M; ++m) {
-      const int s = m % S::P, t = m / S::P;
-      const float d = gu[m] - gv[m];
-      const float2 cq = X1[l0[s] + S::ST * t];
-      ue[m] = fmaf(lam[s], d, gv[m]);
-      D0[s] += d;
-      D1[s] = fmaf(cq.x, d, D1[s]);
-      D2[s] = fmaf(cq.y, d, D2[s]);
-    }
+      for (int s = 0; s < P; ++s) {
+        const int m = s + P * 2 * u;
+        gv[s][u] = f2(ld(Gc + 32 * m), ld(Gc + 32 * (m + P)));
+        gu[s][u] = f2(ld(Gu[s] + 32 * P * (2 * u)), ld(Gu[s] + 32 * P * (2 * u + 1)));
+      }
+#pragma unroll
+    for (int u = 0; u < NU; ++u)
+#pragma unroll
+      for (int s = 0; s < P; ++s) {
+        const float2 d = sub2(gu[s][u], gv[s][u]);
+        const float4 X = XP[2 * (l0[s] + ST * u)];
+        ue[s][u] = __ffma2_rn(f2(lam[s]), d, gv[s][u]);
+        D0[s] = __fadd2_rn(D0[s], d);
+        D1[s] = __ffma2_rn(f2(X.x, X.y), d, D1[s]);
+        D2[s] = __ffma2_rn(f2(X.z, X.w), d, D2[s]);
+      }
   }
   float Sx[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) {
-    const float sD0 = sig[s] * D0[s];
+  for (int s = 0; s < P; ++s) {
+    const float sD0 = sig[s] * (D0[s].x + D0[s].y);
     Sx[0] += sD0;
     Sx[1] = fmaf(c1[s], sD0, Sx[1]);
-    Sx[2] = fmaf(sig[s], D1[s], Sx[2]);
-    Sx[3] += fmaf(c1[s] * c1[s], sD0, sig[s] * D2[s]);
+    Sx[2] = fmaf(sig[s], D1[s].x + D1[s].y, Sx[2]);
+    Sx[3] += fmaf(c1[s] * c1[s], sD0, sig[s] * (D2[s].x + D2[s].y));
   }
   warp_allsum4(Sx);
   const float b0 = fmaf(-Sx[3], inv2T, 2.f * Sx[0]);
   const float b1 = Sx[1] * iT, b2 = Sx[2] * iT;
   const float gm = fmaf(0.25f * Sx[3], iT * iT, -Sx[0] * inv2T);
-  for (int l = lane; l < NV2; l += 32) {
-    const float2 cq = X1[l];
-    X2[l].y = X2[l].x * fmaf(b2, cq.x, gm * cq.y);
+  for (int p = lane; p < NV2 / 2; p += 32) {
+    const float4 X = XP[2 * p];
+    float4 E = XP[2 * p + 1];
+    E.z = E.x * fmaf(b2, X.x, gm * X.z);
+    E.w = E.y * fmaf(b2, X.y, gm * X.w);
+    XP[2 * p + 1] = E;
   }
   // kap e1 of each column: with several columns per lane, lane k evaluates column k's and the
   // owners fetch it by shuffle
-  float ak[S::P], bk[S::P];
-  if constexpr (S::P == 1) {
+  float ak[P], bk[P];
+  if constexpr (P == 1) {
     bk[0] = kap * expf(-c1[0] * c1[0] * inv2T);
   } else {
     const float ck = fmaf((lane < NV1 ? lane : 0) + 0.5f, a.gf.dv1, a.gf.v1min) - u1;
     const float bown = kap * expf(-ck * ck * inv2T);
 #pragma unroll
-    for (int s = 0; s < S::P; ++s) bk[s] = __shfl_sync(0xffffffffu, bown, kc[s]);
+    for (int s = 0; s < P; ++s) bk[s] = __shfl_sync(0xffffffffu, bown, kc[s]);
   }
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) ak[s] = bk[s] * fmaf(gm * c1[s], c1[s], fmaf(b1, c1[s], b0));
+  for (int s = 0; s < P; ++s) ak[s] = bk[s] * fmaf(gm * c1[s], c1[s], fmaf(b1, c1[s], b0));
   __syncwarp();
   // pass 2: G* = G - dt Z + dt Zhat
 #pragma unroll
-  for (int m = 0; m < S::M; ++m) {
-    const int s = m % S::P, t = m / S::P;
-    const float2 eq = X2[l0[s] + S::ST * t];
-    float o = fmaf(ak[s], eq.x, ue[m]);
-    o = fmaf(bk[s], eq.y, o);
-    dst[lane + 32 * m] = o;
-  }
+  for (int u = 0; u < NU; ++u)
+#pragma unroll
+    for (int s = 0; s < P; ++s) {
+      const float4 E = XP[2 * (l0[s] + ST * u) + 1];
+      float2 o = __ffma2_rn(f2(ak[s]), f2(E.x, E.y), ue[s][u]);
+      o = __ffma2_rn(f2(bk[s]), f2(E.z, E.w), o);
+      const int m = s + P * 2 * u;
+      dst[lane + 32 * m] = o.x;
+      dst[lane + 32 * (m + P)] = o.y;
+    }
   if (a.Gexp != nullptr && exports_gstar(g, a.p, i, j)) {
     float* Ge = a.Gexp + (size_t)cell * S::NV + lane;
 #pragma unroll
@@ -568,14 +603,14 @@ template <int NV1, int NV2>
 __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const float* rb,
                                          const float* rc, const float* rt, float* tb, float fv) {
   using S = FlatShape<NV1, NV2>;
+  constexpr int P = S::P, NU = S::M / S::P / 2, ST = S::ST;
   const KGrid& g = a.g;
   const int nc = g.nx * g.ny, cell = j * g.nx + i;
   const int lane = threadIdx.x & 31;
-  // row tables: TS = (s0, s0 c2, s0 c2^2) for the moments of Z*; TA = (wl, e2, c2, g2) and
-  // TC = (c2^2, c2^3) for the update and the heat flux
-  float4* TS = reinterpret_cast<float4*>(tb);
-  float4* TA = TS + NV2;
-  float2* TC = reinterpret_cast<float2*>(TA + NV2);
+  // per row pair (five float4): {s0_a, s0_b, s0 c2_a, s0 c2_b}, {s0 c2^2_a, s0 c2^2_b, -, -}
+  // for the moments of Z*; {wl_a, wl_b, e2_a, e2_b}, {c2_a, c2_b, g2_a, g2_b},
+  // {c2^2_a, c2^2_b, c2^3_a, c2^3_b} for the update and the heat flux
+  const float4* Y = reinterpret_cast<const float4*>(tb);
   const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
   const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT);
   const float Ti11h = field(fv, F_TI11H), Ti12 = field(fv, F_TI12), Ti22h = field(fv, F_TI22H);
@@ -585,19 +620,28 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
   const float w10 = field(fv, F_W10), w11 = field(fv, F_W11), w12 = field(fv, F_W12);
   const float w20 = field(fv, F_W20), w21 = field(fv, F_W21), w30 = field(fv, F_W30);
   for (int l = lane; l < NV2; l += 32) {
+    int h;
+    const int p = pair_slot<NV1, NV2>(l, h);
     const float v2 = fmaf(l + 0.5f, a.gf.dv2, a.gf.v2min);
     const float c2 = v2 - u2;
     const float q = c2 * c2;
     const float av = fabsf(v2);
     const float sg = -av * a.gf.idy;
-    TS[l] = make_float4(sg, sg * c2, sg * q, 0.f);
-    TA[l] = make_float4(om1 * (av * a.dtidy), expf(-q * inv2T), c2, expf(-Ti22h * q));
-    TC[l] = make_float2(q, q * c2);
+    float* T = tb + 20 * p;
+    T[h] = sg;
+    T[2 + h] = sg * c2;
+    T[4 + h] = sg * q;
+    T[8 + h] = om1 * (av * a.dtidy);
+    T[10 + h] = expf(-q * inv2T);
+    T[12 + h] = c2;
+    T[14 + h] = expf(-Ti22h * q);
+    T[16 + h] = q;
+    T[18 + h] = q * c2;
   }
-  float c1[S::P], c1q[S::P];
-  int l0[S::P], kc[S::P];
+  float c1[P], c1q[P];
+  int l0[P], kc[P];
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) {
+  for (int s = 0; s < P; ++s) {
     const int q0 = lane + 32 * s, k = q0 % NV1;
     l0[s] = q0 / NV1;
     kc[s] = k;
@@ -606,30 +650,36 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
   }
   __syncwarp();
   // pass 1: upwind differences and the moments of Z*; G* and the differences stay in registers
-  float gvr[S::M], dr[S::M];
-  float E0[S::P], E1[S::P], E2[S::P];
+  float2 gvr[P][NU], dr[P][NU];
+  float2 E0[P], E1[P], E2[P];
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) E0[s] = E1[s] = E2[s] = 0.f;
+  for (int s = 0; s < P; ++s) E0[s] = E1[s] = E2[s] = f2(0.f);
 #pragma unroll
-  for (int m = 0; m < S::M; ++m) {
-    const int s = m % S::P, t = m / S::P;
-    const float gv = rc[lane + 32 * m];
-    const float gu = (t < S::TOP ? rt : rb)[lane + 32 * m];
-    const float d = gu - gv;
-    gvr[m] = gv;
-    dr[m] = d;
-    const float4 ts = TS[l0[s] + S::ST * t];
-    E0[s] = fmaf(ts.x, d, E0[s]);
-    E1[s] = fmaf(ts.y, d, E1[s]);
-    E2[s] = fmaf(ts.z, d, E2[s]);
-  }
+  for (int u = 0; u < NU; ++u)
+#pragma unroll
+    for (int s = 0; s < P; ++s) {
+      const int m = s + P * 2 * u;
+      const float2 gv = f2(rc[lane + 32 * m], rc[lane + 32 * (m + P)]);
+      const float2 gu = f2((2 * u < S::TOP ? rt : rb)[lane + 32 * m],
+                           (2 * u + 1 < S::TOP ? rt : rb)[lane + 32 * (m + P)]);
+      const float2 d = sub2(gu, gv);
+      gvr[s][u] = gv;
+      dr[s][u] = d;
+      const int p = l0[s] + ST * u;
+      const float4 A = Y[5 * p];
+      const float4 B = Y[5 * p + 1];
+      E0[s] = __ffma2_rn(f2(A.x, A.y), d, E0[s]);
+      E1[s] = __ffma2_rn(f2(A.z, A.w), d, E1[s]);
+      E2[s] = __ffma2_rn(f2(B.x, B.y), d, E2[s]);
+    }
   float Sy[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) {
-    Sy[0] += E0[s];
-    Sy[1] = fmaf(c1[s], E0[s], Sy[1]);
-    Sy[2] += E1[s];
-    Sy[3] += fmaf(c1q[s], E0[s], E2[s]);
+  for (int s = 0; s < P; ++s) {
+    const float e0 = E0[s].x + E0[s].y;
+    Sy[0] += e0;
+    Sy[1] = fmaf(c1[s], e0, Sy[1]);
+    Sy[2] += E1[s].x + E1[s].y;
+    Sy[3] += fmaf(c1q[s], e0, E2[s].x + E2[s].y);
   }
   warp_allsum4(Sy);
   const float b0 = fmaf(-Sy[3], inv2T, 2.f * Sy[0]);
@@ -637,8 +687,8 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
   const float gm = fmaf(0.25f * Sy[3], iT * iT, -Sy[0] * inv2T);
   // per column: the polynomial coefficients of Ghat in c2 (times e1) and the ES Gaussian's
   // cross factor with its row ratio
-  float A0[S::P], A1[S::P], A2[S::P], A3[S::P], x[S::P], rat[S::P];
-  if constexpr (S::P == 1) {
+  float A0[P], A1[P], A2[P], A3[P], x[P], rat[P];
+  if constexpr (P == 1) {
     const float c = c1[0], cq = c1q[0];
     const float C0 = om1kap * fmaf(gm, cq, fmaf(b1, c, b0)) - c * fmaf(c, fmaf(c, w03, w02), w01) - ome;
     const float C1 = fmaf(om1kap, b2, -fmaf(c, fmaf(c, w12, w11), w10));
@@ -650,7 +700,7 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
     A3[0] = -e1 * w30;
     const float c2r = fmaf(l0[0] + 0.5f, a.gf.dv2, a.gf.v2min) - u2;
     x[0] = gam0 * expf(-Ti11h * cq - Ti12 * c * c2r);
-    rat[0] = expf(-Ti12 * c * (S::ST * a.gf.dv2));
+    rat[0] = expf(-Ti12 * c * (ST * a.gf.dv2));
   } else {
     // lane k evaluates column k's coefficients, the Gaussian factor at row 0 and the ratio r of
     // the cross factor between adjacent rows; the owners of column k fetch them by shuffle and
@@ -667,7 +717,7 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
     const float r1 = expf(-Ti12 * c * a.gf.dv2);
     constexpr unsigned full = 0xffffffffu;
 #pragma unroll
-    for (int s = 0; s < S::P; ++s) {
+    for (int s = 0; s < P; ++s) {
       A0[s] = __shfl_sync(full, a0, kc[s]);
       A1[s] = __shfl_sync(full, a1, kc[s]);
       A2[s] = __shfl_sync(full, a2, kc[s]);
@@ -675,7 +725,7 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
       float r = __shfl_sync(full, r1, kc[s]);
       float xs = __shfl_sync(full, x0, kc[s]);
 #pragma unroll
-      for (int b = 1; b < S::ST; b <<= 1) {
+      for (int b = 1; b < ST; b <<= 1) {
         if (l0[s] & b) xs *= r;
         r *= r;
       }
@@ -684,34 +734,46 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
     }
   }
   // pass 2: G^{n+1} = om1 G* + wl (G*_up - G*) + Ghat + gamma exp(...), and the heat flux sums
-  float H0[S::P], H1[S::P], H2[S::P], H3[S::P];
+  float2 H0[P], H1[P], H2[P], H3[P], xp[P];
+  float rat2[P];
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) H0[s] = H1[s] = H2[s] = H3[s] = 0.f;
+  for (int s = 0; s < P; ++s) {
+    H0[s] = H1[s] = H2[s] = H3[s] = f2(0.f);
+    xp[s] = f2(x[s], x[s] * rat[s]);  // the cross factor at visits 2u and 2u + 1
+    rat2[s] = rat[s] * rat[s];
+  }
   float* Go = a.Gout + (size_t)cell * S::NV + lane;
 #pragma unroll
-  for (int m = 0; m < S::M; ++m) {
-    const int s = m % S::P, t = m / S::P;
-    const int l = l0[s] + S::ST * t;
-    const float4 ta = TA[l];
-    const float2 tc = TC[l];
-    float o = fmaf(ta.x, dr[m], om1 * gvr[m]);
-    const float pc = fmaf(fmaf(fmaf(A3[s], ta.z, A2[s]), ta.z, A1[s]), ta.z, A0[s]);
-    o = fmaf(ta.y, pc, o);
-    o = fmaf(ta.w, x[s], o);
-    x[s] *= rat[s];
-    Go[32 * m] = o;
-    H0[s] += o;
-    H1[s] = fmaf(ta.z, o, H1[s]);
-    H2[s] = fmaf(tc.x, o, H2[s]);
-    H3[s] = fmaf(tc.y, o, H3[s]);
-  }
+  for (int u = 0; u < NU; ++u)
+#pragma unroll
+    for (int s = 0; s < P; ++s) {
+      const int p = l0[s] + ST * u;
+      const float4 C = Y[5 * p + 2];
+      const float4 D = Y[5 * p + 3];
+      const float4 F = Y[5 * p + 4];
+      float2 o = __ffma2_rn(f2(C.x, C.y), dr[s][u], __fmul2_rn(f2(om1), gvr[s][u]));
+      const float2 c2p = f2(D.x, D.y);
+      float2 pc = __ffma2_rn(f2(A3[s]), c2p, f2(A2[s]));
+      pc = __ffma2_rn(pc, c2p, f2(A1[s]));
+      pc = __ffma2_rn(pc, c2p, f2(A0[s]));
+      o = __ffma2_rn(f2(C.z, C.w), pc, o);
+      o = __ffma2_rn(f2(D.z, D.w), xp[s], o);
+      xp[s] = __fmul2_rn(xp[s], f2(rat2[s]));
+      const int m = s + P * 2 * u;
+      Go[32 * m] = o.x;
+      Go[32 * (m + P)] = o.y;
+      H0[s] = __fadd2_rn(H0[s], o);
+      H1[s] = __ffma2_rn(c2p, o, H1[s]);
+      H2[s] = __ffma2_rn(f2(F.x, F.y), o, H2[s]);
+      H3[s] = __ffma2_rn(f2(F.z, F.w), o, H3[s]);
+    }
   float Hs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int s = 0; s < S::P; ++s) {
-    Hs[0] = fmaf(c1q[s] * c1[s], H0[s], Hs[0]);
-    Hs[1] = fmaf(c1q[s], H1[s], Hs[1]);
-    Hs[2] = fmaf(c1[s], H2[s], Hs[2]);
-    Hs[3] += H3[s];
+  for (int s = 0; s < P; ++s) {
+    Hs[0] = fmaf(c1q[s] * c1[s], H0[s].x + H0[s].y, Hs[0]);
+    Hs[1] = fmaf(c1q[s], H1[s].x + H1[s].y, Hs[1]);
+    Hs[2] = fmaf(c1[s], H2[s].x + H2[s].y, Hs[2]);
+    Hs[3] += H3[s].x + H3[s].y;
   }
   warp_allsum4(Hs);
   if (lane < 8) a.Hf[lane * nc + cell] = (lane & 1) ? 0.f : Hs[lane >> 1];
@@ -1055,9 +1117,274 @@ static FusedPick pick_fused(const KGrid& g) {
   return FusedPick{k_micro_fused_f32<0, 0>, smem};
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Diffuse-wall cells of the FP32-g step (Section 6.3): the y sweep, the relaxation toward the
+// wall form of Ghat, -(1/tau)(I - Pi_M)[upwind v.grad M] with ghost wall Maxwellians (plus
+// (G - M)/eps when kept), and the heat flux, from the G* the streaming kernel exported.  One CTA
+// per wall cell.  The per-cell quantities (wall densities with their error functions, the
+// Maxwellian prefactors) are FP64, rounded once; the per-velocity arithmetic is FP32, as in the
+// streaming kernel, since FP64 runs at 1/64 of the FP32 rate on this GPU.
+// ------------------------------------------------------------------------------------------
+constexpr int kWallThreadsF = 128;
+
+// Sum N floats over the CTA (kWallThreadsF threads, fixed order); every thread gets the totals.
+template <int N>
+__device__ __forceinline__ void cta_sum(float (&v)[N], float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < N; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+  if (lane == 0)
+#pragma unroll
+    for (int m = 0; m < N; ++m) red[w * N + m] = v[m];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    float s = red[m];
+    for (int q = 1; q < kWallThreadsF / 32; ++q) s += red[q * N + m];
+    v[m] = s;
+  }
+  __syncthreads();
+}
+
+// Eq. (twodim_wall_densities_1): the ghost density factor of a diffuse wall for the normal
+// velocity ua and normal temperature Taa of the cell, wall temperature Tw.
+__device__ __forceinline__ double wall_density_factor(double ua, double Taa, double Tw,
+                                                      double sgn) {
+  constexpr double kPiD = 3.14159265358979323846;
+  return sqrt(Taa / Tw) * exp(-ua * ua / (2.0 * Taa)) +
+         ua * sqrt(kPiD / (2.0 * Tw)) * (erf(ua / sqrt(2.0 * Taa)) + sgn);
+}
+
+__global__ void __launch_bounds__(kWallThreadsF) k_wall_f32(const float* __restrict__ Gs,
+                                                            float* __restrict__ Gout,
+                                                            double* __restrict__ Hout,
+                                                            const double* __restrict__ prim,
+                                                            const int* __restrict__ wall_cells,
+                                                            KGrid g, KParams p, double dt,
+                                                            double eps, int* __restrict__ err) {
+  extern __shared__ __align__(16) float sw[];
+  const int nv1 = g.nv1, nv2 = g.nv2, nv = nv1 * nv2;
+  float* Xt = sw;              // [5][nv1]: v1 factors of the four side Maxwellians and the cell's
+  float* Yt = Xt + 5 * nv1;    // [5][nv2]: v2 factors
+  float* Et = Yt + 5 * nv2;    // [nv2]: row factor of the ES Gaussian
+  float* red = Et + nv2;       // reduction scratch
+  __shared__ float sf[5][4];   // (u1, u2, 1 / (2 T), rho / (2 pi T)) of the five Maxwellians
+  __shared__ float cs[13];     // per-cell scalars, rounded once
+  __shared__ int kind[4];      // 0 neighbour / periodic, 1 extrapolation, 2 specular, 3 diffuse
+  const int cell = wall_cells[blockIdx.x];
+  const int nc = g.nx * g.ny, i = cell % g.nx, j = cell / g.nx, t = threadIdx.x;
+  constexpr double kInv2Pi = 0.15915494309189533577;  // 1 / (2 pi)
+  // FP64 work of the cell on the first warp only: lanes 0..3 the four sides' Maxwellians (the
+  // neighbour's, or the wall's with its density factor), lane 4 the cell's, lane 0 the scalars
+  if (t < 32) {
+    const double rho = prim[P_RHO * nc + cell], u1 = prim[P_U1 * nc + cell];
+    const double u2 = prim[P_U2 * nc + cell], T = prim[P_T * nc + cell];
+    double q0 = u1, q1 = u2, q2 = T, q3 = rho;
+    int kd = 0;
+    if (t < 4) {
+      const int s = t;
+      int ni = i + (s == 0 ? -1 : s == 1 ? 1 : 0);
+      int nj = j + (s == 2 ? -1 : s == 3 ? 1 : 0);
+      bool inside = ni >= 0 && ni < g.nx && nj >= 0 && nj < g.ny;
+      if (!inside && p.bc[s] == MM_BC_PERIODIC) {
+        ni = (ni + g.nx) % g.nx;
+        nj = (nj + g.ny) % g.ny;
+        inside = true;
+      }
+      if (inside) {
+        const int c = nj * g.nx + ni;
+        q0 = prim[P_U1 * nc + c];
+        q1 = prim[P_U2 * nc + c];
+        q2 = prim[P_T * nc + c];
+        q3 = prim[P_RHO * nc + c];
+      } else if (p.bc[s] == MM_BC_EXTRAP) {
+        kd = 1;
+      } else if (p.bc[s] == MM_BC_SPECULAR) {
+        kd = 2;
+      } else {
+        kd = 3;
+        const double Tw = p.wall_T[s], U = p.wall_U[s];
+        const double sgn = (s == 0 || s == 2) ? -1.0 : 1.0;
+        q3 = s < 2 ? rho * wall_density_factor(u1, prim[P_TH11 * nc + cell], Tw, sgn)
+                   : rho * wall_density_factor(u2, prim[P_TH22 * nc + cell], Tw, sgn);
+        q0 = s < 2 ? 0.0 : U;
+        q1 = s < 2 ? U : 0.0;
+        q2 = Tw;
+      }
+      kind[s] = kd;
+    }
+    if (t < 5) {
+      const double iq = 1.0 / q2;
+      sf[t][0] = (float)q0;
+      sf[t][1] = (float)q1;
+      sf[t][2] = (float)(0.5 * iq);
+      sf[t][3] = (float)(q3 * iq * kInv2Pi);
+    }
+    if (t == 0) {
+      const double tau = prim[P_TAU * nc + cell];
+      const double r = 1.0 / (eps + dt * tau), iT = 1.0 / T;
+      cs[0] = (float)(eps * r);       // om1
+      cs[1] = (float)(dt * tau * r);  // om2
+      cs[2] = (float)(1.0 / tau);
+      cs[3] = (float)(1.0 / eps);
+      cs[4] = (float)(0.5 * iT);
+      cs[5] = (float)iT;
+      cs[6] = (float)(g.dv1 * g.dv2 * kInv2Pi * iT);  // kap
+      cs[7] = (float)prim[P_KG * nc + cell];
+      cs[8] = (float)prim[P_TI11 * nc + cell];
+      cs[9] = (float)prim[P_TI12 * nc + cell];
+      cs[10] = (float)prim[P_TI22 * nc + cell];
+      cs[11] = (float)u1;
+      cs[12] = (float)u2;
+    }
+  }
+  __syncthreads();
+  const float v1min = (float)g.v1min, dv1 = (float)g.dv1;
+  const float v2min = (float)g.v2min, dv2 = (float)g.dv2;
+  for (int e = t; e < 5 * nv1; e += kWallThreadsF) {
+    const int q = e / nv1;
+    const float d = fmaf(e % nv1 + 0.5f, dv1, v1min) - sf[q][0];
+    Xt[e] = expf(-d * d * sf[q][2]);
+  }
+  for (int e = t; e < 5 * nv2; e += kWallThreadsF) {
+    const int q = e / nv2;
+    const float d = fmaf(e % nv2 + 0.5f, dv2, v2min) - sf[q][1];
+    Yt[e] = expf(-d * d * sf[q][2]);
+  }
+  const float om1 = cs[0], om2 = cs[1], itau = cs[2], ieps = cs[3];
+  const float inv2T = cs[4], iT = cs[5], kap = cs[6], KG = cs[7];
+  const float Ti11 = cs[8], Ti12 = cs[9], Ti22 = cs[10], u1f = cs[11], u2f = cs[12];
+  if (p.keep_es)
+    for (int l = t; l < nv2; l += kWallThreadsF) {
+      const float c2 = fmaf(l + 0.5f, dv2, v2min) - u2f;
+      Et[l] = expf(-0.5f * Ti22 * c2 * c2);
+    }
+  __syncthreads();
+
+  const float idx = (float)g.idx, idy = (float)g.idy;
+  int kd[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) kd[s] = kind[s];
+  const float pf4 = sf[4][3];
+  // the Maxwellian of side s at (k, l), for the upwind v.grad M (m0: the cell's own)
+  auto side_m = [&](int s, float m0, int k, int l) -> float {
+    if (kd[s] == 1) return m0;
+    if (kd[s] == 2)
+      return s < 2 ? pf4 * Xt[4 * nv1 + nv1 - 1 - k] * Yt[4 * nv2 + l]
+                   : pf4 * Xt[4 * nv1 + k] * Yt[4 * nv2 + nv2 - 1 - l];
+    return sf[s][3] * Xt[s * nv1 + k] * Yt[s * nv2 + l];
+  };
+  auto mup = [&](int k, int l, float v1, float v2, float m0) -> float {
+    float z = 0.f;
+    if (v1 > 0.f) z += v1 * ((m0 - side_m(0, m0, k, l)) * idx);
+    if (v1 < 0.f) z += v1 * ((side_m(1, m0, k, l) - m0) * idx);
+    if (v2 > 0.f) z += v2 * ((m0 - side_m(2, m0, k, l)) * idy);
+    if (v2 < 0.f) z += v2 * ((side_m(3, m0, k, l) - m0) * idy);
+    return z;
+  };
+  const UpwindF ub = upwind_side(g, p, i, j, 2), ut = upwind_side(g, p, i, j, 3);
+  const float* Gc = Gs + (size_t)cell * nv;
+  const float* Gb = Gs + (size_t)ub.cell * nv;
+  const float* Gt = Gs + (size_t)ut.cell * nv;
+  // G*, its upwind y difference term z = -|v2| (G*_up - G*) / dy and the cell's Maxwellian at
+  // element e = l nv1 + k
+  auto element = [&](int e, int& k, int& l, float& v1, float& v2, float& gv, float& z,
+                     float& ml) {
+    k = e % nv1;
+    l = e / nv1;
+    v1 = fmaf(k + 0.5f, dv1, v1min);
+    v2 = fmaf(l + 0.5f, dv2, v2min);
+    gv = Gc[e];
+    const bool top = v2 < 0.f;
+    const UpwindF& u = top ? ut : ub;
+    const int lu = u.mirror ? nv2 - 1 - l : l;
+    const float gu = u.zero ? 0.f : (top ? Gt : Gb)[lu * nv1 + k];
+    z = -fabsf(v2) * idy * (gu - gv);
+    ml = Xt[4 * nv1 + k] * Yt[4 * nv2 + l];  // M / (rho / (2 pi T))
+  };
+  // pass 1: moments (1, c1, c2, |c|^2) of Z* and of the upwind v.grad M
+  float S[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int e = t; e < nv; e += kWallThreadsF) {
+    int k, l;
+    float v1, v2, gv, z, ml;
+    element(e, k, l, v1, v2, gv, z, ml);
+    const float c1 = v1 - u1f, c2 = v2 - u2f, cc = fmaf(c1, c1, c2 * c2);
+    const float mz = mup(k, l, v1, v2, pf4 * ml);
+    S[0] += z;
+    S[1] = fmaf(c1, z, S[1]);
+    S[2] = fmaf(c2, z, S[2]);
+    S[3] = fmaf(cc, z, S[3]);
+    S[4] += mz;
+    S[5] = fmaf(c1, mz, S[5]);
+    S[6] = fmaf(c2, mz, S[6]);
+    S[7] = fmaf(cc, mz, S[7]);
+  }
+  cta_sum<8>(S, red);
+  // projection polynomials kap (b0 + b1 c1 + b2 c2 + gm |c|^2) of Z* (S[0..3]) and of v.grad M
+  // (S[4..7])
+  float B[2][4];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float* m4 = S + 4 * q;
+    B[q][0] = kap * fmaf(-m4[3], inv2T, 2.f * m4[0]);
+    B[q][1] = kap * (m4[1] * iT);
+    B[q][2] = kap * (m4[2] * iT);
+    B[q][3] = kap * fmaf(0.25f * m4[3], iT * iT, -m4[0] * inv2T);
+  }
+  const float dtf = (float)dt;
+  // pass 2: G^{n+1} = om1 G** + om2 Ghat with G** = G* + dt (Pi_M Z* - Z*), and the heat flux
+  float Hs[4] = {0.f, 0.f, 0.f, 0.f};
+  float* Go = Gout + (size_t)cell * nv;
+  for (int e = t; e < nv; e += kWallThreadsF) {
+    int k, l;
+    float v1, v2, gv, z, ml;
+    element(e, k, l, v1, v2, gv, z, ml);
+    const float c1 = v1 - u1f, c2 = v2 - u2f;
+    const float c1q = c1 * c1, cq = fmaf(c2, c2, c1q);
+    const float ps = fmaf(B[0][3], cq, fmaf(B[0][2], c2, fmaf(B[0][1], c1, B[0][0])));
+    const float pw = fmaf(B[1][3], cq, fmaf(B[1][2], c2, fmaf(B[1][1], c1, B[1][0])));
+    const float m = pf4 * ml;
+    const float gs2 = fmaf(dtf, fmaf(ps, ml, -z), gv);
+    float gh = -itau * (mup(k, l, v1, v2, m) - pw * ml);
+    if (p.keep_es)
+      gh = fmaf(fmaf(KG * expf(fmaf(-0.5f * Ti11, c1q, -Ti12 * c1 * c2)), Et[l], -m), ieps, gh);
+    const float o = fmaf(om1, gs2, om2 * gh);
+    Go[e] = o;
+    Hs[0] = fmaf(c1q * c1, o, Hs[0]);
+    Hs[1] = fmaf(c1q * c2, o, Hs[1]);
+    Hs[2] = fmaf(c1 * (c2 * c2), o, Hs[2]);
+    Hs[3] = fmaf(c2 * (c2 * c2), o, Hs[3]);
+  }
+  cta_sum<4>(Hs, red);
+  if (t == 0) {
+    const double f = eps * g.dv1 * g.dv2;
+    bool ok = true;
+    for (int m = 0; m < 4; ++m) {
+      Hout[m * nc + cell] = f * (double)Hs[m];
+      ok = ok && isfinite(Hs[m]);
+    }
+    if (!ok) atomicOr(err, ERR_NONFINITE_G);
+  }
+}
+
 }  // namespace
 
 size_t fused_smem_f32(const KGrid& g) { return pick_fused(g).smem; }
+
+size_t wall_smem_f32(const KGrid& g) {
+  return sizeof(float) * (5 * (size_t)g.nv1 + 6 * (size_t)g.nv2 + 8 * (kWallThreadsF / 32));
+}
+
+void launch_wall_f32(const float* Gs, float* Gout, double* H, const double* prim,
+                     const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
+                     double dt, double eps, int* err, cudaStream_t s) {
+  if (n_wall <= 0) return;
+  k_wall_f32<<<n_wall, kWallThreadsF, wall_smem_f32(g), s>>>(Gs, Gout, H, prim, wall_cells, g, p,
+                                                            dt, eps, err);
+}
 
 KGridF grid_f32(const KGrid& g) {
   return KGridF{(float)g.v1min, (float)g.v2min, (float)g.dv1, (float)g.dv2, (float)g.idx,

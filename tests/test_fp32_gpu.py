@@ -49,6 +49,11 @@ CASES = [
      (I.PERIODIC, I.PERIODIC, I.DIFFUSE, I.DIFFUSE), dict(wall_T=(1.0, 1.0, 1.1, 0.9))),
     ("walls_y_segments_16", dict(nx=12, ny=50, nv1=16, nv2=16),
      (I.EXTRAP, I.SPECULAR, I.DIFFUSE, I.DIFFUSE), dict(wall_T=(1.0, 1.0, 1.2, 1.0))),
+    # moving diffuse walls at the left and bottom (a corner cell with two wall ghosts), the
+    # literal wall form of Ghat (no (G - M)/eps term)
+    ("walls_literal_24", dict(nx=10, ny=8, nv1=24, nv2=24),
+     (I.DIFFUSE, I.EXTRAP, I.DIFFUSE, I.SPECULAR),
+     dict(wall_T=(1.1, 1.0, 0.9, 1.0), wall_U=(0.1, 0.0, -0.2, 0.0), wall_keep_es_term=0)),
     # v2 mesh not symmetric about zero: the column-mapped kernel of the 24^2 shape
     ("asym_24", dict(nx=8, ny=9, nv1=24, nv2=24, v2min=-7.0, v2max=9.0),
      (I.EXTRAP, I.EXTRAP, I.PERIODIC, I.PERIODIC), {}),
