@@ -255,7 +255,15 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
   const KParams& p = c->kp;
   cudaStream_t s = c->stream;
   bool x1_side = false;
-  enqueue_prims(c, dt, eps, s);
+  if constexpr (sizeof(Tg) == sizeof(float)) {
+    // (u1, u2, T) in FP64, then the FP32 coefficients of the phase-space kernels
+    timed(c, T_PRIMS_UT, [&] { launch_prims_uT(c->Q, c->prim, c->kg, s); });
+    timed(c, T_PRIMS, [&] {
+      launch_prims_f32(c->Q, c->prim, c->primf, c->kg, c->kp, dt, eps, c->err, s);
+    });
+  } else {
+    enqueue_prims(c, dt, eps, s);
+  }
   if constexpr (sizeof(Tg) == sizeof(float)) {
     // macro x1 (collision half step and x half fluxes of Q^n) beside the phase-space kernel:
     // forked after the per-cell fields, so that it runs with the FP32 kernel rather than against
@@ -304,8 +312,8 @@ void enqueue_plain(mm_ctx* c, double dt, double eps) {
     timed(c, T_HUNPACK, [&] { launch_h_unpack(c->Hf, c->H, g, eps, s); });
     if (c->n_wall > 0)
       timed(c, T_MICRO_YW, [&] {
-        launch_wall_f32(Ge, Gs, c->H, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps, c->err,
-                        s);
+        launch_wall_f32(Ge, Gs, c->H, c->Q, c->prim, c->wall_cells, c->n_wall, g, p, dt, eps,
+                        c->err, s);
       });
     std::swap(c->G, c->Gs);
   } else {

@@ -349,6 +349,73 @@ __device__ __forceinline__ void prims_body(const double* MMK_R Q, double* MMK_R 
   }
 }
 
+// The FP32 coefficients of cell c for the FP32-g phase-space kernels, the same quantities as
+// prims_body's primf (neighbours' (u1, u2, T) from uT_body): FP64 where the values decide the
+// validity check or come from differences of nearby values (moments to pressure, ES tensor and
+// its determinant, the centred strain and temperature gradient), FP32 from there on, since
+// every result is rounded to FP32 anyway.  No FP64 per-cell field is written besides uT_body's.
+__device__ __forceinline__ void prims_f32_body(const double* MMK_R Q, const double* MMK_R prim,
+                                               float* MMK_R primf, KGrid g, KParams p, double dt,
+                                               double eps, int* MMK_R err, int c) {
+  const int nc = g.nx * g.ny;
+  const int i = c % g.nx, j = c / g.nx;
+  const double rho = Q[c];
+  const double ir = 1.0 / rho;
+  const double u1 = prim[P_U1 * nc + c], u2 = prim[P_U2 * nc + c], T = prim[P_T * nc + c];
+  const double P11 = Q[3 * nc + c] - rho * u1 * u1;
+  const double P12 = Q[4 * nc + c] - rho * u1 * u2;
+  const double P22 = Q[5 * nc + c] - rho * u2 * u2;
+  const double nu = p.nu;
+  const double t11 = P11 * ir, t12 = P12 * ir, t22 = P22 * ir;
+  const double s11 = (1.0 - nu) * T + nu * t11;
+  const double s12 = nu * t12;
+  const double s22 = (1.0 - nu) * T + nu * t22;
+  const double det = s11 * s22 - s12 * s12;
+  const bool ok = rho > 0.0 && P11 > 0.0 && P22 > 0.0 && t11 * t22 - t12 * t12 > 0.0 &&
+                  det > 0.0 && T > 0.0 && isfinite(u1) && isfinite(u2) && isfinite(P12) &&
+                  isfinite(T);
+  if (!ok) atomicOr(err, ERR_NONPHYS_PRIM);
+  double uL1, uL2, TL, uR1, uR2, TR, uB1, uB2, TB, uT1, uT2, TT;
+  side_uT<true>(Q, prim, g, p, nc, i, j, 0, u1, u2, T, uL1, uL2, TL);
+  side_uT<true>(Q, prim, g, p, nc, i, j, 1, u1, u2, T, uR1, uR2, TR);
+  side_uT<true>(Q, prim, g, p, nc, i, j, 2, u1, u2, T, uB1, uB2, TB);
+  side_uT<true>(Q, prim, g, p, nc, i, j, 3, u1, u2, T, uT1, uT2, TT);
+  const float dTdx = (float)((0.5 * (TR + T) - 0.5 * (T + TL)) * g.idx);
+  const float dTdy = (float)((0.5 * (TT + T) - 0.5 * (T + TB)) * g.idy);
+  const float sg11 = (float)((uR1 - uL1) * 0.5 * g.idx - (uT2 - uB2) * 0.5 * g.idy);
+  const float sg12 = (float)((uT1 - uB1) * 0.5 * g.idy + (uR2 - uL2) * 0.5 * g.idx);
+  // FP32 from here
+  const float Tf = (float)T, rhof = (float)rho, idet = 1.0f / (float)det;
+  const float tau = (float)tau_of(p, rho, T);
+  const float KG = rhof * (float)kInv2Pi * rsqrtf((float)det);
+  const float iT = 1.0f / Tf;
+  const float kap = (float)(dt * g.dv1 * g.dv2 * kInv2Pi) * iT;
+  const float dtf = (float)dt, epsf = (float)eps;
+  const float iden = 1.0f / fmaf(dtf, tau, epsf);
+  const float om1 = epsf * iden;
+  const float om2 = dtf * tau * iden;
+  const float mu = rhof * (float)kInv2Pi * iT;
+  const float wt = dtf * iden * mu;
+  const float h2T2 = 0.5f * iT * iT;
+  const float ieps = 1.0f / epsf;
+  const float w[9] = {wt * (-2.0f * dTdx * iT), wt * (0.5f * sg11 * iT), wt * (h2T2 * dTdx),
+                      wt * (-2.0f * dTdy * iT), wt * (sg12 * iT),        wt * (h2T2 * dTdy),
+                      wt * (-0.5f * sg11 * iT), wt * (h2T2 * dTdx),      wt * (h2T2 * dTdy)};
+  primf[F_U1 * nc + c] = (float)u1;
+  primf[F_U2 * nc + c] = (float)u2;
+  primf[F_INV2T * nc + c] = 0.5f * iT;
+  primf[F_IT * nc + c] = iT;
+  primf[F_KAP * nc + c] = kap;
+  primf[F_OM1 * nc + c] = om1;
+  primf[F_OM1KAP * nc + c] = om1 * kap;
+  primf[F_GAM0 * nc + c] = om2 * ieps * KG;
+  primf[F_OME * nc + c] = om2 * mu * ieps;
+  primf[F_TI11H * nc + c] = 0.5f * (float)s22 * idet;
+  primf[F_TI12 * nc + c] = -(float)s12 * idet;
+  primf[F_TI22H * nc + c] = 0.5f * (float)s11 * idet;
+  for (int m = 0; m < 9; ++m) primf[(F_W01 + m) * nc + c] = w[m];
+}
+
 // Flux through the boundary face on side s of boundary cell state qc, given that cell's own
 // half fluxes (Fp, Fm) and full flux K along the face normal.
 __device__ __forceinline__ void boundary_face(const KParams& p, const double qc[6], int s,

@@ -75,6 +75,10 @@ MicroShape micro_shape(int nv1, int nv2);
 // launch_prims the rest (it reads the neighbours' (u1, u2, T) there): always in this order.
 void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s, int c0 = 0,
                      int c1 = -1);
+// The FP32 coefficients of every cell for the FP32-g kernels (after launch_prims_uT; writes no
+// other FP64 field).
+void launch_prims_f32(const double* Q, const double* prim, float* primf, const KGrid& g,
+                      const KParams& p, double dt, double eps, int* err, cudaStream_t s);
 // Q [6][nc] from primitive fields P4 [4][nc] = (rho, u1, u2, T), isotropic temperature tensor
 void launch_q_from_prim(const double* P4, double* Q, int nc, cudaStream_t s);
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
@@ -114,10 +118,10 @@ void launch_micro_y_wall(const Tg* Gs, Tg* Gout, double* H, const double* prim,
                          double* Rm = nullptr);
 // Diffuse-wall cells of the FP32-g step from the G* the fused kernel exported (Gs): G^{n+1} of
 // those cells into Gout and their heat flux into H (FP64); one CTA per cell, per-velocity
-// arithmetic in FP32.
-void launch_wall_f32(const float* Gs, float* Gout, double* H, const double* prim,
-                     const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
-                     double dt, double eps, int* err, cudaStream_t s);
+// arithmetic in FP32.  Reads Q^n and the (u1, u2, T) fields of launch_prims_uT.
+void launch_wall_f32(const float* Gs, float* Gout, double* H, const double* Q,
+                     const double* prim, const int* wall_cells, int n_wall, const KGrid& g,
+                     const KParams& p, double dt, double eps, int* err, cudaStream_t s);
 // Fused FP32-g micro step (x sweep, y sweep, relaxation, heat flux) streaming over column
 // segments: reads Gin once and writes Gout (a different buffer); cells next to a diffuse wall are
 // left to the wall kernel, which reads the G* this kernel exports to Gexp.  One warp per cell

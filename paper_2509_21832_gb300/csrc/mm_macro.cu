@@ -31,6 +31,13 @@ __global__ void k_prims(const double* __restrict__ Q, double* __restrict__ prim,
   if (c < c1) prims_body<true>(Q, prim, primf, g, p, dt, eps, ieps, err, c);
 }
 
+__global__ void k_prims_f32(const double* __restrict__ Q, const double* __restrict__ prim,
+                            float* __restrict__ primf, KGrid g, KParams p, double dt, double eps,
+                            int* __restrict__ err, int c0, int c1) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < c1) prims_f32_body(Q, prim, primf, g, p, dt, eps, err, c);
+}
+
 __global__ void k_macro_x1(const double* __restrict__ Qn, MacroBufs mb, KGrid g, KParams p,
                            double dt, double eps, int* __restrict__ err, int c0, int c1) {
   const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -92,6 +99,13 @@ void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, c
 
 void launch_q_from_prim(const double* P4, double* Q, int nc, cudaStream_t s) {
   if (nc > 0) k_q_from_prim<<<std::min((nc + 255) / 256, 152 * 8), 256, 0, s>>>(P4, Q, nc);
+}
+
+void launch_prims_f32(const double* Q, const double* prim, float* primf, const KGrid& g,
+                      const KParams& p, double dt, double eps, int* err, cudaStream_t s) {
+  const int c1 = end_of(g, -1);
+  if (c1 > 0)
+    k_prims_f32<<<blocks_of(0, c1, 128), 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, err, 0, c1);
 }
 
 void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s, int c0,

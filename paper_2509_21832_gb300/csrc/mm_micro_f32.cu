@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "mm_body_macro.cuh"
 #include "mm_internal.cuh"
 
 namespace mmk {
@@ -1161,6 +1162,7 @@ __device__ __forceinline__ double wall_density_factor(double ua, double Taa, dou
 __global__ void __launch_bounds__(kWallThreadsF) k_wall_f32(const float* __restrict__ Gs,
                                                             float* __restrict__ Gout,
                                                             double* __restrict__ Hout,
+                                                            const double* __restrict__ Q,
                                                             const double* __restrict__ prim,
                                                             const int* __restrict__ wall_cells,
                                                             KGrid g, KParams p, double dt,
@@ -1180,8 +1182,13 @@ __global__ void __launch_bounds__(kWallThreadsF) k_wall_f32(const float* __restr
   // FP64 work of the cell on the first warp only: lanes 0..3 the four sides' Maxwellians (the
   // neighbour's, or the wall's with its density factor), lane 4 the cell's, lane 0 the scalars
   if (t < 32) {
-    const double rho = prim[P_RHO * nc + cell], u1 = prim[P_U1 * nc + cell];
+    // the cell's moments; (u1, u2, T) of every cell from the fields kernel
+    const double rho = Q[cell], u1 = prim[P_U1 * nc + cell];
     const double u2 = prim[P_U2 * nc + cell], T = prim[P_T * nc + cell];
+    const double ir = 1.0 / rho;
+    const double P11 = Q[3 * nc + cell] - rho * u1 * u1;
+    const double P12 = Q[4 * nc + cell] - rho * u1 * u2;
+    const double P22 = Q[5 * nc + cell] - rho * u2 * u2;
     double q0 = u1, q1 = u2, q2 = T, q3 = rho;
     int kd = 0;
     if (t < 4) {
@@ -1199,7 +1206,7 @@ __global__ void __launch_bounds__(kWallThreadsF) k_wall_f32(const float* __restr
         q0 = prim[P_U1 * nc + c];
         q1 = prim[P_U2 * nc + c];
         q2 = prim[P_T * nc + c];
-        q3 = prim[P_RHO * nc + c];
+        q3 = Q[c];
       } else if (p.bc[s] == MM_BC_EXTRAP) {
         kd = 1;
       } else if (p.bc[s] == MM_BC_SPECULAR) {
@@ -1208,8 +1215,8 @@ __global__ void __launch_bounds__(kWallThreadsF) k_wall_f32(const float* __restr
         kd = 3;
         const double Tw = p.wall_T[s], U = p.wall_U[s];
         const double sgn = (s == 0 || s == 2) ? -1.0 : 1.0;
-        q3 = s < 2 ? rho * wall_density_factor(u1, prim[P_TH11 * nc + cell], Tw, sgn)
-                   : rho * wall_density_factor(u2, prim[P_TH22 * nc + cell], Tw, sgn);
+        q3 = s < 2 ? rho * wall_density_factor(u1, P11 * ir, Tw, sgn)
+                   : rho * wall_density_factor(u2, P22 * ir, Tw, sgn);
         q0 = s < 2 ? 0.0 : U;
         q1 = s < 2 ? U : 0.0;
         q2 = Tw;
@@ -1224,7 +1231,12 @@ __global__ void __launch_bounds__(kWallThreadsF) k_wall_f32(const float* __restr
       sf[t][3] = (float)(q3 * iq * kInv2Pi);
     }
     if (t == 0) {
-      const double tau = prim[P_TAU * nc + cell];
+      // tau, and the inverse and normalisation of the ES tensor (Eq. 2-19)
+      const double tau = macro_body::tau_of(p, rho, T);
+      const double nu = p.nu;
+      const double s11 = (1.0 - nu) * T + nu * (P11 * ir), s12 = nu * (P12 * ir);
+      const double s22 = (1.0 - nu) * T + nu * (P22 * ir);
+      const double det = s11 * s22 - s12 * s12, idet = 1.0 / det;
       const double r = 1.0 / (eps + dt * tau), iT = 1.0 / T;
       cs[0] = (float)(eps * r);       // om1
       cs[1] = (float)(dt * tau * r);  // om2
@@ -1233,10 +1245,10 @@ __global__ void __launch_bounds__(kWallThreadsF) k_wall_f32(const float* __restr
       cs[4] = (float)(0.5 * iT);
       cs[5] = (float)iT;
       cs[6] = (float)(g.dv1 * g.dv2 * kInv2Pi * iT);  // kap
-      cs[7] = (float)prim[P_KG * nc + cell];
-      cs[8] = (float)prim[P_TI11 * nc + cell];
-      cs[9] = (float)prim[P_TI12 * nc + cell];
-      cs[10] = (float)prim[P_TI22 * nc + cell];
+      cs[7] = (float)(rho * kInv2Pi * rsqrt(det));  // KG
+      cs[8] = (float)(s22 * idet);                   // Ti11
+      cs[9] = (float)(-s12 * idet);                  // Ti12
+      cs[10] = (float)(s11 * idet);                  // Ti22
       cs[11] = (float)u1;
       cs[12] = (float)u2;
     }
@@ -1378,12 +1390,12 @@ size_t wall_smem_f32(const KGrid& g) {
   return sizeof(float) * (5 * (size_t)g.nv1 + 6 * (size_t)g.nv2 + 8 * (kWallThreadsF / 32));
 }
 
-void launch_wall_f32(const float* Gs, float* Gout, double* H, const double* prim,
-                     const int* wall_cells, int n_wall, const KGrid& g, const KParams& p,
-                     double dt, double eps, int* err, cudaStream_t s) {
+void launch_wall_f32(const float* Gs, float* Gout, double* H, const double* Q,
+                     const double* prim, const int* wall_cells, int n_wall, const KGrid& g,
+                     const KParams& p, double dt, double eps, int* err, cudaStream_t s) {
   if (n_wall <= 0) return;
-  k_wall_f32<<<n_wall, kWallThreadsF, wall_smem_f32(g), s>>>(Gs, Gout, H, prim, wall_cells, g, p,
-                                                            dt, eps, err);
+  k_wall_f32<<<n_wall, kWallThreadsF, wall_smem_f32(g), s>>>(Gs, Gout, H, Q, prim, wall_cells, g,
+                                                            p, dt, eps, err);
 }
 
 KGridF grid_f32(const KGrid& g) {
