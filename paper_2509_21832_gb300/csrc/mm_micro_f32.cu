@@ -907,7 +907,9 @@ struct StagedShape {
   static constexpr int W = kFusedWarps;
   static constexpr int STAGE = (W + 2) * S::NV;  // floats: the g blocks of columns i0-1 .. i0+W
   static constexpr int RING = 3 * S::NV;          // per warp
-  static constexpr int TABLES = 14 * NV2;         // per warp
+  // per warp: the x sweep's tables (4 NV2 floats) and the y sweep's (10 NV2) share one area; a
+  // warp's sweeps run one after the other with a warp barrier between them
+  static constexpr int TABLES = 10 * NV2;
   static constexpr int FLOATS = STAGE + W * (RING + TABLES) + 6;  // + two mbarriers, a flag
 };
 
@@ -939,7 +941,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   float* stage = smf;
   float* ring = smf + T::STAGE + w * (T::RING + T::TABLES);
   float* xt = ring + T::RING;
-  float* yt = xt + 4 * NV2;
+  float* yt = xt;
   // full: the stage holds the next row (the bulk copies' bytes have landed); empty: every warp
   // has finished reading the stage, so that it may be refilled
   float* bars = smf + T::STAGE + W * (T::RING + T::TABLES);
