@@ -350,10 +350,11 @@ __device__ __forceinline__ void prims_body(const double* MMK_R Q, double* MMK_R 
 }
 
 // The FP32 coefficients of cell c for the FP32-g phase-space kernels, the same quantities as
-// prims_body's primf (neighbours' (u1, u2, T) from uT_body): FP64 where the values decide the
-// validity check or come from differences of nearby values (moments to pressure, ES tensor and
-// its determinant, the centred strain and temperature gradient), FP32 from there on, since
-// every result is rounded to FP32 anyway.  No FP64 per-cell field is written besides uT_body's.
+// prims_body's primf (neighbours' (u1, u2, T) from uT_body).  FP64, rounded once: the pressure,
+// the ES tensor with its determinant, inverse and normalisation, 1/T and the projector scale, and
+// the centred strain and temperature differences (the validity check and cancellation need it).
+// FP32: the relaxation weights and the coefficients of the transport term, products of those
+// rounded values.  No FP64 per-cell field is written besides uT_body's.
 __device__ __forceinline__ void prims_f32_body(const double* MMK_R Q, const double* MMK_R prim,
                                                float* MMK_R primf, KGrid g, KParams p, double dt,
                                                double eps, int* MMK_R err, int c) {
@@ -384,13 +385,13 @@ __device__ __forceinline__ void prims_f32_body(const double* MMK_R Q, const doub
   const float dTdy = (float)((0.5 * (TT + T) - 0.5 * (T + TB)) * g.idy);
   const float sg11 = (float)((uR1 - uL1) * 0.5 * g.idx - (uT2 - uB2) * 0.5 * g.idy);
   const float sg12 = (float)((uT1 - uB1) * 0.5 * g.idy + (uR2 - uL2) * 0.5 * g.idx);
-  // FP32 from here
-  const float Tf = (float)T, rhof = (float)rho, idet = 1.0f / (float)det;
+  const double idet = 1.0 / det, iTd = 1.0 / T;
+  const float KG = (float)(rho * kInv2Pi * rsqrt(det));
+  const float iT = (float)iTd;
+  const float kap = (float)(dt * g.dv1 * g.dv2 * kInv2Pi * iTd);
   const float tau = (float)tau_of(p, rho, T);
-  const float KG = rhof * (float)kInv2Pi * rsqrtf((float)det);
-  const float iT = 1.0f / Tf;
-  const float kap = (float)(dt * g.dv1 * g.dv2 * kInv2Pi) * iT;
-  const float dtf = (float)dt, epsf = (float)eps;
+  // FP32 from here
+  const float rhof = (float)rho, dtf = (float)dt, epsf = (float)eps;
   const float iden = 1.0f / fmaf(dtf, tau, epsf);
   const float om1 = epsf * iden;
   const float om2 = dtf * tau * iden;
@@ -403,16 +404,16 @@ __device__ __forceinline__ void prims_f32_body(const double* MMK_R Q, const doub
                       wt * (-0.5f * sg11 * iT), wt * (h2T2 * dTdx),      wt * (h2T2 * dTdy)};
   primf[F_U1 * nc + c] = (float)u1;
   primf[F_U2 * nc + c] = (float)u2;
-  primf[F_INV2T * nc + c] = 0.5f * iT;
+  primf[F_INV2T * nc + c] = (float)(0.5 * iTd);
   primf[F_IT * nc + c] = iT;
   primf[F_KAP * nc + c] = kap;
   primf[F_OM1 * nc + c] = om1;
   primf[F_OM1KAP * nc + c] = om1 * kap;
   primf[F_GAM0 * nc + c] = om2 * ieps * KG;
   primf[F_OME * nc + c] = om2 * mu * ieps;
-  primf[F_TI11H * nc + c] = 0.5f * (float)s22 * idet;
-  primf[F_TI12 * nc + c] = -(float)s12 * idet;
-  primf[F_TI22H * nc + c] = 0.5f * (float)s11 * idet;
+  primf[F_TI11H * nc + c] = (float)(0.5 * s22 * idet);
+  primf[F_TI12 * nc + c] = (float)(-s12 * idet);
+  primf[F_TI22H * nc + c] = (float)(0.5 * s11 * idet);
   for (int m = 0; m < 9; ++m) primf[(F_W01 + m) * nc + c] = w[m];
 }
 
