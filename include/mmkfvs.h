@@ -63,9 +63,10 @@ enum { MM_TAU_RHO = 0, MM_TAU_HARDSPHERE2D = 1, MM_TAU_PRESSURE = 2, MM_TAU_CONS
  * dt = CFL / (V1/dx + V2/dy) that reproduces the step counts printed in Section 6.2. */
 enum { MM_CFL_MIN = 0, MM_CFL_SUM = 1 };
 
-/* Storage of g: FP64, or FP32 with moments, projector coefficients, macro update and the
- * Gaussian tensor inverse in FP64 (the paper uses FP64 throughout; FP32 g is this library's
- * mixed-precision extension). */
+/* Storage of g: FP64, or FP32 with the Gaussian tensor inverse, 1/T, the projector scale, the
+ * heat-flux totals and the macro update in FP64, and g's transport, velocity sums and
+ * relaxation in FP32 (the paper uses FP64 throughout; FP32 g is this library's mixed-precision
+ * extension). */
 enum { MM_PREC_FP64 = 0, MM_PREC_G_FP32 = 1 };  /* MM_PREC_G_FP32 needs nv1 <= 32 */
 
 typedef struct {

@@ -2,12 +2,13 @@
 // 2509.21832): the same split upwind transport with projection, relaxation toward Ghat and heat
 // flux as mm_micro.cu, with g stored and transported in FP32.
 //
-// Precision split: no FP64 instruction runs here (the FP64 pipe of GB300 runs at 1/61 of FP32
-// and a warp instruction costs its full issue time even with one active lane, so an FP64
-// epilogue per cell would bound the kernel); per-cell coefficients come from the prims kernel,
-// computed in FP64 and rounded once; velocity sums are FP32 (per-lane partial sums over its
-// rows, then a pairwise warp butterfly); the heat flux leaves as (hi, lo) FP32 pairs (lo = 0
-// here) that the per-cell unpack kernel turns into FP64.
+// Precision split: no FP64 instruction runs in the streaming kernels (the FP64 pipe of GB300
+// runs at 1/64 of FP32 and a warp instruction costs its full issue time even with one active
+// lane, so an FP64 epilogue per cell would bound the kernel); per-cell coefficients come from
+// the fields kernel (the ES tensor inverse, 1/T and the projector scale in FP64 rounded once,
+// the relaxation weights as FP32 products of those); velocity sums are FP32 (per-lane partial
+// sums over its rows, then a pairwise warp butterfly); the heat flux leaves as (hi, lo) FP32
+// pairs (lo = 0 here) that the per-cell unpack kernel turns into FP64.
 //
 // Three kernels stream the same arithmetic, chosen on the host (pick_fused):
 //  - k_micro_staged_f32 (24^2 and 16^2 meshes symmetric in v2): flat lane mapping, the four
