@@ -73,8 +73,7 @@ MicroShape micro_shape(int nv1, int nv2);
 
 // Per-cell fields: launch_prims_uT writes every cell's (u1, u2, T) into prim, then
 // launch_prims the rest (it reads the neighbours' (u1, u2, T) there): always in this order.
-void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s, int c0 = 0,
-                     int c1 = -1);
+void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s);
 // The FP32 coefficients of every cell for the FP32-g kernels (after launch_prims_uT; writes no
 // other FP64 field).
 void launch_prims_f32(const double* Q, const double* prim, float* primf, const KGrid& g,
@@ -82,7 +81,7 @@ void launch_prims_f32(const double* Q, const double* prim, float* primf, const K
 // Q [6][nc] from primitive fields P4 [4][nc] = (rho, u1, u2, T), isotropic temperature tensor
 void launch_q_from_prim(const double* P4, double* Q, int nc, cudaStream_t s);
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
-                  double dt, double eps, int* err, cudaStream_t s, int c0 = 0, int c1 = -1);
+                  double dt, double eps, int* err, cudaStream_t s);
 // The sweeps over the cells [cell0, cell0 + ncells) (ncells < 0: every cell from cell0 = 0).
 template <typename Tg>
 void launch_micro_x(const Tg* Gin, Tg* Gout, const double* prim, const KGrid& g,
@@ -133,12 +132,10 @@ int fused_segments_f32(const KGrid& g, const MicroShape& ms);
 size_t fused_smem_f32(const KGrid& g);
 // Opt-in shared memory per CTA of the target GPU (sm_103a)
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
-// Segments [seg0, seg1) of the nseg row segments (seg1 < 0: all): rows
-// [seg0 * seg_rows, min(seg1 * seg_rows, ny)) with seg_rows = ceil(ny / nseg).
+// nseg row segments of seg_rows = ceil(ny / nseg) rows each
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
-                            const MicroShape& ms, int nseg, int* err, cudaStream_t s,
-                            int seg0 = 0, int seg1 = -1);
+                            const MicroShape& ms, int nseg, int* err, cudaStream_t s);
 // Buffers of the macro step: Q* and Q**, each cell's half fluxes along x (of Q*) and y (of Q**)
 // [Fp(6) Fm(6)][ny][nx], and the fluxes through the non-periodic boundary faces
 // BX [2 sides][6][ny], BY [2 sides][6][nx].
@@ -154,15 +151,14 @@ constexpr size_t macro_doubles(int nx, int ny) {
   return (size_t)nx * ny * (6 + 6 + 12 + 12) + 12 * (size_t)ny + 12 * (size_t)nx;
 }
 void launch_macro_x1(const double* Qn, const MacroBufs& mb, const KGrid& g, const KParams& p,
-                     double dt, double eps, int* err, cudaStream_t s, int c0 = 0, int c1 = -1);
+                     double dt, double eps, int* err, cudaStream_t s);
 void launch_macro_x2(const double* H, const MacroBufs& mb, const KGrid& g, const KParams& p,
-                     double dt, int* err, cudaStream_t s, int c0 = 0, int c1 = -1);
+                     double dt, int* err, cudaStream_t s);
 // srcq (optional): [6][ny][nx] rates added times dt after the y transport
 void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGrid& g,
                     const KParams& p, double dt, double eps, int* err, cudaStream_t s,
-                    const double* srcq = nullptr, int c0 = 0, int c1 = -1);
-void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s,
-                     int c0 = 0, int c1 = -1);
+                    const double* srcq = nullptr);
+void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s);
 __host__ __device__ inline MacroBufs carve_macro(double* base, int nx, int ny) {
   const size_t nc = (size_t)nx * ny;
   MacroBufs mb;

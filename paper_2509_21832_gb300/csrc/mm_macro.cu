@@ -17,51 +17,50 @@ namespace {
 
 using namespace macro_body;
 
-// Every per-cell kernel takes the cells [c0, c1) (whole rows of a band, or the whole grid).
-__global__ void k_prims_uT(const double* __restrict__ Q, double* __restrict__ prim, int nc, int c0,
-                           int c1) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < c1) uT_body(Q, prim, nc, c);
+// One thread per cell c < nc = nx ny.
+__global__ void k_prims_uT(const double* __restrict__ Q, double* __restrict__ prim, int nc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) uT_body(Q, prim, nc, c);
 }
 
 __global__ void k_prims(const double* __restrict__ Q, double* __restrict__ prim,
                         float* __restrict__ primf, KGrid g, KParams p, double dt, double eps,
-                        double ieps, int* __restrict__ err, int c0, int c1) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < c1) prims_body<true>(Q, prim, primf, g, p, dt, eps, ieps, err, c);
+                        double ieps, int* __restrict__ err) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < g.nx * g.ny) prims_body<true>(Q, prim, primf, g, p, dt, eps, ieps, err, c);
 }
 
 __global__ void k_prims_f32(const double* __restrict__ Q, const double* __restrict__ prim,
                             float* __restrict__ primf, KGrid g, KParams p, double dt, double eps,
-                            int* __restrict__ err, int c0, int c1) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < c1) prims_f32_body(Q, prim, primf, g, p, dt, eps, err, c);
+                            int* __restrict__ err) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < g.nx * g.ny) prims_f32_body(Q, prim, primf, g, p, dt, eps, err, c);
 }
 
 __global__ void k_macro_x1(const double* __restrict__ Qn, MacroBufs mb, KGrid g, KParams p,
-                           double dt, double eps, int* __restrict__ err, int c0, int c1) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < c1) macro_x1_body(Qn, mb, g, p, dt, eps, err, c);
+                           double dt, double eps, int* __restrict__ err) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < g.nx * g.ny) macro_x1_body(Qn, mb, g, p, dt, eps, err, c);
 }
 
 __global__ void k_macro_x2(const double* __restrict__ H, MacroBufs mb, KGrid g, KParams p,
-                           double dt, int* __restrict__ err, int c0, int c1) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < c1) macro_x2_body(H, mb, g, p, dt, err, c);
+                           double dt, int* __restrict__ err) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < g.nx * g.ny) macro_x2_body(H, mb, g, p, dt, err, c);
 }
 
 __global__ void k_macro_y(const double* __restrict__ H, MacroBufs mb, double* __restrict__ Qn,
                           KGrid g, KParams p, double dt, double eps, int* __restrict__ err,
-                          const double* __restrict__ srcq, int c0, int c1) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < c1) macro_y_body(H, mb, Qn, g, p, dt, eps, err, c, srcq);
+                          const double* __restrict__ srcq) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < g.nx * g.ny) macro_y_body(H, mb, Qn, g, p, dt, eps, err, c, srcq);
 }
 
 // Heat flux of the FP32-g kernels: compensated FP32 (hi, lo) totals -> FP64, times eps dv1 dv2.
 __global__ void k_h_unpack(const float* __restrict__ Hf, double* __restrict__ H, int nc,
-                           double hscale, int c0, int c1) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= c1) return;
+                           double hscale) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
   for (int m = 0; m < 4; ++m)
     H[m * nc + c] = hscale * ((double)Hf[(2 * m) * nc + c] + (double)Hf[(2 * m + 1) * nc + c]);
 }
@@ -85,16 +84,12 @@ __global__ void k_q_from_prim(const double* __restrict__ P4, double* __restrict_
 }  // namespace
 
 namespace {
-int end_of(const KGrid& g, int c1) { return c1 < 0 ? g.nx * g.ny : c1; }
-int blocks_of(int c0, int c1, int t) { return (c1 - c0 + t - 1) / t; }
+int blocks_of(const KGrid& g, int t) { return (g.nx * g.ny + t - 1) / t; }
 }  // namespace
 
 void launch_prims(const double* Q, double* prim, float* primf, const KGrid& g, const KParams& p,
-                  double dt, double eps, int* err, cudaStream_t s, int c0, int c1) {
-  c1 = end_of(g, c1);
-  if (c1 > c0)
-    k_prims<<<blocks_of(c0, c1, 128), 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, 1.0 / eps, err,
-                                                    c0, c1);
+                  double dt, double eps, int* err, cudaStream_t s) {
+  k_prims<<<blocks_of(g, 128), 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, 1.0 / eps, err);
 }
 
 void launch_q_from_prim(const double* P4, double* Q, int nc, cudaStream_t s) {
@@ -103,45 +98,31 @@ void launch_q_from_prim(const double* P4, double* Q, int nc, cudaStream_t s) {
 
 void launch_prims_f32(const double* Q, const double* prim, float* primf, const KGrid& g,
                       const KParams& p, double dt, double eps, int* err, cudaStream_t s) {
-  const int c1 = end_of(g, -1);
-  if (c1 > 0)
-    k_prims_f32<<<blocks_of(0, c1, 128), 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, err, 0, c1);
+  k_prims_f32<<<blocks_of(g, 128), 128, 0, s>>>(Q, prim, primf, g, p, dt, eps, err);
 }
 
-void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s, int c0,
-                     int c1) {
-  c1 = end_of(g, c1);
-  if (c1 > c0)
-    k_prims_uT<<<blocks_of(c0, c1, 256), 256, 0, s>>>(Q, prim, g.nx * g.ny, c0, c1);
+void launch_prims_uT(const double* Q, double* prim, const KGrid& g, cudaStream_t s) {
+  k_prims_uT<<<blocks_of(g, 256), 256, 0, s>>>(Q, prim, g.nx * g.ny);
 }
 
 void launch_macro_x1(const double* Qn, const MacroBufs& mb, const KGrid& g, const KParams& p,
-                     double dt, double eps, int* err, cudaStream_t s, int c0, int c1) {
-  c1 = end_of(g, c1);
-  if (c1 > c0)
-    k_macro_x1<<<blocks_of(c0, c1, 128), 128, 0, s>>>(Qn, mb, g, p, dt, eps, err, c0, c1);
+                     double dt, double eps, int* err, cudaStream_t s) {
+  k_macro_x1<<<blocks_of(g, 128), 128, 0, s>>>(Qn, mb, g, p, dt, eps, err);
 }
 
 void launch_macro_x2(const double* H, const MacroBufs& mb, const KGrid& g, const KParams& p,
-                     double dt, int* err, cudaStream_t s, int c0, int c1) {
-  c1 = end_of(g, c1);
-  if (c1 > c0) k_macro_x2<<<blocks_of(c0, c1, 128), 128, 0, s>>>(H, mb, g, p, dt, err, c0, c1);
+                     double dt, int* err, cudaStream_t s) {
+  k_macro_x2<<<blocks_of(g, 128), 128, 0, s>>>(H, mb, g, p, dt, err);
 }
 
 void launch_macro_y(const double* H, const MacroBufs& mb, double* Qn, const KGrid& g,
                     const KParams& p, double dt, double eps, int* err, cudaStream_t s,
-                    const double* srcq, int c0, int c1) {
-  c1 = end_of(g, c1);
-  if (c1 > c0)
-    k_macro_y<<<blocks_of(c0, c1, 128), 128, 0, s>>>(H, mb, Qn, g, p, dt, eps, err, srcq, c0, c1);
+                    const double* srcq) {
+  k_macro_y<<<blocks_of(g, 128), 128, 0, s>>>(H, mb, Qn, g, p, dt, eps, err, srcq);
 }
 
-void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s,
-                     int c0, int c1) {
-  c1 = end_of(g, c1);
-  if (c1 > c0)
-    k_h_unpack<<<blocks_of(c0, c1, 128), 128, 0, s>>>(Hf, H, g.nx * g.ny, eps * g.dv1 * g.dv2,
-                                                      c0, c1);
+void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cudaStream_t s) {
+  k_h_unpack<<<blocks_of(g, 128), 128, 0, s>>>(Hf, H, g.nx * g.ny, eps * g.dv1 * g.dv2);
 }
 
 }  // namespace mmk

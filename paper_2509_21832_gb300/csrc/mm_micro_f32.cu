@@ -91,8 +91,7 @@ struct FusedF32 {
   float dtidx, dtidy;
   int R;         // rows per pass: 32 / nv1
   int seg_rows;  // rows per segment
-  int nseg;      // segments covered by this launch, from segment seg0 on
-  int seg0;
+  int nseg;      // row segments
   int* err;      // device error word (ERR_WAIT_TIMEOUT from a bounded wait)
 };
 
@@ -398,7 +397,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_fused_f32(FusedF3
   const int gw = blockIdx.x * kFusedWarps + w;
   if (gw >= g.nx * a.nseg) return;  // whole warp leaves; no CTA-wide barrier is used below
   const int i = gw % g.nx;
-  const int seg = a.seg0 + gw / g.nx;
+  const int seg = gw / g.nx;
   const int j0 = seg * a.seg_rows;
   const int j1 = min(g.ny, j0 + a.seg_rows);
   if (j0 >= j1) return;
@@ -807,7 +806,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_flat_f32(FusedF32
   const int gw = blockIdx.x * kFusedWarps + w;
   if (gw >= g.nx * a.nseg) return;  // whole warp leaves; no CTA-wide barrier is used below
   const int i = gw % g.nx;
-  const int seg = a.seg0 + gw / g.nx;
+  const int seg = gw / g.nx;
   const int j0 = seg * a.seg_rows;
   const int j1 = min(g.ny, j0 + a.seg_rows);
   if (j0 >= j1) return;
@@ -950,7 +949,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   const uint32_t bar_empty = smem_addr(bars + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 4);
   const int ncx = (g.nx + W - 1) / W;
-  const int cx = blockIdx.x % ncx, seg = a.seg0 + blockIdx.x / ncx;
+  const int cx = blockIdx.x % ncx, seg = blockIdx.x / ncx;
   const int i0 = cx * W, i = i0 + w;
   const bool col = i < g.nx;  // warps past the last column only read nothing from the stage
   const int j0 = seg * a.seg_rows;
@@ -1428,8 +1427,7 @@ int fused_segments_f32(const KGrid& g, const MicroShape& ms) {
 
 void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* Hf,
                             const float* primf, const KGrid& g, const KParams& p, double dt,
-                            const MicroShape& ms, int nseg, int* err, cudaStream_t s, int seg0,
-                            int seg1) {
+                            const MicroShape& ms, int nseg, int* err, cudaStream_t s) {
   (void)ms;
   const FusedPick f = pick_fused(g);
   FusedF32 a;
@@ -1445,11 +1443,8 @@ void launch_micro_fused_f32(const float* Gin, float* Gout, float* Gexp, float* H
   a.dtidx = (float)(dt * g.idx);
   a.dtidy = (float)(dt * g.idy);
   a.R = 32 / g.nv1;
-  if (seg1 < 0 || seg1 > nseg) seg1 = nseg;
-  if (seg0 >= seg1) return;
   a.seg_rows = (g.ny + nseg - 1) / nseg;
-  a.seg0 = seg0;
-  a.nseg = seg1 - seg0;
+  a.nseg = nseg;
   // one warp per column and segment; the staged kernels give a CTA kFusedWarps adjacent columns
   const int warps = ((g.nx + kFusedWarps - 1) / kFusedWarps) * kFusedWarps * a.nseg;
   if (f.smem > 48 * 1024)
