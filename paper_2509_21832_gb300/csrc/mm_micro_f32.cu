@@ -442,6 +442,15 @@ __device__ __forceinline__ void l2_prefetch_bulk(const void* p, unsigned bytes) 
 
 constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 
+// The flat-mapped sweeps read a cell's fields from shared memory as float4 groups in this order.
+static_assert(F_U1 == 0 && F_U2 == 1 && F_INV2T == 2 && F_IT == 3 && F_KAP == 4 && F_OM1 == 5 &&
+                  F_OM1KAP == 6 && F_GAM0 == 7 && F_OME == 8 && F_TI11H == 9 && F_TI12 == 10 &&
+                  F_TI22H == 11 && F_W01 == 12 && F_W02 == 13 && F_W03 == 14 && F_W10 == 15 &&
+                  F_W11 == 16 && F_W12 == 17 && F_W20 == 18 && F_W21 == 19 && F_W30 == 20 &&
+                  NPRIMF == 21,
+              "field order");
+constexpr int kFieldSlot = 24;  // floats per cell's fields in shared memory (16-byte multiple)
+
 template <int NV1, int NV2>
 struct FlatShape {
   static constexpr int NV = NV1 * NV2;
@@ -449,7 +458,7 @@ struct FlatShape {
   static constexpr int P = NV1 / cgcd(NV1, 32);     // v1 columns per lane
   static constexpr int ST = 32 / cgcd(NV1, 32);     // row stride within a column
   static constexpr int TOP = NV2 / (2 * ST);        // visits t < TOP are rows with v2 < 0
-  static constexpr int PER_WARP = 3 * NV + 14 * NV2;  // ring + tables, floats
+  static constexpr int PER_WARP = 3 * NV + 14 * NV2 + kFieldSlot;  // ring, tables, fields
   static_assert(NV % 32 == 0 && M % P == 0 && (M / P) * ST == NV2, "flat shape");
   static_assert((NV2 / 2) % ST == 0 && NV <= 1024 && NV2 % 2 == 0, "flat shape");
 };
@@ -478,7 +487,7 @@ __device__ __forceinline__ int pair_slot(int l, int& half) {
 template <int NV1, int NV2, bool STAGED>
 __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float* dst, float* xt,
                                          const float* Gcb, const float* Gl, const float* Gr,
-                                         bool mirl, bool mirr, float fv) {
+                                         bool mirl, bool mirr, const float* fs) {
   using S = FlatShape<NV1, NV2>;
   constexpr int P = S::P, NU = S::M / S::P / 2, ST = S::ST;
   const KGrid& g = a.g;
@@ -486,8 +495,8 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
   const int lane = threadIdx.x & 31;
   // per row pair: {c2_a, c2_b, c2_a^2, c2_b^2}, {e2_a, e2_b, projection term a, b}
   float4* XP = reinterpret_cast<float4*>(xt);
-  const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
-  const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT), kap = field(fv, F_KAP);
+  const float4 f0 = *reinterpret_cast<const float4*>(fs);  // (u1, u2, 1/2T, 1/T)
+  const float u1 = f0.x, u2 = f0.y, inv2T = f0.z, iT = f0.w, kap = fs[F_KAP];
   for (int l = lane; l < NV2; l += 32) {
     int h;
     const int p = pair_slot<NV1, NV2>(l, h);
@@ -602,7 +611,8 @@ __device__ __forceinline__ void fx_sweep(const FusedF32& a, int i, int j, float*
 // above (rt) the cell (flat mapping).
 template <int NV1, int NV2>
 __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const float* rb,
-                                         const float* rc, const float* rt, float* tb, float fv) {
+                                         const float* rc, const float* rt, float* tb,
+                                         const float* fs) {
   using S = FlatShape<NV1, NV2>;
   constexpr int P = S::P, NU = S::M / S::P / 2, ST = S::ST;
   const KGrid& g = a.g;
@@ -612,14 +622,13 @@ __device__ __forceinline__ void fy_sweep(const FusedF32& a, int i, int j, const 
   // for the moments of Z*; {wl_a, wl_b, e2_a, e2_b}, {c2_a, c2_b, g2_a, g2_b},
   // {c2^2_a, c2^2_b, c2^3_a, c2^3_b} for the update and the heat flux
   const float4* Y = reinterpret_cast<const float4*>(tb);
-  const float u1 = field(fv, F_U1), u2 = field(fv, F_U2);
-  const float inv2T = field(fv, F_INV2T), iT = field(fv, F_IT);
-  const float Ti11h = field(fv, F_TI11H), Ti12 = field(fv, F_TI12), Ti22h = field(fv, F_TI22H);
-  const float om1 = field(fv, F_OM1), om1kap = field(fv, F_OM1KAP);
-  const float gam0 = field(fv, F_GAM0), ome = field(fv, F_OME);
-  const float w01 = field(fv, F_W01), w02 = field(fv, F_W02), w03 = field(fv, F_W03);
-  const float w10 = field(fv, F_W10), w11 = field(fv, F_W11), w12 = field(fv, F_W12);
-  const float w20 = field(fv, F_W20), w21 = field(fv, F_W21), w30 = field(fv, F_W30);
+  const float4* F4 = reinterpret_cast<const float4*>(fs);
+  const float4 fa = F4[0], fb = F4[1], fc = F4[2], fd = F4[3], fe = F4[4];
+  const float u1 = fa.x, u2 = fa.y, inv2T = fa.z, iT = fa.w;
+  const float om1 = fb.y, om1kap = fb.z, gam0 = fb.w;
+  const float ome = fc.x, Ti11h = fc.y, Ti12 = fc.z, Ti22h = fc.w;
+  const float w01 = fd.x, w02 = fd.y, w03 = fd.z, w10 = fd.w;
+  const float w11 = fe.x, w12 = fe.y, w20 = fe.z, w21 = fe.w, w30 = fs[F_W30];
   for (int l = lane; l < NV2; l += 32) {
     int h;
     const int p = pair_slot<NV1, NV2>(l, h);
@@ -803,6 +812,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_flat_f32(FusedF32
   float* ring = smf + (size_t)w * S::PER_WARP;
   float* xt = ring + 3 * S::NV;
   float* yt = xt + 4 * NV2;
+  float* fld = yt + 10 * NV2;
   const int gw = blockIdx.x * kFusedWarps + w;
   if (gw >= g.nx * a.nseg) return;  // whole warp leaves; no CTA-wide barrier is used below
   const int i = gw % g.nx;
@@ -818,12 +828,20 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_flat_f32(FusedF32
     if ((threadIdx.x & 31) == 0 && jj < g.ny)
       l2_prefetch_bulk(a.Gin + (size_t)(jj * g.nx + i) * S::NV, (unsigned)(S::NV * sizeof(float)));
   };
+  // a cell's fields into the warp's shared-memory slot (lane f reads field f); the previous
+  // sweep ended with a warp barrier, so nobody reads the slot any more
+  auto fields_of = [&](int cell) {
+    const float f = load_fields(a.pf, g.nx * g.ny, cell);
+    if ((threadIdx.x & 31) < NPRIMF) fld[threadIdx.x & 31] = f;
+    __syncwarp();
+    return fld;
+  };
   auto xsweep = [&](int jj, float* dst) {
     const UpwindF ul = upwind_side(g, a.p, i, jj, 0), ur = upwind_side(g, a.p, i, jj, 1);
     const float* Gl = ul.zero ? kZeroRowF : a.Gin + (size_t)ul.cell * S::NV;
     const float* Gr = ur.zero ? kZeroRowF : a.Gin + (size_t)ur.cell * S::NV;
     fx_sweep<NV1, NV2, false>(a, i, jj, dst, xt, a.Gin + (size_t)(jj * g.nx + i) * S::NV, Gl, Gr,
-                              ul.mirror, ur.mirror, load_fields(a.pf, g.nx * g.ny, jj * g.nx + i));
+                              ul.mirror, ur.mirror, fields_of(jj * g.nx + i));
   };
   prefetch(j0 + 1);
   if (j0 > 0 || pery) xsweep(j0 > 0 ? j0 - 1 : g.ny - 1, slot(0));
@@ -842,7 +860,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_flat_f32(FusedF32
     const float* rt = rc;
     if (hast) rt = slot(pos + 1);
     else if (a.p.bc[3] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 1)); rt = slot(pos + 1); }
-    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt, load_fields(a.pf, g.nx * g.ny, j * g.nx + i));
+    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt, fields_of(j * g.nx + i));
   }
 }
 
@@ -910,7 +928,8 @@ struct StagedShape {
   // per warp: the x sweep's tables (4 NV2 floats) and the y sweep's (10 NV2) share one area; a
   // warp's sweeps run one after the other with a warp barrier between them
   static constexpr int TABLES = 10 * NV2;
-  static constexpr int FLOATS = STAGE + W * (RING + TABLES) + 6;  // + two mbarriers, a flag
+  static constexpr int FIELDS = 3 * kFieldSlot;  // per warp: fields of three x-swept rows
+  static constexpr int FLOATS = STAGE + W * (RING + TABLES + FIELDS) + 6;  // + 2 mbarriers, flag
 };
 
 // Source of stage slot sigma (column c = i0 - 1 + sigma) for row jj: the column's block; beyond
@@ -944,7 +963,10 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   float* yt = xt;
   // full: the stage holds the next row (the bulk copies' bytes have landed); empty: every warp
   // has finished reading the stage, so that it may be refilled
-  float* bars = smf + T::STAGE + W * (T::RING + T::TABLES);
+  // per-cell fields of the x-swept rows in three slots like the G* ring (a row's fields serve
+  // its x sweep and, one iteration later, its y sweep), fetched two rows ahead by cp.async
+  float* fld = smf + T::STAGE + W * (T::RING + T::TABLES) + w * T::FIELDS;
+  float* bars = smf + T::STAGE + W * (T::RING + T::TABLES + T::FIELDS);
   const uint32_t bar = smem_addr(bars);
   const uint32_t bar_empty = smem_addr(bars + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 4);
@@ -1004,6 +1026,27 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   uint32_t eparity = 0;       // phase of the empty barrier (thread 0)
   bool pending = true;        // thread 0: a copy issued whose completion no warp has seen yet
   if (threadIdx.x == 0) issue(xrow(0));
+  // fields of ring position pos (x-swept row number pos - fpos0): lane f copies field f
+  const int fpos0 = halo ? 0 : 1;
+  auto fslot = [&](int pos) { return fld + (pos % 3) * kFieldSlot; };
+  auto fetch = [&](int pos) {
+    const int xn = pos - fpos0;
+    if (col && xn >= 0 && xn < nx_rows && lane < NPRIMF) {
+      const float* src = a.pf + (size_t)lane * g.nx * g.ny + (size_t)xrow(xn) * g.nx + i;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(fslot(pos) + lane)),
+                   "l"(src)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto fields_landed = [&]() {  // every fetch but the newest has landed, for every lane
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncwarp();
+  };
+  fetch(0);
+  fetch(1);
+  fetch(2);
+  fields_landed();
   // Give up after a wait ran out (here or in another warp): thread 0 first lets its copies land
   // (bounded again), so that no bulk copy writes into the shared memory of a finished CTA.
   auto give_up = [&]() {
@@ -1012,6 +1055,7 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
       *abort_flag = 1;
     }
     if (threadIdx.x == 0 && pending) mbar_wait_bounded(bar, parity);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     return false;
   };
   // x sweep number n into ring position pos; the warp then releases the stage, and thread 0
@@ -1020,7 +1064,6 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   auto xstep = [&](int n, int pos) -> bool {
     if (*abort_flag) return give_up();
     const int jj = xrow(n);
-    const float fvx = col ? load_fields(a.pf, g.nx * g.ny, jj * g.nx + i) : 0.f;
     // the sweep's warp shuffles need every lane: a warp sweeps only if all its lanes saw the copy
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
     if (!ok) return give_up();
@@ -1028,7 +1071,8 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
     if (threadIdx.x == 0) pending = false;
     if (col)
       fx_sweep<NV1, NV2, true>(a, i, jj, slot(pos), xt, stage + (w + 1) * S::NV,
-                               stage + w * S::NV, stage + (w + 2) * S::NV, mirl, mirr, fvx);
+                               stage + w * S::NV, stage + (w + 2) * S::NV, mirl, mirr,
+                               fslot(pos));
     __syncwarp();
     if (lane == 0)
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_empty) : "memory");
@@ -1052,8 +1096,8 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   if (!xstep(n++, 1)) return;
   for (int j = j0; j < j1; ++j) {
     const int pos = j - j0 + 1;
-    // the y sweep's per-cell fields, in flight during this iteration's x sweep
-    const float fvy = col ? load_fields(a.pf, g.nx * g.ny, j * g.nx + i) : 0.f;
+    fetch(pos + 2);    // for the next iteration's x sweep, into the slot of row j - 1
+    fields_landed();   // row j + 1's, for this iteration's x sweep
     if (j + 1 < g.ny || pery)
       if (!xstep(n++, pos + 1)) return;
     if (!col || diffuse_wall_cell(g, a.p, i, j)) continue;  // wall cells: the wall kernel
@@ -1065,8 +1109,9 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
     const float* rt = rc;
     if (hast) rt = slot(pos + 1);
     else if (a.p.bc[3] == MM_BC_SPECULAR) { mirror_rows<NV1, NV2>(rc, slot(pos + 1)); rt = slot(pos + 1); }
-    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt, fvy);
+    fy_sweep<NV1, NV2>(a, i, j, rb, rc, rt, yt, fslot(pos));
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // The kernel for a velocity mesh and its shared memory per CTA.  Flat-mapped kernels for the
