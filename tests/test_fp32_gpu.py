@@ -49,6 +49,11 @@ CASES = [
      (I.PERIODIC, I.PERIODIC, I.DIFFUSE, I.DIFFUSE), dict(wall_T=(1.0, 1.0, 1.1, 0.9))),
     ("walls_y_segments_16", dict(nx=12, ny=50, nv1=16, nv2=16),
      (I.EXTRAP, I.SPECULAR, I.DIFFUSE, I.DIFFUSE), dict(wall_T=(1.0, 1.0, 1.2, 1.0))),
+    # several row segments with periodic y (the first and last segments' halo rows wrap, and so
+    # do the rows whose coefficients are fetched ahead) and with specular y walls (mirrored rows
+    # in the first and last segments)
+    ("periodic_segments_24", dict(nx=6, ny=64, nv1=24, nv2=24), (I.PERIODIC,) * 4, {}),
+    ("specular_segments_16", dict(nx=5, ny=48, nv1=16, nv2=16), (I.SPECULAR,) * 4, {}),
     # moving diffuse walls at the left and bottom (a corner cell with two wall ghosts), the
     # literal wall form of Ghat (no (G - M)/eps term)
     ("walls_literal_24", dict(nx=10, ny=8, nv1=24, nv2=24),
