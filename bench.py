@@ -256,7 +256,7 @@ def fp32_variant(args, stream):
     from paper_2509_21832_gb300 import inputs as I
     pr = I.riemann4_diffuse(n=args.variant_n, nv=24, eps=1e-2, seed=0, nsteps=100)
     out = {"workload": "riemann4_diffuse_%dx%dx24x24" % (pr.grid.nx, pr.grid.ny),
-           "eps": pr.eps, "steps": pr.nsteps, "dtype": "g f32, macro/moments f64"}
+           "eps": pr.eps, "steps": pr.nsteps, "dtype": "g f32 (transport, velocity sums, relaxation); ES tensor inverse, heat-flux totals, macro update f64"}
     res = {}
     for prec in (I.PREC_G_FP32, I.PREC_FP64):
         params = I.Params(**{**pr.params.__dict__, "precision": prec})
