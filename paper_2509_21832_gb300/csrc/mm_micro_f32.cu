@@ -929,7 +929,11 @@ struct StagedShape {
   // warp's sweeps run one after the other with a warp barrier between them
   static constexpr int TABLES = 10 * NV2;
   static constexpr int FIELDS = 3 * kFieldSlot;  // per warp: fields of three x-swept rows
-  static constexpr int FLOATS = STAGE + W * (RING + TABLES + FIELDS) + 6;  // + 2 mbarriers, flag
+  // stage buffers (rows in flight): one; two leave room for 3 CTAs per SM only and measured
+  // slower (2.02 against 1.86 ms at 1024^2 x 24^2)
+  static constexpr int NSTAGE = 1;
+  // + a full and an empty mbarrier per stage buffer and the abort flag
+  static constexpr int FLOATS = NSTAGE * STAGE + W * (RING + TABLES + FIELDS) + 4 * NSTAGE + 2;
 };
 
 // Source of stage slot sigma (column c = i0 - 1 + sigma) for row jj: the column's block; beyond
@@ -957,19 +961,20 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   extern __shared__ __align__(16) float smf[];
   const KGrid& g = a.g;
   const int w = threadIdx.x >> 5;
-  float* stage = smf;
-  float* ring = smf + T::STAGE + w * (T::RING + T::TABLES);
+  constexpr int NS = T::NSTAGE;
+  float* stage0 = smf;
+  float* ring = smf + NS * T::STAGE + w * (T::RING + T::TABLES);
   float* xt = ring + T::RING;
   float* yt = xt;
   // full: the stage holds the next row (the bulk copies' bytes have landed); empty: every warp
   // has finished reading the stage, so that it may be refilled
   // per-cell fields of the x-swept rows in three slots like the G* ring (a row's fields serve
   // its x sweep and, one iteration later, its y sweep), fetched two rows ahead by cp.async
-  float* fld = smf + T::STAGE + W * (T::RING + T::TABLES) + w * T::FIELDS;
-  float* bars = smf + T::STAGE + W * (T::RING + T::TABLES + T::FIELDS);
-  const uint32_t bar = smem_addr(bars);
-  const uint32_t bar_empty = smem_addr(bars + 2);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 4);
+  float* fld = smf + NS * T::STAGE + W * (T::RING + T::TABLES) + w * T::FIELDS;
+  float* bars = smf + NS * T::STAGE + W * (T::RING + T::TABLES + T::FIELDS);
+  auto bar_full = [&](int b) { return smem_addr(bars + 4 * b); };
+  auto bar_empty = [&](int b) { return smem_addr(bars + 4 * b + 2); };
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 4 * NS);
   const int ncx = (g.nx + W - 1) / W;
   const int cx = blockIdx.x % ncx, seg = blockIdx.x / ncx;
   const int i0 = cx * W, i = i0 + w;
@@ -984,14 +989,19 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   auto slot = [&](int pos) { return ring + (size_t)(pos % 3) * S::NV; };
 
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_empty), "r"(W) : "memory");
+    for (int b = 0; b < NS; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_full(b)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_empty(b)), "r"(W)
+                   : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
   __syncthreads();
   // bulk copies of row jj's blocks into the stage (thread 0)
-  auto issue = [&](int jj) {
+  auto issue = [&](int jj, int b) {
+    float* stage = stage0 + b * T::STAGE;
+    const uint32_t bar = bar_full(b);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     const float* src[W + 2];
     unsigned bytes = 0;
@@ -1022,10 +1032,13 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
     if (jj >= g.ny) jj -= g.ny;
     return jj;
   };
-  uint32_t parity = 0;        // phase of the full barrier awaited next
-  uint32_t eparity = 0;       // phase of the empty barrier (thread 0)
-  bool pending = true;        // thread 0: a copy issued whose completion no warp has seen yet
-  if (threadIdx.x == 0) issue(xrow(0));
+  // x-swept row n uses stage buffer n % NS, in that buffer's phase (n / NS) & 1
+  unsigned pending = 0;  // thread 0: bit b set while a copy into buffer b has not been awaited
+  if (threadIdx.x == 0)
+    for (int b = 0; b < NS && b < nx_rows; ++b) {
+      issue(xrow(b), b);
+      pending |= 1u << b;
+    }
   // fields of ring position pos (x-swept row number pos - fpos0): lane f copies field f
   const int fpos0 = halo ? 0 : 1;
   auto fslot = [&](int pos) { return fld + (pos % 3) * kFieldSlot; };
@@ -1048,13 +1061,16 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   fetch(2);
   fields_landed();
   // Give up after a wait ran out (here or in another warp): thread 0 first lets its copies land
-  // (bounded again), so that no bulk copy writes into the shared memory of a finished CTA.
-  auto give_up = [&]() {
+  // (bounded again), so that no bulk copy writes into the shared memory of a finished CTA; at x
+  // row n the copies not yet awaited are those of rows n .. n + NS - 1.
+  auto give_up = [&](int n) {
     if (lane == 0) {
       atomicOr(a.err, ERR_WAIT_TIMEOUT);
       *abort_flag = 1;
     }
-    if (threadIdx.x == 0 && pending) mbar_wait_bounded(bar, parity);
+    if (threadIdx.x == 0)
+      for (int r = n; r < n + NS; ++r)
+        if (pending & (1u << (r % NS))) mbar_wait_bounded(bar_full(r % NS), (r / NS) & 1u);
     asm volatile("cp.async.wait_all;" ::: "memory");
     return false;
   };
@@ -1062,32 +1078,33 @@ __global__ void __launch_bounds__(32 * kFusedWarps, 4) k_micro_staged_f32(FusedF
   // refills it with the next row as soon as every warp has released it (the other warps go on
   // to their y sweeps meanwhile)
   auto xstep = [&](int n, int pos) -> bool {
-    if (*abort_flag) return give_up();
+    if (*abort_flag) return give_up(n);
     const int jj = xrow(n);
+    const int b = n % NS;
+    const uint32_t ph = (n / NS) & 1u;
+    float* stage = stage0 + b * T::STAGE;
     // the sweep's warp shuffles need every lane: a warp sweeps only if all its lanes saw the copy
-    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
-    if (!ok) return give_up();
-    parity ^= 1u;
-    if (threadIdx.x == 0) pending = false;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar_full(b), ph));
+    if (!ok) return give_up(n);
+    if (threadIdx.x == 0) pending &= ~(1u << b);
     if (col)
       fx_sweep<NV1, NV2, true>(a, i, jj, slot(pos), xt, stage + (w + 1) * S::NV,
                                stage + w * S::NV, stage + (w + 2) * S::NV, mirl, mirr,
                                fslot(pos));
     __syncwarp();
     if (lane == 0)
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_empty) : "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_empty(b)) : "memory");
     if (threadIdx.x == 0) {
-      const bool free = mbar_wait_bounded(bar_empty, eparity);
-      if (free && n + 1 < nx_rows) {
-        issue(xrow(n + 1));
-        pending = true;
+      const bool free = mbar_wait_bounded(bar_empty(b), ph);
+      if (free && n + NS < nx_rows) {
+        issue(xrow(n + NS), b);
+        pending |= 1u << b;
       }
       if (!free) {
         atomicOr(a.err, ERR_WAIT_TIMEOUT);
         *abort_flag = 1;
       }
     }
-    eparity ^= 1u;
     __syncwarp();
     return true;
   };
