@@ -138,9 +138,12 @@ def test_checkpoint_resume_bitwise():
     assert np.array_equal(Qa, Qb) and np.array_equal(Ga, Gb) and np.array_equal(Ha, Hb)
 
 
-def test_nonphysical_state_is_reported():
+@pytest.mark.parametrize("prec", [I.PREC_FP64, I.PREC_G_FP32])
+def test_nonphysical_state_is_reported(prec):
+    """A negative density is reported as MM_ERR_NONPHYSICAL by either precision's fields
+    kernel."""
     g = I.Grid(nx=6, ny=5, nv1=8, nv2=8)
-    p = I.Params(bc=(I.PERIODIC,) * 4)
+    p = I.Params(bc=(I.PERIODIC,) * 4, precision=prec)
     Q = I.smooth_state(g, seed=1)
     Q[0, 2, 3] = -1.0
     with api.Solver(g, p) as s:
