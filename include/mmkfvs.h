@@ -382,6 +382,13 @@ void mm1d_destroy(mm1d_ctx* c);
 mm_status mm_diag_exp(const double* x_dev, double* y_fast_dev, double* y_lib_dev, size_t n,
                       void* cuda_stream);
 
+/* Diagnostic: evaluate the error function used by the KFVS half fluxes (Section 5.4: a
+ * polynomial on |x| < 1.5, the library erf elsewhere) and the CUDA library erf on n FP64 device
+ * values x_dev, into caller-owned device arrays; synchronises cuda_stream.  Used to test the
+ * fluxes' erf against the library erf.  MM_ERR_INVALID_ARG for a NULL array. */
+mm_status mm_diag_erf(const double* x_dev, double* y_fast_dev, double* y_lib_dev, size_t n,
+                      void* cuda_stream);
+
 /* Diagnostic: the FP64 pipe's throughput.  Launches `ctas` CTAs of 256 threads on cuda_stream;
  * each thread runs `iters` rounds of 8 independent FP64 fused multiply-adds d <- a d + b
  * (a = 1 - 2^-20, b = 2^-30, d starting at 1 + lane/256) and writes the sum of its 8 chains to

@@ -53,7 +53,7 @@ EXPORTS = ["mm_create", "mm_create_borrowed", "mm_scratch_bytes", "mm_device_byt
            "mm_sync", "mm_get_moments", "mm_get_moments_device", "mm_get_g", "mm_dt_for_cfl",
            "mm_last_error", "mm_set_timing", "mm_get_timing", "mm_num_kernels",
            "mm_kernel_name", "mm_destroy", "mm_step_static_scratch", "mm_diag_exp", "mm_step_host",
-           "mm_diag_bounded_wait", "mm_diag_fp64_fma",
+           "mm_diag_erf", "mm_diag_bounded_wait", "mm_diag_fp64_fma",
            "mm_batch_create", "mm_batch_set_state", "mm_batch_step", "mm_batch_autotune",
            "mm_batch_set_graph", "mm_batch_sync", "mm_batch_get_moments", "mm_batch_get_g",
            "mm_batch_tiles", "mm_batch_diag_hold",
@@ -134,6 +134,8 @@ def load(build_if_needed: bool = True):
         getattr(L, name).restype = ctypes.c_int
     L.mm_diag_exp.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
     L.mm_diag_exp.restype = ctypes.c_int
+    L.mm_diag_erf.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
+    L.mm_diag_erf.restype = ctypes.c_int
     L.mm_diag_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int, vp]
     L.mm_diag_bounded_wait.restype = ctypes.c_int
     L.mm_diag_fp64_fma.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
@@ -313,6 +315,20 @@ def mm_diag_exp(x_dev, stream=0):
                             ctypes.c_void_p(int(stream)))
     if st != MM_OK:
         raise MMError(st, "mm_diag_exp")
+    return yf, yl
+
+
+def mm_diag_erf(x_dev, stream=0):
+    """(flux, library) error functions of a CUDA float64 tensor, computed on the device."""
+    import torch
+    if not isinstance(x_dev, torch.Tensor) or not x_dev.is_cuda or x_dev.dtype != torch.float64:
+        raise TypeError("expected a float64 CUDA tensor")
+    x_dev = x_dev.contiguous()
+    yf, yl = torch.empty_like(x_dev), torch.empty_like(x_dev)
+    st = load().mm_diag_erf(x_dev.data_ptr(), yf.data_ptr(), yl.data_ptr(), x_dev.numel(),
+                            ctypes.c_void_p(int(stream)))
+    if st != MM_OK:
+        raise MMError(st, "mm_diag_erf")
     return yf, yl
 
 

@@ -4,6 +4,7 @@
 
 #include <cmath>
 
+#include "mm_erf.cuh"
 #include "mm_exp.cuh"
 #include "mm_internal.cuh"
 
@@ -94,7 +95,7 @@ __device__ __forceinline__ void abJK(const double q[6], double ir, int dir, doub
   const double s2 = 2.0 * Pn * ir;  // 2 th
   const double h = rsqrt(s2);       // 1 / sqrt(2 th)
   a = kInvSqrtPi * (s2 * h) * expd(-(un * h) * (un * h));
-  b = erf(un * h);
+  b = erfd(un * h);
   if (dir == 1) {
     J[0] = rho;
     J[1] = rho * u1;

@@ -81,6 +81,15 @@ __global__ void k_q_from_prim(const double* __restrict__ P4, double* __restrict_
   }
 }
 
+__global__ void k_diag_erf(const double* __restrict__ x, double* __restrict__ yf,
+                           double* __restrict__ yl, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x) {
+    yf[q] = erfd(x[q]);
+    yl[q] = erf(x[q]);
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -126,3 +135,14 @@ void launch_h_unpack(const float* Hf, double* H, const KGrid& g, double eps, cud
 }
 
 }  // namespace mmk
+
+extern "C" mm_status mm_diag_erf(const double* x_dev, double* y_fast_dev, double* y_lib_dev,
+                                 size_t n, void* cuda_stream) {
+  if (!x_dev || !y_fast_dev || !y_lib_dev) return MM_ERR_INVALID_ARG;
+  if (n == 0) return MM_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  mmk::k_diag_erf<<<152 * 4, 256, 0, s>>>(x_dev, y_fast_dev, y_lib_dev, n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? MM_OK : MM_ERR_CUDA;
+}
