@@ -60,7 +60,7 @@ __device__ __forceinline__ bool coll_half(const KParams& p, const double q[6], d
                                           double dt, double o[6], double& ir) {
   double rho, u1, u2, P11, P12, P22;
   prim6(q, rho, u1, u2, P11, P12, P22, ir);
-  const double T = (P11 + P22) * 0.5 / rho;
+  const double T = (P11 + P22) * (0.5 * ir);
   const bool ok = rho > 0.0 && T > 0.0 && isfinite(T) && isfinite(u1) && isfinite(u2) &&
                   isfinite(P12);
   const double a = tau_of(p, rho, T) * (1.0 - p.nu);
@@ -80,8 +80,8 @@ __device__ __forceinline__ bool coll_half(const KParams& p, const double q[6], d
 
 // a, b, J, K of Eq. (flux-2D-1) (dir 1) / (flux-2D-2) (dir 2) for the Gaussian with moments q:
 // a = sqrt(2 th/pi) exp(-u^2/(2 th)), b = erf(u/sqrt(2 th)), th = P_nn/rho (the normal
-// temperature); ir = 1/rho (from the caller, which has it already), one reciprocal of P_nn and
-// one reciprocal square root.
+// temperature); ir = 1/rho (from the caller, which has it already) and one reciprocal square
+// root h = 1/sqrt(2 th), from which 1/P_nn = 2 h^2 / rho (a few ulp, in a correction term of J).
 __device__ __forceinline__ void abJK(const double q[6], double ir, int dir, double& a, double& b,
                                      double J[6], double K[6]) {
   const double rho = q[0];
@@ -91,9 +91,9 @@ __device__ __forceinline__ void abJK(const double q[6], double ir, int dir, doub
   const double P22 = q[5] - rho * u2 * u2;
   const double Pn = dir == 1 ? P11 : P22;
   const double un = dir == 1 ? u1 : u2;
-  const double iPn = 1.0 / Pn;
   const double s2 = 2.0 * Pn * ir;  // 2 th
   const double h = rsqrt(s2);       // 1 / sqrt(2 th)
+  const double iPn = 2.0 * (h * h) * ir;
   a = kInvSqrtPi * (s2 * h) * expd(-(un * h) * (un * h));
   b = erfd(un * h);
   if (dir == 1) {
@@ -386,8 +386,11 @@ __device__ __forceinline__ void prims_f32_body(const double* MMK_R Q, const doub
   const float dTdy = (float)((0.5 * (TT + T) - 0.5 * (T + TB)) * g.idy);
   const float sg11 = (float)((uR1 - uL1) * 0.5 * g.idx - (uT2 - uB2) * 0.5 * g.idy);
   const float sg12 = (float)((uT1 - uB1) * 0.5 * g.idy + (uR2 - uL2) * 0.5 * g.idx);
-  const double idet = 1.0 / det, iTd = 1.0 / T;
-  const float KG = (float)(rho * kInv2Pi * rsqrt(det));
+  // reciprocals through reciprocal square roots (a few FP64 ulp, far below the FP32 rounding
+  // that follows; cheaper than divisions on the FP64 pipe)
+  const double rsd = rsqrt(det), rsT = rsqrt(T);
+  const double idet = rsd * rsd, iTd = rsT * rsT;
+  const float KG = (float)(rho * kInv2Pi * rsd);
   const float iT = (float)iTd;
   const float kap = (float)(dt * g.dv1 * g.dv2 * kInv2Pi * iTd);
   const float tau = (float)tau_of(p, rho, T);
